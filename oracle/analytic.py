@@ -1,0 +1,239 @@
+"""Closed forms and exact solves that pin the oracle and judge the method.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+* Neufeld / Harrington slab escape profile (Sec. 3.2, eq. Neufeld):
+  J(x, a tau0) = x^2 / (4 sqrt(6 pi) a tau0) sech(sqrt(pi^3/54) x^3 / (a tau0)),
+  normalised to 1/(4 pi).  Its bin masses have a closed form through the
+  Gudermannian gd(y) = 2 atan(tanh(y/2)): with c = sqrt(pi^3/54)/(a tau0) the
+  normalised CDF is 1/2 + gd(c x^3)/pi.
+* The DDMC walk with a fixed (quantised) table is an absorbing Markov chain
+  over states (cell, bin).  Expected visits v solve (I - P)^T v = s for the
+  source distribution s; expected escapes per state/outcome are v_s q_so; the
+  mean and second moment of the number of transitions solve (I - P) t = 1 and
+  (I - P) m2 = 2 t - 1.  This is exact for the walk, up to linear-algebra
+  rounding, with no Monte Carlo noise.
+* Quadrature references for the Dawson integral, the Voigt function of eq. H
+  (also through the Faddeeva function, H(a,x) = Re w(x + i a)) and bin means.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.integrate as si
+import scipy.optimize as so
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+import scipy.special as ss
+
+TWO32 = 4294967296.0
+ACT_MOVE, ACT_ESCAPE, ACT_TO_MC, ACT_REBIN = 0, 1, 2, 3
+FLAG_MOVING = 1 << 30
+FLAG_THIN = 1 << 31
+
+
+# --------------------------------------------------------------------------- Neufeld profile
+def neufeld_J(x, atau0):
+    """Angle-averaged escaping intensity of a static slab, eq. Neufeld."""
+    x = np.asarray(x, dtype=np.float64)
+    c = np.sqrt(np.pi ** 3 / 54.0) / atau0
+    return x * x / (4.0 * np.sqrt(6.0 * np.pi) * atau0) / np.cosh(c * x ** 3)
+
+
+def neufeld_cdf(x, atau0):
+    """Normalised CDF of 4 pi J(x): 1/2 + gd(c x^3)/pi = (2/pi) atan(exp(c x^3))."""
+    c = np.sqrt(np.pi ** 3 / 54.0) / atau0
+    y = c * np.asarray(x, dtype=np.float64) ** 3
+    return 2.0 / np.pi * np.arctan(np.exp(y))
+
+
+def neufeld_bin_mass(edges, atau0):
+    """Probability that an escaping photon falls in each bin of ``edges``.
+
+    Differences are taken of the lower tail (2/pi) atan(e^y) left of line centre
+    and of the upper tail (2/pi) atan(e^-y) right of it, so far-wing bins keep
+    full relative precision."""
+    c = np.sqrt(np.pi ** 3 / 54.0) / atau0
+    y = c * np.asarray(edges, dtype=np.float64) ** 3
+    lo = 2.0 / np.pi * np.arctan(np.exp(np.minimum(y, 0.0)))      # F(x) for x <= 0
+    up = 2.0 / np.pi * np.arctan(np.exp(-np.maximum(y, 0.0)))     # 1 - F(x) for x >= 0
+    F = np.where(y <= 0.0, lo, 1.0 - up)
+    mass = np.diff(F)
+    right = y[:-1] >= 0.0
+    left = y[1:] <= 0.0
+    mass[right] = up[:-1][right] - up[1:][right]
+    mass[left] = lo[1:][left] - lo[:-1][left]
+    return mass
+
+
+def neufeld_peak(atau0):
+    """Peak location and height: xbar tanh xbar = 2/3 with xbar = sqrt(pi^3/54) x^3 / (a tau0).
+
+    Returns (xbar, x_p, J(x_p))."""
+    xbar = so.brentq(lambda v: v * np.tanh(v) - 2.0 / 3.0, 0.1, 5.0, xtol=1e-15)
+    x_p = (xbar * atau0 / np.sqrt(np.pi ** 3 / 54.0)) ** (1.0 / 3.0)
+    return xbar, x_p, float(neufeld_J(x_p, atau0))
+
+
+# --------------------------------------------------------------------------- quadrature references
+def dawson_quad(x):
+    """F(x) = int_0^x exp(y^2 - x^2) dy by adaptive quadrature of the definition."""
+    x = float(x)
+    if x == 0.0:
+        return 0.0
+    val, _ = si.quad(lambda y: np.exp((y - x) * (y + x)), 0.0, x, epsabs=0.0, epsrel=1e-13, limit=400)
+    return val
+
+
+def voigt_faddeeva(a, x):
+    """H(a,x) = Re w(x + i a): the exact Voigt-Hjerting function of eq. H."""
+    return np.real(ss.wofz(np.asarray(x, dtype=np.float64) + 1j * a))
+
+
+def voigt_quad(a, x):
+    """H(a,x) = (a/pi) int exp(-y^2) / (a^2 + (y-x)^2) dy by quadrature (eq. H)."""
+    f = lambda y: np.exp(-y * y) / (a * a + (y - x) ** 2)
+    pts = sorted({-6.0, x - 50 * a, x, x + 50 * a, 6.0})
+    pts = [p for p in pts if -8.0 <= p <= 8.0]
+    val, _ = si.quad(f, -8.0, 8.0, points=pts, epsabs=0.0, epsrel=1e-12, limit=800)
+    return a / np.pi * val
+
+
+def bin_mean_quad(Hfun, a, xlo, xhi):
+    val, _ = si.quad(lambda y: Hfun(a, y), xlo, xhi, epsabs=0.0, epsrel=1e-12, limit=400)
+    return val / (xhi - xlo)
+
+
+# --------------------------------------------------------------------------- exact absorbing chain
+def quantised_probs(thr: np.ndarray) -> np.ndarray:
+    """Per-state outcome probabilities implied by the cumulative thresholds: shape (S, K)."""
+    S, Km1 = thr.shape
+    c = np.concatenate([np.zeros((S, 1)), thr.astype(np.float64), np.full((S, 1), TWO32)], axis=1)
+    return np.diff(c, axis=1) / TWO32
+
+
+def source_states(w, edges=None):
+    """States and probabilities of the centre source: the centre cell(s) (both
+    neighbours of the midplane for even counts) and the bin(s) containing x0."""
+    cells = []
+    for a in range(3):
+        m = w.n[a]
+        cells.append([m // 2] if m % 2 else [m // 2 - 1, m // 2])
+    e = w.edges() if edges is None else np.asarray(edges)
+    bins = [j for j in range(1, w.J) if e[j] == w.x0]
+    bins = [bins[0] - 1, bins[0]] if bins else [j for j in range(w.J) if e[j] < w.x0 < e[j + 1]]
+    states, probs = [], []
+    n0, n1 = w.n[0], w.n[1]
+    for i2 in cells[2]:
+        for i1 in cells[1]:
+            for i0 in cells[0]:
+                c = i0 + n0 * (i1 + n1 * i2)
+                for j in bins:
+                    states.append(c * w.J + j)
+                    probs.append(1.0 / (len(cells[0]) * len(cells[1]) * len(cells[2]) * len(bins)))
+    return np.array(states, dtype=np.int64), np.array(probs)
+
+
+def _neighbour(w, c, axis, side):
+    n = w.n
+    idx = [c % n[0], (c // n[0]) % n[1], c // (n[0] * n[1])]
+    idx[axis] += side
+    if idx[axis] < 0 or idx[axis] >= n[axis]:
+        return -1
+    return idx[0] + n[0] * (idx[1] + n[1] * idx[2])
+
+
+def chain_solve(w, table, edges=None):
+    """Exact expectations of the DDMC walk on a quantised table.
+
+    Returns a dict with the expected escape histogram per emitted packet (J+2
+    bins, static cells only), expected escapes per face, escapes per
+    (state, outcome), the mean and variance of the number of transitions."""
+    J, K = w.J, 2 + 2 * w.ndim
+    thr, flags = table["thr"], table["flags"]
+    S = thr.shape[0]
+    q = quantised_probs(thr)
+    nf = 2 * w.ndim
+    rows, cols, vals = [], [], []
+    esc = np.zeros((S, K))
+    for s in range(S):
+        c, j = divmod(s, J)
+        fl = int(flags[s])
+        for o in range(K):
+            p = q[s, o]
+            if p == 0.0:
+                continue
+            act = (fl >> (2 * o)) & 3
+            if act == ACT_ESCAPE:
+                esc[s, o] = p
+                continue
+            if act == ACT_TO_MC:
+                raise ValueError("chain_solve handles DDMC-only tables")
+            if o < 2:
+                rows.append(s); cols.append(s + (1 if o else -1)); vals.append(p)
+                continue
+            face = o - 2
+            nb = _neighbour(w, c, face // 2, 1 if face & 1 else -1)
+            if act == ACT_MOVE:
+                rows.append(s); cols.append(nb * J + j); vals.append(p)
+            else:
+                m = int(table["rebin_m"][c * nf + face])
+                pr = float(table["rebin_thr"][c * nf + face]) / TWO32
+                for jn, pj in ((j + m, pr), (j + m + 1, 1.0 - pr)):
+                    jn = min(max(jn, 0), J - 1)
+                    if pj > 0:
+                        rows.append(s); cols.append(nb * J + jn); vals.append(p * pj)
+    P = sp.csr_matrix((vals, (rows, cols)), shape=(S, S))
+    A = (sp.identity(S, format="csr") - P).tocsc()
+    lu = spla.splu(A)
+    src_s, src_p = source_states(w, edges)
+    src = np.zeros(S)
+    src[src_s] = src_p
+    v = lu.solve(src, trans="T")
+    t = lu.solve(np.ones(S))
+    m2 = lu.solve(2.0 * t - 1.0)
+    mean = float(src @ t)
+    var = float(src @ m2) - mean * mean
+    esc_so = v[:, None] * esc
+    hist = np.zeros(J + 2)
+    faces = np.zeros(6)
+    for o in range(2, K):
+        faces[o - 2] = esc_so[:, o].sum()
+        per_state = esc_so[:, o].reshape(-1, J)
+        moving = (flags.reshape(-1, J) & FLAG_MOVING) != 0
+        hist[1:J + 1] += np.where(moving, 0.0, per_state).sum(axis=0)
+    return dict(hist=hist, faces=faces, esc_so=esc_so, visits=v, steps_mean=mean, steps_var=var,
+                escape_total=float(esc_so.sum()))
+
+
+# --------------------------------------------------------------------------- comparisons
+def l1_distance(p, q):
+    p = np.asarray(p, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    return float(np.abs(p / p.sum() - q / q.sum()).sum())
+
+
+def compare_counts_to_probs(counts, probs, n, min_expected=20.0):
+    """Bin-wise z-scores of multinomial counts against exact probabilities.
+
+    Returns (max |z|, fraction of bins with |z| > 3, chi2 p-value) over bins with
+    expected count >= min_expected (G12 reading of 'within 3 sigma')."""
+    counts = np.asarray(counts, dtype=np.float64)
+    probs = np.asarray(probs, dtype=np.float64)
+    e = n * probs
+    sel = e >= min_expected
+    z = (counts[sel] - e[sel]) / np.sqrt(e[sel] * (1.0 - probs[sel]))
+    chi2 = float(((counts[sel] - e[sel]) ** 2 / e[sel]).sum())
+    dof = max(int(sel.sum()) - 1, 1)
+    pval = float(ss.chdtrc(dof, chi2))
+    return float(np.abs(z).max()) if z.size else 0.0, float((np.abs(z) > 3).mean()) if z.size else 0.0, pval
+
+
+def compare_two_samples(c1, n1, c2, n2, min_expected=20.0):
+    """Bin-wise z-scores between two independent multinomial samples."""
+    c1 = np.asarray(c1, dtype=np.float64)
+    c2 = np.asarray(c2, dtype=np.float64)
+    p1, p2 = c1 / n1, c2 / n2
+    sel = (c1 + c2) * min(n1, n2) / (n1 + n2) >= min_expected
+    var = p1[sel] * (1 - p1[sel]) / n1 + p2[sel] * (1 - p2[sel]) / n2
+    z = (p1[sel] - p2[sel]) / np.sqrt(np.maximum(var, 1e-300))
+    return float(np.abs(z).max()) if z.size else 0.0, float((np.abs(z) > 3).mean()) if z.size else 0.0

@@ -1,0 +1,168 @@
+"""ctypes wrapper around the C oracle (``rddmc_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Functions mirror the C
+entry points; arrays are numpy.  Unit conversions the C code does not do
+(velocity in km/s -> Doppler units with v_th = 12.85 (T/1e4 K)^(1/2) km/s,
+Sec. 2.1) are done here, on the oracle side.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+
+class OrcGrid(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("J", ctypes.c_int32), ("hybrid", ctypes.c_int32),
+        ("R", ctypes.c_double), ("tau0", ctypes.c_double), ("T", ctypes.c_double),
+        ("tau_ddmc", ctypes.c_double), ("lam", ctypes.c_double), ("f_mu", ctypes.c_double),
+        ("edges", ctypes.c_void_p), ("n_rel", ctypes.c_void_p), ("u", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+    ]
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        d, u32, u64, i32, vp = ctypes.c_double, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+        for name in ("orc_dawson",):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [d]
+        for name in ("orc_voigt_H", "orc_voigt_Hint"):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [d, d]
+        L.orc_bin_mean_H.restype = d
+        L.orc_bin_mean_H.argtypes = [d, d, d]
+        L.orc_damping.restype = d
+        L.orc_damping.argtypes = [d]
+        L.orc_philox4x32_10.restype = None
+        L.orc_philox4x32_10.argtypes = [vp, vp, vp]
+        L.orc_build_table.restype = i32
+        L.orc_build_table.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, vp]
+        L.orc_tally_len.restype = i32
+        L.orc_tally_len.argtypes = [i32]
+        L.orc_walk_ddmc.restype = i32
+        L.orc_walk_ddmc.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, d, u64, u64, u64, u64, i32, i32, vp]
+        _LIB = L
+    return _LIB
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --------------------------------------------------------------------------- physics
+def damping(T: float) -> float:
+    return lib().orc_damping(float(T))
+
+
+def dawson(x):
+    f = lib().orc_dawson
+    return np.vectorize(lambda v: f(float(v)), otypes=[np.float64])(x)
+
+
+def voigt_H(a, x):
+    f = lib().orc_voigt_H
+    return np.vectorize(lambda v: f(float(a), float(v)), otypes=[np.float64])(x)
+
+
+def voigt_Hint(a, x):
+    f = lib().orc_voigt_Hint
+    return np.vectorize(lambda v: f(float(a), float(v)), otypes=[np.float64])(x)
+
+
+def bin_mean_H(a, xlo, xhi):
+    f = lib().orc_bin_mean_H
+    return np.vectorize(lambda l, h: f(float(a), float(l), float(h)), otypes=[np.float64])(xlo, xhi)
+
+
+def philox(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------- grid / table
+def vth_kms(T: float) -> float:
+    """Thermal velocity v_th = 12.85 (T/1e4 K)^(1/2) km/s (Sec. 2.1)."""
+    return 12.85 * np.sqrt(T / 1.0e4)
+
+
+class Grid:
+    """An oracle grid built from a workload; keeps the numpy buffers alive."""
+
+    def __init__(self, w, hybrid=False, tau_ddmc=5.0, lam=0.7104, f_mu=0.5, n_rel=None, edges=None):
+        self.w = w
+        e = w.edges() if edges is None else edges
+        self.edges = np.ascontiguousarray(e, dtype=np.float64)
+        self.n_rel = None if n_rel is None else np.ascontiguousarray(n_rel, dtype=np.float64)
+        v = w.velocity_kms()
+        self.u = None if v is None else np.ascontiguousarray(v / vth_kms(w.T), dtype=np.float64)
+        m = w.mask()
+        self.mask = None if m is None else np.ascontiguousarray(m, dtype=np.uint8)
+        g = OrcGrid()
+        g.ndim = w.ndim
+        for a in range(3):
+            g.n[a] = w.n[a]
+        g.J, g.hybrid = w.J, int(hybrid)
+        g.R, g.tau0, g.T = w.R, w.tau0, w.T
+        g.tau_ddmc, g.lam, g.f_mu = tau_ddmc, lam, f_mu
+        g.edges, g.n_rel, g.u, g.mask = (_ptr(self.edges), _ptr(self.n_rel), _ptr(self.u), _ptr(self.mask))
+        self.g = g
+        self.K = 2 + 2 * w.ndim
+        self.ncell = w.ncell
+        self.J = w.J
+
+    def table(self):
+        nS = self.ncell * self.J
+        K = self.K
+        t = dict(
+            thr=np.zeros(nS * (K - 1), dtype=np.uint32), flags=np.zeros(nS, dtype=np.uint32),
+            rebin_m=np.zeros(self.ncell * 2 * self.w.ndim, dtype=np.int32),
+            rebin_thr=np.zeros(self.ncell * 2 * self.w.ndim, dtype=np.uint32),
+            k=np.zeros(nS, dtype=np.float64), rate=np.zeros(nS * K, dtype=np.float64))
+        rc = lib().orc_build_table(ctypes.byref(self.g), _ptr(t["thr"]), _ptr(t["flags"]), _ptr(t["rebin_m"]),
+                                   _ptr(t["rebin_thr"]), _ptr(t["k"]), _ptr(t["rate"]))
+        if rc != 0:
+            raise RuntimeError(f"orc_build_table failed: {rc}")
+        t["thr"] = t["thr"].reshape(nS, K - 1)
+        t["rate"] = t["rate"].reshape(nS, K)
+        return t
+
+
+TALLY_NAMES = ["emitted", "escaped", "aborted", "steps", "mc_events", "conversions", "clamps", "draws"]
+
+
+def unpack_tally(t: np.ndarray, J: int) -> dict:
+    d = {name: int(t[i]) for i, name in enumerate(TALLY_NAMES)}
+    d["faces"] = t[8:14].astype(np.uint64).copy()
+    d["hist"] = t[14:14 + J + 2].astype(np.uint64).copy()
+    return d
+
+
+def walk(grid: Grid, table: dict, seed: int, p0: int, npk: int, max_steps: int = (1 << 62),
+         literal: bool = False, nthreads: int = 0) -> dict:
+    """Run packets [p0, p0+npk) of the DDMC walk; returns the integer tallies."""
+    if nthreads <= 0:
+        nthreads = os.cpu_count() or 1
+    L = lib().orc_tally_len(grid.J)
+    out = np.zeros(L, dtype=np.uint64)
+    thr = np.ascontiguousarray(table["thr"].ravel())
+    rate = np.ascontiguousarray(table["rate"].ravel())
+    rc = lib().orc_walk_ddmc(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
+                             _ptr(table["rebin_thr"]), _ptr(rate), float(grid.w.x0), int(seed), int(p0),
+                             int(npk), int(max_steps), int(literal), int(nthreads), _ptr(out))
+    if rc == -1:
+        raise ValueError("orc_walk_ddmc: bad input")
+    res = unpack_tally(out, grid.J)
+    res["status"] = rc
+    return res

@@ -1,0 +1,509 @@
+/*
+ * rddmc_oracle.c -- FP64 CPU oracle for resonant discrete diffusion Monte Carlo
+ * (Smith, Tsang, Bromm & Milosavljevic 2017, "Discrete diffusion Lyman alpha
+ * radiative transfer").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link or call this
+ * file: only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark use it.  It shares no code, header or constant table with the CUDA
+ * library; the two are written independently from the paper.
+ *
+ * Everything here is plain, slow, double precision and follows the paper's
+ * order of operations:
+ *   - Dawson integral F(x): Maclaurin series near 0, Rybicki's (1989,
+ *     Computers in Physics 3(2), 85) sampling-theorem series elsewhere.
+ *   - Hjerting-Voigt H(a,x) to second order in a, and its integral calH(a,x)
+ *     (Sec. 2.3, eq. H_approx and the integrated form below it).
+ *   - bin-mean opacity k_j = k0 (calH(x_j+) - calH(x_j-)) / dx_j (Sec. 2.3).
+ *   - leakage coefficients eq. z-leakage, eq. x-leakage; the hybrid
+ *     DDMC->MC boundary coefficient with extrapolation distance lambda (Sec. 5.1);
+ *     the comoving Doppler shift of bin edges across faces, eq. velocity-shift.
+ *   - Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011, SC'11).
+ *   - the DDMC walk of Sec. 2.4: the leakage with the smallest sampled distance
+ *     is executed.  Two forms are provided: the literal competing exponentials
+ *     (eq. l_min_1, l_min_2) and the equivalent categorical draw on quantised
+ *     cumulative probabilities, which defines the random-stream contract shared
+ *     (as a specification, not as code) with the GPU walk.
+ *
+ * Random-stream contract (fixed by this project; not in the paper):
+ *   key  = (seed_lo, seed_hi); for packet p and draw index n of that packet,
+ *   ctr  = ((n>>2)_lo, (n>>2)_hi, p_lo, p_hi); the 32-bit word is lane n&3 of
+ *   Philox4x32-10(ctr, key).  A uniform in (0,1) is (w + 0.5) * 2^-32.
+ *   Draw 0 of a packet picks the source cell/bin; every DDMC transition uses one
+ *   word; a Doppler rebin uses one more word; a DDMC escape from a moving cell
+ *   uses five more words (face point 2, mu, phi, x in bin).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_SQRTPI 1.77245385090551602730
+#define ORC_TWO32 4294967296.0
+
+/* ------------------------------------------------------------------------- */
+/* Physics (Sec. 2.1, Sec. 2.3)                                               */
+/* ------------------------------------------------------------------------- */
+
+/* Damping parameter a = 4.702e-4 * (T / 1e4 K)^(-1/2)  (Sec. 2.1). */
+double orc_damping(double T) { return 4.702e-4 / sqrt(T / 1.0e4); }
+
+/* Dawson integral F(x) = int_0^x exp(y^2 - x^2) dy.
+ * |x| < 0.2: Maclaurin series F(x) = sum_n (-1)^n 2^n x^(2n+1) / (2n+1)!!.
+ * otherwise: Rybicki (1989): F(x) = lim_{h->0} pi^(-1/2) sum_{n odd} e^{-(x-nh)^2}/n,
+ * re-centred on the even multiple n0 of h nearest to x, h = 0.2 (aliasing error
+ * ~ exp(-(pi/2h)^2) ~ 1e-27), terms with |n'| h <= 8.2 kept. */
+double orc_dawson(double x) {
+    double ax = fabs(x), sgn = (x < 0.0) ? -1.0 : 1.0;
+    if (ax < 0.2) {
+        double x2 = ax * ax, term = ax, sum = ax;
+        for (int n = 1; n < 40; ++n) {
+            term *= -2.0 * x2 / (2.0 * n + 1.0);
+            sum += term;
+            if (fabs(term) < 1e-18 * fabs(sum)) break;
+        }
+        return sgn * sum;
+    }
+    const double h = 0.2;
+    const int N = 41;
+    long n0 = 2L * lround(ax / (2.0 * h));
+    double xp = ax - (double)n0 * h;
+    double sum = 0.0;
+    for (int k = -N; k <= N; ++k) {
+        long np = 2L * k + 1L;
+        long den = np + n0;
+        if (den == 0) continue;
+        double d = xp - (double)np * h;
+        sum += exp(-d * d) / (double)den;
+    }
+    return sgn * sum / ORC_SQRTPI;
+}
+
+/* H(a,x) to second order in a (eq. H_approx). */
+double orc_voigt_H(double a, double x) {
+    double e = exp(-x * x);
+    return e + 2.0 * a / ORC_SQRTPI * (2.0 * x * orc_dawson(x) - 1.0) + a * a * e * (1.0 - 2.0 * x * x);
+}
+
+/* calH(a,x) = int_0^x H(a,y) dy = (sqrt(pi)/2) erf(x) - (2a/sqrt(pi)) F(x) + a^2 x e^{-x^2}. */
+double orc_voigt_Hint(double a, double x) {
+    return 0.5 * ORC_SQRTPI * erf(x) - 2.0 * a / ORC_SQRTPI * orc_dawson(x) + a * a * x * exp(-x * x);
+}
+
+/* Bin mean of H over [xlo, xhi]: (calH(xhi) - calH(xlo)) / (xhi - xlo).
+ * The erf difference is formed from erfc on the side away from line centre,
+ * where erf(x) -> 1 would cancel in double precision. */
+double orc_bin_mean_H(double a, double xlo, double xhi) {
+    double derf;
+    if (xlo >= 0.0)
+        derf = erfc(xlo) - erfc(xhi);
+    else if (xhi <= 0.0)
+        derf = erfc(-xhi) - erfc(-xlo);
+    else
+        derf = erf(xhi) - erf(xlo);
+    double dF = orc_dawson(xhi) - orc_dawson(xlo);
+    double dG = xhi * exp(-xhi * xhi) - xlo * exp(-xlo * xlo);
+    return (0.5 * ORC_SQRTPI * derf - 2.0 * a / ORC_SQRTPI * dF + a * a * dG) / (xhi - xlo);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al. 2011)                                        */
+/* ------------------------------------------------------------------------- */
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Word n of packet p's stream (see the contract in the header comment). */
+static uint32_t orc_word(uint64_t seed, uint64_t p, uint64_t n) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint64_t b = n >> 2;
+    uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), (uint32_t)p, (uint32_t)(p >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[n & 3];
+}
+
+static double orc_unif(uint32_t w) { return ((double)w + 0.5) / ORC_TWO32; }
+
+/* ------------------------------------------------------------------------- */
+/* Grid and leakage table (Sec. 2.3, Sec. 2.5, Sec. 5.1)                      */
+/* ------------------------------------------------------------------------- */
+
+typedef struct orc_grid {
+    int32_t ndim;     /* 1: slab (axis 0 only), 3: Cartesian cube */
+    int32_t n[3];     /* cells per axis; unused axes hold 1 */
+    int32_t J;        /* frequency bins */
+    int32_t hybrid;   /* 0: DDMC in every state; 1: thin states hand off to MC */
+    double R;         /* half-width of the domain [-R, R]^ndim */
+    double tau0;      /* k0 * R for unit density */
+    double T;         /* gas temperature (K), isothermal */
+    double tau_ddmc;  /* thick threshold on tau_ij = k_ij dz */
+    double lambda;    /* extrapolation distance of the DDMC->MC coefficient */
+    double f_mu;      /* flux directionality factor of eq. velocity-shift */
+    const double* edges;  /* J+1 ascending comoving frequency edges */
+    const double* n_rel;  /* per-cell density scale, NULL = 1 */
+    const double* u;      /* per-cell bulk velocity / v_th, 3 per cell, NULL = static */
+    const uint8_t* mask;  /* per-cell 1 = medium, 0 = vacuum, NULL = all medium */
+} orc_grid;
+
+/* Actions stored two bits per outcome in the flags word. */
+#define ORC_ACT_MOVE 0u
+#define ORC_ACT_ESCAPE 1u
+#define ORC_ACT_TO_MC 2u
+#define ORC_ACT_REBIN 3u
+#define ORC_FLAG_MOVING (1u << 30) /* the cell has non-zero bulk velocity */
+#define ORC_FLAG_THIN (1u << 31)   /* hybrid mode: the state is an MC state */
+
+static int64_t orc_ncell(const orc_grid* g) { return (int64_t)g->n[0] * g->n[1] * g->n[2]; }
+static int orc_nout(const orc_grid* g) { return 2 + 2 * g->ndim; }
+
+static int orc_in_medium(const orc_grid* g, const int idx[3]) {
+    for (int a = 0; a < 3; ++a)
+        if (idx[a] < 0 || idx[a] >= g->n[a]) return 0;
+    int64_t c = idx[0] + (int64_t)g->n[0] * (idx[1] + (int64_t)g->n[1] * idx[2]);
+    return g->mask ? (g->mask[c] != 0) : 1;
+}
+
+static int64_t orc_cell_of(const orc_grid* g, const int idx[3]) {
+    return idx[0] + (int64_t)g->n[0] * (idx[1] + (int64_t)g->n[1] * idx[2]);
+}
+
+static void orc_idx_of(const orc_grid* g, int64_t c, int idx[3]) {
+    idx[0] = (int)(c % g->n[0]);
+    idx[1] = (int)((c / g->n[0]) % g->n[1]);
+    idx[2] = (int)(c / ((int64_t)g->n[0] * g->n[1]));
+}
+
+/* Line-centre absorption coefficient k0 of cell c (tau0 = k0 R at unit density). */
+static double orc_k0(const orc_grid* g, int64_t c) {
+    return g->tau0 / g->R * (g->n_rel ? g->n_rel[c] : 1.0);
+}
+
+static double orc_dz(const orc_grid* g, int axis) { return 2.0 * g->R / g->n[axis]; }
+
+/* Comoving frequency shift for crossing from cell c to cell nb through the face
+ * with unit normal +/- e_axis: x' = x + f_mu n.(u_c - u_nb), the isothermal
+ * form of eq. velocity-shift. */
+static double orc_face_shift(const orc_grid* g, int64_t c, int64_t nb, int axis, int side) {
+    if (!g->u) return 0.0;
+    double du = g->u[3 * c + axis] - g->u[3 * nb + axis];
+    return g->f_mu * (double)side * du;
+}
+
+/* Quantise a cumulative probability to a 32-bit threshold: round half to even
+ * of C * 2^32, saturating at 2^32 - 1 so that the last outcome always keeps at
+ * least one count. */
+static uint32_t orc_quantise(double C) {
+    double t = nearbyint(C * ORC_TWO32);
+    if (t < 0.0) t = 0.0;
+    if (t > ORC_TWO32 - 1.0) t = ORC_TWO32 - 1.0;
+    return (uint32_t)t;
+}
+
+/*
+ * Build the dense leakage table: one row per state s = c*J + j.
+ * Outcome order: 0 bin-1, 1 bin+1, then for each axis a: 2+2a (-e_a), 3+2a (+e_a).
+ * thr[s*(K-1) + k]: quantised cumulative probability of outcomes 0..k.
+ * flags[s]: 2-bit action per outcome, ORC_FLAG_MOVING, ORC_FLAG_THIN.
+ * rebin_m / rebin_thr [c*2*ndim + face]: Doppler rebin of uniform bins across
+ *   that face (new bin = j + m + [w >= thr]); face = 2a + (side > 0).
+ * k_out (optional): k_ij.  rate_out (optional): the K leakage coefficients.
+ * Returns 0, or -1 for an unsupported grid.
+ */
+int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* rebin_m,
+                    uint32_t* rebin_thr, double* k_out, double* rate_out) {
+    if (g->ndim != 1 && g->ndim != 3) return -1;
+    const int J = g->J, K = orc_nout(g);
+    const int64_t nc = orc_ncell(g);
+    const double a = orc_damping(g->T);
+    double* phi = (double*)malloc(sizeof(double) * J);
+    for (int j = 0; j < J; ++j) phi[j] = orc_bin_mean_H(a, g->edges[j], g->edges[j + 1]);
+    double dzmin = 1e300;
+    for (int ax = 0; ax < g->ndim; ++ax) dzmin = fmin(dzmin, orc_dz(g, ax));
+
+    for (int64_t c = 0; c < nc; ++c) {
+        int idx[3];
+        orc_idx_of(g, c, idx);
+        const double k0c = orc_k0(g, c);
+        int moving = 0;
+        if (g->u)
+            for (int ax = 0; ax < 3; ++ax) moving |= (g->u[3 * c + ax] != 0.0);
+        /* Doppler rebin per face, uniform bins assumed (checked by the caller). */
+        double dx0 = g->edges[1] - g->edges[0];
+        for (int ax = 0; ax < g->ndim; ++ax)
+            for (int sd = 0; sd < 2; ++sd) {
+                int side = sd ? 1 : -1, nidx[3] = {idx[0], idx[1], idx[2]};
+                nidx[ax] += side;
+                double delta = 0.0;
+                if (orc_in_medium(g, idx) && orc_in_medium(g, nidx))
+                    delta = orc_face_shift(g, c, orc_cell_of(g, nidx), ax, side);
+                double q = delta / dx0, m = floor(q), f = q - m;
+                rebin_m[c * 2 * g->ndim + 2 * ax + sd] = (int32_t)m;
+                rebin_thr[c * 2 * g->ndim + 2 * ax + sd] = orc_quantise(1.0 - f);
+            }
+        for (int j = 0; j < J; ++j) {
+            const int64_t s = c * J + j;
+            const double dxj = g->edges[j + 1] - g->edges[j];
+            const double k = k0c * phi[j];
+            double rate[8] = {0};
+            unsigned act[8] = {0};
+            int thin = g->hybrid && (k * dzmin < g->tau_ddmc);
+            /* frequency leakage, eq. x-leakage; no flux beyond the grid ends */
+            for (int sd = 0; sd < 2; ++sd) {
+                int jn = j + (sd ? 1 : -1);
+                if (jn < 0 || jn >= J) { rate[sd] = 0.0; act[sd] = ORC_ACT_MOVE; continue; }
+                double dxn = g->edges[jn + 1] - g->edges[jn];
+                double kn = k0c * phi[jn];
+                rate[sd] = 1.0 / (dxj * (dxj / k + dxn / kn));
+                act[sd] = (g->hybrid && kn * dzmin < g->tau_ddmc) ? ORC_ACT_TO_MC : ORC_ACT_MOVE;
+            }
+            /* spatial leakage, eq. z-leakage; exterior and thin neighbours use
+             * the extrapolation-distance form of Sec. 5.1 */
+            for (int ax = 0; ax < g->ndim; ++ax) {
+                const double dz = orc_dz(g, ax);
+                for (int sd = 0; sd < 2; ++sd) {
+                    int side = sd ? 1 : -1, o = 2 + 2 * ax + sd, nidx[3] = {idx[0], idx[1], idx[2]};
+                    nidx[ax] += side;
+                    double r_bnd = 1.0 / (3.0 * dz) * 2.0 / (k * dz + 2.0 * g->lambda);
+                    if (!orc_in_medium(g, nidx)) { rate[o] = r_bnd; act[o] = ORC_ACT_ESCAPE; continue; }
+                    int64_t nb = orc_cell_of(g, nidx);
+                    double delta = orc_face_shift(g, c, nb, ax, side);
+                    double knb = orc_k0(g, nb) *
+                                 (delta == 0.0 ? phi[j]
+                                               : orc_bin_mean_H(a, g->edges[j] + delta, g->edges[j + 1] + delta));
+                    double dznb = dz;
+                    if (g->hybrid && knb * dznb < g->tau_ddmc) { rate[o] = r_bnd; act[o] = ORC_ACT_TO_MC; continue; }
+                    rate[o] = 1.0 / (3.0 * dz) * 2.0 / (k * dz + knb * dznb);
+                    act[o] = (delta != 0.0) ? ORC_ACT_REBIN : ORC_ACT_MOVE;
+                }
+            }
+            double tot = 0.0;
+            for (int o = 0; o < K; ++o) tot += rate[o];
+            double C = 0.0;
+            for (int o = 0; o < K - 1; ++o) {
+                C += rate[o] / tot;
+                thr[s * (K - 1) + o] = orc_quantise(C);
+            }
+            uint32_t fl = 0;
+            for (int o = 0; o < K; ++o) fl |= (act[o] & 3u) << (2 * o);
+            if (moving) fl |= ORC_FLAG_MOVING;
+            if (thin) fl |= ORC_FLAG_THIN;
+            flags[s] = fl;
+            if (k_out) k_out[s] = k;
+            if (rate_out)
+                for (int o = 0; o < K; ++o) rate_out[s * K + o] = rate[o];
+        }
+    }
+    free(phi);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Walk (Sec. 2.4)                                                           */
+/* ------------------------------------------------------------------------- */
+
+/* Tally layout (uint64): see ORC_T_* ; faces [ORC_T_FACE, +6); histogram of
+ * escape frequency [ORC_T_HIST, +J+2) with 0 = below the grid, J+1 = above. */
+#define ORC_T_EMITTED 0
+#define ORC_T_ESCAPED 1
+#define ORC_T_ABORTED 2
+#define ORC_T_STEPS 3
+#define ORC_T_MC_EVENTS 4
+#define ORC_T_CONVERSIONS 5
+#define ORC_T_CLAMPS 6
+#define ORC_T_DRAWS 7
+#define ORC_T_FACE 8
+#define ORC_T_HIST 14
+
+int orc_tally_len(int J) { return ORC_T_HIST + J + 2; }
+
+/* Source: the cell(s) at the domain centre and the bin(s) containing x0.  With
+ * an even count the centre is a face/edge and both neighbours are used with
+ * equal probability (the paper enforces odd counts instead). */
+typedef struct orc_source {
+    int ncand[3];
+    int cand[3][2];
+    int nbin;
+    int bin[2];
+} orc_source;
+
+static int orc_make_source(const orc_grid* g, double x0, orc_source* src) {
+    for (int ax = 0; ax < 3; ++ax) {
+        int n = g->n[ax];
+        if (n % 2) { src->ncand[ax] = 1; src->cand[ax][0] = src->cand[ax][1] = n / 2; }
+        else { src->ncand[ax] = 2; src->cand[ax][0] = n / 2 - 1; src->cand[ax][1] = n / 2; }
+    }
+    src->nbin = 0;
+    for (int j = 1; j < g->J; ++j)
+        if (g->edges[j] == x0) { src->nbin = 2; src->bin[0] = j - 1; src->bin[1] = j; }
+    if (!src->nbin) {
+        for (int j = 0; j < g->J; ++j)
+            if (g->edges[j] < x0 && x0 < g->edges[j + 1]) { src->nbin = 1; src->bin[0] = src->bin[1] = j; }
+    }
+    return src->nbin ? 0 : -1;
+}
+
+/* Draw 0: bit 31-a picks the cell along axis a (a = 0,1,2), bit 28 picks the bin. */
+static void orc_emit(const orc_source* src, uint32_t w, int idx[3], int* j) {
+    for (int ax = 0; ax < 3; ++ax) idx[ax] = src->cand[ax][src->ncand[ax] == 2 ? (w >> (31 - ax)) & 1u : 0];
+    *j = src->bin[src->nbin == 2 ? (w >> 28) & 1u : 0];
+}
+
+typedef struct orc_walk_args {
+    const orc_grid* g;
+    const uint32_t* thr;
+    const uint32_t* flags;
+    const int32_t* rebin_m;
+    const uint32_t* rebin_thr;
+    const double* rate;  /* for the competing-exponentials form */
+    const orc_source* src;
+    uint64_t seed, p0, p1, max_steps;
+    int literal;         /* 1: competing exponentials in FP64 (eq. l_min_1/2) */
+    uint64_t* tally;     /* per-thread */
+    int status;
+} orc_walk_args;
+
+/* Escape through the face of outcome o from cell c at bin j: tally the
+ * observer-frame frequency.  Static cell: the packet's bin.  Moving cell: a
+ * point on the face, an isotropic outward direction (mu uniform on (0,1],
+ * azimuth uniform) and x uniform in the bin; x_obs = x + n.u_c. */
+static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t pk, uint64_t* n, uint64_t* t) {
+    const orc_grid* g = A->g;
+    const int J = g->J;
+    int face = o - 2;
+    t[ORC_T_ESCAPED]++;
+    t[ORC_T_FACE + face]++;
+    if (!(A->flags[c * J + j] & ORC_FLAG_MOVING)) { t[ORC_T_HIST + 1 + j]++; return; }
+    /* face point (2 words) is drawn for the position tally; unused here */
+    (void)orc_word(A->seed, pk, (*n)++);
+    (void)orc_word(A->seed, pk, (*n)++);
+    double mu = 1.0 - orc_unif(orc_word(A->seed, pk, (*n)++));
+    double ph = 2.0 * ORC_PI * orc_unif(orc_word(A->seed, pk, (*n)++));
+    double xu = orc_unif(orc_word(A->seed, pk, (*n)++));
+    double x = g->edges[j] + xu * (g->edges[j + 1] - g->edges[j]);
+    int ax = face / 2, side = (face & 1) ? 1 : -1;
+    int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    double nu = side * mu * g->u[3 * c + ax] + st * (cos(ph) * g->u[3 * c + t1] + sin(ph) * g->u[3 * c + t2]);
+    double xo = x + nu;
+    int b;
+    if (xo < g->edges[0]) b = 0;
+    else if (xo >= g->edges[J]) b = J + 1;
+    else {
+        b = 1;
+        while (b < J && xo >= g->edges[b]) ++b;
+    }
+    t[ORC_T_HIST + b]++;
+}
+
+static void* orc_walk_thread(void* vp) {
+    orc_walk_args* A = (orc_walk_args*)vp;
+    const orc_grid* g = A->g;
+    const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim;
+    uint64_t* t = A->tally;
+    for (uint64_t pk = A->p0; pk < A->p1; ++pk) {
+        uint64_t n = 0, steps = 0;
+        int idx[3], j;
+        orc_emit(A->src, orc_word(A->seed, pk, n++), idx, &j);
+        t[ORC_T_EMITTED]++;
+        int64_t c = orc_cell_of(g, idx);
+        for (;;) {
+            if (steps >= A->max_steps) { t[ORC_T_ABORTED]++; break; }
+            const int64_t s = c * J + j;
+            if (A->flags[s] & ORC_FLAG_THIN) { A->status = -2; t[ORC_T_ABORTED]++; break; }
+            int o;
+            if (!A->literal) {
+                /* categorical draw: outcome o iff thr[o-1] <= w < thr[o] */
+                uint32_t w = orc_word(A->seed, pk, n++);
+                o = 0;
+                while (o < K - 1 && w >= A->thr[s * (K - 1) + o]) ++o;
+            } else {
+                /* eq. l_min_2: dl_X = -ln(xi)/k_X for every process; eq. l_min_1: execute the smallest */
+                double best = INFINITY;
+                o = -1;
+                for (int q = 0; q < K; ++q) {
+                    double xi = orc_unif(orc_word(A->seed, pk, n++));
+                    double kx = A->rate[s * K + q];
+                    if (kx <= 0.0) continue;
+                    double dl = -log(xi) / kx;
+                    if (dl < best) { best = dl; o = q; }
+                }
+            }
+            ++steps;
+            t[ORC_T_STEPS]++;
+            unsigned act = (A->flags[s] >> (2 * o)) & 3u;
+            if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, j, o, pk, &n, t); break; }
+            if (act == ORC_ACT_TO_MC) { A->status = -2; t[ORC_T_ABORTED]++; break; }
+            if (o < 2) { j += o ? 1 : -1; continue; }
+            int face = o - 2, ax = face / 2, side = (face & 1) ? 1 : -1;
+            if (act == ORC_ACT_REBIN) {
+                uint32_t w1 = orc_word(A->seed, pk, n++);
+                int jn = j + A->rebin_m[c * nf + face] + (w1 >= A->rebin_thr[c * nf + face] ? 1 : 0);
+                if (jn < 0) { jn = 0; t[ORC_T_CLAMPS]++; }
+                if (jn > J - 1) { jn = J - 1; t[ORC_T_CLAMPS]++; }
+                j = jn;
+            }
+            idx[ax] += side;
+            c = orc_cell_of(g, idx);
+        }
+        t[ORC_T_DRAWS] += n;
+    }
+    return NULL;
+}
+
+/*
+ * Run packets [p0, p0+np) of the DDMC walk on a table built by orc_build_table.
+ * literal = 0: categorical draw on the quantised thresholds (the stream contract);
+ * literal = 1: competing exponentials on the FP64 rates (a different stream use,
+ *              equal in distribution up to the quantisation of the thresholds).
+ * tally must hold orc_tally_len(J) words; it is overwritten.
+ * Returns 0, -1 on bad input, -2 if a packet met a thin (MC) state: the hybrid
+ * walk is orc_hybrid_walk_slab.
+ */
+int orc_walk_ddmc(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
+                  const uint32_t* rebin_thr, const double* rate, double x0, uint64_t seed, uint64_t p0,
+                  uint64_t np, uint64_t max_steps, int literal, int nthreads, uint64_t* tally) {
+    orc_source src;
+    if (orc_make_source(g, x0, &src)) return -1;
+    if (literal && !rate) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if ((uint64_t)nthreads > np) nthreads = np ? (int)np : 1;
+    const int L = orc_tally_len(g->J);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
+    orc_walk_args* args = (orc_walk_args*)calloc(nthreads, sizeof(orc_walk_args));
+    uint64_t* tl = (uint64_t*)calloc((size_t)nthreads * L, sizeof(uint64_t));
+    for (int i = 0; i < nthreads; ++i) {
+        orc_walk_args* A = &args[i];
+        A->g = g; A->thr = thr; A->flags = flags; A->rebin_m = rebin_m; A->rebin_thr = rebin_thr;
+        A->rate = rate; A->src = &src; A->seed = seed; A->max_steps = max_steps; A->literal = literal;
+        A->p0 = p0 + np * (uint64_t)i / nthreads;
+        A->p1 = p0 + np * (uint64_t)(i + 1) / nthreads;
+        A->tally = tl + (size_t)i * L;
+        pthread_create(&th[i], NULL, orc_walk_thread, A);
+    }
+    int status = 0;
+    memset(tally, 0, sizeof(uint64_t) * L);
+    for (int i = 0; i < nthreads; ++i) {
+        pthread_join(th[i], NULL);
+        for (int q = 0; q < L; ++q) tally[q] += tl[(size_t)i * L + q];
+        if (args[i].status) status = args[i].status;
+    }
+    free(th); free(args); free(tl);
+    return status;
+}

@@ -1,0 +1,98 @@
+"""Seeded synthetic workloads (grids, media, sources) shared by the tests, the
+benchmark, the CUDA path and the CPU oracle.
+
+This module only *describes inputs*: grid sizes, frequency edges, densities,
+velocities and seeds.  It holds none of the method's arithmetic (no opacities,
+leakage coefficients or random walks), so both implementations may use it.
+
+Slab workloads follow Sec. 3.2 / Sec. 4.2 of Smith et al. (2017): a uniform,
+static, isothermal slab |z| <= R with a monochromatic line-centre source at the
+midplane.  P1 is the setup of Fig. 2 (a tau0 = 1e9, T = 10 K,
+dz ~ 0.01 R, dx ~ 0.05 (a tau0)^(1/3) over |x| <= 2.5 (a tau0)^(1/3)); P2 is the
+coarser matched resolution n_z = 101, n_x = 51 suggested in Sec. 4.2.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional, Tuple
+
+import numpy as np
+
+GEOM_SLAB_1D = 1
+GEOM_CART_3D = 3
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    ndim: int                 # 1 = slab along one axis, 3 = Cartesian cube
+    n: Tuple[int, int, int]   # cells per axis (unused axes 1)
+    J: int                    # frequency bins
+    x_min: float              # comoving frequency range in Doppler widths
+    x_max: float
+    tau0: float               # k0 * R at unit density (line-centre optical depth)
+    T: float                  # K, isothermal
+    packets: int
+    seed: int
+    R: float = 1.0
+    x0: float = 0.0           # source frequency
+    sphere: bool = False      # 3D: medium only in cells whose centre has r < R
+    vmax_kms: float = 0.0     # 3D Hubble-like outflow v = vmax * r / R
+    atau0_nominal: Optional[float] = None  # the a*tau0 the config is quoted at
+
+    @property
+    def ncell(self) -> int:
+        return int(self.n[0] * self.n[1] * self.n[2])
+
+    def edges(self) -> np.ndarray:
+        """J+1 uniform bin edges over [x_min, x_max] (float64)."""
+        return np.linspace(self.x_min, self.x_max, self.J + 1, dtype=np.float64)
+
+    def cell_centres(self) -> np.ndarray:
+        """Cell-centre coordinates, shape (ncell, 3), axis 0 fastest; unused axes 0."""
+        axes = []
+        for a in range(3):
+            if a < self.ndim:
+                m = self.n[a]
+                axes.append(-self.R + (np.arange(m) + 0.5) * (2.0 * self.R / m))
+            else:
+                axes.append(np.zeros(1))
+        z, y, x = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+        return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+    def mask(self) -> Optional[np.ndarray]:
+        """uint8 medium mask (1 = medium, 0 = vacuum), or None for a full grid."""
+        if not self.sphere:
+            return None
+        r = np.linalg.norm(self.cell_centres(), axis=1)
+        return (r < self.R).astype(np.uint8)
+
+    def velocity_kms(self) -> Optional[np.ndarray]:
+        """Per-cell bulk velocity in km/s, shape (ncell, 3), or None if static."""
+        if self.vmax_kms == 0.0:
+            return None
+        return (self.vmax_kms * self.cell_centres() / self.R).astype(np.float64)
+
+    def with_(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+
+# k0 R for a tau0 = 1e9 at T = 10 K: a(10 K) = 4.702e-4 * (1e-3)^(-1/2) = 1.48691e-2.
+_TAU0_ATAU1E9_T10 = 6.725395e10
+
+C1 = Workload("slab_tau1e5_64x128", 1, (64, 1, 1), 128, -30.0, 30.0, 1.0e5, 1.0e4, 100_000, 0x5EED0001)
+C2 = Workload("slab_tau1e7_256x512", 1, (256, 1, 1), 512, -60.0, 60.0, 1.0e7, 1.0e4, 10_000_000, 0x5EED0002)
+P1 = Workload("slab_atau1e9_T10_201x101", 1, (201, 1, 1), 101, -2500.0, 2500.0, _TAU0_ATAU1E9_T10, 10.0,
+              1_000_000, 0x5EED0011, atau0_nominal=1.0e9)
+P2 = Workload("slab_atau1e9_T10_101x51", 1, (101, 1, 1), 51, -2500.0, 2500.0, _TAU0_ATAU1E9_T10, 10.0,
+              1_000_000, 0x5EED0012, atau0_nominal=1.0e9)
+C3 = Workload("sphere_tau1e7_64c_128b", 3, (64, 64, 64), 128, -80.0, 80.0, 1.0e7, 1.0e4, 10_000_000,
+              0x5EED0003, sphere=True)
+
+# Small grids for parity tests: several row tiles and ragged sizes, cheap enough
+# for the oracle to finish in seconds.
+TINY = Workload("slab_tiny_8x16", 1, (8, 1, 1), 16, -8.0, 8.0, 2.0e2, 1.0e4, 20_000, 0x5EED0101)
+SMALL = Workload("slab_small_13x37", 1, (13, 1, 1), 37, -12.0, 12.0, 1.0e3, 1.0e4, 20_000, 0x5EED0102)
+GREY_LIKE = Workload("slab_wide_bins_31x9", 1, (31, 1, 1), 9, -90.0, 90.0, 3.0e4, 1.0e4, 20_000, 0x5EED0103)
+
+ALL = {w.name: w for w in (C1, C2, P1, P2, C3, TINY, SMALL, GREY_LIKE)}
