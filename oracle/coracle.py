@@ -139,7 +139,7 @@ class Grid:
         return t
 
 
-TALLY_NAMES = ["emitted", "escaped", "aborted", "steps", "mc_events", "conversions", "clamps", "draws"]
+TALLY_NAMES = ["emitted", "escaped", "aborted", "steps", "mc_events", "conversions", "clamps", "event_draws"]
 
 
 def unpack_tally(t: np.ndarray, J: int) -> dict:

@@ -26,12 +26,15 @@
  *     (as a specification, not as code) with the GPU walk.
  *
  * Random-stream contract (fixed by this project; not in the paper):
- *   key  = (seed_lo, seed_hi); for packet p and draw index n of that packet,
- *   ctr  = ((n>>2)_lo, (n>>2)_hi, p_lo, p_hi); the 32-bit word is lane n&3 of
- *   Philox4x32-10(ctr, key).  A uniform in (0,1) is (w + 0.5) * 2^-32.
- *   Draw 0 of a packet picks the source cell/bin; every DDMC transition uses one
- *   word; a Doppler rebin uses one more word; a DDMC escape from a moving cell
- *   uses five more words (face point 2, mu, phi, x in bin).
+ *   key = (seed_lo, seed_hi).  Each packet p (< 2^63) owns two streams of 32-bit
+ *   words, selected by the top bit of the last counter word:
+ *     transition stream: transition t of p uses lane t&3 of
+ *       Philox4x32-10(ctr = ((t>>2)_lo, (t>>2)_hi, p_lo, p_hi), key);
+ *     event stream: event draw e of p uses lane e&3 of
+ *       Philox4x32-10(ctr = ((e>>2)_lo, (e>>2)_hi, p_lo, p_hi | 2^31), key).
+ *   Event draw 0 picks the source cell/bin; a Doppler rebin takes the next event
+ *   draw; a DDMC escape from a moving cell takes five (face point 2, mu, phi,
+ *   x in bin).  A uniform in (0,1) is (w + 0.5) * 2^-32.
  */
 #include <math.h>
 #include <pthread.h>
@@ -129,15 +132,19 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Word n of packet p's stream (see the contract in the header comment). */
-static uint32_t orc_word(uint64_t seed, uint64_t p, uint64_t n) {
+/* Word n of stream `which` (0 transitions, 1 events) of packet p (see the
+ * contract in the header comment). */
+static uint32_t orc_word(uint64_t seed, uint64_t p, int which, uint64_t n) {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint64_t b = n >> 2;
-    uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), (uint32_t)p, (uint32_t)(p >> 32)};
+    uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), (uint32_t)p,
+                       (uint32_t)(p >> 32) | (which ? 0x80000000u : 0u)};
     uint32_t out[4];
     orc_philox4x32_10(ctr, key, out);
     return out[n & 3];
 }
+#define ORC_TRANS 0
+#define ORC_EVENT 1
 
 static double orc_unif(uint32_t w) { return ((double)w + 0.5) / ORC_TWO32; }
 
@@ -327,7 +334,7 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
 #define ORC_T_MC_EVENTS 4
 #define ORC_T_CONVERSIONS 5
 #define ORC_T_CLAMPS 6
-#define ORC_T_DRAWS 7
+#define ORC_T_EVENT_DRAWS 7
 #define ORC_T_FACE 8
 #define ORC_T_HIST 14
 
@@ -383,7 +390,7 @@ typedef struct orc_walk_args {
  * observer-frame frequency.  Static cell: the packet's bin.  Moving cell: a
  * point on the face, an isotropic outward direction (mu uniform on (0,1],
  * azimuth uniform) and x uniform in the bin; x_obs = x + n.u_c. */
-static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t pk, uint64_t* n, uint64_t* t) {
+static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t pk, uint64_t* e, uint64_t* t) {
     const orc_grid* g = A->g;
     const int J = g->J;
     int face = o - 2;
@@ -391,11 +398,11 @@ static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t
     t[ORC_T_FACE + face]++;
     if (!(A->flags[c * J + j] & ORC_FLAG_MOVING)) { t[ORC_T_HIST + 1 + j]++; return; }
     /* face point (2 words) is drawn for the position tally; unused here */
-    (void)orc_word(A->seed, pk, (*n)++);
-    (void)orc_word(A->seed, pk, (*n)++);
-    double mu = 1.0 - orc_unif(orc_word(A->seed, pk, (*n)++));
-    double ph = 2.0 * ORC_PI * orc_unif(orc_word(A->seed, pk, (*n)++));
-    double xu = orc_unif(orc_word(A->seed, pk, (*n)++));
+    (void)orc_word(A->seed, pk, ORC_EVENT, (*e)++);
+    (void)orc_word(A->seed, pk, ORC_EVENT, (*e)++);
+    double mu = 1.0 - orc_unif(orc_word(A->seed, pk, ORC_EVENT, (*e)++));
+    double ph = 2.0 * ORC_PI * orc_unif(orc_word(A->seed, pk, ORC_EVENT, (*e)++));
+    double xu = orc_unif(orc_word(A->seed, pk, ORC_EVENT, (*e)++));
     double x = g->edges[j] + xu * (g->edges[j + 1] - g->edges[j]);
     int ax = face / 2, side = (face & 1) ? 1 : -1;
     int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
@@ -418,9 +425,9 @@ static void* orc_walk_thread(void* vp) {
     const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim;
     uint64_t* t = A->tally;
     for (uint64_t pk = A->p0; pk < A->p1; ++pk) {
-        uint64_t n = 0, steps = 0;
+        uint64_t e = 0, steps = 0;
         int idx[3], j;
-        orc_emit(A->src, orc_word(A->seed, pk, n++), idx, &j);
+        orc_emit(A->src, orc_word(A->seed, pk, ORC_EVENT, e++), idx, &j);
         t[ORC_T_EMITTED]++;
         int64_t c = orc_cell_of(g, idx);
         for (;;) {
@@ -430,7 +437,7 @@ static void* orc_walk_thread(void* vp) {
             int o;
             if (!A->literal) {
                 /* categorical draw: outcome o iff thr[o-1] <= w < thr[o] */
-                uint32_t w = orc_word(A->seed, pk, n++);
+                uint32_t w = orc_word(A->seed, pk, ORC_TRANS, steps);
                 o = 0;
                 while (o < K - 1 && w >= A->thr[s * (K - 1) + o]) ++o;
             } else {
@@ -438,7 +445,7 @@ static void* orc_walk_thread(void* vp) {
                 double best = INFINITY;
                 o = -1;
                 for (int q = 0; q < K; ++q) {
-                    double xi = orc_unif(orc_word(A->seed, pk, n++));
+                    double xi = orc_unif(orc_word(A->seed, pk, ORC_TRANS, 8 * steps + q));
                     double kx = A->rate[s * K + q];
                     if (kx <= 0.0) continue;
                     double dl = -log(xi) / kx;
@@ -448,12 +455,12 @@ static void* orc_walk_thread(void* vp) {
             ++steps;
             t[ORC_T_STEPS]++;
             unsigned act = (A->flags[s] >> (2 * o)) & 3u;
-            if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, j, o, pk, &n, t); break; }
+            if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, j, o, pk, &e, t); break; }
             if (act == ORC_ACT_TO_MC) { A->status = -2; t[ORC_T_ABORTED]++; break; }
             if (o < 2) { j += o ? 1 : -1; continue; }
             int face = o - 2, ax = face / 2, side = (face & 1) ? 1 : -1;
             if (act == ORC_ACT_REBIN) {
-                uint32_t w1 = orc_word(A->seed, pk, n++);
+                uint32_t w1 = orc_word(A->seed, pk, ORC_EVENT, e++);
                 int jn = j + A->rebin_m[c * nf + face] + (w1 >= A->rebin_thr[c * nf + face] ? 1 : 0);
                 if (jn < 0) { jn = 0; t[ORC_T_CLAMPS]++; }
                 if (jn > J - 1) { jn = J - 1; t[ORC_T_CLAMPS]++; }
@@ -462,7 +469,7 @@ static void* orc_walk_thread(void* vp) {
             idx[ax] += side;
             c = orc_cell_of(g, idx);
         }
-        t[ORC_T_DRAWS] += n;
+        t[ORC_T_EVENT_DRAWS] += e;
     }
     return NULL;
 }
