@@ -1,0 +1,295 @@
+/*
+ * rddmc.h -- C-ABI of the GB300 (sm_103a) resonant discrete diffusion Monte
+ * Carlo library (Smith, Tsang, Bromm & Milosavljevic 2017, "Discrete diffusion
+ * Lyman alpha radiative transfer").
+ *
+ * The problem a caller states (Sec. 2.2, Sec. 2.4): a medium on a Cartesian
+ * grid of cells (hydrogen density, temperature, bulk velocity per cell), a
+ * discretisation of the comoving frequency x = (nu - nu0)/dnu_D into bins, and
+ * a monochromatic source at the domain centre.  The library walks photon
+ * packets on the joint (cell, bin) grid with the Fokker-Planck leakage
+ * probabilities of Sec. 2.3 until they leave the domain, and tallies the
+ * escaping spectrum.
+ *
+ * Conventions for every function:
+ *   - returns an int status: RDDMC_OK (0) or a negative RDDMC_ERR_* code;
+ *     never throws, never exits, never prints;
+ *   - "host" pointers are read during the call only; "device" pointers are
+ *     caller-owned device memory (for example PyTorch tensors) that must stay
+ *     valid until the stream work enqueued by the call has finished;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); device work is enqueued on it and the call does not synchronise
+ *     unless stated;
+ *   - the library allocates no device memory and never frees caller memory;
+ *     the grid handle owns host memory only.
+ */
+#ifndef RDDMC_H
+#define RDDMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- statuses */
+#define RDDMC_OK 0
+#define RDDMC_ERR_ARG -1          /* invalid argument (null, out of range, inconsistent) */
+#define RDDMC_ERR_UNSUPPORTED -2  /* valid input the library does not implement */
+#define RDDMC_ERR_SIZE -3         /* a caller buffer is smaller than required */
+#define RDDMC_ERR_CUDA -4         /* a CUDA runtime call or kernel launch failed */
+#define RDDMC_ERR_STEP_LIMIT -5   /* device status: packets aborted by the step watchdog */
+#define RDDMC_ERR_TABLE -6        /* the table buffer was not filled for this grid */
+
+/* ------------------------------------------------------------- enumerations */
+#define RDDMC_GEOM_SLAB_1D 1      /* slab |z| <= R, one spatial axis */
+#define RDDMC_GEOM_CART_3D 3      /* cube [-R,R]^3 of Cartesian cells */
+
+#define RDDMC_MODE_DDMC 0         /* DDMC in every state (Sec. 3.2 test problems) */
+#define RDDMC_MODE_HYBRID 1       /* thin states hand off to continuous MC (Sec. 5.1-5.2) */
+
+#define RDDMC_LAYOUT_DEDUP 0      /* one row block per class of identical cells */
+#define RDDMC_LAYOUT_DENSE 1      /* one row block per cell */
+
+/*
+ * Grid description (host data, copied by rddmc_build_grid).
+ *   geometry   RDDMC_GEOM_SLAB_1D or RDDMC_GEOM_CART_3D.
+ *   n[3]       cells per axis; a slab uses n[0] and requires n[1] = n[2] = 1.
+ *              Cell index c = i0 + n0*(i1 + n1*i2); cubic domain [-R, R]^d with
+ *              uniform widths dz_a = 2R/n[a] (Sec. 2.3, eq. z-leakage).
+ *   nbins      number J of frequency bins (>= 1, <= 65535).
+ *   layout     RDDMC_LAYOUT_DEDUP or RDDMC_LAYOUT_DENSE (table organisation).
+ *   R          half-width of the domain (length unit of the problem).
+ *   tau0       line-centre optical depth k0 R at unit density (k_x = k0 H(a,x),
+ *              Sec. 2.3); a cell's k0 is tau0/R times its n_rel.
+ *   T          gas temperature in K (isothermal; sets a = 4.702e-4 T4^-1/2 and
+ *              v_th = 12.85 T4^1/2 km/s, Sec. 2.1).
+ *   freq_edges host, nbins+1 strictly increasing comoving x edges (FP64).  Moving
+ *              media (v_kms != NULL) require uniform bins.
+ *   n_rel      host, ncell relative densities >= 0 (FP64), or NULL for 1.
+ *   v_kms      host, 3*ncell bulk velocities in km/s (xyz per cell, FP64), or NULL.
+ *   mask       host, ncell bytes: 1 medium, 0 vacuum (a packet entering a vacuum
+ *              cell escapes), or NULL for all medium.
+ */
+typedef struct rddmc_grid_desc {
+    int32_t geometry;
+    int32_t n[3];
+    int32_t nbins;
+    int32_t layout;
+    double R;
+    double tau0;
+    double T;
+    const double* freq_edges;
+    const double* n_rel;
+    const double* v_kms;
+    const uint8_t* mask;
+} rddmc_grid_desc;
+
+/*
+ * Leakage parameters (Sec. 2.5, Sec. 5.1).
+ *   tau_ddmc  thick threshold on tau_ij = k_ij dz (paper suggests 5).
+ *   lambda    extrapolation distance of the boundary coefficient (0.7104).
+ *   f_mu      flux directionality factor of eq. velocity-shift (1/2 isotropic).
+ *   mode      RDDMC_MODE_DDMC or RDDMC_MODE_HYBRID.
+ */
+typedef struct rddmc_leak_params {
+    double tau_ddmc;
+    double lambda;
+    double f_mu;
+    int32_t mode;
+    int32_t reserved;
+} rddmc_leak_params;
+
+/*
+ * Run options of one rddmc_launch_packets call.
+ *   seed          Philox4x32-10 key (see the stream contract below).
+ *   n_packets     packets with ids [0, n_packets), n_packets < 2^63.
+ *   max_steps     watchdog: a packet about to take transition max_steps+1 is
+ *                 aborted and counted (0 = 2^62).
+ *   steps_per_launch  time slice: each packet advances at most this many
+ *                 transitions in this call and its state is saved to the state
+ *                 buffer; a later call with resume = 1 continues it.  0 = run
+ *                 every packet to escape or abort.  Must be a multiple of 4.
+ *   resume        0: every packet starts at the source (state buffer is only
+ *                 written); 1: continue the packets saved by a previous call on
+ *                 the same state buffer, grid, seed and n_packets.
+ *   ctas_per_sm, threads_per_cta, chunk  launch schedule (0 = library default):
+ *                 persistent grid of ctas_per_sm * #SM CTAs of threads_per_cta
+ *                 threads (a multiple of 32, at most 256); `chunk` transitions
+ *                 (multiple of 4) between warp refills.
+ *   table_in_smem 1: stage the row table in shared memory when it fits;
+ *                 0: gather rows from global memory (L1/L2).
+ */
+typedef struct rddmc_run_opts {
+    uint64_t seed;
+    uint64_t n_packets;
+    uint64_t max_steps;
+    uint64_t steps_per_launch;
+    int32_t resume;
+    int32_t ctas_per_sm;
+    int32_t threads_per_cta;
+    int32_t chunk;
+    int32_t table_in_smem;
+    int32_t reserved;
+} rddmc_run_opts;
+
+/* Buffer sizes for a grid (from rddmc_grid_sizes). */
+typedef struct rddmc_sizes {
+    uint64_t table_bytes;        /* device table buffer (rows, class map, descriptors) */
+    uint64_t tally_bytes;        /* device tally buffer */
+    uint64_t state_bytes;        /* device state buffer for the n_packets asked for */
+    int32_t n_class;             /* row blocks in the table */
+    int32_t row_bytes;           /* 16 (slab) or 32 (3D) */
+    int32_t n_outcomes;          /* 4 (slab) or 8 (3D) */
+    int32_t reserved;
+} rddmc_sizes;
+
+/* Integer tallies of everything launched since the last reset. */
+typedef struct rddmc_tallies {
+    uint64_t emitted;      /* packets started at the source */
+    uint64_t escaped;      /* packets that left the domain */
+    uint64_t aborted;      /* packets stopped by the step watchdog */
+    uint64_t steps;        /* DDMC transitions executed */
+    uint64_t mc_events;    /* continuous-MC events (scatterings and face crossings) */
+    uint64_t conversions;  /* DDMC <-> MC hand-offs */
+    uint64_t clamps;       /* Doppler rebins clamped to the frequency grid ends */
+    uint64_t event_draws;  /* words taken from the packets' event streams */
+    int32_t status;        /* RDDMC_OK or a device-side error code */
+    int32_t nbins;         /* J; the histogram has J + 2 entries */
+    int32_t nfaces;        /* 2 (slab) or 6 (3D) */
+    int32_t reserved;
+} rddmc_tallies;
+
+typedef struct rddmc_grid rddmc_grid; /* opaque host handle */
+
+/*
+ * Random-stream contract.  key = (seed_lo, seed_hi).  Packet p owns two
+ * Philox4x32-10 streams of 32-bit words: transition t uses lane t&3 of
+ * Philox(ctr = ((t>>2)_lo, (t>>2)_hi, p_lo, p_hi)); event draw e uses lane e&3
+ * of Philox(ctr = ((e>>2)_lo, (e>>2)_hi, p_lo, p_hi | 2^31)).  Event draw 0
+ * picks the source cell and bin (bit 31-a: cell along axis a when two cells
+ * straddle the centre; bit 28: bin when x0 is a bin edge); a Doppler rebin
+ * takes one event draw; a DDMC escape from a moving cell takes five.
+ */
+
+/*
+ * rddmc_build_grid -- validate a grid description and build the host handle.
+ * Groups cells whose leakage rows are provably identical (same density,
+ * velocity and neighbour data on every face) into classes when layout is
+ * RDDMC_LAYOUT_DEDUP; this is the factoring of space and frequency noted for
+ * uniform media in Sec. 2.3.  Host-only: no device memory is touched.
+ *   desc  host, grid description (read during the call only).
+ *   out   host, receives the handle; release it with rddmc_destroy_grid.
+ * Errors: RDDMC_ERR_ARG (nulls, non-increasing edges, negative density, bad
+ * counts), RDDMC_ERR_UNSUPPORTED (moving media with non-uniform bins).
+ */
+int rddmc_build_grid(const rddmc_grid_desc* desc, rddmc_grid** out);
+
+/* Release a handle from rddmc_build_grid (NULL is ignored). */
+void rddmc_destroy_grid(rddmc_grid* grid);
+
+/*
+ * rddmc_grid_sizes -- byte sizes of the caller-owned device buffers.
+ *   n_packets  packet count the state buffer must hold.
+ *   out        host, receives the sizes.
+ */
+int rddmc_grid_sizes(const rddmc_grid* grid, uint64_t n_packets, rddmc_sizes* out);
+
+/*
+ * rddmc_precompute_leakage -- fill the device table (FP64 kernel).
+ * Per state (cell class i, bin j): the bin-mean opacity
+ * k_ij = k0_i (calH(a, x_j+) - calH(a, x_j-)) / dx_j (Sec. 2.3), the spatial
+ * leakage coefficients of eq. z-leakage (exterior faces and, in hybrid mode,
+ * thin neighbours use the boundary form 2/(3 dz (k dz + 2 lambda)), Sec. 5.1),
+ * the frequency leakage coefficients of eq. x-leakage (none beyond the grid
+ * ends), and the neighbour opacity over the Doppler-shifted bin
+ * (eq. velocity-shift).  The probabilities p_X = k_X / sum k are accumulated in
+ * the outcome order (bin-1, bin+1, -e0, +e0[, -e1, +e1, -e2, +e2]) and stored
+ * as 32-bit thresholds round-half-even(C * 2^32) saturated at 2^32 - 1.
+ *   d_table      device, at least sizes.table_bytes, 256-byte aligned.
+ *   table_bytes  its size.
+ * Errors: RDDMC_ERR_ARG, RDDMC_ERR_SIZE, RDDMC_ERR_CUDA.
+ */
+int rddmc_precompute_leakage(rddmc_grid* grid, const rddmc_leak_params* params, void* d_table,
+                             size_t table_bytes, void* stream);
+
+/*
+ * rddmc_reset_tallies -- zero the device tally buffer (stream-ordered).
+ *   d_tallies  device, at least sizes.tally_bytes, 8-byte aligned.
+ */
+int rddmc_reset_tallies(const rddmc_grid* grid, void* d_tallies, size_t tally_bytes, void* stream);
+
+/*
+ * rddmc_launch_packets -- walk packets (Sec. 2.4) with one persistent kernel.
+ * Each thread holds one packet: it draws one word of the packet's transition
+ * stream per transition, gathers the 16/32-byte row of its state and takes the
+ * outcome whose threshold interval holds the word (the categorical form of the
+ * competing exponentials of eq. l_min_1/2: the argmin of independent
+ * exponentials with rates k_X is X with probability k_X / sum k).  Packets
+ * leaving the domain (Sec. 2.4: removed at the boundary) are tallied; finished
+ * lanes refill from a global packet cursor one warp at a time.  Tallies are
+ * accumulated into d_tallies (call rddmc_reset_tallies first).
+ *   d_table    device, filled by rddmc_precompute_leakage for this grid.
+ *   opts       host, run options.
+ *   d_state    device scratch of sizes.state_bytes for opts->n_packets,
+ *              256-byte aligned: packet cursor and per-packet saved state.
+ *   d_tallies  device tally buffer.
+ * Errors: RDDMC_ERR_ARG, RDDMC_ERR_SIZE, RDDMC_ERR_UNSUPPORTED (hybrid mode,
+ * not yet implemented), RDDMC_ERR_CUDA.  Device-side conditions (watchdog
+ * aborts) are reported by rddmc_read_tallies.
+ */
+int rddmc_launch_packets(const rddmc_grid* grid, const void* d_table, const rddmc_run_opts* opts,
+                         void* d_state, size_t state_bytes, void* d_tallies, size_t tally_bytes,
+                         void* stream);
+
+/*
+ * rddmc_read_tallies -- copy the tallies to the host; synchronises `stream`.
+ *   out        host, counters and status.
+ *   hist       host, J+2 uint64 (index 0: below the frequency grid, 1..J: bins,
+ *              J+1: above) of escaping packets in the observer frame, or NULL.
+ *   faces      host, 2 (slab: -z, +z) or 6 (-x,+x,-y,+y,-z,+z) uint64 escape
+ *              counts per exterior face direction, or NULL.
+ * Returns RDDMC_OK; `out->status` holds RDDMC_ERR_STEP_LIMIT if any packet was
+ * aborted.
+ */
+int rddmc_read_tallies(const rddmc_grid* grid, const void* d_tallies, rddmc_tallies* out, uint64_t* hist,
+                       uint64_t* faces, void* stream);
+
+/*
+ * rddmc_table_rows -- expand the device table to one row per state (host), for
+ * inspection and parity checks.  Synchronises `stream`.
+ *   thr    host, ncell * J * (n_outcomes - 1) uint32 cumulative thresholds.
+ *   flags  host, ncell * J uint32 flag words (2-bit action per outcome:
+ *          0 move, 1 escape, 2 to MC, 3 move with Doppler rebin; bit 30 moving
+ *          cell; bit 31 thin state).
+ */
+int rddmc_table_rows(const rddmc_grid* grid, const void* d_table, uint32_t* thr, uint32_t* flags, void* stream);
+
+/*
+ * rddmc_read_packet_states -- copy saved per-packet states [first, first+count)
+ * from a state buffer to the host (checkpoint inspection and sampled parity
+ * checks).  Synchronises `stream`.  A state is meaningful once a launch with
+ * steps_per_launch > 0 or resume = 1 has processed that packet.
+ *   n_packets  the n_packets the state buffer was laid out for.
+ *   cell, bin  host, count uint32 each: cell index and frequency bin.
+ *   steps      host, count uint64: transitions taken so far.
+ *   event_draws host, count uint64: event-stream words taken so far.
+ *   status     host, count bytes: 0 not started, 1 in flight, 2 finished.
+ * Any output pointer may be NULL.  Errors: RDDMC_ERR_ARG (range), RDDMC_ERR_CUDA.
+ */
+int rddmc_read_packet_states(const rddmc_grid* grid, const void* d_state, uint64_t n_packets, uint64_t first,
+                             uint64_t count, uint32_t* cell, uint32_t* bin, uint64_t* steps, uint64_t* event_draws,
+                             uint8_t* status, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* rddmc_status_string(int status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int rddmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDDMC_H */

@@ -50,6 +50,10 @@ def lib():
         L.orc_tally_len.argtypes = [i32]
         L.orc_walk_ddmc.restype = i32
         L.orc_walk_ddmc.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, d, u64, u64, u64, u64, i32, i32, vp]
+        L.orc_walk_slice.restype = i32
+        L.orc_walk_slice.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, d, u64, u64, u64, u64, i32, vp]
+        L.orc_replay_packet.restype = i32
+        L.orc_replay_packet.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, d, u64, u64, u64, u64, vp, vp]
         _LIB = L
     return _LIB
 
@@ -163,6 +167,37 @@ def walk(grid: Grid, table: dict, seed: int, p0: int, npk: int, max_steps: int =
                              int(npk), int(max_steps), int(literal), int(nthreads), _ptr(out))
     if rc == -1:
         raise ValueError("orc_walk_ddmc: bad input")
+    res = unpack_tally(out, grid.J)
+    res["status"] = rc
+    return res
+
+
+def replay_packet(grid: Grid, table: dict, seed: int, pid: int, n_trans: int, max_steps: int = (1 << 62)) -> dict:
+    """State of one packet after at most n_trans transitions (the oracle's own table)."""
+    out = np.zeros(5, dtype=np.uint64)
+    tl = np.zeros(lib().orc_tally_len(grid.J), dtype=np.uint64)
+    thr = np.ascontiguousarray(table["thr"].ravel())
+    rc = lib().orc_replay_packet(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
+                                 _ptr(table["rebin_thr"]), float(grid.w.x0), int(seed), int(pid), int(n_trans),
+                                 int(max_steps), _ptr(out), _ptr(tl))
+    if rc == -1:
+        raise ValueError("orc_replay_packet: bad input")
+    d = dict(cell=int(out[0]), bin=int(out[1]), steps=int(out[2]), event_draws=int(out[3]), done=int(out[4]))
+    d["tally"] = unpack_tally(tl, grid.J)
+    return d
+
+
+def walk_slice(grid: Grid, table: dict, seed: int, p0: int, npk: int, n_trans: int, nthreads: int = 0) -> dict:
+    """Start packets [p0, p0+npk) and advance each by at most n_trans transitions."""
+    if nthreads <= 0:
+        nthreads = os.cpu_count() or 1
+    out = np.zeros(lib().orc_tally_len(grid.J), dtype=np.uint64)
+    thr = np.ascontiguousarray(table["thr"].ravel())
+    rc = lib().orc_walk_slice(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
+                              _ptr(table["rebin_thr"]), float(grid.w.x0), int(seed), int(p0), int(npk),
+                              int(n_trans), int(nthreads), _ptr(out))
+    if rc == -1:
+        raise ValueError("orc_walk_slice: bad input")
     res = unpack_tally(out, grid.J)
     res["status"] = rc
     return res

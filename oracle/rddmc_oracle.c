@@ -382,6 +382,7 @@ typedef struct orc_walk_args {
     const orc_source* src;
     uint64_t seed, p0, p1, max_steps;
     int literal;         /* 1: competing exponentials in FP64 (eq. l_min_1/2) */
+    uint64_t limit;      /* transitions per packet, UINT64_MAX = until escape or abort */
     uint64_t* tally;     /* per-thread */
     int status;
 } orc_walk_args;
@@ -419,57 +420,78 @@ static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t
     t[ORC_T_HIST + b]++;
 }
 
-static void* orc_walk_thread(void* vp) {
-    orc_walk_args* A = (orc_walk_args*)vp;
+/* Per-packet state of the walk. */
+typedef struct orc_pstate {
+    int idx[3];
+    int j;
+    uint64_t steps, e;
+    int done;      /* 0 in flight, 1 escaped, 2 aborted, 3 met an MC state */
+} orc_pstate;
+
+/* Advance packet pk by at most `limit` transitions (stopping at escape or at
+ * the watchdog), accumulating tallies into t. */
+static void orc_advance(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t limit, uint64_t* t) {
     const orc_grid* g = A->g;
     const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim;
+    int64_t c = orc_cell_of(g, P->idx);
+    for (uint64_t n = 0; n < limit; ++n) {
+        if (P->steps >= A->max_steps) { t[ORC_T_ABORTED]++; P->done = 2; return; }
+        const int64_t s = c * J + P->j;
+        if (A->flags[s] & ORC_FLAG_THIN) { A->status = -2; t[ORC_T_ABORTED]++; P->done = 3; return; }
+        int o;
+        if (!A->literal) {
+            /* categorical draw: outcome o iff thr[o-1] <= w < thr[o] */
+            uint32_t w = orc_word(A->seed, pk, ORC_TRANS, P->steps);
+            o = 0;
+            while (o < K - 1 && w >= A->thr[s * (K - 1) + o]) ++o;
+        } else {
+            /* eq. l_min_2: dl_X = -ln(xi)/k_X for every process; eq. l_min_1: execute the smallest */
+            double best = INFINITY;
+            o = -1;
+            for (int q = 0; q < K; ++q) {
+                double xi = orc_unif(orc_word(A->seed, pk, ORC_TRANS, 8 * P->steps + q));
+                double kx = A->rate[s * K + q];
+                if (kx <= 0.0) continue;
+                double dl = -log(xi) / kx;
+                if (dl < best) { best = dl; o = q; }
+            }
+        }
+        P->steps++;
+        t[ORC_T_STEPS]++;
+        unsigned act = (A->flags[s] >> (2 * o)) & 3u;
+        if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, P->j, o, pk, &P->e, t); P->done = 1; return; }
+        if (act == ORC_ACT_TO_MC) { A->status = -2; t[ORC_T_ABORTED]++; P->done = 3; return; }
+        if (o < 2) { P->j += o ? 1 : -1; continue; }
+        int face = o - 2, ax = face / 2, side = (face & 1) ? 1 : -1;
+        if (act == ORC_ACT_REBIN) {
+            uint32_t w1 = orc_word(A->seed, pk, ORC_EVENT, P->e++);
+            int jn = P->j + A->rebin_m[c * nf + face] + (w1 >= A->rebin_thr[c * nf + face] ? 1 : 0);
+            if (jn < 0) { jn = 0; t[ORC_T_CLAMPS]++; }
+            if (jn > J - 1) { jn = J - 1; t[ORC_T_CLAMPS]++; }
+            P->j = jn;
+        }
+        P->idx[ax] += side;
+        c = orc_cell_of(g, P->idx);
+    }
+}
+
+static void orc_start(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t* t) {
+    memset(P, 0, sizeof(*P));
+    orc_emit(A->src, orc_word(A->seed, pk, ORC_EVENT, P->e++), P->idx, &P->j);
+    t[ORC_T_EMITTED]++;
+}
+
+static void* orc_walk_thread(void* vp) {
+    orc_walk_args* A = (orc_walk_args*)vp;
     uint64_t* t = A->tally;
     for (uint64_t pk = A->p0; pk < A->p1; ++pk) {
-        uint64_t e = 0, steps = 0;
-        int idx[3], j;
-        orc_emit(A->src, orc_word(A->seed, pk, ORC_EVENT, e++), idx, &j);
-        t[ORC_T_EMITTED]++;
-        int64_t c = orc_cell_of(g, idx);
-        for (;;) {
-            if (steps >= A->max_steps) { t[ORC_T_ABORTED]++; break; }
-            const int64_t s = c * J + j;
-            if (A->flags[s] & ORC_FLAG_THIN) { A->status = -2; t[ORC_T_ABORTED]++; break; }
-            int o;
-            if (!A->literal) {
-                /* categorical draw: outcome o iff thr[o-1] <= w < thr[o] */
-                uint32_t w = orc_word(A->seed, pk, ORC_TRANS, steps);
-                o = 0;
-                while (o < K - 1 && w >= A->thr[s * (K - 1) + o]) ++o;
-            } else {
-                /* eq. l_min_2: dl_X = -ln(xi)/k_X for every process; eq. l_min_1: execute the smallest */
-                double best = INFINITY;
-                o = -1;
-                for (int q = 0; q < K; ++q) {
-                    double xi = orc_unif(orc_word(A->seed, pk, ORC_TRANS, 8 * steps + q));
-                    double kx = A->rate[s * K + q];
-                    if (kx <= 0.0) continue;
-                    double dl = -log(xi) / kx;
-                    if (dl < best) { best = dl; o = q; }
-                }
-            }
-            ++steps;
-            t[ORC_T_STEPS]++;
-            unsigned act = (A->flags[s] >> (2 * o)) & 3u;
-            if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, j, o, pk, &e, t); break; }
-            if (act == ORC_ACT_TO_MC) { A->status = -2; t[ORC_T_ABORTED]++; break; }
-            if (o < 2) { j += o ? 1 : -1; continue; }
-            int face = o - 2, ax = face / 2, side = (face & 1) ? 1 : -1;
-            if (act == ORC_ACT_REBIN) {
-                uint32_t w1 = orc_word(A->seed, pk, ORC_EVENT, e++);
-                int jn = j + A->rebin_m[c * nf + face] + (w1 >= A->rebin_thr[c * nf + face] ? 1 : 0);
-                if (jn < 0) { jn = 0; t[ORC_T_CLAMPS]++; }
-                if (jn > J - 1) { jn = J - 1; t[ORC_T_CLAMPS]++; }
-                j = jn;
-            }
-            idx[ax] += side;
-            c = orc_cell_of(g, idx);
-        }
-        t[ORC_T_EVENT_DRAWS] += e;
+        orc_pstate P;
+        orc_start(A, pk, &P, t);
+        if (A->limit == UINT64_MAX)
+            while (!P.done) orc_advance(A, pk, &P, UINT64_MAX, t);
+        else
+            orc_advance(A, pk, &P, A->limit, t);
+        t[ORC_T_EVENT_DRAWS] += P.e;
     }
     return NULL;
 }
@@ -483,9 +505,10 @@ static void* orc_walk_thread(void* vp) {
  * Returns 0, -1 on bad input, -2 if a packet met a thin (MC) state: the hybrid
  * walk is orc_hybrid_walk_slab.
  */
-int orc_walk_ddmc(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
-                  const uint32_t* rebin_thr, const double* rate, double x0, uint64_t seed, uint64_t p0,
-                  uint64_t np, uint64_t max_steps, int literal, int nthreads, uint64_t* tally) {
+static int orc_walk_run(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
+                        const uint32_t* rebin_thr, const double* rate, double x0, uint64_t seed, uint64_t p0,
+                        uint64_t np, uint64_t max_steps, int literal, uint64_t limit, int nthreads,
+                        uint64_t* tally) {
     orc_source src;
     if (orc_make_source(g, x0, &src)) return -1;
     if (literal && !rate) return -1;
@@ -499,6 +522,7 @@ int orc_walk_ddmc(const orc_grid* g, const uint32_t* thr, const uint32_t* flags,
         orc_walk_args* A = &args[i];
         A->g = g; A->thr = thr; A->flags = flags; A->rebin_m = rebin_m; A->rebin_thr = rebin_thr;
         A->rate = rate; A->src = &src; A->seed = seed; A->max_steps = max_steps; A->literal = literal;
+        A->limit = limit;
         A->p0 = p0 + np * (uint64_t)i / nthreads;
         A->p1 = p0 + np * (uint64_t)(i + 1) / nthreads;
         A->tally = tl + (size_t)i * L;
@@ -513,4 +537,48 @@ int orc_walk_ddmc(const orc_grid* g, const uint32_t* thr, const uint32_t* flags,
     }
     free(th); free(args); free(tl);
     return status;
+}
+
+int orc_walk_ddmc(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
+                  const uint32_t* rebin_thr, const double* rate, double x0, uint64_t seed, uint64_t p0,
+                  uint64_t np, uint64_t max_steps, int literal, int nthreads, uint64_t* tally) {
+    return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, rate, x0, seed, p0, np, max_steps, literal, UINT64_MAX,
+                        nthreads, tally);
+}
+
+/* Start packets [p0, p0+np) at the source and advance each by at most
+ * n_trans transitions (a bounded slice of the walk, as one time slice of the
+ * GPU walk does); the tallies count what happened within the slice. */
+int orc_walk_slice(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
+                   const uint32_t* rebin_thr, double x0, uint64_t seed, uint64_t p0, uint64_t np,
+                   uint64_t n_trans, int nthreads, uint64_t* tally) {
+    return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, NULL, x0, seed, p0, np, (uint64_t)1 << 62, 0, n_trans,
+                        nthreads, tally);
+}
+
+/*
+ * Replay packet `pk` for at most n_trans transitions; writes its state
+ * (cell index, bin, transitions, event draws, done flag) to out[5] and its
+ * tallies to tally (orc_tally_len(J) words, overwritten).
+ */
+int orc_replay_packet(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
+                      const uint32_t* rebin_thr, double x0, uint64_t seed, uint64_t pk, uint64_t n_trans,
+                      uint64_t max_steps, uint64_t* out, uint64_t* tally) {
+    orc_source src;
+    if (orc_make_source(g, x0, &src)) return -1;
+    orc_walk_args A;
+    memset(&A, 0, sizeof(A));
+    A.g = g; A.thr = thr; A.flags = flags; A.rebin_m = rebin_m; A.rebin_thr = rebin_thr; A.src = &src;
+    A.seed = seed; A.max_steps = max_steps;
+    memset(tally, 0, sizeof(uint64_t) * orc_tally_len(g->J));
+    orc_pstate P;
+    orc_start(&A, pk, &P, tally);
+    orc_advance(&A, pk, &P, n_trans, tally);
+    tally[ORC_T_EVENT_DRAWS] += P.e;
+    out[0] = (uint64_t)orc_cell_of(g, P.idx);
+    out[1] = (uint64_t)P.j;
+    out[2] = P.steps;
+    out[3] = P.e;
+    out[4] = (uint64_t)P.done;
+    return A.status;
 }

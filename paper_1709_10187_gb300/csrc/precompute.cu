@@ -1,0 +1,140 @@
+// precompute.cu -- FP64 leakage-table kernels (Sec. 2.3, Sec. 2.5, Sec. 5.1).
+//
+// Kernel 1: phi[j] = bin mean of H(a,x) over bin j (k_ij = k0_i phi_j).
+// Kernel 2: one thread per (class, bin) row: leakage coefficients of
+//   eq. x-leakage and eq. z-leakage, the boundary / thin-neighbour form
+//   2/(3 dz (k dz + 2 lambda)), probabilities p_X = k_X / sum k accumulated in
+//   outcome order, 32-bit thresholds round-half-even(C 2^32) saturated at
+//   2^32 - 1, and the flag word (2-bit action per outcome, moving, thin).
+// FP64 throughout: 1 - p of thick states and far-wing bin means (dcalH ~ a dx /
+// (sqrt(pi) x^2) ~ 1e-8 against calH ~ 0.886) are below FP32 resolution.  This
+// file is compiled without fused multiply-adds so every product and sum is
+// rounded as written.
+#include <cstring>
+
+#include "grid.h"
+#include "voigt.cuh"
+
+namespace rddmc {
+namespace {
+
+__global__ void phi_kernel(const double* __restrict__ edges, double* __restrict__ phi, int J, double a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    phi[j] = voigt_bin_mean_f64(a, edges[j], edges[j + 1]);
+}
+
+__device__ __forceinline__ uint32_t quantise_dev(double C) {
+    double t = rint(C * 4294967296.0);
+    t = fmax(t, 0.0);
+    t = fmin(t, 4294967295.0);
+    return (uint32_t)t;
+}
+
+template <int NDIM>
+__global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ cdesc,
+                            const double* __restrict__ edges, const double* __restrict__ phi,
+                            uint32_t* __restrict__ rows, int64_t nrow) {
+    constexpr int K = 2 + 2 * NDIM;
+    constexpr int W = NDIM == 1 ? 4 : 8;  // words per row
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrow) return;
+    const int J = h.J;
+    const int cls = (int)(r / J);
+    const int j = (int)(r - (int64_t)cls * J);
+    const ClassDesc& D = cdesc[cls];
+    const bool hybrid = h.mode == RDDMC_MODE_HYBRID;
+    double dzmin = h.dz[0];
+    for (int ax = 1; ax < NDIM; ++ax) dzmin = fmin(dzmin, h.dz[ax]);
+
+    const double dxj = edges[j + 1] - edges[j];
+    const double k = D.k0 * phi[j];
+    double rate[K];
+    uint32_t act[K];
+    // frequency leakage, eq. x-leakage; zero flux beyond the grid ends
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        const int jn = j + (sd ? 1 : -1);
+        if (jn < 0 || jn >= J) { rate[sd] = 0.0; act[sd] = ACT_MOVE; continue; }
+        const double dxn = edges[jn + 1] - edges[jn];
+        const double kn = D.k0 * phi[jn];
+        rate[sd] = 1.0 / (dxj * (dxj / k + dxn / kn));
+        act[sd] = (hybrid && kn * dzmin < h.tau_ddmc) ? ACT_TO_MC : ACT_MOVE;
+    }
+    // spatial leakage, eq. z-leakage; exterior faces and thin neighbours use the
+    // extrapolation-distance form of Sec. 5.1
+#pragma unroll
+    for (int ax = 0; ax < NDIM; ++ax) {
+        const double dz = h.dz[ax];
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            const int o = 2 + 2 * ax + sd;
+            const FaceDesc& F = D.face[2 * ax + sd];
+            const double r_bnd = 1.0 / (3.0 * dz) * 2.0 / (k * dz + 2.0 * h.lambda);
+            if (F.exterior) { rate[o] = r_bnd; act[o] = ACT_ESCAPE; continue; }
+            // neighbour opacity over the Doppler-shifted bin (eq. velocity-shift)
+            const double knb = F.k0_nb * (F.delta == 0.0 ? phi[j]
+                                                         : voigt_bin_mean_f64(h.a, edges[j] + F.delta,
+                                                                              edges[j + 1] + F.delta));
+            const double dznb = dz;
+            if (hybrid && knb * dznb < h.tau_ddmc) { rate[o] = r_bnd; act[o] = ACT_TO_MC; continue; }
+            rate[o] = 1.0 / (3.0 * dz) * 2.0 / (k * dz + knb * dznb);
+            act[o] = F.delta != 0.0 ? ACT_REBIN : ACT_MOVE;
+        }
+    }
+    double tot = 0.0;
+#pragma unroll
+    for (int o = 0; o < K; ++o) tot += rate[o];
+    uint32_t out[W];
+    double C = 0.0;
+#pragma unroll
+    for (int o = 0; o < K - 1; ++o) {
+        C += rate[o] / tot;
+        out[o] = quantise_dev(C);
+    }
+    uint32_t fl = 0;
+#pragma unroll
+    for (int o = 0; o < K; ++o) fl |= (act[o] & 3u) << (2 * o);
+    if (D.moving) fl |= FLAG_MOVING;
+    if (hybrid && k * dzmin < h.tau_ddmc) fl |= FLAG_THIN;
+    out[W - 1] = fl;
+    if (NDIM == 1) {
+        reinterpret_cast<uint4*>(rows)[r] = make_uint4(out[0], out[1], out[2], out[3]);
+    } else {
+        uint4* p = reinterpret_cast<uint4*>(rows) + 2 * r;
+        p[0] = make_uint4(out[0], out[1], out[2], out[3]);
+        p[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_precompute(const rddmc_grid& g, void* d_table, cudaStream_t s) {
+    char* base = (char*)d_table;
+    const double* edges = (const double*)(base + g.off_edges);
+    double* phi = (double*)(base + g.off_phi);
+    phi_kernel<<<(g.J + 127) / 128, 128, 0, s>>>(edges, phi, g.J, g.a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    TableHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.J = g.J;
+    h.mode = g.params.mode;
+    h.tau_ddmc = g.params.tau_ddmc;
+    h.lambda = g.params.lambda;
+    h.f_mu = g.params.f_mu;
+    h.a = g.a;
+    for (int a = 0; a < 3; ++a) h.dz[a] = 2.0 * g.R / g.n[a];
+    const int64_t nrow = (int64_t)g.n_class * g.J;
+    const int threads = 128;
+    const int64_t blocks = (nrow + threads - 1) / threads;
+    const ClassDesc* cd = (const ClassDesc*)(base + g.off_cdesc);
+    uint32_t* rows = (uint32_t*)(base + g.off_rows);
+    if (g.ndim == 1)
+        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, nrow);
+    else
+        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, nrow);
+    return cudaGetLastError();
+}
+
+}  // namespace rddmc

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of the C-ABI in ``include/rddmc.h``.
+
+Argument marshalling only: every step of the walk runs in the CUDA library.
+PyTorch supplies device memory (tensors whose ``data_ptr()`` is passed) and
+streams.  Loading fails loudly when the library has not been built; there is no
+CPU fallback.
+
+Low-level functions mirror the C names (``build_grid``, ``grid_sizes``,
+``precompute_leakage``, ``reset_tallies``, ``launch_packets``,
+``read_tallies``, ``table_rows``).  ``Problem`` bundles them for a workload:
+it owns the handle and the caller-side device buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librddmc.so")
+
+OK, ERR_ARG, ERR_UNSUPPORTED, ERR_SIZE, ERR_CUDA, ERR_STEP_LIMIT, ERR_TABLE = 0, -1, -2, -3, -4, -5, -6
+GEOM_SLAB_1D, GEOM_CART_3D = 1, 3
+MODE_DDMC, MODE_HYBRID = 0, 1
+LAYOUT_DEDUP, LAYOUT_DENSE = 0, 1
+
+EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc_precompute_leakage",
+            "rddmc_reset_tallies", "rddmc_launch_packets", "rddmc_read_tallies", "rddmc_table_rows",
+            "rddmc_read_packet_states", "rddmc_status_string", "rddmc_version"]
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("nbins", ctypes.c_int32),
+                ("layout", ctypes.c_int32), ("R", ctypes.c_double), ("tau0", ctypes.c_double),
+                ("T", ctypes.c_double), ("freq_edges", ctypes.c_void_p), ("n_rel", ctypes.c_void_p),
+                ("v_kms", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+
+
+class LeakParams(ctypes.Structure):
+    _fields_ = [("tau_ddmc", ctypes.c_double), ("lam", ctypes.c_double), ("f_mu", ctypes.c_double),
+                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class RunOpts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_packets", ctypes.c_uint64), ("max_steps", ctypes.c_uint64),
+                ("steps_per_launch", ctypes.c_uint64), ("resume", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("threads_per_cta", ctypes.c_int32), ("chunk", ctypes.c_int32), ("table_in_smem", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("table_bytes", ctypes.c_uint64), ("tally_bytes", ctypes.c_uint64), ("state_bytes", ctypes.c_uint64),
+                ("n_class", ctypes.c_int32), ("row_bytes", ctypes.c_int32), ("n_outcomes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Tallies(ctypes.Structure):
+    _fields_ = [("emitted", ctypes.c_uint64), ("escaped", ctypes.c_uint64), ("aborted", ctypes.c_uint64),
+                ("steps", ctypes.c_uint64), ("mc_events", ctypes.c_uint64), ("conversions", ctypes.c_uint64),
+                ("clamps", ctypes.c_uint64), ("event_draws", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("nbins", ctypes.c_int32), ("nfaces", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class RDDMCError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} failed: {status} ({status_string(status)})")
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run paper_1709_10187_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, u64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t
+        L.rddmc_build_grid.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(vp)]
+        L.rddmc_destroy_grid.argtypes = [vp]
+        L.rddmc_destroy_grid.restype = None
+        L.rddmc_grid_sizes.argtypes = [vp, u64, ctypes.POINTER(Sizes)]
+        L.rddmc_precompute_leakage.argtypes = [vp, ctypes.POINTER(LeakParams), vp, sz, vp]
+        L.rddmc_reset_tallies.argtypes = [vp, vp, sz, vp]
+        L.rddmc_launch_packets.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp, sz, vp]
+        L.rddmc_read_tallies.argtypes = [vp, vp, ctypes.POINTER(Tallies), vp, vp, vp]
+        L.rddmc_table_rows.argtypes = [vp, vp, vp, vp, vp]
+        L.rddmc_read_packet_states.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, vp, vp, vp]
+        L.rddmc_status_string.argtypes = [i32]
+        L.rddmc_status_string.restype = ctypes.c_char_p
+        L.rddmc_version.argtypes = []
+        for name in EXPORTED:
+            if name not in ("rddmc_destroy_grid", "rddmc_status_string"):
+                getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def status_string(s: int) -> str:
+    return lib().rddmc_status_string(int(s)).decode()
+
+
+def _check(fn: str, s: int):
+    if s != OK:
+        raise RDDMCError(fn, s)
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+# ----------------------------------------------------------------------------- C names
+def build_grid(geometry, n, edges, R, tau0, T, n_rel=None, v_kms=None, mask=None, layout=LAYOUT_DEDUP):
+    """rddmc_build_grid; returns an opaque handle (int)."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    nr = None if n_rel is None else np.ascontiguousarray(n_rel, dtype=np.float64)
+    v = None if v_kms is None else np.ascontiguousarray(v_kms, dtype=np.float64)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    d = GridDesc()
+    d.geometry = geometry
+    for a in range(3):
+        d.n[a] = int(n[a])
+    d.nbins = len(e) - 1
+    d.layout = layout
+    d.R, d.tau0, d.T = float(R), float(tau0), float(T)
+    d.freq_edges, d.n_rel, d.v_kms, d.mask = (ctypes.c_void_p(e.ctypes.data), _np_ptr(nr), _np_ptr(v), _np_ptr(m))
+    h = ctypes.c_void_p()
+    _check("rddmc_build_grid", lib().rddmc_build_grid(ctypes.byref(d), ctypes.byref(h)))
+    return h.value
+
+
+def destroy_grid(grid):
+    if grid:
+        lib().rddmc_destroy_grid(ctypes.c_void_p(grid))
+
+
+def grid_sizes(grid, n_packets: int) -> Sizes:
+    s = Sizes()
+    _check("rddmc_grid_sizes", lib().rddmc_grid_sizes(ctypes.c_void_p(grid), int(n_packets), ctypes.byref(s)))
+    return s
+
+
+def precompute_leakage(grid, params: LeakParams, d_table: int, table_bytes: int, stream: int = 0):
+    _check("rddmc_precompute_leakage", lib().rddmc_precompute_leakage(
+        ctypes.c_void_p(grid), ctypes.byref(params), ctypes.c_void_p(d_table), int(table_bytes),
+        ctypes.c_void_p(stream)))
+
+
+def reset_tallies(grid, d_tallies: int, tally_bytes: int, stream: int = 0):
+    _check("rddmc_reset_tallies", lib().rddmc_reset_tallies(ctypes.c_void_p(grid), ctypes.c_void_p(d_tallies),
+                                                            int(tally_bytes), ctypes.c_void_p(stream)))
+
+
+def launch_packets(grid, d_table: int, opts: RunOpts, d_state: int, state_bytes: int, d_tallies: int,
+                   tally_bytes: int, stream: int = 0):
+    _check("rddmc_launch_packets", lib().rddmc_launch_packets(
+        ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(opts), ctypes.c_void_p(d_state),
+        int(state_bytes), ctypes.c_void_p(d_tallies), int(tally_bytes), ctypes.c_void_p(stream)))
+
+
+def read_tallies(grid, d_tallies: int, J: int, nfaces: int, stream: int = 0) -> dict:
+    t = Tallies()
+    hist = np.zeros(J + 2, dtype=np.uint64)
+    faces = np.zeros(nfaces, dtype=np.uint64)
+    _check("rddmc_read_tallies", lib().rddmc_read_tallies(ctypes.c_void_p(grid), ctypes.c_void_p(d_tallies),
+                                                          ctypes.byref(t), _np_ptr(hist), _np_ptr(faces),
+                                                          ctypes.c_void_p(stream)))
+    d = {k: int(getattr(t, k)) for k, _ in Tallies._fields_ if k != "reserved"}
+    d["hist"] = hist
+    d["faces"] = faces
+    return d
+
+
+def table_rows(grid, d_table: int, ncell: int, J: int, K: int, stream: int = 0):
+    thr = np.zeros(ncell * J * (K - 1), dtype=np.uint32)
+    flags = np.zeros(ncell * J, dtype=np.uint32)
+    _check("rddmc_table_rows", lib().rddmc_table_rows(ctypes.c_void_p(grid), ctypes.c_void_p(d_table),
+                                                      _np_ptr(thr), _np_ptr(flags), ctypes.c_void_p(stream)))
+    return thr.reshape(ncell * J, K - 1), flags
+
+
+def read_packet_states(grid, d_state: int, n_packets: int, first: int, count: int, stream: int = 0) -> dict:
+    out = dict(cell=np.zeros(count, np.uint32), bin=np.zeros(count, np.uint32), steps=np.zeros(count, np.uint64),
+               event_draws=np.zeros(count, np.uint64), status=np.zeros(count, np.uint8))
+    _check("rddmc_read_packet_states", lib().rddmc_read_packet_states(
+        ctypes.c_void_p(grid), ctypes.c_void_p(d_state), int(n_packets), int(first), int(count),
+        _np_ptr(out["cell"]), _np_ptr(out["bin"]), _np_ptr(out["steps"]), _np_ptr(out["event_draws"]),
+        _np_ptr(out["status"]), ctypes.c_void_p(stream)))
+    return out
+
+
+# ----------------------------------------------------------------------------- convenience
+class Problem:
+    """A workload bound to the library: handle, table, tallies and packet state
+    in caller-owned torch device buffers."""
+
+    def __init__(self, w, mode=MODE_DDMC, layout=LAYOUT_DEDUP, tau_ddmc=5.0, lam=0.7104, f_mu=0.5,
+                 device="cuda", n_rel=None, edges=None):
+        import torch
+        self.torch = torch
+        self.w = w
+        self.device = torch.device(device)
+        geom = GEOM_SLAB_1D if w.ndim == 1 else GEOM_CART_3D
+        self.edges = np.asarray(w.edges() if edges is None else edges, dtype=np.float64)
+        self.grid = build_grid(geom, w.n, self.edges, w.R, w.tau0, w.T, n_rel=n_rel, v_kms=w.velocity_kms(),
+                               mask=w.mask(), layout=layout)
+        self.J = len(self.edges) - 1
+        self.nfaces = 2 * w.ndim
+        self.K = 2 + 2 * w.ndim
+        s = grid_sizes(self.grid, 1)
+        self.sizes = s
+        self.table = torch.empty(int(s.table_bytes), dtype=torch.uint8, device=self.device)
+        self.tally = torch.zeros(int(s.tally_bytes) // 8, dtype=torch.int64, device=self.device)
+        self.state = None
+        self.state_packets = 0
+        self.params = LeakParams(tau_ddmc, lam, f_mu, mode, 0)
+        precompute_leakage(self.grid, self.params, self.table.data_ptr(), self.table.numel(), self.stream())
+
+    def stream(self) -> int:
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def ensure_state(self, n_packets: int):
+        need = int(grid_sizes(self.grid, n_packets).state_bytes)
+        if self.state is None or self.state.numel() < need:
+            self.state = self.torch.empty(need, dtype=self.torch.uint8, device=self.device)
+        return self.state
+
+    def reset(self):
+        reset_tallies(self.grid, self.tally.data_ptr(), self.tally.numel() * 8, self.stream())
+
+    def launch(self, n_packets: int, seed: int, max_steps: int = 0, steps_per_launch: int = 0, resume: int = 0,
+               ctas_per_sm: int = 0, threads_per_cta: int = 0, chunk: int = 0, table_in_smem: int = 1):
+        st = self.ensure_state(n_packets)
+        o = RunOpts(seed, n_packets, max_steps, steps_per_launch, resume, ctas_per_sm, threads_per_cta, chunk,
+                    table_in_smem, 0)
+        launch_packets(self.grid, self.table.data_ptr(), o, st.data_ptr(), st.numel(), self.tally.data_ptr(),
+                       self.tally.numel() * 8, self.stream())
+
+    def read(self) -> dict:
+        return read_tallies(self.grid, self.tally.data_ptr(), self.J, self.nfaces, self.stream())
+
+    def run(self, n_packets: int, seed: int, **kw) -> dict:
+        self.reset()
+        self.launch(n_packets, seed, **kw)
+        return self.read()
+
+    def packet_states(self, n_packets: int, first: int, count: int) -> dict:
+        return read_packet_states(self.grid, self.state.data_ptr(), n_packets, first, count, self.stream())
+
+    def rows(self):
+        return table_rows(self.grid, self.table.data_ptr(), self.w.ncell, self.J, self.K, self.stream())
+
+    def close(self):
+        destroy_grid(self.grid)
+        self.grid = None
+
+    def __del__(self):
+        try:
+            if self.grid:
+                destroy_grid(self.grid)
+        except Exception:
+            pass

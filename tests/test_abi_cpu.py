@@ -1,0 +1,89 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+declared in include/rddmc.h, and its host-only calls (grid validation, class
+deduplication, buffer sizes) behave as documented."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1709_10187_gb300 import build as B
+from paper_1709_10187_gb300 import rddmc as R
+from paper_1709_10187_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "rddmc.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(rddmc_\w+)\s*\(", txt, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = _declared()
+    assert len(names) >= 10
+    L = R.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(R.EXPORTED)
+    assert R.lib().rddmc_version() >= 100
+    assert R.status_string(R.ERR_SIZE) == "buffer too small"
+
+
+def _grid(w, **kw):
+    return R.build_grid(R.GEOM_SLAB_1D if w.ndim == 1 else R.GEOM_CART_3D, w.n, w.edges(), w.R, w.tau0, w.T,
+                        v_kms=w.velocity_kms(), mask=w.mask(), **kw)
+
+
+def test_dedup_classes_and_sizes():
+    g = _grid(W.C2)
+    s = R.grid_sizes(g, 10_000_000)
+    # uniform static slab: left boundary cell, interior cells, right boundary cell
+    assert s.n_class == 3 and s.row_bytes == 16 and s.n_outcomes == 4
+    assert s.table_bytes >= 3 * 512 * 16
+    assert s.tally_bytes == (22 + 512 + 2) * 8
+    assert s.state_bytes >= 10_000_000 * 25
+    R.destroy_grid(g)
+    g = _grid(W.C2, layout=R.LAYOUT_DENSE)
+    assert R.grid_sizes(g, 1).n_class == 256
+    R.destroy_grid(g)
+    # a density gradient leaves every cell its own class
+    w = W.SMALL
+    g = R.build_grid(R.GEOM_SLAB_1D, w.n, w.edges(), w.R, w.tau0, w.T, n_rel=np.linspace(0.5, 2.0, w.ncell))
+    assert R.grid_sizes(g, 1).n_class == w.ncell
+    R.destroy_grid(g)
+
+
+@pytest.mark.parametrize("bad", ["nbins", "edges", "tau0", "slab_n", "density", "source"])
+def test_grid_validation_rejects_bad_input(bad):
+    w = W.SMALL
+    e = w.edges()
+    kw = dict(geometry=R.GEOM_SLAB_1D, n=w.n, edges=e, R=w.R, tau0=w.tau0, T=w.T)
+    if bad == "nbins":
+        kw["edges"] = e[:1]
+    elif bad == "edges":
+        e2 = e.copy(); e2[3] = e2[2]; kw["edges"] = e2
+    elif bad == "tau0":
+        kw["tau0"] = -1.0
+    elif bad == "slab_n":
+        kw["n"] = (w.n[0], 2, 1)
+    elif bad == "density":
+        kw["n_rel"] = np.full(w.ncell, -1.0)
+    elif bad == "source":
+        kw["edges"] = np.linspace(1.0, 5.0, w.J + 1)   # x0 = 0 outside the grid
+    with pytest.raises(R.RDDMCError) as ei:
+        R.build_grid(**kw)
+    assert ei.value.status == R.ERR_ARG
+
+
+def test_moving_medium_requires_uniform_bins():
+    w = W.Workload("m", 3, (4, 4, 4), 8, -8.0, 8.0, 1e3, 1e4, 1, 1, sphere=True, vmax_kms=20.0)
+    e = np.concatenate([[-8.0], np.sort(np.random.default_rng(1).uniform(-8, 8, 7)), [8.0]])
+    with pytest.raises(R.RDDMCError) as ei:
+        R.build_grid(R.GEOM_CART_3D, w.n, e, w.R, w.tau0, w.T, v_kms=w.velocity_kms(), mask=w.mask())
+    assert ei.value.status == R.ERR_UNSUPPORTED

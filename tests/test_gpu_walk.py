@@ -1,0 +1,191 @@
+"""GPU parity of the leakage table and the DDMC walk against the FP64 oracle.
+
+Integer results are compared bit-exactly (thresholds to one count where CUDA's
+and the C library's erf/exp may round differently), spectra statistically
+against the exact absorbing chain and the Neufeld profile.  All calls go
+through the C-ABI (paper_1709_10187_gb300.rddmc)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import analytic as A  # noqa: E402
+from oracle import coracle as C  # noqa: E402
+from paper_1709_10187_gb300 import build as B  # noqa: E402
+from paper_1709_10187_gb300 import rddmc as R  # noqa: E402
+from paper_1709_10187_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+# Edge cases: a single grey bin, a single cell (both faces exterior), a wide
+# histogram that does not fit shared memory, odd cell/bin counts.
+ONE_BIN = W.Workload("slab_one_bin_9x1", 1, (9, 1, 1), 1, -5.0, 5.0, 50.0, 1.0e4, 4000, 0x5EED0201)
+ONE_CELL = W.Workload("slab_one_cell_1x21", 1, (1, 1, 1), 21, -10.0, 10.0, 30.0, 1.0e4, 4000, 0x5EED0202)
+WIDE_J = W.Workload("slab_wide_hist_5x9001", 1, (5, 1, 1), 9001, -450.0, 450.0, 2.0e3, 1.0e4, 1000, 0x5EED0203)
+BIT_EXACT = [W.TINY, W.SMALL, W.GREY_LIKE, ONE_BIN, ONE_CELL, WIDE_J]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    assert torch.cuda.is_available()
+
+
+def _oracle(w, hybrid=False):
+    g = C.Grid(w, hybrid=hybrid)
+    return g, g.table()
+
+
+def _same_tallies(gpu, orc, check_draws=True):
+    for k in ("emitted", "escaped", "aborted", "steps", "clamps"):
+        assert gpu[k] == orc[k], (k, gpu[k], orc[k])
+    if check_draws:
+        assert gpu["event_draws"] == orc["event_draws"]
+    assert np.array_equal(gpu["hist"], orc["hist"])
+    assert np.array_equal(gpu["faces"], orc["faces"][: len(gpu["faces"])])
+
+
+@pytest.mark.parametrize("w", BIT_EXACT + [W.C1, W.C2, W.P1, W.P2], ids=lambda w: w.name)
+@pytest.mark.parametrize("hybrid", [False, True], ids=["ddmc", "hybrid"])
+def test_table_matches_oracle(w, hybrid):
+    og, ot = _oracle(w, hybrid)
+    p = R.Problem(w, mode=R.MODE_HYBRID if hybrid else R.MODE_DDMC)
+    thr, flags = p.rows()
+    assert np.array_equal(flags, ot["flags"])
+    d = thr.astype(np.int64) - ot["thr"].astype(np.int64)
+    assert np.abs(d).max() <= 1
+    assert (d != 0).mean() <= 1e-4, (d != 0).sum()
+
+
+@pytest.mark.parametrize("w", BIT_EXACT, ids=lambda w: w.name)
+def test_walk_bit_exact_vs_oracle(w):
+    og, ot = _oracle(w)
+    p = R.Problem(w)
+    thr, flags = p.rows()
+    assert np.array_equal(thr, ot["thr"]), "tables differ: bit-exact walk needs identical thresholds"
+    gpu = p.run(w.packets, w.seed)
+    orc = C.walk(og, ot, w.seed, 0, w.packets)
+    _same_tallies(gpu, orc)
+    assert gpu["status"] == R.OK
+    assert gpu["emitted"] == gpu["escaped"] == w.packets
+
+
+def test_walk_bit_exact_c1_subset_and_p2():
+    for w, npk in ((W.C1, 200), (W.P2, 20000)):
+        og, ot = _oracle(w)
+        p = R.Problem(w)
+        thr, _ = p.rows()
+        assert np.array_equal(thr, ot["thr"])
+        _same_tallies(p.run(npk, w.seed), C.walk(og, ot, w.seed, 0, npk))
+
+
+def test_time_sliced_launches_equal_one_launch():
+    w = W.SMALL
+    p = R.Problem(w)
+    one = p.run(w.packets, w.seed)
+    p.reset()
+    n = 0
+    while True:
+        p.launch(w.packets, w.seed, steps_per_launch=64, resume=1 if n else 0)
+        n += 1
+        t = p.read()
+        if t["escaped"] + t["aborted"] == w.packets:
+            break
+        assert n < 10_000
+    _same_tallies(t, one)
+    assert n > 10
+
+
+def test_watchdog_aborts_match_oracle():
+    w = W.SMALL
+    og, ot = _oracle(w)
+    p = R.Problem(w)
+    gpu = p.run(w.packets, w.seed, max_steps=1001)
+    orc = C.walk(og, ot, w.seed, 0, w.packets, max_steps=1001)
+    _same_tallies(gpu, orc)
+    assert gpu["aborted"] > 0 and gpu["status"] == R.ERR_STEP_LIMIT
+
+
+@pytest.mark.parametrize("sched", [dict(ctas_per_sm=1, threads_per_cta=64, chunk=4, table_in_smem=0),
+                                   dict(ctas_per_sm=2, threads_per_cta=256, chunk=256, table_in_smem=1),
+                                   dict(threads_per_cta=96, chunk=12)])
+def test_schedule_does_not_change_results(sched):
+    w = W.SMALL
+    p = R.Problem(w)
+    ref = p.run(w.packets, w.seed)
+    _same_tallies(p.run(w.packets, w.seed, **sched), ref)
+
+
+def test_dense_layout_equals_dedup_layout():
+    w = W.GREY_LIKE
+    a = R.Problem(w).run(w.packets, w.seed)
+    b = R.Problem(w, layout=R.LAYOUT_DENSE).run(w.packets, w.seed)
+    _same_tallies(a, b)
+
+
+@pytest.mark.parametrize("npk", [1, 31, 33, 1000])
+def test_ragged_packet_counts(npk):
+    w = W.TINY
+    og, ot = _oracle(w)
+    _same_tallies(R.Problem(w).run(npk, w.seed + npk), C.walk(og, ot, w.seed + npk, 0, npk))
+
+
+def test_hybrid_launch_reports_unsupported():
+    p = R.Problem(W.TINY, mode=R.MODE_HYBRID)
+    with pytest.raises(R.RDDMCError) as ei:
+        p.run(10, 1)
+    assert ei.value.status == R.ERR_UNSUPPORTED
+
+
+def test_spectrum_p1_matches_chain_and_neufeld():
+    # Fig. 2 setup, 1e6 packets: 3 sigma against the exact chain; L1 <= 2% vs eq. Neufeld.
+    w = W.P1
+    og, ot = _oracle(w)
+    ch = A.chain_solve(w, ot)
+    gpu = R.Problem(w).run(w.packets, w.seed)
+    N = w.packets
+    assert gpu["escaped"] == N
+    zmax, frac, pval = A.compare_counts_to_probs(gpu["hist"], ch["hist"], N)
+    assert zmax < 5.0 and frac <= 0.02 and pval > 1e-3, (zmax, frac, pval)
+    zs = (gpu["steps"] / N - ch["steps_mean"]) / np.sqrt(ch["steps_var"] / N)
+    assert abs(zs) < 4.0
+    l1 = A.l1_distance(gpu["hist"][1:-1], A.neufeld_bin_mass(w.edges(), C.damping(w.T) * w.tau0))
+    assert l1 <= 0.02, l1
+
+
+def test_spectrum_c1_matches_chain():
+    w = W.C1
+    og, ot = _oracle(w)
+    ch = A.chain_solve(w, ot)
+    gpu = R.Problem(w).run(w.packets, w.seed)
+    zmax, frac, pval = A.compare_counts_to_probs(gpu["hist"], ch["hist"], w.packets)
+    assert zmax < 5.0 and frac <= 0.02 and pval > 1e-3, (zmax, frac, pval)
+    zs = (gpu["steps"] / w.packets - ch["steps_mean"]) / np.sqrt(ch["steps_var"] / w.packets)
+    assert abs(zs) < 4.0
+
+
+def test_c2_full_size_sampled_packets_replay_exactly():
+    # tau0 = 1e7 slab, 256 x 512, all 1e7 packets, one time slice of 4096
+    # transitions as the benchmark launches it; sampled packets are replayed one
+    # by one by the oracle and must end in the same state.
+    w = W.C2
+    S = 4096
+    og, ot = _oracle(w)
+    p = R.Problem(w)
+    thr, _ = p.rows()
+    assert np.array_equal(thr, ot["thr"])
+    p.reset()
+    p.launch(w.packets, w.seed, steps_per_launch=S)
+    t = p.read()
+    assert t["emitted"] == w.packets
+    ids = np.unique(np.concatenate([np.arange(8), np.linspace(8, w.packets - 1, 40).astype(np.int64)]))
+    for pid in ids:
+        st = p.packet_states(w.packets, int(pid), 1)
+        ref = C.replay_packet(og, ot, w.seed, int(pid), S)
+        assert st["status"][0] == (2 if ref["done"] else 1)
+        if not ref["done"]:
+            assert (st["cell"][0], st["bin"][0], st["steps"][0], st["event_draws"][0]) == \
+                (ref["cell"], ref["bin"], ref["steps"], ref["event_draws"])
+    # every packet advanced S transitions unless it escaped first
+    assert t["steps"] <= w.packets * S
+    assert t["steps"] + t["escaped"] * S >= w.packets * S
