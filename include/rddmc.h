@@ -3,12 +3,12 @@
  * Carlo library (Smith, Tsang, Bromm & Milosavljevic 2017, "Discrete diffusion
  * Lyman alpha radiative transfer").
  *
- * The problem a caller states (Sec. 2.2, Sec. 2.4): a medium on a Cartesian
+ * The problem a caller states (Sec. 2.2, Sec. 2.3): a medium on a Cartesian
  * grid of cells (hydrogen density, temperature, bulk velocity per cell), a
  * discretisation of the comoving frequency x = (nu - nu0)/dnu_D into bins, and
  * a monochromatic source at the domain centre.  The library walks photon
  * packets on the joint (cell, bin) grid with the Fokker-Planck leakage
- * probabilities of Sec. 2.3 until they leave the domain, and tallies the
+ * probabilities of Sec. 2.2 until they leave the domain, and tallies the
  * escaping spectrum.
  *
  * Conventions for every function:
@@ -57,12 +57,12 @@ extern "C" {
  *   geometry   RDDMC_GEOM_SLAB_1D or RDDMC_GEOM_CART_3D.
  *   n[3]       cells per axis; a slab uses n[0] and requires n[1] = n[2] = 1.
  *              Cell index c = i0 + n0*(i1 + n1*i2); cubic domain [-R, R]^d with
- *              uniform widths dz_a = 2R/n[a] (Sec. 2.3, eq. z-leakage).
+ *              uniform widths dz_a = 2R/n[a] (Sec. 2.2, eq. z-leakage).
  *   nbins      number J of frequency bins (>= 1, <= 65535).
  *   layout     RDDMC_LAYOUT_DEDUP or RDDMC_LAYOUT_DENSE (table organisation).
  *   R          half-width of the domain (length unit of the problem).
  *   tau0       line-centre optical depth k0 R at unit density (k_x = k0 H(a,x),
- *              Sec. 2.3); a cell's k0 is tau0/R times its n_rel.
+ *              Sec. 2.2); a cell's k0 is tau0/R times its n_rel.
  *   T          gas temperature in K (isothermal; sets a = 4.702e-4 T4^-1/2 and
  *              v_th = 12.85 T4^1/2 km/s, Sec. 2.1).
  *   freq_edges host, nbins+1 strictly increasing comoving x edges (FP64).  Moving
@@ -158,7 +158,7 @@ typedef struct rddmc_tallies {
     int32_t status;        /* RDDMC_OK or a device-side error code */
     int32_t nbins;         /* J; the histogram has J + 2 entries */
     int32_t nfaces;        /* 2 (slab) or 6 (3D) */
-    int32_t reserved;
+    int32_t nsb;           /* impact-parameter bins (64) of the surface-brightness histogram */
 } rddmc_tallies;
 
 typedef struct rddmc_grid rddmc_grid; /* opaque host handle */
@@ -170,7 +170,9 @@ typedef struct rddmc_grid rddmc_grid; /* opaque host handle */
  * of Philox(ctr = ((e>>2)_lo, (e>>2)_hi, p_lo, p_hi | 2^31)).  Event draw 0
  * picks the source cell and bin (bit 31-a: cell along axis a when two cells
  * straddle the centre; bit 28: bin when x0 is a bin edge); a Doppler rebin
- * takes one event draw; a DDMC escape from a moving cell takes five.
+ * takes one event draw; a DDMC escape takes five (a point on the exit face:
+ * two; the outward direction: mu uniform on (0,1] and the azimuth; x uniform
+ * in the bin) in 3D and from a moving slab cell, none from a static slab cell.
  */
 
 /*
@@ -178,7 +180,7 @@ typedef struct rddmc_grid rddmc_grid; /* opaque host handle */
  * Groups cells whose leakage rows are provably identical (same density,
  * velocity and neighbour data on every face) into classes when layout is
  * RDDMC_LAYOUT_DEDUP; this is the factoring of space and frequency noted for
- * uniform media in Sec. 2.3.  Host-only: no device memory is touched.
+ * uniform media in Sec. 2.2.  Host-only: no device memory is touched.
  *   desc  host, grid description (read during the call only).
  *   out   host, receives the handle; release it with rddmc_destroy_grid.
  * Errors: RDDMC_ERR_ARG (nulls, non-increasing edges, negative density, bad
@@ -199,7 +201,7 @@ int rddmc_grid_sizes(const rddmc_grid* grid, uint64_t n_packets, rddmc_sizes* ou
 /*
  * rddmc_precompute_leakage -- fill the device table (FP64 kernel).
  * Per state (cell class i, bin j): the bin-mean opacity
- * k_ij = k0_i (calH(a, x_j+) - calH(a, x_j-)) / dx_j (Sec. 2.3), the spatial
+ * k_ij = k0_i (calH(a, x_j+) - calH(a, x_j-)) / dx_j (Sec. 2.2), the spatial
  * leakage coefficients of eq. z-leakage (exterior faces and, in hybrid mode,
  * thin neighbours use the boundary form 2/(3 dz (k dz + 2 lambda)), Sec. 5.1),
  * the frequency leakage coefficients of eq. x-leakage (none beyond the grid
@@ -221,13 +223,13 @@ int rddmc_precompute_leakage(rddmc_grid* grid, const rddmc_leak_params* params, 
 int rddmc_reset_tallies(const rddmc_grid* grid, void* d_tallies, size_t tally_bytes, void* stream);
 
 /*
- * rddmc_launch_packets -- walk packets (Sec. 2.4) with one persistent kernel.
+ * rddmc_launch_packets -- walk packets (Sec. 2.3) with one persistent kernel.
  * Each thread holds one packet: it draws one word of the packet's transition
  * stream per transition, gathers the 16/32-byte row of its state and takes the
  * outcome whose threshold interval holds the word (the categorical form of the
  * competing exponentials of eq. l_min_1/2: the argmin of independent
  * exponentials with rates k_X is X with probability k_X / sum k).  Packets
- * leaving the domain (Sec. 2.4: removed at the boundary) are tallied; finished
+ * leaving the domain (Sec. 2.3: removed at the boundary) are tallied; finished
  * lanes refill from a global packet cursor one warp at a time.  Tallies are
  * accumulated into d_tallies (call rddmc_reset_tallies first).
  *   d_table    device, filled by rddmc_precompute_leakage for this grid.
@@ -236,7 +238,7 @@ int rddmc_reset_tallies(const rddmc_grid* grid, void* d_tallies, size_t tally_by
  *              256-byte aligned: packet cursor and per-packet saved state.
  *   d_tallies  device tally buffer.
  * Errors: RDDMC_ERR_ARG, RDDMC_ERR_SIZE, RDDMC_ERR_UNSUPPORTED (hybrid mode,
- * not yet implemented), RDDMC_ERR_CUDA.  Device-side conditions (watchdog
+ * not yet implemented), RDDMC_ERR_TABLE, RDDMC_ERR_CUDA.  Device-side conditions (watchdog
  * aborts) are reported by rddmc_read_tallies.
  */
 int rddmc_launch_packets(const rddmc_grid* grid, const void* d_table, const rddmc_run_opts* opts,
@@ -250,11 +252,16 @@ int rddmc_launch_packets(const rddmc_grid* grid, const void* d_table, const rddm
  *              J+1: above) of escaping packets in the observer frame, or NULL.
  *   faces      host, 2 (slab: -z, +z) or 6 (-x,+x,-y,+y,-z,+z) uint64 escape
  *              counts per exterior face direction, or NULL.
+ *   sb         host, 64 uint64, or NULL: 3D escapes binned by impact parameter
+ *              b = |r x n| of the escaping ray (r the exit point relative to
+ *              the domain centre, n the direction), 64 bins over b/R in
+ *              [0, 1.28) with larger b in the last bin (angle-averaged radial
+ *              surface brightness; directional binning, Sec. 5.4).
  * Returns RDDMC_OK; `out->status` holds RDDMC_ERR_STEP_LIMIT if any packet was
  * aborted.
  */
 int rddmc_read_tallies(const rddmc_grid* grid, const void* d_tallies, rddmc_tallies* out, uint64_t* hist,
-                       uint64_t* faces, void* stream);
+                       uint64_t* faces, uint64_t* sb, void* stream);
 
 /*
  * rddmc_table_rows -- expand the device table to one row per state (host), for

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Functions mirror the C
 entry points; arrays are numpy.  Unit conversions the C code does not do
 (velocity in km/s -> Doppler units with v_th = 12.85 (T/1e4 K)^(1/2) km/s,
-Sec. 2.1) are done here, on the oracle side.
+Sec. 2.1) happen in the C code.
 """
 from __future__ import annotations
 
@@ -22,7 +22,7 @@ class OrcGrid(ctypes.Structure):
         ("ndim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("J", ctypes.c_int32), ("hybrid", ctypes.c_int32),
         ("R", ctypes.c_double), ("tau0", ctypes.c_double), ("T", ctypes.c_double),
         ("tau_ddmc", ctypes.c_double), ("lam", ctypes.c_double), ("f_mu", ctypes.c_double),
-        ("edges", ctypes.c_void_p), ("n_rel", ctypes.c_void_p), ("u", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+        ("edges", ctypes.c_void_p), ("n_rel", ctypes.c_void_p), ("v", ctypes.c_void_p), ("mask", ctypes.c_void_p),
     ]
 
 
@@ -110,7 +110,7 @@ class Grid:
         self.edges = np.ascontiguousarray(e, dtype=np.float64)
         self.n_rel = None if n_rel is None else np.ascontiguousarray(n_rel, dtype=np.float64)
         v = w.velocity_kms()
-        self.u = None if v is None else np.ascontiguousarray(v / vth_kms(w.T), dtype=np.float64)
+        self.v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
         m = w.mask()
         self.mask = None if m is None else np.ascontiguousarray(m, dtype=np.uint8)
         g = OrcGrid()
@@ -120,7 +120,7 @@ class Grid:
         g.J, g.hybrid = w.J, int(hybrid)
         g.R, g.tau0, g.T = w.R, w.tau0, w.T
         g.tau_ddmc, g.lam, g.f_mu = tau_ddmc, lam, f_mu
-        g.edges, g.n_rel, g.u, g.mask = (_ptr(self.edges), _ptr(self.n_rel), _ptr(self.u), _ptr(self.mask))
+        g.edges, g.n_rel, g.v, g.mask = (_ptr(self.edges), _ptr(self.n_rel), _ptr(self.v), _ptr(self.mask))
         self.g = g
         self.K = 2 + 2 * w.ndim
         self.ncell = w.ncell
@@ -143,6 +143,8 @@ class Grid:
         return t
 
 
+NSB = 64          # impact-parameter bins over b/R in [0, 1.28)
+SB_MAX = 1.28
 TALLY_NAMES = ["emitted", "escaped", "aborted", "steps", "mc_events", "conversions", "clamps", "event_draws"]
 
 
@@ -150,6 +152,7 @@ def unpack_tally(t: np.ndarray, J: int) -> dict:
     d = {name: int(t[i]) for i, name in enumerate(TALLY_NAMES)}
     d["faces"] = t[8:14].astype(np.uint64).copy()
     d["hist"] = t[14:14 + J + 2].astype(np.uint64).copy()
+    d["sb"] = t[14 + J + 2:14 + J + 2 + NSB].astype(np.uint64).copy()
     return d
 
 

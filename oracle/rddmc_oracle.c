@@ -13,13 +13,13 @@
  *   - Dawson integral F(x): Maclaurin series near 0, Rybicki's (1989,
  *     Computers in Physics 3(2), 85) sampling-theorem series elsewhere.
  *   - Hjerting-Voigt H(a,x) to second order in a, and its integral calH(a,x)
- *     (Sec. 2.3, eq. H_approx and the integrated form below it).
- *   - bin-mean opacity k_j = k0 (calH(x_j+) - calH(x_j-)) / dx_j (Sec. 2.3).
+ *     (Sec. 2.2, eq. H_approx and the integrated form below it).
+ *   - bin-mean opacity k_j = k0 (calH(x_j+) - calH(x_j-)) / dx_j (Sec. 2.2).
  *   - leakage coefficients eq. z-leakage, eq. x-leakage; the hybrid
  *     DDMC->MC boundary coefficient with extrapolation distance lambda (Sec. 5.1);
  *     the comoving Doppler shift of bin edges across faces, eq. velocity-shift.
  *   - Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011, SC'11).
- *   - the DDMC walk of Sec. 2.4: the leakage with the smallest sampled distance
+ *   - the DDMC walk of Sec. 2.3: the leakage with the smallest sampled distance
  *     is executed.  Two forms are provided: the literal competing exponentials
  *     (eq. l_min_1, l_min_2) and the equivalent categorical draw on quantised
  *     cumulative probabilities, which defines the random-stream contract shared
@@ -33,8 +33,9 @@
  *     event stream: event draw e of p uses lane e&3 of
  *       Philox4x32-10(ctr = ((e>>2)_lo, (e>>2)_hi, p_lo, p_hi | 2^31), key).
  *   Event draw 0 picks the source cell/bin; a Doppler rebin takes the next event
- *   draw; a DDMC escape from a moving cell takes five (face point 2, mu, phi,
- *   x in bin).  A uniform in (0,1) is (w + 0.5) * 2^-32.
+ *   draw; a DDMC escape takes five (face point 2, mu, phi, x in bin) in 3D or
+ *   from a moving slab cell, none from a static slab cell.  A uniform in (0,1)
+ *   is (w + 0.5) * 2^-32.
  */
 #include <math.h>
 #include <pthread.h>
@@ -47,7 +48,7 @@
 #define ORC_TWO32 4294967296.0
 
 /* ------------------------------------------------------------------------- */
-/* Physics (Sec. 2.1, Sec. 2.3)                                               */
+/* Physics (Sec. 2.1, Sec. 2.2)                                               */
 /* ------------------------------------------------------------------------- */
 
 /* Damping parameter a = 4.702e-4 * (T / 1e4 K)^(-1/2)  (Sec. 2.1). */
@@ -149,7 +150,7 @@ static uint32_t orc_word(uint64_t seed, uint64_t p, int which, uint64_t n) {
 static double orc_unif(uint32_t w) { return ((double)w + 0.5) / ORC_TWO32; }
 
 /* ------------------------------------------------------------------------- */
-/* Grid and leakage table (Sec. 2.3, Sec. 2.5, Sec. 5.1)                      */
+/* Grid and leakage table (Sec. 2.2, Sec. 2.5, Sec. 5.1)                      */
 /* ------------------------------------------------------------------------- */
 
 typedef struct orc_grid {
@@ -165,7 +166,7 @@ typedef struct orc_grid {
     double f_mu;      /* flux directionality factor of eq. velocity-shift */
     const double* edges;  /* J+1 ascending comoving frequency edges */
     const double* n_rel;  /* per-cell density scale, NULL = 1 */
-    const double* u;      /* per-cell bulk velocity / v_th, 3 per cell, NULL = static */
+    const double* v;      /* per-cell bulk velocity in km/s, 3 per cell, NULL = static */
     const uint8_t* mask;  /* per-cell 1 = medium, 0 = vacuum, NULL = all medium */
 } orc_grid;
 
@@ -204,13 +205,16 @@ static double orc_k0(const orc_grid* g, int64_t c) {
 
 static double orc_dz(const orc_grid* g, int axis) { return 2.0 * g->R / g->n[axis]; }
 
+/* Thermal velocity v_th = 12.85 (T/1e4 K)^(1/2) km/s (Sec. 2.1). */
+static double orc_vth(const orc_grid* g) { return 12.85 * sqrt(g->T / 1.0e4); }
+
 /* Comoving frequency shift for crossing from cell c to cell nb through the face
- * with unit normal +/- e_axis: x' = x + f_mu n.(u_c - u_nb), the isothermal
- * form of eq. velocity-shift. */
+ * with unit normal +/- e_axis: x' = x + f_mu n.(v_c - v_nb)/v_th, the
+ * isothermal form of eq. velocity-shift. */
 static double orc_face_shift(const orc_grid* g, int64_t c, int64_t nb, int axis, int side) {
-    if (!g->u) return 0.0;
-    double du = g->u[3 * c + axis] - g->u[3 * nb + axis];
-    return g->f_mu * (double)side * du;
+    if (!g->v) return 0.0;
+    double dv = g->v[3 * c + axis] - g->v[3 * nb + axis];
+    return g->f_mu * (double)side * (dv / orc_vth(g));
 }
 
 /* Quantise a cumulative probability to a 32-bit threshold: round half to even
@@ -249,8 +253,8 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
         orc_idx_of(g, c, idx);
         const double k0c = orc_k0(g, c);
         int moving = 0;
-        if (g->u)
-            for (int ax = 0; ax < 3; ++ax) moving |= (g->u[3 * c + ax] != 0.0);
+        if (g->v)
+            for (int ax = 0; ax < 3; ++ax) moving |= (g->v[3 * c + ax] != 0.0);
         /* Doppler rebin per face, uniform bins assumed (checked by the caller). */
         double dx0 = g->edges[1] - g->edges[0];
         for (int ax = 0; ax < g->ndim; ++ax)
@@ -322,7 +326,7 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
 }
 
 /* ------------------------------------------------------------------------- */
-/* Walk (Sec. 2.4)                                                           */
+/* Walk (Sec. 2.3)                                                           */
 /* ------------------------------------------------------------------------- */
 
 /* Tally layout (uint64): see ORC_T_* ; faces [ORC_T_FACE, +6); histogram of
@@ -337,8 +341,10 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
 #define ORC_T_EVENT_DRAWS 7
 #define ORC_T_FACE 8
 #define ORC_T_HIST 14
+#define ORC_NSB 64          /* impact-parameter bins over b/R in [0, 1.28); larger b in the last bin */
+#define ORC_SB_MAX 1.28
 
-int orc_tally_len(int J) { return ORC_T_HIST + J + 2; }
+int orc_tally_len(int J) { return ORC_T_HIST + J + 2 + ORC_NSB; }
 
 /* Source: the cell(s) at the domain centre and the bin(s) containing x0.  With
  * an even count the centre is a face/edge and both neighbours are used with
@@ -387,28 +393,43 @@ typedef struct orc_walk_args {
     int status;
 } orc_walk_args;
 
-/* Escape through the face of outcome o from cell c at bin j: tally the
- * observer-frame frequency.  Static cell: the packet's bin.  Moving cell: a
- * point on the face, an isotropic outward direction (mu uniform on (0,1],
- * azimuth uniform) and x uniform in the bin; x_obs = x + n.u_c. */
+/* Escape through the face of outcome o from cell c at bin j.
+ * Slab, static cell: tally the packet's bin.  Otherwise draw a point on the
+ * face (uniform over the cell's face, two draws for the tangential axes), an
+ * isotropic outward direction (mu uniform on (0,1], azimuth phi uniform) and x
+ * uniform in the bin; tally x_obs = x + n.u_c (u = v/v_th) and, in 3D, the
+ * impact parameter b = |r x n| of the escaping ray. */
 static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t pk, uint64_t* e, uint64_t* t) {
     const orc_grid* g = A->g;
     const int J = g->J;
     int face = o - 2;
     t[ORC_T_ESCAPED]++;
     t[ORC_T_FACE + face]++;
-    if (!(A->flags[c * J + j] & ORC_FLAG_MOVING)) { t[ORC_T_HIST + 1 + j]++; return; }
-    /* face point (2 words) is drawn for the position tally; unused here */
-    (void)orc_word(A->seed, pk, ORC_EVENT, (*e)++);
-    (void)orc_word(A->seed, pk, ORC_EVENT, (*e)++);
+    if (g->ndim == 1 && !(A->flags[c * J + j] & ORC_FLAG_MOVING)) { t[ORC_T_HIST + 1 + j]++; return; }
+    int ax = face / 2, side = (face & 1) ? 1 : -1;
+    int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+    int idx[3];
+    orc_idx_of(g, c, idx);
+    double r[3];
+    r[ax] = -g->R + (idx[ax] + (side > 0 ? 1 : 0)) * orc_dz(g, ax);
+    double p1 = orc_unif(orc_word(A->seed, pk, ORC_EVENT, (*e)++));
+    double p2 = orc_unif(orc_word(A->seed, pk, ORC_EVENT, (*e)++));
+    r[t1] = (t1 < g->ndim) ? -g->R + (idx[t1] + p1) * orc_dz(g, t1) : 0.0;
+    r[t2] = (t2 < g->ndim) ? -g->R + (idx[t2] + p2) * orc_dz(g, t2) : 0.0;
     double mu = 1.0 - orc_unif(orc_word(A->seed, pk, ORC_EVENT, (*e)++));
     double ph = 2.0 * ORC_PI * orc_unif(orc_word(A->seed, pk, ORC_EVENT, (*e)++));
     double xu = orc_unif(orc_word(A->seed, pk, ORC_EVENT, (*e)++));
     double x = g->edges[j] + xu * (g->edges[j + 1] - g->edges[j]);
-    int ax = face / 2, side = (face & 1) ? 1 : -1;
-    int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
     double st = sqrt(fmax(0.0, 1.0 - mu * mu));
-    double nu = side * mu * g->u[3 * c + ax] + st * (cos(ph) * g->u[3 * c + t1] + sin(ph) * g->u[3 * c + t2]);
+    double n[3];
+    n[ax] = side * mu;
+    n[t1] = st * cos(ph);
+    n[t2] = st * sin(ph);
+    double nu = 0.0;
+    if (g->v) {
+        double vth = orc_vth(g);
+        nu = n[0] * (g->v[3 * c + 0] / vth) + n[1] * (g->v[3 * c + 1] / vth) + n[2] * (g->v[3 * c + 2] / vth);
+    }
     double xo = x + nu;
     int b;
     if (xo < g->edges[0]) b = 0;
@@ -418,6 +439,14 @@ static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t
         while (b < J && xo >= g->edges[b]) ++b;
     }
     t[ORC_T_HIST + b]++;
+    if (g->ndim == 3) {
+        double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        double rn = r[0] * n[0] + r[1] * n[1] + r[2] * n[2];
+        double bb = sqrt(fmax(0.0, rr - rn * rn)) / g->R;
+        int k = (int)(bb / ORC_SB_MAX * ORC_NSB);
+        if (k > ORC_NSB - 1) k = ORC_NSB - 1;
+        t[ORC_T_HIST + J + 2 + k]++;
+    }
 }
 
 /* Per-packet state of the walk. */

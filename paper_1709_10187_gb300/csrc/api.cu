@@ -47,7 +47,8 @@ uint64_t state_bytes_for(uint64_t np) {
     return b;
 }
 
-uint64_t tally_bytes_for(int J) { return (uint64_t)(kHistOff + J + 2) * 8ull; }
+int tally_words(int J) { return kHistOff + J + 2 + kNsb; }
+uint64_t tally_bytes_for(int J) { return (uint64_t)tally_words(J) * 8ull; }
 
 }  // namespace rddmc
 
@@ -116,16 +117,12 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
     g->n_rel.resize(ncell);
     for (int64_t c = 0; c < ncell; ++c) g->n_rel[c] = d->n_rel ? d->n_rel[c] : 1.0;
     if (d->mask) g->mask.assign(d->mask, d->mask + ncell);
+    g->vth = 12.85 * std::sqrt(d->T / 1.0e4);  // Sec. 2.1
     if (d->v_kms) {
-        const double vth = 12.85 * std::sqrt(d->T / 1.0e4);  // Sec. 2.1
-        g->u.resize(3 * ncell);
         bool any = false;
-        for (int64_t i = 0; i < 3 * ncell; ++i) {
-            g->u[i] = d->v_kms[i] / vth;
-            any |= g->u[i] != 0.0;
-        }
+        for (int64_t i = 0; i < 3 * ncell; ++i) any |= d->v_kms[i] != 0.0;
         g->moving = any;
-        if (!any) g->u.clear();
+        if (any) g->v.assign(d->v_kms, d->v_kms + 3 * ncell);
     }
     if (g->moving && !g->uniform_bins) { delete g; return RDDMC_ERR_UNSUPPORTED; }
 
@@ -152,8 +149,11 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
     }
 
     // Classes of cells with identical rows.  A row depends only on the cell's
-    // density and velocity and, per face, on whether the neighbour is medium and
-    // on its density and normal velocity, so equal keys give equal rows.
+    // density and on whether it moves and, per face, on whether the neighbour is
+    // medium, on its density and on the normal velocity difference across the
+    // face (the Doppler shift of eq. velocity-shift), so equal keys give equal
+    // rows.  The cell's own velocity is only needed at escape and is read from
+    // a per-cell array.
     g->cell_class.assign(ncell, UINT32_MAX);
     if (g->layout == RDDMC_LAYOUT_DENSE) {
         for (int64_t c = 0; c < ncell; ++c) g->cell_class[c] = (uint32_t)c;
@@ -168,7 +168,8 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
             if (!g->in_medium(idx)) continue;
             key.clear();
             key.push_back(g->n_rel[c]);
-            for (int a = 0; a < 3; ++a) key.push_back(g->u.empty() ? 0.0 : g->u[3 * c + a]);
+            key.push_back((!g->v.empty() && (g->v[3 * c] != 0.0 || g->v[3 * c + 1] != 0.0 || g->v[3 * c + 2] != 0.0))
+                              ? 1.0 : 0.0);
             for (int ax = 0; ax < g->ndim; ++ax)
                 for (int sd = 0; sd < 2; ++sd) {
                     int nidx[3] = {idx[0], idx[1], idx[2]};
@@ -177,7 +178,7 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
                     const int64_t nb = g->cell_of(nidx);
                     key.push_back(0.0);
                     key.push_back(g->n_rel[nb]);
-                    key.push_back(g->u.empty() ? 0.0 : g->u[3 * nb + ax]);
+                    key.push_back(g->v.empty() ? 0.0 : g->v[3 * c + ax] - g->v[3 * nb + ax]);
                 }
             auto it = ids.find(key);
             if (it == ids.end()) {
@@ -198,7 +199,7 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
     g->off_class = off; off += align256((uint64_t)ncell * 4);
     g->off_cdesc = off; off += align256((uint64_t)g->n_class * sizeof(ClassDesc));
     g->off_rebin = off; off += align256((uint64_t)g->n_class * g->nfaces * sizeof(Rebin));
-    g->off_cvel = off; off += align256((uint64_t)g->n_class * 16);
+    g->off_vel = off; off += align256(g->moving ? (uint64_t)ncell * 24 : 0);
     g->off_edges = off; off += align256((uint64_t)(J + 1) * 8);
     g->off_phi = off; off += align256((uint64_t)J * 8);
     g->off_rows = off; off += align256((uint64_t)g->n_class * J * g->row_bytes);
@@ -236,7 +237,6 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
     // Per-class inputs of the FP64 precompute kernel.
     std::vector<ClassDesc> cd(g->n_class);
     std::vector<Rebin> rb((size_t)g->n_class * g->nfaces);
-    std::vector<float> cvel((size_t)g->n_class * 4, 0.0f);
     const double dx0 = g->edges[1] - g->edges[0];
     for (int k = 0; k < g->n_class; ++k) {
         const int64_t c = g->class_rep[k];
@@ -245,9 +245,7 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
         ClassDesc& D = cd[k];
         std::memset(&D, 0, sizeof(D));
         D.k0 = g->tau0 / g->R * g->n_rel[c];
-        for (int a = 0; a < 3; ++a) D.u[a] = g->u.empty() ? 0.0 : g->u[3 * c + a];
-        D.moving = (D.u[0] != 0.0 || D.u[1] != 0.0 || D.u[2] != 0.0) ? 1 : 0;
-        for (int a = 0; a < 3; ++a) cvel[4 * k + a] = (float)D.u[a];
+        D.moving = (!g->v.empty() && (g->v[3 * c] != 0.0 || g->v[3 * c + 1] != 0.0 || g->v[3 * c + 2] != 0.0)) ? 1 : 0;
         for (int ax = 0; ax < g->ndim; ++ax)
             for (int sd = 0; sd < 2; ++sd) {
                 const int side = sd ? 1 : -1, f = 2 * ax + sd;
@@ -260,7 +258,8 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
                     const int64_t nb = g->cell_of(nidx);
                     D.face[f].exterior = 0;
                     D.face[f].k0_nb = g->tau0 / g->R * g->n_rel[nb];
-                    if (!g->u.empty()) delta = p->f_mu * (double)side * (g->u[3 * c + ax] - g->u[3 * nb + ax]);
+                    if (!g->v.empty())
+                        delta = p->f_mu * (double)side * ((g->v[3 * c + ax] - g->v[3 * nb + ax]) / g->vth);
                 }
                 D.face[f].delta = delta;
                 const double q = delta / dx0, m = std::floor(q), fr = q - m;
@@ -276,9 +275,9 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
     h.row_bytes = g->row_bytes;
     for (int a = 0; a < 3; ++a) { h.n[a] = g->n[a]; h.dz[a] = 2.0 * g->R / g->n[a]; }
     h.mode = p->mode;
-    h.off_class = g->off_class; h.off_cdesc = g->off_cdesc; h.off_rebin = g->off_rebin; h.off_cvel = g->off_cvel;
+    h.off_class = g->off_class; h.off_cdesc = g->off_cdesc; h.off_rebin = g->off_rebin; h.off_vel = g->off_vel;
     h.off_edges = g->off_edges; h.off_phi = g->off_phi; h.off_rows = g->off_rows; h.total = g->table_bytes;
-    h.tau_ddmc = p->tau_ddmc; h.lambda = p->lambda; h.f_mu = p->f_mu; h.a = g->a;
+    h.tau_ddmc = p->tau_ddmc; h.lambda = p->lambda; h.f_mu = p->f_mu; h.a = g->a; h.vth = g->vth;
 
     char* base = (char*)d_table;
     cudaError_t e;
@@ -292,8 +291,8 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
     if ((e = cudaMemcpyAsync(base + g->off_rebin, rb.data(), rb.size() * sizeof(Rebin), cudaMemcpyHostToDevice, s)) !=
         cudaSuccess)
         return cuda_status(e);
-    if ((e = cudaMemcpyAsync(base + g->off_cvel, cvel.data(), cvel.size() * 4, cudaMemcpyHostToDevice, s)) !=
-        cudaSuccess)
+    if (g->moving && (e = cudaMemcpyAsync(base + g->off_vel, g->v.data(), g->v.size() * 8, cudaMemcpyHostToDevice,
+                                          s)) != cudaSuccess)
         return cuda_status(e);
     if ((e = cudaMemcpyAsync(base + g->off_edges, g->edges.data(), g->edges.size() * 8, cudaMemcpyHostToDevice, s)) !=
         cudaSuccess)
@@ -326,16 +325,15 @@ int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_r
     if (state_bytes < state_bytes_for(o->n_packets)) return RDDMC_ERR_SIZE;
     if (tally_bytes < tally_bytes_for(g->J)) return RDDMC_ERR_SIZE;
     if (g->params.mode == RDDMC_MODE_HYBRID) return RDDMC_ERR_UNSUPPORTED;
-    if (g->ndim != 1) return RDDMC_ERR_UNSUPPORTED;
     WalkLaunch w{d_table, d_state, (unsigned long long*)d_tallies, *o};
     return cuda_status(launch_walk(*g, w, (cudaStream_t)stream));
 }
 
 int rddmc_read_tallies(const rddmc_grid* g, const void* d_tallies, rddmc_tallies* out, uint64_t* hist,
-                       uint64_t* faces, void* stream) {
+                       uint64_t* faces, uint64_t* sb, void* stream) {
     if (!g || !d_tallies || !out) return RDDMC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<uint64_t> t(kHistOff + g->J + 2);
+    std::vector<uint64_t> t(tally_words(g->J));
     cudaError_t e = cudaMemcpyAsync(t.data(), d_tallies, t.size() * 8, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return RDDMC_ERR_CUDA;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return RDDMC_ERR_CUDA;
@@ -352,9 +350,10 @@ int rddmc_read_tallies(const rddmc_grid* g, const void* d_tallies, rddmc_tallies
     if (t[C_STATUS_BITS] & STATUS_UNSUPPORTED_EVENT) out->status = RDDMC_ERR_UNSUPPORTED;
     out->nbins = g->J;
     out->nfaces = g->nfaces;
-    out->reserved = 0;
+    out->nsb = kNsb;
     if (hist) std::memcpy(hist, t.data() + kHistOff, (size_t)(g->J + 2) * 8);
     if (faces) std::memcpy(faces, t.data() + kFaceOff, (size_t)g->nfaces * 8);
+    if (sb) std::memcpy(sb, t.data() + kHistOff + g->J + 2, (size_t)kNsb * 8);
     return RDDMC_OK;
 }
 
@@ -378,9 +377,11 @@ int rddmc_table_rows(const rddmc_grid* g, const void* d_table, uint32_t* thr, ui
                 flags[s_] = 0;
                 continue;
             }
+            // stored words: thr0, thr1, thr2, flags[, thr3..thr6]; FLAG_FASTX is
+            // an encoding detail of the walk and is not returned
             const uint32_t* r = &rows[((uint64_t)k * g->J + j) * wpr];
-            for (int o = 0; o < K - 1; ++o) thr[s_ * (K - 1) + o] = r[o];
-            flags[s_] = r[wpr - 1];
+            for (int o = 0; o < K - 1; ++o) thr[s_ * (K - 1) + o] = o < 3 ? r[o] : r[o + 1];
+            flags[s_] = r[3] & ~FLAG_FASTX;
         }
     }
     return RDDMC_OK;

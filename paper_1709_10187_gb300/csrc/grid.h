@@ -23,7 +23,8 @@ struct rddmc_grid {
     std::vector<uint32_t> cell_class;   // UINT32_MAX for vacuum cells
     std::vector<int64_t> class_rep;     // a representative cell per class
     std::vector<double> n_rel;          // per cell (copied)
-    std::vector<double> u;              // per cell x3, Doppler units (empty if static)
+    std::vector<double> v;              // per cell x3, km/s (empty if static)
+    double vth = 12.85;                 // thermal velocity, km/s
     std::vector<uint8_t> mask;          // per cell (empty = all medium)
     // source (centre cells and bins containing x0 = 0)
     int src_ncand[3] = {1, 1, 1};
@@ -31,7 +32,7 @@ struct rddmc_grid {
     int src_nbin = 0;
     int src_bin[2] = {0, 0};
     // table layout (byte offsets)
-    uint64_t off_class = 0, off_cdesc = 0, off_rebin = 0, off_cvel = 0, off_edges = 0, off_phi = 0,
+    uint64_t off_class = 0, off_cdesc = 0, off_rebin = 0, off_vel = 0, off_edges = 0, off_phi = 0,
              off_rows = 0, table_bytes = 0;
     // leakage parameters of the last precompute
     rddmc_leak_params params{};
@@ -61,5 +62,6 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
 
 uint64_t state_bytes_for(uint64_t n_packets);
 uint64_t tally_bytes_for(int J);
+int tally_words(int J);
 
 }  // namespace rddmc

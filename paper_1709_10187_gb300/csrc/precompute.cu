@@ -1,4 +1,4 @@
-// precompute.cu -- FP64 leakage-table kernels (Sec. 2.3, Sec. 2.5, Sec. 5.1).
+// precompute.cu -- FP64 leakage-table kernels (Sec. 2.2, Sec. 2.5, Sec. 5.1).
 //
 // Kernel 1: phi[j] = bin mean of H(a,x) over bin j (k_ij = k0_i phi_j).
 // Kernel 2: one thread per (class, bin) row: leakage coefficients of
@@ -36,7 +36,7 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
                             const double* __restrict__ edges, const double* __restrict__ phi,
                             uint32_t* __restrict__ rows, int64_t nrow) {
     constexpr int K = 2 + 2 * NDIM;
-    constexpr int W = NDIM == 1 ? 4 : 8;  // words per row
+    constexpr int W = NDIM == 1 ? 4 : 8;  // words per row, the last holding the flags
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrow) return;
     const int J = h.J;
@@ -85,7 +85,7 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
     double tot = 0.0;
 #pragma unroll
     for (int o = 0; o < K; ++o) tot += rate[o];
-    uint32_t out[W];
+    uint32_t out[W - 1];
     double C = 0.0;
 #pragma unroll
     for (int o = 0; o < K - 1; ++o) {
@@ -95,15 +95,17 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
     uint32_t fl = 0;
 #pragma unroll
     for (int o = 0; o < K; ++o) fl |= (act[o] & 3u) << (2 * o);
+    if (act[0] == ACT_MOVE && act[1] == ACT_MOVE) fl |= FLAG_FASTX;
     if (D.moving) fl |= FLAG_MOVING;
     if (hybrid && k * dzmin < h.tau_ddmc) fl |= FLAG_THIN;
-    out[W - 1] = fl;
+    // word order: thr0, thr1, thr2, flags[, thr3..thr6] so that the first 16
+    // bytes carry everything a frequency move needs
     if (NDIM == 1) {
-        reinterpret_cast<uint4*>(rows)[r] = make_uint4(out[0], out[1], out[2], out[3]);
+        reinterpret_cast<uint4*>(rows)[r] = make_uint4(out[0], out[1], out[2], fl);
     } else {
         uint4* p = reinterpret_cast<uint4*>(rows) + 2 * r;
-        p[0] = make_uint4(out[0], out[1], out[2], out[3]);
-        p[1] = make_uint4(out[4], out[5], out[6], out[7]);
+        p[0] = make_uint4(out[0], out[1], out[2], fl);
+        p[1] = make_uint4(out[3], out[4], out[5], out[6]);
     }
 }
 

@@ -2,12 +2,15 @@
 //
 // Device table buffer (caller-owned, filled by rddmc_precompute_leakage):
 //   [TableHeader | cell_class u32[ncell] | ClassDesc[n_class] | Rebin[n_class*nfaces]
-//    | ClassVel float4[n_class] | edges f64[J+1] | phi f64[J] | rows]
+//    | cell velocity f64[3*ncell] (moving media only) | edges f64[J+1] | phi f64[J] | rows]
 // every region 256-byte aligned.  Rows are n_class blocks of J rows; a row is
 // 16 bytes in a slab {thr0, thr1, thr2, flags} and 32 bytes in 3D
-// {thr0..thr6, flags}.  Outcome order: bin-1, bin+1, then -e_a, +e_a per axis.
+// {thr0, thr1, thr2, flags, thr3, thr4, thr5, thr6}: the first 16 bytes always
+// hold both frequency thresholds and the flags, which is all the frequency-move
+// fast path reads.  Outcome order: bin-1, bin+1, then -e_a, +e_a per axis.
 //
-// Tally buffer (u64): [0, 16) counters, [16, 22) faces, [22, 22+J+2) histogram.
+// Tally buffer (u64): [0, 16) counters, [16, 22) faces, [22, 22+J+2) escape
+// histogram, then kNsb impact-parameter bins.
 // State buffer: [0, 256) cursor and spare words, then SoA per-packet arrays.
 #pragma once
 #include <cstdint>
@@ -20,6 +23,8 @@ constexpr int kMaxFaces = 6;
 constexpr int kCounters = 16;
 constexpr int kFaceOff = 16;
 constexpr int kHistOff = 22;
+constexpr int kNsb = 64;            // impact-parameter bins over b/R in [0, kSbMax)
+constexpr double kSbMax = 1.28;
 
 enum Counter : int {
     C_EMITTED = 0, C_ESCAPED = 1, C_ABORTED = 2, C_STEPS = 3, C_MC_EVENTS = 4,
@@ -28,6 +33,7 @@ enum Counter : int {
 
 // 2-bit actions per outcome in the flags word.
 constexpr uint32_t ACT_MOVE = 0u, ACT_ESCAPE = 1u, ACT_TO_MC = 2u, ACT_REBIN = 3u;
+constexpr uint32_t FLAG_FASTX = 1u << 29;   // both frequency outcomes are plain moves
 constexpr uint32_t FLAG_MOVING = 1u << 30;
 constexpr uint32_t FLAG_THIN = 1u << 31;
 
@@ -45,8 +51,7 @@ struct FaceDesc {
 
 struct ClassDesc {
     double k0;          // tau0/R * n_rel of the cells in this class
-    double u[3];        // bulk velocity / v_th
-    int32_t moving;
+    int32_t moving;     // the cells have non-zero bulk velocity
     int32_t pad;
     FaceDesc face[kMaxFaces];
 };
@@ -61,8 +66,8 @@ struct TableHeader {
     uint32_t filled;
     int32_t ndim, J, ncell, n_class, K, row_bytes;
     int32_t n[3], mode;
-    uint64_t off_class, off_cdesc, off_rebin, off_cvel, off_edges, off_phi, off_rows, total;
-    double tau_ddmc, lambda, f_mu, a, dz[3];
+    uint64_t off_class, off_cdesc, off_rebin, off_vel, off_edges, off_phi, off_rows, total;
+    double tau_ddmc, lambda, f_mu, a, dz[3], vth;
 };
 
 // ------------------------------------------------------------------ Philox

@@ -1,4 +1,4 @@
-// voigt.cuh -- device line-profile functions (Sec. 2.1, Sec. 2.3) in FP64.
+// voigt.cuh -- device line-profile functions (Sec. 2.1, Sec. 2.2) in FP64.
 //
 // dawson_f64: F(x) = int_0^x exp(y^2 - x^2) dy.  |x| < 0.5: its power series
 //   F(x) = sum_k (-2)^k x^(2k+1) / (2k+1)!!.  Elsewhere Rybicki's (1989,
@@ -55,7 +55,7 @@ __device__ __forceinline__ double voigt_hint_diff_f64(double a, double lo, doubl
     return 0.88622692545275801365 * derf - 2.0 * a * 0.56418958354775628695 * dF + a * a * dG;
 }
 
-// Bin mean of H over [lo, hi] (k_j / k0 of Sec. 2.3).
+// Bin mean of H over [lo, hi] (k_j / k0 of Sec. 2.2).
 __device__ __forceinline__ double voigt_bin_mean_f64(double a, double lo, double hi) {
     return voigt_hint_diff_f64(a, lo, hi) / (hi - lo);
 }

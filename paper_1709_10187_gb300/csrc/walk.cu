@@ -1,20 +1,25 @@
-// walk.cu -- persistent DDMC walk kernel (Sec. 2.4) for slabs.
+// walk.cu -- persistent DDMC walk kernel (Sec. 2.3) for slabs and 3D grids.
 //
 // One packet per thread.  A transition draws one 32-bit word of the packet's
 // transition stream (lane t&3 of Philox4x32-10 keyed by (t>>2, packet); every
-// lane's t stays a multiple of 4 at a refill, so a warp makes one Philox call
-// per four transitions without divergence), gathers the 16-byte row
-// {thr0, thr1, thr2, flags} of its state (cell class, bin) and takes outcome
-// o = #{k : w >= thr_k}: the categorical form of the competing exponentials of
-// eq. l_min_1/2.  Outcomes are bin-1, bin+1, cell-1, cell+1; the 2-bit action
-// of the outcome selects a plain move (the fast path) or the slow path
-// (escape through an exterior face, Doppler rebin across a face).
+// lane's t is a multiple of 4 when a chunk starts, so a warp makes one Philox
+// call per four transitions without divergence, and the call for the next four
+// is issued while the current four are walked).  The word w selects outcome
+// o = #{k : w >= thr_k} of the state's row: the categorical form of the
+// competing exponentials of eq. l_min_1/2.
+//
+// Frequency moves dominate (the core of the line, Sec. 4.2), so the fast path
+// reads only the first 16 bytes of a row {thr0, thr1, thr2, flags}: when
+// w < thr1 and both frequency outcomes are plain moves, the packet moves one
+// bin down (w < thr0) or up.  Everything else -- spatial moves, Doppler
+// rebins, escapes through exterior faces -- goes through one generic step that
+// evaluates every threshold and the outcome's 2-bit action.
 //
 // Lanes whose packet escaped, was aborted by the watchdog or reached the end of
 // its time slice take new packet ids from a global cursor, one atomicAdd per
 // warp (__ballot_sync / __popc prefix).  Tallies are integer: per-thread
 // registers for counters, warp-aggregated (__match_any_sync) shared-memory
-// atomics for the escape histogram and faces, flushed to the u64 tally buffer
+// atomics for the escape histograms and faces, flushed to the u64 tally buffer
 // in global memory when the CTA finishes.
 #include <cstring>
 
@@ -26,11 +31,11 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kSmemHistMax = 8192;  // histogram entries kept in shared memory
 
-struct SlabWalkParams {
+struct WalkParams {
     const uint4* rows;
     const uint32_t* cell_class;
     const Rebin* rebin;
-    const ClassDesc* cdesc;
+    const double* cell_v;     // km/s, 3 per cell (moving media)
     const double* edges;
     unsigned long long* cursor;
     uint32_t* st_cell;
@@ -41,10 +46,30 @@ struct SlabWalkParams {
     unsigned long long* tally;
     unsigned long long n_packets, max_steps, slice;
     uint32_t k0, k1;
-    int J, n_rows, ncell, chunk;
-    int resume, save_state, hist_in_smem;
-    int src_ncell, src_cell0, src_cell1, src_nbin, src_bin0, src_bin1;
+    uint32_t rk0[10], rk1[10];  // Philox round keys k + r * (Weyl constant)
+    int J, n_rows, n_class, ncell, chunk;
+    int n0, n01;
+    double R, dz[3], vth;
+    int resume, save_state, hist_in_smem, moving;
+    int src_ncand[3], src_cand[3][2], src_nbin, src_bin[2];
 };
+
+// Philox4x32-10 with precomputed round keys (held in the kernel's parameter bank).
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const WalkParams& P) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ P.rk0[r], lo1, hi0 ^ c.w ^ P.rk1[r], lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ unsigned word_of(const uint4& r, unsigned q) {
+    return q == 0 ? r.x : (q == 1 ? r.y : (q == 2 ? r.z : r.w));
+}
 
 // Shared-memory tally update aggregated over the lanes that hit the same index.
 __device__ __forceinline__ void smem_tally(unsigned long long* s, unsigned idx) {
@@ -54,55 +79,152 @@ __device__ __forceinline__ void smem_tally(unsigned long long* s, unsigned idx) 
     if ((int)(threadIdx.x & 31) == leader) atomicAdd(&s[idx], (unsigned long long)__popc(peers));
 }
 
-// Observer-frame escape bin of a packet leaving a moving cell through face
-// (axis 0, side): a point on the face (two draws, unused by a slab), an
-// isotropic outward direction (mu uniform on (0,1], azimuth uniform), x uniform
-// in the bin; x_obs = x + n.u (FP64).  Returns the histogram index.
-__device__ __noinline__ int moving_escape_bin(const SlabWalkParams& P, const ClassDesc& D, unsigned bin, int side,
-                                 unsigned long long pid, unsigned long long& e) {
-    (void)event_word(pid, e++, P.k0, P.k1);
-    (void)event_word(pid, e++, P.k0, P.k1);
+struct EscapeBins {
+    int hist;   // escape-frequency bin (0 below the grid, J+1 above)
+    int sb;     // impact-parameter bin, -1 if not tallied
+};
+
+// Escape through `face` of `cell` at `bin`.  A static slab cell tallies its bin.
+// Otherwise (3D, or a moving slab cell): a point on the face (two event draws
+// for the tangential axes), an isotropic outward direction (mu uniform on
+// (0,1], azimuth uniform), x uniform in the bin, all FP64;
+// x_obs = x + n.(v/v_th) and, in 3D, the impact parameter b = |r x n|.
+template <int NDIM>
+__device__ __noinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cell, unsigned bin, unsigned face,
+                                               unsigned long long pid, unsigned long long e, bool moving) {
+    EscapeBins out;
+    out.sb = -1;
+    if (NDIM == 1 && !moving) { out.hist = (int)bin + 1; return out; }
+    const int ax = (int)(face >> 1), side = (face & 1u) ? 1 : -1;
+    const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+    int idx[3];
+    idx[0] = (int)(cell % (unsigned)P.n0);
+    idx[1] = NDIM == 3 ? (int)((cell / (unsigned)P.n0) % (unsigned)(P.n01 / P.n0)) : 0;
+    idx[2] = NDIM == 3 ? (int)(cell / (unsigned)P.n01) : 0;
     const double inv = 1.0 / 4294967296.0;
-    const double mu = 1.0 - ((double)event_word(pid, e++, P.k0, P.k1) + 0.5) * inv;
-    const double ph = 2.0 * 3.14159265358979323846 * (((double)event_word(pid, e++, P.k0, P.k1) + 0.5) * inv);
-    const double xu = ((double)event_word(pid, e++, P.k0, P.k1) + 0.5) * inv;
+    double r[3];
+    r[ax] = -P.R + (double)(idx[ax] + (side > 0 ? 1 : 0)) * P.dz[ax];
+    const double p1 = ((double)event_word(pid, e, P.k0, P.k1) + 0.5) * inv;
+    const double p2 = ((double)event_word(pid, e + 1, P.k0, P.k1) + 0.5) * inv;
+    r[t1] = (t1 < NDIM) ? -P.R + ((double)idx[t1] + p1) * P.dz[t1] : 0.0;
+    r[t2] = (t2 < NDIM) ? -P.R + ((double)idx[t2] + p2) * P.dz[t2] : 0.0;
+    const double mu = 1.0 - ((double)event_word(pid, e + 2, P.k0, P.k1) + 0.5) * inv;
+    const double ph = 2.0 * 3.14159265358979323846 * (((double)event_word(pid, e + 3, P.k0, P.k1) + 0.5) * inv);
+    const double xu = ((double)event_word(pid, e + 4, P.k0, P.k1) + 0.5) * inv;
     const double x = P.edges[bin] + xu * (P.edges[bin + 1] - P.edges[bin]);
     const double st = sqrt(fmax(0.0, 1.0 - mu * mu));
-    const double nu = (double)side * mu * D.u[0] + st * (cos(ph) * D.u[1] + sin(ph) * D.u[2]);
-    const double xo = x + nu;
-    if (xo < P.edges[0]) return 0;
-    if (xo >= P.edges[P.J]) return P.J + 1;
-    int lo = 0, hi = P.J;  // find j with edges[j] <= xo < edges[j+1]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (xo >= P.edges[mid]) lo = mid; else hi = mid;
+    double n[3];
+    n[ax] = (double)side * mu;
+    n[t1] = st * cos(ph);
+    n[t2] = st * sin(ph);
+    double nu = 0.0;
+    if (moving) {
+        const double* v = P.cell_v + 3ull * cell;
+        nu = n[0] * (v[0] / P.vth) + n[1] * (v[1] / P.vth) + n[2] * (v[2] / P.vth);
     }
-    return lo + 1;
+    const double xo = x + nu;
+    if (xo < P.edges[0]) {
+        out.hist = 0;
+    } else if (xo >= P.edges[P.J]) {
+        out.hist = P.J + 1;
+    } else {
+        int lo = 0, hi = P.J;  // edges[lo] <= xo < edges[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (xo >= P.edges[mid]) lo = mid; else hi = mid;
+        }
+        out.hist = lo + 1;
+    }
+    if (NDIM == 3) {
+        const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const double rn = r[0] * n[0] + r[1] * n[1] + r[2] * n[2];
+        const double b = sqrt(fmax(0.0, rr - rn * rn)) / P.R;
+        int k = (int)(b / kSbMax * kNsb);
+        out.sb = k > kNsb - 1 ? kNsb - 1 : k;
+    }
+    return out;
 }
 
-template <bool SMEM_ROWS>
-__global__ void __launch_bounds__(256, 3) slab_walk_kernel(const SlabWalkParams P) {
+template <int NDIM, bool SMEM_ROWS>
+__global__ void __launch_bounds__(256, 3) walk_kernel(const WalkParams P) {
+    constexpr int RW = NDIM == 1 ? 1 : 2;  // uint4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(smem_raw);  // kCounters
     unsigned long long* s_face = s_cnt + kCounters;                              // 8
-    unsigned long long* s_hist = s_face + 8;                                      // J+2 if in smem
+    unsigned long long* s_sb = s_face + 8;                                        // kNsb
+    unsigned long long* s_hist = s_sb + kNsb;                                     // J+2 if in smem
     const int nhist = P.J + 2;
     uint4* s_rows = reinterpret_cast<uint4*>(s_hist + (P.hist_in_smem ? ((nhist + 1) & ~1) : 0));
 
-    for (int i = threadIdx.x; i < kCounters + 8; i += blockDim.x) s_cnt[i] = 0ull;
+    for (int i = threadIdx.x; i < kCounters + 8 + kNsb; i += blockDim.x) s_cnt[i] = 0ull;
     if (P.hist_in_smem)
         for (int i = threadIdx.x; i < nhist; i += blockDim.x) s_hist[i] = 0ull;
     if (SMEM_ROWS)
-        for (int i = threadIdx.x; i < P.n_rows; i += blockDim.x) s_rows[i] = __ldg(&P.rows[i]);
+        for (int i = threadIdx.x; i < P.n_rows * RW; i += blockDim.x) s_rows[i] = __ldg(&P.rows[i]);
     __syncthreads();
+    const uint4* rows = SMEM_ROWS ? s_rows : P.rows;
 
     const unsigned lane = threadIdx.x & 31u;
-    const int J = P.J;
+    const unsigned J = (unsigned)P.J;
+    const unsigned nr1 = (unsigned)P.n_rows - 1u;
     bool have = false, exhausted = false;
     unsigned long long pid = 0, t = 0, e = 0, t_stop = 0;
-    unsigned cell = 0, bin = 0, cls = 0, base = 0;
+    unsigned cell = 0, cls = 0, s = 0;  // s = cls * J + bin: the row of the state
     unsigned long long n_steps = 0, n_edraw = 0;
     unsigned n_emit = 0, n_esc = 0, n_abort = 0, n_clamp = 0, status_bits = 0;
+
+    // One full transition: every threshold, the outcome's action, spatial moves
+    // with the class lookup, Doppler rebins and escapes.  Returns true when the
+    // packet has finished.
+    auto generic = [&](unsigned w) -> bool {
+        const unsigned ri = min(s, nr1);
+        const uint4 a = SMEM_ROWS ? rows[ri * RW] : __ldg(&rows[ri * RW]);
+        unsigned o = (unsigned)(w >= a.x) + (unsigned)(w >= a.y) + (unsigned)(w >= a.z);
+        if (NDIM == 3) {
+            const uint4 b = SMEM_ROWS ? rows[ri * RW + 1] : __ldg(&rows[ri * RW + 1]);
+            o += (unsigned)(w >= b.x) + (unsigned)(w >= b.y) + (unsigned)(w >= b.z) + (unsigned)(w >= b.w);
+        }
+        const unsigned fl = a.w;
+        const unsigned act = (fl >> (2u * o)) & 3u;
+        const unsigned bin = min(s - cls * J, J - 1u);
+        if (o < 2u) {
+            if (act == ACT_MOVE) { s += o ? 1u : 0xffffffffu; return false; }
+            status_bits |= (unsigned)STATUS_UNSUPPORTED_EVENT;  // hand-off to MC: not in this walk
+            ++n_abort;
+            return true;
+        }
+        const unsigned face = o - 2u;
+        if (act == ACT_ESCAPE) {
+            const EscapeBins eb = escape_bins<NDIM>(P, cell, bin, face, pid, e, (fl & FLAG_MOVING) != 0u);
+            if (NDIM == 3 || (fl & FLAG_MOVING)) e += 5;
+            if (P.hist_in_smem) smem_tally(s_hist, (unsigned)eb.hist);
+            else atomicAdd(&P.tally[kHistOff + eb.hist], 1ull);
+            if (eb.sb >= 0) smem_tally(s_sb, (unsigned)eb.sb);
+            smem_tally(s_face, face);
+            ++n_esc;
+            return true;
+        }
+        if (act == ACT_TO_MC) {
+            status_bits |= (unsigned)STATUS_UNSUPPORTED_EVENT;
+            ++n_abort;
+            return true;
+        }
+        unsigned nbin = bin;
+        if (act == ACT_REBIN) {
+            const Rebin rb = P.rebin[min(cls, (unsigned)P.n_class - 1u) * (2u * NDIM) + face];
+            const unsigned w1 = event_word(pid, e++, P.k0, P.k1);
+            int jn = (int)bin + rb.m + (w1 >= rb.thr ? 1 : 0);
+            if (jn < 0) { jn = 0; ++n_clamp; }
+            if (jn > (int)J - 1) { jn = (int)J - 1; ++n_clamp; }
+            nbin = (unsigned)jn;
+        }
+        const unsigned ax = face >> 1;
+        const unsigned stride = NDIM == 1 ? 1u : (ax == 0 ? 1u : (ax == 1 ? (unsigned)P.n0 : (unsigned)P.n01));
+        cell = min((face & 1u) ? cell + stride : cell - stride, (unsigned)P.ncell - 1u);
+        cls = __ldg(&P.cell_class[cell]);
+        s = cls * J + nbin;
+        return false;
+    };
 
     for (;;) {
         // ---- warp-cooperative refill
@@ -118,6 +240,7 @@ __global__ void __launch_bounds__(256, 3) slab_walk_kernel(const SlabWalkParams 
                     exhausted = true;
                 } else {
                     const uint8_t st = P.resume ? P.st_status[pid] : (uint8_t)PK_FRESH;
+                    unsigned bin = 0;
                     if (st == PK_INFLIGHT) {
                         cell = P.st_cell[pid];
                         bin = P.st_bin[pid];
@@ -125,10 +248,14 @@ __global__ void __launch_bounds__(256, 3) slab_walk_kernel(const SlabWalkParams 
                         e = P.st_e[pid];
                         have = true;
                     } else if (st == PK_FRESH) {
-                        // event draw 0: bit 31 picks the centre cell, bit 28 the bin
+                        // event draw 0: bit 31-a picks the centre cell on axis a, bit 28 the bin
                         const unsigned w = event_word(pid, 0, P.k0, P.k1);
-                        cell = (P.src_ncell == 2 && ((w >> 31) & 1u)) ? P.src_cell1 : P.src_cell0;
-                        bin = (P.src_nbin == 2 && ((w >> 28) & 1u)) ? P.src_bin1 : P.src_bin0;
+                        unsigned idx[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            idx[a] = (unsigned)P.src_cand[a][(P.src_ncand[a] == 2) ? ((w >> (31 - a)) & 1u) : 0u];
+                        cell = idx[0] + (unsigned)P.n0 * idx[1] + (unsigned)P.n01 * idx[2];
+                        bin = (unsigned)P.src_bin[(P.src_nbin == 2) ? ((w >> 28) & 1u) : 0u];
                         t = 0;
                         e = 1;
                         ++n_emit;
@@ -136,9 +263,8 @@ __global__ void __launch_bounds__(256, 3) slab_walk_kernel(const SlabWalkParams 
                     }
                     if (have) {
                         cell = min(cell, (unsigned)P.ncell - 1u);
-                        bin = min(bin, (unsigned)J - 1u);
                         cls = __ldg(&P.cell_class[cell]);
-                        base = cls * (unsigned)J;
+                        s = cls * J + min(bin, J - 1u);
                         t_stop = P.slice ? t + P.slice : ~0ull;
                     }
                 }
@@ -154,61 +280,56 @@ __global__ void __launch_bounds__(256, 3) slab_walk_kernel(const SlabWalkParams 
         const unsigned long long t0 = t;
         const unsigned long long e0 = e;
         bool fin = false;
-        while (t < lim) {
-            const unsigned long long blk = t >> 2;
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), (uint32_t)pid,
-                                                     (uint32_t)(pid >> 32)),
-                                          P.k0, P.k1);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const unsigned w = q == 0 ? r.x : (q == 1 ? r.y : (q == 2 ? r.z : r.w));
-                // every index below is clamped into its buffer, so no table content
-                // can send a read or a tally outside its array
-                const unsigned ri = min(base + bin, (unsigned)P.n_rows - 1u);
-                const uint4 row = SMEM_ROWS ? s_rows[ri] : __ldg(&P.rows[ri]);
-                const unsigned o = (unsigned)(w >= row.x) + (unsigned)(w >= row.y) + (unsigned)(w >= row.z);
-                const unsigned act = (row.w >> (2u * o)) & 3u;
-                ++t;
-                if (act == ACT_MOVE) {
-                    if (o < 2u) {
-                        bin = bin + 2u * o - 1u;
-                    } else {
-                        cell = min(cell + 2u * (o - 2u) - 1u, (unsigned)P.ncell - 1u);
-                        cls = __ldg(&P.cell_class[cell]);
-                        base = cls * (unsigned)J;
+        {
+            const uint32_t pl = (uint32_t)pid, ph = (uint32_t)(pid >> 32);
+            unsigned long long blk = t >> 2;
+            const unsigned ng = (unsigned)((lim - t) >> 2);  // full groups of four
+            uint4 rn = philox_rk(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), pl, ph), P);
+            unsigned g = 0;
+            while (g < ng) {
+                const uint4 r = rn;
+                ++blk;
+                rn = philox_rk(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), pl, ph), P);
+                unsigned q;
+#define RDDMC_FAST(W, Q)                                                                  \
+    {                                                                                     \
+        const unsigned ri_ = min(s, nr1);                                                 \
+        const uint4 a_ = SMEM_ROWS ? rows[ri_ * RW] : __ldg(&rows[ri_ * RW]);             \
+        if ((W) < a_.y && (a_.w & FLAG_FASTX)) {                                          \
+            s += ((W) >= a_.x) ? 1u : 0xffffffffu;                                        \
+        } else {                                                                          \
+            q = (Q);                                                                      \
+            goto slow;                                                                    \
+        }                                                                                 \
+    }
+                RDDMC_FAST(r.x, 0u)
+                RDDMC_FAST(r.y, 1u)
+                RDDMC_FAST(r.z, 2u)
+                RDDMC_FAST(r.w, 3u)
+#undef RDDMC_FAST
+                ++g;
+                continue;
+            slow:
+                for (; q < 4u; ++q) {
+                    if (generic(word_of(r, q))) {
+                        fin = true;
+                        t += 4ull * g + q + 1ull;
+                        goto chunk_done;
                     }
-                } else if (act == ACT_REBIN) {
-                    const int face = (int)o - 2;
-                    const Rebin rb = P.rebin[min(cls, (unsigned)P.n_rows / (unsigned)J - 1u) * 2u + (unsigned)face];
-                    const unsigned w1 = event_word(pid, e++, P.k0, P.k1);
-                    int jn = (int)bin + rb.m + (w1 >= rb.thr ? 1 : 0);
-                    if (jn < 0) { jn = 0; ++n_clamp; }
-                    if (jn > J - 1) { jn = J - 1; ++n_clamp; }
-                    bin = (unsigned)jn;
-                    cell = min(cell + 2u * (o - 2u) - 1u, (unsigned)P.ncell - 1u);
-                    cls = __ldg(&P.cell_class[cell]);
-                    base = cls * (unsigned)J;
-                } else if (act == ACT_ESCAPE) {
-                    const int face = (int)o - 2;
-                    int h = (int)min(bin, (unsigned)J - 1u) + 1;
-                    if (row.w & FLAG_MOVING)
-                        h = moving_escape_bin(P, P.cdesc[min(cls, (unsigned)P.n_rows / (unsigned)J - 1u)],
-                                              min(bin, (unsigned)J - 1u), face ? 1 : -1, pid, e);
-                    if (P.hist_in_smem) smem_tally(s_hist, (unsigned)h);
-                    else atomicAdd(&P.tally[kHistOff + h], 1ull);
-                    smem_tally(s_face, (unsigned)face);
-                    ++n_esc;
-                    fin = true;
-                } else {
-                    // hand-off to continuous MC: not available in this walk
-                    status_bits |= (unsigned)STATUS_UNSUPPORTED_EVENT;
-                    ++n_abort;
-                    fin = true;
                 }
-                if (fin || t >= lim) break;
+                ++g;
             }
-            if (fin) break;
+            t += 4ull * ng;
+            // at most three transitions left before the watchdog limit
+            while (t < lim) {
+                const unsigned long long b = t >> 2;
+                const uint4 r = philox_rk(make_uint4((uint32_t)b, (uint32_t)(b >> 32), pl, ph), P);
+                const bool f = generic(word_of(r, (unsigned)t & 3u));
+                ++t;
+                if (f) { fin = true; break; }
+            }
         }
+    chunk_done:
         n_steps += t - t0;
         n_edraw += e - e0;
         if (fin) {
@@ -220,7 +341,7 @@ __global__ void __launch_bounds__(256, 3) slab_walk_kernel(const SlabWalkParams 
             if (P.save_state) P.st_status[pid] = PK_DONE;
         } else if (t >= t_stop) {
             P.st_cell[pid] = cell;
-            P.st_bin[pid] = bin;
+            P.st_bin[pid] = min(s - cls * J, J - 1u);
             P.st_t[pid] = t;
             P.st_e[pid] = e;
             P.st_status[pid] = PK_INFLIGHT;
@@ -234,6 +355,7 @@ __global__ void __launch_bounds__(256, 3) slab_walk_kernel(const SlabWalkParams 
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
         unsigned long long x = v[i];
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
         v[i] = x;
     }
@@ -252,11 +374,27 @@ __global__ void __launch_bounds__(256, 3) slab_walk_kernel(const SlabWalkParams 
         if (i == C_STATUS_BITS) atomicOr(&P.tally[i], s_cnt[i]);
         else atomicAdd(&P.tally[i], s_cnt[i]);
     }
-    for (int i = threadIdx.x; i < 2; i += blockDim.x)
+    for (int i = threadIdx.x; i < 2 * NDIM; i += blockDim.x)
         if (s_face[i]) atomicAdd(&P.tally[kFaceOff + i], s_face[i]);
     if (P.hist_in_smem)
         for (int i = threadIdx.x; i < nhist; i += blockDim.x)
             if (s_hist[i]) atomicAdd(&P.tally[kHistOff + i], s_hist[i]);
+    for (int i = threadIdx.x; i < kNsb; i += blockDim.x)
+        if (s_sb[i]) atomicAdd(&P.tally[kHistOff + nhist + i], s_sb[i]);
+}
+
+template <int NDIM, bool SMEM>
+cudaError_t launch_variant(const WalkParams& P, int threads, size_t smem, int ctas, int nsm, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<NDIM, SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (!ctas) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, walk_kernel<NDIM, SMEM>, threads, smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (ctas < 1) ctas = 1;
+    walk_kernel<NDIM, SMEM><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -265,12 +403,12 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     const rddmc_run_opts& o = w.opts;
     const char* tb = (const char*)w.d_table;
     char* sb = (char*)w.d_state;
-    SlabWalkParams P;
+    WalkParams P;
     std::memset(&P, 0, sizeof(P));
     P.rows = (const uint4*)(tb + g.off_rows);
     P.cell_class = (const uint32_t*)(tb + g.off_class);
     P.rebin = (const Rebin*)(tb + g.off_rebin);
-    P.cdesc = (const ClassDesc*)(tb + g.off_cdesc);
+    P.cell_v = (const double*)(tb + g.off_vel);
     P.edges = (const double*)(tb + g.off_edges);
     const uint64_t np = o.n_packets;
     uint64_t off = 256;
@@ -286,19 +424,32 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     P.slice = o.steps_per_launch;
     P.k0 = (uint32_t)o.seed;
     P.k1 = (uint32_t)(o.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        P.rk0[r] = P.k0 + (uint32_t)r * 0x9E3779B9u;
+        P.rk1[r] = P.k1 + (uint32_t)r * 0xBB67AE85u;
+    }
     P.J = g.J;
+    P.n_class = g.n_class;
     P.n_rows = g.n_class * g.J;
     P.ncell = (int)g.ncell;
-    P.chunk = o.chunk ? o.chunk : 64;
+    P.n0 = g.n[0];
+    P.n01 = g.n[0] * g.n[1];
+    P.R = g.R;
+    for (int a = 0; a < 3; ++a) P.dz[a] = 2.0 * g.R / g.n[a];
+    P.vth = g.vth;
+    P.chunk = o.chunk ? o.chunk : 256;
     P.resume = o.resume;
     P.save_state = (o.steps_per_launch != 0 || o.resume) ? 1 : 0;
     P.hist_in_smem = (g.J + 2 <= kSmemHistMax) ? 1 : 0;
-    P.src_ncell = g.src_ncand[0];
-    P.src_cell0 = g.src_cand[0][0];
-    P.src_cell1 = g.src_cand[0][1];
+    P.moving = g.moving ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        P.src_ncand[a] = g.src_ncand[a];
+        P.src_cand[a][0] = g.src_cand[a][0];
+        P.src_cand[a][1] = g.src_cand[a][1];
+    }
     P.src_nbin = g.src_nbin;
-    P.src_bin0 = g.src_bin[0];
-    P.src_bin1 = g.src_bin[1];
+    P.src_bin[0] = g.src_bin[0];
+    P.src_bin[1] = g.src_bin[1];
 
     int dev = 0, nsm = 0, smem_optin = 0;
     cudaError_t e;
@@ -307,35 +458,17 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     if ((e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return e;
     const int threads = o.threads_per_cta ? o.threads_per_cta : 256;
-    size_t smem = (size_t)(kCounters + 8) * 8;
+    size_t smem = (size_t)(kCounters + 8 + kNsb) * 8;
     if (P.hist_in_smem) smem += (size_t)((g.J + 2 + 1) & ~1) * 8;
-    const size_t rows_bytes = (size_t)P.n_rows * 16;
+    const size_t rows_bytes = (size_t)P.n_rows * g.row_bytes;
     const bool use_smem_rows = o.table_in_smem && smem + rows_bytes <= (size_t)smem_optin;
     if (use_smem_rows) smem += rows_bytes;
-    int ctas = o.ctas_per_sm;
-    if (use_smem_rows) {
-        if ((e = cudaFuncSetAttribute(slab_walk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem)) != cudaSuccess)
-            return e;
-        if (!ctas && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, slab_walk_kernel<true>, threads,
-                                                                        smem)) != cudaSuccess)
-            return e;
-    } else {
-        if ((e = cudaFuncSetAttribute(slab_walk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem)) != cudaSuccess)
-            return e;
-        if (!ctas && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, slab_walk_kernel<false>, threads,
-                                                                        smem)) != cudaSuccess)
-            return e;
-    }
-    if (ctas < 1) ctas = 1;
     if ((e = cudaMemsetAsync(P.cursor, 0, 8, s)) != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)(ctas * nsm);
-    if (use_smem_rows)
-        slab_walk_kernel<true><<<blocks, threads, smem, s>>>(P);
-    else
-        slab_walk_kernel<false><<<blocks, threads, smem, s>>>(P);
-    return cudaGetLastError();
+    if (g.ndim == 1)
+        return use_smem_rows ? launch_variant<1, true>(P, threads, smem, o.ctas_per_sm, nsm, s)
+                             : launch_variant<1, false>(P, threads, smem, o.ctas_per_sm, nsm, s);
+    return use_smem_rows ? launch_variant<3, true>(P, threads, smem, o.ctas_per_sm, nsm, s)
+                         : launch_variant<3, false>(P, threads, smem, o.ctas_per_sm, nsm, s);
 }
 
 }  // namespace rddmc

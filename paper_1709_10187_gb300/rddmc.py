@@ -25,6 +25,7 @@ OK, ERR_ARG, ERR_UNSUPPORTED, ERR_SIZE, ERR_CUDA, ERR_STEP_LIMIT, ERR_TABLE = 0,
 GEOM_SLAB_1D, GEOM_CART_3D = 1, 3
 MODE_DDMC, MODE_HYBRID = 0, 1
 LAYOUT_DEDUP, LAYOUT_DENSE = 0, 1
+NSB = 64  # impact-parameter bins of the surface-brightness histogram
 
 EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc_precompute_leakage",
             "rddmc_reset_tallies", "rddmc_launch_packets", "rddmc_read_tallies", "rddmc_table_rows",
@@ -60,7 +61,7 @@ class Tallies(ctypes.Structure):
     _fields_ = [("emitted", ctypes.c_uint64), ("escaped", ctypes.c_uint64), ("aborted", ctypes.c_uint64),
                 ("steps", ctypes.c_uint64), ("mc_events", ctypes.c_uint64), ("conversions", ctypes.c_uint64),
                 ("clamps", ctypes.c_uint64), ("event_draws", ctypes.c_uint64), ("status", ctypes.c_int32),
-                ("nbins", ctypes.c_int32), ("nfaces", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("nbins", ctypes.c_int32), ("nfaces", ctypes.c_int32), ("nsb", ctypes.c_int32)]
 
 
 class RDDMCError(RuntimeError):
@@ -88,7 +89,7 @@ def lib():
         L.rddmc_precompute_leakage.argtypes = [vp, ctypes.POINTER(LeakParams), vp, sz, vp]
         L.rddmc_reset_tallies.argtypes = [vp, vp, sz, vp]
         L.rddmc_launch_packets.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp, sz, vp]
-        L.rddmc_read_tallies.argtypes = [vp, vp, ctypes.POINTER(Tallies), vp, vp, vp]
+        L.rddmc_read_tallies.argtypes = [vp, vp, ctypes.POINTER(Tallies), vp, vp, vp, vp]
         L.rddmc_table_rows.argtypes = [vp, vp, vp, vp, vp]
         L.rddmc_read_packet_states.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, vp, vp, vp]
         L.rddmc_status_string.argtypes = [i32]
@@ -167,12 +168,14 @@ def read_tallies(grid, d_tallies: int, J: int, nfaces: int, stream: int = 0) -> 
     t = Tallies()
     hist = np.zeros(J + 2, dtype=np.uint64)
     faces = np.zeros(nfaces, dtype=np.uint64)
+    sb = np.zeros(NSB, dtype=np.uint64)
     _check("rddmc_read_tallies", lib().rddmc_read_tallies(ctypes.c_void_p(grid), ctypes.c_void_p(d_tallies),
                                                           ctypes.byref(t), _np_ptr(hist), _np_ptr(faces),
-                                                          ctypes.c_void_p(stream)))
-    d = {k: int(getattr(t, k)) for k, _ in Tallies._fields_ if k != "reserved"}
+                                                          _np_ptr(sb), ctypes.c_void_p(stream)))
+    d = {k: int(getattr(t, k)) for k, _ in Tallies._fields_}
     d["hist"] = hist
     d["faces"] = faces
+    d["sb"] = sb
     return d
 
 

@@ -89,10 +89,21 @@ P2 = Workload("slab_atau1e9_T10_101x51", 1, (101, 1, 1), 51, -2500.0, 2500.0, _T
 C3 = Workload("sphere_tau1e7_64c_128b", 3, (64, 64, 64), 128, -80.0, 80.0, 1.0e7, 1.0e4, 10_000_000,
               0x5EED0003, sphere=True)
 
+C3_V20 = C3.with_(name="sphere_tau1e7_64c_128b_v20", vmax_kms=20.0)
+C3_V200 = C3.with_(name="sphere_tau1e7_64c_128b_v200", vmax_kms=200.0)
+
 # Small grids for parity tests: several row tiles and ragged sizes, cheap enough
 # for the oracle to finish in seconds.
 TINY = Workload("slab_tiny_8x16", 1, (8, 1, 1), 16, -8.0, 8.0, 2.0e2, 1.0e4, 20_000, 0x5EED0101)
 SMALL = Workload("slab_small_13x37", 1, (13, 1, 1), 37, -12.0, 12.0, 1.0e3, 1.0e4, 20_000, 0x5EED0102)
 GREY_LIKE = Workload("slab_wide_bins_31x9", 1, (31, 1, 1), 9, -90.0, 90.0, 3.0e4, 1.0e4, 20_000, 0x5EED0103)
 
-ALL = {w.name: w for w in (C1, C2, P1, P2, C3, TINY, SMALL, GREY_LIKE)}
+# 3D spheres small enough for the exact chain: cube of 8^3 cells, medium where
+# the cell centre is inside r < R, static or in Hubble-like outflow.
+SPHERE8 = Workload("sphere_tiny_8c_16b", 3, (8, 8, 8), 16, -16.0, 16.0, 1.0e3, 1.0e4, 20_000, 0x5EED0301, sphere=True)
+SPHERE8_V = SPHERE8.with_(name="sphere_tiny_8c_16b_v20", vmax_kms=20.0, seed=0x5EED0302)
+SPHERE9_V = Workload("sphere_small_9c_21b_v20", 3, (9, 9, 9), 21, -21.0, 21.0, 3.0e3, 1.0e4, 10_000, 0x5EED0303,
+                     sphere=True, vmax_kms=20.0)
+
+ALL = {w.name: w for w in (C1, C2, P1, P2, C3, C3_V20, C3_V200, TINY, SMALL, GREY_LIKE, SPHERE8, SPHERE8_V,
+                           SPHERE9_V)}

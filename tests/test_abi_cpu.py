@@ -46,7 +46,7 @@ def test_dedup_classes_and_sizes():
     # uniform static slab: left boundary cell, interior cells, right boundary cell
     assert s.n_class == 3 and s.row_bytes == 16 and s.n_outcomes == 4
     assert s.table_bytes >= 3 * 512 * 16
-    assert s.tally_bytes == (22 + 512 + 2) * 8
+    assert s.tally_bytes == (22 + 512 + 2 + 64) * 8
     assert s.state_bytes >= 10_000_000 * 25
     R.destroy_grid(g)
     g = _grid(W.C2, layout=R.LAYOUT_DENSE)
@@ -87,3 +87,13 @@ def test_moving_medium_requires_uniform_bins():
     with pytest.raises(R.RDDMCError) as ei:
         R.build_grid(R.GEOM_CART_3D, w.n, e, w.R, w.tau0, w.T, v_kms=w.velocity_kms(), mask=w.mask())
     assert ei.value.status == R.ERR_UNSUPPORTED
+
+
+def test_hubble_sphere_has_few_classes():
+    # Homologous flow: every interior face sees the same velocity difference, so
+    # the sphere's cells fall into classes by their exterior-face pattern only.
+    w = W.C3.with_(vmax_kms=200.0)
+    g = _grid(w)
+    n_class = R.grid_sizes(g, 1).n_class
+    R.destroy_grid(g)
+    assert 1 < n_class <= 64, n_class

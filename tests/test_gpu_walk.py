@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 ONE_BIN = W.Workload("slab_one_bin_9x1", 1, (9, 1, 1), 1, -5.0, 5.0, 50.0, 1.0e4, 4000, 0x5EED0201)
 ONE_CELL = W.Workload("slab_one_cell_1x21", 1, (1, 1, 1), 21, -10.0, 10.0, 30.0, 1.0e4, 4000, 0x5EED0202)
 WIDE_J = W.Workload("slab_wide_hist_5x9001", 1, (5, 1, 1), 9001, -450.0, 450.0, 2.0e3, 1.0e4, 1000, 0x5EED0203)
-BIT_EXACT = [W.TINY, W.SMALL, W.GREY_LIKE, ONE_BIN, ONE_CELL, WIDE_J]
+BIT_EXACT = [W.TINY, W.SMALL, W.GREY_LIKE, ONE_BIN, ONE_CELL, WIDE_J, W.SPHERE8, W.SPHERE8_V, W.SPHERE9_V]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -43,9 +43,10 @@ def _same_tallies(gpu, orc, check_draws=True):
         assert gpu["event_draws"] == orc["event_draws"]
     assert np.array_equal(gpu["hist"], orc["hist"])
     assert np.array_equal(gpu["faces"], orc["faces"][: len(gpu["faces"])])
+    assert np.array_equal(gpu["sb"], orc["sb"])
 
 
-@pytest.mark.parametrize("w", BIT_EXACT + [W.C1, W.C2, W.P1, W.P2], ids=lambda w: w.name)
+@pytest.mark.parametrize("w", BIT_EXACT + [W.C1, W.C2, W.P1, W.P2, W.C3, W.C3_V200], ids=lambda w: w.name)
 @pytest.mark.parametrize("hybrid", [False, True], ids=["ddmc", "hybrid"])
 def test_table_matches_oracle(w, hybrid):
     og, ot = _oracle(w, hybrid)
@@ -189,3 +190,64 @@ def test_c2_full_size_sampled_packets_replay_exactly():
     # every packet advanced S transitions unless it escaped first
     assert t["steps"] <= w.packets * S
     assert t["steps"] + t["escaped"] * S >= w.packets * S
+
+
+def _sampled_replay(w, S, n_ids=40):
+    og, ot = _oracle(w)
+    p = R.Problem(w)
+    thr, flags = p.rows()
+    assert np.array_equal(thr, ot["thr"])
+    p.reset()
+    p.launch(w.packets, w.seed, steps_per_launch=S)
+    t = p.read()
+    assert t["emitted"] == w.packets
+    ids = np.unique(np.concatenate([np.arange(8), np.linspace(8, w.packets - 1, n_ids).astype(np.int64)]))
+    for pid in ids:
+        st = p.packet_states(w.packets, int(pid), 1)
+        ref = C.replay_packet(og, ot, w.seed, int(pid), S)
+        assert st["status"][0] == (2 if ref["done"] else 1)
+        if not ref["done"]:
+            assert (st["cell"][0], st["bin"][0], st["steps"][0], st["event_draws"][0]) == \
+                (ref["cell"], ref["bin"], ref["steps"], ref["event_draws"])
+    return t
+
+
+@pytest.mark.parametrize("w", [W.C3, W.C3_V200], ids=lambda w: w.name)
+def test_c3_full_size_sampled_packets_replay_exactly(w):
+    # 64^3 sphere x 128 bins, all 1e7 packets, one slice of 2048 transitions;
+    # sampled packets replayed one by one by the oracle end in the same state.
+    t = _sampled_replay(w, 2048)
+    assert t["steps"] <= w.packets * 2048
+
+
+@pytest.mark.parametrize("w", [W.SPHERE8, W.SPHERE9_V.with_(vmax_kms=0.0, name="sphere_small_static")],
+                         ids=lambda w: w.name)
+def test_static_sphere_matches_chain_and_is_isotropic(w):
+    og, ot = _oracle(w)
+    ch = A.chain_solve(w, ot)
+    N = 200_000
+    gpu = R.Problem(w).run(N, w.seed + 7)
+    assert gpu["escaped"] == N
+    zmax, frac, pval = A.compare_counts_to_probs(gpu["hist"], ch["hist"], N)
+    assert zmax < 5.0 and frac <= 0.02 and pval > 1e-3, (zmax, frac, pval)
+    # six faces equally likely; escape points lie at b <= ~R (sphere of radius R)
+    f = gpu["faces"].astype(float)
+    z = (f - N / 6) / np.sqrt(N / 6 * 5 / 6)
+    assert np.all(np.abs(z) < 4.0), f
+    sb = gpu["sb"].astype(float)
+    assert sb.sum() == N and sb[int(1.25 / 1.28 * 64):].sum() == 0
+
+
+def test_outflow_shifts_escape_spectrum_red():
+    # Hubble-like outflow: photons are redshifted relative to the static sphere
+    # (qualitative, Sec. 5.4 discusses the red/blue asymmetry).
+    w0 = W.SPHERE9_V.with_(vmax_kms=0.0, name="s0")
+    w1 = W.SPHERE9_V.with_(vmax_kms=200.0, name="s1")
+    N = 100_000
+    e = w0.edges()
+    xc = 0.5 * (e[1:] + e[:-1])
+    m = []
+    for w in (w0, w1):
+        h = R.Problem(w).run(N, w.seed)["hist"][1:-1].astype(float)
+        m.append((h * xc).sum() / h.sum())
+    assert m[1] < m[0] - 0.5, m

@@ -1,4 +1,4 @@
-"""Pins of the oracle's opacity functions (Sec. 2.1, Sec. 2.3) against
+"""Pins of the oracle's opacity functions (Sec. 2.1, Sec. 2.2) against
 quadrature of their definitions, library special functions and limits."""
 import numpy as np
 import pytest

@@ -1,4 +1,4 @@
-"""Pins of the oracle's leakage table (Sec. 2.3 eqs. z-leakage, x-leakage;
+"""Pins of the oracle's leakage table (Sec. 2.2 eqs. z-leakage, x-leakage;
 Sec. 5.1 boundary coefficient) against the PDE it discretises and the
 paper's stated reductions, and of the 32-bit quantisation."""
 import numpy as np
@@ -18,7 +18,7 @@ def _table(w, **kw):
 
 @pytest.mark.parametrize("w", [W.TINY, W.C1, W.P2])
 def test_spatial_rate_is_ficks_law_diffusion(w):
-    # Interior uniform cells: k_z-leak = 1/(3 k_j dz^2) (Sec. 2.3 reduction), i.e. a
+    # Interior uniform cells: k_z-leak = 1/(3 k_j dz^2) (Sec. 2.2 reduction), i.e. a
     # random walk of step dz with diffusion coefficient D = r dz^2 = 1/(3 k), the
     # coefficient of Fick's law (eq. Ficks-Law).
     g, t = _table(w)
@@ -33,7 +33,7 @@ def test_spatial_rate_is_ficks_law_diffusion(w):
 
 @pytest.mark.parametrize("w", [W.TINY, W.C1, W.P2])
 def test_frequency_rate_is_fokker_planck_diffusion(w):
-    # Uniform bins: k_x-leak = [(1/k_j + 1/k_j+1) dx^2]^-1 (harmonic mean, Sec. 2.3);
+    # Uniform bins: k_x-leak = [(1/k_j + 1/k_j+1) dx^2]^-1 (harmonic mean, Sec. 2.2);
     # where neighbouring opacities are equal the walk's diffusion coefficient r dx^2
     # is k/2, the coefficient of eq. Fokker-Planck.
     g, t = _table(w)
@@ -52,7 +52,7 @@ def test_frequency_rate_is_fokker_planck_diffusion(w):
 
 
 def test_flux_conservation_with_nonuniform_bins_and_density():
-    # Sec. 2.3: the discrete equation conserves photon flux across interfaces:
+    # Sec. 2.2: the discrete equation conserves photon flux across interfaces:
     # dx_j r(j->j+1) = dx_j+1 r(j+1->j) and, for equal widths, r(i->i+1) = r(i+1->i)
     # between cells of different density.
     w = W.SMALL

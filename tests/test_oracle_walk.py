@@ -1,4 +1,4 @@
-"""Pins of the oracle's random stream and DDMC walk (Sec. 2.4): Philox
+"""Pins of the oracle's random stream and DDMC walk (Sec. 2.3): Philox
 known-answer vectors, the exact absorbing chain, the literal competing
 exponentials, conservation and the step watchdog."""
 import os
