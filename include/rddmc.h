@@ -289,6 +289,33 @@ int rddmc_read_packet_states(const rddmc_grid* grid, const void* d_state, uint64
                              uint64_t count, uint32_t* cell, uint32_t* bin, uint64_t* steps, uint64_t* event_draws,
                              uint8_t* status, void* stream);
 
+/*
+ * rddmc_launch_packets_noalloc -- rddmc_launch_packets for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this is a deployment
+ * variant.  A caller that cannot call cudaMalloc (for example a plug-in inside
+ * a host application that owns all device memory and gives the plug-in none,
+ * or code that must not trigger the implicit device-wide synchronisation
+ * cudaMalloc can cause) has no state buffer to pass.  This entry point keeps
+ * the packet cursor and the saved packet states in a fixed array compiled into
+ * the library: RDDMC_NOALLOC_SCRATCH_BYTES of device memory that every GPU
+ * which loads the library holds until the process exits.  It allocates
+ * nothing itself.
+ *   Arguments and results are those of rddmc_launch_packets without d_state
+ *   and state_bytes.  A run to completion (steps_per_launch = 0, resume = 0)
+ *   takes any packet count; time-sliced or resumed runs must fit their
+ *   per-packet state in the array (about 1.3 million packets) and otherwise
+ *   get RDDMC_ERR_SIZE.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.  All calls share the array and it keeps the previous call's
+ *   contents: the cursor is reset by every launch, and resume = 1 continues the
+ *   packets the previous call saved there.  Calls whose work overlaps on the
+ *   GPU race on the array and must be serialised by the caller.
+ */
+#define RDDMC_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int rddmc_launch_packets_noalloc(const rddmc_grid* grid, const void* d_table, const rddmc_run_opts* opts,
+                                 void* d_tallies, size_t tally_bytes, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* rddmc_status_string(int status);
 

@@ -29,7 +29,7 @@ NSB = 64  # impact-parameter bins of the surface-brightness histogram
 
 EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc_precompute_leakage",
             "rddmc_reset_tallies", "rddmc_launch_packets", "rddmc_read_tallies", "rddmc_table_rows",
-            "rddmc_read_packet_states", "rddmc_status_string", "rddmc_version"]
+            "rddmc_read_packet_states", "rddmc_launch_packets_noalloc", "rddmc_status_string", "rddmc_version"]
 
 
 class GridDesc(ctypes.Structure):
@@ -92,6 +92,7 @@ def lib():
         L.rddmc_read_tallies.argtypes = [vp, vp, ctypes.POINTER(Tallies), vp, vp, vp, vp]
         L.rddmc_table_rows.argtypes = [vp, vp, vp, vp, vp]
         L.rddmc_read_packet_states.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, vp, vp, vp]
+        L.rddmc_launch_packets_noalloc.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp]
         L.rddmc_status_string.argtypes = [i32]
         L.rddmc_status_string.restype = ctypes.c_char_p
         L.rddmc_version.argtypes = []
@@ -162,6 +163,15 @@ def launch_packets(grid, d_table: int, opts: RunOpts, d_state: int, state_bytes:
     _check("rddmc_launch_packets", lib().rddmc_launch_packets(
         ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(opts), ctypes.c_void_p(d_state),
         int(state_bytes), ctypes.c_void_p(d_tallies), int(tally_bytes), ctypes.c_void_p(stream)))
+
+
+def launch_packets_noalloc(grid, d_table: int, opts: RunOpts, d_tallies: int, tally_bytes: int, stream: int = 0):
+    """rddmc_launch_packets_noalloc: the walk with the library's fixed scratch
+    array in place of a caller state buffer (for callers that cannot allocate
+    device memory); concurrent calls race on that array."""
+    _check("rddmc_launch_packets_noalloc", lib().rddmc_launch_packets_noalloc(
+        ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(opts), ctypes.c_void_p(d_tallies),
+        int(tally_bytes), ctypes.c_void_p(stream)))
 
 
 def read_tallies(grid, d_tallies: int, J: int, nfaces: int, stream: int = 0) -> dict:
