@@ -245,6 +245,12 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
     const double a = orc_damping(g->T);
     double* phi = (double*)malloc(sizeof(double) * J);
     for (int j = 0; j < J; ++j) phi[j] = orc_bin_mean_H(a, g->edges[j], g->edges[j + 1]);
+    /* memo of the shifted bin means phi_j(delta) for the distinct face shifts
+     * met so far (a pure function of delta; a Hubble flow has a single one) */
+    enum { NMEMO = 16 };
+    double memo_delta[NMEMO];
+    double* memo_phi[NMEMO];
+    int nmemo = 0;
     double dzmin = 1e300;
     for (int ax = 0; ax < g->ndim; ++ax) dzmin = fmin(dzmin, orc_dz(g, ax));
 
@@ -295,9 +301,23 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
                     if (!orc_in_medium(g, nidx)) { rate[o] = r_bnd; act[o] = ORC_ACT_ESCAPE; continue; }
                     int64_t nb = orc_cell_of(g, nidx);
                     double delta = orc_face_shift(g, c, nb, ax, side);
-                    double knb = orc_k0(g, nb) *
-                                 (delta == 0.0 ? phi[j]
-                                               : orc_bin_mean_H(a, g->edges[j] + delta, g->edges[j + 1] + delta));
+                    double phin;
+                    if (delta == 0.0) {
+                        phin = phi[j];
+                    } else {
+                        int m = 0;
+                        while (m < nmemo && memo_delta[m] != delta) ++m;
+                        if (m == nmemo && nmemo < NMEMO) {
+                            memo_delta[nmemo] = delta;
+                            memo_phi[nmemo] = (double*)malloc(sizeof(double) * J);
+                            for (int jj = 0; jj < J; ++jj)
+                                memo_phi[nmemo][jj] = orc_bin_mean_H(a, g->edges[jj] + delta, g->edges[jj + 1] + delta);
+                            ++nmemo;
+                        }
+                        phin = (m < nmemo) ? memo_phi[m][j]
+                                           : orc_bin_mean_H(a, g->edges[j] + delta, g->edges[j + 1] + delta);
+                    }
+                    double knb = orc_k0(g, nb) * phin;
                     double dznb = dz;
                     if (g->hybrid && knb * dznb < g->tau_ddmc) { rate[o] = r_bnd; act[o] = ORC_ACT_TO_MC; continue; }
                     rate[o] = 1.0 / (3.0 * dz) * 2.0 / (k * dz + knb * dznb);
@@ -322,6 +342,7 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
         }
     }
     free(phi);
+    for (int m = 0; m < nmemo; ++m) free(memo_phi[m]);
     return 0;
 }
 

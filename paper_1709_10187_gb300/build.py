@@ -27,8 +27,10 @@ def nvcc() -> str:
 
 
 def _flags():
+    # RDDMC_NVCC_EXTRA: extra nvcc options for tuning builds (e.g. -DRDDMC_WALK_MIN_BLOCKS=4)
+    extra = os.environ.get("RDDMC_NVCC_EXTRA", "").split()
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-O2",
-                   "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+                   "-I", os.path.join(ROOT, "include"), "-I", CSRC] + extra
 
 
 def _stale() -> bool:

@@ -203,6 +203,7 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
     g->off_edges = off; off += align256((uint64_t)(J + 1) * 8);
     g->off_phi = off; off += align256((uint64_t)J * 8);
     g->off_rows = off; off += align256((uint64_t)g->n_class * J * g->row_bytes);
+    g->off_fast = off; off += align256((uint64_t)g->n_class * J * 8);
     g->table_bytes = off;
     *out = g;
     return RDDMC_OK;
@@ -276,7 +277,8 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
     for (int a = 0; a < 3; ++a) { h.n[a] = g->n[a]; h.dz[a] = 2.0 * g->R / g->n[a]; }
     h.mode = p->mode;
     h.off_class = g->off_class; h.off_cdesc = g->off_cdesc; h.off_rebin = g->off_rebin; h.off_vel = g->off_vel;
-    h.off_edges = g->off_edges; h.off_phi = g->off_phi; h.off_rows = g->off_rows; h.total = g->table_bytes;
+    h.off_edges = g->off_edges; h.off_phi = g->off_phi; h.off_rows = g->off_rows; h.off_fast = g->off_fast;
+    h.total = g->table_bytes;
     h.tau_ddmc = p->tau_ddmc; h.lambda = p->lambda; h.f_mu = p->f_mu; h.a = g->a; h.vth = g->vth;
 
     char* base = (char*)d_table;

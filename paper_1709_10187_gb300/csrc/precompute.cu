@@ -34,7 +34,7 @@ __device__ __forceinline__ uint32_t quantise_dev(double C) {
 template <int NDIM>
 __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ cdesc,
                             const double* __restrict__ edges, const double* __restrict__ phi,
-                            uint32_t* __restrict__ rows, int64_t nrow) {
+                            uint32_t* __restrict__ rows, uint2* __restrict__ fast, int64_t nrow) {
     constexpr int K = 2 + 2 * NDIM;
     constexpr int W = NDIM == 1 ? 4 : 8;  // words per row, the last holding the flags
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,6 +100,7 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
     if (hybrid && k * dzmin < h.tau_ddmc) fl |= FLAG_THIN;
     // word order: thr0, thr1, thr2, flags[, thr3..thr6] so that the first 16
     // bytes carry everything a frequency move needs
+    fast[r] = make_uint2(out[0], (fl & FLAG_FASTX) ? out[1] : 0u);
     if (NDIM == 1) {
         reinterpret_cast<uint4*>(rows)[r] = make_uint4(out[0], out[1], out[2], fl);
     } else {
@@ -132,10 +133,11 @@ cudaError_t launch_precompute(const rddmc_grid& g, void* d_table, cudaStream_t s
     const int64_t blocks = (nrow + threads - 1) / threads;
     const ClassDesc* cd = (const ClassDesc*)(base + g.off_cdesc);
     uint32_t* rows = (uint32_t*)(base + g.off_rows);
+    uint2* fast = (uint2*)(base + g.off_fast);
     if (g.ndim == 1)
-        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, nrow);
+        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, nrow);
     else
-        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, nrow);
+        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, nrow);
     return cudaGetLastError();
 }
 

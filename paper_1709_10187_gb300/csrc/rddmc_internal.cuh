@@ -2,12 +2,17 @@
 //
 // Device table buffer (caller-owned, filled by rddmc_precompute_leakage):
 //   [TableHeader | cell_class u32[ncell] | ClassDesc[n_class] | Rebin[n_class*nfaces]
-//    | cell velocity f64[3*ncell] (moving media only) | edges f64[J+1] | phi f64[J] | rows]
+//    | cell velocity f64[3*ncell] (moving media only) | edges f64[J+1] | phi f64[J] | rows
+//    | fast heads uint2[n_class*J]]
 // every region 256-byte aligned.  Rows are n_class blocks of J rows; a row is
 // 16 bytes in a slab {thr0, thr1, thr2, flags} and 32 bytes in 3D
 // {thr0, thr1, thr2, flags, thr3, thr4, thr5, thr6}: the first 16 bytes always
 // hold both frequency thresholds and the flags, which is all the frequency-move
-// fast path reads.  Outcome order: bin-1, bin+1, then -e_a, +e_a per axis.
+// fast path needs.  A fast head {thr0, thr1 or 0} repeats the two frequency
+// thresholds of each row in 8 bytes, with thr1 replaced by 0 when a frequency
+// outcome is not a plain move, so that a frequency move reads 8 bytes and one
+// failed compare sends every other case to the full row.  Outcome order:
+// bin-1, bin+1, then -e_a, +e_a per axis.
 //
 // Tally buffer (u64): [0, 16) counters, [16, 22) faces, [22, 22+J+2) escape
 // histogram, then kNsb impact-parameter bins.
@@ -66,7 +71,7 @@ struct TableHeader {
     uint32_t filled;
     int32_t ndim, J, ncell, n_class, K, row_bytes;
     int32_t n[3], mode;
-    uint64_t off_class, off_cdesc, off_rebin, off_vel, off_edges, off_phi, off_rows, total;
+    uint64_t off_class, off_cdesc, off_rebin, off_vel, off_edges, off_phi, off_rows, off_fast, total;
     double tau_ddmc, lambda, f_mu, a, dz[3], vth;
 };
 

@@ -9,10 +9,11 @@
 // competing exponentials of eq. l_min_1/2.
 //
 // Frequency moves dominate (the core of the line, Sec. 4.2), so the fast path
-// reads only the first 16 bytes of a row {thr0, thr1, thr2, flags}: when
-// w < thr1 and both frequency outcomes are plain moves, the packet moves one
-// bin down (w < thr0) or up.  Everything else -- spatial moves, Doppler
-// rebins, escapes through exterior faces -- goes through one generic step that
+// reads only the state's 8-byte fast head {thr0, thr1 or 0}, staged in shared
+// memory: when w < thr1 the packet moves one bin down (w < thr0) or up.
+// Everything else -- spatial moves, Doppler rebins, escapes through exterior
+// faces, and frequency outcomes that are not plain moves (their head holds 0)
+// -- goes through one generic step that reads the full row (through L1) and
 // evaluates every threshold and the outcome's 2-bit action.
 //
 // Lanes whose packet escaped, was aborted by the watchdog or reached the end of
@@ -28,11 +29,16 @@
 namespace rddmc {
 namespace {
 
+#ifndef RDDMC_WALK_MIN_BLOCKS
+#define RDDMC_WALK_MIN_BLOCKS 4  // resident 256-thread CTAs per SM the register budget targets
+#endif
+
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kSmemHistMax = 8192;  // histogram entries kept in shared memory
 
 struct WalkParams {
     const uint4* rows;
+    const uint2* fast;
     const uint32_t* cell_class;
     const Rebin* rebin;
     const double* cell_v;     // km/s, 3 per cell (moving media)
@@ -146,7 +152,7 @@ __device__ __noinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cel
 }
 
 template <int NDIM, bool SMEM_ROWS>
-__global__ void __launch_bounds__(256, 3) walk_kernel(const WalkParams P) {
+__global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const WalkParams P) {
     constexpr int RW = NDIM == 1 ? 1 : 2;  // uint4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(smem_raw);  // kCounters
@@ -154,15 +160,16 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const WalkParams P) {
     unsigned long long* s_sb = s_face + 8;                                        // kNsb
     unsigned long long* s_hist = s_sb + kNsb;                                     // J+2 if in smem
     const int nhist = P.J + 2;
-    uint4* s_rows = reinterpret_cast<uint4*>(s_hist + (P.hist_in_smem ? ((nhist + 1) & ~1) : 0));
+    uint2* s_fast = reinterpret_cast<uint2*>(s_hist + (P.hist_in_smem ? ((nhist + 1) & ~1) : 0));
 
     for (int i = threadIdx.x; i < kCounters + 8 + kNsb; i += blockDim.x) s_cnt[i] = 0ull;
     if (P.hist_in_smem)
         for (int i = threadIdx.x; i < nhist; i += blockDim.x) s_hist[i] = 0ull;
     if (SMEM_ROWS)
-        for (int i = threadIdx.x; i < P.n_rows * RW; i += blockDim.x) s_rows[i] = __ldg(&P.rows[i]);
+        for (int i = threadIdx.x; i < P.n_rows; i += blockDim.x) s_fast[i] = __ldg(&P.fast[i]);
     __syncthreads();
-    const uint4* rows = SMEM_ROWS ? s_rows : P.rows;
+    const uint4* rows = P.rows;
+    const uint2* fast = SMEM_ROWS ? s_fast : P.fast;
 
     const unsigned lane = threadIdx.x & 31u;
     const unsigned J = (unsigned)P.J;
@@ -178,10 +185,10 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const WalkParams P) {
     // packet has finished.
     auto generic = [&](unsigned w) -> bool {
         const unsigned ri = min(s, nr1);
-        const uint4 a = SMEM_ROWS ? rows[ri * RW] : __ldg(&rows[ri * RW]);
+        const uint4 a = __ldg(&rows[ri * RW]);
         unsigned o = (unsigned)(w >= a.x) + (unsigned)(w >= a.y) + (unsigned)(w >= a.z);
         if (NDIM == 3) {
-            const uint4 b = SMEM_ROWS ? rows[ri * RW + 1] : __ldg(&rows[ri * RW + 1]);
+            const uint4 b = __ldg(&rows[ri * RW + 1]);
             o += (unsigned)(w >= b.x) + (unsigned)(w >= b.y) + (unsigned)(w >= b.z) + (unsigned)(w >= b.w);
         }
         const unsigned fl = a.w;
@@ -293,10 +300,9 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const WalkParams P) {
                 unsigned q;
 #define RDDMC_FAST(W, Q)                                                                  \
     {                                                                                     \
-        const unsigned ri_ = min(s, nr1);                                                 \
-        const uint4 a_ = SMEM_ROWS ? rows[ri_ * RW] : __ldg(&rows[ri_ * RW]);             \
-        if ((W) < a_.y && (a_.w & FLAG_FASTX)) {                                          \
-            s += ((W) >= a_.x) ? 1u : 0xffffffffu;                                        \
+        const uint2 f_ = SMEM_ROWS ? fast[min(s, nr1)] : __ldg(&fast[min(s, nr1)]);       \
+        if ((W) < f_.y) {                                                                 \
+            s += ((W) >= f_.x) ? 1u : 0xffffffffu;                                        \
         } else {                                                                          \
             q = (Q);                                                                      \
             goto slow;                                                                    \
@@ -406,6 +412,7 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     WalkParams P;
     std::memset(&P, 0, sizeof(P));
     P.rows = (const uint4*)(tb + g.off_rows);
+    P.fast = (const uint2*)(tb + g.off_fast);
     P.cell_class = (const uint32_t*)(tb + g.off_class);
     P.rebin = (const Rebin*)(tb + g.off_rebin);
     P.cell_v = (const double*)(tb + g.off_vel);
@@ -460,7 +467,7 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     const int threads = o.threads_per_cta ? o.threads_per_cta : 256;
     size_t smem = (size_t)(kCounters + 8 + kNsb) * 8;
     if (P.hist_in_smem) smem += (size_t)((g.J + 2 + 1) & ~1) * 8;
-    const size_t rows_bytes = (size_t)P.n_rows * g.row_bytes;
+    const size_t rows_bytes = (size_t)P.n_rows * 8;  // fast heads
     const bool use_smem_rows = o.table_in_smem && smem + rows_bytes <= (size_t)smem_optin;
     if (use_smem_rows) smem += rows_bytes;
     if ((e = cudaMemsetAsync(P.cursor, 0, 8, s)) != cudaSuccess) return e;

@@ -247,7 +247,7 @@ class Problem:
         reset_tallies(self.grid, self.tally.data_ptr(), self.tally.numel() * 8, self.stream())
 
     def launch(self, n_packets: int, seed: int, max_steps: int = 0, steps_per_launch: int = 0, resume: int = 0,
-               ctas_per_sm: int = 0, threads_per_cta: int = 0, chunk: int = 0, table_in_smem: int = 1):
+               ctas_per_sm: int = 0, threads_per_cta: int = 0, chunk: int = 0, table_in_smem: int = 0):
         st = self.ensure_state(n_packets)
         o = RunOpts(seed, n_packets, max_steps, steps_per_launch, resume, ctas_per_sm, threads_per_cta, chunk,
                     table_in_smem, 0)
