@@ -237,3 +237,41 @@ def compare_two_samples(c1, n1, c2, n2, min_expected=20.0):
     var = p1[sel] * (1 - p1[sel]) / n1 + p2[sel] * (1 - p2[sel]) / n2
     z = (p1[sel] - p2[sel]) / np.sqrt(np.maximum(var, 1e-300))
     return float(np.abs(z).max()) if z.size else 0.0, float((np.abs(z) > 3).mean()) if z.size else 0.0
+
+
+# --------------------------------------------------------------------------- redistribution (Appendix A)
+def R_IIA(x, xp, a):
+    """Angle-averaged redistribution for isotropic coherent scattering without
+    recoil (Appendix A): R(x, x') = 1/(pi H(x',a)) int_zeta^inf e^{-u^2}
+    [atan((xmin + u)/a) - atan((xmax - u)/a)] du, zeta = |x - x'|/2; the
+    density of the outgoing x given the incoming x'."""
+    xmax, xmin = max(x, xp), min(x, xp)
+    zeta = 0.5 * abs(x - xp)
+    f = lambda u: np.exp(-u * u) * (np.arctan((xmin + u) / a) - np.arctan((xmax - u) / a))
+    pts = [p for p in (zeta, 0.5 * (xmax - xmin) + 0.0, xmax, abs(xmax)) if p >= zeta]
+    val, _ = si.quad(f, zeta, zeta + 12.0, points=sorted(set(pts))[1:] or None, epsabs=1e-14, epsrel=1e-10,
+                     limit=400)
+    return val / (np.pi * voigt_faddeeva(a, xp))
+
+
+def R_IA_core(x, xp):
+    """Core (a -> 0) limit printed in Appendix A: (sqrt(pi)/2) e^{x'^2} erfc(max(|x|,|x'|))."""
+    return 0.5 * np.sqrt(np.pi) * np.exp(xp * xp) * ss.erfc(max(abs(x), abs(xp)))
+
+
+def R_IIA_wing(x, xp):
+    """Wing limit printed in Appendix A: (2x'/(x+x'))^2 [e^{-zeta^2}/sqrt(pi) - zeta erfc(zeta)]."""
+    zeta = 0.5 * abs(x - xp)
+    return (2.0 * xp / (x + xp)) ** 2 * (np.exp(-zeta * zeta) / np.sqrt(np.pi) - zeta * ss.erfc(zeta))
+
+
+def R_IIA_bin_probs(edges, xp, a, n_sub=8):
+    """Probability of each outgoing-frequency bin, integrating R_II-A over the bin
+    with Gauss-Legendre nodes."""
+    gx, gw = np.polynomial.legendre.leggauss(n_sub)
+    out = np.zeros(len(edges) - 1)
+    for i in range(len(edges) - 1):
+        lo, hi = edges[i], edges[i + 1]
+        xs = 0.5 * (hi - lo) * gx + 0.5 * (hi + lo)
+        out[i] = 0.5 * (hi - lo) * sum(w * R_IIA(x, xp, a) for x, w in zip(xs, gw))
+    return out

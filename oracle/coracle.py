@@ -49,11 +49,16 @@ def lib():
         L.orc_tally_len.restype = i32
         L.orc_tally_len.argtypes = [i32]
         L.orc_walk_ddmc.restype = i32
-        L.orc_walk_ddmc.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, d, u64, u64, u64, u64, i32, i32, vp]
+        L.orc_walk_ddmc.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, vp, d, u64, u64, u64, u64, i32, i32,
+                                    vp]
         L.orc_walk_slice.restype = i32
-        L.orc_walk_slice.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, d, u64, u64, u64, u64, i32, vp]
+        L.orc_walk_slice.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, d, u64, u64, u64, u64, i32, vp]
         L.orc_replay_packet.restype = i32
-        L.orc_replay_packet.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, d, u64, u64, u64, u64, vp, vp]
+        L.orc_replay_packet.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, d, u64, u64, u64, u64, vp, vp]
+        L.orc_scatter_samples.restype = None
+        L.orc_scatter_samples.argtypes = [d, d, u64, u64, vp]
+        L.orc_upar_table.restype = None
+        L.orc_upar_table.argtypes = [d, vp]
         _LIB = L
     return _LIB
 
@@ -166,7 +171,7 @@ def walk(grid: Grid, table: dict, seed: int, p0: int, npk: int, max_steps: int =
     thr = np.ascontiguousarray(table["thr"].ravel())
     rate = np.ascontiguousarray(table["rate"].ravel())
     rc = lib().orc_walk_ddmc(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
-                             _ptr(table["rebin_thr"]), _ptr(rate), float(grid.w.x0), int(seed), int(p0),
+                             _ptr(table["rebin_thr"]), _ptr(rate), _ptr(table["k"]), float(grid.w.x0), int(seed), int(p0),
                              int(npk), int(max_steps), int(literal), int(nthreads), _ptr(out))
     if rc == -1:
         raise ValueError("orc_walk_ddmc: bad input")
@@ -181,7 +186,8 @@ def replay_packet(grid: Grid, table: dict, seed: int, pid: int, n_trans: int, ma
     tl = np.zeros(lib().orc_tally_len(grid.J), dtype=np.uint64)
     thr = np.ascontiguousarray(table["thr"].ravel())
     rc = lib().orc_replay_packet(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
-                                 _ptr(table["rebin_thr"]), float(grid.w.x0), int(seed), int(pid), int(n_trans),
+                                 _ptr(table["rebin_thr"]), _ptr(table["k"]), float(grid.w.x0), int(seed), int(pid),
+                                 int(n_trans),
                                  int(max_steps), _ptr(out), _ptr(tl))
     if rc == -1:
         raise ValueError("orc_replay_packet: bad input")
@@ -197,10 +203,25 @@ def walk_slice(grid: Grid, table: dict, seed: int, p0: int, npk: int, n_trans: i
     out = np.zeros(lib().orc_tally_len(grid.J), dtype=np.uint64)
     thr = np.ascontiguousarray(table["thr"].ravel())
     rc = lib().orc_walk_slice(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
-                              _ptr(table["rebin_thr"]), float(grid.w.x0), int(seed), int(p0), int(npk),
+                              _ptr(table["rebin_thr"]), _ptr(table["k"]), float(grid.w.x0), int(seed), int(p0),
+                              int(npk),
                               int(n_trans), int(nthreads), _ptr(out))
     if rc == -1:
         raise ValueError("orc_walk_slice: bad input")
     res = unpack_tally(out, grid.J)
     res["status"] = rc
     return res
+
+
+def scatter_samples(T: float, x_in: float, seed: int, n: int) -> np.ndarray:
+    """Outgoing frequencies of n independent scatterings at x_in (density R_II-A)."""
+    out = np.zeros(n, dtype=np.float64)
+    lib().orc_scatter_samples(float(T), float(x_in), int(seed), int(n), _ptr(out))
+    return out
+
+
+def upar_table(T: float) -> np.ndarray:
+    """Envelope split points (u1, u0) of the u_par sampler on the |x| grid (step 1/16)."""
+    out = np.zeros(2 * 1024, dtype=np.float64)
+    lib().orc_upar_table(float(damping(T)), _ptr(out))
+    return out.reshape(1024, 2)

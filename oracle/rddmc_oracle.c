@@ -410,6 +410,8 @@ typedef struct orc_walk_args {
     uint64_t seed, p0, p1, max_steps;
     int literal;         /* 1: competing exponentials in FP64 (eq. l_min_1/2) */
     uint64_t limit;      /* transitions per packet, UINT64_MAX = until escape or abort */
+    const double* k;     /* k_ij per state (hybrid walk) */
+    const double* upar;  /* (u1, u0) rejection-envelope split points per |x| grid point (hybrid) */
     uint64_t* tally;     /* per-thread */
     int status;
 } orc_walk_args;
@@ -470,6 +472,284 @@ static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Continuous MC in thin states (Sec. 5.1, Sec. 5.2)                          */
+/* ------------------------------------------------------------------------- */
+
+#define ORC_UPAR_STEP (1.0 / 16.0)  /* |x| grid of the envelope split points */
+#define ORC_UPAR_N 1024
+
+/* Mass of the three-part envelope of f(u) = e^{-u^2} / (a^2 + (x-u)^2) (x >= 0):
+ * u < u1: e^{-u^2} g(u1);  u1 <= u <= u0: c2 g(u), c2 = max of e^{-u^2} there;
+ * u > u0: e^{-u0^2} g(u), with g(u) = 1/(a^2 + (x-u)^2) and u1 <= u0 <= x,
+ * 0 <= u0.  Every piece bounds f because g rises up to x and e^{-u^2} falls
+ * away from 0. */
+static double orc_env_mass(double a, double x, double u1, double u0) {
+    double g1 = 1.0 / (a * a + (x - u1) * (x - u1));
+    double w1 = g1 * 0.5 * ORC_SQRTPI * (1.0 + erf(u1));
+    double th1 = atan((u1 - x) / a), th0 = atan((u0 - x) / a);
+    double c2 = (u1 <= 0.0) ? 1.0 : exp(-u1 * u1);
+    double w2 = c2 * (th0 - th1) / a;
+    double w3 = exp(-u0 * u0) * (0.5 * ORC_PI - th0) / a;
+    return w1 + w2 + w3;
+}
+
+/* Split points minimising the envelope mass on a grid of candidates, for each
+ * |x| = i * ORC_UPAR_STEP.  Any valid pair samples the same distribution; the
+ * choice only sets the acceptance rate. */
+void orc_upar_table(double a, double* tab) {
+    for (int i = 0; i < ORC_UPAR_N; ++i) {
+        double x = i * ORC_UPAR_STEP, best = INFINITY, b1 = -40.0, b0 = 0.0;
+        for (int p = 0; p <= 24; ++p) {
+            double u0 = x * p / 24.0;
+            for (int q = 0; q <= 25; ++q) {
+                double u1 = (q == 25) ? -40.0 : -3.0 + (u0 + 3.0) * q / 24.0;
+                double m = orc_env_mass(a, x, u1, u0);
+                if (m < best) { best = m; b1 = u1; b0 = u0; }
+            }
+        }
+        tab[2 * i] = b1;
+        tab[2 * i + 1] = b0;
+    }
+}
+
+static double orc_ev(const orc_walk_args* A, uint64_t pk, uint64_t* e) {
+    return orc_unif(orc_word(A->seed, pk, ORC_EVENT, (*e)++));
+}
+
+/* Parallel atom velocity u (Doppler units) of a scattering at frequency x:
+ * density e^{-u^2} / (a^2 + (x-u)^2) (Sec. 5.2; Maxwellian sign per the
+ * standard Voigt convolution), by rejection from the three-part envelope. */
+static double orc_sample_upar(const orc_walk_args* A, double a, double xin, uint64_t pk, uint64_t* e) {
+    const double x = fabs(xin), sg = xin < 0.0 ? -1.0 : 1.0;
+    int i = (int)(x / ORC_UPAR_STEP);
+    if (i > ORC_UPAR_N - 1) i = ORC_UPAR_N - 1;
+    const double u1 = A->upar[2 * i], u0 = A->upar[2 * i + 1];
+    const double g1 = 1.0 / (a * a + (x - u1) * (x - u1));
+    const double th1 = atan((u1 - x) / a), th0 = atan((u0 - x) / a);
+    const double c2 = (u1 <= 0.0) ? 1.0 : exp(-u1 * u1);
+    const double w1 = g1 * 0.5 * ORC_SQRTPI * (1.0 + erf(u1));
+    const double w2 = c2 * (th0 - th1) / a;
+    const double w3 = exp(-u0 * u0) * (0.5 * ORC_PI - th0) / a;
+    const double sig = sqrt(0.5);
+    for (int it = 0; it < 1000000; ++it) {
+        double pick = orc_ev(A, pk, e) * (w1 + w2 + w3), u, acc;
+        if (pick < w1) {
+            /* Gaussian N(0, 1/2) below u1: rejection from the full Gaussian
+             * when u1 >= 0, Marsaglia's tail method otherwise */
+            if (u1 >= 0.0) {
+                do {
+                    double r1 = orc_ev(A, pk, e), r2 = orc_ev(A, pk, e);
+                    u = sig * sqrt(-2.0 * log(r1)) * cos(2.0 * ORC_PI * r2);
+                } while (u >= u1);
+            } else {
+                const double c = -u1 / sig;
+                double X;
+                for (;;) {
+                    double r1 = orc_ev(A, pk, e), r2 = orc_ev(A, pk, e);
+                    X = sqrt(c * c - 2.0 * log(r1));
+                    if (r2 * X < c) break;
+                }
+                u = -sig * X;
+            }
+            acc = (1.0 / (a * a + (x - u) * (x - u))) / g1;
+        } else if (pick < w1 + w2) {
+            double th = th1 + orc_ev(A, pk, e) * (th0 - th1);
+            u = x + a * tan(th);
+            acc = exp(-u * u) / c2;
+        } else {
+            double th = th0 + orc_ev(A, pk, e) * (0.5 * ORC_PI - th0);
+            u = x + a * tan(th);
+            acc = exp(u0 * u0 - u * u);
+        }
+        if (orc_ev(A, pk, e) < acc) return sg * u;
+    }
+    return sg * x;
+}
+
+/* Isotropic direction: mu uniform on (-1,1), azimuth uniform. */
+static void orc_iso_dir(const orc_walk_args* A, uint64_t pk, uint64_t* e, double n[3]) {
+    double mu = 2.0 * orc_ev(A, pk, e) - 1.0, ph = 2.0 * ORC_PI * orc_ev(A, pk, e);
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    n[0] = st * cos(ph); n[1] = st * sin(ph); n[2] = mu;
+}
+
+/* Direction uniform over the half-space around +/- e_ax (mu uniform on (0,1]). */
+static void orc_half_dir(const orc_walk_args* A, uint64_t pk, uint64_t* e, int ax, int side, double n[3]) {
+    double mu = 1.0 - orc_ev(A, pk, e), ph = 2.0 * ORC_PI * orc_ev(A, pk, e);
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    n[ax] = side * mu; n[(ax + 1) % 3] = st * cos(ph); n[(ax + 2) % 3] = st * sin(ph);
+}
+
+/* Coherent scattering in the atom frame, isotropic phase function, no recoil:
+ * x' = x + u_par (mu - 1) + u_perp sqrt(1 - mu^2), u_perp ~ N(0, 1/2),
+ * mu = n.n' (Sec. 5.2). */
+static double orc_scatter(const orc_walk_args* A, double a, double x, double n[3], uint64_t pk, uint64_t* e) {
+    double up = orc_sample_upar(A, a, x, pk, e);
+    double r1 = orc_ev(A, pk, e), r2 = orc_ev(A, pk, e);
+    double uperp = sqrt(0.5) * sqrt(-2.0 * log(r1)) * cos(2.0 * ORC_PI * r2);
+    double nn[3];
+    orc_iso_dir(A, pk, e, nn);
+    double mu = n[0] * nn[0] + n[1] * nn[1] + n[2] * nn[2];
+    if (mu > 1.0) mu = 1.0;
+    if (mu < -1.0) mu = -1.0;
+    n[0] = nn[0]; n[1] = nn[1]; n[2] = nn[2];
+    return x + up * (mu - 1.0) + uperp * sqrt(1.0 - mu * mu);
+}
+
+static int orc_bin_of(const orc_grid* g, double x) {
+    if (x < g->edges[0]) return -1;
+    if (x >= g->edges[g->J]) return g->J;
+    int lo = 0, hi = g->J;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (x >= g->edges[mid]) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+static int orc_is_thick(const orc_walk_args* A, int64_t c, int j) {
+    if (j < 0 || j >= A->g->J) return 0;
+    return !(A->flags[c * A->g->J + j] & ORC_FLAG_THIN);
+}
+
+static double orc_u(const orc_grid* g, int64_t c, int a) { return g->v ? g->v[3 * c + a] / orc_vth(g) : 0.0; }
+
+typedef struct orc_mc {
+    int idx[3];
+    double r[3], n[3], x;
+} orc_mc;
+
+/* Tally an escape of an MC packet leaving cell c through face (ax, side). */
+static void orc_mc_escape(const orc_walk_args* A, const orc_mc* m, int64_t c, int ax, int side, uint64_t* t) {
+    const orc_grid* g = A->g;
+    const int J = g->J;
+    t[ORC_T_ESCAPED]++;
+    t[ORC_T_FACE + 2 * ax + (side > 0 ? 1 : 0)]++;
+    double xo = m->x + m->n[0] * orc_u(g, c, 0) + m->n[1] * orc_u(g, c, 1) + m->n[2] * orc_u(g, c, 2);
+    int b = orc_bin_of(g, xo);
+    t[ORC_T_HIST + (b < 0 ? 0 : (b >= J ? J + 1 : b + 1))]++;
+    if (g->ndim == 3) {
+        double rr = m->r[0] * m->r[0] + m->r[1] * m->r[1] + m->r[2] * m->r[2];
+        double rn = m->r[0] * m->n[0] + m->r[1] * m->n[1] + m->r[2] * m->n[2];
+        double bb = sqrt(fmax(0.0, rr - rn * rn)) / g->R;
+        int k = (int)(bb / ORC_SB_MAX * ORC_NSB);
+        if (k > ORC_NSB - 1) k = ORC_NSB - 1;
+        t[ORC_T_HIST + J + 2 + k]++;
+    }
+}
+
+/* Cross from the MC packet's cell through face (ax, side): escape, continue in
+ * a thin neighbour, convert to DDMC in a thick neighbour with probability
+ * 2/(tau + 2 lambda) (2/3 + mu) (Sec. 5.1), or reflect from it (random point on
+ * the face, isotropic inward direction).  Returns 0 to continue MC, 1 escaped,
+ * 2 converted to DDMC (state in *cell_out, *bin_out). */
+static int orc_mc_cross(orc_walk_args* A, orc_mc* m, int ax, int side, uint64_t pk, uint64_t* e, uint64_t* t,
+                        int64_t* cell_out, int* bin_out) {
+    const orc_grid* g = A->g;
+    int64_t c = orc_cell_of(g, m->idx);
+    int nidx[3] = {m->idx[0], m->idx[1], m->idx[2]};
+    nidx[ax] += side;
+    if (!orc_in_medium(g, nidx)) { orc_mc_escape(A, m, c, ax, side, t); return 1; }
+    int64_t nb = orc_cell_of(g, nidx);
+    double xn = m->x + m->n[0] * (orc_u(g, c, 0) - orc_u(g, nb, 0)) + m->n[1] * (orc_u(g, c, 1) - orc_u(g, nb, 1)) +
+                m->n[2] * (orc_u(g, c, 2) - orc_u(g, nb, 2));
+    int jn = orc_bin_of(g, xn);
+    if (!orc_is_thick(A, nb, jn)) {
+        m->idx[ax] += side;
+        m->x = xn;
+        return 0;
+    }
+    double tau = A->k[nb * g->J + jn] * orc_dz(g, ax);
+    double P = 2.0 / (tau + 2.0 * g->lambda) * (2.0 / 3.0 + fabs(m->n[ax]));
+    if (orc_ev(A, pk, e) < P) {
+        t[ORC_T_CONVERSIONS]++;
+        *cell_out = nb;
+        *bin_out = jn;
+        return 2;
+    }
+    /* reflect: a random point on the same face, isotropic inward direction */
+    int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+    double p1 = orc_ev(A, pk, e), p2 = orc_ev(A, pk, e);
+    if (t1 < g->ndim) m->r[t1] = -g->R + (m->idx[t1] + p1) * orc_dz(g, t1);
+    if (t2 < g->ndim) m->r[t2] = -g->R + (m->idx[t2] + p2) * orc_dz(g, t2);
+    orc_half_dir(A, pk, e, ax, -side, m->n);
+    int j = orc_bin_of(g, m->x);
+    if (orc_is_thick(A, c, j)) {
+        t[ORC_T_CONVERSIONS]++;
+        *cell_out = c;
+        *bin_out = j;
+        return 2;
+    }
+    return 0;
+}
+
+/* Run an MC packet until it converts to DDMC (returns 2, state in *cell_out,
+ * *bin_out), escapes (1) or meets the event watchdog (3). */
+static int orc_mc_run(orc_walk_args* A, orc_mc* m, uint64_t pk, uint64_t* e, uint64_t* t, int64_t* cell_out,
+                      int* bin_out) {
+    const orc_grid* g = A->g;
+    const double a = orc_damping(g->T);
+    for (uint64_t ev = 0;; ++ev) {
+        if (ev >= A->max_steps) return 3;
+        int64_t c = orc_cell_of(g, m->idx);
+        double k = orc_k0(g, c) * orc_voigt_H(a, m->x);
+        double s = -log(orc_ev(A, pk, e)) / k;
+        /* distance to the cell boundary along n */
+        double dmin = INFINITY;
+        int fax = -1, fside = 0;
+        for (int ax = 0; ax < g->ndim; ++ax) {
+            if (m->n[ax] == 0.0) continue;
+            double lo = -g->R + m->idx[ax] * orc_dz(g, ax), hi = lo + orc_dz(g, ax);
+            double d = m->n[ax] > 0.0 ? (hi - m->r[ax]) / m->n[ax] : (lo - m->r[ax]) / m->n[ax];
+            if (d < 0.0) d = 0.0;
+            if (d < dmin) { dmin = d; fax = ax; fside = m->n[ax] > 0.0 ? 1 : -1; }
+        }
+        t[ORC_T_MC_EVENTS]++;
+        if (s < dmin) {
+            for (int q = 0; q < 3; ++q) m->r[q] += s * m->n[q];
+            m->x = orc_scatter(A, a, m->x, m->n, pk, e);
+            int j = orc_bin_of(g, m->x);
+            if (orc_is_thick(A, c, j)) {
+                t[ORC_T_CONVERSIONS]++;
+                *cell_out = c;
+                *bin_out = j;
+                return 2;
+            }
+            continue;
+        }
+        for (int q = 0; q < 3; ++q) m->r[q] += dmin * m->n[q];
+        m->r[fax] = -g->R + (m->idx[fax] + (fside > 0 ? 1 : 0)) * orc_dz(g, fax);
+        int rc = orc_mc_cross(A, m, fax, fside, pk, e, t, cell_out, bin_out);
+        if (rc) return rc;
+    }
+}
+
+/* A DDMC packet at (c, j) hands off to MC.  Spatial outcome into a thin
+ * neighbour: a random point on the face and an isotropic outward direction,
+ * x uniform in the bin, then the crossing into the neighbour.  Frequency
+ * outcome into a thin bin j_new (or a thin source state): a random point in
+ * the cell, an isotropic direction, x uniform in bin j_new. */
+static void orc_handoff(orc_walk_args* A, int64_t c, int j, int face, uint64_t pk, uint64_t* e, orc_mc* m) {
+    const orc_grid* g = A->g;
+    orc_idx_of(g, c, m->idx);
+    for (int q = 0; q < 3; ++q) m->r[q] = 0.0;
+    if (face >= 0) {
+        int ax = face / 2, side = (face & 1) ? 1 : -1;
+        int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+        m->r[ax] = -g->R + (m->idx[ax] + (side > 0 ? 1 : 0)) * orc_dz(g, ax);
+        double p1 = orc_ev(A, pk, e), p2 = orc_ev(A, pk, e);
+        if (t1 < g->ndim) m->r[t1] = -g->R + (m->idx[t1] + p1) * orc_dz(g, t1);
+        if (t2 < g->ndim) m->r[t2] = -g->R + (m->idx[t2] + p2) * orc_dz(g, t2);
+        orc_half_dir(A, pk, e, ax, side, m->n);
+    } else {
+        double p[3] = {orc_ev(A, pk, e), orc_ev(A, pk, e), orc_ev(A, pk, e)};
+        for (int ax = 0; ax < g->ndim; ++ax) m->r[ax] = -g->R + (m->idx[ax] + p[ax]) * orc_dz(g, ax);
+        orc_iso_dir(A, pk, e, m->n);
+    }
+    m->x = g->edges[j] + orc_ev(A, pk, e) * (g->edges[j + 1] - g->edges[j]);
+}
+
 /* Per-packet state of the walk. */
 typedef struct orc_pstate {
     int idx[3];
@@ -484,10 +764,24 @@ static void orc_advance(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t l
     const orc_grid* g = A->g;
     const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim;
     int64_t c = orc_cell_of(g, P->idx);
+    if (A->flags[c * J + P->j] & ORC_FLAG_THIN) {
+        /* only a source state can be thin: the packet starts as MC */
+        if (!A->upar) { A->status = -2; t[ORC_T_ABORTED]++; P->done = 3; return; }
+        orc_mc m;
+        t[ORC_T_CONVERSIONS]++;
+        orc_handoff(A, c, P->j, -1, pk, &P->e, &m);
+        int64_t cn;
+        int jn;
+        int rc = orc_mc_run(A, &m, pk, &P->e, t, &cn, &jn);
+        if (rc == 1) { P->done = 1; return; }
+        if (rc == 3) { t[ORC_T_ABORTED]++; P->done = 2; return; }
+        orc_idx_of(g, cn, P->idx);
+        P->j = jn;
+        c = cn;
+    }
     for (uint64_t n = 0; n < limit; ++n) {
         if (P->steps >= A->max_steps) { t[ORC_T_ABORTED]++; P->done = 2; return; }
         const int64_t s = c * J + P->j;
-        if (A->flags[s] & ORC_FLAG_THIN) { A->status = -2; t[ORC_T_ABORTED]++; P->done = 3; return; }
         int o;
         if (!A->literal) {
             /* categorical draw: outcome o iff thr[o-1] <= w < thr[o] */
@@ -510,7 +804,25 @@ static void orc_advance(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t l
         t[ORC_T_STEPS]++;
         unsigned act = (A->flags[s] >> (2 * o)) & 3u;
         if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, P->j, o, pk, &P->e, t); P->done = 1; return; }
-        if (act == ORC_ACT_TO_MC) { A->status = -2; t[ORC_T_ABORTED]++; P->done = 3; return; }
+        if (act == ORC_ACT_TO_MC) {
+            if (!A->upar) { A->status = -2; t[ORC_T_ABORTED]++; P->done = 3; return; }
+            orc_mc m;
+            t[ORC_T_CONVERSIONS]++;
+            int64_t cn; int jn, rc;
+            if (o < 2) {
+                orc_handoff(A, c, P->j + (o ? 1 : -1), -1, pk, &P->e, &m);
+                rc = orc_mc_run(A, &m, pk, &P->e, t, &cn, &jn);
+            } else {
+                orc_handoff(A, c, P->j, o - 2, pk, &P->e, &m);
+                int face = o - 2;
+                rc = orc_mc_cross(A, &m, face / 2, (face & 1) ? 1 : -1, pk, &P->e, t, &cn, &jn);
+                if (rc == 0) rc = orc_mc_run(A, &m, pk, &P->e, t, &cn, &jn);
+            }
+            if (rc == 1) { P->done = 1; return; }
+            if (rc == 3) { t[ORC_T_ABORTED]++; P->done = 2; return; }
+            orc_idx_of(g, cn, P->idx); P->j = jn; c = cn;
+            continue;
+        }
         if (o < 2) { P->j += o ? 1 : -1; continue; }
         int face = o - 2, ax = face / 2, side = (face & 1) ? 1 : -1;
         if (act == ORC_ACT_REBIN) {
@@ -556,9 +868,15 @@ static void* orc_walk_thread(void* vp) {
  * walk is orc_hybrid_walk_slab.
  */
 static int orc_walk_run(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
-                        const uint32_t* rebin_thr, const double* rate, double x0, uint64_t seed, uint64_t p0,
-                        uint64_t np, uint64_t max_steps, int literal, uint64_t limit, int nthreads,
+                        const uint32_t* rebin_thr, const double* rate, const double* k, double x0, uint64_t seed,
+                        uint64_t p0, uint64_t np, uint64_t max_steps, int literal, uint64_t limit, int nthreads,
                         uint64_t* tally) {
+    double* upar = NULL;
+    if (g->hybrid) {
+        if (!k) return -1;
+        upar = (double*)malloc(sizeof(double) * 2 * ORC_UPAR_N);
+        orc_upar_table(orc_damping(g->T), upar);
+    }
     orc_source src;
     if (orc_make_source(g, x0, &src)) return -1;
     if (literal && !rate) return -1;
@@ -573,6 +891,8 @@ static int orc_walk_run(const orc_grid* g, const uint32_t* thr, const uint32_t* 
         A->g = g; A->thr = thr; A->flags = flags; A->rebin_m = rebin_m; A->rebin_thr = rebin_thr;
         A->rate = rate; A->src = &src; A->seed = seed; A->max_steps = max_steps; A->literal = literal;
         A->limit = limit;
+        A->k = k;
+        A->upar = upar;
         A->p0 = p0 + np * (uint64_t)i / nthreads;
         A->p1 = p0 + np * (uint64_t)(i + 1) / nthreads;
         A->tally = tl + (size_t)i * L;
@@ -585,24 +905,24 @@ static int orc_walk_run(const orc_grid* g, const uint32_t* thr, const uint32_t* 
         for (int q = 0; q < L; ++q) tally[q] += tl[(size_t)i * L + q];
         if (args[i].status) status = args[i].status;
     }
-    free(th); free(args); free(tl);
+    free(th); free(args); free(tl); free(upar);
     return status;
 }
 
 int orc_walk_ddmc(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
-                  const uint32_t* rebin_thr, const double* rate, double x0, uint64_t seed, uint64_t p0,
-                  uint64_t np, uint64_t max_steps, int literal, int nthreads, uint64_t* tally) {
-    return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, rate, x0, seed, p0, np, max_steps, literal, UINT64_MAX,
-                        nthreads, tally);
+                  const uint32_t* rebin_thr, const double* rate, const double* k, double x0, uint64_t seed,
+                  uint64_t p0, uint64_t np, uint64_t max_steps, int literal, int nthreads, uint64_t* tally) {
+    return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, rate, k, x0, seed, p0, np, max_steps, literal,
+                        UINT64_MAX, nthreads, tally);
 }
 
 /* Start packets [p0, p0+np) at the source and advance each by at most
  * n_trans transitions (a bounded slice of the walk, as one time slice of the
  * GPU walk does); the tallies count what happened within the slice. */
 int orc_walk_slice(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
-                   const uint32_t* rebin_thr, double x0, uint64_t seed, uint64_t p0, uint64_t np,
+                   const uint32_t* rebin_thr, const double* k, double x0, uint64_t seed, uint64_t p0, uint64_t np,
                    uint64_t n_trans, int nthreads, uint64_t* tally) {
-    return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, NULL, x0, seed, p0, np, (uint64_t)1 << 62, 0, n_trans,
+    return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, NULL, k, x0, seed, p0, np, (uint64_t)1 << 62, 0, n_trans,
                         nthreads, tally);
 }
 
@@ -612,14 +932,21 @@ int orc_walk_slice(const orc_grid* g, const uint32_t* thr, const uint32_t* flags
  * tallies to tally (orc_tally_len(J) words, overwritten).
  */
 int orc_replay_packet(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
-                      const uint32_t* rebin_thr, double x0, uint64_t seed, uint64_t pk, uint64_t n_trans,
-                      uint64_t max_steps, uint64_t* out, uint64_t* tally) {
+                      const uint32_t* rebin_thr, const double* k, double x0, uint64_t seed, uint64_t pk,
+                      uint64_t n_trans, uint64_t max_steps, uint64_t* out, uint64_t* tally) {
     orc_source src;
     if (orc_make_source(g, x0, &src)) return -1;
     orc_walk_args A;
     memset(&A, 0, sizeof(A));
     A.g = g; A.thr = thr; A.flags = flags; A.rebin_m = rebin_m; A.rebin_thr = rebin_thr; A.src = &src;
-    A.seed = seed; A.max_steps = max_steps;
+    A.seed = seed; A.max_steps = max_steps; A.k = k;
+    double* upar = NULL;
+    if (g->hybrid) {
+        if (!k) return -1;
+        upar = (double*)malloc(sizeof(double) * 2 * ORC_UPAR_N);
+        orc_upar_table(orc_damping(g->T), upar);
+    }
+    A.upar = upar;
     memset(tally, 0, sizeof(uint64_t) * orc_tally_len(g->J));
     orc_pstate P;
     orc_start(&A, pk, &P, tally);
@@ -630,5 +957,25 @@ int orc_replay_packet(const orc_grid* g, const uint32_t* thr, const uint32_t* fl
     out[2] = P.steps;
     out[3] = P.e;
     out[4] = (uint64_t)P.done;
+    free(upar);
     return A.status;
+}
+
+/* Outgoing frequencies of n independent scatterings of a photon at x_in with
+ * incoming direction +e_z (isotropic phase function, no recoil); sample i uses
+ * the event stream of packet i.  Their density is R_II-A(x_out, x_in). */
+void orc_scatter_samples(double T, double x_in, uint64_t seed, uint64_t n, double* out) {
+    orc_walk_args A;
+    memset(&A, 0, sizeof(A));
+    A.seed = seed;
+    double* upar = (double*)malloc(sizeof(double) * 2 * ORC_UPAR_N);
+    const double a = orc_damping(T);
+    orc_upar_table(a, upar);
+    A.upar = upar;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t e = 0;
+        double d[3] = {0.0, 0.0, 1.0};
+        out[i] = orc_scatter(&A, a, x_in, d, i, &e);
+    }
+    free(upar);
 }
