@@ -237,8 +237,17 @@ int rddmc_reset_tallies(const rddmc_grid* grid, void* d_tallies, size_t tally_by
  *   d_state    device scratch of sizes.state_bytes for opts->n_packets,
  *              256-byte aligned: packet cursor and per-packet saved state.
  *   d_tallies  device tally buffer.
- * Errors: RDDMC_ERR_ARG, RDDMC_ERR_SIZE, RDDMC_ERR_UNSUPPORTED (hybrid mode,
- * not yet implemented), RDDMC_ERR_TABLE, RDDMC_ERR_CUDA.  Device-side conditions (watchdog
+ * Hybrid mode (RDDMC_MODE_HYBRID, Sec. 5.1-5.2): a leak into a thin neighbour
+ * hands the packet to continuous MC at a random point of the face with an
+ * isotropic outward direction, a leak into a thin bin at a random point of the
+ * cell with an isotropic direction (x uniform in the bin in both cases).  MC
+ * packets (FP32) fly with k = k0 H(a,x), scatter coherently in the atom frame
+ * (isotropic phase function, no recoil), convert back to DDMC after scattering
+ * into a thick bin, and at a face into a thick neighbour convert with
+ * probability 2/(tau + 2 lambda) (2/3 + mu) or reflect.  MC events do not count
+ * against steps_per_launch; max_steps (1e8 when 0) bounds the events of one MC
+ * excursion.
+ * Errors: RDDMC_ERR_ARG, RDDMC_ERR_SIZE, RDDMC_ERR_TABLE, RDDMC_ERR_CUDA.  Device-side conditions (watchdog
  * aborts) are reported by rddmc_read_tallies.
  */
 int rddmc_launch_packets(const rddmc_grid* grid, const void* d_table, const rddmc_run_opts* opts,
@@ -288,6 +297,18 @@ int rddmc_table_rows(const rddmc_grid* grid, const void* d_table, uint32_t* thr,
 int rddmc_read_packet_states(const rddmc_grid* grid, const void* d_state, uint64_t n_packets, uint64_t first,
                              uint64_t count, uint32_t* cell, uint32_t* bin, uint64_t* steps, uint64_t* event_draws,
                              uint8_t* status, void* stream);
+
+/*
+ * rddmc_scatter_samples -- run the walk's FP32 scattering sampler n times at
+ * the incoming frequency x_in (incoming direction +z; sample i uses the event
+ * stream of packet i under `seed`) and write the outgoing frequencies to
+ * d_out (device, n floats).  Their density is the angle-averaged
+ * redistribution function R_II-A(x, x_in) of Appendix A.  For checking the
+ * sampler; the table must be precomputed (the sampler's envelope table lives
+ * there).
+ */
+int rddmc_scatter_samples(const rddmc_grid* grid, const void* d_table, double x_in, uint64_t seed, uint64_t n,
+                          float* d_out, void* stream);
 
 /*
  * rddmc_launch_packets_noalloc -- rddmc_launch_packets for callers that cannot

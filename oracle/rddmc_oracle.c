@@ -685,13 +685,15 @@ static int orc_mc_cross(orc_walk_args* A, orc_mc* m, int ax, int side, uint64_t 
 }
 
 /* Run an MC packet until it converts to DDMC (returns 2, state in *cell_out,
- * *bin_out), escapes (1) or meets the event watchdog (3). */
+ * *bin_out), escapes (1) or meets the event watchdog (3): at most
+ * min(max_steps, 1e8) events per excursion. */
 static int orc_mc_run(orc_walk_args* A, orc_mc* m, uint64_t pk, uint64_t* e, uint64_t* t, int64_t* cell_out,
                       int* bin_out) {
     const orc_grid* g = A->g;
     const double a = orc_damping(g->T);
+    const uint64_t cap = A->max_steps < (uint64_t)100000000 ? A->max_steps : (uint64_t)100000000;
     for (uint64_t ev = 0;; ++ev) {
-        if (ev >= A->max_steps) return 3;
+        if (ev >= cap) return 3;
         int64_t c = orc_cell_of(g, m->idx);
         double k = orc_k0(g, c) * orc_voigt_H(a, m->x);
         double s = -log(orc_ev(A, pk, e)) / k;

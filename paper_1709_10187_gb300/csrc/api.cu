@@ -204,6 +204,8 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
     g->off_phi = off; off += align256((uint64_t)J * 8);
     g->off_rows = off; off += align256((uint64_t)g->n_class * J * g->row_bytes);
     g->off_fast = off; off += align256((uint64_t)g->n_class * J * 8);
+    g->off_tau = off; off += align256((uint64_t)g->n_class * J * 4);
+    g->off_upar = off; off += align256((uint64_t)kUparN * 8);
     g->table_bytes = off;
     *out = g;
     return RDDMC_OK;
@@ -278,6 +280,7 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
     h.mode = p->mode;
     h.off_class = g->off_class; h.off_cdesc = g->off_cdesc; h.off_rebin = g->off_rebin; h.off_vel = g->off_vel;
     h.off_edges = g->off_edges; h.off_phi = g->off_phi; h.off_rows = g->off_rows; h.off_fast = g->off_fast;
+    h.off_tau = g->off_tau; h.off_upar = g->off_upar;
     h.total = g->table_bytes;
     h.tau_ddmc = p->tau_ddmc; h.lambda = p->lambda; h.f_mu = p->f_mu; h.a = g->a; h.vth = g->vth;
 
@@ -326,7 +329,6 @@ int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_r
     if (o->resume != 0 && o->resume != 1) return RDDMC_ERR_ARG;
     if (state_bytes < state_bytes_for(o->n_packets)) return RDDMC_ERR_SIZE;
     if (tally_bytes < tally_bytes_for(g->J)) return RDDMC_ERR_SIZE;
-    if (g->params.mode == RDDMC_MODE_HYBRID) return RDDMC_ERR_UNSUPPORTED;
     WalkLaunch w{d_table, d_state, (unsigned long long*)d_tallies, *o};
     return cuda_status(launch_walk(*g, w, (cudaStream_t)stream));
 }
@@ -410,6 +412,13 @@ int rddmc_read_packet_states(const rddmc_grid* g, const void* d_state, uint64_t 
     if (status && e == cudaSuccess) e = cudaMemcpyAsync(status, sb + o_st + first, count, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+}
+
+int rddmc_scatter_samples(const rddmc_grid* g, const void* d_table, double x_in, uint64_t seed, uint64_t n,
+                          float* d_out, void* stream) {
+    if (!g || !d_table || !d_out || n == 0 || !std::isfinite(x_in)) return RDDMC_ERR_ARG;
+    if (!g->precomputed) return RDDMC_ERR_TABLE;
+    return cuda_status(launch_scatter_samples(*g, d_table, x_in, seed, n, d_out, (cudaStream_t)stream));
 }
 
 }  // extern "C"

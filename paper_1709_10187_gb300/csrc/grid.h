@@ -33,7 +33,7 @@ struct rddmc_grid {
     int src_bin[2] = {0, 0};
     // table layout (byte offsets)
     uint64_t off_class = 0, off_cdesc = 0, off_rebin = 0, off_vel = 0, off_edges = 0, off_phi = 0,
-             off_rows = 0, off_fast = 0, table_bytes = 0;
+             off_rows = 0, off_fast = 0, off_tau = 0, off_upar = 0, table_bytes = 0;
     // leakage parameters of the last precompute
     rddmc_leak_params params{};
     bool precomputed = false;
@@ -59,6 +59,8 @@ struct WalkLaunch {
     rddmc_run_opts opts;
 };
 cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s);
+cudaError_t launch_scatter_samples(const rddmc_grid& g, const void* d_table, double x_in, uint64_t seed, uint64_t n,
+                                   float* d_out, cudaStream_t s);
 
 uint64_t state_bytes_for(uint64_t n_packets);
 uint64_t tally_bytes_for(int J);

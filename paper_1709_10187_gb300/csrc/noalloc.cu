@@ -59,7 +59,6 @@ extern "C" int rddmc_launch_packets_noalloc(const rddmc_grid* g, const void* d_t
     if (o->threads_per_cta && (o->threads_per_cta % 32 != 0 || o->threads_per_cta > 256)) return RDDMC_ERR_ARG;
     if (o->resume != 0 && o->resume != 1) return RDDMC_ERR_ARG;
     if (tally_bytes < rddmc::tally_bytes_for(g->J)) return RDDMC_ERR_SIZE;
-    if (g->params.mode == RDDMC_MODE_HYBRID) return RDDMC_ERR_UNSUPPORTED;
     // A run to completion only uses the packet cursor; time-sliced or resumed
     // runs keep every packet's state in the array, which bounds their packet
     // count (about 1.3 million packets).

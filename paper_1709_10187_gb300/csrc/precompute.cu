@@ -34,7 +34,8 @@ __device__ __forceinline__ uint32_t quantise_dev(double C) {
 template <int NDIM>
 __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ cdesc,
                             const double* __restrict__ edges, const double* __restrict__ phi,
-                            uint32_t* __restrict__ rows, uint2* __restrict__ fast, int64_t nrow) {
+                            uint32_t* __restrict__ rows, uint2* __restrict__ fast, float* __restrict__ tau_row,
+                            int64_t nrow) {
     constexpr int K = 2 + 2 * NDIM;
     constexpr int W = NDIM == 1 ? 4 : 8;  // words per row, the last holding the flags
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,6 +102,7 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
     // word order: thr0, thr1, thr2, flags[, thr3..thr6] so that the first 16
     // bytes carry everything a frequency move needs
     fast[r] = make_uint2(out[0], (fl & FLAG_FASTX) ? out[1] : 0u);
+    tau_row[r] = (float)(k * dzmin);
     if (NDIM == 1) {
         reinterpret_cast<uint4*>(rows)[r] = make_uint4(out[0], out[1], out[2], fl);
     } else {
@@ -108,6 +110,34 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
         p[0] = make_uint4(out[0], out[1], out[2], fl);
         p[1] = make_uint4(out[3], out[4], out[5], out[6]);
     }
+}
+
+// Split points (u1, u0) of the three-part rejection envelope of the parallel
+// atom velocity, f(u) = e^{-u^2} / (a^2 + (x-u)^2) (Sec. 5.2), for |x| = i/16:
+//   u < u1: e^{-u^2} g(u1);  u1 <= u <= u0: c g(u), c = max e^{-u^2} on [u1,u0];
+//   u > u0: e^{-u0^2} g(u),  g(u) = 1/(a^2 + (x-u)^2),  u1 <= u0 <= x, u0 >= 0.
+// Each piece bounds f, so any such pair samples f exactly; the pair with the
+// smallest envelope mass on a grid of candidates gives the best acceptance.
+__global__ void upar_kernel(float2* __restrict__ tab, double a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kUparN) return;
+    const double x = (double)i / 16.0;
+    double best = 1e300, b1 = -30.0, b0 = 0.0;
+    for (int p = 0; p <= 32; ++p) {
+        const double u0 = x * p / 32.0;
+        const double th0 = atan((u0 - x) / a);
+        const double m3 = exp(-u0 * u0) * (1.5707963267948966 - th0) / a;
+        for (int q = 0; q <= 33; ++q) {
+            const double u1 = (q == 33) ? -30.0 : -4.0 + (u0 + 4.0) * q / 32.0;
+            const double g1 = 1.0 / (a * a + (x - u1) * (x - u1));
+            const double m1 = g1 * 0.88622692545275801365 * (1.0 + erf(u1));
+            const double c = u1 <= 0.0 ? 1.0 : exp(-u1 * u1);
+            const double m2 = c * (th0 - atan((u1 - x) / a)) / a;
+            const double m = m1 + m2 + m3;
+            if (m < best) { best = m; b1 = u1; b0 = u0; }
+        }
+    }
+    tab[i] = make_float2((float)b1, (float)fmin(b0, x));
 }
 
 }  // namespace
@@ -134,10 +164,13 @@ cudaError_t launch_precompute(const rddmc_grid& g, void* d_table, cudaStream_t s
     const ClassDesc* cd = (const ClassDesc*)(base + g.off_cdesc);
     uint32_t* rows = (uint32_t*)(base + g.off_rows);
     uint2* fast = (uint2*)(base + g.off_fast);
+    float* tau_row = (float*)(base + g.off_tau);
     if (g.ndim == 1)
-        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, nrow);
+        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, nrow);
     else
-        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, nrow);
+        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, nrow);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    upar_kernel<<<(kUparN + 127) / 128, 128, 0, s>>>((float2*)(base + g.off_upar), g.a);
     return cudaGetLastError();
 }
 

@@ -3,7 +3,7 @@
 // Device table buffer (caller-owned, filled by rddmc_precompute_leakage):
 //   [TableHeader | cell_class u32[ncell] | ClassDesc[n_class] | Rebin[n_class*nfaces]
 //    | cell velocity f64[3*ncell] (moving media only) | edges f64[J+1] | phi f64[J] | rows
-//    | fast heads uint2[n_class*J]]
+//    | fast heads uint2[n_class*J] | tau f32[n_class*J] | u_par split points f32x2[kUparN]]
 // every region 256-byte aligned.  Rows are n_class blocks of J rows; a row is
 // 16 bytes in a slab {thr0, thr1, thr2, flags} and 32 bytes in 3D
 // {thr0, thr1, thr2, flags, thr3, thr4, thr5, thr6}: the first 16 bytes always
@@ -30,6 +30,8 @@ constexpr int kFaceOff = 16;
 constexpr int kHistOff = 22;
 constexpr int kNsb = 64;            // impact-parameter bins over b/R in [0, kSbMax)
 constexpr double kSbMax = 1.28;
+constexpr int kUparN = 1024;        // |x| grid of the u_par envelope split points
+constexpr float kUparStep = 1.0f / 16.0f;
 
 enum Counter : int {
     C_EMITTED = 0, C_ESCAPED = 1, C_ABORTED = 2, C_STEPS = 3, C_MC_EVENTS = 4,
@@ -71,7 +73,8 @@ struct TableHeader {
     uint32_t filled;
     int32_t ndim, J, ncell, n_class, K, row_bytes;
     int32_t n[3], mode;
-    uint64_t off_class, off_cdesc, off_rebin, off_vel, off_edges, off_phi, off_rows, off_fast, total;
+    uint64_t off_class, off_cdesc, off_rebin, off_vel, off_edges, off_phi, off_rows, off_fast, off_tau, off_upar,
+        total;
     double tau_ddmc, lambda, f_mu, a, dz[3], vth;
 };
 

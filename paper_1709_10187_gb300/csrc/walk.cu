@@ -25,6 +25,7 @@
 #include <cstring>
 
 #include "grid.h"
+#include "mc.cuh"
 
 namespace rddmc {
 namespace {
@@ -39,6 +40,9 @@ constexpr int kSmemHistMax = 8192;  // histogram entries kept in shared memory
 struct WalkParams {
     const uint4* rows;
     const uint2* fast;
+    const float* tau_row;     // tau_ij = k_ij dz per row (hybrid conversions)
+    const float2* upar;       // u_par envelope split points
+    const ClassDesc* cdesc;
     const uint32_t* cell_class;
     const Rebin* rebin;
     const double* cell_v;     // km/s, 3 per cell (moving media)
@@ -50,13 +54,15 @@ struct WalkParams {
     unsigned long long* st_e;
     uint8_t* st_status;
     unsigned long long* tally;
-    unsigned long long n_packets, max_steps, slice;
+    unsigned long long n_packets, max_steps, slice, mc_cap;
     uint32_t k0, k1;
     uint32_t rk0[10], rk1[10];  // Philox round keys k + r * (Weyl constant)
     int J, n_rows, n_class, ncell, chunk;
     int n0, n01;
     double R, dz[3], vth;
-    int resume, save_state, hist_in_smem, moving;
+    int resume, save_state, hist_in_smem, moving, hybrid;
+    int n[3];
+    float a, lambda;
     int src_ncand[3], src_cand[3][2], src_nbin, src_bin[2];
 };
 
@@ -151,7 +157,196 @@ __device__ __noinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cel
     return out;
 }
 
-template <int NDIM, bool SMEM_ROWS>
+
+// ---------------------------------------------------------------- hybrid MC
+// Continuous MC of a packet in thin states (Sec. 5.1, Sec. 5.2), in FP32.  It
+// runs from a DDMC hand-off until the packet converts back to DDMC, escapes or
+// meets the event watchdog; time slices only count DDMC transitions, so an
+// excursion always finishes within the transition that started it.
+struct McResult {
+    int status;            // 0 back to DDMC at (cell, bin), 1 escaped, 2 aborted
+    unsigned cell, bin;
+    int hist, sb, face;    // escape tallies
+};
+
+struct McPacket {
+    int idx[3];
+    unsigned cell;
+    float r[3], n[3], x;
+};
+
+__device__ __forceinline__ int bin_of(const WalkParams& P, float xf) {
+    const double x = (double)xf;
+    if (x < P.edges[0]) return -1;
+    if (x >= P.edges[P.J]) return P.J;
+    int lo = 0, hi = P.J;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (x >= P.edges[mid]) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int NDIM>
+__device__ __forceinline__ bool thick_state(const WalkParams& P, unsigned cell, int j) {
+    if (j < 0 || j >= P.J) return false;
+    const unsigned cls = min(__ldg(&P.cell_class[min(cell, (unsigned)P.ncell - 1u)]), (unsigned)P.n_class - 1u);
+    const uint4 a = __ldg(&P.rows[(cls * (unsigned)P.J + (unsigned)j) * (NDIM == 1 ? 1u : 2u)]);
+    return (a.w & FLAG_THIN) == 0u;
+}
+
+__device__ __forceinline__ float cell_u(const WalkParams& P, unsigned cell, int a) {
+    return P.moving ? (float)(P.cell_v[3ull * cell + a] / P.vth) : 0.0f;
+}
+
+template <int NDIM>
+__device__ __forceinline__ float face_coord(const WalkParams& P, int ax, int i) {
+    return (float)(-P.R + (double)i * P.dz[ax]);
+}
+
+template <int NDIM>
+__device__ void mc_escape_bins(const WalkParams& P, const McPacket& m, int ax, int side, McResult& res) {
+    const float xo = m.x + m.n[0] * cell_u(P, m.cell, 0) + m.n[1] * cell_u(P, m.cell, 1) +
+                     m.n[2] * cell_u(P, m.cell, 2);
+    const int b = bin_of(P, xo);
+    res.status = 1;
+    res.hist = b < 0 ? 0 : (b >= P.J ? P.J + 1 : b + 1);
+    res.face = 2 * ax + (side > 0 ? 1 : 0);
+    res.sb = -1;
+    if (NDIM == 3) {
+        const float rr = m.r[0] * m.r[0] + m.r[1] * m.r[1] + m.r[2] * m.r[2];
+        const float rn = m.r[0] * m.n[0] + m.r[1] * m.n[1] + m.r[2] * m.n[2];
+        const float b2 = sqrtf(fmaxf(0.0f, rr - rn * rn)) / (float)P.R;
+        res.sb = min((int)(b2 / (float)kSbMax * kNsb), kNsb - 1);
+    }
+}
+
+// Cross from m's cell through face (ax, side): escape, continue into a thin
+// neighbour, convert into a thick neighbour with probability
+// 2/(tau + 2 lambda) (2/3 + mu), or reflect (random point on the face,
+// isotropic inward direction; a reflection into a thick state converts).
+// Returns true when the excursion ends (res filled).
+template <int NDIM>
+__device__ bool mc_cross(const WalkParams& P, McPacket& m, int ax, int side, EventStream& es, unsigned& n_conv,
+                         McResult& res) {
+    int nidx[3] = {m.idx[0], m.idx[1], m.idx[2]};
+    nidx[ax] += side;
+    bool inside = nidx[ax] >= 0 && nidx[ax] < P.n[ax];
+    unsigned nb = 0;
+    if (inside) {
+        nb = (unsigned)nidx[0] + (unsigned)P.n0 * (unsigned)nidx[1] + (unsigned)P.n01 * (unsigned)nidx[2];
+        inside = __ldg(&P.cell_class[min(nb, (unsigned)P.ncell - 1u)]) != 0xffffffffu;
+    }
+    if (!inside) { mc_escape_bins<NDIM>(P, m, ax, side, res); return true; }
+    float xn = m.x;
+    if (P.moving)
+        xn += m.n[0] * (cell_u(P, m.cell, 0) - cell_u(P, nb, 0)) + m.n[1] * (cell_u(P, m.cell, 1) - cell_u(P, nb, 1)) +
+              m.n[2] * (cell_u(P, m.cell, 2) - cell_u(P, nb, 2));
+    const int jn = bin_of(P, xn);
+    if (!thick_state<NDIM>(P, nb, jn)) {
+        m.idx[ax] = nidx[ax];
+        m.cell = nb;
+        m.x = xn;
+        return false;
+    }
+    const unsigned clsn = min(__ldg(&P.cell_class[nb]), (unsigned)P.n_class - 1u);
+    const float tau = P.tau_row[clsn * (unsigned)P.J + (unsigned)jn];
+    const float prob = 2.0f / (tau + 2.0f * P.lambda) * (0.6666667f + fabsf(m.n[ax]));
+    if (es.u01() < prob) {
+        ++n_conv;
+        res.status = 0; res.cell = nb; res.bin = (unsigned)jn;
+        return true;
+    }
+    const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+    const float p1 = es.u01(), p2 = es.u01();
+    if (t1 < NDIM) m.r[t1] = (float)(-P.R + ((double)m.idx[t1] + p1) * P.dz[t1]);
+    if (t2 < NDIM) m.r[t2] = (float)(-P.R + ((double)m.idx[t2] + p2) * P.dz[t2]);
+    half_dir(es, ax, -side, m.n);
+    const int j = bin_of(P, m.x);
+    if (thick_state<NDIM>(P, m.cell, j)) {
+        ++n_conv;
+        res.status = 0; res.cell = m.cell; res.bin = (unsigned)j;
+        return true;
+    }
+    return false;
+}
+
+// DDMC hand-off at (cell, bin) and the MC excursion that follows.  face >= 0:
+// a leak into a thin neighbour through that face (random point on the face,
+// isotropic outward direction, x uniform in bin, then the crossing); face < 0:
+// a leak into the thin bin `bin` of the same cell, or a thin source state
+// (random point in the cell, isotropic direction, x uniform in bin).
+template <int NDIM>
+__device__ __noinline__ McResult mc_excursion(const WalkParams& P, unsigned cell, unsigned bin, int face,
+                                              unsigned long long pid, unsigned long long& e,
+                                              unsigned long long& n_mc, unsigned& n_conv) {
+    EventStream es;
+    es.init(pid, e, P.k0, P.k1);
+    McPacket m;
+    m.cell = cell;
+    m.idx[0] = (int)(cell % (unsigned)P.n0);
+    m.idx[1] = NDIM == 3 ? (int)((cell / (unsigned)P.n0) % (unsigned)P.n[1]) : 0;
+    m.idx[2] = NDIM == 3 ? (int)(cell / (unsigned)P.n01) : 0;
+    m.r[0] = m.r[1] = m.r[2] = 0.0f;
+    McResult res;
+    res.status = 2; res.cell = cell; res.bin = bin; res.hist = 0; res.sb = -1; res.face = 0;
+    ++n_conv;
+    bool done = false;
+    if (face >= 0) {
+        const int ax = face >> 1, side = (face & 1) ? 1 : -1;
+        const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+        m.r[ax] = face_coord<NDIM>(P, ax, m.idx[ax] + (side > 0 ? 1 : 0));
+        const float p1 = es.u01(), p2 = es.u01();
+        if (t1 < NDIM) m.r[t1] = (float)(-P.R + ((double)m.idx[t1] + p1) * P.dz[t1]);
+        if (t2 < NDIM) m.r[t2] = (float)(-P.R + ((double)m.idx[t2] + p2) * P.dz[t2]);
+        half_dir(es, ax, side, m.n);
+        m.x = (float)(P.edges[bin] + (double)es.u01() * (P.edges[bin + 1] - P.edges[bin]));
+        done = mc_cross<NDIM>(P, m, ax, side, es, n_conv, res);
+    } else {
+        const float p0 = es.u01(), p1 = es.u01(), p2 = es.u01();
+        const float pp[3] = {p0, p1, p2};
+        for (int ax = 0; ax < NDIM; ++ax) m.r[ax] = (float)(-P.R + ((double)m.idx[ax] + pp[ax]) * P.dz[ax]);
+        iso_dir(es, m.n);
+        m.x = (float)(P.edges[bin] + (double)es.u01() * (P.edges[bin + 1] - P.edges[bin]));
+    }
+    for (unsigned long long ev = 0; !done; ++ev) {
+        if (ev >= P.mc_cap) { res.status = 2; break; }
+        const unsigned cls = min(__ldg(&P.cell_class[min(m.cell, (unsigned)P.ncell - 1u)]), (unsigned)P.n_class - 1u);
+        const float k = (float)P.cdesc[cls].k0 * voigt_H_f32(P.a, m.x);
+        const float sflight = -__logf(es.u01()) / k;
+        float dmin = 3.0e38f;
+        int fax = 0, fside = 1;
+#pragma unroll
+        for (int ax = 0; ax < NDIM; ++ax) {
+            if (m.n[ax] == 0.0f) continue;
+            const float lo = face_coord<NDIM>(P, ax, m.idx[ax]), hi = face_coord<NDIM>(P, ax, m.idx[ax] + 1);
+            float d = m.n[ax] > 0.0f ? (hi - m.r[ax]) / m.n[ax] : (lo - m.r[ax]) / m.n[ax];
+            d = fmaxf(d, 0.0f);
+            if (d < dmin) { dmin = d; fax = ax; fside = m.n[ax] > 0.0f ? 1 : -1; }
+        }
+        ++n_mc;
+        if (sflight < dmin) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) m.r[q] += sflight * m.n[q];
+            m.x = scatter(P.a, m.x, m.n, P.upar, es);
+            const int j = bin_of(P, m.x);
+            if (thick_state<NDIM>(P, m.cell, j)) {
+                ++n_conv;
+                res.status = 0; res.cell = m.cell; res.bin = (unsigned)j;
+                break;
+            }
+            continue;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) m.r[q] += dmin * m.n[q];
+        m.r[fax] = face_coord<NDIM>(P, fax, m.idx[fax] + (fside > 0 ? 1 : 0));
+        done = mc_cross<NDIM>(P, m, fax, fside, es, n_conv, res);
+    }
+    e = es.e;
+    return res;
+}
+
+template <int NDIM, bool SMEM_ROWS, bool HYBRID>
 __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const WalkParams P) {
     constexpr int RW = NDIM == 1 ? 1 : 2;  // uint4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -177,8 +372,28 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
     bool have = false, exhausted = false;
     unsigned long long pid = 0, t = 0, e = 0, t_stop = 0;
     unsigned cell = 0, cls = 0, s = 0;  // s = cls * J + bin: the row of the state
-    unsigned long long n_steps = 0, n_edraw = 0;
-    unsigned n_emit = 0, n_esc = 0, n_abort = 0, n_clamp = 0, status_bits = 0;
+    unsigned long long n_steps = 0, n_edraw = 0, n_mc = 0;
+    unsigned n_emit = 0, n_esc = 0, n_abort = 0, n_clamp = 0, status_bits = 0, n_conv = 0;
+
+    // Outcome of an MC excursion: back to DDMC (returns false) or finished.
+    auto after_mc = [&](const McResult& res) -> bool {
+        if (res.status == 0) {
+            cell = res.cell;
+            cls = __ldg(&P.cell_class[min(cell, (unsigned)P.ncell - 1u)]);
+            s = cls * J + min(res.bin, J - 1u);
+            return false;
+        }
+        if (res.status == 1) {
+            if (P.hist_in_smem) smem_tally(s_hist, (unsigned)res.hist);
+            else atomicAdd(&P.tally[kHistOff + res.hist], 1ull);
+            if (res.sb >= 0) smem_tally(s_sb, (unsigned)res.sb);
+            smem_tally(s_face, (unsigned)res.face);
+            ++n_esc;
+            return true;
+        }
+        ++n_abort;
+        return true;
+    };
 
     // One full transition: every threshold, the outcome's action, spatial moves
     // with the class lookup, Doppler rebins and escapes.  Returns true when the
@@ -196,7 +411,10 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         const unsigned bin = min(s - cls * J, J - 1u);
         if (o < 2u) {
             if (act == ACT_MOVE) { s += o ? 1u : 0xffffffffu; return false; }
-            status_bits |= (unsigned)STATUS_UNSUPPORTED_EVENT;  // hand-off to MC: not in this walk
+            if (HYBRID && act == ACT_TO_MC)  // leak into a thin bin of this cell
+                return after_mc(mc_excursion<NDIM>(P, cell, o ? min(bin + 1u, J - 1u) : (bin ? bin - 1u : 0u), -1,
+                                                   pid, e, n_mc, n_conv));
+            status_bits |= (unsigned)STATUS_UNSUPPORTED_EVENT;
             ++n_abort;
             return true;
         }
@@ -212,6 +430,8 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
             return true;
         }
         if (act == ACT_TO_MC) {
+            if (HYBRID)  // leak into a thin neighbour cell
+                return after_mc(mc_excursion<NDIM>(P, cell, bin, (int)face, pid, e, n_mc, n_conv));
             status_bits |= (unsigned)STATUS_UNSUPPORTED_EVENT;
             ++n_abort;
             return true;
@@ -273,6 +493,17 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
                         cls = __ldg(&P.cell_class[cell]);
                         s = cls * J + min(bin, J - 1u);
                         t_stop = P.slice ? t + P.slice : ~0ull;
+                        if (HYBRID && st == PK_FRESH) {
+                            // a thin source state starts as MC
+                            const uint4 a0 = __ldg(&rows[min(s, nr1) * RW]);
+                            if (a0.w & FLAG_THIN) {
+                                const unsigned long long e0 = e;
+                                const McResult res = mc_excursion<NDIM>(P, cell, min(bin, J - 1u), -1, pid, e, n_mc,
+                                                                        n_conv);
+                                n_edraw += e - e0;
+                                if (after_mc(res)) have = false;
+                            }
+                        }
                     }
                 }
             }
@@ -357,9 +588,9 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
 
     // ---- flush: warp sums of the per-thread counters, then CTA totals to HBM
     n_edraw += n_emit;  // the source draw of each emitted packet
-    unsigned long long v[7] = {n_emit, n_esc, n_abort, n_steps, n_clamp, n_edraw, status_bits};
+    unsigned long long v[9] = {n_emit, n_esc, n_abort, n_steps, n_clamp, n_edraw, status_bits, n_mc, n_conv};
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < 9; ++i) {
         unsigned long long x = v[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
@@ -373,6 +604,8 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         atomicAdd(&s_cnt[C_CLAMPS], v[4]);
         atomicAdd(&s_cnt[C_EVENT_DRAWS], v[5]);
         if (v[6]) atomicOr(&s_cnt[C_STATUS_BITS], v[6]);
+        atomicAdd(&s_cnt[C_MC_EVENTS], v[7]);
+        atomicAdd(&s_cnt[C_CONVERSIONS], v[8]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kCounters; i += blockDim.x) {
@@ -389,21 +622,48 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         if (s_sb[i]) atomicAdd(&P.tally[kHistOff + nhist + i], s_sb[i]);
 }
 
-template <int NDIM, bool SMEM>
+template <int NDIM, bool SMEM, bool HYBRID>
 cudaError_t launch_variant(const WalkParams& P, int threads, size_t smem, int ctas, int nsm, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<NDIM, SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<NDIM, SMEM, HYBRID>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (!ctas) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, walk_kernel<NDIM, SMEM>, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, walk_kernel<NDIM, SMEM, HYBRID>, threads, smem);
         if (e != cudaSuccess) return e;
     }
     if (ctas < 1) ctas = 1;
-    walk_kernel<NDIM, SMEM><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P);
+    walk_kernel<NDIM, SMEM, HYBRID><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P);
     return cudaGetLastError();
 }
 
+template <int NDIM, bool SMEM>
+cudaError_t launch_mode(const WalkParams& P, int threads, size_t smem, int ctas, int nsm, cudaStream_t s) {
+    return P.hybrid ? launch_variant<NDIM, SMEM, true>(P, threads, smem, ctas, nsm, s)
+                    : launch_variant<NDIM, SMEM, false>(P, threads, smem, ctas, nsm, s);
+}
+
+// One scattering per thread at x_in with incoming direction +e_z; sample i
+// reads the event stream of packet i.
+__global__ void scatter_samples_kernel(float a, float x_in, const float2* __restrict__ upar, uint32_t k0,
+                                       uint32_t k1, unsigned long long n, float* __restrict__ out) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    EventStream es;
+    es.init(i, 0, k0, k1);
+    float d[3] = {0.0f, 0.0f, 1.0f};
+    out[i] = scatter(a, x_in, d, upar, es);
+}
+
 }  // namespace
+
+cudaError_t launch_scatter_samples(const rddmc_grid& g, const void* d_table, double x_in, uint64_t seed, uint64_t n,
+                                   float* d_out, cudaStream_t s) {
+    const float2* upar = (const float2*)((const char*)d_table + g.off_upar);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    scatter_samples_kernel<<<blocks, 256, 0, s>>>((float)g.a, (float)x_in, upar, (uint32_t)seed,
+                                                  (uint32_t)(seed >> 32), n, d_out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s) {
     const rddmc_run_opts& o = w.opts;
@@ -413,6 +673,13 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     std::memset(&P, 0, sizeof(P));
     P.rows = (const uint4*)(tb + g.off_rows);
     P.fast = (const uint2*)(tb + g.off_fast);
+    P.tau_row = (const float*)(tb + g.off_tau);
+    P.upar = (const float2*)(tb + g.off_upar);
+    P.cdesc = (const ClassDesc*)(tb + g.off_cdesc);
+    P.hybrid = g.params.mode == RDDMC_MODE_HYBRID ? 1 : 0;
+    P.a = (float)g.a;
+    P.lambda = (float)g.params.lambda;
+    for (int a = 0; a < 3; ++a) P.n[a] = g.n[a];
     P.cell_class = (const uint32_t*)(tb + g.off_class);
     P.rebin = (const Rebin*)(tb + g.off_rebin);
     P.cell_v = (const double*)(tb + g.off_vel);
@@ -428,6 +695,7 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     P.tally = w.d_tally;
     P.n_packets = np;
     P.max_steps = o.max_steps ? o.max_steps : (1ull << 62);
+    P.mc_cap = o.max_steps ? o.max_steps : 100000000ull;  // events per MC excursion
     P.slice = o.steps_per_launch;
     P.k0 = (uint32_t)o.seed;
     P.k1 = (uint32_t)(o.seed >> 32);
@@ -472,10 +740,10 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     if (use_smem_rows) smem += rows_bytes;
     if ((e = cudaMemsetAsync(P.cursor, 0, 8, s)) != cudaSuccess) return e;
     if (g.ndim == 1)
-        return use_smem_rows ? launch_variant<1, true>(P, threads, smem, o.ctas_per_sm, nsm, s)
-                             : launch_variant<1, false>(P, threads, smem, o.ctas_per_sm, nsm, s);
-    return use_smem_rows ? launch_variant<3, true>(P, threads, smem, o.ctas_per_sm, nsm, s)
-                         : launch_variant<3, false>(P, threads, smem, o.ctas_per_sm, nsm, s);
+        return use_smem_rows ? launch_mode<1, true>(P, threads, smem, o.ctas_per_sm, nsm, s)
+                             : launch_mode<1, false>(P, threads, smem, o.ctas_per_sm, nsm, s);
+    return use_smem_rows ? launch_mode<3, true>(P, threads, smem, o.ctas_per_sm, nsm, s)
+                         : launch_mode<3, false>(P, threads, smem, o.ctas_per_sm, nsm, s);
 }
 
 }  // namespace rddmc

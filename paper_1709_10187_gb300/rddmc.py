@@ -29,7 +29,8 @@ NSB = 64  # impact-parameter bins of the surface-brightness histogram
 
 EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc_precompute_leakage",
             "rddmc_reset_tallies", "rddmc_launch_packets", "rddmc_read_tallies", "rddmc_table_rows",
-            "rddmc_read_packet_states", "rddmc_launch_packets_noalloc", "rddmc_status_string", "rddmc_version"]
+            "rddmc_read_packet_states", "rddmc_launch_packets_noalloc", "rddmc_scatter_samples",
+            "rddmc_status_string", "rddmc_version"]
 
 
 class GridDesc(ctypes.Structure):
@@ -93,6 +94,7 @@ def lib():
         L.rddmc_table_rows.argtypes = [vp, vp, vp, vp, vp]
         L.rddmc_read_packet_states.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, vp, vp, vp]
         L.rddmc_launch_packets_noalloc.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp]
+        L.rddmc_scatter_samples.argtypes = [vp, vp, ctypes.c_double, u64, u64, vp, vp]
         L.rddmc_status_string.argtypes = [i32]
         L.rddmc_status_string.restype = ctypes.c_char_p
         L.rddmc_version.argtypes = []
@@ -172,6 +174,13 @@ def launch_packets_noalloc(grid, d_table: int, opts: RunOpts, d_tallies: int, ta
     _check("rddmc_launch_packets_noalloc", lib().rddmc_launch_packets_noalloc(
         ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(opts), ctypes.c_void_p(d_tallies),
         int(tally_bytes), ctypes.c_void_p(stream)))
+
+
+def scatter_samples(grid, d_table: int, x_in: float, seed: int, n: int, d_out: int, stream: int = 0):
+    """rddmc_scatter_samples: n outgoing frequencies of the device scattering sampler."""
+    _check("rddmc_scatter_samples", lib().rddmc_scatter_samples(
+        ctypes.c_void_p(grid), ctypes.c_void_p(d_table), float(x_in), int(seed), int(n), ctypes.c_void_p(d_out),
+        ctypes.c_void_p(stream)))
 
 
 def read_tallies(grid, d_tallies: int, J: int, nfaces: int, stream: int = 0) -> dict:
@@ -261,6 +270,11 @@ class Problem:
         self.reset()
         self.launch(n_packets, seed, **kw)
         return self.read()
+
+    def scatter(self, x_in: float, seed: int, n: int):
+        out = self.torch.empty(n, dtype=self.torch.float32, device=self.device)
+        scatter_samples(self.grid, self.table.data_ptr(), x_in, seed, n, out.data_ptr(), self.stream())
+        return out.cpu().numpy().astype(np.float64)
 
     def packet_states(self, n_packets: int, first: int, count: int) -> dict:
         return read_packet_states(self.grid, self.state.data_ptr(), n_packets, first, count, self.stream())

@@ -135,13 +135,6 @@ def test_ragged_packet_counts(npk):
     _same_tallies(R.Problem(w).run(npk, w.seed + npk), C.walk(og, ot, w.seed + npk, 0, npk))
 
 
-def test_hybrid_launch_reports_unsupported():
-    p = R.Problem(W.TINY, mode=R.MODE_HYBRID)
-    with pytest.raises(R.RDDMCError) as ei:
-        p.run(10, 1)
-    assert ei.value.status == R.ERR_UNSUPPORTED
-
-
 def test_spectrum_p1_matches_chain_and_neufeld():
     # Fig. 2 setup, 1e6 packets: 3 sigma against the exact chain; L1 <= 2% vs eq. Neufeld.
     w = W.P1
