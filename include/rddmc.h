@@ -298,6 +298,65 @@ int rddmc_read_packet_states(const rddmc_grid* grid, const void* d_state, uint64
                              uint64_t count, uint32_t* cell, uint32_t* bin, uint64_t* steps, uint64_t* event_draws,
                              uint8_t* status, void* stream);
 
+/* ----------------------------------------------------------------- batches
+ * Many independent grids ("instances", each built and precomputed as above,
+ * DDMC mode, any mix of slabs and 3D grids) walked by one persistent launch.
+ * Instance i owns global packet ids [off_i, off_i + n_i) with off_0 = 0 and
+ * off_{i+1} = off_i + n_i; its packet p uses the streams of global id off_i + p
+ * under the run's seed.  Each instance has its own tally block.
+ */
+typedef struct rddmc_batch rddmc_batch; /* opaque host handle */
+
+/* Describe a batch.  grids/d_tables/n_packets: n_inst entries each (host
+ * arrays; the grids and device tables must outlive the batch).  Errors:
+ * RDDMC_ERR_ARG, RDDMC_ERR_TABLE (a table not precomputed),
+ * RDDMC_ERR_UNSUPPORTED (hybrid-mode grid). */
+int rddmc_batch_create(const rddmc_grid* const* grids, const void* const* d_tables, const uint64_t* n_packets,
+                       int n_inst, rddmc_batch** out);
+void rddmc_batch_destroy(rddmc_batch* batch);
+
+/* Sizes of the caller buffers: descriptors (device, 256-byte aligned), tallies
+ * (device; instance blocks of the single-grid tally layout, back to back),
+ * scratch (device, packet cursor), and the total packet count.  Any pointer
+ * may be NULL. */
+int rddmc_batch_sizes(const rddmc_batch* batch, uint64_t* desc_bytes, uint64_t* tally_bytes,
+                      uint64_t* scratch_bytes, uint64_t* total_packets);
+
+/* Copy the instance descriptors to d_desc (synchronises `stream`).
+ * trial_fraction in (0, 1]: the share of each instance's packets (at least
+ * one) that trial launches run, for the autotuner. */
+int rddmc_batch_upload(rddmc_batch* batch, double trial_fraction, void* d_desc, size_t desc_bytes, void* stream);
+
+/* Enqueue one persistent launch over every instance (trial != 0: the trial
+ * subsets only).  Only a memset and a kernel launch are enqueued.  opts: seed,
+ * max_steps, ctas_per_sm, threads_per_cta, chunk (n_packets is ignored;
+ * steps_per_launch and resume must be 0).  Tallies accumulate into d_tallies. */
+int rddmc_batch_launch(const rddmc_batch* batch, const void* d_desc, const rddmc_run_opts* opts, int trial,
+                       void* d_scratch, size_t scratch_bytes, void* d_tallies, size_t tally_bytes, void* stream);
+
+/* Tallies of instance `inst` (as rddmc_read_tallies; synchronises). */
+int rddmc_batch_read_tallies(const rddmc_batch* batch, const void* d_tallies, int inst, rddmc_tallies* out,
+                             uint64_t* hist, uint64_t* faces, uint64_t* sb, void* stream);
+
+/* Capture {zero the tallies, zero the cursor, launch the batch} on `stream`
+ * (a non-default stream) into a CUDA graph and instantiate it;
+ * *graph_exec receives a cudaGraphExec_t.  Replay it with
+ * rddmc_batch_graph_launch; free it with rddmc_batch_graph_destroy. */
+int rddmc_batch_graph_create(const rddmc_batch* batch, const void* d_desc, const rddmc_run_opts* opts,
+                             void* d_scratch, size_t scratch_bytes, void* d_tallies, size_t tally_bytes,
+                             void* stream, void** graph_exec);
+int rddmc_batch_graph_launch(void* graph_exec, void* stream);
+void rddmc_batch_graph_destroy(void* graph_exec);
+
+/* Autotuner: run the trial subsets under every candidate schedule
+ * (threads_per_cta 128 or 256, ctas_per_sm at full or one-less occupancy,
+ * chunk 64, 256 or 1024), timed with CUDA events, and return the one with the
+ * most transitions per second in *best (and the rate in *best_rate, may be
+ * NULL).  Synchronises `stream` and overwrites d_tallies. */
+int rddmc_batch_autotune(const rddmc_batch* batch, const void* d_desc, const rddmc_run_opts* base, void* d_scratch,
+                         size_t scratch_bytes, void* d_tallies, size_t tally_bytes, void* stream,
+                         rddmc_run_opts* best, double* best_rate);
+
 /*
  * rddmc_scatter_samples -- run the walk's FP32 scattering sampler n times at
  * the incoming frequency x_in (incoming direction +z; sample i uses the event

@@ -30,7 +30,9 @@ NSB = 64  # impact-parameter bins of the surface-brightness histogram
 EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc_precompute_leakage",
             "rddmc_reset_tallies", "rddmc_launch_packets", "rddmc_read_tallies", "rddmc_table_rows",
             "rddmc_read_packet_states", "rddmc_launch_packets_noalloc", "rddmc_scatter_samples",
-            "rddmc_status_string", "rddmc_version"]
+            "rddmc_batch_create", "rddmc_batch_destroy", "rddmc_batch_sizes", "rddmc_batch_upload",
+            "rddmc_batch_launch", "rddmc_batch_read_tallies", "rddmc_batch_graph_create", "rddmc_batch_graph_launch",
+            "rddmc_batch_graph_destroy", "rddmc_batch_autotune", "rddmc_status_string", "rddmc_version"]
 
 
 class GridDesc(ctypes.Structure):
@@ -95,11 +97,25 @@ def lib():
         L.rddmc_read_packet_states.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, vp, vp, vp]
         L.rddmc_launch_packets_noalloc.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp]
         L.rddmc_scatter_samples.argtypes = [vp, vp, ctypes.c_double, u64, u64, vp, vp]
+        L.rddmc_batch_create.argtypes = [vp, vp, vp, i32, ctypes.POINTER(vp)]
+        L.rddmc_batch_destroy.argtypes = [vp]
+        L.rddmc_batch_destroy.restype = None
+        L.rddmc_batch_sizes.argtypes = [vp, vp, vp, vp, vp]
+        L.rddmc_batch_upload.argtypes = [vp, ctypes.c_double, vp, sz, vp]
+        L.rddmc_batch_launch.argtypes = [vp, vp, ctypes.POINTER(RunOpts), i32, vp, sz, vp, sz, vp]
+        L.rddmc_batch_read_tallies.argtypes = [vp, vp, i32, ctypes.POINTER(Tallies), vp, vp, vp, vp]
+        L.rddmc_batch_graph_create.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp, sz, vp, ctypes.POINTER(vp)]
+        L.rddmc_batch_graph_launch.argtypes = [vp, vp]
+        L.rddmc_batch_graph_destroy.argtypes = [vp]
+        L.rddmc_batch_graph_destroy.restype = None
+        L.rddmc_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp, sz, vp, ctypes.POINTER(RunOpts),
+                                           ctypes.POINTER(ctypes.c_double)]
         L.rddmc_status_string.argtypes = [i32]
         L.rddmc_status_string.restype = ctypes.c_char_p
         L.rddmc_version.argtypes = []
         for name in EXPORTED:
-            if name not in ("rddmc_destroy_grid", "rddmc_status_string"):
+            if name not in ("rddmc_destroy_grid", "rddmc_status_string", "rddmc_batch_destroy",
+                            "rddmc_batch_graph_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -290,5 +306,91 @@ class Problem:
         try:
             if self.grid:
                 destroy_grid(self.grid)
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many precomputed Problems walked by one persistent launch (C-ABI
+    rddmc_batch_*): descriptors, tallies and scratch in torch device buffers."""
+
+    def __init__(self, problems, n_packets, trial_fraction=0.01):
+        import torch
+        self.torch = torch
+        self.problems = list(problems)
+        self.device = self.problems[0].device
+        n = len(self.problems)
+        grids = (ctypes.c_void_p * n)(*[p.grid for p in self.problems])
+        tables = (ctypes.c_void_p * n)(*[p.table.data_ptr() for p in self.problems])
+        npk = (ctypes.c_uint64 * n)(*[int(v) for v in n_packets])
+        h = ctypes.c_void_p()
+        _check("rddmc_batch_create", lib().rddmc_batch_create(grids, tables, npk, n, ctypes.byref(h)))
+        self.h = h.value
+        db, tb, sb, tot = (ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64())
+        _check("rddmc_batch_sizes", lib().rddmc_batch_sizes(ctypes.c_void_p(self.h), ctypes.byref(db),
+                                                            ctypes.byref(tb), ctypes.byref(sb), ctypes.byref(tot)))
+        self.total = tot.value
+        self.desc = torch.empty(db.value, dtype=torch.uint8, device=self.device)
+        self.tally = torch.zeros(tb.value // 8, dtype=torch.int64, device=self.device)
+        self.scratch = torch.zeros(sb.value // 8, dtype=torch.int64, device=self.device)
+        _check("rddmc_batch_upload", lib().rddmc_batch_upload(ctypes.c_void_p(self.h), float(trial_fraction),
+                                                              ctypes.c_void_p(self.desc.data_ptr()),
+                                                              self.desc.numel(), ctypes.c_void_p(self.stream())))
+
+    def stream(self) -> int:
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def launch(self, opts: RunOpts, trial: bool = False, reset: bool = True):
+        if reset:
+            self.tally.zero_()
+        _check("rddmc_batch_launch", lib().rddmc_batch_launch(
+            ctypes.c_void_p(self.h), ctypes.c_void_p(self.desc.data_ptr()), ctypes.byref(opts), int(trial),
+            ctypes.c_void_p(self.scratch.data_ptr()), self.scratch.numel() * 8, ctypes.c_void_p(self.tally.data_ptr()),
+            self.tally.numel() * 8, ctypes.c_void_p(self.stream())))
+
+    def read(self, inst: int) -> dict:
+        p = self.problems[inst]
+        t = Tallies()
+        hist = np.zeros(p.J + 2, dtype=np.uint64)
+        faces = np.zeros(p.nfaces, dtype=np.uint64)
+        sb = np.zeros(NSB, dtype=np.uint64)
+        _check("rddmc_batch_read_tallies", lib().rddmc_batch_read_tallies(
+            ctypes.c_void_p(self.h), ctypes.c_void_p(self.tally.data_ptr()), int(inst), ctypes.byref(t),
+            _np_ptr(hist), _np_ptr(faces), _np_ptr(sb), ctypes.c_void_p(self.stream())))
+        d = {k: int(getattr(t, k)) for k, _ in Tallies._fields_}
+        d.update(hist=hist, faces=faces, sb=sb)
+        return d
+
+    def graph(self, opts: RunOpts) -> int:
+        ge = ctypes.c_void_p()
+        _check("rddmc_batch_graph_create", lib().rddmc_batch_graph_create(
+            ctypes.c_void_p(self.h), ctypes.c_void_p(self.desc.data_ptr()), ctypes.byref(opts),
+            ctypes.c_void_p(self.scratch.data_ptr()), self.scratch.numel() * 8,
+            ctypes.c_void_p(self.tally.data_ptr()), self.tally.numel() * 8, ctypes.c_void_p(self.stream()),
+            ctypes.byref(ge)))
+        return ge.value
+
+    def graph_launch(self, ge: int):
+        _check("rddmc_batch_graph_launch", lib().rddmc_batch_graph_launch(ctypes.c_void_p(ge),
+                                                                          ctypes.c_void_p(self.stream())))
+
+    @staticmethod
+    def graph_destroy(ge: int):
+        lib().rddmc_batch_graph_destroy(ctypes.c_void_p(ge))
+
+    def autotune(self, base: RunOpts):
+        best = RunOpts()
+        rate = ctypes.c_double()
+        _check("rddmc_batch_autotune", lib().rddmc_batch_autotune(
+            ctypes.c_void_p(self.h), ctypes.c_void_p(self.desc.data_ptr()), ctypes.byref(base),
+            ctypes.c_void_p(self.scratch.data_ptr()), self.scratch.numel() * 8,
+            ctypes.c_void_p(self.tally.data_ptr()), self.tally.numel() * 8, ctypes.c_void_p(self.stream()),
+            ctypes.byref(best), ctypes.byref(rate)))
+        return best, rate.value
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().rddmc_batch_destroy(ctypes.c_void_p(self.h))
         except Exception:
             pass

@@ -107,3 +107,32 @@ SPHERE9_V = Workload("sphere_small_9c_21b_v20", 3, (9, 9, 9), 21, -21.0, 21.0, 3
 
 ALL = {w.name: w for w in (C1, C2, P1, P2, C3, C3_V20, C3_V200, TINY, SMALL, GREY_LIKE, SPHERE8, SPHERE8_V,
                            SPHERE9_V)}
+
+
+def batched_instances(n: int = 512, seed: int = 0x5EED0004, packet_scale: float = 1.0):
+    """The batched workload: n independent slab or sphere instances (p = 1/2),
+    tau0 log-uniform in [1e4, 1e8], T log-uniform in [1e2, 1e5] K, cells
+    uniform in {32..256} (a sphere takes the nearest integer cube root per
+    axis), 128-512 bins, packets log-uniform in [1e4, 1e6] (times
+    packet_scale).  Each instance's frequency grid covers
+    |x| <= max(4 (a tau0)^(1/3), bins/2), with a = 4.702e-4 (T/1e4 K)^(-1/2) the
+    damping parameter, i.e. bins at least one Doppler width wide and the escape
+    peaks (~(a tau0)^(1/3)) inside the grid."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        sphere = bool(rng.random() < 0.5)
+        tau0 = float(10 ** rng.uniform(4, 8))
+        T = float(10 ** rng.uniform(2, 5))
+        cells = int(rng.integers(32, 257))
+        J = int(rng.integers(128, 513))
+        npk = max(1, int(round(packet_scale * 10 ** rng.uniform(4, 6))))
+        atau = 4.702e-4 / np.sqrt(T / 1.0e4) * tau0
+        xmax = float(max(4.0 * atau ** (1.0 / 3.0), J / 2.0))
+        if sphere:
+            m = max(2, int(round(cells ** (1.0 / 3.0))))
+            w = Workload(f"batch{i}_sphere", 3, (m, m, m), J, -xmax, xmax, tau0, T, npk, seed + i, sphere=True)
+        else:
+            w = Workload(f"batch{i}_slab", 1, (cells, 1, 1), J, -xmax, xmax, tau0, T, npk, seed + i)
+        out.append(w)
+    return out
