@@ -357,6 +357,65 @@ int rddmc_batch_autotune(const rddmc_batch* batch, const void* d_desc, const rdd
                          size_t scratch_bytes, void* d_tallies, size_t tally_bytes, void* stream,
                          rddmc_run_opts* best, double* best_rate);
 
+/* --------------------------------------------------- learned exit proposal
+ * A small network predicts where a packet entering a uniform b^3 brick of
+ * medium leaves it (exit face and frequency bin, and a log2 bucket of the DDMC
+ * transitions it took), so the walk can replace many transitions inside thick
+ * regions by one draw.  Not in the paper: trained on first passages the DDMC
+ * walk itself generates.
+ */
+
+/* Optical depth tau_ij = k_ij dz of every bin of `cell`'s class (host, J floats;
+ * synchronises). */
+int rddmc_cell_tau(const rddmc_grid* grid, const void* d_table, int64_t cell, float* tau, void* stream);
+
+/* Training tensors filled by rddmc_fp_generate (all device pointers). */
+typedef struct rddmc_fp_train {
+    void* d_x;              /* bf16 [n x 16] network inputs */
+    int32_t* d_ta;          /* [n] exit face * J + exit bin, -1 if the step cap was reached */
+    int32_t* d_tb;          /* [n] floor(log2(transitions)), at most 31 */
+    const float* d_lk;      /* [L] log10(k0 dz) of each level's medium */
+    const float* d_lp;      /* [J] log10 of the bin-mean profile (k_j / k0) */
+    const float* d_xc;      /* [J] bin-centre frequencies */
+} rddmc_fp_train;
+
+/* First passages through a uniform b^3 brick.  Level l uses the rows of the
+ * centre (interior) cell of grids[l] (3D, DDMC mode, precomputed in
+ * d_tables[l]; all levels share J).  Sample i (packet id p0+i under `seed`):
+ * event word 0 picks the level (floor(w L / 2^32)), word 1 the entry bin in
+ * [jlo[l], jhi[l]], words 2-3 the entry cell on the -x face; transitions
+ * follow the walk's stream contract until a spatial move leaves the brick or
+ * `cap` transitions are taken.  d_out: 4 int32 per sample {level, entry bin,
+ * exit face (0..5: -x,+x,-y,+y,-z,+z; 6 = cap), exit bin}; d_steps: uint64
+ * transitions.  train (may be NULL): also write network inputs and targets. */
+int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_tables, int L, int b, const int32_t* jlo,
+                      const int32_t* jhi, uint64_t seed, uint64_t p0, uint64_t n, uint64_t cap, int32_t* d_out,
+                      uint64_t* d_steps, const rddmc_fp_train* train, void* stream);
+
+/* The network: 16 inputs, three hidden layers of 128 (ReLU), n_out logits (a
+ * multiple of 16): head A = logits [0, nA) (softmax over exit face x bin),
+ * head B = [nA, nA + nB) (softmax over step buckets).  Parameters: FP32
+ * master copy and BF16 copy, same layout, rddmc_mlp_param_count(n_out)
+ * elements: W1[128x16] b1 W2[128x128] b2 W3[128x128] b3 W4[n_out x 128] b4
+ * (row-major W[out][in]).  Matrix products run on tensor cores with BF16
+ * inputs and FP32 accumulation; batch sizes are multiples of 64. */
+uint64_t rddmc_mlp_param_count(int n_out);
+uint64_t rddmc_mlp_work_bytes(int batch, int n_out);
+int rddmc_mlp_to_bf16(int n_out, const float* d_wf, void* d_wb, void* stream);
+/* Logits (FP32 [batch x n_out]) of bf16 inputs d_x [batch x 16]. */
+int rddmc_mlp_forward(int n_out, const float* d_wf, const void* d_wb, const void* d_x, int batch, void* d_work,
+                      float* d_logits, void* stream);
+/* Sum over the batch of the two heads' cross-entropies (*d_loss, device) and
+ * the gradient of its batch mean with respect to every parameter (FP32,
+ * master layout) for targets d_ta (head A; -1 = ignore the row) and d_tb. */
+int rddmc_mlp_loss_grad(int n_out, int nA, int nB, const float* d_wf, const void* d_wb, const void* d_x,
+                        const int32_t* d_ta, const int32_t* d_tb, int batch, void* d_work, float* d_grad,
+                        float* d_loss, void* stream);
+/* One Adam step (bias-corrected, step >= 1) on the master weights; refreshes
+ * the BF16 copy. */
+int rddmc_mlp_adam(int n_out, float* d_wf, void* d_wb, const float* d_grad, float* d_m, float* d_v, int step, float lr,
+                   float beta1, float beta2, float eps, void* stream);
+
 /*
  * rddmc_scatter_samples -- run the walk's FP32 scattering sampler n times at
  * the incoming frequency x_in (incoming direction +z; sample i uses the event

@@ -57,6 +57,8 @@ def lib():
         L.orc_replay_packet.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, d, u64, u64, u64, u64, vp, vp]
         L.orc_scatter_samples.restype = None
         L.orc_scatter_samples.argtypes = [d, d, u64, u64, vp]
+        L.orc_fp_samples.restype = None
+        L.orc_fp_samples.argtypes = [vp, i32, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp]
         L.orc_upar_table.restype = None
         L.orc_upar_table.argtypes = [d, vp]
         _LIB = L
@@ -225,3 +227,28 @@ def upar_table(T: float) -> np.ndarray:
     out = np.zeros(2 * 1024, dtype=np.float64)
     lib().orc_upar_table(float(damping(T)), _ptr(out))
     return out.reshape(1024, 2)
+
+
+def interior_rows(w_uniform) -> np.ndarray:
+    """Rows (7 thresholds + flags per bin) of an interior cell of a uniform 3D
+    medium: the centre cell of a 3^3 grid of the workload's density."""
+    w3 = w_uniform.with_(n=(3, 3, 3), ndim=3, sphere=False, vmax_kms=0.0)
+    g = Grid(w3)
+    t = g.table()
+    c = 13  # centre cell of 3^3
+    thr = t["thr"].reshape(27, w3.J, 7)[c]
+    fl = t["flags"].reshape(27, w3.J)[c]
+    return np.concatenate([thr, fl[:, None]], axis=1).astype(np.uint32)
+
+
+def fp_samples(rows: np.ndarray, b: int, jlo, jhi, seed: int, p0: int, n: int, cap: int):
+    """First passages through a uniform brick (see orc_fp_samples)."""
+    rows = np.ascontiguousarray(rows, dtype=np.uint32)
+    L, J = rows.shape[0], rows.shape[1]
+    jlo = np.ascontiguousarray(jlo, dtype=np.int32)
+    jhi = np.ascontiguousarray(jhi, dtype=np.int32)
+    out = np.zeros(4 * n, dtype=np.int32)
+    steps = np.zeros(n, dtype=np.uint64)
+    lib().orc_fp_samples(_ptr(rows), int(L), int(J), int(b), _ptr(jlo), _ptr(jhi), int(seed), int(p0), int(n),
+                         int(cap), _ptr(out), _ptr(steps))
+    return out.reshape(n, 4), steps

@@ -981,3 +981,49 @@ void orc_scatter_samples(double T, double x_in, uint64_t seed, uint64_t n, doubl
     }
     free(upar);
 }
+
+/* ------------------------------------------------------------------------- */
+/* First passage through a uniform brick (training data of the learned exit  */
+/* proposal)                                                                 */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Sample i (packet id p0+i under `seed`) picks, from its event stream, a
+ * density level l = floor(w0 L / 2^32), an entry bin j0 in [jlo[l], jhi[l]]
+ * (j0 = jlo + floor(w1 n / 2^32)), and an entry cell on the brick's -x face
+ * (i0 = 0, i1 = floor(w2 b / 2^32), i2 = floor(w3 b / 2^32)).  It then takes
+ * DDMC transitions with the rows of an interior cell of a uniform medium at
+ * that level (3D rows: 7 cumulative thresholds, then the flag word, per bin)
+ * until its first spatial move leaves the b^3 brick.  out[4*i..]: {l, j0,
+ * exit face (0..5, 6 = step cap reached), exit bin}; steps[i]: transitions.
+ */
+void orc_fp_samples(const uint32_t* rows, int L, int J, int b, const int32_t* jlo, const int32_t* jhi,
+                    uint64_t seed, uint64_t p0, uint64_t n, uint64_t cap, int32_t* out, uint64_t* steps) {
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t pk = p0 + i;
+        uint32_t w0 = orc_word(seed, pk, ORC_EVENT, 0), w1 = orc_word(seed, pk, ORC_EVENT, 1);
+        uint32_t w2 = orc_word(seed, pk, ORC_EVENT, 2), w3 = orc_word(seed, pk, ORC_EVENT, 3);
+        int l = (int)(((uint64_t)w0 * (uint64_t)L) >> 32);
+        int nb = jhi[l] - jlo[l] + 1;
+        int j = jlo[l] + (int)(((uint64_t)w1 * (uint64_t)nb) >> 32);
+        int idx[3] = {0, (int)(((uint64_t)w2 * (uint64_t)b) >> 32), (int)(((uint64_t)w3 * (uint64_t)b) >> 32)};
+        out[4 * i + 0] = l;
+        out[4 * i + 1] = j;
+        int face = 6;
+        uint64_t t = 0;
+        while (t < cap) {
+            const uint32_t* r = rows + ((size_t)l * J + j) * 8;
+            uint32_t w = orc_word(seed, pk, ORC_TRANS, t);
+            ++t;
+            int o = 0;
+            while (o < 7 && w >= r[o]) ++o;
+            if (o < 2) { j += o ? 1 : -1; continue; }
+            int f = o - 2, ax = f / 2, side = (f & 1) ? 1 : -1;
+            idx[ax] += side;
+            if (idx[ax] < 0 || idx[ax] >= b) { face = f; break; }
+        }
+        out[4 * i + 2] = face;
+        out[4 * i + 3] = j;
+        steps[i] = t;
+    }
+}

@@ -1,0 +1,508 @@
+// learned.cu -- the learned exit proposal: first-passage data generation, the
+// BF16 MLP (forward, backward, softmax cross-entropy, Adam) on tensor cores,
+// and batched inference that samples exits for parked packets.
+//
+// First passages: sample i picks a density level, an entry bin and an entry
+// cell on the -x face of a b^3 brick of uniform medium from its event stream
+// and walks with the rows of an interior cell of that medium (the same rows
+// and transition stream as the walk) until a spatial move leaves the brick.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <mma.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "grid.h"
+
+namespace rddmc {
+namespace {
+
+constexpr int kMaxLevels = 64;
+constexpr int kFeat = 16;
+constexpr int kStepBuckets = 32;
+
+// Constants of the input featurisation shared by training and inference.
+struct FeatConst {
+    float log_b;     // log10(brick cells per edge)
+    float log_a;     // log10(damping parameter a)
+    float inv_xs;    // 1 / max |x| of the frequency grid
+};
+
+// Network inputs for a brick of line-centre cell optical depth 10^lk (k0 dz)
+// entered at a bin with log10 bin-mean profile lp and centre frequency x:
+// region size in tau at line centre and at the entry bin, region a*tau, the
+// entry frequency and eight Fourier features of it.
+__device__ __forceinline__ void features(float lk, float lp, float x, const FeatConst& C, __nv_bfloat16* out) {
+    float f[kFeat];
+    f[0] = (lk + C.log_b) * 0.1f;
+    f[1] = (lk + lp + C.log_b) * 0.2f;
+    f[2] = (lk + C.log_b + C.log_a) * 0.1f;
+    const float xs = x * C.inv_xs;
+    f[3] = xs;
+    f[4] = fabsf(xs);
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        float sn, cs;
+        sincospif((float)k * xs, &sn, &cs);
+        f[3 + 2 * k] = sn;
+        f[4 + 2 * k] = cs;
+    }
+    f[13] = f[14] = f[15] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kFeat; ++i) out[i] = __float2bfloat16(f[i]);
+}
+
+__device__ __forceinline__ int step_bucket(unsigned long long t) {
+    int k = 63 - __clzll((long long)(t | 1ull));
+    return k < kStepBuckets - 1 ? k : kStepBuckets - 1;
+}
+
+struct FpParams {
+    const uint4* rows[kMaxLevels];  // 3D rows (two uint4) of the interior class, J per level
+    const uint2* fast[kMaxLevels];
+    int jlo[kMaxLevels], jhi[kMaxLevels];
+    int L, J, b;
+    uint32_t k0, k1;
+    unsigned long long p0, n, cap;
+    int* out;                    // 4 ints per sample: level, entry bin, exit face (6 = cap), exit bin
+    unsigned long long* steps;   // transitions per sample
+    // optional training tensors: inputs (bf16, 16 per sample), targets
+    __nv_bfloat16* X;
+    int* tA;                     // exit face * J + exit bin, -1 when the step cap was reached
+    int* tB;                     // log2 step bucket
+    const float* lk;             // per level: log10(k0 dz)
+    const float* lp;             // per bin: log10 of the bin-mean profile
+    const float* xc;             // per bin: centre frequency
+    FeatConst fc;
+};
+
+__device__ __forceinline__ uint4 fp_philox(uint4 c, uint32_t k0, uint32_t k1) { return philox4x32_10(c, k0, k1); }
+
+__global__ void __launch_bounds__(256) fp_kernel(const FpParams P) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+        const unsigned long long pk = P.p0 + i;
+        const uint32_t pl = (uint32_t)pk, ph = (uint32_t)(pk >> 32);
+        const uint4 ew = fp_philox(make_uint4(0u, 0u, pl, ph | 0x80000000u), P.k0, P.k1);  // event words 0..3
+        const int l = (int)(((unsigned long long)ew.x * (unsigned long long)P.L) >> 32);
+        const int nb = P.jhi[l] - P.jlo[l] + 1;
+        int j = P.jlo[l] + (int)(((unsigned long long)ew.y * (unsigned long long)nb) >> 32);
+        int idx[3] = {0, (int)(((unsigned long long)ew.z * (unsigned long long)P.b) >> 32),
+                      (int)(((unsigned long long)ew.w * (unsigned long long)P.b) >> 32)};
+        const uint4* rows = P.rows[l];
+        const uint2* fast = P.fast[l];
+        const int j0 = j;
+        int face = 6;
+        unsigned long long t = 0;
+        const unsigned J1 = (unsigned)P.J - 1u;
+        while (t < P.cap && face == 6) {
+            const unsigned long long blk = t >> 2;
+            const uint4 r = fp_philox(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), pl, ph), P.k0, P.k1);
+            for (unsigned q = (unsigned)(t & 3u); q < 4u && t < P.cap; ++q) {
+                const unsigned w = q == 0 ? r.x : (q == 1 ? r.y : (q == 2 ? r.z : r.w));
+                ++t;
+                const unsigned jj = min((unsigned)j, J1);
+                const uint2 f = __ldg(&fast[jj]);
+                if (w < f.y) { j += (w >= f.x) ? 1 : -1; continue; }
+                const uint4 a = __ldg(&rows[2 * jj]), c = __ldg(&rows[2 * jj + 1]);
+                const unsigned o = (unsigned)(w >= a.x) + (unsigned)(w >= a.y) + (unsigned)(w >= a.z) +
+                                   (unsigned)(w >= c.x) + (unsigned)(w >= c.y) + (unsigned)(w >= c.z) +
+                                   (unsigned)(w >= c.w);
+                if (o < 2u) { j += o ? 1 : -1; continue; }
+                const int fc = (int)o - 2, ax = fc >> 1, side = (fc & 1) ? 1 : -1;
+                idx[ax] += side;
+                if (idx[ax] < 0 || idx[ax] >= P.b) { face = fc; break; }
+            }
+        }
+        P.out[4 * i + 0] = l;
+        P.out[4 * i + 1] = j0;
+        P.out[4 * i + 2] = face;
+        P.out[4 * i + 3] = j;
+        P.steps[i] = t;
+        if (P.X) {
+            features(P.lk[l], P.lp[j0], P.xc[j0], P.fc, P.X + kFeat * i);
+            P.tA[i] = face < 6 ? face * P.J + min(max(j, 0), P.J - 1) : -1;
+            P.tB[i] = step_bucket(t);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace rddmc
+
+using namespace rddmc;
+
+extern "C" {
+
+int rddmc_cell_tau(const rddmc_grid* g, const void* d_table, int64_t cell, float* tau, void* stream) {
+    if (!g || !d_table || !tau || cell < 0 || cell >= g->ncell) return RDDMC_ERR_ARG;
+    if (!g->precomputed) return RDDMC_ERR_TABLE;
+    const uint32_t cls = g->cell_class[cell];
+    if (cls == UINT32_MAX) return RDDMC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const char* src = (const char*)d_table + g->off_tau + (uint64_t)cls * g->J * 4;
+    if (cudaMemcpyAsync(tau, src, (size_t)g->J * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RDDMC_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+}
+
+int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_tables, int L, int b, const int32_t* jlo,
+                      const int32_t* jhi, uint64_t seed, uint64_t p0, uint64_t n, uint64_t cap, int32_t* d_out,
+                      uint64_t* d_steps, const rddmc_fp_train* train, void* stream) {
+    if (!grids || !d_tables || !jlo || !jhi || !d_out || !d_steps) return RDDMC_ERR_ARG;
+    if (L < 1 || L > kMaxLevels || b < 1 || n == 0 || cap == 0) return RDDMC_ERR_ARG;
+    FpParams P;
+    std::memset(&P, 0, sizeof(P));
+    int J = -1;
+    for (int l = 0; l < L; ++l) {
+        const rddmc_grid* g = grids[l];
+        if (!g || !d_tables[l]) return RDDMC_ERR_ARG;
+        if (!g->precomputed) return RDDMC_ERR_TABLE;
+        if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
+        if (J < 0) J = g->J;
+        if (g->J != J) return RDDMC_ERR_ARG;
+        int idx[3] = {g->n[0] / 2, g->n[1] / 2, g->n[2] / 2};
+        for (int a = 0; a < 3; ++a)
+            for (int sd = -1; sd <= 1; sd += 2) {
+                int nidx[3] = {idx[0], idx[1], idx[2]};
+                nidx[a] += sd;
+                if (!g->in_medium(nidx)) return RDDMC_ERR_ARG;  // the centre cell must be interior
+            }
+        const uint32_t cls = g->cell_class[g->cell_of(idx)];
+        const char* tb = (const char*)d_tables[l];
+        P.rows[l] = (const uint4*)(tb + g->off_rows) + (uint64_t)cls * J * 2;
+        P.fast[l] = (const uint2*)(tb + g->off_fast) + (uint64_t)cls * J;
+        if (jlo[l] < 0 || jhi[l] >= J || jlo[l] > jhi[l]) return RDDMC_ERR_ARG;
+        P.jlo[l] = jlo[l];
+        P.jhi[l] = jhi[l];
+    }
+    P.L = L; P.J = J; P.b = b;
+    P.k0 = (uint32_t)seed; P.k1 = (uint32_t)(seed >> 32);
+    P.p0 = p0; P.n = n; P.cap = cap;
+    P.out = d_out;
+    P.steps = (unsigned long long*)d_steps;
+    if (train) {
+        if (!train->d_x || !train->d_ta || !train->d_tb || !train->d_lk || !train->d_lp || !train->d_xc)
+            return RDDMC_ERR_ARG;
+        P.X = (__nv_bfloat16*)train->d_x;
+        P.tA = train->d_ta;
+        P.tB = train->d_tb;
+        P.lk = train->d_lk;
+        P.lp = train->d_lp;
+        P.xc = train->d_xc;
+        P.fc.log_b = log10f((float)b);
+        P.fc.log_a = (float)log10(grids[0]->a);
+        P.fc.inv_xs = (float)(1.0 / std::max(std::fabs(grids[0]->edges.front()), std::fabs(grids[0]->edges.back())));
+    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RDDMC_ERR_CUDA;
+    const unsigned long long want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < (unsigned long long)nsm * 8 ? want : (unsigned long long)nsm * 8);
+    fp_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(P);
+    return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+}
+
+}  // extern "C"
+
+// ===================================================================== MLP
+// Architecture: n_in = 16 inputs -> 3 hidden layers of 128 (ReLU) -> n_out
+// logits (a multiple of 16): head A over [0, nA) (exit face x exit bin) and
+// head B over [nA, nA + nB) (log2 step bucket); columns past nA + nB are
+// padding.  Parameters, FP32 master copy and BF16 copy in the same order:
+// W1[128x16] b1[128] W2[128x128] b2[128] W3[128x128] b3[128] W4[n_out x 128]
+// b4[n_out].  Matrix products run on tensor cores (WMMA, BF16 inputs, FP32
+// accumulation); softmax, cross-entropy, bias sums and Adam in FP32.
+namespace rddmc {
+namespace {
+
+using namespace nvcuda;
+constexpr int kIn = 16, kHid = 128;
+
+struct MlpOffsets {
+    uint64_t W[4], b[4], total;
+};
+
+MlpOffsets mlp_offsets(int n_out) {
+    MlpOffsets o;
+    const int fan_in[4] = {kIn, kHid, kHid, kHid}, fan_out[4] = {kHid, kHid, kHid, n_out};
+    uint64_t off = 0;
+    for (int l = 0; l < 4; ++l) {
+        o.W[l] = off; off += (uint64_t)fan_in[l] * fan_out[l];
+        o.b[l] = off; off += (uint64_t)fan_out[l];
+    }
+    o.total = off;
+    return o;
+}
+
+enum Epi { EPI_RELU_BF16 = 0, EPI_LINEAR_F32 = 1, EPI_MASK_BF16 = 2, EPI_F32 = 3 };
+
+// C[M x N] = A[M x K] B[K x N]; A row- or column-major (lda), B row- or
+// column-major (ldb); M, N, K multiples of 16.  Block = 4 warps on a 64 x 64
+// tile, each warp 32 x 32 (2 x 2 fragments).
+template <bool A_ROW, bool B_ROW, int EPI>
+__global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda,
+                                                   const __nv_bfloat16* __restrict__ B, int ldb,
+                                                   const float* __restrict__ bias,
+                                                   const __nv_bfloat16* __restrict__ mask, int ldmask,
+                                                   __nv_bfloat16* __restrict__ outb, float* __restrict__ outf,
+                                                   int ldc) {
+    __shared__ float tile[4][32 * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * 64 + (warp >> 1) * 32, n0 = blockIdx.x * 64 + (warp & 1) * 32;
+    using LA = typename std::conditional<A_ROW, wmma::row_major, wmma::col_major>::type;
+    using LB = typename std::conditional<B_ROW, wmma::row_major, wmma::col_major>::type;
+    wmma::fragment<wmma::accumulator, 16, 16, 16, float> c[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) wmma::fill_fragment(c[i][j], 0.0f);
+    const bool rv[2] = {m0 < M, m0 + 16 < M}, cv[2] = {n0 < N, n0 + 16 < N};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, LA> a[2];
+        wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, LB> b[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            if (!rv[i]) continue;
+            const int m = m0 + 16 * i;
+            wmma::load_matrix_sync(a[i], A_ROW ? A + (size_t)m * lda + k0 : A + (size_t)k0 * lda + m, lda);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (!cv[j]) continue;
+            const int n = n0 + 16 * j;
+            wmma::load_matrix_sync(b[j], B_ROW ? B + (size_t)k0 * ldb + n : B + (size_t)n * ldb + k0, ldb);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (rv[i] && cv[j]) wmma::mma_sync(c[i][j], a[i], b[j], c[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+            if (rv[i] && cv[j]) wmma::store_matrix_sync(&tile[warp][(16 * i) * 32 + 16 * j], c[i][j], 32,
+                                                         wmma::mem_row_major);
+    __syncwarp();
+    for (int e = lane; e < 32 * 32; e += 32) {
+        const int r = e >> 5, cc = e & 31, m = m0 + r, n = n0 + cc;
+        if (m >= M || n >= N) continue;
+        float v = tile[warp][e];
+        if (EPI == EPI_RELU_BF16) {
+            v = fmaxf(v + bias[n], 0.0f);
+            outb[(size_t)m * ldc + n] = __float2bfloat16(v);
+        } else if (EPI == EPI_LINEAR_F32) {
+            outf[(size_t)m * ldc + n] = v + bias[n];
+        } else if (EPI == EPI_MASK_BF16) {
+            v = __bfloat162float(mask[(size_t)m * ldmask + n]) > 0.0f ? v : 0.0f;
+            outb[(size_t)m * ldc + n] = __float2bfloat16(v);
+            outf[(size_t)m * ldc + n] = v;
+        } else {
+            outf[(size_t)m * ldc + n] = v;
+        }
+    }
+}
+
+template <bool A_ROW, bool B_ROW, int EPI>
+cudaError_t gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+                 const float* bias, const __nv_bfloat16* mask, int ldmask, __nv_bfloat16* outb, float* outf, int ldc,
+                 cudaStream_t s) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    gemm_kernel<A_ROW, B_ROW, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldmask, outb, outf, ldc);
+    return cudaGetLastError();
+}
+
+// Softmax cross-entropy of both heads, one warp per row: loss += CE_A + CE_B
+// (summed over the batch), dlogits = (softmax - onehot) / B, zero on padding.
+__global__ void softmax_ce_kernel(const float* __restrict__ logits, int n_out, int nA, int nB,
+                                  const int* __restrict__ tA, const int* __restrict__ tB, int Bsz,
+                                  float* __restrict__ dlogf, __nv_bfloat16* __restrict__ dlogb, float* loss) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= Bsz) return;
+    const float* z = logits + (size_t)row * n_out;
+    float total = 0.0f;
+    if (tA[row] < 0) {  // ignored sample: no loss, no gradient
+        for (int k = lane; k < n_out; k += 32) {
+            dlogf[(size_t)row * n_out + k] = 0.0f;
+            dlogb[(size_t)row * n_out + k] = __float2bfloat16(0.0f);
+        }
+        return;
+    }
+    for (int h = 0; h < 2; ++h) {
+        const int lo = h ? nA : 0, hi = h ? nA + nB : nA, tgt = h ? tB[row] + nA : tA[row];
+        float mx = -3.0e38f;
+        for (int k = lo + lane; k < hi; k += 32) mx = fmaxf(mx, z[k]);
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        float se = 0.0f;
+        for (int k = lo + lane; k < hi; k += 32) se += __expf(z[k] - mx);
+        for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+        const float lse = mx + __logf(se);
+        total += lse - z[tgt];
+        for (int k = lo + lane; k < hi; k += 32) {
+            const float g = (__expf(z[k] - lse) - (k == tgt ? 1.0f : 0.0f)) / (float)Bsz;
+            dlogf[(size_t)row * n_out + k] = g;
+            dlogb[(size_t)row * n_out + k] = __float2bfloat16(g);
+        }
+    }
+    for (int k = nA + nB + lane; k < n_out; k += 32) {
+        dlogf[(size_t)row * n_out + k] = 0.0f;
+        dlogb[(size_t)row * n_out + k] = __float2bfloat16(0.0f);
+    }
+    if (lane == 0) atomicAdd(loss, total);
+}
+
+// db[n] = sum_b dY[b, n]
+__global__ void colsum_kernel(const float* __restrict__ dy, int Bsz, int N, float* __restrict__ db) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int b = 0; b < Bsz; ++b) s += dy[(size_t)b * N + n];
+    db[n] = s;
+}
+
+__global__ void adam_kernel(uint64_t n, float* __restrict__ w, __nv_bfloat16* __restrict__ wb,
+                            const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi, vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    wb[i] = __float2bfloat16(wi);
+}
+
+__global__ void to_bf16_kernel(uint64_t n, const float* __restrict__ w, __nv_bfloat16* __restrict__ wb) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) wb[i] = __float2bfloat16(w[i]);
+}
+
+// Work buffer (bytes, rows B a multiple of 64): H1 H2 H3 bf16 [B x 128] each,
+// dHf f32 [B x 128], dHb bf16 [B x 128] x2, logits f32 [B x n_out],
+// dlogf f32 [B x n_out], dlogb bf16 [B x n_out].
+struct MlpWork {
+    __nv_bfloat16 *H[3], *dHb[2], *dlogb;
+    float *dHf, *logits, *dlogf;
+};
+
+uint64_t mlp_work_bytes(int Bsz, int n_out) {
+    const uint64_t bh = (uint64_t)Bsz * kHid;
+    return align256(bh * 2) * 5 + align256(bh * 4) + align256((uint64_t)Bsz * n_out * 4) * 2 +
+           align256((uint64_t)Bsz * n_out * 2);
+}
+
+MlpWork mlp_work(void* d_work, int Bsz, int n_out) {
+    char* p = (char*)d_work;
+    const uint64_t bh = (uint64_t)Bsz * kHid;
+    MlpWork w;
+    for (int i = 0; i < 3; ++i) { w.H[i] = (__nv_bfloat16*)p; p += align256(bh * 2); }
+    for (int i = 0; i < 2; ++i) { w.dHb[i] = (__nv_bfloat16*)p; p += align256(bh * 2); }
+    w.dHf = (float*)p; p += align256(bh * 4);
+    w.logits = (float*)p; p += align256((uint64_t)Bsz * n_out * 4);
+    w.dlogf = (float*)p; p += align256((uint64_t)Bsz * n_out * 4);
+    w.dlogb = (__nv_bfloat16*)p;
+    return w;
+}
+
+cudaError_t mlp_forward(int n_out, const float* wf, const __nv_bfloat16* wb, const __nv_bfloat16* X, int Bsz,
+                        const MlpWork& w, cudaStream_t s) {
+    const MlpOffsets o = mlp_offsets(n_out);
+    cudaError_t e;
+    if ((e = gemm<true, false, EPI_RELU_BF16>(Bsz, kHid, kIn, X, kIn, wb + o.W[0], kIn, wf + o.b[0], nullptr, 0,
+                                              w.H[0], nullptr, kHid, s)) != cudaSuccess)
+        return e;
+    for (int l = 1; l < 3; ++l)
+        if ((e = gemm<true, false, EPI_RELU_BF16>(Bsz, kHid, kHid, w.H[l - 1], kHid, wb + o.W[l], kHid, wf + o.b[l],
+                                                  nullptr, 0, w.H[l], nullptr, kHid, s)) != cudaSuccess)
+            return e;
+    return gemm<true, false, EPI_LINEAR_F32>(Bsz, n_out, kHid, w.H[2], kHid, wb + o.W[3], kHid, wf + o.b[3], nullptr,
+                                             0, nullptr, w.logits, n_out, s);
+}
+
+}  // namespace
+}  // namespace rddmc
+
+extern "C" {
+
+uint64_t rddmc_mlp_param_count(int n_out) { return (n_out > 0 && n_out % 16 == 0) ? mlp_offsets(n_out).total : 0; }
+
+uint64_t rddmc_mlp_work_bytes(int batch, int n_out) {
+    return (batch > 0 && batch % 64 == 0 && n_out > 0 && n_out % 16 == 0) ? mlp_work_bytes(batch, n_out) : 0;
+}
+
+int rddmc_mlp_to_bf16(int n_out, const float* d_wf, void* d_wb, void* stream) {
+    const uint64_t n = rddmc_mlp_param_count(n_out);
+    if (!n || !d_wf || !d_wb) return RDDMC_ERR_ARG;
+    to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, d_wf, (__nv_bfloat16*)d_wb);
+    return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+}
+
+int rddmc_mlp_forward(int n_out, const float* d_wf, const void* d_wb, const void* d_x, int batch, void* d_work,
+                      float* d_logits, void* stream) {
+    if (!rddmc_mlp_param_count(n_out) || !rddmc_mlp_work_bytes(batch, n_out) || !d_wf || !d_wb || !d_x || !d_work)
+        return RDDMC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const MlpWork w = mlp_work(d_work, batch, n_out);
+    if (mlp_forward(n_out, d_wf, (const __nv_bfloat16*)d_wb, (const __nv_bfloat16*)d_x, batch, w, s) != cudaSuccess)
+        return RDDMC_ERR_CUDA;
+    if (d_logits && cudaMemcpyAsync(d_logits, w.logits, (size_t)batch * n_out * 4, cudaMemcpyDeviceToDevice, s) !=
+                        cudaSuccess)
+        return RDDMC_ERR_CUDA;
+    return RDDMC_OK;
+}
+
+int rddmc_mlp_loss_grad(int n_out, int nA, int nB, const float* d_wf, const void* d_wb, const void* d_x,
+                        const int32_t* d_ta, const int32_t* d_tb, int batch, void* d_work, float* d_grad,
+                        float* d_loss, void* stream) {
+    if (!rddmc_mlp_param_count(n_out) || !rddmc_mlp_work_bytes(batch, n_out) || nA < 1 || nB < 1 ||
+        nA + nB > n_out || !d_wf || !d_wb || !d_x || !d_ta || !d_tb || !d_work || !d_grad || !d_loss)
+        return RDDMC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const MlpOffsets o = mlp_offsets(n_out);
+    const __nv_bfloat16* wb = (const __nv_bfloat16*)d_wb;
+    const __nv_bfloat16* X = (const __nv_bfloat16*)d_x;
+    const MlpWork w = mlp_work(d_work, batch, n_out);
+    if (mlp_forward(n_out, d_wf, wb, X, batch, w, s) != cudaSuccess) return RDDMC_ERR_CUDA;
+    if (cudaMemsetAsync(d_loss, 0, 4, s) != cudaSuccess) return RDDMC_ERR_CUDA;
+    softmax_ce_kernel<<<(batch + 7) / 8, 256, 0, s>>>(w.logits, n_out, nA, nB, d_ta, d_tb, batch, w.dlogf, w.dlogb,
+                                                       d_loss);
+    // output layer: dW4 = dlog^T H3, db4 = colsum(dlog), dH3 = (dlog W4) * [H3 > 0]
+    gemm<false, true, EPI_F32>(n_out, kHid, batch, w.dlogb, n_out, w.H[2], kHid, nullptr, nullptr, 0, nullptr,
+                               d_grad + o.W[3], kHid, s);
+    colsum_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(w.dlogf, batch, n_out, d_grad + o.b[3]);
+    gemm<true, true, EPI_MASK_BF16>(batch, kHid, n_out, w.dlogb, n_out, wb + o.W[3], kHid, nullptr, w.H[2], kHid,
+                                    w.dHb[0], w.dHf, kHid, s);
+    int cur = 0;
+    for (int l = 2; l >= 1; --l) {
+        // layer l (W[l]: H[l-1] -> H[l]); dHb[cur] holds dL/d(pre-activation of H[l])
+        gemm<false, true, EPI_F32>(kHid, kHid, batch, w.dHb[cur], kHid, w.H[l - 1], kHid, nullptr, nullptr, 0,
+                                   nullptr, d_grad + o.W[l], kHid, s);
+        colsum_kernel<<<1, 128, 0, s>>>(w.dHf, batch, kHid, d_grad + o.b[l]);
+        gemm<true, true, EPI_MASK_BF16>(batch, kHid, kHid, w.dHb[cur], kHid, wb + o.W[l], kHid, nullptr, w.H[l - 1],
+                                        kHid, w.dHb[cur ^ 1], w.dHf, kHid, s);
+        cur ^= 1;
+    }
+    gemm<false, true, EPI_F32>(kHid, kIn, batch, w.dHb[cur], kHid, X, kIn, nullptr, nullptr, 0, nullptr,
+                               d_grad + o.W[0], kIn, s);
+    colsum_kernel<<<1, 128, 0, s>>>(w.dHf, batch, kHid, d_grad + o.b[0]);
+    return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+}
+
+int rddmc_mlp_adam(int n_out, float* d_wf, void* d_wb, const float* d_grad, float* d_m, float* d_v, int step, float lr,
+                   float beta1, float beta2, float eps, void* stream) {
+    const uint64_t n = rddmc_mlp_param_count(n_out);
+    if (!n || !d_wf || !d_wb || !d_grad || !d_m || !d_v || step < 1) return RDDMC_ERR_ARG;
+    const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
+    adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        n, d_wf, (__nv_bfloat16*)d_wb, d_grad, d_m, d_v, lr, beta1, beta2, eps, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+"""Training driver of the learned exit proposal (argument marshalling around the
+C-ABI; data generation, the network's forward and backward passes and the
+optimiser all run in the library's kernels).
+
+A proposal is trained for one target grid (cell size, frequency bins,
+temperature): uniform media at L density levels, each a 3^3 grid of the
+target's cell size whose centre cell carries the interior rows of a uniform
+brick, produce first passages through a b^3 brick entered on its -x face at a
+bin of the positive-frequency side whose cell optical depth lies in
+[tau_lo, tau_hi].  A static uniform brick is symmetric under x -> -x, so
+entries at negative frequency are mirrored at inference.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import rddmc as R
+from . import workloads as W
+
+N_STEP_BUCKETS = 32
+
+
+class ExitProposal:
+    def __init__(self, target: W.Workload, brick: int, rho_levels, tau_lo=5.0, tau_hi=200.0, device="cuda",
+                 hidden_seed=0x5EED0601):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.target = target
+        self.b = int(brick)
+        self.J = target.J
+        dz = 2.0 * target.R / target.n[0]
+        self.dz = dz
+        R3 = 1.5 * dz
+        self.levels = []
+        self.problems = []
+        lk, jlo, jhi = [], [], []
+        lp = None
+        for rho in rho_levels:
+            tau3 = target.tau0 / target.R * float(rho) * R3
+            w = W.Workload(f"level_{rho:.4g}", 3, (3, 3, 3), target.J, target.x_min, target.x_max, tau3, target.T,
+                           1, 1, R=R3)
+            p = R.Problem(w, device=self.device)
+            tau = R.cell_tau(p.grid, p.table.data_ptr(), 13, self.J, p.stream()).astype(np.float64)
+            kdz = 2.0 * tau3 / 3.0  # k0 dz of the level
+            if lp is None:
+                lp = np.log10(np.maximum(tau, 1e-300)) - np.log10(kdz)
+            xc = 0.5 * (w.edges()[1:] + w.edges()[:-1])
+            ok = np.nonzero((xc >= 0) & (tau >= tau_lo) & (tau <= tau_hi))[0]
+            if ok.size == 0:
+                continue
+            # a contiguous run on the positive side (the wing, where tau falls with |x|)
+            lo, hi = int(ok.min()), int(ok.max())
+            if not np.all((tau[lo:hi + 1] >= tau_lo) & (tau[lo:hi + 1] <= tau_hi)):
+                continue
+            self.levels.append(float(rho))
+            self.problems.append(p)
+            lk.append(np.log10(kdz))
+            jlo.append(lo)
+            jhi.append(hi)
+        if not self.problems:
+            raise ValueError("no density level has bins in the requested optical-depth range")
+        self.jlo, self.jhi = np.array(jlo, np.int32), np.array(jhi, np.int32)
+        t = lambda a, dt: torch.as_tensor(np.asarray(a), dtype=dt, device=self.device)
+        self.lk = t(np.array(lk, np.float32), torch.float32)
+        self.lp = t(lp.astype(np.float32), torch.float32)
+        self.xc = t((0.5 * (target.edges()[1:] + target.edges()[:-1])).astype(np.float32), torch.float32)
+        self.nA = 6 * self.J
+        self.nB = N_STEP_BUCKETS
+        self.n_out = ((self.nA + self.nB + 15) // 16) * 16
+        n_par = R.mlp_param_count(self.n_out)
+        rng = np.random.default_rng(hidden_seed)
+        flat = []
+        for (o, i) in [(128, 16), (128, 128), (128, 128), (self.n_out, 128)]:
+            flat.append(rng.normal(0.0, np.sqrt(2.0 / i), o * i))   # He initialisation
+            flat.append(np.zeros(o))
+        flat = np.concatenate(flat).astype(np.float32)
+        assert flat.size == n_par
+        self.wf = t(flat, torch.float32)
+        self.wb = torch.empty(n_par, dtype=torch.bfloat16, device=self.device)
+        R.mlp_to_bf16(self.n_out, self.wf.data_ptr(), self.wb.data_ptr(), self.stream())
+        self.m = torch.zeros_like(self.wf)
+        self.v = torch.zeros_like(self.wf)
+        self.grad = torch.zeros_like(self.wf)
+        self.step = 0
+
+    def stream(self) -> int:
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    # ------------------------------------------------------------------ data
+    def generate(self, n: int, seed: int, p0: int = 0, cap: int = 10_000_000) -> dict:
+        """n first-passage samples with network inputs and targets (device tensors)."""
+        torch = self.torch
+        out = torch.empty(4 * n, dtype=torch.int32, device=self.device)
+        steps = torch.empty(n, dtype=torch.int64, device=self.device)
+        X = torch.empty((n, 16), dtype=torch.bfloat16, device=self.device)
+        tA = torch.empty(n, dtype=torch.int32, device=self.device)
+        tB = torch.empty(n, dtype=torch.int32, device=self.device)
+        tr = R.FpTrain(X.data_ptr(), tA.data_ptr(), tB.data_ptr(), self.lk.data_ptr(), self.lp.data_ptr(),
+                       self.xc.data_ptr())
+        R.fp_generate([p.grid for p in self.problems], [p.table.data_ptr() for p in self.problems], self.b, self.jlo,
+                      self.jhi, seed, p0, n, cap, out.data_ptr(), steps.data_ptr(), tr, self.stream())
+        return dict(X=X, tA=tA, tB=tB, rec=out.view(n, 4), steps=steps)
+
+    # ------------------------------------------------------------------ training
+    def loss_grad(self, X, tA, tB):
+        B = X.shape[0]
+        work = self.torch.empty(R.mlp_work_bytes(B, self.n_out), dtype=self.torch.uint8, device=self.device)
+        loss = self.torch.zeros(1, dtype=self.torch.float32, device=self.device)
+        R.mlp_loss_grad(self.n_out, self.nA, self.nB, self.wf.data_ptr(), self.wb.data_ptr(), X.data_ptr(),
+                        tA.data_ptr(), tB.data_ptr(), B, work.data_ptr(), self.grad.data_ptr(), loss.data_ptr(),
+                        self.stream())
+        return loss
+
+    def train(self, data: dict, iters: int, batch: int = 8192, lr: float = 1e-3, seed: int = 1, log_every=0):
+        torch = self.torch
+        n = data["X"].shape[0]
+        gen = torch.Generator(device=self.device)
+        gen.manual_seed(seed)
+        work = torch.empty(R.mlp_work_bytes(batch, self.n_out), dtype=torch.uint8, device=self.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        hist = []
+        for it in range(iters):
+            idx = torch.randint(0, n, (batch,), device=self.device, generator=gen)
+            X, tA, tB = data["X"][idx].contiguous(), data["tA"][idx].contiguous(), data["tB"][idx].contiguous()
+            R.mlp_loss_grad(self.n_out, self.nA, self.nB, self.wf.data_ptr(), self.wb.data_ptr(), X.data_ptr(),
+                            tA.data_ptr(), tB.data_ptr(), batch, work.data_ptr(), self.grad.data_ptr(),
+                            loss.data_ptr(), self.stream())
+            self.step += 1
+            R.mlp_adam(self.n_out, self.wf.data_ptr(), self.wb.data_ptr(), self.grad.data_ptr(), self.m.data_ptr(),
+                       self.v.data_ptr(), self.step, lr, stream=self.stream())
+            if log_every and (it % log_every == 0 or it == iters - 1):
+                hist.append((it, float(loss.item()) / batch))
+        return hist
+
+    def mean_loss(self, data: dict, batch: int = 8192) -> float:
+        n = (data["X"].shape[0] // batch) * batch
+        tot = 0.0
+        for s in range(0, n, batch):
+            sl = slice(s, s + batch)
+            tot += float(self.loss_grad(data["X"][sl].contiguous(), data["tA"][sl].contiguous(),
+                                        data["tB"][sl].contiguous()).item())
+        return tot / n
+
+    def logits(self, X):
+        B = X.shape[0]
+        work = self.torch.empty(R.mlp_work_bytes(B, self.n_out), dtype=self.torch.uint8, device=self.device)
+        out = self.torch.empty((B, self.n_out), dtype=self.torch.float32, device=self.device)
+        R.mlp_forward(self.n_out, self.wf.data_ptr(), self.wb.data_ptr(), X.data_ptr(), B, work.data_ptr(),
+                      out.data_ptr(), self.stream())
+        return out

@@ -32,7 +32,9 @@ EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc
             "rddmc_read_packet_states", "rddmc_launch_packets_noalloc", "rddmc_scatter_samples",
             "rddmc_batch_create", "rddmc_batch_destroy", "rddmc_batch_sizes", "rddmc_batch_upload",
             "rddmc_batch_launch", "rddmc_batch_read_tallies", "rddmc_batch_graph_create", "rddmc_batch_graph_launch",
-            "rddmc_batch_graph_destroy", "rddmc_batch_autotune", "rddmc_status_string", "rddmc_version"]
+            "rddmc_batch_graph_destroy", "rddmc_batch_autotune", "rddmc_cell_tau", "rddmc_fp_generate",
+            "rddmc_mlp_param_count", "rddmc_mlp_work_bytes", "rddmc_mlp_to_bf16", "rddmc_mlp_forward",
+            "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_status_string", "rddmc_version"]
 
 
 class GridDesc(ctypes.Structure):
@@ -67,6 +69,11 @@ class Tallies(ctypes.Structure):
                 ("nbins", ctypes.c_int32), ("nfaces", ctypes.c_int32), ("nsb", ctypes.c_int32)]
 
 
+class FpTrain(ctypes.Structure):
+    _fields_ = [("d_x", ctypes.c_void_p), ("d_ta", ctypes.c_void_p), ("d_tb", ctypes.c_void_p),
+                ("d_lk", ctypes.c_void_p), ("d_lp", ctypes.c_void_p), ("d_xc", ctypes.c_void_p)]
+
+
 class RDDMCError(RuntimeError):
     def __init__(self, fn: str, status: int):
         super().__init__(f"{fn} failed: {status} ({status_string(status)})")
@@ -97,6 +104,16 @@ def lib():
         L.rddmc_read_packet_states.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, vp, vp, vp]
         L.rddmc_launch_packets_noalloc.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp]
         L.rddmc_scatter_samples.argtypes = [vp, vp, ctypes.c_double, u64, u64, vp, vp]
+        L.rddmc_cell_tau.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+        L.rddmc_fp_generate.argtypes = [vp, vp, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp,
+                                        ctypes.POINTER(FpTrain), vp]
+        L.rddmc_mlp_param_count.argtypes = [i32]
+        L.rddmc_mlp_work_bytes.argtypes = [i32, i32]
+        L.rddmc_mlp_to_bf16.argtypes = [i32, vp, vp, vp]
+        L.rddmc_mlp_forward.argtypes = [i32, vp, vp, vp, i32, vp, vp, vp]
+        L.rddmc_mlp_loss_grad.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
+        L.rddmc_mlp_adam.argtypes = [i32, vp, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, vp]
         L.rddmc_batch_create.argtypes = [vp, vp, vp, i32, ctypes.POINTER(vp)]
         L.rddmc_batch_destroy.argtypes = [vp]
         L.rddmc_batch_destroy.restype = None
@@ -117,6 +134,8 @@ def lib():
             if name not in ("rddmc_destroy_grid", "rddmc_status_string", "rddmc_batch_destroy",
                             "rddmc_batch_graph_destroy"):
                 getattr(L, name).restype = ctypes.c_int
+        L.rddmc_mlp_param_count.restype = ctypes.c_uint64
+        L.rddmc_mlp_work_bytes.restype = ctypes.c_uint64
         _LIB = L
     return _LIB
 
@@ -394,3 +413,54 @@ class Batch:
                 lib().rddmc_batch_destroy(ctypes.c_void_p(self.h))
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- learned exit proposal
+def cell_tau(grid, d_table: int, cell: int, J: int, stream: int = 0) -> np.ndarray:
+    out = np.zeros(J, dtype=np.float32)
+    _check("rddmc_cell_tau", lib().rddmc_cell_tau(ctypes.c_void_p(grid), ctypes.c_void_p(d_table), int(cell),
+                                                  _np_ptr(out), ctypes.c_void_p(stream)))
+    return out
+
+
+def fp_generate(grids, d_tables, b, jlo, jhi, seed, p0, n, cap, d_out, d_steps, train=None, stream=0):
+    L = len(grids)
+    g = (ctypes.c_void_p * L)(*grids)
+    t = (ctypes.c_void_p * L)(*d_tables)
+    lo = np.ascontiguousarray(jlo, dtype=np.int32)
+    hi = np.ascontiguousarray(jhi, dtype=np.int32)
+    _check("rddmc_fp_generate", lib().rddmc_fp_generate(
+        g, t, int(L), int(b), _np_ptr(lo), _np_ptr(hi), int(seed), int(p0), int(n), int(cap), ctypes.c_void_p(d_out),
+        ctypes.c_void_p(d_steps), ctypes.byref(train) if train is not None else None, ctypes.c_void_p(stream)))
+
+
+def mlp_param_count(n_out: int) -> int:
+    return int(lib().rddmc_mlp_param_count(int(n_out)))
+
+
+def mlp_work_bytes(batch: int, n_out: int) -> int:
+    return int(lib().rddmc_mlp_work_bytes(int(batch), int(n_out)))
+
+
+def mlp_to_bf16(n_out, d_wf, d_wb, stream=0):
+    _check("rddmc_mlp_to_bf16", lib().rddmc_mlp_to_bf16(int(n_out), ctypes.c_void_p(d_wf), ctypes.c_void_p(d_wb),
+                                                        ctypes.c_void_p(stream)))
+
+
+def mlp_forward(n_out, d_wf, d_wb, d_x, batch, d_work, d_logits, stream=0):
+    _check("rddmc_mlp_forward", lib().rddmc_mlp_forward(int(n_out), ctypes.c_void_p(d_wf), ctypes.c_void_p(d_wb),
+                                                        ctypes.c_void_p(d_x), int(batch), ctypes.c_void_p(d_work),
+                                                        ctypes.c_void_p(d_logits), ctypes.c_void_p(stream)))
+
+
+def mlp_loss_grad(n_out, nA, nB, d_wf, d_wb, d_x, d_ta, d_tb, batch, d_work, d_grad, d_loss, stream=0):
+    _check("rddmc_mlp_loss_grad", lib().rddmc_mlp_loss_grad(
+        int(n_out), int(nA), int(nB), ctypes.c_void_p(d_wf), ctypes.c_void_p(d_wb), ctypes.c_void_p(d_x),
+        ctypes.c_void_p(d_ta), ctypes.c_void_p(d_tb), int(batch), ctypes.c_void_p(d_work), ctypes.c_void_p(d_grad),
+        ctypes.c_void_p(d_loss), ctypes.c_void_p(stream)))
+
+
+def mlp_adam(n_out, d_wf, d_wb, d_grad, d_m, d_v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+    _check("rddmc_mlp_adam", lib().rddmc_mlp_adam(
+        int(n_out), ctypes.c_void_p(d_wf), ctypes.c_void_p(d_wb), ctypes.c_void_p(d_grad), ctypes.c_void_p(d_m),
+        ctypes.c_void_p(d_v), int(step), float(lr), float(beta1), float(beta2), float(eps), ctypes.c_void_p(stream)))

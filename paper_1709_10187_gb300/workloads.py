@@ -136,3 +136,54 @@ def batched_instances(n: int = 512, seed: int = 0x5EED0004, packet_scale: float 
             w = Workload(f"batch{i}_slab", 1, (cells, 1, 1), J, -xmax, xmax, tau0, T, npk, seed + i)
         out.append(w)
     return out
+
+
+def gaussian_random_field(n: int, slope: float, rng) -> np.ndarray:
+    """Zero-mean, unit-variance Gaussian random field on an n^3 periodic grid
+    with power spectrum P(k) ~ k^slope (FFT of white noise shaped by
+    k^(slope/2); the k = 0 mode is dropped)."""
+    noise = rng.standard_normal((n, n, n))
+    fk = np.fft.rfftn(noise)
+    kx = np.fft.fftfreq(n)[:, None, None]
+    ky = np.fft.fftfreq(n)[None, :, None]
+    kz = np.fft.rfftfreq(n)[None, None, :]
+    k = np.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = np.zeros_like(k)
+    amp[k > 0] = k[k > 0] ** (slope / 2.0)
+    g = np.fft.irfftn(fk * amp, s=(n, n, n))
+    g -= g.mean()
+    return g / g.std()
+
+
+@dataclasses.dataclass(frozen=True)
+class ClumpyMedium:
+    """Brick-resolution clumpy medium: a lognormal density and a Gaussian
+    turbulent velocity, constant over bricks of `brick`^3 cells."""
+    workload: Workload
+    brick: int
+    n_rel: np.ndarray   # per cell, axis 0 fastest (mean 1)
+    v_kms: np.ndarray   # per cell x3
+    brick_rho: np.ndarray  # per brick (nb^3, axis 0 fastest)
+
+
+def clumpy_medium(n: int = 128, J: int = 256, x_max: float = 256.0, tau0: float = 1.0e7, T: float = 1.0e4,
+                  brick: int = 8, sigma_ln: float = 1.0, slope: float = -11.0 / 3.0, sigma_v_kms: float = 10.0,
+                  packets: int = 100_000_000, seed: int = 0x5EED0005, name: str = "clumpy") -> ClumpyMedium:
+    """The clumpy 3D workload: an n^3 cube of cells x J bins over [-x_max, x_max],
+    lognormal density rho = exp(sigma_ln g - sigma_ln^2/2) from a Gaussian
+    random field g with spectral slope `slope`, three independent fields of the
+    same spectrum for the velocity (sigma_v per component), both drawn on the
+    (n/brick)^3 grid of bricks and held constant inside each brick; tau0 is the
+    line-centre optical depth centre-to-face at the mean density."""
+    rng = np.random.default_rng(seed)
+    nb = n // brick
+    g = gaussian_random_field(nb, slope, rng)
+    rho_b = np.exp(sigma_ln * g - 0.5 * sigma_ln ** 2)
+    v_b = np.stack([sigma_v_kms * gaussian_random_field(nb, slope, rng) for _ in range(3)], axis=-1)
+    # (i2, i1, i0) index order of the brick fields -> per-cell arrays, axis 0 fastest
+    rep = lambda a: np.repeat(np.repeat(np.repeat(a, brick, axis=0), brick, axis=1), brick, axis=2)
+    rho_c = rep(rho_b)
+    v_c = np.stack([rep(v_b[..., a]) for a in range(3)], axis=-1)
+    w = Workload(name, 3, (n, n, n), J, -x_max, x_max, tau0, T, packets, seed)
+    return ClumpyMedium(w, brick, rho_c.reshape(-1).astype(np.float64), v_c.reshape(-1, 3).astype(np.float64),
+                        rho_b.reshape(-1).astype(np.float64))

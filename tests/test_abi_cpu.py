@@ -21,7 +21,7 @@ def built():
 
 def _declared():
     txt = open(os.path.join(ROOT, "include", "rddmc.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(rddmc_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|void|uint64_t|const char\*)\s+(rddmc_\w+)\s*\(", txt, re.M)))
 
 
 def test_library_exports_every_declared_symbol():

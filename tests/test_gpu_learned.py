@@ -1,0 +1,95 @@
+"""GPU checks of the learned exit proposal: first-passage data bit-exact against
+the oracle, the tensor-core network's loss and gradients against the FP64
+reference network, and training that learns the first-passage distribution."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import coracle as C  # noqa: E402
+from oracle import mlp as M  # noqa: E402
+from paper_1709_10187_gb300 import build as B  # noqa: E402
+from paper_1709_10187_gb300 import learned as Lr  # noqa: E402
+from paper_1709_10187_gb300 import rddmc as R  # noqa: E402
+from paper_1709_10187_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+# a small clumpy-medium target: 32^3 cells, 64 bins over [-64, 64], tau0 = 1e6
+TARGET = W.Workload("clumpy_small", 3, (32, 32, 32), 64, -64.0, 64.0, 1.0e6, 1.0e4, 1, 1)
+RHO = np.logspace(-1.5, 1.5, 8)
+
+
+@pytest.fixture(scope="module")
+def proposal():
+    B.build()
+    return Lr.ExitProposal(TARGET, 4, RHO, tau_lo=5.0, tau_hi=120.0)
+
+
+def test_first_passages_match_oracle_bit_exactly(proposal):
+    p = proposal
+    rows = []
+    for pb, rho in zip(p.problems, p.levels):
+        rows.append(C.interior_rows(pb.w))
+        thr, _ = pb.rows()
+        assert np.array_equal(thr.reshape(27, p.J, 7)[13], rows[-1][:, :7])
+    rows = np.stack(rows)
+    n = 3000
+    d = p.generate(n, seed=77, p0=1000)
+    out, steps = C.fp_samples(rows, p.b, p.jlo, p.jhi, 77, 1000, n, 10_000_000)
+    assert np.array_equal(d["rec"].cpu().numpy(), out)
+    assert np.array_equal(d["steps"].cpu().numpy().astype(np.uint64), steps)
+    tA = d["tA"].cpu().numpy()
+    ok = out[:, 2] < 6
+    assert np.array_equal(tA[ok], out[ok, 2] * p.J + out[ok, 3]) and np.all(tA[~ok] == -1)
+
+
+def test_network_loss_and_gradients_match_fp64_reference(proposal):
+    p = proposal
+    rng = np.random.default_rng(5)
+    Bsz = 256
+    d = p.generate(Bsz, seed=91)
+    X = d["X"]
+    tA, tB = d["tA"], d["tB"]
+    loss = p.loss_grad(X, tA, tB)
+    torch.cuda.synchronize()
+    g_gpu = p.grad.cpu().numpy().astype(np.float64)
+    w_bf = p.wb.float().cpu().numpy().astype(np.float64)   # the weights the tensor cores saw
+    w_f = p.wf.cpu().numpy().astype(np.float64)
+    # biases are applied in FP32 from the master copy
+    flat = w_bf.copy()
+    offs, off = [], 0
+    for (o, i) in M.shapes(p.n_out):
+        offs.append((off + o * i, o))
+        off += o * i + o
+    for s, o in offs:
+        flat[s:s + o] = w_f[s:s + o]
+    lo, g_ref = M.loss_and_grad(flat, p.n_out, p.nA, p.nB, X.float().cpu().numpy(), tA.cpu().numpy(),
+                                tB.cpu().numpy())
+    assert float(loss.item()) / Bsz == pytest.approx(lo, rel=1e-2)
+    off = 0
+    for (o, i) in M.shapes(p.n_out):
+        for size in (o * i, o):
+            a, b = g_gpu[off:off + size], g_ref[off:off + size]
+            assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-7, (off, np.linalg.norm(a - b),
+                                                                              np.linalg.norm(b))
+            off += size
+
+
+def test_training_learns_the_first_passage_distribution(proposal):
+    p = proposal
+    data = p.generate(400_000, seed=123)
+    held = p.generate(32_768, seed=124, p0=10_000_000)
+    before = p.mean_loss(held)
+    p.train(data, iters=600, batch=4096, lr=2e-3)
+    after = p.mean_loss(held)
+    assert after < before - 1.0, (before, after)
+    # exit-face marginal predicted vs empirical on held-out data
+    X = held["X"][:8192].contiguous()
+    logits = p.logits(X).cpu().numpy()[:, :p.nA].reshape(-1, 6, p.J)
+    pr = np.exp(logits - logits.max(axis=(1, 2), keepdims=True))
+    pr /= pr.sum(axis=(1, 2), keepdims=True)
+    pred_face = pr.sum(axis=2).mean(axis=0)
+    tA = held["tA"][:8192].cpu().numpy()
+    emp = np.bincount(tA[tA >= 0] // p.J, minlength=6) / max(1, (tA >= 0).sum())
+    assert 0.5 * np.abs(pred_face - emp).sum() < 0.05, (pred_face, emp)
