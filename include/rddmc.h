@@ -118,8 +118,12 @@ typedef struct rddmc_leak_params {
  *                 persistent grid of ctas_per_sm * #SM CTAs of threads_per_cta
  *                 threads (a multiple of 32, at most 256); `chunk` transitions
  *                 (multiple of 4) between warp refills.
- *   table_in_smem 1: stage the row table in shared memory when it fits;
- *                 0: gather rows from global memory (L1/L2).
+ *   table_in_smem 1: stage the fast row heads in shared memory when they fit;
+ *                 0: gather them from global memory (L1/L2).
+ *   proposal      NULL, or a learned exit proposal (rddmc_proposal; 3D grids in
+ *                 DDMC mode): packets entering an eligible brick are parked for
+ *                 rddmc_propose instead of walking through it.  Requires
+ *                 steps_per_launch > 0 or resume = 1 so parked states are kept.
  */
 typedef struct rddmc_run_opts {
     uint64_t seed;
@@ -132,6 +136,7 @@ typedef struct rddmc_run_opts {
     int32_t chunk;
     int32_t table_in_smem;
     int32_t reserved;
+    const struct rddmc_proposal* proposal;
 } rddmc_run_opts;
 
 /* Buffer sizes for a grid (from rddmc_grid_sizes). */
@@ -155,6 +160,8 @@ typedef struct rddmc_tallies {
     uint64_t conversions;  /* DDMC <-> MC hand-offs */
     uint64_t clamps;       /* Doppler rebins clamped to the frequency grid ends */
     uint64_t event_draws;  /* words taken from the packets' event streams */
+    uint64_t proposals;    /* learned exit proposals taken */
+    uint64_t proposed_steps; /* DDMC transitions the proposals stood in for (sampled) */
     int32_t status;        /* RDDMC_OK or a device-side error code */
     int32_t nbins;         /* J; the histogram has J + 2 entries */
     int32_t nfaces;        /* 2 (slab) or 6 (3D) */
@@ -391,6 +398,35 @@ typedef struct rddmc_fp_train {
 int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_tables, int L, int b, const int32_t* jlo,
                       const int32_t* jhi, uint64_t seed, uint64_t p0, uint64_t n, uint64_t cap, int32_t* d_out,
                       uint64_t* d_steps, const rddmc_fp_train* train, void* stream);
+
+/* A trained proposal attached to a walk (all arrays on the device).  The grid
+ * is cut into bricks of `brick`^3 cells (cells per axis a multiple of brick);
+ * brick B with brick_lk[B] = log10(k0 dz) of its (uniform) medium, or below
+ * -1e29 when it is not eligible, takes proposals for packets that enter it at
+ * a bin j with log_tau_lo <= brick_lk[B] + lp[j] <= log_tau_hi.  The queue
+ * holds the parked packets (count, ids, entry faces; capacity n_packets). */
+typedef struct rddmc_proposal {
+    int32_t brick;
+    int32_t reserved;
+    const float* d_brick_lk;
+    const float* d_lp;
+    const float* d_xc;
+    double log_tau_lo, log_tau_hi;
+    unsigned long long* d_queue_count;
+    unsigned long long* d_queue_pid;
+    int32_t* d_queue_face;
+} rddmc_proposal;
+
+/* Serve the parked packets of a walk with the trained network: features,
+ * tensor-core forward pass in batches of `batch` (a multiple of 64; d_work of
+ * rddmc_mlp_work_bytes(batch, n_out) plus batch * (16 * 2 + n_out * 4)
+ * bytes), one exit (face, bin, step bucket) sampled per packet from its event
+ * stream, mirrored back for negative frequencies, placed across the exit face
+ * (Doppler rebin or escape tally as the face's row says), and the packet set in
+ * flight again.  Clears the queue.  Synchronises `stream`. */
+int rddmc_propose(const rddmc_grid* grid, const void* d_table, const rddmc_proposal* proposal, uint64_t seed,
+                  uint64_t n_packets, void* d_state, void* d_tallies, int n_out, int nA, int nB, const float* d_wf,
+                  const void* d_wb, int batch, void* d_work, uint64_t* n_served, void* stream);
 
 /* The network: 16 inputs, three hidden layers of 128 (ReLU), n_out logits (a
  * multiple of 16): head A = logits [0, nA) (softmax over exit face x bin),

@@ -327,6 +327,14 @@ int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_r
     if (o->chunk < 0 || o->chunk % 4 != 0 || o->ctas_per_sm < 0 || o->threads_per_cta < 0) return RDDMC_ERR_ARG;
     if (o->threads_per_cta && (o->threads_per_cta % 32 != 0 || o->threads_per_cta > 256)) return RDDMC_ERR_ARG;
     if (o->resume != 0 && o->resume != 1) return RDDMC_ERR_ARG;
+    if (o->proposal) {
+        const rddmc_proposal* pr = o->proposal;
+        if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
+        if (o->steps_per_launch == 0 && o->resume == 0) return RDDMC_ERR_ARG;
+        if (pr->brick < 1 || g->n[0] % pr->brick || g->n[1] % pr->brick || g->n[2] % pr->brick) return RDDMC_ERR_ARG;
+        if (!pr->d_brick_lk || !pr->d_lp || !pr->d_xc || !pr->d_queue_count || !pr->d_queue_pid || !pr->d_queue_face)
+            return RDDMC_ERR_ARG;
+    }
     if (state_bytes < state_bytes_for(o->n_packets)) return RDDMC_ERR_SIZE;
     if (tally_bytes < tally_bytes_for(g->J)) return RDDMC_ERR_SIZE;
     WalkLaunch w{d_table, d_state, (unsigned long long*)d_tallies, *o};
@@ -349,6 +357,8 @@ int rddmc_read_tallies(const rddmc_grid* g, const void* d_tallies, rddmc_tallies
     out->conversions = t[C_CONVERSIONS];
     out->clamps = t[C_CLAMPS];
     out->event_draws = t[C_EVENT_DRAWS];
+    out->proposals = t[C_PROPOSALS];
+    out->proposed_steps = t[C_PROPOSED_STEPS];
     out->status = RDDMC_OK;
     if (t[C_ABORTED]) out->status = RDDMC_ERR_STEP_LIMIT;
     if (t[C_STATUS_BITS] & STATUS_UNSUPPORTED_EVENT) out->status = RDDMC_ERR_UNSUPPORTED;

@@ -35,7 +35,8 @@ constexpr float kUparStep = 1.0f / 16.0f;
 
 enum Counter : int {
     C_EMITTED = 0, C_ESCAPED = 1, C_ABORTED = 2, C_STEPS = 3, C_MC_EVENTS = 4,
-    C_CONVERSIONS = 5, C_CLAMPS = 6, C_EVENT_DRAWS = 7, C_STATUS_BITS = 8,
+    C_CONVERSIONS = 5, C_CLAMPS = 6, C_EVENT_DRAWS = 7, C_STATUS_BITS = 8, C_PROPOSALS = 9,
+    C_PROPOSED_STEPS = 10,
 };
 
 // 2-bit actions per outcome in the flags word.
@@ -47,7 +48,7 @@ constexpr uint32_t FLAG_THIN = 1u << 31;
 // Device-side status bits (C_STATUS_BITS).
 constexpr uint64_t STATUS_UNSUPPORTED_EVENT = 1ull << 0;
 
-enum PacketStatus : uint8_t { PK_FRESH = 0, PK_INFLIGHT = 1, PK_DONE = 2 };
+enum PacketStatus : uint8_t { PK_FRESH = 0, PK_INFLIGHT = 1, PK_DONE = 2, PK_PARKED = 3 };
 
 struct FaceDesc {
     int32_t exterior;   // 1: the neighbour is outside the grid or vacuum

@@ -22,9 +22,12 @@
 // registers for counters, warp-aggregated (__match_any_sync) shared-memory
 // atomics for the escape histograms and faces, flushed to the u64 tally buffer
 // in global memory when the CTA finishes.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "grid.h"
+#include "learned_common.cuh"
 #include "mc.cuh"
 
 namespace rddmc {
@@ -64,6 +67,14 @@ struct WalkParams {
     int n[3];
     float a, lambda;
     int src_ncand[3], src_cand[3][2], src_nbin, src_bin[2];
+    // learned exit proposal (3D DDMC): bricks of prop_b^3 cells
+    int prop_b, prop_nbx, prop_nby;
+    const float* prop_lk;
+    const float* prop_lp;
+    float prop_llo, prop_lhi;
+    unsigned long long* prop_qcount;
+    unsigned long long* prop_qpid;
+    int* prop_qface;
 };
 
 // Philox4x32-10 with precomputed round keys (held in the kernel's parameter bank).
@@ -346,7 +357,13 @@ __device__ __noinline__ McResult mc_excursion(const WalkParams& P, unsigned cell
     return res;
 }
 
-template <int NDIM, bool SMEM_ROWS, bool HYBRID>
+__device__ __forceinline__ unsigned brick_of(const WalkParams& P, unsigned cell) {
+    const unsigned i0 = cell % (unsigned)P.n0, i1 = (cell / (unsigned)P.n0) % (unsigned)P.n[1],
+                   i2 = cell / (unsigned)P.n01, b = (unsigned)P.prop_b;
+    return i0 / b + (unsigned)P.prop_nbx * (i1 / b + (unsigned)P.prop_nby * (i2 / b));
+}
+
+template <int NDIM, bool SMEM_ROWS, bool HYBRID, bool PROPOSE>
 __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const WalkParams P) {
     constexpr int RW = NDIM == 1 ? 1 : 2;  // uint4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -374,6 +391,8 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
     unsigned cell = 0, cls = 0, s = 0;  // s = cls * J + bin: the row of the state
     unsigned long long n_steps = 0, n_edraw = 0, n_mc = 0;
     unsigned n_emit = 0, n_esc = 0, n_abort = 0, n_clamp = 0, status_bits = 0, n_conv = 0;
+    bool parked = false;   // the packet entered an eligible brick and waits for a proposal
+    int park_face = 0;
 
     // Outcome of an MC excursion: back to DDMC (returns false) or finished.
     auto after_mc = [&](const McResult& res) -> bool {
@@ -447,9 +466,25 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         }
         const unsigned ax = face >> 1;
         const unsigned stride = NDIM == 1 ? 1u : (ax == 0 ? 1u : (ax == 1 ? (unsigned)P.n0 : (unsigned)P.n01));
+        const unsigned old_cell = cell;
         cell = min((face & 1u) ? cell + stride : cell - stride, (unsigned)P.ncell - 1u);
         cls = __ldg(&P.cell_class[cell]);
         s = cls * J + nbin;
+        if (PROPOSE) {
+            // entering a new brick: park for a proposal when the brick and bin qualify
+            const unsigned bn = brick_of(P, cell);
+            if (bn != brick_of(P, old_cell)) {
+                const float lkb = __ldg(&P.prop_lk[bn]);
+                if (lkb > -1.0e29f) {
+                    const float l = lkb + __ldg(&P.prop_lp[min(nbin, J - 1u)]);
+                    if (l >= P.prop_llo && l <= P.prop_lhi) {
+                        parked = true;
+                        park_face = (int)(face ^ 1u);  // the brick face the packet came through
+                        return true;
+                    }
+                }
+            }
+        }
         return false;
     };
 
@@ -569,7 +604,18 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
     chunk_done:
         n_steps += t - t0;
         n_edraw += e - e0;
-        if (fin) {
+        if (PROPOSE && parked) {
+            P.st_cell[pid] = cell;
+            P.st_bin[pid] = min(s - cls * J, J - 1u);
+            P.st_t[pid] = t;
+            P.st_e[pid] = e;
+            P.st_status[pid] = PK_PARKED;
+            const unsigned long long k = atomicAdd(P.prop_qcount, 1ull);
+            P.prop_qpid[k] = pid;
+            P.prop_qface[k] = park_face;
+            parked = false;
+            have = false;
+        } else if (fin) {
             have = false;
             if (P.save_state) P.st_status[pid] = PK_DONE;
         } else if (t >= P.max_steps) {
@@ -622,24 +668,26 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         if (s_sb[i]) atomicAdd(&P.tally[kHistOff + nhist + i], s_sb[i]);
 }
 
-template <int NDIM, bool SMEM, bool HYBRID>
+template <int NDIM, bool SMEM, bool HYBRID, bool PROPOSE>
 cudaError_t launch_variant(const WalkParams& P, int threads, size_t smem, int ctas, int nsm, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<NDIM, SMEM, HYBRID>,
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<NDIM, SMEM, HYBRID, PROPOSE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (!ctas) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, walk_kernel<NDIM, SMEM, HYBRID>, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, walk_kernel<NDIM, SMEM, HYBRID, PROPOSE>, threads,
+                                                          smem);
         if (e != cudaSuccess) return e;
     }
     if (ctas < 1) ctas = 1;
-    walk_kernel<NDIM, SMEM, HYBRID><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P);
+    walk_kernel<NDIM, SMEM, HYBRID, PROPOSE><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P);
     return cudaGetLastError();
 }
 
 template <int NDIM, bool SMEM>
 cudaError_t launch_mode(const WalkParams& P, int threads, size_t smem, int ctas, int nsm, cudaStream_t s) {
-    return P.hybrid ? launch_variant<NDIM, SMEM, true>(P, threads, smem, ctas, nsm, s)
-                    : launch_variant<NDIM, SMEM, false>(P, threads, smem, ctas, nsm, s);
+    if (NDIM == 3 && P.prop_b) return launch_variant<NDIM, SMEM, false, true>(P, threads, smem, ctas, nsm, s);
+    return P.hybrid ? launch_variant<NDIM, SMEM, true, false>(P, threads, smem, ctas, nsm, s)
+                    : launch_variant<NDIM, SMEM, false, false>(P, threads, smem, ctas, nsm, s);
 }
 
 // One scattering per thread at x_in with incoming direction +e_z; sample i
@@ -654,6 +702,122 @@ __global__ void scatter_samples_kernel(float a, float x_in, const float2* __rest
     out[i] = scatter(a, x_in, d, upar, es);
 }
 
+// ------------------------------------------------------------ proposals
+// Network inputs of queued packets q0 .. q0+cnt (rows past cnt are zeroed).
+// Negative frequencies are mirrored: a static uniform brick is symmetric under
+// x -> -x and the network was trained on x >= 0.
+__global__ void propose_features_kernel(const WalkParams P, const float* __restrict__ xc, FeatConst fc,
+                                        unsigned long long q0, unsigned long long cnt, int batch,
+                                        __nv_bfloat16* __restrict__ X) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= batch) return;
+    if ((unsigned long long)r >= cnt) {
+        for (int i = 0; i < kFeat; ++i) X[r * kFeat + i] = __float2bfloat16(0.0f);
+        return;
+    }
+    const unsigned long long pid = P.prop_qpid[q0 + r];
+    const unsigned cell = min(P.st_cell[pid], (unsigned)P.ncell - 1u);
+    unsigned j = min(P.st_bin[pid], (unsigned)P.J - 1u);
+    if (xc[j] < 0.0f) j = (unsigned)P.J - 1u - j;
+    features(P.prop_lk[brick_of(P, cell)], P.prop_lp[j], xc[j], fc, X + r * kFeat);
+}
+
+// Sample an exit for each queued packet from its logits and place the packet
+// across the exit face; one thread per packet.
+__global__ void propose_place_kernel(const WalkParams P, const float* __restrict__ xc,
+                                     const float* __restrict__ logits, int n_out, int nA, int nB,
+                                     unsigned long long q0, unsigned long long cnt) {
+    const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= cnt) return;
+    const unsigned J = (unsigned)P.J;
+    const unsigned long long pid = P.prop_qpid[q0 + r];
+    const int ef = P.prop_qface[q0 + r];
+    const unsigned cell = min(P.st_cell[pid], (unsigned)P.ncell - 1u);
+    const unsigned bin = min(P.st_bin[pid], J - 1u);
+    const bool mirror = xc[bin] < 0.0f;
+    EventStream es;
+    es.init(pid, P.st_e[pid], P.k0, P.k1);
+    const unsigned long long e_start = es.e;
+    const float* z = logits + r * (unsigned long long)n_out;
+    // head A: exit face (canonical: 0 entry face, 1 opposite, 2-5 sides) x exit bin
+    float mx = -3.0e38f;
+    for (int c = 0; c < nA; ++c) mx = fmaxf(mx, z[c]);
+    float sum = 0.0f;
+    for (int c = 0; c < nA; ++c) sum += __expf(z[c] - mx);
+    float u = es.u01() * sum, acc = 0.0f;
+    int ca = nA - 1;
+    for (int c = 0; c < nA; ++c) {
+        acc += __expf(z[c] - mx);
+        if (acc >= u) { ca = c; break; }
+    }
+    // head B: log2 step bucket
+    mx = -3.0e38f;
+    for (int c = 0; c < nB; ++c) mx = fmaxf(mx, z[nA + c]);
+    sum = 0.0f;
+    for (int c = 0; c < nB; ++c) sum += __expf(z[nA + c] - mx);
+    u = es.u01() * sum;
+    acc = 0.0f;
+    int kb = nB - 1;
+    for (int c = 0; c < nB; ++c) {
+        acc += __expf(z[nA + c] - mx);
+        if (acc >= u) { kb = c; break; }
+    }
+    kb = min(kb, 40);
+    const unsigned long long steps = (1ull << kb) + (unsigned long long)(es.u01() * (float)(1ull << kb));
+    const int fc_ = ca / (int)J;
+    unsigned jo = (unsigned)(ca % (int)J);
+    if (mirror) jo = J - 1u - jo;
+    const int ea = ef >> 1;
+    int f;
+    if (fc_ == 0) f = ef;
+    else if (fc_ == 1) f = ef ^ 1;
+    else if (fc_ < 4) f = 2 * ((ea + 1) % 3) + (fc_ - 2);
+    else f = 2 * ((ea + 2) % 3) + (fc_ - 4);
+    // the cell on the exit face (uniform over the face) and the crossing
+    const unsigned b = (unsigned)P.prop_b;
+    const unsigned ic[3] = {cell % (unsigned)P.n0, (cell / (unsigned)P.n0) % (unsigned)P.n[1], cell / (unsigned)P.n01};
+    unsigned ci[3];
+    const int fa = f >> 1, fs = f & 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ci[a] = (ic[a] / b) * b;
+    ci[fa] += fs ? b - 1u : 0u;
+    for (int a = 0; a < 3; ++a)
+        if (a != fa) ci[a] += min((unsigned)(es.u01() * (float)b), b - 1u);
+    const unsigned cin = min(ci[0] + (unsigned)P.n0 * ci[1] + (unsigned)P.n01 * ci[2], (unsigned)P.ncell - 1u);
+    const unsigned cls = min(__ldg(&P.cell_class[cin]), (unsigned)P.n_class - 1u);
+    const uint4 a0 = __ldg(&P.rows[(cls * J + jo) * 2u]);
+    const unsigned act = (a0.w >> (2u * (2u + (unsigned)f))) & 3u;
+    unsigned long long* T = P.tally;
+    if (act == ACT_ESCAPE) {
+        const EscapeBins eb = escape_bins<3>(P, cin, jo, (unsigned)f, pid, es.e, (a0.w & FLAG_MOVING) != 0u);
+        es.e += 5;
+        atomicAdd(&T[kHistOff + eb.hist], 1ull);
+        atomicAdd(&T[kFaceOff + f], 1ull);
+        if (eb.sb >= 0) atomicAdd(&T[kHistOff + P.J + 2 + eb.sb], 1ull);
+        atomicAdd(&T[C_ESCAPED], 1ull);
+        P.st_status[pid] = PK_DONE;
+    } else {
+        unsigned j2 = jo;
+        if (act == ACT_REBIN) {
+            const Rebin rb = P.rebin[cls * 6u + (unsigned)f];
+            const unsigned w1 = es.next();
+            int jn = (int)jo + rb.m + (w1 >= rb.thr ? 1 : 0);
+            if (jn < 0) { jn = 0; atomicAdd(&T[C_CLAMPS], 1ull); }
+            if (jn > (int)J - 1) { jn = (int)J - 1; atomicAdd(&T[C_CLAMPS], 1ull); }
+            j2 = (unsigned)jn;
+        }
+        const unsigned stride = fa == 0 ? 1u : (fa == 1 ? (unsigned)P.n0 : (unsigned)P.n01);
+        const unsigned nb = min(fs ? cin + stride : cin - stride, (unsigned)P.ncell - 1u);
+        P.st_cell[pid] = nb;
+        P.st_bin[pid] = j2;
+        P.st_status[pid] = PK_INFLIGHT;
+    }
+    P.st_e[pid] = es.e;
+    atomicAdd(&T[C_PROPOSALS], 1ull);
+    atomicAdd(&T[C_PROPOSED_STEPS], steps);
+    atomicAdd(&T[C_EVENT_DRAWS], es.e - e_start);
+}
+
 }  // namespace
 
 cudaError_t launch_scatter_samples(const rddmc_grid& g, const void* d_table, double x_in, uint64_t seed, uint64_t n,
@@ -665,11 +829,10 @@ cudaError_t launch_scatter_samples(const rddmc_grid& g, const void* d_table, dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s) {
+void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     const rddmc_run_opts& o = w.opts;
     const char* tb = (const char*)w.d_table;
     char* sb = (char*)w.d_state;
-    WalkParams P;
     std::memset(&P, 0, sizeof(P));
     P.rows = (const uint4*)(tb + g.off_rows);
     P.fast = (const uint2*)(tb + g.off_fast);
@@ -725,6 +888,26 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     P.src_nbin = g.src_nbin;
     P.src_bin[0] = g.src_bin[0];
     P.src_bin[1] = g.src_bin[1];
+    if (o.proposal) {
+        const rddmc_proposal* pr = o.proposal;
+        P.prop_b = pr->brick;
+        P.prop_nbx = g.n[0] / pr->brick;
+        P.prop_nby = g.n[1] / pr->brick;
+        P.prop_lk = pr->d_brick_lk;
+        P.prop_lp = pr->d_lp;
+        P.prop_llo = (float)pr->log_tau_lo;
+        P.prop_lhi = (float)pr->log_tau_hi;
+        P.prop_qcount = pr->d_queue_count;
+        P.prop_qpid = pr->d_queue_pid;
+        P.prop_qface = pr->d_queue_face;
+        P.save_state = 1;
+    }
+}
+
+cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s) {
+    const rddmc_run_opts& o = w.opts;
+    WalkParams P;
+    fill_walk_params(g, w, P);
 
     int dev = 0, nsm = 0, smem_optin = 0;
     cudaError_t e;
@@ -747,3 +930,53 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
 }
 
 }  // namespace rddmc
+
+extern "C" int rddmc_mlp_forward(int n_out, const float* d_wf, const void* d_wb, const void* d_x, int batch,
+                                 void* d_work, float* d_logits, void* stream);
+extern "C" uint64_t rddmc_mlp_work_bytes(int batch, int n_out);
+
+extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rddmc_proposal* pr, uint64_t seed,
+                             uint64_t n_packets, void* d_state, void* d_tallies, int n_out, int nA, int nB,
+                             const float* d_wf, const void* d_wb, int batch, void* d_work, uint64_t* n_served,
+                             void* stream) {
+    using namespace rddmc;
+    if (!g || !d_table || !pr || !d_state || !d_tallies || !d_wf || !d_wb || !d_work) return RDDMC_ERR_ARG;
+    if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
+    if (batch < 64 || batch % 64 || nA != 6 * g->J || nB < 1 || nA + nB > n_out || n_out % 16) return RDDMC_ERR_ARG;
+    if (pr->brick < 1 || g->n[0] % pr->brick || g->n[1] % pr->brick || g->n[2] % pr->brick) return RDDMC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    WalkLaunch w;
+    std::memset(&w, 0, sizeof(w));
+    w.d_table = d_table;
+    w.d_state = d_state;
+    w.d_tally = (unsigned long long*)d_tallies;
+    w.opts.seed = seed;
+    w.opts.n_packets = n_packets;
+    w.opts.proposal = pr;
+    w.opts.steps_per_launch = 4;
+    WalkParams P;
+    fill_walk_params(*g, w, P);
+    unsigned long long cnt = 0;
+    if (cudaMemcpyAsync(&cnt, pr->d_queue_count, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return RDDMC_ERR_CUDA;
+    const uint64_t mlp_bytes = align256(rddmc_mlp_work_bytes(batch, n_out));
+    __nv_bfloat16* X = (__nv_bfloat16*)((char*)d_work + mlp_bytes);
+    float* logits = (float*)((char*)X + align256((uint64_t)batch * kFeat * 2));
+    FeatConst fc;
+    fc.log_b = log10f((float)pr->brick);
+    fc.log_a = (float)log10(g->a);
+    fc.inv_xs = (float)(1.0 / std::max(std::fabs(g->edges.front()), std::fabs(g->edges.back())));
+    for (unsigned long long q0 = 0; q0 < cnt; q0 += (unsigned long long)batch) {
+        const unsigned long long c = std::min<unsigned long long>(batch, cnt - q0);
+        propose_features_kernel<<<(batch + 127) / 128, 128, 0, s>>>(P, pr->d_xc, fc, q0, c, batch, X);
+        if (cudaGetLastError() != cudaSuccess) return RDDMC_ERR_CUDA;
+        const int rc = rddmc_mlp_forward(n_out, d_wf, d_wb, X, batch, d_work, logits, stream);
+        if (rc != RDDMC_OK) return rc;
+        propose_place_kernel<<<(unsigned)((c + 127) / 128), 128, 0, s>>>(P, pr->d_xc, logits, n_out, nA, nB, q0, c);
+        if (cudaGetLastError() != cudaSuccess) return RDDMC_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(pr->d_queue_count, 0, 8, s) != cudaSuccess) return RDDMC_ERR_CUDA;
+    if (n_served) *n_served = cnt;
+    return cudaStreamSynchronize(s) == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+}

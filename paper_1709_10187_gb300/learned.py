@@ -149,3 +149,52 @@ class ExitProposal:
         R.mlp_forward(self.n_out, self.wf.data_ptr(), self.wb.data_ptr(), X.data_ptr(), B, work.data_ptr(),
                       out.data_ptr(), self.stream())
         return out
+
+
+    # ------------------------------------------------------------------ walking with the proposal
+    def attach(self, problem, brick_rho, batch: int = 4096):
+        """Proposal state for walking `problem` (its grid cut into bricks of
+        self.b^3 cells with per-brick density brick_rho, brick index axis 0
+        fastest).  Bricks whose density lies outside the trained levels take no
+        proposals."""
+        torch = self.torch
+        kdz = problem.w.tau0 / problem.w.R * np.asarray(brick_rho, dtype=np.float64) * self.dz
+        lk = np.log10(kdz)
+        lo, hi = np.log10(min(self.levels)), np.log10(max(self.levels))
+        rho = np.asarray(brick_rho, dtype=np.float64)
+        lk = np.where((np.log10(rho) >= lo) & (np.log10(rho) <= hi), lk, -1.0e30).astype(np.float32)
+        n = max(problem.state_packets, 1)
+        att = dict(
+            lk=torch.as_tensor(lk, device=self.device),
+            count=torch.zeros(1, dtype=torch.int64, device=self.device),
+            batch=batch,
+            work=torch.empty(R.mlp_work_bytes(batch, self.n_out) + 256 + batch * 32 + 256 + batch * self.n_out * 4
+                             + 4096, dtype=torch.uint8, device=self.device))
+        return att
+
+    def run(self, problem, brick_rho, n_packets: int, seed: int, steps_per_launch: int = 4096, batch: int = 4096,
+            tau_lo: float = 5.0, tau_hi: float = 200.0, max_epochs: int = 100_000) -> dict:
+        """Walk n_packets on `problem` with proposals; returns the tallies and
+        the number of walk launches and proposal rounds."""
+        torch = self.torch
+        problem.ensure_state(n_packets)
+        att = self.attach(problem, brick_rho, batch)
+        qpid = torch.empty(n_packets, dtype=torch.int64, device=self.device)
+        qface = torch.empty(n_packets, dtype=torch.int32, device=self.device)
+        prop = R.Proposal(self.b, 0, att["lk"].data_ptr(), self.lp.data_ptr(), self.xc.data_ptr(), np.log10(tau_lo),
+                          np.log10(tau_hi), att["count"].data_ptr(), qpid.data_ptr(), qface.data_ptr())
+        problem.reset()
+        launches = rounds = served = 0
+        for ep in range(max_epochs):
+            problem.launch(n_packets, seed, steps_per_launch=steps_per_launch, resume=1 if ep else 0, proposal=prop)
+            launches += 1
+            k = R.propose(problem.grid, problem.table.data_ptr(), prop, seed, n_packets, problem.state.data_ptr(),
+                          problem.tally.data_ptr(), self.n_out, self.nA, self.nB, self.wf.data_ptr(),
+                          self.wb.data_ptr(), batch, att["work"].data_ptr(), problem.stream())
+            served += k
+            rounds += 1 if k else 0
+            t = problem.read()
+            if t["escaped"] + t["aborted"] >= n_packets:
+                break
+        t["launches"], t["rounds"], t["served"] = launches, rounds, served
+        return t

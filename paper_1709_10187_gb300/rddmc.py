@@ -34,7 +34,7 @@ EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc
             "rddmc_batch_launch", "rddmc_batch_read_tallies", "rddmc_batch_graph_create", "rddmc_batch_graph_launch",
             "rddmc_batch_graph_destroy", "rddmc_batch_autotune", "rddmc_cell_tau", "rddmc_fp_generate",
             "rddmc_mlp_param_count", "rddmc_mlp_work_bytes", "rddmc_mlp_to_bf16", "rddmc_mlp_forward",
-            "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_status_string", "rddmc_version"]
+            "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_propose", "rddmc_status_string", "rddmc_version"]
 
 
 class GridDesc(ctypes.Structure):
@@ -53,7 +53,7 @@ class RunOpts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("n_packets", ctypes.c_uint64), ("max_steps", ctypes.c_uint64),
                 ("steps_per_launch", ctypes.c_uint64), ("resume", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("chunk", ctypes.c_int32), ("table_in_smem", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("proposal", ctypes.c_void_p)]
 
 
 class Sizes(ctypes.Structure):
@@ -65,13 +65,21 @@ class Sizes(ctypes.Structure):
 class Tallies(ctypes.Structure):
     _fields_ = [("emitted", ctypes.c_uint64), ("escaped", ctypes.c_uint64), ("aborted", ctypes.c_uint64),
                 ("steps", ctypes.c_uint64), ("mc_events", ctypes.c_uint64), ("conversions", ctypes.c_uint64),
-                ("clamps", ctypes.c_uint64), ("event_draws", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("clamps", ctypes.c_uint64), ("event_draws", ctypes.c_uint64), ("proposals", ctypes.c_uint64),
+                ("proposed_steps", ctypes.c_uint64), ("status", ctypes.c_int32),
                 ("nbins", ctypes.c_int32), ("nfaces", ctypes.c_int32), ("nsb", ctypes.c_int32)]
 
 
 class FpTrain(ctypes.Structure):
     _fields_ = [("d_x", ctypes.c_void_p), ("d_ta", ctypes.c_void_p), ("d_tb", ctypes.c_void_p),
                 ("d_lk", ctypes.c_void_p), ("d_lp", ctypes.c_void_p), ("d_xc", ctypes.c_void_p)]
+
+
+class Proposal(ctypes.Structure):
+    _fields_ = [("brick", ctypes.c_int32), ("reserved", ctypes.c_int32), ("d_brick_lk", ctypes.c_void_p),
+                ("d_lp", ctypes.c_void_p), ("d_xc", ctypes.c_void_p), ("log_tau_lo", ctypes.c_double),
+                ("log_tau_hi", ctypes.c_double), ("d_queue_count", ctypes.c_void_p), ("d_queue_pid", ctypes.c_void_p),
+                ("d_queue_face", ctypes.c_void_p)]
 
 
 class RDDMCError(RuntimeError):
@@ -107,6 +115,8 @@ def lib():
         L.rddmc_cell_tau.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
         L.rddmc_fp_generate.argtypes = [vp, vp, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp,
                                         ctypes.POINTER(FpTrain), vp]
+        L.rddmc_propose.argtypes = [vp, vp, ctypes.POINTER(Proposal), u64, u64, vp, vp, i32, i32, i32, vp, vp, i32, vp,
+                                    ctypes.POINTER(ctypes.c_uint64), vp]
         L.rddmc_mlp_param_count.argtypes = [i32]
         L.rddmc_mlp_work_bytes.argtypes = [i32, i32]
         L.rddmc_mlp_to_bf16.argtypes = [i32, vp, vp, vp]
@@ -291,10 +301,11 @@ class Problem:
         reset_tallies(self.grid, self.tally.data_ptr(), self.tally.numel() * 8, self.stream())
 
     def launch(self, n_packets: int, seed: int, max_steps: int = 0, steps_per_launch: int = 0, resume: int = 0,
-               ctas_per_sm: int = 0, threads_per_cta: int = 0, chunk: int = 0, table_in_smem: int = 0):
+               ctas_per_sm: int = 0, threads_per_cta: int = 0, chunk: int = 0, table_in_smem: int = 0,
+               proposal: "Proposal" = None):
         st = self.ensure_state(n_packets)
         o = RunOpts(seed, n_packets, max_steps, steps_per_launch, resume, ctas_per_sm, threads_per_cta, chunk,
-                    table_in_smem, 0)
+                    table_in_smem, 0, ctypes.addressof(proposal) if proposal is not None else None)
         launch_packets(self.grid, self.table.data_ptr(), o, st.data_ptr(), st.numel(), self.tally.data_ptr(),
                        self.tally.numel() * 8, self.stream())
 
@@ -464,3 +475,13 @@ def mlp_adam(n_out, d_wf, d_wb, d_grad, d_m, d_v, step, lr, beta1=0.9, beta2=0.9
     _check("rddmc_mlp_adam", lib().rddmc_mlp_adam(
         int(n_out), ctypes.c_void_p(d_wf), ctypes.c_void_p(d_wb), ctypes.c_void_p(d_grad), ctypes.c_void_p(d_m),
         ctypes.c_void_p(d_v), int(step), float(lr), float(beta1), float(beta2), float(eps), ctypes.c_void_p(stream)))
+
+
+def propose(grid, d_table, proposal: Proposal, seed, n_packets, d_state, d_tallies, n_out, nA, nB, d_wf, d_wb, batch,
+            d_work, stream=0) -> int:
+    served = ctypes.c_uint64()
+    _check("rddmc_propose", lib().rddmc_propose(
+        ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(proposal), int(seed), int(n_packets),
+        ctypes.c_void_p(d_state), ctypes.c_void_p(d_tallies), int(n_out), int(nA), int(nB), ctypes.c_void_p(d_wf),
+        ctypes.c_void_p(d_wb), int(batch), ctypes.c_void_p(d_work), ctypes.byref(served), ctypes.c_void_p(stream)))
+    return served.value
