@@ -121,8 +121,8 @@ typedef struct rddmc_leak_params {
  *   table_in_smem 1: stage the fast row heads in shared memory when they fit;
  *                 0: gather them from global memory (L1/L2).
  *   proposal      NULL, or a learned exit proposal (rddmc_proposal; 3D grids in
- *                 DDMC mode): packets entering an eligible brick are parked for
- *                 rddmc_propose instead of walking through it.  Requires
+ *                 DDMC mode): packets in a state it serves are parked for
+ *                 rddmc_propose instead of walking through their brick.  Requires
  *                 steps_per_launch > 0 or resume = 1 so parked states are kept.
  */
 typedef struct rddmc_run_opts {
@@ -384,53 +384,74 @@ typedef struct rddmc_fp_train {
     const float* d_lk;      /* [L] log10(k0 dz) of each level's medium */
     const float* d_lp;      /* [J] log10 of the bin-mean profile (k_j / k0) */
     const float* d_xc;      /* [J] bin-centre frequencies */
+    int32_t* d_tc;          /* [n] exit face * b^2 + exit position, -1 on a cap; may be NULL */
 } rddmc_fp_train;
 
-/* First passages through a uniform b^3 brick.  Level l uses the rows of the
- * centre (interior) cell of grids[l] (3D, DDMC mode, precomputed in
- * d_tables[l]; all levels share J).  Sample i (packet id p0+i under `seed`):
- * event word 0 picks the level (floor(w L / 2^32)), word 1 the entry bin in
- * [jlo[l], jhi[l]], words 2-3 the entry cell on the -x face; transitions
- * follow the walk's stream contract until a spatial move leaves the brick or
- * `cap` transitions are taken.  d_out: 4 int32 per sample {level, entry bin,
- * exit face (0..5: -x,+x,-y,+y,-z,+z; 6 = cap), exit bin}; d_steps: uint64
- * transitions.  train (may be NULL): also write network inputs and targets. */
+/* First passages through a uniform b^3 brick (1 <= b <= 64), the training data
+ * of the learned exit proposal (an extension beyond the paper: a learned
+ * stand-in for many DDMC transitions, Sec. 2.3, inside thick regions).
+ * Level l uses the rows of the centre (interior) cell of grids[l] (3D, DDMC
+ * mode, precomputed in d_tables[l]; all levels share J).  Sample i (packet id
+ * p0+i under `seed`) reads event words 0..2: word 0 picks the level
+ * (floor(w L / 2^32)), word 1 the start bin jlo[l] + floor(w (jhi[l]-jlo[l]+1)
+ * / 2^32), word 2 a brick cell m = floor(w b^3 / 2^32) = i0 + b i1 + b^2 i2,
+ * which is folded into the fundamental domain of the cube's symmetry group
+ * (each coordinate i -> min(i, b-1-i), then sorted ascending).  Transitions
+ * follow the walk's stream contract from (folded cell, start bin) until a
+ * spatial move leaves the brick or `cap` transitions are taken.  d_out: 8
+ * int32 per sample {level, start bin, folded cell c0 + b c1 + b^2 c2, exit
+ * face (0..5: -x,+x,-y,+y,-z,+z; 6 = cap), exit bin, exit position (q1 + b
+ * q2: the last cell's coordinates along the two axes other than the exit
+ * face's, lower axis first; -1 on a cap), 0, 0}; d_steps: uint64 transitions.
+ * train (may be NULL): also write network inputs and targets. */
 int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_tables, int L, int b, const int32_t* jlo,
                       const int32_t* jhi, uint64_t seed, uint64_t p0, uint64_t n, uint64_t cap, int32_t* d_out,
                       uint64_t* d_steps, const rddmc_fp_train* train, void* stream);
 
 /* A trained proposal attached to a walk (all arrays on the device).  The grid
- * is cut into bricks of `brick`^3 cells (cells per axis a multiple of brick);
- * brick B with brick_lk[B] = log10(k0 dz) of its (uniform) medium, or below
- * -1e29 when it is not eligible, takes proposals for packets that enter it at
- * a bin j with log_tau_lo <= brick_lk[B] + lp[j] <= log_tau_hi.  The queue
- * holds the parked packets (count, ids, entry faces; capacity n_packets). */
+ * is cut into bricks of `brick`^3 cells (1 <= brick <= 64) whose boundaries
+ * sit at cell indices = offset (mod brick) on every axis: a cell with index i
+ * on an axis has brick coordinate (i + (brick - offset) % brick) / brick, and
+ * the brick index is c0 + nb0 (c1 + nb1 c2) with nb_a = ceil((n_a +
+ * (brick - offset) % brick) / brick); n_bricks must equal nb0 nb1 nb2, the
+ * length of d_brick_lk.  Only bricks wholly inside the grid take proposals.
+ * Brick B with brick_lk[B] = log10(k0 dz) of its (uniform) medium, or below
+ * -1e29 when it is not eligible, serves a packet in one of its cells at bin j
+ * when log_tau_lo <= brick_lk[B] + lp[j] <= log_tau_hi.  The walk is Markov in
+ * (cell, bin), so a packet may be handed over in any such state: the walk
+ * checks once per chunk of transitions (and at emission or resumption) and
+ * parks the packet in the queue (count, ids; capacity n_packets). */
 typedef struct rddmc_proposal {
     int32_t brick;
-    int32_t reserved;
+    int32_t offset;
     const float* d_brick_lk;
     const float* d_lp;
     const float* d_xc;
     double log_tau_lo, log_tau_hi;
     unsigned long long* d_queue_count;
     unsigned long long* d_queue_pid;
-    int32_t* d_queue_face;
+    int32_t n_bricks;
+    int32_t reserved;
 } rddmc_proposal;
 
-/* Serve the parked packets of a walk with the trained network: features,
- * tensor-core forward pass in batches of `batch` (a multiple of 64; d_work of
- * rddmc_mlp_work_bytes(batch, n_out) plus batch * (16 * 2 + n_out * 4)
- * bytes), one exit (face, bin, step bucket) sampled per packet from its event
- * stream, mirrored back for negative frequencies, placed across the exit face
- * (Doppler rebin or escape tally as the face's row says), and the packet set in
- * flight again.  Clears the queue.  Synchronises `stream`. */
+/* Serve the parked packets of a walk with the trained network: features of
+ * the packet's cell folded into its brick's fundamental domain, tensor-core
+ * forward pass in batches of at most `batch` rows (a multiple of 64; d_work of
+ * rddmc_mlp_work_bytes(batch, n_out) plus batch * (16 * 2 + n_out * 4) bytes),
+ * one exit (face, bin, step bucket, and the exit cell on the face from head C
+ * when nC = 6 brick^2, uniform when nC = 0) sampled per packet from its event
+ * stream, mapped back to the world frame (and mirrored back for negative
+ * frequencies), placed across the exit face (Doppler rebin or escape tally as
+ * the face's row says), and the packet set in flight again.  Clears the queue.
+ * Synchronises `stream`. */
 int rddmc_propose(const rddmc_grid* grid, const void* d_table, const rddmc_proposal* proposal, uint64_t seed,
-                  uint64_t n_packets, void* d_state, void* d_tallies, int n_out, int nA, int nB, const float* d_wf,
-                  const void* d_wb, int batch, void* d_work, uint64_t* n_served, void* stream);
+                  uint64_t n_packets, void* d_state, void* d_tallies, int n_out, int nA, int nB, int nC,
+                  const float* d_wf, const void* d_wb, int batch, void* d_work, uint64_t* n_served, void* stream);
 
 /* The network: 16 inputs, three hidden layers of 128 (ReLU), n_out logits (a
  * multiple of 16): head A = logits [0, nA) (softmax over exit face x bin),
- * head B = [nA, nA + nB) (softmax over step buckets).  Parameters: FP32
+ * head B = [nA, nA + nB) (softmax over step buckets), optional head C =
+ * [nA + nB, nA + nB + 6 S) (per exit face, a softmax over its S exit cells).  Parameters: FP32
  * master copy and BF16 copy, same layout, rddmc_mlp_param_count(n_out)
  * elements: W1[128x16] b1 W2[128x128] b2 W3[128x128] b3 W4[n_out x 128] b4
  * (row-major W[out][in]).  Matrix products run on tensor cores with BF16
@@ -441,12 +462,14 @@ int rddmc_mlp_to_bf16(int n_out, const float* d_wf, void* d_wb, void* stream);
 /* Logits (FP32 [batch x n_out]) of bf16 inputs d_x [batch x 16]. */
 int rddmc_mlp_forward(int n_out, const float* d_wf, const void* d_wb, const void* d_x, int batch, void* d_work,
                       float* d_logits, void* stream);
-/* Sum over the batch of the two heads' cross-entropies (*d_loss, device) and
- * the gradient of its batch mean with respect to every parameter (FP32,
- * master layout) for targets d_ta (head A; -1 = ignore the row) and d_tb. */
-int rddmc_mlp_loss_grad(int n_out, int nA, int nB, const float* d_wf, const void* d_wb, const void* d_x,
-                        const int32_t* d_ta, const int32_t* d_tb, int batch, void* d_work, float* d_grad,
-                        float* d_loss, void* stream);
+/* Sum over the batch of the heads' cross-entropies (*d_loss, device) and the
+ * gradient of its batch mean with respect to every parameter (FP32, master
+ * layout) for targets d_ta (head A; -1 = ignore the row), d_tb (head B) and,
+ * when nC = 6 S > 0, d_tc (head C = logits [nA + nB, nA + nB + nC): a
+ * softmax over the S logits of slice d_tc / S only; -1 = no head-C term). */
+int rddmc_mlp_loss_grad(int n_out, int nA, int nB, int nC, int S, const float* d_wf, const void* d_wb,
+                        const void* d_x, const int32_t* d_ta, const int32_t* d_tb, const int32_t* d_tc, int batch,
+                        void* d_work, float* d_grad, float* d_loss, void* stream);
 /* One Adam step (bias-corrected, step >= 1) on the master weights; refreshes
  * the BF16 copy. */
 int rddmc_mlp_adam(int n_out, float* d_wf, void* d_wb, const float* d_grad, float* d_m, float* d_v, int step, float lr,

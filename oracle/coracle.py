@@ -242,13 +242,15 @@ def interior_rows(w_uniform) -> np.ndarray:
 
 
 def fp_samples(rows: np.ndarray, b: int, jlo, jhi, seed: int, p0: int, n: int, cap: int):
-    """First passages through a uniform brick (see orc_fp_samples)."""
+    """First passages through a uniform brick (see orc_fp_samples): records
+    [n x 8] {level, start bin, folded start cell, exit face, exit bin, exit
+    position, 0, 0} and transition counts."""
     rows = np.ascontiguousarray(rows, dtype=np.uint32)
     L, J = rows.shape[0], rows.shape[1]
     jlo = np.ascontiguousarray(jlo, dtype=np.int32)
     jhi = np.ascontiguousarray(jhi, dtype=np.int32)
-    out = np.zeros(4 * n, dtype=np.int32)
+    out = np.zeros(8 * n, dtype=np.int32)
     steps = np.zeros(n, dtype=np.uint64)
     lib().orc_fp_samples(_ptr(rows), int(L), int(J), int(b), _ptr(jlo), _ptr(jhi), int(seed), int(p0), int(n),
                          int(cap), _ptr(out), _ptr(steps))
-    return out.reshape(n, 4), steps
+    return out.reshape(n, 8), steps

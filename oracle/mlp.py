@@ -1,9 +1,12 @@
 """FP64 reference of the learned-proposal network (test infrastructure only).
 
 16 inputs -> three hidden layers of 128 with ReLU -> n_out logits; head A is
-a softmax over logits [0, nA), head B over [nA, nA + nB).  The loss is the
-batch mean of the two heads' cross-entropies (rows with target A < 0 are
-ignored, but still count in the mean).  Parameters use the library's flat
+a softmax over logits [0, nA), head B over [nA, nA + nB), and the optional
+head C (nC = 6 S logits after head B) a conditional softmax: for a target
+tC = f S + q only the S logits of slice f take part (the exit position on
+face f given that face).  The loss is the batch mean of the heads'
+cross-entropies (rows with target A < 0 are ignored, but still count in the
+mean; a head-C target < 0 drops that head's term).  Parameters use the library's flat
 layout: W1[128x16] b1 W2[128x128] b2 W3[128x128] b3 W4[n_out x 128] b4,
 row-major W[out][in].
 """
@@ -31,7 +34,7 @@ def pack(params):
     return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params])
 
 
-def loss_and_grad(flat, n_out, nA, nB, X, tA, tB):
+def loss_and_grad(flat, n_out, nA, nB, X, tA, tB, nC=0, S=0, tC=None):
     """Mean loss over the batch and its gradient (flat, master layout)."""
     params = unpack(flat, n_out)
     X = np.asarray(X, dtype=np.float64)
@@ -46,7 +49,11 @@ def loss_and_grad(flat, n_out, nA, nB, X, tA, tB):
     for r in range(B):
         if tA[r] < 0:
             continue
-        for lo, hi, t in ((0, nA, tA[r]), (nA, nA + nB, nA + tB[r])):
+        heads = [(0, nA, tA[r]), (nA, nA + nB, nA + tB[r])]
+        if nC and tC is not None and tC[r] >= 0:
+            lo = nA + nB + (tC[r] // S) * S
+            heads.append((lo, lo + S, nA + nB + tC[r]))
+        for lo, hi, t in heads:
             z = logits[r, lo:hi]
             m = z.max()
             lse = m + np.log(np.exp(z - m).sum())

@@ -988,42 +988,68 @@ void orc_scatter_samples(double T, double x_in, uint64_t seed, uint64_t n, doubl
 /* ------------------------------------------------------------------------- */
 
 /*
- * Sample i (packet id p0+i under `seed`) picks, from its event stream, a
- * density level l = floor(w0 L / 2^32), an entry bin j0 in [jlo[l], jhi[l]]
- * (j0 = jlo + floor(w1 n / 2^32)), and an entry cell on the brick's -x face
- * (i0 = 0, i1 = floor(w2 b / 2^32), i2 = floor(w3 b / 2^32)).  It then takes
+ * Sample i (packet id p0+i under `seed`) reads event words 0..2 of its event
+ * stream: w0 picks a density level l = floor(w0 L / 2^32), w1 a start bin
+ * j0 = jlo[l] + floor(w1 n / 2^32) with n = jhi[l] - jlo[l] + 1, and w2 a
+ * cell of the b^3 brick, m = floor(w2 b^3 / 2^32) = i0 + b i1 + b^2 i2.  The
+ * cell is folded into the fundamental domain of the cube's symmetry group:
+ * each coordinate i becomes min(i, b-1-i), then the three are sorted
+ * ascending, (c0 <= c1 <= c2).  A uniform static brick is invariant under
+ * these reflections and axis permutations, so the first passage from any cell
+ * is the image of one from its folded cell.  From (c, j0) the sample takes
  * DDMC transitions with the rows of an interior cell of a uniform medium at
  * that level (3D rows: 7 cumulative thresholds, then the flag word, per bin)
- * until its first spatial move leaves the b^3 brick.  out[4*i..]: {l, j0,
- * exit face (0..5, 6 = step cap reached), exit bin}; steps[i]: transitions.
+ * until its first spatial move leaves the brick, or `cap` transitions.
+ * out[8*i..]: {l, j0, folded start cell c0 + b c1 + b^2 c2, exit face (0..5 =
+ * -x,+x,-y,+y,-z,+z; 6 = step cap reached), exit bin, exit position (the
+ * coordinates of the last cell inside the brick along the two axes other than
+ * the exit face's, lower axis first: q1 + b q2; -1 on a cap), 0, 0};
+ * steps[i]: transitions.
  */
 void orc_fp_samples(const uint32_t* rows, int L, int J, int b, const int32_t* jlo, const int32_t* jhi,
                     uint64_t seed, uint64_t p0, uint64_t n, uint64_t cap, int32_t* out, uint64_t* steps) {
     for (uint64_t i = 0; i < n; ++i) {
         const uint64_t pk = p0 + i;
-        uint32_t w0 = orc_word(seed, pk, ORC_EVENT, 0), w1 = orc_word(seed, pk, ORC_EVENT, 1);
-        uint32_t w2 = orc_word(seed, pk, ORC_EVENT, 2), w3 = orc_word(seed, pk, ORC_EVENT, 3);
-        int l = (int)(((uint64_t)w0 * (uint64_t)L) >> 32);
-        int nb = jhi[l] - jlo[l] + 1;
+        const uint32_t w0 = orc_word(seed, pk, ORC_EVENT, 0);
+        const uint32_t w1 = orc_word(seed, pk, ORC_EVENT, 1);
+        const uint32_t w2 = orc_word(seed, pk, ORC_EVENT, 2);
+        const int l = (int)(((uint64_t)w0 * (uint64_t)L) >> 32);
+        const int nb = jhi[l] - jlo[l] + 1;
         int j = jlo[l] + (int)(((uint64_t)w1 * (uint64_t)nb) >> 32);
-        int idx[3] = {0, (int)(((uint64_t)w2 * (uint64_t)b) >> 32), (int)(((uint64_t)w3 * (uint64_t)b) >> 32)};
-        out[4 * i + 0] = l;
-        out[4 * i + 1] = j;
-        int face = 6;
+        const int m = (int)(((uint64_t)w2 * (uint64_t)(b * b * b)) >> 32);
+        int idx[3] = {m % b, (m / b) % b, m / (b * b)};
+        /* fold: reflect each axis into its lower half, then sort */
+        for (int a = 0; a < 3; ++a)
+            if (b - 1 - idx[a] < idx[a]) idx[a] = b - 1 - idx[a];
+        for (int pass = 0; pass < 2; ++pass)
+            for (int a = 0; a < 2; ++a)
+                if (idx[a + 1] < idx[a]) { int tmp = idx[a]; idx[a] = idx[a + 1]; idx[a + 1] = tmp; }
+        out[8 * i + 0] = l;
+        out[8 * i + 1] = j;
+        out[8 * i + 2] = idx[0] + b * idx[1] + b * b * idx[2];
+        int face = 6, pos = -1;
         uint64_t t = 0;
         while (t < cap) {
             const uint32_t* r = rows + ((size_t)l * J + j) * 8;
-            uint32_t w = orc_word(seed, pk, ORC_TRANS, t);
+            uint32_t wt = orc_word(seed, pk, ORC_TRANS, t);
             ++t;
             int o = 0;
-            while (o < 7 && w >= r[o]) ++o;
+            while (o < 7 && wt >= r[o]) ++o;
             if (o < 2) { j += o ? 1 : -1; continue; }
             int f = o - 2, ax = f / 2, side = (f & 1) ? 1 : -1;
+            if (idx[ax] + side < 0 || idx[ax] + side >= b) {
+                face = f;
+                const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;  /* the other two axes, lower first */
+                pos = idx[u] + b * idx[v];
+                break;
+            }
             idx[ax] += side;
-            if (idx[ax] < 0 || idx[ax] >= b) { face = f; break; }
         }
-        out[4 * i + 2] = face;
-        out[4 * i + 3] = j;
+        out[8 * i + 3] = face;
+        out[8 * i + 4] = j;
+        out[8 * i + 5] = pos;
+        out[8 * i + 6] = 0;
+        out[8 * i + 7] = 0;
         steps[i] = t;
     }
 }

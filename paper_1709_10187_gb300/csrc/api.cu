@@ -331,8 +331,9 @@ int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_r
         const rddmc_proposal* pr = o->proposal;
         if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
         if (o->steps_per_launch == 0 && o->resume == 0) return RDDMC_ERR_ARG;
-        if (pr->brick < 1 || g->n[0] % pr->brick || g->n[1] % pr->brick || g->n[2] % pr->brick) return RDDMC_ERR_ARG;
-        if (!pr->d_brick_lk || !pr->d_lp || !pr->d_xc || !pr->d_queue_count || !pr->d_queue_pid || !pr->d_queue_face)
+        if (pr->brick < 1 || pr->brick > 64 || pr->offset < 0 || pr->offset >= pr->brick) return RDDMC_ERR_ARG;
+        if ((int64_t)pr->n_bricks != proposal_bricks(*g, *pr)) return RDDMC_ERR_ARG;
+        if (!pr->d_brick_lk || !pr->d_lp || !pr->d_xc || !pr->d_queue_count || !pr->d_queue_pid)
             return RDDMC_ERR_ARG;
     }
     if (state_bytes < state_bytes_for(o->n_packets)) return RDDMC_ERR_SIZE;

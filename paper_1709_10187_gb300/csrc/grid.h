@@ -66,4 +66,12 @@ uint64_t state_bytes_for(uint64_t n_packets);
 uint64_t tally_bytes_for(int J);
 int tally_words(int J);
 
+// Bricks (partial ones included) of a proposal's lattice on grid g.
+inline int64_t proposal_bricks(const rddmc_grid& g, const rddmc_proposal& pr) {
+    const int sh = (pr.brick - pr.offset % pr.brick) % pr.brick;
+    int64_t nb = 1;
+    for (int a = 0; a < 3; ++a) nb *= (g.n[a] + sh + pr.brick - 1) / pr.brick;
+    return nb;
+}
+
 }  // namespace rddmc

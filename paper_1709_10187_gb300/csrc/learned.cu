@@ -2,10 +2,11 @@
 // BF16 MLP (forward, backward, softmax cross-entropy, Adam) on tensor cores,
 // and batched inference that samples exits for parked packets.
 //
-// First passages: sample i picks a density level, an entry bin and an entry
-// cell on the -x face of a b^3 brick of uniform medium from its event stream
-// and walks with the rows of an interior cell of that medium (the same rows
-// and transition stream as the walk) until a spatial move leaves the brick.
+// First passages: sample i picks a density level, a start bin and a cell of a
+// b^3 brick of uniform medium from its event stream, folds the cell into the
+// fundamental domain of the cube's symmetry group and walks from it with the
+// rows of an interior cell of that medium (the same rows and transition
+// stream as the walk) until a spatial move leaves the brick.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <mma.h>
@@ -30,12 +31,13 @@ struct FpParams {
     int L, J, b;
     uint32_t k0, k1;
     unsigned long long p0, n, cap;
-    int* out;                    // 4 ints per sample: level, entry bin, exit face (6 = cap), exit bin
+    int* out;                    // 8 ints per sample (rddmc_fp_generate)
     unsigned long long* steps;   // transitions per sample
     // optional training tensors: inputs (bf16, 16 per sample), targets
     __nv_bfloat16* X;
     int* tA;                     // exit face * J + exit bin, -1 when the step cap was reached
     int* tB;                     // log2 step bucket
+    int* tC;                     // exit face * b^2 + exit position, -1 when the step cap was reached
     const float* lk;             // per level: log10(k0 dz)
     const float* lp;             // per bin: log10 of the bin-mean profile
     const float* xc;             // per bin: centre frequency
@@ -50,15 +52,20 @@ __global__ void __launch_bounds__(256) fp_kernel(const FpParams P) {
         const unsigned long long pk = P.p0 + i;
         const uint32_t pl = (uint32_t)pk, ph = (uint32_t)(pk >> 32);
         const uint4 ew = fp_philox(make_uint4(0u, 0u, pl, ph | 0x80000000u), P.k0, P.k1);  // event words 0..3
-        const int l = (int)(((unsigned long long)ew.x * (unsigned long long)P.L) >> 32);
+        const int l = min((int)(((unsigned long long)ew.x * (unsigned long long)P.L) >> 32), P.L - 1);
         const int nb = P.jhi[l] - P.jlo[l] + 1;
         int j = P.jlo[l] + (int)(((unsigned long long)ew.y * (unsigned long long)nb) >> 32);
-        int idx[3] = {0, (int)(((unsigned long long)ew.z * (unsigned long long)P.b) >> 32),
-                      (int)(((unsigned long long)ew.w * (unsigned long long)P.b) >> 32)};
+        const int m = (int)(((unsigned long long)ew.z * (unsigned long long)(P.b * P.b * P.b)) >> 32);
+        const int lw[3] = {m % P.b, (m / P.b) % P.b, m / (P.b * P.b)};
+        int idx[3], perm[3];
+        bool flip[3];
+        fold_cell(lw, P.b, idx, perm, flip);
         const uint4* rows = P.rows[l];
         const uint2* fast = P.fast[l];
         const int j0 = j;
-        int face = 6;
+        const int start = idx[0] + P.b * (idx[1] + P.b * idx[2]);
+        const int c0[3] = {idx[0], idx[1], idx[2]};
+        int face = 6, pos = -1;
         unsigned long long t = 0;
         const unsigned J1 = (unsigned)P.J - 1u;
         while (t < P.cap && face == 6) {
@@ -76,19 +83,30 @@ __global__ void __launch_bounds__(256) fp_kernel(const FpParams P) {
                                    (unsigned)(w >= c.w);
                 if (o < 2u) { j += o ? 1 : -1; continue; }
                 const int fc = (int)o - 2, ax = fc >> 1, side = (fc & 1) ? 1 : -1;
+                if (idx[ax] + side < 0 || idx[ax] + side >= P.b) {
+                    face = fc;
+                    const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;  // the other two axes, lower first
+                    pos = idx[u] + P.b * idx[v];
+                    break;
+                }
                 idx[ax] += side;
-                if (idx[ax] < 0 || idx[ax] >= P.b) { face = fc; break; }
             }
         }
-        P.out[4 * i + 0] = l;
-        P.out[4 * i + 1] = j0;
-        P.out[4 * i + 2] = face;
-        P.out[4 * i + 3] = j;
+        int* o8 = P.out + 8 * i;
+        o8[0] = l;
+        o8[1] = j0;
+        o8[2] = start;
+        o8[3] = face;
+        o8[4] = j;
+        o8[5] = pos;
+        o8[6] = 0;
+        o8[7] = 0;
         P.steps[i] = t;
         if (P.X) {
-            features(P.lk[l], P.lp[j0], P.xc[j0], P.fc, P.X + kFeat * i);
+            features(P.lk[l], P.lp[j0], P.xc[j0], c0, P.b, P.fc, P.X + kFeat * i);
             P.tA[i] = face < 6 ? face * P.J + min(max(j, 0), P.J - 1) : -1;
             P.tB[i] = step_bucket(t);
+            if (P.tC) P.tC[i] = face < 6 ? face * P.b * P.b + pos : -1;
         }
     }
 }
@@ -115,7 +133,7 @@ int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_table
                       const int32_t* jhi, uint64_t seed, uint64_t p0, uint64_t n, uint64_t cap, int32_t* d_out,
                       uint64_t* d_steps, const rddmc_fp_train* train, void* stream) {
     if (!grids || !d_tables || !jlo || !jhi || !d_out || !d_steps) return RDDMC_ERR_ARG;
-    if (L < 1 || L > kMaxLevels || b < 1 || n == 0 || cap == 0) return RDDMC_ERR_ARG;
+    if (L < 1 || L > kMaxLevels || b < 1 || b > 64 || n == 0 || cap == 0) return RDDMC_ERR_ARG;
     FpParams P;
     std::memset(&P, 0, sizeof(P));
     int J = -1;
@@ -152,6 +170,7 @@ int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_table
         P.X = (__nv_bfloat16*)train->d_x;
         P.tA = train->d_ta;
         P.tB = train->d_tb;
+        P.tC = train->d_tc;
         P.lk = train->d_lk;
         P.lp = train->d_lp;
         P.xc = train->d_xc;
@@ -173,9 +192,10 @@ int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_table
 
 // ===================================================================== MLP
 // Architecture: n_in = 16 inputs -> 3 hidden layers of 128 (ReLU) -> n_out
-// logits (a multiple of 16): head A over [0, nA) (exit face x exit bin) and
-// head B over [nA, nA + nB) (log2 step bucket); columns past nA + nB are
-// padding.  Parameters, FP32 master copy and BF16 copy in the same order:
+// logits (a multiple of 16): head A over [0, nA) (exit face x exit bin),
+// head B over [nA, nA + nB) (log2 step bucket) and head C over
+// [nA + nB, nA + nB + 6 S) (exit cell on each face, S = b^2 per face, used
+// one slice at a time); columns past the heads are padding.  Parameters, FP32 master copy and BF16 copy in the same order:
 // W1[128x16] b1[128] W2[128x128] b2[128] W3[128x128] b3[128] W4[n_out x 128]
 // b4[n_out].  Matrix products run on tensor cores (WMMA, BF16 inputs, FP32
 // accumulation); softmax, cross-entropy, bias sums and Adam in FP32.
@@ -280,24 +300,36 @@ cudaError_t gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __n
     return cudaGetLastError();
 }
 
-// Softmax cross-entropy of both heads, one warp per row: loss += CE_A + CE_B
-// (summed over the batch), dlogits = (softmax - onehot) / B, zero on padding.
-__global__ void softmax_ce_kernel(const float* __restrict__ logits, int n_out, int nA, int nB,
-                                  const int* __restrict__ tA, const int* __restrict__ tB, int Bsz,
-                                  float* __restrict__ dlogf, __nv_bfloat16* __restrict__ dlogb, float* loss) {
+// Softmax cross-entropy of the heads, one warp per row: loss += CE_A + CE_B
+// (+ CE_C over the S logits of the target's slice when head C is present and
+// its target is >= 0), summed over the batch; dlogits = (softmax - onehot) / B
+// on the logits a head used, zero elsewhere.
+__global__ void softmax_ce_kernel(const float* __restrict__ logits, int n_out, int nA, int nB, int nC, int S,
+                                  const int* __restrict__ tA, const int* __restrict__ tB, const int* __restrict__ tC,
+                                  int Bsz, float* __restrict__ dlogf, __nv_bfloat16* __restrict__ dlogb,
+                                  float* loss) {
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (row >= Bsz) return;
     const float* z = logits + (size_t)row * n_out;
+    float* gf = dlogf + (size_t)row * n_out;
+    __nv_bfloat16* gb = dlogb + (size_t)row * n_out;
     float total = 0.0f;
-    if (tA[row] < 0) {  // ignored sample: no loss, no gradient
-        for (int k = lane; k < n_out; k += 32) {
-            dlogf[(size_t)row * n_out + k] = 0.0f;
-            dlogb[(size_t)row * n_out + k] = __float2bfloat16(0.0f);
-        }
-        return;
+    const bool skip = tA[row] < 0;  // ignored sample: no loss, no gradient
+    // zero everything past heads A and B (head C's unused slices, padding)
+    for (int k = (skip ? 0 : nA + nB) + lane; k < n_out; k += 32) {
+        gf[k] = 0.0f;
+        gb[k] = __float2bfloat16(0.0f);
     }
-    for (int h = 0; h < 2; ++h) {
-        const int lo = h ? nA : 0, hi = h ? nA + nB : nA, tgt = h ? tB[row] + nA : tA[row];
+    if (skip) return;
+    __syncwarp();
+    int tc = (nC > 0 && tC) ? tC[row] : -1;
+    if (tc >= nC) tc = -1;
+    const int nh = tc >= 0 ? 3 : 2;
+    for (int h = 0; h < nh; ++h) {
+        int lo, hi, tgt;
+        if (h == 0) { lo = 0; hi = nA; tgt = tA[row]; }
+        else if (h == 1) { lo = nA; hi = nA + nB; tgt = nA + tB[row]; }
+        else { lo = nA + nB + (tc / S) * S; hi = lo + S; tgt = nA + nB + tc; }
         float mx = -3.0e38f;
         for (int k = lo + lane; k < hi; k += 32) mx = fmaxf(mx, z[k]);
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -308,13 +340,9 @@ __global__ void softmax_ce_kernel(const float* __restrict__ logits, int n_out, i
         total += lse - z[tgt];
         for (int k = lo + lane; k < hi; k += 32) {
             const float g = (__expf(z[k] - lse) - (k == tgt ? 1.0f : 0.0f)) / (float)Bsz;
-            dlogf[(size_t)row * n_out + k] = g;
-            dlogb[(size_t)row * n_out + k] = __float2bfloat16(g);
+            gf[k] = g;
+            gb[k] = __float2bfloat16(g);
         }
-    }
-    for (int k = nA + nB + lane; k < n_out; k += 32) {
-        dlogf[(size_t)row * n_out + k] = 0.0f;
-        dlogb[(size_t)row * n_out + k] = __float2bfloat16(0.0f);
     }
     if (lane == 0) atomicAdd(loss, total);
 }
@@ -421,12 +449,13 @@ int rddmc_mlp_forward(int n_out, const float* d_wf, const void* d_wb, const void
     return RDDMC_OK;
 }
 
-int rddmc_mlp_loss_grad(int n_out, int nA, int nB, const float* d_wf, const void* d_wb, const void* d_x,
-                        const int32_t* d_ta, const int32_t* d_tb, int batch, void* d_work, float* d_grad,
-                        float* d_loss, void* stream) {
-    if (!rddmc_mlp_param_count(n_out) || !rddmc_mlp_work_bytes(batch, n_out) || nA < 1 || nB < 1 ||
-        nA + nB > n_out || !d_wf || !d_wb || !d_x || !d_ta || !d_tb || !d_work || !d_grad || !d_loss)
+int rddmc_mlp_loss_grad(int n_out, int nA, int nB, int nC, int S, const float* d_wf, const void* d_wb,
+                        const void* d_x, const int32_t* d_ta, const int32_t* d_tb, const int32_t* d_tc, int batch,
+                        void* d_work, float* d_grad, float* d_loss, void* stream) {
+    if (!rddmc_mlp_param_count(n_out) || !rddmc_mlp_work_bytes(batch, n_out) || nA < 1 || nB < 1 || nC < 0 ||
+        nA + nB + nC > n_out || !d_wf || !d_wb || !d_x || !d_ta || !d_tb || !d_work || !d_grad || !d_loss)
         return RDDMC_ERR_ARG;
+    if (nC > 0 && (S < 1 || nC != 6 * S || !d_tc)) return RDDMC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const MlpOffsets o = mlp_offsets(n_out);
     const __nv_bfloat16* wb = (const __nv_bfloat16*)d_wb;
@@ -434,8 +463,8 @@ int rddmc_mlp_loss_grad(int n_out, int nA, int nB, const float* d_wf, const void
     const MlpWork w = mlp_work(d_work, batch, n_out);
     if (mlp_forward(n_out, d_wf, wb, X, batch, w, s) != cudaSuccess) return RDDMC_ERR_CUDA;
     if (cudaMemsetAsync(d_loss, 0, 4, s) != cudaSuccess) return RDDMC_ERR_CUDA;
-    softmax_ce_kernel<<<(batch + 7) / 8, 256, 0, s>>>(w.logits, n_out, nA, nB, d_ta, d_tb, batch, w.dlogf, w.dlogb,
-                                                       d_loss);
+    softmax_ce_kernel<<<(batch + 7) / 8, 256, 0, s>>>(w.logits, n_out, nA, nB, nC, S, d_ta, d_tb,
+                                                       nC > 0 ? d_tc : nullptr, batch, w.dlogf, w.dlogb, d_loss);
     // output layer: dW4 = dlog^T H3, db4 = colsum(dlog), dH3 = (dlog W4) * [H3 > 0]
     gemm<false, true, EPI_F32>(n_out, kHid, batch, w.dlogb, n_out, w.H[2], kHid, nullptr, nullptr, 0, nullptr,
                                d_grad + o.W[3], kHid, s);

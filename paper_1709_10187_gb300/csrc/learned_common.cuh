@@ -17,11 +17,32 @@ struct FeatConst {
     float inv_xs;    // 1 / max |x| of the frequency grid
 };
 
+// Fold of a brick cell into the fundamental domain of the cube's symmetry
+// group: each coordinate l becomes c = min(l, b-1-l) (flip[a] records the
+// reflection), then the axes are sorted so that c[perm[0]] <= c[perm[1]] <=
+// c[perm[2]]; canonical axis k is world axis perm[k].
+__device__ __forceinline__ void fold_cell(const int l[3], int b, int C[3], int perm[3], bool flip[3]) {
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        flip[a] = b - 1 - l[a] < l[a];
+        c[a] = flip[a] ? b - 1 - l[a] : l[a];
+    }
+    int p0 = 0, p1 = 1, p2 = 2, t;
+    if (c[p1] < c[p0]) { t = p0; p0 = p1; p1 = t; }
+    if (c[p2] < c[p1]) { t = p1; p1 = p2; p2 = t; }
+    if (c[p1] < c[p0]) { t = p0; p0 = p1; p1 = t; }
+    perm[0] = p0; perm[1] = p1; perm[2] = p2;
+    C[0] = c[p0]; C[1] = c[p1]; C[2] = c[p2];
+}
+
 // Network inputs for a brick of line-centre cell optical depth 10^lk (k0 dz)
-// entered at a bin with log10 bin-mean profile lp and centre frequency x:
-// region size in tau at line centre and at the entry bin, region a*tau, the
-// entry frequency and eight Fourier features of it.
-__device__ __forceinline__ void features(float lk, float lp, float x, const FeatConst& C, __nv_bfloat16* out) {
+// at a bin with log10 bin-mean profile lp and centre frequency x, at the cell
+// with folded brick coordinates c[3]: region size in tau at line centre and at
+// the bin, region a*tau, the frequency and eight Fourier features of it, and
+// the cell's position, (2c + 1) / b - 1 per axis.
+__device__ __forceinline__ void features(float lk, float lp, float x, const int c[3], int b, const FeatConst& C,
+                                         __nv_bfloat16* out) {
     float f[kFeat];
     f[0] = (lk + C.log_b) * 0.1f;
     f[1] = (lk + lp + C.log_b) * 0.2f;
@@ -36,7 +57,9 @@ __device__ __forceinline__ void features(float lk, float lp, float x, const Feat
         f[3 + 2 * k] = sn;
         f[4 + 2 * k] = cs;
     }
-    f[13] = f[14] = f[15] = 0.0f;
+    const float inv_b = 1.0f / (float)b;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[13 + a] = (float)(2 * c[a] + 1) * inv_b - 1.0f;
 #pragma unroll
     for (int i = 0; i < kFeat; ++i) out[i] = __float2bfloat16(f[i]);
 }

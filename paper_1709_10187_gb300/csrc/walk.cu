@@ -67,14 +67,14 @@ struct WalkParams {
     int n[3];
     float a, lambda;
     int src_ncand[3], src_cand[3][2], src_nbin, src_bin[2];
-    // learned exit proposal (3D DDMC): bricks of prop_b^3 cells
-    int prop_b, prop_nbx, prop_nby;
+    // learned exit proposal (3D DDMC): bricks of prop_b^3 cells, brick
+    // coordinate (i + prop_sh) / prop_b of cell index i on every axis
+    int prop_b, prop_sh, prop_nbx, prop_nby;
     const float* prop_lk;
     const float* prop_lp;
     float prop_llo, prop_lhi;
     unsigned long long* prop_qcount;
     unsigned long long* prop_qpid;
-    int* prop_qface;
 };
 
 // Philox4x32-10 with precomputed round keys (held in the kernel's parameter bank).
@@ -357,10 +357,35 @@ __device__ __noinline__ McResult mc_excursion(const WalkParams& P, unsigned cell
     return res;
 }
 
+__device__ __forceinline__ void cell_coords(const WalkParams& P, unsigned cell, unsigned ic[3]) {
+    ic[0] = cell % (unsigned)P.n0;
+    ic[1] = (cell / (unsigned)P.n0) % (unsigned)P.n[1];
+    ic[2] = cell / (unsigned)P.n01;
+}
+
 __device__ __forceinline__ unsigned brick_of(const WalkParams& P, unsigned cell) {
-    const unsigned i0 = cell % (unsigned)P.n0, i1 = (cell / (unsigned)P.n0) % (unsigned)P.n[1],
-                   i2 = cell / (unsigned)P.n01, b = (unsigned)P.prop_b;
-    return i0 / b + (unsigned)P.prop_nbx * (i1 / b + (unsigned)P.prop_nby * (i2 / b));
+    unsigned ic[3];
+    cell_coords(P, cell, ic);
+    const unsigned b = (unsigned)P.prop_b, sh = (unsigned)P.prop_sh;
+    return (ic[0] + sh) / b + (unsigned)P.prop_nbx * ((ic[1] + sh) / b + (unsigned)P.prop_nby * ((ic[2] + sh) / b));
+}
+
+// Whether a packet at (cell, bin) is served by the proposal: its brick lies
+// wholly inside the grid, is eligible (brick_lk above -1e29) and the bin's cell
+// optical depth 10^(brick_lk + lp[bin]) lies in [10^llo, 10^lhi].
+__device__ __forceinline__ bool prop_takes(const WalkParams& P, unsigned cell, unsigned bin) {
+    unsigned ic[3];
+    cell_coords(P, cell, ic);
+    const int b = P.prop_b, sh = P.prop_sh;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int lo = (((int)ic[a] + sh) / b) * b - sh;
+        if (lo < 0 || lo + b > P.n[a]) return false;
+    }
+    const float lkb = __ldg(&P.prop_lk[brick_of(P, cell)]);
+    if (!(lkb > -1.0e29f)) return false;
+    const float l = lkb + __ldg(&P.prop_lp[min(bin, (unsigned)P.J - 1u)]);
+    return l >= P.prop_llo && l <= P.prop_lhi;
 }
 
 template <int NDIM, bool SMEM_ROWS, bool HYBRID, bool PROPOSE>
@@ -391,8 +416,6 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
     unsigned cell = 0, cls = 0, s = 0;  // s = cls * J + bin: the row of the state
     unsigned long long n_steps = 0, n_edraw = 0, n_mc = 0;
     unsigned n_emit = 0, n_esc = 0, n_abort = 0, n_clamp = 0, status_bits = 0, n_conv = 0;
-    bool parked = false;   // the packet entered an eligible brick and waits for a proposal
-    int park_face = 0;
 
     // Outcome of an MC excursion: back to DDMC (returns false) or finished.
     auto after_mc = [&](const McResult& res) -> bool {
@@ -470,21 +493,6 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         cell = min((face & 1u) ? cell + stride : cell - stride, (unsigned)P.ncell - 1u);
         cls = __ldg(&P.cell_class[cell]);
         s = cls * J + nbin;
-        if (PROPOSE) {
-            // entering a new brick: park for a proposal when the brick and bin qualify
-            const unsigned bn = brick_of(P, cell);
-            if (bn != brick_of(P, old_cell)) {
-                const float lkb = __ldg(&P.prop_lk[bn]);
-                if (lkb > -1.0e29f) {
-                    const float l = lkb + __ldg(&P.prop_lp[min(nbin, J - 1u)]);
-                    if (l >= P.prop_llo && l <= P.prop_lhi) {
-                        parked = true;
-                        park_face = (int)(face ^ 1u);  // the brick face the packet came through
-                        return true;
-                    }
-                }
-            }
-        }
         return false;
     };
 
@@ -545,6 +553,19 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         }
         if (__all_sync(FULL, exhausted && !have)) break;
         if (!have) continue;
+        if (PROPOSE && prop_takes(P, cell, min(s - cls * J, J - 1u))) {
+            // the walk is Markov in (cell, bin): a packet in a state the proposal
+            // serves waits for it (checked once per chunk of transitions)
+            P.st_cell[pid] = cell;
+            P.st_bin[pid] = min(s - cls * J, J - 1u);
+            P.st_t[pid] = t;
+            P.st_e[pid] = e;
+            P.st_status[pid] = PK_PARKED;
+            const unsigned long long k = atomicAdd(P.prop_qcount, 1ull);
+            P.prop_qpid[min(k, P.n_packets - 1ull)] = pid;
+            have = false;
+            continue;
+        }
 
         // ---- run up to `chunk` transitions
         unsigned long long lim = t + (unsigned long long)P.chunk;
@@ -604,18 +625,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
     chunk_done:
         n_steps += t - t0;
         n_edraw += e - e0;
-        if (PROPOSE && parked) {
-            P.st_cell[pid] = cell;
-            P.st_bin[pid] = min(s - cls * J, J - 1u);
-            P.st_t[pid] = t;
-            P.st_e[pid] = e;
-            P.st_status[pid] = PK_PARKED;
-            const unsigned long long k = atomicAdd(P.prop_qcount, 1ull);
-            P.prop_qpid[k] = pid;
-            P.prop_qface[k] = park_face;
-            parked = false;
-            have = false;
-        } else if (fin) {
+        if (fin) {
             have = false;
             if (P.save_state) P.st_status[pid] = PK_DONE;
         } else if (t >= P.max_steps) {
@@ -703,6 +713,27 @@ __global__ void scatter_samples_kernel(float a, float x_in, const float2* __rest
 }
 
 // ------------------------------------------------------------ proposals
+// A parked packet's cell, folded into the fundamental domain of its brick (the
+// frame the network was trained in): a uniform static brick is invariant
+// under the cube's reflections and axis permutations, so the exit sampled in
+// the folded frame is mapped back by the inverse transform.
+__device__ __forceinline__ void brick_base(const WalkParams& P, const unsigned ic[3], int base[3]) {
+    const int b = P.prop_b, sh = P.prop_sh;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) base[a] = (((int)ic[a] + sh) / b) * b - sh;
+}
+
+__device__ __forceinline__ void fold_parked(const WalkParams& P, unsigned cell, int base[3], int C[3], int perm[3],
+                                            bool flip[3]) {
+    unsigned ic[3];
+    cell_coords(P, cell, ic);
+    brick_base(P, ic, base);
+    int l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) l[a] = min(max((int)ic[a] - base[a], 0), P.prop_b - 1);
+    fold_cell(l, P.prop_b, C, perm, flip);
+}
+
 // Network inputs of queued packets q0 .. q0+cnt (rows past cnt are zeroed).
 // Negative frequencies are mirrored: a static uniform brick is symmetric under
 // x -> -x and the network was trained on x >= 0.
@@ -719,19 +750,40 @@ __global__ void propose_features_kernel(const WalkParams P, const float* __restr
     const unsigned cell = min(P.st_cell[pid], (unsigned)P.ncell - 1u);
     unsigned j = min(P.st_bin[pid], (unsigned)P.J - 1u);
     if (xc[j] < 0.0f) j = (unsigned)P.J - 1u - j;
-    features(P.prop_lk[brick_of(P, cell)], P.prop_lp[j], xc[j], fc, X + r * kFeat);
+    int base[3], C[3], perm[3];
+    bool flip[3];
+    fold_parked(P, cell, base, C, perm, flip);
+    features(P.prop_lk[brick_of(P, cell)], P.prop_lp[j], xc[j], C, P.prop_b, fc, X + r * kFeat);
+}
+
+// Inverse-CDF draw from softmax(z[0..n)) with uniform u in (0,1).
+__device__ __forceinline__ int softmax_draw(const float* __restrict__ z, int n, float u) {
+    float mx = -3.0e38f;
+    for (int c = 0; c < n; ++c) mx = fmaxf(mx, z[c]);
+    float sum = 0.0f;
+    for (int c = 0; c < n; ++c) sum += __expf(z[c] - mx);
+    const float target = u * sum;
+    float acc = 0.0f;
+    for (int c = 0; c < n; ++c) {
+        acc += __expf(z[c] - mx);
+        if (acc >= target) return c;
+    }
+    return n - 1;
 }
 
 // Sample an exit for each queued packet from its logits and place the packet
-// across the exit face; one thread per packet.
+// across the exit face; one thread per packet.  Event draws, in order: the exit
+// (face, bin) of head A, the step bucket of head B and a uniform inside it,
+// then the exit cell on the face -- one draw from head C's slice of that face
+// when nC > 0, else two uniform coordinates -- then the crossing's own draws
+// (a Doppler rebin, or the five of an escape).
 __global__ void propose_place_kernel(const WalkParams P, const float* __restrict__ xc,
-                                     const float* __restrict__ logits, int n_out, int nA, int nB,
+                                     const float* __restrict__ logits, int n_out, int nA, int nB, int nC,
                                      unsigned long long q0, unsigned long long cnt) {
     const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= cnt) return;
     const unsigned J = (unsigned)P.J;
     const unsigned long long pid = P.prop_qpid[q0 + r];
-    const int ef = P.prop_qface[q0 + r];
     const unsigned cell = min(P.st_cell[pid], (unsigned)P.ncell - 1u);
     const unsigned bin = min(P.st_bin[pid], J - 1u);
     const bool mirror = xc[bin] < 0.0f;
@@ -739,57 +791,54 @@ __global__ void propose_place_kernel(const WalkParams P, const float* __restrict
     es.init(pid, P.st_e[pid], P.k0, P.k1);
     const unsigned long long e_start = es.e;
     const float* z = logits + r * (unsigned long long)n_out;
-    // head A: exit face (canonical: 0 entry face, 1 opposite, 2-5 sides) x exit bin
-    float mx = -3.0e38f;
-    for (int c = 0; c < nA; ++c) mx = fmaxf(mx, z[c]);
-    float sum = 0.0f;
-    for (int c = 0; c < nA; ++c) sum += __expf(z[c] - mx);
-    float u = es.u01() * sum, acc = 0.0f;
-    int ca = nA - 1;
-    for (int c = 0; c < nA; ++c) {
-        acc += __expf(z[c] - mx);
-        if (acc >= u) { ca = c; break; }
-    }
+    // head A: exit face (folded frame) x exit bin
+    const int ca = softmax_draw(z, nA, es.u01());
     // head B: log2 step bucket
-    mx = -3.0e38f;
-    for (int c = 0; c < nB; ++c) mx = fmaxf(mx, z[nA + c]);
-    sum = 0.0f;
-    for (int c = 0; c < nB; ++c) sum += __expf(z[nA + c] - mx);
-    u = es.u01() * sum;
-    acc = 0.0f;
-    int kb = nB - 1;
-    for (int c = 0; c < nB; ++c) {
-        acc += __expf(z[nA + c] - mx);
-        if (acc >= u) { kb = c; break; }
-    }
-    kb = min(kb, 40);
+    const int kb = min(softmax_draw(z + nA, nB, es.u01()), 40);
     const unsigned long long steps = (1ull << kb) + (unsigned long long)(es.u01() * (float)(1ull << kb));
+    const int b = P.prop_b;
     const int fc_ = ca / (int)J;
     unsigned jo = (unsigned)(ca % (int)J);
     if (mirror) jo = J - 1u - jo;
-    const int ea = ef >> 1;
-    int f;
-    if (fc_ == 0) f = ef;
-    else if (fc_ == 1) f = ef ^ 1;
-    else if (fc_ < 4) f = 2 * ((ea + 1) % 3) + (fc_ - 2);
-    else f = 2 * ((ea + 2) % 3) + (fc_ - 4);
-    // the cell on the exit face (uniform over the face) and the crossing
-    const unsigned b = (unsigned)P.prop_b;
-    const unsigned ic[3] = {cell % (unsigned)P.n0, (cell / (unsigned)P.n0) % (unsigned)P.n[1], cell / (unsigned)P.n01};
-    unsigned ci[3];
-    const int fa = f >> 1, fs = f & 1;
+    // exit cell on the folded frame's face: coordinates (q1, q2) along the
+    // other two axes, lower axis first
+    int q1, q2;
+    if (nC > 0) {
+        const int S = b * b;
+        const int pq = softmax_draw(z + nA + nB + fc_ * S, S, es.u01());
+        q1 = pq % b;
+        q2 = pq / b;
+    } else {
+        q1 = min((int)(es.u01() * (float)b), b - 1);
+        q2 = min((int)(es.u01() * (float)b), b - 1);
+    }
+    int base[3], C[3], perm[3];
+    bool flip[3];
+    fold_parked(P, cell, base, C, perm, flip);
+    const int cax = fc_ >> 1, cside = fc_ & 1;
+    int cc[3];
+    cc[cax] = cside ? b - 1 : 0;
+    cc[cax == 0 ? 1 : 0] = q1;
+    cc[cax == 2 ? 1 : 2] = q2;
+    // folded -> world: folded axis k is world axis perm[k], reflected when flip[perm[k]]
+    int wc[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) ci[a] = (ic[a] / b) * b;
-    ci[fa] += fs ? b - 1u : 0u;
-    for (int a = 0; a < 3; ++a)
-        if (a != fa) ci[a] += min((unsigned)(es.u01() * (float)b), b - 1u);
-    const unsigned cin = min(ci[0] + (unsigned)P.n0 * ci[1] + (unsigned)P.n01 * ci[2], (unsigned)P.ncell - 1u);
+    for (int k = 0; k < 3; ++k) {
+        const int wa = perm[k];
+        const int loc = flip[wa] ? b - 1 - cc[k] : cc[k];
+        wc[wa] = min(max(base[wa] + loc, 0), P.n[wa] - 1);
+    }
+    const int fa = perm[cax];
+    const int fs = cside ^ (flip[fa] ? 1 : 0);
+    const unsigned f = (unsigned)(2 * fa + fs);
+    const unsigned cin = min((unsigned)wc[0] + (unsigned)P.n0 * (unsigned)wc[1] + (unsigned)P.n01 * (unsigned)wc[2],
+                             (unsigned)P.ncell - 1u);
     const unsigned cls = min(__ldg(&P.cell_class[cin]), (unsigned)P.n_class - 1u);
     const uint4 a0 = __ldg(&P.rows[(cls * J + jo) * 2u]);
-    const unsigned act = (a0.w >> (2u * (2u + (unsigned)f))) & 3u;
+    const unsigned act = (a0.w >> (2u * (2u + f))) & 3u;
     unsigned long long* T = P.tally;
     if (act == ACT_ESCAPE) {
-        const EscapeBins eb = escape_bins<3>(P, cin, jo, (unsigned)f, pid, es.e, (a0.w & FLAG_MOVING) != 0u);
+        const EscapeBins eb = escape_bins<3>(P, cin, jo, f, pid, es.e, (a0.w & FLAG_MOVING) != 0u);
         es.e += 5;
         atomicAdd(&T[kHistOff + eb.hist], 1ull);
         atomicAdd(&T[kFaceOff + f], 1ull);
@@ -799,7 +848,7 @@ __global__ void propose_place_kernel(const WalkParams P, const float* __restrict
     } else {
         unsigned j2 = jo;
         if (act == ACT_REBIN) {
-            const Rebin rb = P.rebin[cls * 6u + (unsigned)f];
+            const Rebin rb = P.rebin[cls * 6u + f];
             const unsigned w1 = es.next();
             int jn = (int)jo + rb.m + (w1 >= rb.thr ? 1 : 0);
             if (jn < 0) { jn = 0; atomicAdd(&T[C_CLAMPS], 1ull); }
@@ -891,15 +940,15 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     if (o.proposal) {
         const rddmc_proposal* pr = o.proposal;
         P.prop_b = pr->brick;
-        P.prop_nbx = g.n[0] / pr->brick;
-        P.prop_nby = g.n[1] / pr->brick;
+        P.prop_sh = (pr->brick - pr->offset % pr->brick) % pr->brick;
+        P.prop_nbx = (g.n[0] + P.prop_sh + pr->brick - 1) / pr->brick;
+        P.prop_nby = (g.n[1] + P.prop_sh + pr->brick - 1) / pr->brick;
         P.prop_lk = pr->d_brick_lk;
         P.prop_lp = pr->d_lp;
         P.prop_llo = (float)pr->log_tau_lo;
         P.prop_lhi = (float)pr->log_tau_hi;
         P.prop_qcount = pr->d_queue_count;
         P.prop_qpid = pr->d_queue_pid;
-        P.prop_qface = pr->d_queue_face;
         P.save_state = 1;
     }
 }
@@ -936,14 +985,18 @@ extern "C" int rddmc_mlp_forward(int n_out, const float* d_wf, const void* d_wb,
 extern "C" uint64_t rddmc_mlp_work_bytes(int batch, int n_out);
 
 extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rddmc_proposal* pr, uint64_t seed,
-                             uint64_t n_packets, void* d_state, void* d_tallies, int n_out, int nA, int nB,
+                             uint64_t n_packets, void* d_state, void* d_tallies, int n_out, int nA, int nB, int nC,
                              const float* d_wf, const void* d_wb, int batch, void* d_work, uint64_t* n_served,
                              void* stream) {
     using namespace rddmc;
     if (!g || !d_table || !pr || !d_state || !d_tallies || !d_wf || !d_wb || !d_work) return RDDMC_ERR_ARG;
     if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
-    if (batch < 64 || batch % 64 || nA != 6 * g->J || nB < 1 || nA + nB > n_out || n_out % 16) return RDDMC_ERR_ARG;
-    if (pr->brick < 1 || g->n[0] % pr->brick || g->n[1] % pr->brick || g->n[2] % pr->brick) return RDDMC_ERR_ARG;
+    if (batch < 64 || batch % 64 || nA != 6 * g->J || nB < 1 || nB > 41 || nC < 0 || nA + nB + nC > n_out ||
+        n_out % 16)
+        return RDDMC_ERR_ARG;
+    if (pr->brick < 1 || pr->brick > 64 || pr->offset < 0 || pr->offset >= pr->brick) return RDDMC_ERR_ARG;
+    if (nC != 0 && nC != 6 * pr->brick * pr->brick) return RDDMC_ERR_ARG;
+    if ((int64_t)pr->n_bricks != proposal_bricks(*g, *pr)) return RDDMC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     WalkLaunch w;
     std::memset(&w, 0, sizeof(w));
@@ -969,11 +1022,13 @@ extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rdd
     fc.inv_xs = (float)(1.0 / std::max(std::fabs(g->edges.front()), std::fabs(g->edges.back())));
     for (unsigned long long q0 = 0; q0 < cnt; q0 += (unsigned long long)batch) {
         const unsigned long long c = std::min<unsigned long long>(batch, cnt - q0);
-        propose_features_kernel<<<(batch + 127) / 128, 128, 0, s>>>(P, pr->d_xc, fc, q0, c, batch, X);
+        const int rows = (int)((c + 63) / 64 * 64);  // forward only the rows in use
+        propose_features_kernel<<<(rows + 127) / 128, 128, 0, s>>>(P, pr->d_xc, fc, q0, c, rows, X);
         if (cudaGetLastError() != cudaSuccess) return RDDMC_ERR_CUDA;
-        const int rc = rddmc_mlp_forward(n_out, d_wf, d_wb, X, batch, d_work, logits, stream);
+        const int rc = rddmc_mlp_forward(n_out, d_wf, d_wb, X, rows, d_work, logits, stream);
         if (rc != RDDMC_OK) return rc;
-        propose_place_kernel<<<(unsigned)((c + 127) / 128), 128, 0, s>>>(P, pr->d_xc, logits, n_out, nA, nB, q0, c);
+        propose_place_kernel<<<(unsigned)((c + 127) / 128), 128, 0, s>>>(P, pr->d_xc, logits, n_out, nA, nB, nC,
+                                                                          q0, c);
         if (cudaGetLastError() != cudaSuccess) return RDDMC_ERR_CUDA;
     }
     if (cudaMemsetAsync(pr->d_queue_count, 0, 8, s) != cudaSuccess) return RDDMC_ERR_CUDA;

@@ -5,10 +5,16 @@ optimiser all run in the library's kernels).
 A proposal is trained for one target grid (cell size, frequency bins,
 temperature): uniform media at L density levels, each a 3^3 grid of the
 target's cell size whose centre cell carries the interior rows of a uniform
-brick, produce first passages through a b^3 brick entered on its -x face at a
-bin of the positive-frequency side whose cell optical depth lies in
-[tau_lo, tau_hi].  A static uniform brick is symmetric under x -> -x, so
-entries at negative frequency are mirrored at inference.
+brick, produce first passages through a b^3 brick from a cell of the brick
+(folded into the fundamental domain of the cube's symmetry group) at a bin of
+the positive-frequency side whose cell optical depth lies in [tau_lo, tau_hi].
+A static uniform brick is symmetric under x -> -x and under the cube's
+reflections and axis permutations, so a packet at negative frequency is
+mirrored, and its cell folded, at inference.  The walk is Markov in
+(cell, bin): a packet can be handed to the proposal in any state it serves.
+
+The network has three heads: exit face x exit bin (A), log2 step bucket (B)
+and, per exit face, the exit cell on that face (C).
 """
 from __future__ import annotations
 
@@ -22,7 +28,7 @@ N_STEP_BUCKETS = 32
 
 class ExitProposal:
     def __init__(self, target: W.Workload, brick: int, rho_levels, tau_lo=5.0, tau_hi=200.0, device="cuda",
-                 hidden_seed=0x5EED0601):
+                 hidden_seed=0x5EED0601, position_head=True):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -67,7 +73,9 @@ class ExitProposal:
         self.xc = t((0.5 * (target.edges()[1:] + target.edges()[:-1])).astype(np.float32), torch.float32)
         self.nA = 6 * self.J
         self.nB = N_STEP_BUCKETS
-        self.n_out = ((self.nA + self.nB + 15) // 16) * 16
+        self.S = self.b * self.b
+        self.nC = 6 * self.S if position_head else 0
+        self.n_out = ((self.nA + self.nB + self.nC + 15) // 16) * 16
         n_par = R.mlp_param_count(self.n_out)
         rng = np.random.default_rng(hidden_seed)
         flat = []
@@ -91,29 +99,39 @@ class ExitProposal:
     def generate(self, n: int, seed: int, p0: int = 0, cap: int = 10_000_000) -> dict:
         """n first-passage samples with network inputs and targets (device tensors)."""
         torch = self.torch
-        out = torch.empty(4 * n, dtype=torch.int32, device=self.device)
+        out = torch.empty(8 * n, dtype=torch.int32, device=self.device)
         steps = torch.empty(n, dtype=torch.int64, device=self.device)
         X = torch.empty((n, 16), dtype=torch.bfloat16, device=self.device)
         tA = torch.empty(n, dtype=torch.int32, device=self.device)
         tB = torch.empty(n, dtype=torch.int32, device=self.device)
+        tC = torch.empty(n, dtype=torch.int32, device=self.device)
         tr = R.FpTrain(X.data_ptr(), tA.data_ptr(), tB.data_ptr(), self.lk.data_ptr(), self.lp.data_ptr(),
-                       self.xc.data_ptr())
+                       self.xc.data_ptr(), tC.data_ptr())
         R.fp_generate([p.grid for p in self.problems], [p.table.data_ptr() for p in self.problems], self.b, self.jlo,
                       self.jhi, seed, p0, n, cap, out.data_ptr(), steps.data_ptr(), tr, self.stream())
-        return dict(X=X, tA=tA, tB=tB, rec=out.view(n, 4), steps=steps)
+        return dict(X=X, tA=tA, tB=tB, tC=tC, rec=out.view(n, 8), steps=steps)
 
     # ------------------------------------------------------------------ training
-    def loss_grad(self, X, tA, tB):
+    def _loss_grad(self, X, tA, tB, tC, B, work, loss):
+        R.mlp_loss_grad(self.n_out, self.nA, self.nB, self.wf.data_ptr(), self.wb.data_ptr(), X.data_ptr(),
+                        tA.data_ptr(), tB.data_ptr(), B, work.data_ptr(), self.grad.data_ptr(), loss.data_ptr(),
+                        self.stream(), nC=self.nC, S=self.S, d_tc=tC.data_ptr() if self.nC else 0)
+
+    def loss_grad(self, X, tA, tB, tC=None):
         B = X.shape[0]
         work = self.torch.empty(R.mlp_work_bytes(B, self.n_out), dtype=self.torch.uint8, device=self.device)
         loss = self.torch.zeros(1, dtype=self.torch.float32, device=self.device)
-        R.mlp_loss_grad(self.n_out, self.nA, self.nB, self.wf.data_ptr(), self.wb.data_ptr(), X.data_ptr(),
-                        tA.data_ptr(), tB.data_ptr(), B, work.data_ptr(), self.grad.data_ptr(), loss.data_ptr(),
-                        self.stream())
+        if tC is None:
+            tC = self.torch.full((B,), -1, dtype=self.torch.int32, device=self.device)
+        self._loss_grad(X, tA, tB, tC, B, work, loss)
         return loss
 
-    def train(self, data: dict, iters: int, batch: int = 8192, lr: float = 1e-3, seed: int = 1, log_every=0):
+    def train(self, data: dict, iters: int, batch: int = 8192, lr: float = 1e-3, seed: int = 1, log_every=0,
+              lr_final: float = None):
+        """Adam on random minibatches; the step size decays from lr to lr_final
+        (default lr / 20) on a cosine schedule."""
         torch = self.torch
+        lr_final = lr / 20.0 if lr_final is None else lr_final
         n = data["X"].shape[0]
         gen = torch.Generator(device=self.device)
         gen.manual_seed(seed)
@@ -122,13 +140,12 @@ class ExitProposal:
         hist = []
         for it in range(iters):
             idx = torch.randint(0, n, (batch,), device=self.device, generator=gen)
-            X, tA, tB = data["X"][idx].contiguous(), data["tA"][idx].contiguous(), data["tB"][idx].contiguous()
-            R.mlp_loss_grad(self.n_out, self.nA, self.nB, self.wf.data_ptr(), self.wb.data_ptr(), X.data_ptr(),
-                            tA.data_ptr(), tB.data_ptr(), batch, work.data_ptr(), self.grad.data_ptr(),
-                            loss.data_ptr(), self.stream())
+            X, tA, tB, tC = (data[k][idx].contiguous() for k in ("X", "tA", "tB", "tC"))
+            self._loss_grad(X, tA, tB, tC, batch, work, loss)
             self.step += 1
+            lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * it / max(1, iters - 1)))
             R.mlp_adam(self.n_out, self.wf.data_ptr(), self.wb.data_ptr(), self.grad.data_ptr(), self.m.data_ptr(),
-                       self.v.data_ptr(), self.step, lr, stream=self.stream())
+                       self.v.data_ptr(), self.step, lr_t, stream=self.stream())
             if log_every and (it % log_every == 0 or it == iters - 1):
                 hist.append((it, float(loss.item()) / batch))
         return hist
@@ -138,8 +155,7 @@ class ExitProposal:
         tot = 0.0
         for s in range(0, n, batch):
             sl = slice(s, s + batch)
-            tot += float(self.loss_grad(data["X"][sl].contiguous(), data["tA"][sl].contiguous(),
-                                        data["tB"][sl].contiguous()).item())
+            tot += float(self.loss_grad(*(data[k][sl].contiguous() for k in ("X", "tA", "tB", "tC"))).item())
         return tot / n
 
     def logits(self, X):
@@ -150,39 +166,40 @@ class ExitProposal:
                       out.data_ptr(), self.stream())
         return out
 
-
     # ------------------------------------------------------------------ walking with the proposal
-    def attach(self, problem, brick_rho, batch: int = 4096):
-        """Proposal state for walking `problem` (its grid cut into bricks of
-        self.b^3 cells with per-brick density brick_rho, brick index axis 0
-        fastest).  Bricks whose density lies outside the trained levels take no
-        proposals."""
+    def attach(self, problem, brick_rho, offset: int = 0, batch: int = 4096):
+        """Proposal state for walking `problem`, its grid cut into bricks of
+        self.b^3 cells with boundaries at cell indices = offset (mod b) and
+        per-brick density brick_rho (partial bricks included, brick index axis
+        0 fastest).  Bricks whose density lies outside the trained levels take
+        no proposals; nor do partial bricks."""
         torch = self.torch
-        kdz = problem.w.tau0 / problem.w.R * np.asarray(brick_rho, dtype=np.float64) * self.dz
-        lk = np.log10(kdz)
-        lo, hi = np.log10(min(self.levels)), np.log10(max(self.levels))
         rho = np.asarray(brick_rho, dtype=np.float64)
+        lk = np.log10(problem.w.tau0 / problem.w.R * rho * self.dz)
+        lo, hi = np.log10(min(self.levels)), np.log10(max(self.levels))
         lk = np.where((np.log10(rho) >= lo) & (np.log10(rho) <= hi), lk, -1.0e30).astype(np.float32)
-        n = max(problem.state_packets, 1)
-        att = dict(
+        return dict(
             lk=torch.as_tensor(lk, device=self.device),
             count=torch.zeros(1, dtype=torch.int64, device=self.device),
+            offset=int(offset),
             batch=batch,
             work=torch.empty(R.mlp_work_bytes(batch, self.n_out) + 256 + batch * 32 + 256 + batch * self.n_out * 4
                              + 4096, dtype=torch.uint8, device=self.device))
-        return att
 
-    def run(self, problem, brick_rho, n_packets: int, seed: int, steps_per_launch: int = 4096, batch: int = 4096,
-            tau_lo: float = 5.0, tau_hi: float = 200.0, max_epochs: int = 100_000) -> dict:
-        """Walk n_packets on `problem` with proposals; returns the tallies and
-        the number of walk launches and proposal rounds."""
+    def run(self, problem, brick_rho, n_packets: int, seed: int, offset: int = 0, steps_per_launch: int = 16384, batch: int = 65536, tau_lo: float = 5.0, tau_hi: float = 200.0,
+            max_epochs: int = 1_000_000) -> dict:
+        """Walk n_packets on `problem` with proposals: walk launches of at most
+        steps_per_launch transitions per packet alternate with proposal rounds
+        for the packets parked meanwhile, until every packet has escaped or been
+        aborted.  Returns the tallies and the number of walk launches, proposal
+        rounds and proposals served."""
         torch = self.torch
         problem.ensure_state(n_packets)
-        att = self.attach(problem, brick_rho, batch)
+        att = self.attach(problem, brick_rho, offset, batch)
         qpid = torch.empty(n_packets, dtype=torch.int64, device=self.device)
-        qface = torch.empty(n_packets, dtype=torch.int32, device=self.device)
-        prop = R.Proposal(self.b, 0, att["lk"].data_ptr(), self.lp.data_ptr(), self.xc.data_ptr(), np.log10(tau_lo),
-                          np.log10(tau_hi), att["count"].data_ptr(), qpid.data_ptr(), qface.data_ptr())
+        prop = R.Proposal(self.b, att["offset"], att["lk"].data_ptr(), self.lp.data_ptr(), self.xc.data_ptr(),
+                          np.log10(tau_lo), np.log10(tau_hi), att["count"].data_ptr(), qpid.data_ptr(),
+                          int(att["lk"].numel()), 0)
         problem.reset()
         launches = rounds = served = 0
         for ep in range(max_epochs):
@@ -190,7 +207,7 @@ class ExitProposal:
             launches += 1
             k = R.propose(problem.grid, problem.table.data_ptr(), prop, seed, n_packets, problem.state.data_ptr(),
                           problem.tally.data_ptr(), self.n_out, self.nA, self.nB, self.wf.data_ptr(),
-                          self.wb.data_ptr(), batch, att["work"].data_ptr(), problem.stream())
+                          self.wb.data_ptr(), batch, att["work"].data_ptr(), problem.stream(), nC=self.nC)
             served += k
             rounds += 1 if k else 0
             t = problem.read()

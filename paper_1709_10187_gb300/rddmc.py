@@ -72,14 +72,15 @@ class Tallies(ctypes.Structure):
 
 class FpTrain(ctypes.Structure):
     _fields_ = [("d_x", ctypes.c_void_p), ("d_ta", ctypes.c_void_p), ("d_tb", ctypes.c_void_p),
-                ("d_lk", ctypes.c_void_p), ("d_lp", ctypes.c_void_p), ("d_xc", ctypes.c_void_p)]
+                ("d_lk", ctypes.c_void_p), ("d_lp", ctypes.c_void_p), ("d_xc", ctypes.c_void_p),
+                ("d_tc", ctypes.c_void_p)]
 
 
 class Proposal(ctypes.Structure):
-    _fields_ = [("brick", ctypes.c_int32), ("reserved", ctypes.c_int32), ("d_brick_lk", ctypes.c_void_p),
+    _fields_ = [("brick", ctypes.c_int32), ("offset", ctypes.c_int32), ("d_brick_lk", ctypes.c_void_p),
                 ("d_lp", ctypes.c_void_p), ("d_xc", ctypes.c_void_p), ("log_tau_lo", ctypes.c_double),
                 ("log_tau_hi", ctypes.c_double), ("d_queue_count", ctypes.c_void_p), ("d_queue_pid", ctypes.c_void_p),
-                ("d_queue_face", ctypes.c_void_p)]
+                ("n_bricks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class RDDMCError(RuntimeError):
@@ -115,13 +116,13 @@ def lib():
         L.rddmc_cell_tau.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
         L.rddmc_fp_generate.argtypes = [vp, vp, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp,
                                         ctypes.POINTER(FpTrain), vp]
-        L.rddmc_propose.argtypes = [vp, vp, ctypes.POINTER(Proposal), u64, u64, vp, vp, i32, i32, i32, vp, vp, i32, vp,
-                                    ctypes.POINTER(ctypes.c_uint64), vp]
+        L.rddmc_propose.argtypes = [vp, vp, ctypes.POINTER(Proposal), u64, u64, vp, vp, i32, i32, i32, i32, vp, vp, i32,
+                                    vp, ctypes.POINTER(ctypes.c_uint64), vp]
         L.rddmc_mlp_param_count.argtypes = [i32]
         L.rddmc_mlp_work_bytes.argtypes = [i32, i32]
         L.rddmc_mlp_to_bf16.argtypes = [i32, vp, vp, vp]
         L.rddmc_mlp_forward.argtypes = [i32, vp, vp, vp, i32, vp, vp, vp]
-        L.rddmc_mlp_loss_grad.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
+        L.rddmc_mlp_loss_grad.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         L.rddmc_mlp_adam.argtypes = [i32, vp, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float, vp]
         L.rddmc_batch_create.argtypes = [vp, vp, vp, i32, ctypes.POINTER(vp)]
@@ -435,6 +436,8 @@ def cell_tau(grid, d_table: int, cell: int, J: int, stream: int = 0) -> np.ndarr
 
 
 def fp_generate(grids, d_tables, b, jlo, jhi, seed, p0, n, cap, d_out, d_steps, train=None, stream=0):
+    """First passages through a uniform brick: d_out receives 8 int32 per
+    sample (rddmc_fp_generate)."""
     L = len(grids)
     g = (ctypes.c_void_p * L)(*grids)
     t = (ctypes.c_void_p * L)(*d_tables)
@@ -464,11 +467,12 @@ def mlp_forward(n_out, d_wf, d_wb, d_x, batch, d_work, d_logits, stream=0):
                                                         ctypes.c_void_p(d_logits), ctypes.c_void_p(stream)))
 
 
-def mlp_loss_grad(n_out, nA, nB, d_wf, d_wb, d_x, d_ta, d_tb, batch, d_work, d_grad, d_loss, stream=0):
+def mlp_loss_grad(n_out, nA, nB, d_wf, d_wb, d_x, d_ta, d_tb, batch, d_work, d_grad, d_loss, stream=0, nC=0, S=0,
+                  d_tc=0):
     _check("rddmc_mlp_loss_grad", lib().rddmc_mlp_loss_grad(
-        int(n_out), int(nA), int(nB), ctypes.c_void_p(d_wf), ctypes.c_void_p(d_wb), ctypes.c_void_p(d_x),
-        ctypes.c_void_p(d_ta), ctypes.c_void_p(d_tb), int(batch), ctypes.c_void_p(d_work), ctypes.c_void_p(d_grad),
-        ctypes.c_void_p(d_loss), ctypes.c_void_p(stream)))
+        int(n_out), int(nA), int(nB), int(nC), int(S), ctypes.c_void_p(d_wf), ctypes.c_void_p(d_wb),
+        ctypes.c_void_p(d_x), ctypes.c_void_p(d_ta), ctypes.c_void_p(d_tb), ctypes.c_void_p(d_tc or None), int(batch),
+        ctypes.c_void_p(d_work), ctypes.c_void_p(d_grad), ctypes.c_void_p(d_loss), ctypes.c_void_p(stream)))
 
 
 def mlp_adam(n_out, d_wf, d_wb, d_grad, d_m, d_v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
@@ -478,10 +482,11 @@ def mlp_adam(n_out, d_wf, d_wb, d_grad, d_m, d_v, step, lr, beta1=0.9, beta2=0.9
 
 
 def propose(grid, d_table, proposal: Proposal, seed, n_packets, d_state, d_tallies, n_out, nA, nB, d_wf, d_wb, batch,
-            d_work, stream=0) -> int:
+            d_work, stream=0, nC=0) -> int:
     served = ctypes.c_uint64()
     _check("rddmc_propose", lib().rddmc_propose(
         ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(proposal), int(seed), int(n_packets),
-        ctypes.c_void_p(d_state), ctypes.c_void_p(d_tallies), int(n_out), int(nA), int(nB), ctypes.c_void_p(d_wf),
+        ctypes.c_void_p(d_state), ctypes.c_void_p(d_tallies), int(n_out), int(nA), int(nB), int(nC),
+        ctypes.c_void_p(d_wf),
         ctypes.c_void_p(d_wb), int(batch), ctypes.c_void_p(d_work), ctypes.byref(served), ctypes.c_void_p(stream)))
     return served.value

@@ -158,32 +158,53 @@ def gaussian_random_field(n: int, slope: float, rng) -> np.ndarray:
 @dataclasses.dataclass(frozen=True)
 class ClumpyMedium:
     """Brick-resolution clumpy medium: a lognormal density and a Gaussian
-    turbulent velocity, constant over bricks of `brick`^3 cells."""
+    turbulent velocity, constant over bricks of `brick`^3 cells whose
+    boundaries sit at cell indices = offset (mod brick) on every axis (partial
+    bricks at the cube's faces when offset > 0)."""
     workload: Workload
     brick: int
     n_rel: np.ndarray   # per cell, axis 0 fastest (mean 1)
     v_kms: np.ndarray   # per cell x3
-    brick_rho: np.ndarray  # per brick (nb^3, axis 0 fastest)
+    brick_rho: np.ndarray  # per brick (nbx^3, axis 0 fastest)
+    offset: int = 0
+    nbx: int = 0        # bricks per axis, partial ones included
+    full: np.ndarray = None  # per brick: True when all brick^3 cells lie in the cube
+
+
+def brick_lattice(n: int, brick: int, offset: int):
+    """Bricks per axis and the brick coordinate of every cell index along an
+    axis of n cells for a lattice of `brick`-cell bricks with a boundary at
+    cell index `offset`."""
+    sh = (brick - offset % brick) % brick
+    nbx = (n + sh + brick - 1) // brick
+    c = (np.arange(n) + sh) // brick
+    return nbx, c, sh
 
 
 def clumpy_medium(n: int = 128, J: int = 256, x_max: float = 256.0, tau0: float = 1.0e7, T: float = 1.0e4,
                   brick: int = 8, sigma_ln: float = 1.0, slope: float = -11.0 / 3.0, sigma_v_kms: float = 10.0,
-                  packets: int = 100_000_000, seed: int = 0x5EED0005, name: str = "clumpy") -> ClumpyMedium:
+                  packets: int = 100_000_000, seed: int = 0x5EED0005, name: str = "clumpy",
+                  offset: int = 0) -> ClumpyMedium:
     """The clumpy 3D workload: an n^3 cube of cells x J bins over [-x_max, x_max],
     lognormal density rho = exp(sigma_ln g - sigma_ln^2/2) from a Gaussian
     random field g with spectral slope `slope`, three independent fields of the
     same spectrum for the velocity (sigma_v per component), both drawn on the
-    (n/brick)^3 grid of bricks and held constant inside each brick; tau0 is the
-    line-centre optical depth centre-to-face at the mean density."""
+    grid of bricks and held constant inside each brick; tau0 is the line-centre
+    optical depth centre-to-face at the mean density.  The brick boundaries sit
+    at cell indices = offset (mod brick); with offset 0 and n a multiple of
+    brick every brick is whole."""
     rng = np.random.default_rng(seed)
-    nb = n // brick
-    g = gaussian_random_field(nb, slope, rng)
+    nbx, c, sh = brick_lattice(n, brick, offset)
+    g = gaussian_random_field(nbx, slope, rng)
     rho_b = np.exp(sigma_ln * g - 0.5 * sigma_ln ** 2)
-    v_b = np.stack([sigma_v_kms * gaussian_random_field(nb, slope, rng) for _ in range(3)], axis=-1)
+    v_b = np.stack([sigma_v_kms * gaussian_random_field(nbx, slope, rng) for _ in range(3)], axis=-1)
     # (i2, i1, i0) index order of the brick fields -> per-cell arrays, axis 0 fastest
-    rep = lambda a: np.repeat(np.repeat(np.repeat(a, brick, axis=0), brick, axis=1), brick, axis=2)
+    rep = lambda a: a[np.ix_(c, c, c)]
     rho_c = rep(rho_b)
     v_c = np.stack([rep(v_b[..., a]) for a in range(3)], axis=-1)
+    lo = np.arange(nbx) * brick - sh
+    full1 = (lo >= 0) & (lo + brick <= n)
+    full = full1[:, None, None] & full1[None, :, None] & full1[None, None, :]
     w = Workload(name, 3, (n, n, n), J, -x_max, x_max, tau0, T, packets, seed)
     return ClumpyMedium(w, brick, rho_c.reshape(-1).astype(np.float64), v_c.reshape(-1, 3).astype(np.float64),
-                        rho_b.reshape(-1).astype(np.float64))
+                        rho_b.reshape(-1).astype(np.float64), offset, nbx, full.reshape(-1))

@@ -39,9 +39,10 @@ def test_first_passages_match_oracle_bit_exactly(proposal):
     out, steps = C.fp_samples(rows, p.b, p.jlo, p.jhi, 77, 1000, n, 10_000_000)
     assert np.array_equal(d["rec"].cpu().numpy(), out)
     assert np.array_equal(d["steps"].cpu().numpy().astype(np.uint64), steps)
-    tA = d["tA"].cpu().numpy()
-    ok = out[:, 2] < 6
-    assert np.array_equal(tA[ok], out[ok, 2] * p.J + out[ok, 3]) and np.all(tA[~ok] == -1)
+    tA, tC = d["tA"].cpu().numpy(), d["tC"].cpu().numpy()
+    ok = out[:, 3] < 6
+    assert np.array_equal(tA[ok], out[ok, 3] * p.J + out[ok, 4]) and np.all(tA[~ok] == -1)
+    assert np.array_equal(tC[ok], out[ok, 3] * p.S + out[ok, 5]) and np.all(tC[~ok] == -1)
 
 
 def test_network_loss_and_gradients_match_fp64_reference(proposal):
@@ -50,8 +51,9 @@ def test_network_loss_and_gradients_match_fp64_reference(proposal):
     Bsz = 256
     d = p.generate(Bsz, seed=91)
     X = d["X"]
-    tA, tB = d["tA"], d["tB"]
-    loss = p.loss_grad(X, tA, tB)
+    tA, tB, tC = d["tA"], d["tB"], d["tC"]
+    assert p.nC == 6 * p.b * p.b
+    loss = p.loss_grad(X, tA, tB, tC)
     torch.cuda.synchronize()
     g_gpu = p.grad.cpu().numpy().astype(np.float64)
     w_bf = p.wb.float().cpu().numpy().astype(np.float64)   # the weights the tensor cores saw
@@ -65,7 +67,7 @@ def test_network_loss_and_gradients_match_fp64_reference(proposal):
     for s, o in offs:
         flat[s:s + o] = w_f[s:s + o]
     lo, g_ref = M.loss_and_grad(flat, p.n_out, p.nA, p.nB, X.float().cpu().numpy(), tA.cpu().numpy(),
-                                tB.cpu().numpy())
+                                tB.cpu().numpy(), p.nC, p.S, tC.cpu().numpy())
     assert float(loss.item()) / Bsz == pytest.approx(lo, rel=1e-2)
     off = 0
     for (o, i) in M.shapes(p.n_out):
