@@ -120,10 +120,21 @@ typedef struct rddmc_leak_params {
  *                 (multiple of 4) between warp refills.
  *   table_in_smem 1: stage the fast row heads in shared memory when they fit;
  *                 0: gather them from global memory (L1/L2).
+ *   time_slice_us wall-time slice (0 = none): a thread that reaches a chunk
+ *                 boundary more than this many microseconds after its CTA
+ *                 started saves its packet and takes no new one.  Needs saved
+ *                 states (steps_per_launch > 0, resume = 1 or a proposal).
+ *                 Results do not depend on where packets are cut.  When states
+ *                 are saved and resume = 0, every packet is first marked as not
+ *                 started, so packets a sliced call never reached start in a
+ *                 later call with resume = 1.
  *   proposal      NULL, or a learned exit proposal (rddmc_proposal; 3D grids in
  *                 DDMC mode): packets in a state it serves are parked for
- *                 rddmc_propose instead of walking through their brick.  Requires
- *                 steps_per_launch > 0 or resume = 1 so parked states are kept.
+ *                 rddmc_propose instead of walking through their brick.  The
+ *                 walk checks at transition counts that are multiples of
+ *                 `chunk` (and at emission), so parking does not depend on
+ *                 slicing.  Requires steps_per_launch > 0, resume = 1 or
+ *                 time_slice_us > 0 so parked states are kept.
  */
 typedef struct rddmc_run_opts {
     uint64_t seed;
@@ -135,7 +146,7 @@ typedef struct rddmc_run_opts {
     int32_t threads_per_cta;
     int32_t chunk;
     int32_t table_in_smem;
-    int32_t reserved;
+    int32_t time_slice_us;
     const struct rddmc_proposal* proposal;
 } rddmc_run_opts;
 
@@ -414,9 +425,16 @@ int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_table
  * on an axis has brick coordinate (i + (brick - offset) % brick) / brick, and
  * the brick index is c0 + nb0 (c1 + nb1 c2) with nb_a = ceil((n_a +
  * (brick - offset) % brick) / brick); n_bricks must equal nb0 nb1 nb2, the
- * length of d_brick_lk.  Only bricks wholly inside the grid take proposals.
+ * length of d_brick_lk.  Only bricks wholly inside the grid take proposals,
+ * and only in their inner cube: cells whose brick-local coordinates all lie in
+ * [margin, brick - 1 - margin] (0 <= 2 margin < brick).  The network models
+ * the first passage out of that inner cube of side brick - 2 margin; with
+ * margin >= 1 on a medium that is uniform over each brick, every cell of the
+ * inner cube and all its neighbours share one medium, so the first passage is
+ * exactly that of a uniform medium, and the walk takes over in the brick's
+ * outer shell (density contrast, Doppler shifts and exterior faces included).
  * Brick B with brick_lk[B] = log10(k0 dz) of its (uniform) medium, or below
- * -1e29 when it is not eligible, serves a packet in one of its cells at bin j
+ * -1e29 when it is not eligible, serves a packet in its inner cube at bin j
  * when log_tau_lo <= brick_lk[B] + lp[j] <= log_tau_hi.  The walk is Markov in
  * (cell, bin), so a packet may be handed over in any such state: the walk
  * checks once per chunk of transitions (and at emission or resumption) and
@@ -431,7 +449,7 @@ typedef struct rddmc_proposal {
     unsigned long long* d_queue_count;
     unsigned long long* d_queue_pid;
     int32_t n_bricks;
-    int32_t reserved;
+    int32_t margin;
 } rddmc_proposal;
 
 /* Serve the parked packets of a walk with the trained network: features of
@@ -439,10 +457,11 @@ typedef struct rddmc_proposal {
  * forward pass in batches of at most `batch` rows (a multiple of 64; d_work of
  * rddmc_mlp_work_bytes(batch, n_out) plus batch * (16 * 2 + n_out * 4) bytes),
  * one exit (face, bin, step bucket, and the exit cell on the face from head C
- * when nC = 6 brick^2, uniform when nC = 0) sampled per packet from its event
+ * when nC = 6 (brick - 2 margin)^2, uniform when nC = 0) sampled per packet
+ * from its event
  * stream, mapped back to the world frame (and mirrored back for negative
- * frequencies), placed across the exit face (Doppler rebin or escape tally as
- * the face's row says), and the packet set in flight again.  Clears the queue.
+ * frequencies), placed across the exit face of the inner cube (Doppler rebin
+ * or escape tally as the face's row says), and the packet set in flight again.  Clears the queue.
  * Synchronises `stream`. */
 int rddmc_propose(const rddmc_grid* grid, const void* d_table, const rddmc_proposal* proposal, uint64_t seed,
                   uint64_t n_packets, void* d_state, void* d_tallies, int n_out, int nA, int nB, int nC,

@@ -327,11 +327,14 @@ int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_r
     if (o->chunk < 0 || o->chunk % 4 != 0 || o->ctas_per_sm < 0 || o->threads_per_cta < 0) return RDDMC_ERR_ARG;
     if (o->threads_per_cta && (o->threads_per_cta % 32 != 0 || o->threads_per_cta > 256)) return RDDMC_ERR_ARG;
     if (o->resume != 0 && o->resume != 1) return RDDMC_ERR_ARG;
+    if (o->time_slice_us < 0) return RDDMC_ERR_ARG;
+    if (o->time_slice_us > 0 && o->steps_per_launch == 0 && o->resume == 0 && !o->proposal) return RDDMC_ERR_ARG;
     if (o->proposal) {
         const rddmc_proposal* pr = o->proposal;
         if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
-        if (o->steps_per_launch == 0 && o->resume == 0) return RDDMC_ERR_ARG;
+        if (o->steps_per_launch == 0 && o->resume == 0 && o->time_slice_us == 0) return RDDMC_ERR_ARG;
         if (pr->brick < 1 || pr->brick > 64 || pr->offset < 0 || pr->offset >= pr->brick) return RDDMC_ERR_ARG;
+        if (pr->margin < 0 || 2 * pr->margin >= pr->brick) return RDDMC_ERR_ARG;
         if ((int64_t)pr->n_bricks != proposal_bricks(*g, *pr)) return RDDMC_ERR_ARG;
         if (!pr->d_brick_lk || !pr->d_lp || !pr->d_xc || !pr->d_queue_count || !pr->d_queue_pid)
             return RDDMC_ERR_ARG;

@@ -369,7 +369,7 @@ cudaError_t enqueue(const rddmc_batch* b, const BatchParams& P, const rddmc_run_
 
 int check_opts(const rddmc_run_opts* o) {
     if (!o) return RDDMC_ERR_ARG;
-    if (o->steps_per_launch != 0 || o->resume != 0) return RDDMC_ERR_UNSUPPORTED;
+    if (o->steps_per_launch != 0 || o->resume != 0 || o->time_slice_us != 0) return RDDMC_ERR_UNSUPPORTED;
     if (o->chunk < 0 || o->chunk % 4 != 0 || o->ctas_per_sm < 0 || o->threads_per_cta < 0) return RDDMC_ERR_ARG;
     if (o->threads_per_cta && (o->threads_per_cta % 32 != 0 || o->threads_per_cta > 256)) return RDDMC_ERR_ARG;
     return RDDMC_OK;

@@ -58,12 +58,14 @@ extern "C" int rddmc_launch_packets_noalloc(const rddmc_grid* g, const void* d_t
     if (o->chunk < 0 || o->chunk % 4 != 0 || o->ctas_per_sm < 0 || o->threads_per_cta < 0) return RDDMC_ERR_ARG;
     if (o->threads_per_cta && (o->threads_per_cta % 32 != 0 || o->threads_per_cta > 256)) return RDDMC_ERR_ARG;
     if (o->resume != 0 && o->resume != 1) return RDDMC_ERR_ARG;
+    if (o->time_slice_us < 0) return RDDMC_ERR_ARG;
+    if (o->time_slice_us > 0 && o->steps_per_launch == 0 && o->resume == 0) return RDDMC_ERR_ARG;
     if (o->proposal) return RDDMC_ERR_UNSUPPORTED;  // parked packets need a caller-owned state buffer
     if (tally_bytes < rddmc::tally_bytes_for(g->J)) return RDDMC_ERR_SIZE;
     // A run to completion only uses the packet cursor; time-sliced or resumed
     // runs keep every packet's state in the array, which bounds their packet
     // count (about 1.3 million packets).
-    const bool sliced = o->steps_per_launch != 0 || o->resume != 0;
+    const bool sliced = o->steps_per_launch != 0 || o->resume != 0 || o->time_slice_us != 0;
     const uint64_t need = sliced ? rddmc::state_bytes_for(o->n_packets) : 256ull;
     if (need > (uint64_t)RDDMC_NOALLOC_SCRATCH_BYTES) return RDDMC_ERR_SIZE;
     void* scratch = nullptr;

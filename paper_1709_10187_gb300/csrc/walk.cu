@@ -58,6 +58,7 @@ struct WalkParams {
     uint8_t* st_status;
     unsigned long long* tally;
     unsigned long long n_packets, max_steps, slice, mc_cap;
+    unsigned long long time_slice_ns;  // wall-time slice of the launch (0 = none)
     uint32_t k0, k1;
     uint32_t rk0[10], rk1[10];  // Philox round keys k + r * (Weyl constant)
     int J, n_rows, n_class, ncell, chunk;
@@ -68,8 +69,10 @@ struct WalkParams {
     float a, lambda;
     int src_ncand[3], src_cand[3][2], src_nbin, src_bin[2];
     // learned exit proposal (3D DDMC): bricks of prop_b^3 cells, brick
-    // coordinate (i + prop_sh) / prop_b of cell index i on every axis
-    int prop_b, prop_sh, prop_nbx, prop_nby;
+    // coordinate (i + prop_sh) / prop_b of cell index i on every axis; the
+    // served region of a brick is its inner cube of side prop_r = prop_b -
+    // 2 prop_m
+    int prop_b, prop_sh, prop_nbx, prop_nby, prop_m, prop_r;
     const float* prop_lk;
     const float* prop_lp;
     float prop_llo, prop_lhi;
@@ -88,6 +91,12 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const WalkParams& P) {
         c = make_uint4(hi1 ^ c.y ^ P.rk0[r], lo1, hi0 ^ c.w ^ P.rk1[r], lo0);
     }
     return c;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ unsigned word_of(const uint4& r, unsigned q) {
@@ -371,16 +380,19 @@ __device__ __forceinline__ unsigned brick_of(const WalkParams& P, unsigned cell)
 }
 
 // Whether a packet at (cell, bin) is served by the proposal: its brick lies
-// wholly inside the grid, is eligible (brick_lk above -1e29) and the bin's cell
+// wholly inside the grid, the cell lies in the brick's inner cube (margin
+// prop_m), the brick is eligible (brick_lk above -1e29) and the bin's cell
 // optical depth 10^(brick_lk + lp[bin]) lies in [10^llo, 10^lhi].
 __device__ __forceinline__ bool prop_takes(const WalkParams& P, unsigned cell, unsigned bin) {
     unsigned ic[3];
     cell_coords(P, cell, ic);
-    const int b = P.prop_b, sh = P.prop_sh;
+    const int b = P.prop_b, sh = P.prop_sh, m = P.prop_m;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int lo = (((int)ic[a] + sh) / b) * b - sh;
         if (lo < 0 || lo + b > P.n[a]) return false;
+        const int l = (int)ic[a] - lo;
+        if (l < m || l > b - 1 - m) return false;
     }
     const float lkb = __ldg(&P.prop_lk[brick_of(P, cell)]);
     if (!(lkb > -1.0e29f)) return false;
@@ -411,6 +423,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
     const unsigned lane = threadIdx.x & 31u;
     const unsigned J = (unsigned)P.J;
     const unsigned nr1 = (unsigned)P.n_rows - 1u;
+    const unsigned long long t_begin = P.time_slice_ns ? global_ns() : 0ull;
     bool have = false, exhausted = false;
     unsigned long long pid = 0, t = 0, e = 0, t_stop = 0;
     unsigned cell = 0, cls = 0, s = 0;  // s = cls * J + bin: the row of the state
@@ -553,6 +566,17 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         }
         if (__all_sync(FULL, exhausted && !have)) break;
         if (!have) continue;
+        if (P.time_slice_ns && global_ns() - t_begin > P.time_slice_ns) {
+            // end of the wall-time slice: save the packet, take no new one
+            P.st_cell[pid] = cell;
+            P.st_bin[pid] = min(s - cls * J, J - 1u);
+            P.st_t[pid] = t;
+            P.st_e[pid] = e;
+            P.st_status[pid] = PK_INFLIGHT;
+            have = false;
+            exhausted = true;
+            continue;
+        }
         if (PROPOSE && prop_takes(P, cell, min(s - cls * J, J - 1u))) {
             // the walk is Markov in (cell, bin): a packet in a state the proposal
             // serves waits for it (checked once per chunk of transitions)
@@ -561,14 +585,22 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
             P.st_t[pid] = t;
             P.st_e[pid] = e;
             P.st_status[pid] = PK_PARKED;
-            const unsigned long long k = atomicAdd(P.prop_qcount, 1ull);
+            // one queue atomic per warp: the lanes parking now share a block of slots
+            const unsigned grp = __activemask();
+            const int lead = __ffs(grp) - 1;
+            unsigned long long k0q = 0;
+            if ((int)lane == lead) k0q = atomicAdd(P.prop_qcount, (unsigned long long)__popc(grp));
+            k0q = __shfl_sync(grp, k0q, lead);
+            const unsigned long long k = k0q + (unsigned long long)__popc(grp & ((1u << lane) - 1u));
             P.prop_qpid[min(k, P.n_packets - 1ull)] = pid;
             have = false;
             continue;
         }
 
-        // ---- run up to `chunk` transitions
-        unsigned long long lim = t + (unsigned long long)P.chunk;
+        // ---- run up to `chunk` transitions (with a proposal, up to the next
+        // multiple of chunk, so the parking checkpoints do not depend on slicing)
+        unsigned long long lim = PROPOSE ? (t / (unsigned long long)P.chunk + 1ull) * (unsigned long long)P.chunk
+                                         : t + (unsigned long long)P.chunk;
         lim = lim < t_stop ? lim : t_stop;
         lim = lim < P.max_steps ? lim : P.max_steps;
         const unsigned long long t0 = t;
@@ -717,10 +749,12 @@ __global__ void scatter_samples_kernel(float a, float x_in, const float2* __rest
 // frame the network was trained in): a uniform static brick is invariant
 // under the cube's reflections and axis permutations, so the exit sampled in
 // the folded frame is mapped back by the inverse transform.
+// First cell, per axis, of the inner cube (the served region) of the brick
+// holding a cell.
 __device__ __forceinline__ void brick_base(const WalkParams& P, const unsigned ic[3], int base[3]) {
     const int b = P.prop_b, sh = P.prop_sh;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) base[a] = (((int)ic[a] + sh) / b) * b - sh;
+    for (int a = 0; a < 3; ++a) base[a] = (((int)ic[a] + sh) / b) * b - sh + P.prop_m;
 }
 
 __device__ __forceinline__ void fold_parked(const WalkParams& P, unsigned cell, int base[3], int C[3], int perm[3],
@@ -730,8 +764,8 @@ __device__ __forceinline__ void fold_parked(const WalkParams& P, unsigned cell, 
     brick_base(P, ic, base);
     int l[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) l[a] = min(max((int)ic[a] - base[a], 0), P.prop_b - 1);
-    fold_cell(l, P.prop_b, C, perm, flip);
+    for (int a = 0; a < 3; ++a) l[a] = min(max((int)ic[a] - base[a], 0), P.prop_r - 1);
+    fold_cell(l, P.prop_r, C, perm, flip);
 }
 
 // Network inputs of queued packets q0 .. q0+cnt (rows past cnt are zeroed).
@@ -753,7 +787,7 @@ __global__ void propose_features_kernel(const WalkParams P, const float* __restr
     int base[3], C[3], perm[3];
     bool flip[3];
     fold_parked(P, cell, base, C, perm, flip);
-    features(P.prop_lk[brick_of(P, cell)], P.prop_lp[j], xc[j], C, P.prop_b, fc, X + r * kFeat);
+    features(P.prop_lk[brick_of(P, cell)], P.prop_lp[j], xc[j], C, P.prop_r, fc, X + r * kFeat);
 }
 
 // Inverse-CDF draw from softmax(z[0..n)) with uniform u in (0,1).
@@ -796,7 +830,7 @@ __global__ void propose_place_kernel(const WalkParams P, const float* __restrict
     // head B: log2 step bucket
     const int kb = min(softmax_draw(z + nA, nB, es.u01()), 40);
     const unsigned long long steps = (1ull << kb) + (unsigned long long)(es.u01() * (float)(1ull << kb));
-    const int b = P.prop_b;
+    const int b = P.prop_r;  // side of the served inner cube
     const int fc_ = ca / (int)J;
     unsigned jo = (unsigned)(ca % (int)J);
     if (mirror) jo = J - 1u - jo;
@@ -909,6 +943,7 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     P.max_steps = o.max_steps ? o.max_steps : (1ull << 62);
     P.mc_cap = o.max_steps ? o.max_steps : 100000000ull;  // events per MC excursion
     P.slice = o.steps_per_launch;
+    P.time_slice_ns = o.time_slice_us > 0 ? (unsigned long long)o.time_slice_us * 1000ull : 0ull;
     P.k0 = (uint32_t)o.seed;
     P.k1 = (uint32_t)(o.seed >> 32);
     for (int r = 0; r < 10; ++r) {
@@ -926,7 +961,7 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     P.vth = g.vth;
     P.chunk = o.chunk ? o.chunk : 256;
     P.resume = o.resume;
-    P.save_state = (o.steps_per_launch != 0 || o.resume) ? 1 : 0;
+    P.save_state = (o.steps_per_launch != 0 || o.resume || o.time_slice_us > 0) ? 1 : 0;
     P.hist_in_smem = (g.J + 2 <= kSmemHistMax) ? 1 : 0;
     P.moving = g.moving ? 1 : 0;
     for (int a = 0; a < 3; ++a) {
@@ -943,6 +978,8 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
         P.prop_sh = (pr->brick - pr->offset % pr->brick) % pr->brick;
         P.prop_nbx = (g.n[0] + P.prop_sh + pr->brick - 1) / pr->brick;
         P.prop_nby = (g.n[1] + P.prop_sh + pr->brick - 1) / pr->brick;
+        P.prop_m = pr->margin;
+        P.prop_r = pr->brick - 2 * pr->margin;
         P.prop_lk = pr->d_brick_lk;
         P.prop_lp = pr->d_lp;
         P.prop_llo = (float)pr->log_tau_lo;
@@ -971,6 +1008,8 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
     const bool use_smem_rows = o.table_in_smem && smem + rows_bytes <= (size_t)smem_optin;
     if (use_smem_rows) smem += rows_bytes;
     if ((e = cudaMemsetAsync(P.cursor, 0, 8, s)) != cudaSuccess) return e;
+    if (P.save_state && !o.resume && (e = cudaMemsetAsync(P.st_status, PK_FRESH, o.n_packets, s)) != cudaSuccess)
+        return e;
     if (g.ndim == 1)
         return use_smem_rows ? launch_mode<1, true>(P, threads, smem, o.ctas_per_sm, nsm, s)
                              : launch_mode<1, false>(P, threads, smem, o.ctas_per_sm, nsm, s);
@@ -995,7 +1034,9 @@ extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rdd
         n_out % 16)
         return RDDMC_ERR_ARG;
     if (pr->brick < 1 || pr->brick > 64 || pr->offset < 0 || pr->offset >= pr->brick) return RDDMC_ERR_ARG;
-    if (nC != 0 && nC != 6 * pr->brick * pr->brick) return RDDMC_ERR_ARG;
+    if (pr->margin < 0 || 2 * pr->margin >= pr->brick) return RDDMC_ERR_ARG;
+    const int side = pr->brick - 2 * pr->margin;
+    if (nC != 0 && nC != 6 * side * side) return RDDMC_ERR_ARG;
     if ((int64_t)pr->n_bricks != proposal_bricks(*g, *pr)) return RDDMC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     WalkLaunch w;
@@ -1017,7 +1058,7 @@ extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rdd
     __nv_bfloat16* X = (__nv_bfloat16*)((char*)d_work + mlp_bytes);
     float* logits = (float*)((char*)X + align256((uint64_t)batch * kFeat * 2));
     FeatConst fc;
-    fc.log_b = log10f((float)pr->brick);
+    fc.log_b = log10f((float)(pr->brick - 2 * pr->margin));
     fc.log_a = (float)log10(g->a);
     fc.inv_xs = (float)(1.0 / std::max(std::fabs(g->edges.front()), std::fabs(g->edges.back())));
     for (unsigned long long q0 = 0; q0 < cnt; q0 += (unsigned long long)batch) {

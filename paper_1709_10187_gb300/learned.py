@@ -167,43 +167,64 @@ class ExitProposal:
         return out
 
     # ------------------------------------------------------------------ walking with the proposal
-    def attach(self, problem, brick_rho, offset: int = 0, batch: int = 4096):
+    def attach(self, problem, brick_rho, offset: int = 0, batch: int = 4096, margin: int = 0,
+               exclude_surface: bool = False):
         """Proposal state for walking `problem`, its grid cut into bricks of
-        self.b^3 cells with boundaries at cell indices = offset (mod b) and
-        per-brick density brick_rho (partial bricks included, brick index axis
-        0 fastest).  Bricks whose density lies outside the trained levels take
-        no proposals; nor do partial bricks."""
+        (self.b + 2 margin)^3 cells with boundaries at cell indices = offset
+        (mod that size) and per-brick density brick_rho (partial bricks
+        included, brick index axis 0 fastest); each brick serves its inner cube
+        of self.b^3 cells.  Bricks whose density lies outside the trained levels
+        take no proposals; nor do partial bricks, nor (exclude_surface) bricks
+        on the lattice's outer layer.  With margin >= 1 on a brick-uniform
+        medium the served cubes see only their own medium and no surface
+        exclusion is needed."""
         torch = self.torch
+        lat = self.b + 2 * int(margin)
         rho = np.asarray(brick_rho, dtype=np.float64)
         lk = np.log10(problem.w.tau0 / problem.w.R * rho * self.dz)
         lo, hi = np.log10(min(self.levels)), np.log10(max(self.levels))
-        lk = np.where((np.log10(rho) >= lo) & (np.log10(rho) <= hi), lk, -1.0e30).astype(np.float32)
+        ok = (np.log10(rho) >= lo) & (np.log10(rho) <= hi)
+        if exclude_surface:
+            nb = [(problem.w.n[a] + (lat - offset % lat) % lat + lat - 1) // lat for a in range(3)]
+            c2, c1, c0 = np.meshgrid(np.arange(nb[2]), np.arange(nb[1]), np.arange(nb[0]), indexing="ij")
+            inner = np.ones_like(c0, dtype=bool)
+            for c, m in ((c0, nb[0]), (c1, nb[1]), (c2, nb[2])):
+                inner &= (c > 0) & (c < m - 1)
+            ok &= inner.reshape(-1)
+        lk = np.where(ok, lk, -1.0e30).astype(np.float32)
         return dict(
             lk=torch.as_tensor(lk, device=self.device),
             count=torch.zeros(1, dtype=torch.int64, device=self.device),
-            offset=int(offset),
+            offset=int(offset), lattice=lat, margin=int(margin),
             batch=batch,
             work=torch.empty(R.mlp_work_bytes(batch, self.n_out) + 256 + batch * 32 + 256 + batch * self.n_out * 4
                              + 4096, dtype=torch.uint8, device=self.device))
 
-    def run(self, problem, brick_rho, n_packets: int, seed: int, offset: int = 0, steps_per_launch: int = 16384, batch: int = 65536, tau_lo: float = 5.0, tau_hi: float = 200.0,
-            max_epochs: int = 1_000_000) -> dict:
-        """Walk n_packets on `problem` with proposals: walk launches of at most
-        steps_per_launch transitions per packet alternate with proposal rounds
-        for the packets parked meanwhile, until every packet has escaped or been
-        aborted.  Returns the tallies and the number of walk launches, proposal
-        rounds and proposals served."""
+    def proposal(self, att, qpid, tau_lo: float, tau_hi: float):
+        """The C-ABI proposal struct for an attach() state and a queue buffer."""
+        return R.Proposal(att["lattice"], att["offset"], att["lk"].data_ptr(), self.lp.data_ptr(), self.xc.data_ptr(),
+                          np.log10(tau_lo), np.log10(tau_hi), att["count"].data_ptr(), qpid.data_ptr(),
+                          int(att["lk"].numel()), att["margin"])
+
+    def run(self, problem, brick_rho, n_packets: int, seed: int, offset: int = 0, steps_per_launch: int = 0,
+            batch: int = 65536, tau_lo: float = 5.0, tau_hi: float = 200.0, max_epochs: int = 1_000_000,
+            margin: int = 0, exclude_surface: bool = False, time_slice_us: int = 1000) -> dict:
+        """Walk n_packets on `problem` with proposals: walk launches bounded by
+        time_slice_us of wall time (and steps_per_launch transitions per packet,
+        0 = no bound) alternate with proposal rounds for the packets parked
+        meanwhile, until every packet has escaped or been aborted.  The tallies
+        do not depend on the slicing.  Returns the tallies and the number of
+        walk launches, proposal rounds and proposals served."""
         torch = self.torch
         problem.ensure_state(n_packets)
-        att = self.attach(problem, brick_rho, offset, batch)
+        att = self.attach(problem, brick_rho, offset, batch, margin, exclude_surface)
         qpid = torch.empty(n_packets, dtype=torch.int64, device=self.device)
-        prop = R.Proposal(self.b, att["offset"], att["lk"].data_ptr(), self.lp.data_ptr(), self.xc.data_ptr(),
-                          np.log10(tau_lo), np.log10(tau_hi), att["count"].data_ptr(), qpid.data_ptr(),
-                          int(att["lk"].numel()), 0)
+        prop = self.proposal(att, qpid, tau_lo, tau_hi)
         problem.reset()
         launches = rounds = served = 0
         for ep in range(max_epochs):
-            problem.launch(n_packets, seed, steps_per_launch=steps_per_launch, resume=1 if ep else 0, proposal=prop)
+            problem.launch(n_packets, seed, steps_per_launch=steps_per_launch, resume=1 if ep else 0, proposal=prop,
+                           time_slice_us=time_slice_us)
             launches += 1
             k = R.propose(problem.grid, problem.table.data_ptr(), prop, seed, n_packets, problem.state.data_ptr(),
                           problem.tally.data_ptr(), self.n_out, self.nA, self.nB, self.wf.data_ptr(),

@@ -53,7 +53,7 @@ class RunOpts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("n_packets", ctypes.c_uint64), ("max_steps", ctypes.c_uint64),
                 ("steps_per_launch", ctypes.c_uint64), ("resume", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("chunk", ctypes.c_int32), ("table_in_smem", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("proposal", ctypes.c_void_p)]
+                ("time_slice_us", ctypes.c_int32), ("proposal", ctypes.c_void_p)]
 
 
 class Sizes(ctypes.Structure):
@@ -80,7 +80,7 @@ class Proposal(ctypes.Structure):
     _fields_ = [("brick", ctypes.c_int32), ("offset", ctypes.c_int32), ("d_brick_lk", ctypes.c_void_p),
                 ("d_lp", ctypes.c_void_p), ("d_xc", ctypes.c_void_p), ("log_tau_lo", ctypes.c_double),
                 ("log_tau_hi", ctypes.c_double), ("d_queue_count", ctypes.c_void_p), ("d_queue_pid", ctypes.c_void_p),
-                ("n_bricks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_bricks", ctypes.c_int32), ("margin", ctypes.c_int32)]
 
 
 class RDDMCError(RuntimeError):
@@ -268,15 +268,15 @@ class Problem:
     in caller-owned torch device buffers."""
 
     def __init__(self, w, mode=MODE_DDMC, layout=LAYOUT_DEDUP, tau_ddmc=5.0, lam=0.7104, f_mu=0.5,
-                 device="cuda", n_rel=None, edges=None):
+                 device="cuda", n_rel=None, edges=None, v_kms=None):
         import torch
         self.torch = torch
         self.w = w
         self.device = torch.device(device)
         geom = GEOM_SLAB_1D if w.ndim == 1 else GEOM_CART_3D
         self.edges = np.asarray(w.edges() if edges is None else edges, dtype=np.float64)
-        self.grid = build_grid(geom, w.n, self.edges, w.R, w.tau0, w.T, n_rel=n_rel, v_kms=w.velocity_kms(),
-                               mask=w.mask(), layout=layout)
+        self.grid = build_grid(geom, w.n, self.edges, w.R, w.tau0, w.T, n_rel=n_rel,
+                               v_kms=w.velocity_kms() if v_kms is None else v_kms, mask=w.mask(), layout=layout)
         self.J = len(self.edges) - 1
         self.nfaces = 2 * w.ndim
         self.K = 2 + 2 * w.ndim
@@ -301,12 +301,18 @@ class Problem:
     def reset(self):
         reset_tallies(self.grid, self.tally.data_ptr(), self.tally.numel() * 8, self.stream())
 
+    @classmethod
+    def clumpy(cls, med, **kw):
+        """A Problem on a clumpy medium (workloads.ClumpyMedium): its density and
+        turbulent velocity per cell."""
+        return cls(med.workload, n_rel=med.n_rel, v_kms=med.v_kms, **kw)
+
     def launch(self, n_packets: int, seed: int, max_steps: int = 0, steps_per_launch: int = 0, resume: int = 0,
                ctas_per_sm: int = 0, threads_per_cta: int = 0, chunk: int = 0, table_in_smem: int = 0,
-               proposal: "Proposal" = None):
+               proposal: "Proposal" = None, time_slice_us: int = 0):
         st = self.ensure_state(n_packets)
         o = RunOpts(seed, n_packets, max_steps, steps_per_launch, resume, ctas_per_sm, threads_per_cta, chunk,
-                    table_in_smem, 0, ctypes.addressof(proposal) if proposal is not None else None)
+                    table_in_smem, time_slice_us, ctypes.addressof(proposal) if proposal is not None else None)
         launch_packets(self.grid, self.table.data_ptr(), o, st.data_ptr(), st.numel(), self.tally.data_ptr(),
                        self.tally.numel() * 8, self.stream())
 
