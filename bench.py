@@ -280,10 +280,165 @@ def run_native(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h},
         "peaks_source": peak_kind,
     }
+    if world == 1 and not args.no_extras:
+        with torch.cuda.stream(stream):
+            line["extras"] = _extras(R, torch)
     if world == 1 and not args.no_cpu_baseline:
         cb, _ = _cpu_sample()
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- extras
+# Measured after the timed region, on one GPU: the other workloads of the
+# method and the learned proposal against the plain walk.  Each is timed with
+# CUDA events or a device synchronisation on both sides.
+
+def _sliced_rate(R, torch, prob, npk, seed, slice_, launches=5, warm=2):
+    """Transitions/s (and MC events/s) of time-sliced launches over npk packets."""
+    s = prob.stream()
+    prob.ensure_state(npk)
+    prob.reset()
+    for i in range(warm):
+        prob.launch(npk, seed, steps_per_launch=slice_, resume=1 if i else 0)
+    b = prob.read()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(torch.cuda.current_stream())
+    for i in range(launches):
+        prob.launch(npk, seed, steps_per_launch=slice_, resume=1)
+    a1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    dt = a0.elapsed_time(a1) / 1e3
+    e = prob.read()
+    return {"transitions_per_s": (e["steps"] - b["steps"]) / dt,
+            "mc_events_per_s": (e["mc_events"] - b["mc_events"]) / dt,
+            "escaped_per_s": (e["escaped"] - b["escaped"]) / dt, "packets": npk, "slice": slice_,
+            "launches": launches}
+
+
+def _batched(R, torch, packet_scale=0.01, max_steps=1_000_000):
+    """The batched workload: 512 slab/sphere instances in one persistent launch,
+    schedule picked by the autotuner, replayed from a captured CUDA graph."""
+    ws = W.batched_instances(512, packet_scale=packet_scale)
+    npk = [w.packets for w in ws]
+    t0 = time.perf_counter()
+    probs = [R.Problem(w) for w in ws]
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    b = R.Batch(probs, npk, trial_fraction=0.02)
+    base = R.RunOpts(0xBA7C4, 0, max_steps, 0, 0, 0, 0, 0, 0, 0)
+    best, trial_rate = b.autotune(base)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ge = b.graph(best)
+        try:
+            b.graph_launch(ge)  # warm-up replay
+            b.tally.zero_()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a0.record(side)
+            b.graph_launch(ge)
+            a1.record(side)
+            torch.cuda.synchronize()
+            dt = a0.elapsed_time(a1) / 1e3
+            tot = {"steps": 0, "escaped": 0, "aborted": 0, "emitted": 0}
+            for i in range(len(ws)):
+                t = b.read(i)
+                for k in tot:
+                    tot[k] += t[k]
+        finally:
+            R.Batch.graph_destroy(ge)
+    torch.cuda.current_stream().wait_stream(side)
+    return {"instances": len(ws), "packets": int(sum(npk)), "max_steps": max_steps,
+            "transitions_per_s": tot["steps"] / dt, "escaped_per_s": tot["escaped"] / dt,
+            "escaped": tot["escaped"], "aborted": tot["aborted"], "ms": dt * 1e3,
+            "schedule": {"threads_per_cta": best.threads_per_cta, "ctas_per_sm": best.ctas_per_sm,
+                         "chunk": best.chunk},
+            "autotune_trial_transitions_per_s": trial_rate, "setup_s": t_setup}
+
+
+def _l1(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a / a.sum() - b / b.sum()).sum())
+
+
+def _learned_vs_plain(R, torch, n=64, brick=16, margin=1, J=64, x_max=64.0, tau0=1.0e7, npk=400_000,
+                      ndata=1_500_000, iters=4000):
+    """Escape spectrum of the clumpy 3D medium by the plain walk and by the walk
+    with the learned exit proposal (trained here on first passages the plain
+    walk generates), each compared with an independent plain reference of 4x
+    the packets; then plain at the packet count that gives the learned run's
+    L1, so both are timed at equal escape-spectrum error."""
+    from paper_1709_10187_gb300 import learned as Lr
+    med = W.clumpy_medium(n=n, J=J, x_max=x_max, tau0=tau0, brick=brick, packets=npk)
+    prob = R.Problem.clumpy(med)
+    rho = med.brick_rho
+    levels = np.logspace(np.log10(rho.min()) - 0.05, np.log10(rho.max()) + 0.05, 24)
+    t0 = time.perf_counter()
+    prop = Lr.ExitProposal(med.workload, brick - 2 * margin, levels, tau_lo=5.0, tau_hi=1.0e12)
+    data = prop.generate(ndata, seed=11, cap=50_000_000)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    prop.train(data, iters=iters, batch=8192, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del data
+    seed = 0xC0FFEE
+    kw = dict(margin=margin, tau_lo=5.0, tau_hi=1.0e12)
+    prop.run(prob, rho, 2000, seed + 7, **kw)  # warm-up
+    prob.run(2000, seed + 7)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, out
+
+    t_l, lr = timed(lambda: prop.run(prob, rho, npk, seed, **kw))
+    t_p, pl = timed(lambda: prob.run(npk, seed))
+    ref = prob.run(4 * npk, seed + 1)
+    l1_l, l1_p = _l1(lr["hist"], ref["hist"]), _l1(pl["hist"], ref["hist"])
+    # plain at the learned run's L1 (L1 ~ N^-1/2 while noise dominates)
+    n_eq = int(min(4 * npk, max(npk // 16, npk * (l1_p / max(l1_l, 1e-12)) ** 2)))
+    t_e, pe = timed(lambda: prob.run(n_eq, seed + 2))
+    return {"workload": f"clumpy_{n}c_{J}b_brick{brick}_tau{tau0:.0e}", "packets": npk,
+            "proposal_region": brick - 2 * margin, "levels": len(prop.levels),
+            "train_samples": ndata, "train_iters": iters, "data_s": t_data, "train_s": t_train,
+            "learned": {"s": t_l, "l1": l1_l, "transitions_per_packet": lr["steps"] / npk,
+                        "proposals_per_packet": lr["proposals"] / npk, "launches": lr["launches"]},
+            "plain": {"s": t_p, "l1": l1_p, "transitions_per_packet": pl["steps"] / npk},
+            "plain_at_equal_l1": {"packets": n_eq, "s": t_e, "l1": _l1(pe["hist"], ref["hist"])},
+            "speedup_at_equal_l1": t_e / t_l, "reference_packets": 4 * npk}
+
+
+def _extras(R, torch, only=None):
+    out = {}
+    jobs = [("c3_sphere_static", lambda: _sliced_rate(R, torch, R.Problem(W.C3), 1_000_000, W.C3.seed, 4096)),
+            ("c3_sphere_v20", lambda: _sliced_rate(R, torch, R.Problem(W.C3_V20), 1_000_000, W.C3.seed, 4096)),
+            ("c3_sphere_v200", lambda: _sliced_rate(R, torch, R.Problem(W.C3_V200), 1_000_000, W.C3.seed, 4096)),
+            ("c2_hybrid", lambda: _sliced_rate(R, torch, R.Problem(W.C2, mode=R.MODE_HYBRID), 1_000_000,
+                                               W.C2.seed, 4096)),
+            ("batched_512", lambda: _batched(R, torch)),
+            ("learned_vs_plain", lambda: _learned_vs_plain(R, torch))]
+    if only:
+        small = {"learned_small": lambda: _learned_vs_plain(R, torch, n=32, brick=8, tau0=1.0e6, npk=100_000,
+                                                            ndata=300_000, iters=300)}
+        jobs = [(k, f) for k, f in jobs + list(small.items()) if k == only]
+        if not jobs:
+            raise SystemExit(f"unknown extra {only!r}")
+    for name, fn in jobs:
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as exc:  # reported, not hidden: the main line still prints
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def _kernel_hash():
@@ -307,12 +462,24 @@ def main():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--table-in-smem", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads and the learned-vs-plain comparison")
+    ap.add_argument("--extra", default="", help="run only this extra (c3_sphere_static, c3_sphere_v20, "
+                    "c3_sphere_v200, c2_hybrid, batched_512, learned_vs_plain, learned_small) and print it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.extra:
+        # one extra workload alone (for profiling); no timed region, no bench line
+        import torch
+        from paper_1709_10187_gb300 import build as B
+        from paper_1709_10187_gb300 import rddmc as R
+        B.build()
+        print(json.dumps({"extra": args.extra, **_extras(R, torch, only=args.extra)}), flush=True)
         return
     if world > 1:
         import torch
