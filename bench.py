@@ -257,8 +257,9 @@ def run_native(args, rank, world, local_rank):
     alu_peak = N_SM * 128 * PEAK_SM_MHZ * 1e6 / 1e12
     prof = _profile_traffic()
     traffic = None
-    if prof and prof.get("kernel_hash") == _kernel_hash():
-        traffic = prof["dram_bytes_per_transition"] * trans_per_launch
+    if (prof and prof.get("kernel_hash") == _kernel_hash() and prof.get("packets") == npk
+            and prof.get("slice_transitions") == slice_):
+        traffic = prof["dram_bytes_per_launch"]  # one ncu capture of this launch configuration
     gather_gbs = ROW_BYTES * trans_per_launch / mean_launch_s / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -221,7 +221,7 @@ MlpOffsets mlp_offsets(int n_out) {
     return o;
 }
 
-enum Epi { EPI_RELU_BF16 = 0, EPI_LINEAR_F32 = 1, EPI_MASK_BF16 = 2, EPI_F32 = 3 };
+enum Epi { EPI_RELU_BF16 = 0, EPI_LINEAR_F32 = 1, EPI_MASK_BF16 = 2, EPI_F32 = 3, EPI_F32_ADD = 4 };
 
 // C[M x N] = A[M x K] B[K x N]; A row- or column-major (lda), B row- or
 // column-major (ldb); M, N, K multiples of 16.  Block = 4 warps on a 64 x 64
@@ -244,7 +244,10 @@ __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const __
 #pragma unroll
         for (int j = 0; j < 2; ++j) wmma::fill_fragment(c[i][j], 0.0f);
     const bool rv[2] = {m0 < M, m0 + 16 < M}, cv[2] = {n0 < N, n0 + 16 < N};
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    // split-K: blockIdx.z takes a contiguous range of K (multiples of 16)
+    const int kc = ((K + (int)gridDim.z * 16 - 1) / ((int)gridDim.z * 16)) * 16;
+    const int kb = (int)blockIdx.z * kc, ke = min(K, kb + kc);
+    for (int k0 = kb; k0 < ke; k0 += 16) {
         wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, LA> a[2];
         wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, LB> b[2];
 #pragma unroll
@@ -285,6 +288,8 @@ __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const __
             v = __bfloat162float(mask[(size_t)m * ldmask + n]) > 0.0f ? v : 0.0f;
             outb[(size_t)m * ldc + n] = __float2bfloat16(v);
             outf[(size_t)m * ldc + n] = v;
+        } else if (EPI == EPI_F32_ADD) {
+            atomicAdd(&outf[(size_t)m * ldc + n], v);  // partial sum of a K split
         } else {
             outf[(size_t)m * ldc + n] = v;
         }
@@ -294,8 +299,8 @@ __global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const __
 template <bool A_ROW, bool B_ROW, int EPI>
 cudaError_t gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
                  const float* bias, const __nv_bfloat16* mask, int ldmask, __nv_bfloat16* outb, float* outf, int ldc,
-                 cudaStream_t s) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
+                 cudaStream_t s, int ksplit = 1) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64, ksplit);
     gemm_kernel<A_ROW, B_ROW, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldmask, outb, outf, ldc);
     return cudaGetLastError();
 }
@@ -347,13 +352,38 @@ __global__ void softmax_ce_kernel(const float* __restrict__ logits, int n_out, i
     if (lane == 0) atomicAdd(loss, total);
 }
 
-// db[n] = sum_b dY[b, n]
-__global__ void colsum_kernel(const float* __restrict__ dy, int Bsz, int N, float* __restrict__ db) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    float s = 0.0f;
-    for (int b = 0; b < Bsz; ++b) s += dy[(size_t)b * N + n];
-    db[n] = s;
+// db[n] += sum over the block's rows of dY[b, n]: blocks of 32 columns x 8 row
+// lanes, each block a contiguous range of rows; db must start at zero.
+__global__ void colsum_kernel(const float* __restrict__ dy, int Bsz, int N, int rows_per_block,
+                              float* __restrict__ db) {
+    __shared__ float part[8][33];
+    const int n = blockIdx.x * 32 + threadIdx.x;
+    const int r0 = blockIdx.y * rows_per_block, r1 = min(Bsz, r0 + rows_per_block);
+    float acc = 0.0f;
+    if (n < N)
+        for (int r = r0 + (int)threadIdx.y; r < r1; r += 8) acc += dy[(size_t)r * N + n];
+    part[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < N) {
+        float t = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += part[i][threadIdx.x];
+        atomicAdd(&db[n], t);
+    }
+}
+
+cudaError_t colsum(const float* dy, int Bsz, int N, float* db, cudaStream_t s) {
+    const int rpb = 256;
+    dim3 grid((N + 31) / 32, (Bsz + rpb - 1) / rpb);
+    colsum_kernel<<<grid, dim3(32, 8), 0, s>>>(dy, Bsz, N, rpb, db);
+    return cudaGetLastError();
+}
+
+// K splits for a weight-gradient product (K = batch rows): about two waves of
+// CTAs over the GPU, each split at least 128 rows long.
+int ksplit_for(int M, int N, int K) {
+    const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
+    return std::max(1, std::min(K / 128, (304 + tiles - 1) / tiles));
 }
 
 __global__ void adam_kernel(uint64_t n, float* __restrict__ w, __nv_bfloat16* __restrict__ wb,
@@ -465,25 +495,27 @@ int rddmc_mlp_loss_grad(int n_out, int nA, int nB, int nC, int S, const float* d
     if (cudaMemsetAsync(d_loss, 0, 4, s) != cudaSuccess) return RDDMC_ERR_CUDA;
     softmax_ce_kernel<<<(batch + 7) / 8, 256, 0, s>>>(w.logits, n_out, nA, nB, nC, S, d_ta, d_tb,
                                                        nC > 0 ? d_tc : nullptr, batch, w.dlogf, w.dlogb, d_loss);
+    // gradients accumulate (split-K products, column sums) into a zeroed buffer
+    if (cudaMemsetAsync(d_grad, 0, o.total * sizeof(float), s) != cudaSuccess) return RDDMC_ERR_CUDA;
     // output layer: dW4 = dlog^T H3, db4 = colsum(dlog), dH3 = (dlog W4) * [H3 > 0]
-    gemm<false, true, EPI_F32>(n_out, kHid, batch, w.dlogb, n_out, w.H[2], kHid, nullptr, nullptr, 0, nullptr,
-                               d_grad + o.W[3], kHid, s);
-    colsum_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(w.dlogf, batch, n_out, d_grad + o.b[3]);
+    gemm<false, true, EPI_F32_ADD>(n_out, kHid, batch, w.dlogb, n_out, w.H[2], kHid, nullptr, nullptr, 0, nullptr,
+                                   d_grad + o.W[3], kHid, s, ksplit_for(n_out, kHid, batch));
+    colsum(w.dlogf, batch, n_out, d_grad + o.b[3], s);
     gemm<true, true, EPI_MASK_BF16>(batch, kHid, n_out, w.dlogb, n_out, wb + o.W[3], kHid, nullptr, w.H[2], kHid,
                                     w.dHb[0], w.dHf, kHid, s);
     int cur = 0;
     for (int l = 2; l >= 1; --l) {
         // layer l (W[l]: H[l-1] -> H[l]); dHb[cur] holds dL/d(pre-activation of H[l])
-        gemm<false, true, EPI_F32>(kHid, kHid, batch, w.dHb[cur], kHid, w.H[l - 1], kHid, nullptr, nullptr, 0,
-                                   nullptr, d_grad + o.W[l], kHid, s);
-        colsum_kernel<<<1, 128, 0, s>>>(w.dHf, batch, kHid, d_grad + o.b[l]);
+        gemm<false, true, EPI_F32_ADD>(kHid, kHid, batch, w.dHb[cur], kHid, w.H[l - 1], kHid, nullptr, nullptr, 0,
+                                       nullptr, d_grad + o.W[l], kHid, s, ksplit_for(kHid, kHid, batch));
+        colsum(w.dHf, batch, kHid, d_grad + o.b[l], s);
         gemm<true, true, EPI_MASK_BF16>(batch, kHid, kHid, w.dHb[cur], kHid, wb + o.W[l], kHid, nullptr, w.H[l - 1],
                                         kHid, w.dHb[cur ^ 1], w.dHf, kHid, s);
         cur ^= 1;
     }
-    gemm<false, true, EPI_F32>(kHid, kIn, batch, w.dHb[cur], kHid, X, kIn, nullptr, nullptr, 0, nullptr,
-                               d_grad + o.W[0], kIn, s);
-    colsum_kernel<<<1, 128, 0, s>>>(w.dHf, batch, kHid, d_grad + o.b[0]);
+    gemm<false, true, EPI_F32_ADD>(kHid, kIn, batch, w.dHb[cur], kHid, X, kIn, nullptr, nullptr, 0, nullptr,
+                                   d_grad + o.W[0], kIn, s, ksplit_for(kHid, kIn, batch));
+    colsum(w.dHf, batch, kHid, d_grad + o.b[0], s);
     return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
 }
 
