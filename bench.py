@@ -10,8 +10,8 @@ tallies escapes and saves its state.  A full run to escape needs ~3e8
 transitions per packet (3e15 in total), so the job is timed slice by slice.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-For N > 1 launch with torchrun; each rank walks its own disjoint range of packet
-ids (weak scaling, no data-path collective).  `--impl reference` times the FP64
+For N > 1 launch with torchrun; each rank walks its own packets under its own
+Philox key (seed offset by rank: weak scaling, no data-path collective).  `--impl reference` times the FP64
 CPU oracle on a bounded sample of the same workload on the host cores.
 """
 import argparse
@@ -160,6 +160,26 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def rank_seed(seed: int, rank: int, packets_per_rank: int) -> int:
+    """Philox key of a rank's packets: every rank walks its own packets under
+    its own key (weak scaling; no data-path exchange)."""
+    return seed + rank * packets_per_rank
+
+
+def combine_ranks(dist, device, tsec, trans, escaped, e2e_dt, e2e_trans):
+    """Whole-job figures from per-rank ones: the slowest rank's times, the sum of
+    the work (transitions, escapes) over all ranks."""
+    if not dist:
+        return tsec, float(trans), float(escaped), e2e_dt, float(e2e_trans)
+    import torch
+    t = torch.tensor([tsec, float(trans), float(escaped), e2e_dt, float(e2e_trans)], device=device,
+                     dtype=torch.float64)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1]), float(t[2]), float(tmax[3]), float(t[4])
+
+
 def run_native(args, rank, world, local_rank):
     import torch
     from paper_1709_10187_gb300 import build as B
@@ -174,7 +194,7 @@ def run_native(args, rank, world, local_rank):
     w = W.C2
     npk = w.packets
     seed = w.seed
-    p0_rank = rank * npk  # disjoint packet ids per rank (weak scaling)
+    key = rank_seed(seed, rank, npk)
     slice_ = args.slice
     stream = torch.cuda.Stream(dev)
     sched = dict(ctas_per_sm=args.ctas_per_sm, threads_per_cta=args.threads, chunk=args.chunk,
@@ -187,7 +207,7 @@ def run_native(args, rank, world, local_rank):
         s = stream.cuda_stream
 
         def launch(resume):
-            o = R.RunOpts(seed + p0_rank, npk, 0, slice_, resume, sched["ctas_per_sm"], sched["threads_per_cta"],
+            o = R.RunOpts(key, npk, 0, slice_, resume, sched["ctas_per_sm"], sched["threads_per_cta"],
                           sched["chunk"], sched["table_in_smem"], 0)
             R.launch_packets(prob.grid, prob.table.data_ptr(), o, prob.state.data_ptr(), prob.state.numel(),
                              prob.tally.data_ptr(), prob.tally.numel() * 8, s)
@@ -236,17 +256,8 @@ def run_native(args, rank, world, local_rank):
         d2h = (22 + prob.J + 2) * 8
 
     tsec = elapsed_ms / 1e3
-    if dist:
-        t = torch.tensor([tsec, float(trans), float(escaped), e2e_dt, float(e2e_trans)], device=dev,
-                         dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        tsec_max, trans_tot, esc_tot, e2e_dt_max, e2e_tot = (float(tmax[0]), float(t[1]), float(t[2]),
-                                                             float(tmax[3]), float(t[4]))
-    else:
-        tsec_max, trans_tot, esc_tot, e2e_dt_max, e2e_tot = tsec, float(trans), float(escaped), e2e_dt, \
-            float(e2e_trans)
+    tsec_max, trans_tot, esc_tot, e2e_dt_max, e2e_tot = combine_ranks(
+        dist, dev, tsec, trans, escaped, e2e_dt, e2e_trans)
     if rank != 0:
         return
     value = trans_tot / tsec_max
