@@ -41,6 +41,7 @@ extern "C" {
 #define RDDMC_ERR_CUDA -4         /* a CUDA runtime call or kernel launch failed */
 #define RDDMC_ERR_STEP_LIMIT -5   /* device status: packets aborted by the step watchdog */
 #define RDDMC_ERR_TABLE -6        /* the table buffer was not filled for this grid */
+#define RDDMC_ERR_TIMEOUT -7      /* device status: a bounded wait of a tensor-core product ran out */
 
 /* ------------------------------------------------------------- enumerations */
 #define RDDMC_GEOM_SLAB_1D 1      /* slab |z| <= R, one spatial axis */
@@ -474,7 +475,9 @@ int rddmc_propose(const rddmc_grid* grid, const void* d_table, const rddmc_propo
  * master copy and BF16 copy, same layout, rddmc_mlp_param_count(n_out)
  * elements: W1[128x16] b1 W2[128x128] b2 W3[128x128] b3 W4[n_out x 128] b4
  * (row-major W[out][in]).  Matrix products run on tensor cores with BF16
- * inputs and FP32 accumulation; batch sizes are multiples of 64. */
+ * inputs and FP32 accumulation -- the forward products as tcgen05.mma with
+ * tensor-memory accumulators, the backward products as warp-level MMA;
+ * batch sizes are multiples of 64. */
 uint64_t rddmc_mlp_param_count(int n_out);
 uint64_t rddmc_mlp_work_bytes(int batch, int n_out);
 int rddmc_mlp_to_bf16(int n_out, const float* d_wf, void* d_wb, void* stream);
@@ -489,6 +492,10 @@ int rddmc_mlp_forward(int n_out, const float* d_wf, const void* d_wb, const void
 int rddmc_mlp_loss_grad(int n_out, int nA, int nB, int nC, int S, const float* d_wf, const void* d_wb,
                         const void* d_x, const int32_t* d_ta, const int32_t* d_tb, const int32_t* d_tc, int batch,
                         void* d_work, float* d_grad, float* d_loss, void* stream);
+/* Synchronise `stream`, then report and clear the network's device status:
+ * RDDMC_OK, or RDDMC_ERR_TIMEOUT when a tensor-core product's bounded wait ran
+ * out since the last call (its output tile was left unwritten). */
+int rddmc_mlp_status(void* stream);
 /* One Adam step (bias-corrected, step >= 1) on the master weights; refreshes
  * the BF16 copy. */
 int rddmc_mlp_adam(int n_out, float* d_wf, void* d_wb, const float* d_grad, float* d_m, float* d_v, int step, float lr,

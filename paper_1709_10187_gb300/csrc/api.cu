@@ -65,6 +65,7 @@ const char* rddmc_status_string(int s) {
         case RDDMC_ERR_CUDA: return "CUDA error";
         case RDDMC_ERR_STEP_LIMIT: return "packets aborted by the step watchdog";
         case RDDMC_ERR_TABLE: return "table not precomputed for this grid";
+        case RDDMC_ERR_TIMEOUT: return "a bounded device wait ran out";
         default: return "unknown status";
     }
 }

@@ -18,6 +18,7 @@
 
 #include "grid.h"
 #include "learned_common.cuh"
+#include "umma.cuh"
 
 namespace rddmc {
 namespace {
@@ -432,19 +433,51 @@ MlpWork mlp_work(void* d_work, int Bsz, int n_out) {
     return w;
 }
 
+// Device status of the tensor-core products (set when a bounded wait runs out).
+__device__ unsigned g_tc_err = 0;
+
+unsigned* tc_err_ptr() {
+    static unsigned* p = nullptr;
+    if (!p) {
+        void* a = nullptr;
+        if (cudaGetSymbolAddress(&a, g_tc_err) != cudaSuccess) return nullptr;
+        p = (unsigned*)a;
+    }
+    return p;
+}
+
+// C = epi(A W^T + bias) on tcgen05 (umma.cuh): A [M x K], W [N x K], K <= 128.
+template <int EPI>
+cudaError_t gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* W, int ldw,
+                    const float* bias, __nv_bfloat16* outb, float* outf, int ldc, cudaStream_t s) {
+    unsigned* err = tc_err_ptr();
+    if (!err || K % 16 || K > 128 || N % 16) return cudaErrorInvalidValue;
+    const int NT = std::min(256, N);
+    // at least 80 KiB of shared memory: at most two CTAs per SM, so their TMEM
+    // accumulators (<= 256 columns each) always fit the SM's 512 columns
+    const size_t smem = std::max<size_t>(umma::smem_bytes(NT, K), 80 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(umma::gemm_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + NT - 1) / NT, (M + umma::kTileM - 1) / umma::kTileM);
+    umma::gemm_tc_kernel<EPI><<<grid, umma::kThreads, smem, s>>>(M, N, K, NT, A, lda, W, ldw, bias, outb, outf, ldc,
+                                                                  err);
+    return cudaGetLastError();
+}
+
 cudaError_t mlp_forward(int n_out, const float* wf, const __nv_bfloat16* wb, const __nv_bfloat16* X, int Bsz,
                         const MlpWork& w, cudaStream_t s) {
     const MlpOffsets o = mlp_offsets(n_out);
     cudaError_t e;
-    if ((e = gemm<true, false, EPI_RELU_BF16>(Bsz, kHid, kIn, X, kIn, wb + o.W[0], kIn, wf + o.b[0], nullptr, 0,
-                                              w.H[0], nullptr, kHid, s)) != cudaSuccess)
+    if ((e = gemm_tc<umma::RELU_BF16>(Bsz, kHid, kIn, X, kIn, wb + o.W[0], kIn, wf + o.b[0], w.H[0], nullptr, kHid,
+                                      s)) != cudaSuccess)
         return e;
     for (int l = 1; l < 3; ++l)
-        if ((e = gemm<true, false, EPI_RELU_BF16>(Bsz, kHid, kHid, w.H[l - 1], kHid, wb + o.W[l], kHid, wf + o.b[l],
-                                                  nullptr, 0, w.H[l], nullptr, kHid, s)) != cudaSuccess)
+        if ((e = gemm_tc<umma::RELU_BF16>(Bsz, kHid, kHid, w.H[l - 1], kHid, wb + o.W[l], kHid, wf + o.b[l], w.H[l],
+                                          nullptr, kHid, s)) != cudaSuccess)
             return e;
-    return gemm<true, false, EPI_LINEAR_F32>(Bsz, n_out, kHid, w.H[2], kHid, wb + o.W[3], kHid, wf + o.b[3], nullptr,
-                                             0, nullptr, w.logits, n_out, s);
+    return gemm_tc<umma::LINEAR_F32>(Bsz, n_out, kHid, w.H[2], kHid, wb + o.W[3], kHid, wf + o.b[3], nullptr,
+                                     w.logits, n_out, s);
 }
 
 }  // namespace
@@ -517,6 +550,17 @@ int rddmc_mlp_loss_grad(int n_out, int nA, int nB, int nC, int S, const float* d
                                    d_grad + o.W[0], kIn, s, ksplit_for(kHid, kIn, batch));
     colsum(w.dHf, batch, kHid, d_grad + o.b[0], s);
     return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+}
+
+int rddmc_mlp_status(void* stream) {
+    unsigned* p = tc_err_ptr();
+    if (!p) return RDDMC_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned v = 0;
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaMemcpy(&v, p, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return RDDMC_ERR_CUDA;
+    if (v && cudaMemset(p, 0, 4) != cudaSuccess) return RDDMC_ERR_CUDA;
+    return v ? RDDMC_ERR_TIMEOUT : RDDMC_OK;
 }
 
 int rddmc_mlp_adam(int n_out, float* d_wf, void* d_wb, const float* d_grad, float* d_m, float* d_v, int step, float lr,

@@ -1,0 +1,180 @@
+// umma.cuh -- dense BF16 products on the 5th-generation tensor cores
+// (tcgen05.mma, FP32 accumulators in tensor memory) for the learned proposal's
+// network: C[M x N] = A[M x K] W[N x K]^T (+ bias, epilogue), both operands
+// row-major with K contiguous ("K-major"), K a multiple of 16 and at most 128.
+//
+// One CTA of 128 threads computes a 128 x NT tile (NT <= 256, a multiple of
+// 16): the threads stage A and W in shared memory in the 128-byte swizzled
+// K-major layout (rows of 64 BF16 = 128 B, eight-row atoms of 1 KiB, 16-byte
+// chunk c of row r stored at chunk c ^ (r mod 8)), one elected thread issues
+// K/16 tcgen05.mma instructions into a TMEM accumulator of 128 lanes x NT
+// columns and commits them to an mbarrier; every warp then reads its 32 lanes
+// back with tcgen05.ld for the epilogue.  Waits are bounded: a wait that runs
+// out sets the error word and the tile's outputs are left unwritten.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rddmc {
+namespace umma {
+
+constexpr int kTileM = 128;
+constexpr int kThreads = 128;
+constexpr int kPanel = 64;  // BF16 per 128-byte swizzled row
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading byte offset (unused
+// by swizzled K-major layouts, set to 16 B), stride byte offset between
+// eight-row atoms (1 KiB), descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__host__ __device__ constexpr int tmem_cols(int nt) {
+    return nt <= 32 ? 32 : (nt <= 64 ? 64 : (nt <= 128 ? 128 : 256));
+}
+
+// Copy rows [row0, row0 + rows) x K of a row-major BF16 matrix into the
+// swizzled K-major layout at dst (1 KiB aligned; rows a multiple of 8); rows
+// past `valid` are zero.
+__device__ __forceinline__ void stage(const __nv_bfloat16* __restrict__ src, int ld, int row0, int rows, int valid,
+                                      int K, unsigned char* dst) {
+    const int chunks_per_row = K / 8;  // 16-byte chunks of K
+    const int total = rows * chunks_per_row;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int r = i / chunks_per_row, q = i % chunks_per_row;
+        const int p = q >> 3, c = q & 7;  // panel, chunk in the 128-byte row
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r < valid) v = *reinterpret_cast<const uint4*>(src + (size_t)(row0 + r) * ld + q * 8);
+        unsigned char* d = dst + (size_t)p * rows * 128 + (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
+                           ((c ^ (r & 7)) << 4);
+        *reinterpret_cast<uint4*>(d) = v;
+    }
+}
+
+enum Epi { RELU_BF16 = 0, LINEAR_F32 = 1 };
+
+// C = epi(A W^T + bias).  Grid: (ceil(N / NT), ceil(M / 128)); dynamic shared
+// memory smem_bytes(NT, K).  err: set to 1 when a wait ran out.
+template <int EPI>
+__global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, int NT,
+                                                           const __nv_bfloat16* __restrict__ A, int lda,
+                                                           const __nv_bfloat16* __restrict__ W, int ldw,
+                                                           const float* __restrict__ bias,
+                                                           __nv_bfloat16* __restrict__ outb, float* __restrict__ outf,
+                                                           int ldc, unsigned* err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int panels = (K + kPanel - 1) / kPanel;
+    unsigned char* sA = base;
+    unsigned char* sB = sA + (size_t)panels * kTileM * 128;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + (size_t)panels * NT * 128);
+    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(mbar + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kTileM, n0 = blockIdx.x * NT;
+    const int ncols = tmem_cols(NT);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(taddr_s)), "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    stage(A, lda, m0, kTileM, min(kTileM, M - m0), K, sA);
+    stage(W, ldw, n0, NT, min(NT, N - n0), K, sB);
+    asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor-core reads
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *taddr_s;
+
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = instr_desc(kTileM, NT);
+        for (int s = 0; s < K / 16; ++s) {
+            const int p = s >> 2, off = (s & 3) * 32;  // panel, byte offset of the 16-wide K slice
+            const uint64_t ad = smem_desc(smem_u32(sA + (size_t)p * kTileM * 128 + off));
+            const uint64_t bd = smem_desc(smem_u32(sB + (size_t)p * NT * 128 + off));
+            const uint32_t acc = s > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_u32(mbar)));
+    }
+    // bounded wait for the products (phase 0)
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(smem_u32(mbar)));
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!done) {
+        if (threadIdx.x == 0) atomicOr(err, 1u);
+    } else {
+        // warp w reads TMEM lanes 32w..32w+31: thread t holds row m0 + 32w + t
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < NT; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (c0 + j >= NT || n >= N) continue;
+                    const float x = __uint_as_float(v[j]) + bias[n];
+                    if (EPI == RELU_BF16) outb[(size_t)row * ldc + n] = __float2bfloat16(fmaxf(x, 0.0f));
+                    else outf[(size_t)row * ldc + n] = x;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(ncols));
+    }
+}
+
+// Dynamic shared memory of a 128 x NT tile with K-long rows (+1 KiB alignment
+// slack, mbarrier and TMEM address).
+__host__ __device__ constexpr size_t smem_bytes(int nt, int k) {
+    return 1024 + (size_t)((k + kPanel - 1) / kPanel) * (kTileM + nt) * 128 + 64;
+}
+
+}  // namespace umma
+}  // namespace rddmc

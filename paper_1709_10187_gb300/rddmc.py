@@ -21,7 +21,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librddmc.so")
 
-OK, ERR_ARG, ERR_UNSUPPORTED, ERR_SIZE, ERR_CUDA, ERR_STEP_LIMIT, ERR_TABLE = 0, -1, -2, -3, -4, -5, -6
+OK, ERR_ARG, ERR_UNSUPPORTED, ERR_SIZE, ERR_CUDA, ERR_STEP_LIMIT, ERR_TABLE, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 GEOM_SLAB_1D, GEOM_CART_3D = 1, 3
 MODE_DDMC, MODE_HYBRID = 0, 1
 LAYOUT_DEDUP, LAYOUT_DENSE = 0, 1
@@ -34,7 +34,7 @@ EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc
             "rddmc_batch_launch", "rddmc_batch_read_tallies", "rddmc_batch_graph_create", "rddmc_batch_graph_launch",
             "rddmc_batch_graph_destroy", "rddmc_batch_autotune", "rddmc_cell_tau", "rddmc_fp_generate",
             "rddmc_mlp_param_count", "rddmc_mlp_work_bytes", "rddmc_mlp_to_bf16", "rddmc_mlp_forward",
-            "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_propose", "rddmc_status_string", "rddmc_version"]
+            "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_mlp_status", "rddmc_propose", "rddmc_status_string", "rddmc_version"]
 
 
 class GridDesc(ctypes.Structure):
@@ -119,6 +119,7 @@ def lib():
         L.rddmc_propose.argtypes = [vp, vp, ctypes.POINTER(Proposal), u64, u64, vp, vp, i32, i32, i32, i32, vp, vp, i32,
                                     vp, ctypes.POINTER(ctypes.c_uint64), vp]
         L.rddmc_mlp_param_count.argtypes = [i32]
+        L.rddmc_mlp_status.argtypes = [vp]
         L.rddmc_mlp_work_bytes.argtypes = [i32, i32]
         L.rddmc_mlp_to_bf16.argtypes = [i32, vp, vp, vp]
         L.rddmc_mlp_forward.argtypes = [i32, vp, vp, vp, i32, vp, vp, vp]
@@ -479,6 +480,11 @@ def mlp_loss_grad(n_out, nA, nB, d_wf, d_wb, d_x, d_ta, d_tb, batch, d_work, d_g
         int(n_out), int(nA), int(nB), int(nC), int(S), ctypes.c_void_p(d_wf), ctypes.c_void_p(d_wb),
         ctypes.c_void_p(d_x), ctypes.c_void_p(d_ta), ctypes.c_void_p(d_tb), ctypes.c_void_p(d_tc or None), int(batch),
         ctypes.c_void_p(d_work), ctypes.c_void_p(d_grad), ctypes.c_void_p(d_loss), ctypes.c_void_p(stream)))
+
+
+def mlp_status(stream=0):
+    """Synchronise and raise if a tensor-core product's bounded wait ran out."""
+    _check("rddmc_mlp_status", lib().rddmc_mlp_status(ctypes.c_void_p(stream)))
 
 
 def mlp_adam(n_out, d_wf, d_wb, d_grad, d_m, d_v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):

@@ -95,3 +95,31 @@ def test_training_learns_the_first_passage_distribution(proposal):
     tA = held["tA"][:8192].cpu().numpy()
     emp = np.bincount(tA[tA >= 0] // p.J, minlength=6) / max(1, (tA >= 0).sum())
     assert 0.5 * np.abs(pred_face - emp).sum() < 0.05, (pred_face, emp)
+
+
+@pytest.mark.parametrize("Bsz", [64, 192, 4096])
+def test_tensor_core_forward_matches_fp64(proposal, Bsz):
+    """Logits of the tcgen05 forward pass against an FP64 forward of the same
+    BF16 weights and inputs (hidden activations rounded to BF16 as stored),
+    on batches that leave the last 128-row tile partly empty."""
+    p = proposal
+    d = p.generate(Bsz, seed=5150 + Bsz)
+    X = d["X"]
+    z = p.logits(X).cpu().numpy().astype(np.float64)
+    R.mlp_status(p.stream())
+    wb = p.wb.float().cpu().numpy().astype(np.float64)
+    wf = p.wf.cpu().numpy().astype(np.float64)
+    layers, off = [], 0
+    for (o, i) in M.shapes(p.n_out):
+        W = wb[off:off + o * i].reshape(o, i)
+        off += o * i
+        b = wf[off:off + o]
+        off += o
+        layers.append((W, b))
+    h = X.float().cpu().numpy().astype(np.float64)
+    for l, (W, b) in enumerate(layers):
+        h = h @ W.T + b
+        if l < 3:
+            h = torch.tensor(np.maximum(h, 0.0), dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    err = np.abs(z - h).max() / max(1.0, np.abs(h).max())
+    assert err < 2e-3, err
