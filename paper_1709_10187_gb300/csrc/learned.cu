@@ -456,12 +456,16 @@ cudaError_t gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const 
     // at least 80 KiB of shared memory: at most two CTAs per SM, so their TMEM
     // accumulators (<= 256 columns each) always fit the SM's 512 columns
     const size_t smem = std::max<size_t>(umma::smem_bytes(NT, K), 80 * 1024);
-    cudaError_t e = cudaFuncSetAttribute(umma::gemm_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     dim3 grid((N + NT - 1) / NT, (M + umma::kTileM - 1) / umma::kTileM);
-    umma::gemm_tc_kernel<EPI><<<grid, umma::kThreads, smem, s>>>(M, N, K, NT, A, lda, W, ldw, bias, outb, outf, ldc,
-                                                                  err);
+    CUtensorMap mapA, mapW;
+    std::memset(&mapA, 0, sizeof(mapA));
+    std::memset(&mapW, 0, sizeof(mapW));
+    const bool tma = K % umma::kPanel == 0 && umma::make_map(&mapA, A, M, K, lda, umma::kTileM) &&
+                     umma::make_map(&mapW, W, N, K, ldw, NT);
+    auto kern = tma ? umma::gemm_tc_kernel<EPI, true> : umma::gemm_tc_kernel<EPI, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, umma::kThreads, smem, s>>>(M, N, K, NT, A, lda, W, ldw, mapA, mapW, bias, outb, outf, ldc, err);
     return cudaGetLastError();
 }
 

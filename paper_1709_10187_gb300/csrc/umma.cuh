@@ -4,14 +4,17 @@
 // row-major with K contiguous ("K-major"), K a multiple of 16 and at most 128.
 //
 // One CTA of 128 threads computes a 128 x NT tile (NT <= 256, a multiple of
-// 16): the threads stage A and W in shared memory in the 128-byte swizzled
-// K-major layout (rows of 64 BF16 = 128 B, eight-row atoms of 1 KiB, 16-byte
-// chunk c of row r stored at chunk c ^ (r mod 8)), one elected thread issues
+// 16).  A and W are staged in shared memory in the 128-byte swizzled K-major
+// layout (rows of 64 BF16 = 128 B, eight-row atoms of 1 KiB, 16-byte chunk c
+// of row r stored at chunk c ^ (r mod 8)): by TMA (cp.async.bulk.tensor with
+// 128-byte swizzle, rows past the matrix filled with zeros by the copy engine)
+// when K is a multiple of 64, else by the threads.  One elected thread issues
 // K/16 tcgen05.mma instructions into a TMEM accumulator of 128 lanes x NT
 // columns and commits them to an mbarrier; every warp then reads its 32 lanes
 // back with tcgen05.ld for the epilogue.  Waits are bounded: a wait that runs
 // out sets the error word and the tile's outputs are left unwritten.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -70,12 +73,36 @@ __device__ __forceinline__ void stage(const __nv_bfloat16* __restrict__ src, int
 
 enum Epi { RELU_BF16 = 0, LINEAR_F32 = 1 };
 
+// Bounded wait for phase 0 of an mbarrier; returns false when it ran out.
+__device__ __forceinline__ bool wait_phase0(uint64_t* mbar) {
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(smem_u32(mbar)));
+    }
+    return done != 0;
+}
+
+// TMA copy of the box at element coordinates (x, y) of a 2D tensor map into
+// shared memory, completing `bytes` of the mbarrier's transaction count.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(mbar))
+        : "memory");
+}
+
 // C = epi(A W^T + bias).  Grid: (ceil(N / NT), ceil(M / 128)); dynamic shared
-// memory smem_bytes(NT, K).  err: set to 1 when a wait ran out.
-template <int EPI>
+// memory smem_bytes(NT, K).  TMA: stage by tensor maps mapA (A: K x M, box 64 x
+// 128) and mapW (W: K x N, box 64 x NT), K a multiple of 64.  err: set to 1
+// when a wait ran out.
+template <int EPI, bool TMA>
 __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, int NT,
                                                            const __nv_bfloat16* __restrict__ A, int lda,
                                                            const __nv_bfloat16* __restrict__ W, int ldw,
+                                                           const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapW,
                                                            const float* __restrict__ bias,
                                                            __nv_bfloat16* __restrict__ outb, float* __restrict__ outf,
                                                            int ldc, unsigned* err) {
@@ -85,7 +112,8 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
     unsigned char* sA = base;
     unsigned char* sB = sA + (size_t)panels * kTileM * 128;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + (size_t)panels * NT * 128);
-    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(mbar + 1);
+    uint64_t* tbar = mbar + 1;
+    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(mbar + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kTileM, n0 = blockIdx.x * NT;
@@ -98,17 +126,33 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
     }
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(tbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    stage(A, lda, m0, kTileM, min(kTileM, M - m0), K, sA);
-    stage(W, ldw, n0, NT, min(NT, N - n0), K, sB);
-    asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor-core reads
+    if (!TMA) {
+        stage(A, lda, m0, kTileM, min(kTileM, M - m0), K, sA);
+        stage(W, ldw, n0, NT, min(NT, N - n0), K, sB);
+        asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor-core reads
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *taddr_s;
 
-    if (threadIdx.x == 0) {
+    bool staged = true;
+    if (TMA && threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)(panels * (kTileM + NT) * 128);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(tbar)), "r"(bytes)
+                     : "memory");
+        for (int p = 0; p < panels; ++p) {
+            tma_load_2d(sA + (size_t)p * kTileM * 128, &mapA, p * kPanel, m0, tbar);
+            tma_load_2d(sB + (size_t)p * NT * 128, &mapW, p * kPanel, n0, tbar);
+        }
+        staged = wait_phase0(tbar);
+        if (!staged) atomicOr(err, 1u);
+    }
+
+    if (threadIdx.x == 0 && staged) {
         const uint32_t idesc = instr_desc(kTileM, NT);
         for (int s = 0; s < K / 16; ++s) {
             const int p = s >> 2, off = (s & 3) * 32;  // panel, byte offset of the 16-wide K slice
@@ -124,12 +168,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
                      :: "r"(smem_u32(mbar)));
     }
     // bounded wait for the products (phase 0)
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done) : "r"(smem_u32(mbar)));
-    }
+    const bool done = wait_phase0(mbar);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!done) {
         if (threadIdx.x == 0) atomicOr(err, 1u);
@@ -174,6 +213,31 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
 // slack, mbarrier and TMEM address).
 __host__ __device__ constexpr size_t smem_bytes(int nt, int k) {
     return 1024 + (size_t)((k + kPanel - 1) / kPanel) * (kTileM + nt) * 128 + 64;
+}
+
+// 2D BF16 tensor map of a row-major [rows x cols] matrix with leading
+// dimension ld, box of box_rows x 64 columns, 128-byte swizzle, zero fill.
+inline bool make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (Encode)fn;
+    }
+    if (((uintptr_t)ptr & 15u) || ((size_t)ld * 2) % 16) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kPanel, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace umma

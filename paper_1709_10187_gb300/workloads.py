@@ -150,7 +150,7 @@ def gaussian_random_field(n: int, slope: float, rng) -> np.ndarray:
     k = np.sqrt(kx * kx + ky * ky + kz * kz)
     amp = np.zeros_like(k)
     amp[k > 0] = k[k > 0] ** (slope / 2.0)
-    g = np.fft.irfftn(fk * amp, s=(n, n, n))
+    g = np.fft.irfftn(fk * amp, s=(n, n, n), axes=(0, 1, 2))
     g -= g.mean()
     return g / g.std()
 
