@@ -439,7 +439,12 @@ def _extras(R, torch, only=None):
             ("learned_vs_plain", lambda: _learned_vs_plain(R, torch))]
     if only:
         small = {"learned_small": lambda: _learned_vs_plain(R, torch, n=32, brick=8, tau0=1.0e6, npk=100_000,
-                                                            ndata=300_000, iters=300)}
+                                                            ndata=300_000, iters=300),
+                 # the clumpy workload's grid and frequency grid: 128^3 cells x 256 bins over [-256, 256]
+                 "learned_c5": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0, tau0=1.0e7,
+                                                         npk=200_000, ndata=1_500_000, iters=4000),
+                 "learned_c5_tau1e8": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0,
+                                                                tau0=1.0e8, npk=100_000, ndata=600_000, iters=4000)}
         jobs = [(k, f) for k, f in jobs + list(small.items()) if k == only]
         if not jobs:
             raise SystemExit(f"unknown extra {only!r}")
@@ -477,7 +482,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads and the learned-vs-plain comparison")
     ap.add_argument("--extra", default="", help="run only this extra (c3_sphere_static, c3_sphere_v20, "
-                    "c3_sphere_v200, c2_hybrid, batched_512, learned_vs_plain, learned_small) and print it")
+                    "c3_sphere_v200, c2_hybrid, batched_512, learned_vs_plain, learned_small, learned_c5, learned_c5_tau1e8) and print it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

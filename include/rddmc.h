@@ -507,8 +507,8 @@ int rddmc_mlp_adam(int n_out, float* d_wf, void* d_wb, const float* d_grad, floa
  * stream of packet i under `seed`) and write the outgoing frequencies to
  * d_out (device, n floats).  Their density is the angle-averaged
  * redistribution function R_II-A(x, x_in) of Appendix A.  For checking the
- * sampler; the table must be precomputed (the sampler's envelope table lives
- * there).
+ * sampler; the table must be precomputed in hybrid mode (the sampler's
+ * envelope table lives there): RDDMC_ERR_UNSUPPORTED for a DDMC-mode table.
  */
 int rddmc_scatter_samples(const rddmc_grid* grid, const void* d_table, double x_in, uint64_t seed, uint64_t n,
                           float* d_out, void* stream);

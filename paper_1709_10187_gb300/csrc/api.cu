@@ -433,6 +433,7 @@ int rddmc_scatter_samples(const rddmc_grid* g, const void* d_table, double x_in,
                           float* d_out, void* stream) {
     if (!g || !d_table || !d_out || n == 0 || !std::isfinite(x_in)) return RDDMC_ERR_ARG;
     if (!g->precomputed) return RDDMC_ERR_TABLE;
+    if (g->params.mode != RDDMC_MODE_HYBRID) return RDDMC_ERR_UNSUPPORTED;  // no envelope table in DDMC mode
     return cuda_status(launch_scatter_samples(*g, d_table, x_in, seed, n, d_out, (cudaStream_t)stream));
 }
 

@@ -170,7 +170,9 @@ cudaError_t launch_precompute(const rddmc_grid& g, void* d_table, cudaStream_t s
     else
         rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, nrow);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    upar_kernel<<<(kUparN + 127) / 128, 128, 0, s>>>((float2*)(base + g.off_upar), g.a);
+    // the u_par envelope table serves only the continuous MC of the hybrid scheme
+    if (g.params.mode == RDDMC_MODE_HYBRID)
+        upar_kernel<<<(kUparN + 127) / 128, 128, 0, s>>>((float2*)(base + g.off_upar), g.a);
     return cudaGetLastError();
 }
 
