@@ -329,6 +329,25 @@ def _sliced_rate(R, torch, prob, npk, seed, slice_, launches=5, warm=2):
             "launches": launches}
 
 
+def _complete(R, torch, w, npk):
+    """A run to completion: escaped packets/s over the wall time from launch to
+    the last packet's escape (CUDA events around one launch)."""
+    prob = R.Problem(w)
+    prob.run(min(npk, 2000), w.seed + 1)  # warm-up
+    prob.reset()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(torch.cuda.current_stream())
+    prob.launch(npk, w.seed)
+    a1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    dt = a0.elapsed_time(a1) / 1e3
+    t = prob.read()
+    return {"workload": w.name, "packets": npk, "s": dt, "escaped": t["escaped"], "aborted": t["aborted"],
+            "escaped_per_s": t["escaped"] / dt, "transitions_per_s": t["steps"] / dt,
+            "transitions_per_packet": t["steps"] / npk}
+
+
 def _batched(R, torch, packet_scale=0.01, max_steps=1_000_000):
     """The batched workload: 512 slab/sphere instances in one persistent launch,
     schedule picked by the autotuner, replayed from a captured CUDA graph."""
@@ -435,6 +454,8 @@ def _extras(R, torch, only=None):
             ("c3_sphere_v200", lambda: _sliced_rate(R, torch, R.Problem(W.C3_V200), 1_000_000, W.C3.seed, 4096)),
             ("c2_hybrid", lambda: _sliced_rate(R, torch, R.Problem(W.C2, mode=R.MODE_HYBRID), 1_000_000,
                                                W.C2.seed, 4096)),
+            ("c1_complete", lambda: _complete(R, torch, W.C1, W.C1.packets)),
+            ("c2_complete_1e5", lambda: _complete(R, torch, W.C2, 100_000)),
             ("batched_512", lambda: _batched(R, torch)),
             ("learned_vs_plain", lambda: _learned_vs_plain(R, torch))]
     if only:
@@ -482,7 +503,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads and the learned-vs-plain comparison")
     ap.add_argument("--extra", default="", help="run only this extra (c3_sphere_static, c3_sphere_v20, "
-                    "c3_sphere_v200, c2_hybrid, batched_512, learned_vs_plain, learned_small, learned_c5, learned_c5_tau1e8) and print it")
+                    "c3_sphere_v200, c2_hybrid, c1_complete, c2_complete_1e5, batched_512, learned_vs_plain, learned_small, learned_c5, learned_c5_tau1e8) and print it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
