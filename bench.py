@@ -455,7 +455,6 @@ def _extras(R, torch, only=None):
             ("c2_hybrid", lambda: _sliced_rate(R, torch, R.Problem(W.C2, mode=R.MODE_HYBRID), 1_000_000,
                                                W.C2.seed, 4096)),
             ("c1_complete", lambda: _complete(R, torch, W.C1, W.C1.packets)),
-            ("c2_complete_1e5", lambda: _complete(R, torch, W.C2, 100_000)),
             ("batched_512", lambda: _batched(R, torch)),
             ("learned_vs_plain", lambda: _learned_vs_plain(R, torch))]
     if only:
@@ -464,6 +463,8 @@ def _extras(R, torch, only=None):
                  # the clumpy workload's grid and frequency grid: 128^3 cells x 256 bins over [-256, 256]
                  "learned_c5": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0, tau0=1.0e7,
                                                          npk=200_000, ndata=1_500_000, iters=4000),
+                 # a C2 subset run to completion: bounded below by its slowest packet (~3e9 transitions)
+                 "c2_complete_1e5": lambda: _complete(R, torch, W.C2, 100_000),
                  "learned_c5_tau1e8": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0,
                                                                 tau0=1.0e8, npk=100_000, ndata=600_000, iters=4000)}
         jobs = [(k, f) for k, f in jobs + list(small.items()) if k == only]
