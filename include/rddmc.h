@@ -475,9 +475,8 @@ int rddmc_propose(const rddmc_grid* grid, const void* d_table, const rddmc_propo
  * master copy and BF16 copy, same layout, rddmc_mlp_param_count(n_out)
  * elements: W1[128x16] b1 W2[128x128] b2 W3[128x128] b3 W4[n_out x 128] b4
  * (row-major W[out][in]).  Matrix products run on tensor cores with BF16
- * inputs and FP32 accumulation -- the forward products as tcgen05.mma with
- * tensor-memory accumulators, the backward products as warp-level MMA;
- * batch sizes are multiples of 64. */
+ * inputs and FP32 accumulation: tcgen05.mma with tensor-memory accumulators
+ * and TMA-staged operands; batch sizes are multiples of 64. */
 uint64_t rddmc_mlp_param_count(int n_out);
 uint64_t rddmc_mlp_work_bytes(int batch, int n_out);
 int rddmc_mlp_to_bf16(int n_out, const float* d_wf, void* d_wb, void* stream);

@@ -9,7 +9,6 @@
 // stream as the walk) until a spatial move leaves the brick.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <mma.h>
 
 #include <algorithm>
 #include <cmath>
@@ -198,12 +197,13 @@ int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_table
 // [nA + nB, nA + nB + 6 S) (exit cell on each face, S = b^2 per face, used
 // one slice at a time); columns past the heads are padding.  Parameters, FP32 master copy and BF16 copy in the same order:
 // W1[128x16] b1[128] W2[128x128] b2[128] W3[128x128] b3[128] W4[n_out x 128]
-// b4[n_out].  Matrix products run on tensor cores (WMMA, BF16 inputs, FP32
-// accumulation); softmax, cross-entropy, bias sums and Adam in FP32.
+// b4[n_out].  Every matrix product runs on the tcgen05 tensor cores
+// (umma.cuh: BF16 operands, FP32 accumulators in tensor memory), the backward
+// ones on transposed copies so that both operands are K-major; softmax,
+// cross-entropy, bias sums and Adam in FP32.
 namespace rddmc {
 namespace {
 
-using namespace nvcuda;
 constexpr int kIn = 16, kHid = 128;
 
 struct MlpOffsets {
@@ -220,90 +220,6 @@ MlpOffsets mlp_offsets(int n_out) {
     }
     o.total = off;
     return o;
-}
-
-enum Epi { EPI_RELU_BF16 = 0, EPI_LINEAR_F32 = 1, EPI_MASK_BF16 = 2, EPI_F32 = 3, EPI_F32_ADD = 4 };
-
-// C[M x N] = A[M x K] B[K x N]; A row- or column-major (lda), B row- or
-// column-major (ldb); M, N, K multiples of 16.  Block = 4 warps on a 64 x 64
-// tile, each warp 32 x 32 (2 x 2 fragments).
-template <bool A_ROW, bool B_ROW, int EPI>
-__global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda,
-                                                   const __nv_bfloat16* __restrict__ B, int ldb,
-                                                   const float* __restrict__ bias,
-                                                   const __nv_bfloat16* __restrict__ mask, int ldmask,
-                                                   __nv_bfloat16* __restrict__ outb, float* __restrict__ outf,
-                                                   int ldc) {
-    __shared__ float tile[4][32 * 32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * 64 + (warp >> 1) * 32, n0 = blockIdx.x * 64 + (warp & 1) * 32;
-    using LA = typename std::conditional<A_ROW, wmma::row_major, wmma::col_major>::type;
-    using LB = typename std::conditional<B_ROW, wmma::row_major, wmma::col_major>::type;
-    wmma::fragment<wmma::accumulator, 16, 16, 16, float> c[2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) wmma::fill_fragment(c[i][j], 0.0f);
-    const bool rv[2] = {m0 < M, m0 + 16 < M}, cv[2] = {n0 < N, n0 + 16 < N};
-    // split-K: blockIdx.z takes a contiguous range of K (multiples of 16)
-    const int kc = ((K + (int)gridDim.z * 16 - 1) / ((int)gridDim.z * 16)) * 16;
-    const int kb = (int)blockIdx.z * kc, ke = min(K, kb + kc);
-    for (int k0 = kb; k0 < ke; k0 += 16) {
-        wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, LA> a[2];
-        wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, LB> b[2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            if (!rv[i]) continue;
-            const int m = m0 + 16 * i;
-            wmma::load_matrix_sync(a[i], A_ROW ? A + (size_t)m * lda + k0 : A + (size_t)k0 * lda + m, lda);
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            if (!cv[j]) continue;
-            const int n = n0 + 16 * j;
-            wmma::load_matrix_sync(b[j], B_ROW ? B + (size_t)k0 * ldb + n : B + (size_t)n * ldb + k0, ldb);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-                if (rv[i] && cv[j]) wmma::mma_sync(c[i][j], a[i], b[j], c[i][j]);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-            if (rv[i] && cv[j]) wmma::store_matrix_sync(&tile[warp][(16 * i) * 32 + 16 * j], c[i][j], 32,
-                                                         wmma::mem_row_major);
-    __syncwarp();
-    for (int e = lane; e < 32 * 32; e += 32) {
-        const int r = e >> 5, cc = e & 31, m = m0 + r, n = n0 + cc;
-        if (m >= M || n >= N) continue;
-        float v = tile[warp][e];
-        if (EPI == EPI_RELU_BF16) {
-            v = fmaxf(v + bias[n], 0.0f);
-            outb[(size_t)m * ldc + n] = __float2bfloat16(v);
-        } else if (EPI == EPI_LINEAR_F32) {
-            outf[(size_t)m * ldc + n] = v + bias[n];
-        } else if (EPI == EPI_MASK_BF16) {
-            v = __bfloat162float(mask[(size_t)m * ldmask + n]) > 0.0f ? v : 0.0f;
-            outb[(size_t)m * ldc + n] = __float2bfloat16(v);
-            outf[(size_t)m * ldc + n] = v;
-        } else if (EPI == EPI_F32_ADD) {
-            atomicAdd(&outf[(size_t)m * ldc + n], v);  // partial sum of a K split
-        } else {
-            outf[(size_t)m * ldc + n] = v;
-        }
-    }
-}
-
-template <bool A_ROW, bool B_ROW, int EPI>
-cudaError_t gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
-                 const float* bias, const __nv_bfloat16* mask, int ldmask, __nv_bfloat16* outb, float* outf, int ldc,
-                 cudaStream_t s, int ksplit = 1) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64, ksplit);
-    gemm_kernel<A_ROW, B_ROW, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, bias, mask, ldmask, outb, outf, ldc);
-    return cudaGetLastError();
 }
 
 // Softmax cross-entropy of the heads, one warp per row: loss += CE_A + CE_B
@@ -380,11 +296,13 @@ cudaError_t colsum(const float* dy, int Bsz, int N, float* db, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// K splits for a weight-gradient product (K = batch rows): about two waves of
-// CTAs over the GPU, each split at least 128 rows long.
+// K splits for a weight-gradient product (K = batch rows) on 128 x min(N, 256)
+// tensor-core tiles: about two waves of CTAs over the GPU, at most one split
+// per 64-column panel of K.
 int ksplit_for(int M, int N, int K) {
-    const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
-    return std::max(1, std::min(K / 128, (304 + tiles - 1) / tiles));
+    const int nt = std::min(256, N);
+    const int tiles = ((M + 127) / 128) * ((N + nt - 1) / nt);
+    return std::max(1, std::min((K + 63) / 64, (304 + tiles - 1) / tiles));
 }
 
 __global__ void adam_kernel(uint64_t n, float* __restrict__ w, __nv_bfloat16* __restrict__ wb,
@@ -412,12 +330,13 @@ __global__ void to_bf16_kernel(uint64_t n, const float* __restrict__ w, __nv_bfl
 struct MlpWork {
     __nv_bfloat16 *H[3], *dHb[2], *dlogb;
     float *dHf, *logits, *dlogf;
+    __nv_bfloat16 *dZT, *HT, *WT;  // transposed copies for the K-major products of the backward pass
 };
 
 uint64_t mlp_work_bytes(int Bsz, int n_out) {
     const uint64_t bh = (uint64_t)Bsz * kHid;
     return align256(bh * 2) * 5 + align256(bh * 4) + align256((uint64_t)Bsz * n_out * 4) * 2 +
-           align256((uint64_t)Bsz * n_out * 2);
+           align256((uint64_t)Bsz * n_out * 2) * 2 + align256(bh * 2) + align256((uint64_t)n_out * kHid * 2);
 }
 
 MlpWork mlp_work(void* d_work, int Bsz, int n_out) {
@@ -429,7 +348,10 @@ MlpWork mlp_work(void* d_work, int Bsz, int n_out) {
     w.dHf = (float*)p; p += align256(bh * 4);
     w.logits = (float*)p; p += align256((uint64_t)Bsz * n_out * 4);
     w.dlogf = (float*)p; p += align256((uint64_t)Bsz * n_out * 4);
-    w.dlogb = (__nv_bfloat16*)p;
+    w.dlogb = (__nv_bfloat16*)p; p += align256((uint64_t)Bsz * n_out * 2);
+    w.dZT = (__nv_bfloat16*)p; p += align256((uint64_t)Bsz * n_out * 2);   // [n_out x B] or [128 x B]
+    w.HT = (__nv_bfloat16*)p; p += align256(bh * 2);                          // [128 x B] or [16 x B]
+    w.WT = (__nv_bfloat16*)p;                                                 // [128 x n_out]
     return w;
 }
 
@@ -449,26 +371,39 @@ unsigned* tc_err_ptr() {
     return addr[dev];
 }
 
-// C = epi(A W^T + bias) on tcgen05 (umma.cuh): A [M x K], W [N x K], K <= 128.
+// C = epi(A W^T (+ bias)) on tcgen05 (umma.cuh): A [M x K], W [N x K], both K
+// contiguous; ksplit > 1 only with F32_ADD.  K <= 128 and not a multiple of 64
+// is staged by the threads, everything else by TMA.
 template <int EPI>
 cudaError_t gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* W, int ldw,
-                    const float* bias, __nv_bfloat16* outb, float* outf, int ldc, cudaStream_t s) {
+                    const float* bias, const __nv_bfloat16* mask, int ldmask, __nv_bfloat16* outb, float* outf,
+                    int ldc, cudaStream_t s, int ksplit = 1) {
     unsigned* err = tc_err_ptr();
-    if (!err || K % 16 || K > 128 || N % 16) return cudaErrorInvalidValue;
+    if (!err || K % 16 || N % 16 || ksplit < 1 || (ksplit > 1 && EPI != umma::F32_ADD)) return cudaErrorInvalidValue;
     const int NT = std::min(256, N);
     // at least 80 KiB of shared memory: at most two CTAs per SM, so their TMEM
     // accumulators (<= 256 columns each) always fit the SM's 512 columns
-    const size_t smem = std::max<size_t>(umma::smem_bytes(NT, K), 80 * 1024);
-    dim3 grid((N + NT - 1) / NT, (M + umma::kTileM - 1) / umma::kTileM);
+    const size_t smem = std::max<size_t>(umma::smem_bytes(NT), 80 * 1024);
+    dim3 grid((N + NT - 1) / NT, (M + umma::kTileM - 1) / umma::kTileM, ksplit);
     CUtensorMap mapA, mapW;
     std::memset(&mapA, 0, sizeof(mapA));
     std::memset(&mapW, 0, sizeof(mapW));
-    const bool tma = K % umma::kPanel == 0 && umma::make_map(&mapA, A, M, K, lda, umma::kTileM) &&
-                     umma::make_map(&mapW, W, N, K, ldw, NT);
-    auto kern = tma ? umma::gemm_tc_kernel<EPI, true> : umma::gemm_tc_kernel<EPI, false>;
+    const bool staged = K <= 128 && K % umma::kPanel != 0;
+    if (staged && ksplit != 1) return cudaErrorInvalidValue;
+    if (!staged && !(umma::make_map(&mapA, A, M, K, lda, umma::kTileM) && umma::make_map(&mapW, W, N, K, ldw, NT)))
+        return cudaErrorInvalidValue;
+    auto kern = staged ? umma::gemm_tc_kernel<EPI, false> : umma::gemm_tc_kernel<EPI, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, umma::kThreads, smem, s>>>(M, N, K, NT, A, lda, W, ldw, mapA, mapW, bias, outb, outf, ldc, err);
+    kern<<<grid, umma::kThreads, smem, s>>>(M, N, K, NT, A, lda, W, ldw, mapA, mapW, bias, mask, ldmask, outb, outf,
+                                            ldc, err);
+    return cudaGetLastError();
+}
+
+cudaError_t transpose(const __nv_bfloat16* in, int rows, int cols, int ld_in, __nv_bfloat16* out, int ld_out,
+                      cudaStream_t s) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    umma::transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(in, rows, cols, ld_in, out, ld_out);
     return cudaGetLastError();
 }
 
@@ -476,15 +411,15 @@ cudaError_t mlp_forward(int n_out, const float* wf, const __nv_bfloat16* wb, con
                         const MlpWork& w, cudaStream_t s) {
     const MlpOffsets o = mlp_offsets(n_out);
     cudaError_t e;
-    if ((e = gemm_tc<umma::RELU_BF16>(Bsz, kHid, kIn, X, kIn, wb + o.W[0], kIn, wf + o.b[0], w.H[0], nullptr, kHid,
-                                      s)) != cudaSuccess)
+    if ((e = gemm_tc<umma::RELU_BF16>(Bsz, kHid, kIn, X, kIn, wb + o.W[0], kIn, wf + o.b[0], nullptr, 0, w.H[0],
+                                      nullptr, kHid, s)) != cudaSuccess)
         return e;
     for (int l = 1; l < 3; ++l)
-        if ((e = gemm_tc<umma::RELU_BF16>(Bsz, kHid, kHid, w.H[l - 1], kHid, wb + o.W[l], kHid, wf + o.b[l], w.H[l],
-                                          nullptr, kHid, s)) != cudaSuccess)
+        if ((e = gemm_tc<umma::RELU_BF16>(Bsz, kHid, kHid, w.H[l - 1], kHid, wb + o.W[l], kHid, wf + o.b[l],
+                                          nullptr, 0, w.H[l], nullptr, kHid, s)) != cudaSuccess)
             return e;
-    return gemm_tc<umma::LINEAR_F32>(Bsz, n_out, kHid, w.H[2], kHid, wb + o.W[3], kHid, wf + o.b[3], nullptr,
-                                     w.logits, n_out, s);
+    return gemm_tc<umma::LINEAR_F32>(Bsz, n_out, kHid, w.H[2], kHid, wb + o.W[3], kHid, wf + o.b[3], nullptr, 0,
+                                     nullptr, w.logits, n_out, s);
 }
 
 }  // namespace
@@ -537,25 +472,40 @@ int rddmc_mlp_loss_grad(int n_out, int nA, int nB, int nC, int S, const float* d
                                                        nC > 0 ? d_tc : nullptr, batch, w.dlogf, w.dlogb, d_loss);
     // gradients accumulate (split-K products, column sums) into a zeroed buffer
     if (cudaMemsetAsync(d_grad, 0, o.total * sizeof(float), s) != cudaSuccess) return RDDMC_ERR_CUDA;
-    // output layer: dW4 = dlog^T H3, db4 = colsum(dlog), dH3 = (dlog W4) * [H3 > 0]
-    gemm<false, true, EPI_F32_ADD>(n_out, kHid, batch, w.dlogb, n_out, w.H[2], kHid, nullptr, nullptr, 0, nullptr,
-                                   d_grad + o.W[3], kHid, s, ksplit_for(n_out, kHid, batch));
-    colsum(w.dlogf, batch, n_out, d_grad + o.b[3], s);
-    gemm<true, true, EPI_MASK_BF16>(batch, kHid, n_out, w.dlogb, n_out, wb + o.W[3], kHid, nullptr, w.H[2], kHid,
-                                    w.dHb[0], w.dHf, kHid, s);
+    // Every product runs on tcgen05 with K contiguous in both operands:
+    //   dW = dZ^T H     as (dZ^T [out x B]) (H^T [in x B])^T, K = batch, split over K
+    //   dH = (dZ W) .* [H > 0]  as (dZ [B x out]) (W^T [in x out])^T, K = out
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    // output layer
+    chk(transpose(w.dlogb, batch, n_out, n_out, w.dZT, batch, s));
+    chk(transpose(w.H[2], batch, kHid, kHid, w.HT, batch, s));
+    chk(gemm_tc<umma::F32_ADD>(n_out, kHid, batch, w.dZT, batch, w.HT, batch, nullptr, nullptr, 0, nullptr,
+                               d_grad + o.W[3], kHid, s, ksplit_for(n_out, kHid, batch)));
+    chk(colsum(w.dlogf, batch, n_out, d_grad + o.b[3], s));
+    chk(transpose(wb + o.W[3], n_out, kHid, kHid, w.WT, n_out, s));
+    chk(gemm_tc<umma::MASK_BF16>(batch, kHid, n_out, w.dlogb, n_out, w.WT, n_out, nullptr, w.H[2], kHid, w.dHb[0],
+                                 w.dHf, kHid, s));
     int cur = 0;
     for (int l = 2; l >= 1; --l) {
         // layer l (W[l]: H[l-1] -> H[l]); dHb[cur] holds dL/d(pre-activation of H[l])
-        gemm<false, true, EPI_F32_ADD>(kHid, kHid, batch, w.dHb[cur], kHid, w.H[l - 1], kHid, nullptr, nullptr, 0,
-                                       nullptr, d_grad + o.W[l], kHid, s, ksplit_for(kHid, kHid, batch));
-        colsum(w.dHf, batch, kHid, d_grad + o.b[l], s);
-        gemm<true, true, EPI_MASK_BF16>(batch, kHid, kHid, w.dHb[cur], kHid, wb + o.W[l], kHid, nullptr, w.H[l - 1],
-                                        kHid, w.dHb[cur ^ 1], w.dHf, kHid, s);
+        chk(transpose(w.dHb[cur], batch, kHid, kHid, w.dZT, batch, s));
+        chk(transpose(w.H[l - 1], batch, kHid, kHid, w.HT, batch, s));
+        chk(gemm_tc<umma::F32_ADD>(kHid, kHid, batch, w.dZT, batch, w.HT, batch, nullptr, nullptr, 0, nullptr,
+                                   d_grad + o.W[l], kHid, s, ksplit_for(kHid, kHid, batch)));
+        chk(colsum(w.dHf, batch, kHid, d_grad + o.b[l], s));
+        chk(transpose(wb + o.W[l], kHid, kHid, kHid, w.WT, kHid, s));
+        chk(gemm_tc<umma::MASK_BF16>(batch, kHid, kHid, w.dHb[cur], kHid, w.WT, kHid, nullptr, w.H[l - 1], kHid,
+                                     w.dHb[cur ^ 1], w.dHf, kHid, s));
         cur ^= 1;
     }
-    gemm<false, true, EPI_F32_ADD>(kHid, kIn, batch, w.dHb[cur], kHid, X, kIn, nullptr, nullptr, 0, nullptr,
-                                   d_grad + o.W[0], kIn, s, ksplit_for(kHid, kIn, batch));
-    colsum(w.dHf, batch, kHid, d_grad + o.b[0], s);
+    // input layer: dW1 = dZ1^T X
+    chk(transpose(w.dHb[cur], batch, kHid, kHid, w.dZT, batch, s));
+    chk(transpose(X, batch, kIn, kIn, w.HT, batch, s));
+    chk(gemm_tc<umma::F32_ADD>(kHid, kIn, batch, w.dZT, batch, w.HT, batch, nullptr, nullptr, 0, nullptr,
+                               d_grad + o.W[0], kIn, s, ksplit_for(kHid, kIn, batch)));
+    chk(colsum(w.dHf, batch, kHid, d_grad + o.b[0], s));
+    if (e != cudaSuccess) return RDDMC_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
 }
 

@@ -1,18 +1,21 @@
 // umma.cuh -- dense BF16 products on the 5th-generation tensor cores
 // (tcgen05.mma, FP32 accumulators in tensor memory) for the learned proposal's
 // network: C[M x N] = A[M x K] W[N x K]^T (+ bias, epilogue), both operands
-// row-major with K contiguous ("K-major"), K a multiple of 16 and at most 128.
+// row-major with K contiguous ("K-major"), K a multiple of 16.
 //
 // One CTA of 128 threads computes a 128 x NT tile (NT <= 256, a multiple of
-// 16).  A and W are staged in shared memory in the 128-byte swizzled K-major
-// layout (rows of 64 BF16 = 128 B, eight-row atoms of 1 KiB, 16-byte chunk c
-// of row r stored at chunk c ^ (r mod 8)): by TMA (cp.async.bulk.tensor with
-// 128-byte swizzle, rows past the matrix filled with zeros by the copy engine)
-// when K is a multiple of 64, else by the threads.  One elected thread issues
-// K/16 tcgen05.mma instructions into a TMEM accumulator of 128 lanes x NT
-// columns and commits them to an mbarrier; every warp then reads its 32 lanes
-// back with tcgen05.ld for the epilogue.  Waits are bounded: a wait that runs
-// out sets the error word and the tile's outputs are left unwritten.
+// 16), over K in blocks of 128 (two 64-column panels), optionally a range of
+// K per blockIdx.z (split-K).  A block of A and W is staged in shared memory
+// in the 128-byte swizzled K-major layout (rows of 64 BF16 = 128 B, eight-row
+// atoms of 1 KiB, 16-byte chunk c of row r stored at chunk c ^ (r mod 8)): by
+// TMA (cp.async.bulk.tensor with 128-byte swizzle; rows and columns past the
+// matrix filled with zeros by the copy engine), or by the threads for a single
+// block with K not a multiple of 64.  One elected thread issues the block's
+// tcgen05.mma instructions into a TMEM accumulator of 128 lanes x NT columns,
+// commits them to an mbarrier and waits before reusing the shared memory;
+// after the last block every warp reads its 32 lanes back with tcgen05.ld for
+// the epilogue.  Waits are bounded: a wait that runs out sets the error word
+// and the tile's outputs are left unwritten.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -71,21 +74,21 @@ __device__ __forceinline__ void stage(const __nv_bfloat16* __restrict__ src, int
     }
 }
 
-enum Epi { RELU_BF16 = 0, LINEAR_F32 = 1 };
+enum Epi { RELU_BF16 = 0, LINEAR_F32 = 1, MASK_BF16 = 2, F32_ADD = 3 };
 
-// Bounded wait for phase 0 of an mbarrier; returns false when it ran out.
-__device__ __forceinline__ bool wait_phase0(uint64_t* mbar) {
+// Bounded wait for the given phase parity of an mbarrier; false when it ran out.
+__device__ __forceinline__ bool wait_parity(uint64_t* mbar, uint32_t parity) {
     uint32_t done = 0;
     for (int it = 0; it < (1 << 22) && !done; ++it) {
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done) : "r"(smem_u32(mbar)));
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity));
     }
     return done != 0;
 }
 
 // TMA copy of the box at element coordinates (x, y) of a 2D tensor map into
-// shared memory, completing `bytes` of the mbarrier's transaction count.
+// shared memory, counted on the mbarrier's transaction bytes.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* mbar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
@@ -93,10 +96,32 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// C = epi(A W^T + bias).  Grid: (ceil(N / NT), ceil(M / 128)); dynamic shared
-// memory smem_bytes(NT, K).  TMA: stage by tensor maps mapA (A: K x M, box 64 x
-// 128) and mapW (W: K x N, box 64 x NT), K a multiple of 64.  err: set to 1
-// when a wait ran out.
+// Issue the tcgen05.mma instructions of one staged block: `slices` K-slices of
+// 16 (four per 64-column panel), the first of them overwriting the accumulator
+// when `first`.
+__device__ __forceinline__ void mma_block(uint32_t tmem, unsigned char* sA, unsigned char* sB, int NT, int slices,
+                                          bool first) {
+    const uint32_t idesc = instr_desc(kTileM, NT);
+    for (int s = 0; s < slices; ++s) {
+        const int p = s >> 2, off = (s & 3) * 32;  // panel, byte offset of the 16-wide K slice
+        const uint64_t ad = smem_desc(smem_u32(sA + (size_t)p * kTileM * 128 + off));
+        const uint64_t bd = smem_desc(smem_u32(sB + (size_t)p * NT * 128 + off));
+        const uint32_t acc = (first && s == 0) ? 0u : 1u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+}
+
+// C = epi(A W^T (+ bias)) for A [M x K], W [N x K], both K contiguous.
+// Grid: (ceil(N / NT), ceil(M / 128), ksplit); blockIdx.z takes a range of K
+// in blocks of 128 (64-column panels).  TMA path: tensor maps mapA (box 64 x
+// 128) and mapW (box 64 x NT), any K (columns past K are zero-filled);
+// thread-staged path: K <= 128.  Epilogues: RELU_BF16 and LINEAR_F32 add the
+// bias; MASK_BF16 keeps entries where mask > 0 and writes them to outb (BF16)
+// and outf (FP32); F32_ADD adds into outf (split-K partial sums).  err: set
+// to 1 when a wait ran out (the tile's outputs are then left unwritten).
 template <int EPI, bool TMA>
 __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, int NT,
                                                            const __nv_bfloat16* __restrict__ A, int lda,
@@ -104,20 +129,26 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
                                                            const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapW,
                                                            const float* __restrict__ bias,
+                                                           const __nv_bfloat16* __restrict__ mask, int ldmask,
                                                            __nv_bfloat16* __restrict__ outb, float* __restrict__ outf,
                                                            int ldc, unsigned* err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int panels = (K + kPanel - 1) / kPanel;
+    constexpr int kMaxPanels = 2;  // a K block is at most 128 wide
     unsigned char* sA = base;
-    unsigned char* sB = sA + (size_t)panels * kTileM * 128;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + (size_t)panels * NT * 128);
+    unsigned char* sB = sA + (size_t)kMaxPanels * kTileM * 128;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + (size_t)kMaxPanels * NT * 128);
     uint64_t* tbar = mbar + 1;
     uint32_t* taddr_s = reinterpret_cast<uint32_t*>(mbar + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kTileM, n0 = blockIdx.x * NT;
     const int ncols = tmem_cols(NT);
+    // this split's range of K, in whole 64-column panels
+    const int kpanels = (K + kPanel - 1) / kPanel;
+    const int per = (kpanels + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int p_begin = (int)blockIdx.z * per, p_end = min(kpanels, p_begin + per);
+    if (p_begin >= p_end) return;  // an empty split adds nothing
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -129,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(tbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    if (!TMA) {
+    if (!TMA) {  // one block: K <= 128
         stage(A, lda, m0, kTileM, min(kTileM, M - m0), K, sA);
         stage(W, ldw, n0, NT, min(NT, N - n0), K, sB);
         asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor-core reads
@@ -139,40 +170,43 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *taddr_s;
 
-    bool staged = true;
-    if (TMA && threadIdx.x == 0) {
-        const uint32_t bytes = (uint32_t)(panels * (kTileM + NT) * 128);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(tbar)), "r"(bytes)
-                     : "memory");
-        for (int p = 0; p < panels; ++p) {
-            tma_load_2d(sA + (size_t)p * kTileM * 128, &mapA, p * kPanel, m0, tbar);
-            tma_load_2d(sB + (size_t)p * NT * 128, &mapW, p * kPanel, n0, tbar);
+    // one thread stages (TMA), issues and waits, block by block; the smem of a
+    // block is reused only after its products completed
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        uint32_t phase = 0;
+        if (TMA) {
+            for (int p = p_begin; p < p_end && ok; p += kMaxPanels, phase ^= 1u) {
+                const int np = min(kMaxPanels, p_end - p);
+                const uint32_t bytes = (uint32_t)(np * (kTileM + NT) * 128);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             :: "r"(smem_u32(tbar)), "r"(bytes) : "memory");
+                for (int q = 0; q < np; ++q) {
+                    tma_load_2d(sA + (size_t)q * kTileM * 128, &mapA, (p + q) * kPanel, m0, tbar);
+                    tma_load_2d(sB + (size_t)q * NT * 128, &mapW, (p + q) * kPanel, n0, tbar);
+                }
+                ok = wait_parity(tbar, phase);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                mma_block(tmem, sA, sB, NT, 4 * np, p == p_begin);  // columns past K were zero-filled
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_u32(mbar)));
+                ok = wait_parity(mbar, phase);
+            }
+        } else {
+            mma_block(tmem, sA, sB, NT, K / 16, true);  // only the staged K columns
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(mbar)));
+            ok = wait_parity(mbar, 0);
         }
-        staged = wait_phase0(tbar);
-        if (!staged) atomicOr(err, 1u);
+        if (!ok) atomicOr(err, 1u);
+        ok_s = ok ? 1 : 0;
     }
-
-    if (threadIdx.x == 0 && staged) {
-        const uint32_t idesc = instr_desc(kTileM, NT);
-        for (int s = 0; s < K / 16; ++s) {
-            const int p = s >> 2, off = (s & 3) * 32;  // panel, byte offset of the 16-wide K slice
-            const uint64_t ad = smem_desc(smem_u32(sA + (size_t)p * kTileM * 128 + off));
-            const uint64_t bd = smem_desc(smem_u32(sB + (size_t)p * NT * 128 + off));
-            const uint32_t acc = s > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(smem_u32(mbar)));
-    }
-    // bounded wait for the products (phase 0)
-    const bool done = wait_phase0(mbar);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!done) {
-        if (threadIdx.x == 0) atomicOr(err, 1u);
-    } else {
+    if (ok_s) {
         // warp w reads TMEM lanes 32w..32w+31: thread t holds row m0 + 32w + t
         const int row = m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < NT; c0 += 32) {
@@ -194,9 +228,19 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
                 for (int j = 0; j < 32; ++j) {
                     const int n = n0 + c0 + j;
                     if (c0 + j >= NT || n >= N) continue;
-                    const float x = __uint_as_float(v[j]) + bias[n];
-                    if (EPI == RELU_BF16) outb[(size_t)row * ldc + n] = __float2bfloat16(fmaxf(x, 0.0f));
-                    else outf[(size_t)row * ldc + n] = x;
+                    const float x = __uint_as_float(v[j]);
+                    const size_t o = (size_t)row * ldc + n;
+                    if (EPI == RELU_BF16) {
+                        outb[o] = __float2bfloat16(fmaxf(x + bias[n], 0.0f));
+                    } else if (EPI == LINEAR_F32) {
+                        outf[o] = x + bias[n];
+                    } else if (EPI == MASK_BF16) {
+                        const float y = __bfloat162float(mask[(size_t)row * ldmask + n]) > 0.0f ? x : 0.0f;
+                        outb[o] = __float2bfloat16(y);
+                        outf[o] = y;
+                    } else {
+                        atomicAdd(&outf[o], x);
+                    }
                 }
             }
         }
@@ -209,10 +253,27 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
     }
 }
 
-// Dynamic shared memory of a 128 x NT tile with K-long rows (+1 KiB alignment
-// slack, mbarrier and TMEM address).
-__host__ __device__ constexpr size_t smem_bytes(int nt, int k) {
-    return 1024 + (size_t)((k + kPanel - 1) / kPanel) * (kTileM + nt) * 128 + 64;
+// BF16 transpose: out[c][r] = in[r][c] for in [rows x cols] (leading dims
+// ld_in, ld_out), 32 x 32 tiles through shared memory.
+__global__ void transpose_bf16_kernel(const __nv_bfloat16* __restrict__ in, int rows, int cols, int ld_in,
+                                      __nv_bfloat16* __restrict__ out, int ld_out) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        t[i][threadIdx.x] = (r < rows && c < cols) ? in[(size_t)r * ld_in + c] : __float2bfloat16(0.0f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[(size_t)c * ld_out + r] = t[threadIdx.x][i];
+    }
+}
+
+// Dynamic shared memory of a 128 x NT tile: two 64-column panels of A and W
+// (+1 KiB alignment slack, two mbarriers and the TMEM address).
+__host__ __device__ constexpr size_t smem_bytes(int nt) {
+    return 1024 + (size_t)2 * (kTileM + nt) * 128 + 64;
 }
 
 // 2D BF16 tensor map of a row-major [rows x cols] matrix with leading
