@@ -463,7 +463,9 @@ typedef struct rddmc_proposal {
  * stream, mapped back to the world frame (and mirrored back for negative
  * frequencies), placed across the exit face of the inner cube (Doppler rebin
  * or escape tally as the face's row says), and the packet set in flight again.  Clears the queue.
- * Synchronises `stream`. */
+ * Reads the queue's count with one synchronisation of `stream`, then enqueues
+ * the work on `stream` without waiting for it (work queued after it on the
+ * same stream sees its results). */
 int rddmc_propose(const rddmc_grid* grid, const void* d_table, const rddmc_proposal* proposal, uint64_t seed,
                   uint64_t n_packets, void* d_state, void* d_tallies, int n_out, int nA, int nB, int nC,
                   const float* d_wf, const void* d_wb, int batch, void* d_work, uint64_t* n_served, void* stream);

@@ -1074,5 +1074,6 @@ extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rdd
     }
     if (cudaMemsetAsync(pr->d_queue_count, 0, 8, s) != cudaSuccess) return RDDMC_ERR_CUDA;
     if (n_served) *n_served = cnt;
-    return cudaStreamSynchronize(s) == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+    // no final synchronisation: work queued next on `stream` runs after these kernels
+    return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
 }

@@ -222,6 +222,7 @@ class ExitProposal:
         prop = self.proposal(att, qpid, tau_lo, tau_hi)
         problem.reset()
         launches = rounds = served = 0
+        t = None
         for ep in range(max_epochs):
             problem.launch(n_packets, seed, steps_per_launch=steps_per_launch, resume=1 if ep else 0, proposal=prop,
                            time_slice_us=time_slice_us)
@@ -231,8 +232,12 @@ class ExitProposal:
                           self.wb.data_ptr(), batch, att["work"].data_ptr(), problem.stream(), nC=self.nC)
             served += k
             rounds += 1 if k else 0
-            t = problem.read()
-            if t["escaped"] + t["aborted"] >= n_packets:
-                break
+            # the termination test synchronises: every few epochs, and whenever a
+            # round found nothing parked (the end is near or reached)
+            if k == 0 or ep % 8 == 7:
+                t = problem.read()
+                if t["escaped"] + t["aborted"] >= n_packets:
+                    break
+        t = problem.read()
         t["launches"], t["rounds"], t["served"] = launches, rounds, served
         return t
