@@ -466,7 +466,9 @@ def _extras(R, torch, only=None):
                  # a C2 subset run to completion: bounded below by its slowest packet (~3e9 transitions)
                  "c2_complete_1e5": lambda: _complete(R, torch, W.C2, 100_000),
                  "learned_c5_tau1e8": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0,
-                                                                tau0=1.0e8, npk=100_000, ndata=600_000, iters=4000)}
+                                                                tau0=1.0e8, npk=100_000, ndata=600_000, iters=4000),
+                 "learned_c5_tau1e9": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0,
+                                                                tau0=1.0e9, npk=20_000, ndata=300_000, iters=3000)}
         jobs = [(k, f) for k, f in jobs + list(small.items()) if k == only]
         if not jobs:
             raise SystemExit(f"unknown extra {only!r}")
@@ -504,7 +506,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads and the learned-vs-plain comparison")
     ap.add_argument("--extra", default="", help="run only this extra (c3_sphere_static, c3_sphere_v20, "
-                    "c3_sphere_v200, c2_hybrid, c1_complete, c2_complete_1e5, batched_512, learned_vs_plain, learned_small, learned_c5, learned_c5_tau1e8) and print it")
+                    "c3_sphere_v200, c2_hybrid, c1_complete, c2_complete_1e5, batched_512, learned_vs_plain, learned_small, learned_c5, learned_c5_tau1e8, learned_c5_tau1e9) and print it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
