@@ -333,10 +333,14 @@ struct MlpWork {
     __nv_bfloat16 *dZT, *HT, *WT;  // transposed copies for the K-major products of the backward pass
 };
 
+// The transposed copies serve every layer: dZT holds [n_out x B] and [128 x B],
+// WT holds [128 x n_out] and [128 x 128], so both take max(n_out, 128) rows.
 uint64_t mlp_work_bytes(int Bsz, int n_out) {
     const uint64_t bh = (uint64_t)Bsz * kHid;
+    const uint64_t wide = (uint64_t)std::max(n_out, kHid);
     return align256(bh * 2) * 5 + align256(bh * 4) + align256((uint64_t)Bsz * n_out * 4) * 2 +
-           align256((uint64_t)Bsz * n_out * 2) * 2 + align256(bh * 2) + align256((uint64_t)n_out * kHid * 2);
+           align256((uint64_t)Bsz * n_out * 2) + align256((uint64_t)Bsz * wide * 2) + align256(bh * 2) +
+           align256(wide * kHid * 2);
 }
 
 MlpWork mlp_work(void* d_work, int Bsz, int n_out) {
@@ -349,9 +353,9 @@ MlpWork mlp_work(void* d_work, int Bsz, int n_out) {
     w.logits = (float*)p; p += align256((uint64_t)Bsz * n_out * 4);
     w.dlogf = (float*)p; p += align256((uint64_t)Bsz * n_out * 4);
     w.dlogb = (__nv_bfloat16*)p; p += align256((uint64_t)Bsz * n_out * 2);
-    w.dZT = (__nv_bfloat16*)p; p += align256((uint64_t)Bsz * n_out * 2);   // [n_out x B] or [128 x B]
+    w.dZT = (__nv_bfloat16*)p; p += align256((uint64_t)Bsz * std::max(n_out, kHid) * 2);  // [n_out or 128 x B]
     w.HT = (__nv_bfloat16*)p; p += align256(bh * 2);                          // [128 x B] or [16 x B]
-    w.WT = (__nv_bfloat16*)p;                                                 // [128 x n_out]
+    w.WT = (__nv_bfloat16*)p;                                                 // [128 x n_out or 128]
     return w;
 }
 

@@ -123,3 +123,86 @@ def test_tensor_core_forward_matches_fp64(proposal, Bsz):
             h = torch.tensor(np.maximum(h, 0.0), dtype=torch.float32).to(torch.bfloat16).double().numpy()
     err = np.abs(z - h).max() / max(1.0, np.abs(h).max())
     assert err < 2e-3, err
+
+
+def _bf16(x):
+    return torch.tensor(np.asarray(x), dtype=torch.float32).to(torch.bfloat16).double().numpy()
+
+
+def _device_rounded_grads(layers, X, tA, tB, nA, nB, n_out):
+    """Loss and gradients in FP64 with BF16 rounding exactly where the device
+    stores BF16: hidden activations, the logit gradient used in products, and
+    the back-propagated gradients; bias gradients sum the unrounded values."""
+    B = X.shape[0]
+    hs = [X]
+    for l, (W, b) in enumerate(layers[:3]):
+        hs.append(_bf16(np.maximum(hs[-1] @ W.T + b, 0.0)))
+    W4, b4 = layers[3]
+    z = hs[3] @ W4.T + b4
+    g = np.zeros_like(z)
+    loss = 0.0
+    for r in range(B):
+        for lo, hi, t in ((0, nA, tA[r]), (nA, nA + nB, nA + tB[r])):
+            zz = z[r, lo:hi]
+            m = zz.max()
+            lse = m + np.log(np.exp(zz - m).sum())
+            loss += lse - z[r, t]
+            g[r, lo:hi] = np.exp(zz - lse)
+            g[r, t] -= 1.0
+    g /= B
+    grads = [None] * 4
+    gb = _bf16(g)
+    grads[3] = (gb.T @ hs[3], g.sum(axis=0))
+    d = gb
+    for l in (2, 1, 0):
+        W_next = layers[l + 1][0]
+        df = (d @ W_next) * (hs[l + 1] > 0)
+        db = _bf16(df)
+        grads[l] = (db.T @ hs[l], df.sum(axis=0))
+        d = db
+    return loss / B, np.concatenate([np.concatenate([gw.ravel(), gbias]) for gw, gbias in grads])
+
+
+@pytest.mark.parametrize("n_out,nA,nB", [(64, 40, 16), (128, 96, 32), (320, 288, 32)])
+def test_network_gradients_for_narrow_and_wide_heads(n_out, nA, nB):
+    """Loss and gradients of random networks whose output layer is narrower
+    than, equal to or wider than the hidden layers (the backward pass reuses
+    its transposed copies across layers), against an FP64 reference that
+    rounds to BF16 where the device stores BF16; what is left is FP32
+    accumulation and the fast exponential."""
+    B.build()
+    rng = np.random.default_rng(n_out)
+    n_par = R.mlp_param_count(n_out)
+    wf = torch.tensor(rng.normal(0.0, 0.1, n_par).astype(np.float32), device="cuda")
+    wb = torch.empty(n_par, dtype=torch.bfloat16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    R.mlp_to_bf16(n_out, wf.data_ptr(), wb.data_ptr(), s)
+    batch = 192
+    X = torch.tensor(rng.normal(0.0, 1.0, (batch, 16)), dtype=torch.bfloat16, device="cuda")
+    tA = torch.tensor(rng.integers(0, nA, batch), dtype=torch.int32, device="cuda")
+    tB = torch.tensor(rng.integers(0, nB, batch), dtype=torch.int32, device="cuda")
+    work = torch.empty(R.mlp_work_bytes(batch, n_out), dtype=torch.uint8, device="cuda")
+    grad = torch.empty(n_par, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    R.mlp_loss_grad(n_out, nA, nB, wf.data_ptr(), wb.data_ptr(), X.data_ptr(), tA.data_ptr(), tB.data_ptr(), batch,
+                    work.data_ptr(), grad.data_ptr(), loss.data_ptr(), s)
+    R.mlp_status(s)
+    wbf = wb.float().cpu().numpy().astype(np.float64)
+    w64 = wf.cpu().numpy().astype(np.float64)
+    layers, off = [], 0
+    for (o, i) in M.shapes(n_out):
+        W = wbf[off:off + o * i].reshape(o, i)
+        off += o * i
+        layers.append((W, w64[off:off + o]))
+        off += o
+    lo, g_ref = _device_rounded_grads(layers, X.float().cpu().numpy().astype(np.float64), tA.cpu().numpy(),
+                                      tB.cpu().numpy(), nA, nB, n_out)
+    assert float(loss.item()) / batch == pytest.approx(lo, rel=1e-4)
+    g = grad.cpu().numpy().astype(np.float64)
+    off = 0
+    for (o, i) in M.shapes(n_out):
+        for size in (o * i, o):
+            a, b = g[off:off + size], g_ref[off:off + size]
+            assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-7, (n_out, off, np.linalg.norm(a - b),
+                                                                              np.linalg.norm(b))
+            off += size
