@@ -455,6 +455,7 @@ def _extras(R, torch, only=None):
             ("c2_hybrid", lambda: _sliced_rate(R, torch, R.Problem(W.C2, mode=R.MODE_HYBRID), 1_000_000,
                                                W.C2.seed, 4096)),
             ("c1_complete", lambda: _complete(R, torch, W.C1, W.C1.packets)),
+            ("c2_widecore_complete", lambda: _complete(R, torch, W.C2_WIDECORE, W.C2_WIDECORE.packets)),
             ("batched_512", lambda: _batched(R, torch)),
             ("learned_vs_plain", lambda: _learned_vs_plain(R, torch))]
     if only:
@@ -506,7 +507,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads and the learned-vs-plain comparison")
     ap.add_argument("--extra", default="", help="run only this extra (c3_sphere_static, c3_sphere_v20, "
-                    "c3_sphere_v200, c2_hybrid, c1_complete, c2_complete_1e5, batched_512, learned_vs_plain, learned_small, learned_c5, learned_c5_tau1e8, learned_c5_tau1e9) and print it")
+                    "c3_sphere_v200, c2_hybrid, c1_complete, c2_widecore_complete, c2_complete_1e5, batched_512, learned_vs_plain, learned_small, learned_c5, learned_c5_tau1e8, learned_c5_tau1e9) and print it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -39,13 +39,20 @@ class Workload:
     sphere: bool = False      # 3D: medium only in cells whose centre has r < R
     vmax_kms: float = 0.0     # 3D Hubble-like outflow v = vmax * r / R
     atau0_nominal: Optional[float] = None  # the a*tau0 the config is quoted at
+    core_half: float = 0.0    # > 0: one central bin [-core_half, core_half], unit-width wing bins
 
     @property
     def ncell(self) -> int:
         return int(self.n[0] * self.n[1] * self.n[2])
 
     def edges(self) -> np.ndarray:
-        """J+1 uniform bin edges over [x_min, x_max] (float64)."""
+        """J+1 bin edges (float64): uniform over [x_min, x_max], or with
+        core_half > 0 the wide-core grid of wide_core_edges(x_max, core_half)."""
+        if self.core_half > 0.0:
+            e = wide_core_edges(self.x_max, self.core_half)
+            if len(e) != self.J + 1 or e[0] != self.x_min:
+                raise ValueError(f"{self.name}: J / x_min do not match the wide-core grid ({len(e) - 1} bins)")
+            return e
         return np.linspace(self.x_min, self.x_max, self.J + 1, dtype=np.float64)
 
     def cell_centres(self) -> np.ndarray:
@@ -77,11 +84,25 @@ class Workload:
         return dataclasses.replace(self, **kw)
 
 
+def wide_core_edges(x_max: float, core_half: float, dx: float = 1.0) -> np.ndarray:
+    """Frequency edges with the resolution Sec. 5.1 suggests: one central bin
+    [-core_half, core_half] at least 2 x_cw wide (an effective core-skipping
+    scheme) and wing bins dx wide out to the last edge <= x_max."""
+    k = int(np.floor((x_max - core_half) / dx + 1e-9))
+    wing = core_half + dx * np.arange(1, k + 1)
+    return np.concatenate([-wing[::-1], [-core_half, core_half], wing]).astype(np.float64)
+
+
 # k0 R for a tau0 = 1e9 at T = 10 K: a(10 K) = 4.702e-4 * (1e-3)^(-1/2) = 1.48691e-2.
 _TAU0_ATAU1E9_T10 = 6.725395e10
 
 C1 = Workload("slab_tau1e5_64x128", 1, (64, 1, 1), 128, -30.0, 30.0, 1.0e5, 1.0e4, 100_000, 0x5EED0001)
 C2 = Workload("slab_tau1e7_256x512", 1, (256, 1, 1), 512, -60.0, 60.0, 1.0e7, 1.0e4, 10_000_000, 0x5EED0002)
+# C2 on the wide-core grid: central bin +-3.3 (x_cw = 3.255 at 1e4 K), unit wing bins to +-59.3 (113 bins)
+C2_WIDECORE = Workload("slab_tau1e7_256x113_widecore", 1, (256, 1, 1), 113, -59.3, 59.3, 1.0e7, 1.0e4, 10_000_000,
+                       0x5EED0012, core_half=3.3)
+C1_WIDECORE = Workload("slab_tau1e5_64x53_widecore", 1, (64, 1, 1), 53, -29.3, 29.3, 1.0e5, 1.0e4, 100_000,
+                       0x5EED0011, core_half=3.3)
 P1 = Workload("slab_atau1e9_T10_201x101", 1, (201, 1, 1), 101, -2500.0, 2500.0, _TAU0_ATAU1E9_T10, 10.0,
               1_000_000, 0x5EED0011, atau0_nominal=1.0e9)
 P2 = Workload("slab_atau1e9_T10_101x51", 1, (101, 1, 1), 51, -2500.0, 2500.0, _TAU0_ATAU1E9_T10, 10.0,
@@ -105,7 +126,7 @@ SPHERE8_V = SPHERE8.with_(name="sphere_tiny_8c_16b_v20", vmax_kms=20.0, seed=0x5
 SPHERE9_V = Workload("sphere_small_9c_21b_v20", 3, (9, 9, 9), 21, -21.0, 21.0, 3.0e3, 1.0e4, 10_000, 0x5EED0303,
                      sphere=True, vmax_kms=20.0)
 
-ALL = {w.name: w for w in (C1, C2, P1, P2, C3, C3_V20, C3_V200, TINY, SMALL, GREY_LIKE, SPHERE8, SPHERE8_V,
+ALL = {w.name: w for w in (C1, C2, C1_WIDECORE, C2_WIDECORE, P1, P2, C3, C3_V20, C3_V200, TINY, SMALL, GREY_LIKE, SPHERE8, SPHERE8_V,
                            SPHERE9_V)}
 
 

@@ -162,6 +162,35 @@ def test_spectrum_c1_matches_chain():
     assert abs(zs) < 4.0
 
 
+def test_wide_core_grid_walk_is_bit_exact():
+    # non-uniform bins (one wide core bin, unit wing bins) on the tau0 = 1e5 slab
+    w = W.C1_WIDECORE
+    og, ot = _oracle(w)
+    thr, flags = R.Problem(w).rows()
+    d = thr.astype(np.int64) - ot["thr"].astype(np.int64)
+    assert np.abs(d).max() <= 1 and np.array_equal(flags, ot["flags"])
+    # the oracle walks the table the device exported, so one-count differences
+    # cannot make the trajectories part
+    n = 20_000
+    _same_tallies(R.Problem(w).run(n, w.seed), C.walk(og, dict(ot, thr=thr, flags=flags), w.seed, 0, n))
+
+
+def test_c2_wide_core_run_to_completion_matches_chain():
+    # every one of 1e6 packets of the tau0 = 1e7 slab on the wide-core grid walked
+    # to escape (~2e4 transitions each), against the exact chain's spectrum and
+    # mean transition count
+    w = W.C2_WIDECORE
+    og, ot = _oracle(w)
+    ch = A.chain_solve(w, ot)
+    n = 1_000_000
+    gpu = R.Problem(w).run(n, w.seed)
+    assert gpu["escaped"] == n and gpu["aborted"] == 0
+    zmax, frac, pval = A.compare_counts_to_probs(gpu["hist"], ch["hist"], n)
+    assert zmax < 5.0 and frac <= 0.02 and pval > 1e-3, (zmax, frac, pval)
+    zs = (gpu["steps"] / n - ch["steps_mean"]) / np.sqrt(ch["steps_var"] / n)
+    assert abs(zs) < 4.0, zs
+
+
 def test_c2_full_size_sampled_packets_replay_exactly():
     # tau0 = 1e7 slab, 256 x 512, all 1e7 packets, one time slice of 4096
     # transitions as the benchmark launches it; sampled packets are replayed one

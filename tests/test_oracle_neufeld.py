@@ -75,3 +75,19 @@ def test_exact_chain_on_low_opacity_configs_is_far_from_neufeld():
     l1 = A.l1_distance(ch["hist"][1:-1], A.neufeld_bin_mass(w.edges(), C.damping(w.T) * w.tau0))
     assert 0.4 < l1 < 0.7
     assert ch["steps_mean"] == pytest.approx(8.756e5, rel=2e-3)
+
+
+def test_wide_core_grid_keeps_the_analytic_accuracy_at_a_fraction_of_the_transitions():
+    # Sec. 5.1: one central bin at least 2 x_cw wide and unit-width wing bins act
+    # as a core-skipping scheme.  On the tau0 = 1e7 slab the exact chain on that
+    # grid is as close to eq. Neufeld as on the uniform 512-bin grid, while a
+    # packet takes over a thousand times fewer transitions.
+    atau0 = C.damping(W.C2.T) * W.C2.tau0
+    res = {}
+    for w in (W.C2, W.C2_WIDECORE):
+        t = C.Grid(w).table()
+        ch = A.chain_solve(w, t)
+        res[w.name] = (A.l1_distance(ch["hist"][1:-1], A.neufeld_bin_mass(w.edges(), atau0)), ch["steps_mean"])
+    (l1_u, steps_u), (l1_w, steps_w) = res[W.C2.name], res[W.C2_WIDECORE.name]
+    assert l1_w <= 0.08 and abs(l1_w - l1_u) <= 0.005, (l1_w, l1_u)
+    assert steps_u / steps_w > 1.0e3, (steps_u, steps_w)
