@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.integrate as si
+import scipy.linalg as sla
 import scipy.optimize as so
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
@@ -142,12 +143,10 @@ def _neighbour(w, c, axis, side):
     return idx[0] + n[0] * (idx[1] + n[1] * idx[2])
 
 
-def chain_solve(w, table, edges=None):
-    """Exact expectations of the DDMC walk on a quantised table.
-
-    Returns a dict with the expected escape histogram per emitted packet (J+2
-    bins, static cells only), expected escapes per face, escapes per
-    (state, outcome), the mean and variance of the number of transitions."""
+def chain_matrix(w, table):
+    """Transition matrix of the DDMC walk between its states (sparse, S x S;
+    each row sums to one minus the state's escape probability) and the
+    escape probability per (state, outcome), from the quantised thresholds."""
     J, K = w.J, 2 + 2 * w.ndim
     thr, flags = table["thr"], table["flags"]
     S = thr.shape[0]
@@ -182,7 +181,19 @@ def chain_solve(w, table, edges=None):
                     jn = min(max(jn, 0), J - 1)
                     if pj > 0:
                         rows.append(s); cols.append(nb * J + jn); vals.append(p * pj)
-    P = sp.csr_matrix((vals, (rows, cols)), shape=(S, S))
+    return sp.csr_matrix((vals, (rows, cols)), shape=(S, S)), esc
+
+
+def chain_solve(w, table, edges=None):
+    """Exact expectations of the DDMC walk on a quantised table.
+
+    Returns a dict with the expected escape histogram per emitted packet (J+2
+    bins, static cells only), expected escapes per face, escapes per
+    (state, outcome), the mean and variance of the number of transitions."""
+    J, K = w.J, 2 + 2 * w.ndim
+    flags = table["flags"]
+    P, esc = chain_matrix(w, table)
+    S = P.shape[0]
     A = (sp.identity(S, format="csr") - P).tocsc()
     lu = spla.splu(A)
     src_s, src_p = source_states(w, edges)
@@ -203,6 +214,37 @@ def chain_solve(w, table, edges=None):
         hist[1:J + 1] += np.where(moving, 0.0, per_state).sum(axis=0)
     return dict(hist=hist, faces=faces, esc_so=esc_so, visits=v, steps_mean=mean, steps_var=var,
                 escape_total=float(esc_so.sum()))
+
+
+def chain_time(w, table, t_edges, edges=None):
+    """Exact expectations of the time-dependent DDMC walk (Sec. 2.3): the walk
+    is a continuous-time Markov chain whose state s is left at the total
+    leakage rate K_s (per unit path length; c = 1) for the outcomes of the
+    quantised thresholds, so the occupancy is p(t) = p(0) exp(Q t) with
+    Q = diag(K) (P - I).  For time steps [t_edges[n], t_edges[n+1]] returns
+    the occupancy at each step's end (nt x S), the expected path length spent
+    in each state during each step (nt x S), both per emitted packet, and the
+    escape probability per step (nt).  Dense: for small grids."""
+    P, esc = chain_matrix(w, table)
+    S = P.shape[0]
+    K = np.asarray(table["rate"], dtype=np.float64).sum(axis=1)
+    Q = K[:, None] * (P.toarray() - np.eye(S))
+    src_s, src_p = source_states(w, edges)
+    p = np.zeros(S)
+    p[src_s] = src_p
+    occ, path, esc_t = [], [], []
+    for n in range(len(t_edges) - 1):
+        h = float(t_edges[n + 1] - t_edges[n])
+        M = np.zeros((2 * S, 2 * S))
+        M[:S, :S] = Q * h
+        M[:S, S:] = np.eye(S) * h
+        E = sla.expm(M)  # top-left exp(Q h), top-right int_0^h exp(Q u) du
+        pn = p @ E[:S, :S]
+        path.append(p @ E[:S, S:])
+        occ.append(pn)
+        esc_t.append(p.sum() - pn.sum())
+        p = pn
+    return np.array(occ), np.array(path), np.array(esc_t)
 
 
 # --------------------------------------------------------------------------- comparisons

@@ -57,6 +57,8 @@ def lib():
         L.orc_replay_packet.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, d, u64, u64, u64, u64, vp, vp]
         L.orc_scatter_samples.restype = None
         L.orc_scatter_samples.argtypes = [d, d, u64, u64, vp]
+        L.orc_walk_time.restype = ctypes.c_int
+        L.orc_walk_time.argtypes = [vp, vp, vp, vp, vp, vp, d, u64, u64, u64, vp, i32, u64, i32, vp, vp, vp, vp, vp]
         L.orc_fp_samples.restype = None
         L.orc_fp_samples.argtypes = [vp, i32, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp]
         L.orc_upar_table.restype = None
@@ -196,6 +198,36 @@ def replay_packet(grid: Grid, table: dict, seed: int, pid: int, n_trans: int, ma
     d = dict(cell=int(out[0]), bin=int(out[1]), steps=int(out[2]), event_draws=int(out[3]), done=int(out[4]))
     d["tally"] = unpack_tally(tl, grid.J)
     return d
+
+
+def walk_time(grid: Grid, table: dict, seed: int, p0: int, npk: int, t_edges, max_steps: int = (1 << 62),
+              nthreads: int = 0) -> dict:
+    """Time-dependent walk of packets [p0, p0+npk) emitted at t_edges[0]
+    (orc_walk_time): per step n the packets in each state at its end (bins,
+    nt x S), the path length spent in each state (path, nt x S) and the
+    escapes (esc, nt), plus the walk's tallies and transition/dwell counts."""
+    if nthreads <= 0:
+        nthreads = os.cpu_count() or 1
+    te = np.ascontiguousarray(t_edges, dtype=np.float64)
+    nt = len(te) - 1
+    S = grid.ncell * grid.J
+    bins = np.zeros(nt * S, dtype=np.uint64)
+    path = np.zeros(nt * S, dtype=np.float64)
+    esc = np.zeros(nt, dtype=np.uint64)
+    tally = np.zeros(lib().orc_tally_len(grid.J), dtype=np.uint64)
+    stats = np.zeros(3, dtype=np.uint64)
+    thr = np.ascontiguousarray(table["thr"].ravel())
+    rate = np.ascontiguousarray(table["rate"].ravel())
+    rc = lib().orc_walk_time(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
+                             _ptr(table["rebin_thr"]), _ptr(rate), float(grid.w.x0), int(seed), int(p0), int(npk),
+                             _ptr(te), int(nt), int(max_steps), int(nthreads), _ptr(bins), _ptr(path), _ptr(esc),
+                             _ptr(tally), _ptr(stats))
+    if rc != 0:
+        raise RuntimeError(f"orc_walk_time failed: {rc}")
+    out = unpack_tally(tally, grid.J)
+    out.update(bins=bins.reshape(nt, S), path=path.reshape(nt, S), esc=esc, transitions=int(stats[0]),
+               dwells=int(stats[1]), aborted_time=int(stats[2]))
+    return out
 
 
 def walk_slice(grid: Grid, table: dict, seed: int, p0: int, npk: int, n_trans: int, nthreads: int = 0) -> dict:

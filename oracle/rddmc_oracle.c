@@ -139,13 +139,14 @@ static uint32_t orc_word(uint64_t seed, uint64_t p, int which, uint64_t n) {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint64_t b = n >> 2;
     uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), (uint32_t)p,
-                       (uint32_t)(p >> 32) | (which ? 0x80000000u : 0u)};
+                       (uint32_t)(p >> 32) | (which == 1 ? 0x80000000u : (which == 2 ? 0x40000000u : 0u))};
     uint32_t out[4];
     orc_philox4x32_10(ctr, key, out);
     return out[n & 3];
 }
 #define ORC_TRANS 0
 #define ORC_EVENT 1
+#define ORC_TIME 2   /* dwell draws of the time-dependent walk (packet ids < 2^62) */
 
 static double orc_unif(uint32_t w) { return ((double)w + 0.5) / ORC_TWO32; }
 
@@ -916,6 +917,162 @@ int orc_walk_ddmc(const orc_grid* g, const uint32_t* thr, const uint32_t* flags,
                   uint64_t p0, uint64_t np, uint64_t max_steps, int literal, int nthreads, uint64_t* tally) {
     return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, rate, k, x0, seed, p0, np, max_steps, literal,
                         UINT64_MAX, nthreads, tally);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Time-dependent walk (Sec. 2.3: causality within a time step; eq.          */
+/* E_estimator: bin and path estimates of the energy density)                */
+/* ------------------------------------------------------------------------- */
+
+typedef struct orc_time_args {
+    orc_walk_args w;
+    const double* t_edges;
+    int nt;
+    uint64_t* bins;   /* per thread: nt x S */
+    double* path;     /* per thread: nt x S */
+    uint64_t* esc;    /* per thread: nt */
+    uint64_t steps, dwells, aborted;
+} orc_time_args;
+
+/* One DDMC transition of packet P in its current state (categorical draw on
+ * the transition stream, action of the outcome).  Returns 1 if the packet
+ * escaped, -1 if it met an MC state, 0 otherwise. */
+static int orc_time_transition(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t* t) {
+    const orc_grid* g = A->g;
+    const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim;
+    int64_t c = orc_cell_of(g, P->idx);
+    const int64_t s = c * J + P->j;
+    uint32_t w = orc_word(A->seed, pk, ORC_TRANS, P->steps);
+    int o = 0;
+    while (o < K - 1 && w >= A->thr[s * (K - 1) + o]) ++o;
+    P->steps++;
+    t[ORC_T_STEPS]++;
+    unsigned act = (A->flags[s] >> (2 * o)) & 3u;
+    if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, P->j, o, pk, &P->e, t); return 1; }
+    if (act == ORC_ACT_TO_MC) return -1;
+    if (o < 2) { P->j += o ? 1 : -1; return 0; }
+    int face = o - 2, ax = face / 2, side = (face & 1) ? 1 : -1;
+    if (act == ORC_ACT_REBIN) {
+        uint32_t w1 = orc_word(A->seed, pk, ORC_EVENT, P->e++);
+        int jn = P->j + A->rebin_m[c * nf + face] + (w1 >= A->rebin_thr[c * nf + face] ? 1 : 0);
+        if (jn < 0) { jn = 0; t[ORC_T_CLAMPS]++; }
+        if (jn > J - 1) { jn = J - 1; t[ORC_T_CLAMPS]++; }
+        P->j = jn;
+    }
+    P->idx[ax] += side;
+    return 0;
+}
+
+static void* orc_time_thread(void* vp) {
+    orc_time_args* T = (orc_time_args*)vp;
+    orc_walk_args* A = &T->w;
+    const orc_grid* g = A->g;
+    const int J = g->J, K = orc_nout(g);
+    const int64_t S = (int64_t)orc_ncell(g) * J;
+    for (uint64_t pk = A->p0; pk < A->p1; ++pk) {
+        orc_pstate P;
+        orc_start(A, pk, &P, A->tally);
+        double tau = T->t_edges[0];
+        uint64_t d = 0;  /* dwell draws */
+        int done = 0;
+        for (int n = 0; n < T->nt && !done; ++n) {
+            const double t_end = T->t_edges[n + 1];
+            for (;;) {
+                if (P.steps >= A->max_steps) { T->aborted++; done = 2; break; }
+                const int64_t s = orc_cell_of(g, P.idx) * J + P.j;
+                double ksum = 0.0;
+                for (int q = 0; q < K; ++q) ksum += A->rate[s * K + q];
+                /* eq. l_min_2: the smallest of the exponential leakage lengths is Exp(sum k) */
+                const double dl = -log(orc_unif(orc_word(A->seed, pk, ORC_TIME, d++))) / ksum;
+                T->dwells++;
+                if (tau + dl > t_end) {          /* causality: stay in the state until t_end */
+                    T->path[(size_t)n * S + s] += t_end - tau;
+                    tau = t_end;
+                    T->bins[(size_t)n * S + s]++;
+                    break;
+                }
+                T->path[(size_t)n * S + s] += dl;
+                tau += dl;
+                int r = orc_time_transition(A, pk, &P, A->tally);
+                if (r == 1) { T->esc[n]++; done = 1; break; }
+                if (r == -1) { A->status = -2; done = 3; break; }
+            }
+        }
+        A->tally[ORC_T_EVENT_DRAWS] += P.e;
+    }
+    return NULL;
+}
+
+/*
+ * Time-dependent DDMC walk of packets [p0, p0+np), all emitted at the source at
+ * t_edges[0] (a flash), through the steps [t_edges[n], t_edges[n+1]], n < nt.
+ * Path lengths and times share one unit (c = 1), the unit of the grid's R.
+ * In state s a packet draws a dwell path dl = -ln(xi) / K_s, K_s the sum of the
+ * state's leakage coefficients (rate[s*K..]): by eq. l_min_1/2 the smallest of
+ * the competing exponential lengths is Exp(K_s), independent of the process
+ * that wins, which the categorical draw picks.  xi is word d of the packet's
+ * time stream (lane d&3 of Philox4x32-10(ctr = (d>>2, p_lo, p_hi | 2^30))).
+ * If the dwell would pass the step's end, the packet stays in its state until
+ * t_end without leaking (Sec. 2.3) and draws a new dwell in the next step (the
+ * exponential is memoryless).  Outputs, accumulated (+=):
+ *   bins[n*S + s]: packets in state s at t_edges[n+1] (the bin estimate)
+ *   path[n*S + s]: path length spent in state s during step n (the path estimate)
+ *   esc[n]: packets escaped during step n;  tally: the walk's counters
+ * with S = ncell * J.  DDMC tables only.  stats[3] = {transitions, dwell draws,
+ * aborted}.  Returns 0, -1 on bad input, -2 if a packet met an MC state.
+ */
+int orc_walk_time(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
+                  const uint32_t* rebin_thr, const double* rate, double x0, uint64_t seed, uint64_t p0, uint64_t np,
+                  const double* t_edges, int nt, uint64_t max_steps, int nthreads, uint64_t* bins, double* path,
+                  uint64_t* esc, uint64_t* tally, uint64_t* stats) {
+    if (!g || !thr || !flags || !rate || !t_edges || nt < 1 || !bins || !path || !esc || !tally || !stats) return -1;
+    if (p0 + np > ((uint64_t)1 << 62)) return -1;
+    for (int n = 0; n < nt; ++n)
+        if (!(t_edges[n + 1] > t_edges[n])) return -1;
+    orc_source src;
+    if (orc_make_source(g, x0, &src)) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if ((uint64_t)nthreads > np) nthreads = np ? (int)np : 1;
+    const int L = orc_tally_len(g->J);
+    const size_t S = (size_t)orc_ncell(g) * g->J;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
+    orc_time_args* args = (orc_time_args*)calloc(nthreads, sizeof(orc_time_args));
+    uint64_t* tl = (uint64_t*)calloc((size_t)nthreads * L, sizeof(uint64_t));
+    uint64_t* tb = (uint64_t*)calloc((size_t)nthreads * nt * S, sizeof(uint64_t));
+    double* tp = (double*)calloc((size_t)nthreads * nt * S, sizeof(double));
+    uint64_t* te = (uint64_t*)calloc((size_t)nthreads * nt, sizeof(uint64_t));
+    for (int i = 0; i < nthreads; ++i) {
+        orc_time_args* T = &args[i];
+        orc_walk_args* A = &T->w;
+        A->g = g; A->thr = thr; A->flags = flags; A->rebin_m = rebin_m; A->rebin_thr = rebin_thr;
+        A->rate = rate; A->src = &src; A->seed = seed; A->max_steps = max_steps;
+        A->p0 = p0 + np * (uint64_t)i / nthreads;
+        A->p1 = p0 + np * (uint64_t)(i + 1) / nthreads;
+        A->tally = tl + (size_t)i * L;
+        T->t_edges = t_edges; T->nt = nt;
+        T->bins = tb + (size_t)i * nt * S;
+        T->path = tp + (size_t)i * nt * S;
+        T->esc = te + (size_t)i * nt;
+        pthread_create(&th[i], NULL, orc_time_thread, T);
+    }
+    int status = 0;
+    memset(tally, 0, sizeof(uint64_t) * L);
+    stats[0] = stats[1] = stats[2] = 0;
+    for (int i = 0; i < nthreads; ++i) {
+        pthread_join(th[i], NULL);
+        for (int q = 0; q < L; ++q) tally[q] += tl[(size_t)i * L + q];
+        for (size_t q = 0; q < (size_t)nt * S; ++q) {
+            bins[q] += tb[(size_t)i * nt * S + q];
+            path[q] += tp[(size_t)i * nt * S + q];
+        }
+        for (int n = 0; n < nt; ++n) esc[n] += te[(size_t)i * nt + n];
+        stats[0] += args[i].w.tally[ORC_T_STEPS];
+        stats[1] += args[i].dwells;
+        stats[2] += args[i].aborted;
+        if (args[i].w.status) status = args[i].w.status;
+    }
+    free(th); free(args); free(tl); free(tb); free(tp); free(te);
+    return status;
 }
 
 /* Start packets [p0, p0+np) at the source and advance each by at most

@@ -1,0 +1,103 @@
+"""Pins of the oracle's time-dependent walk (Sec. 2.3: causality within a time
+step; eq. E_estimator: bin and path estimates of the energy density).
+
+The walk with exponential dwells is a continuous-time Markov chain: state s is
+left at rate K_s (the sum of its leakage coefficients, per unit path length,
+c = 1) for the outcomes of the quantised thresholds.  Its exact occupancy
+p(t) = p(0) exp(Q t) and the integral of p over a step give the expected bin
+and path estimates; the grey medium reduces to Fick diffusion with
+D = 1 / (3 k), whose point-source solution is a Gaussian (the paper's first
+time-dependent test)."""
+import numpy as np
+import pytest
+from scipy.special import erf
+from scipy.stats import chi2
+
+from oracle import analytic as A
+from oracle import coracle as C
+from paper_1709_10187_gb300 import workloads as W
+
+GREY = W.Workload("grey_slab_101x1", 1, (101, 1, 1), 1, -5.0, 5.0, 1.0e3, 1.0e4, 100_000, 0x5EED0901)
+
+
+def _check_against_chain(w, t_edges, n, seed):
+    g = C.Grid(w)
+    t = g.table()
+    r = C.walk_time(g, t, seed, 0, n, t_edges)
+    occ, path, esc = A.chain_time(w, t, t_edges)
+    assert r["emitted"] == n and r["aborted"] == 0
+    for k in range(len(t_edges) - 1):
+        e = occ[k] * n
+        o = r["bins"][k].astype(np.float64)
+        sel = e >= 20.0
+        z = (o[sel] - e[sel]) / np.sqrt(e[sel] * (1.0 - occ[k][sel]))
+        # none beyond 5 sigma, at most max(1, 2 %) beyond 3 sigma, chi^2 p > 1e-3
+        m = int(sel.sum())
+        assert np.abs(z).max() < 5.0 and int((np.abs(z) > 3.0).sum()) <= max(1, int(np.ceil(0.02 * m))), (k, z)
+        assert chi2.sf(float((z * z).sum()), m) > 1e-3, (k, float((z * z).sum()), m)
+        assert np.all(o[e < 1e-9] == 0)
+        # escapes during the step: binomial around the chain's probability
+        pe = esc[k]
+        ze = (r["esc"][k] - n * pe) / np.sqrt(max(n * pe * (1 - pe), 1e-12))
+        assert abs(ze) < 5.0 or abs(r["esc"][k] - n * pe) < 3.0, (k, r["esc"][k], n * pe)
+        # path per state: each packet contributes X in [0, dt], so Var(sum) <= dt * E(sum)
+        dt = t_edges[k + 1] - t_edges[k]
+        ep = path[k] * n
+        assert np.all(np.abs(r["path"][k] - ep) <= 5.0 * np.sqrt(dt * ep) + 1e-9 * dt), k
+    return r
+
+
+@pytest.mark.parametrize("w,t_edges", [
+    (W.TINY, [0.0, 0.1, 0.3, 1.0, 3.0, 10.0]),
+    (W.SMALL, [0.0, 0.3, 1.0, 3.0, 10.0, 30.0]),
+], ids=lambda v: getattr(v, "name", "edges"))
+def test_time_walk_follows_the_continuous_time_chain(w, t_edges):
+    r = _check_against_chain(w, np.array(t_edges), 40_000, w.seed)
+    # every packet is in some state at each step's end or has escaped by then
+    alive = 40_000 - np.cumsum(r["esc"])
+    assert np.array_equal(r["bins"].sum(axis=1), alive)
+
+
+def test_causality_stops_packets_at_step_ends():
+    # splitting a step in two changes no packet's fate: the exponential dwell
+    # is memoryless, so the bin counts at the common step ends agree in law;
+    # the path sums over the split step equal the unsplit one's in expectation
+    w = W.TINY
+    g = C.Grid(w)
+    t = g.table()
+    n = 40_000
+    a = C.walk_time(g, t, w.seed, 0, n, [0.0, 1.0, 3.0])
+    b = C.walk_time(g, t, w.seed + 1, 0, n, [0.0, 0.5, 1.0, 3.0])
+    for (ka, kb) in ((0, 1), (1, 2)):
+        zmax, frac = A.compare_two_samples(a["bins"][ka], n, b["bins"][kb], n)
+        assert zmax < 5.0 and frac <= 0.05, (zmax, frac)
+    pa = a["path"][0].sum()
+    pb = b["path"][0].sum() + b["path"][1].sum()
+    assert abs(pa - pb) <= 0.01 * pa
+
+
+def test_grey_medium_diffuses_like_the_fick_gaussian():
+    # one grey bin, 101 thick cells: E(z, t) = exp(-z^2 / 4Dt) / sqrt(4 pi D t),
+    # D = 1 / (3 k), while the front stays well inside the slab
+    w = GREY
+    g = C.Grid(w)
+    t = g.table()
+    k = float(t["k"][w.n[0] // 2])
+    D = 1.0 / (3.0 * k)
+    sig = np.array([0.10, 0.15, 0.20])
+    t_edges = np.concatenate([[0.0], sig ** 2 / (2.0 * D)])
+    n = w.packets
+    r = C.walk_time(g, t, w.seed, 0, n, t_edges)
+    occ, _, _ = A.chain_time(w, t, t_edges)
+    e = np.linspace(-w.R, w.R, w.n[0] + 1)
+    for q in range(len(sig)):
+        s2 = 2.0 * D * t_edges[q + 1]
+        gauss = 0.5 * np.diff(erf(e / np.sqrt(2.0 * s2)))
+        l1_chain = A.l1_distance(occ[q], gauss)
+        l1_mc = A.l1_distance(r["bins"][q].astype(np.float64), gauss)
+        # the discrete chain is Fick diffusion on cells: a lattice walk differs
+        # from the cell-integrated Gaussian at second order in dz / sigma; the
+        # MC adds its noise
+        dz = 2.0 * w.R / w.n[0]
+        assert l1_chain <= 0.2 * (dz / sig[q]) ** 2 + 1e-3, (q, l1_chain)
+        assert l1_mc <= l1_chain + 4.0 * np.sqrt(2.0 * w.n[0] / (np.pi * n)), (q, l1_mc)
