@@ -317,6 +317,68 @@ int rddmc_read_packet_states(const rddmc_grid* grid, const void* d_state, uint64
                              uint64_t count, uint32_t* cell, uint32_t* bin, uint64_t* steps, uint64_t* event_draws,
                              uint8_t* status, void* stream);
 
+/* ------------------------------------------------------ time-dependent walk
+ * Sec. 2.3 (causality within a time step) and eq. E_estimator (the 'bin' and
+ * 'path' estimates of the spectral energy density per cell, bin and step).
+ * Every packet is emitted at the source at the start of the first step (a
+ * flash) and advanced step by step, one launch per step.  In state s a packet
+ * draws a dwell path dl = -ln(xi) / K_s, K_s the sum of the state's leakage
+ * coefficients (eq. l_min_1/2: the smallest of the competing exponential
+ * lengths is Exp(K_s), whichever process wins), then one transition of the
+ * DDMC walk.  A dwell that passes the end of the step leaves the packet in its
+ * state until then without leaking; the next step draws a fresh dwell.
+ * Lengths and times share one unit, that of the grid's R (c = 1).  DDMC-mode
+ * tables only.
+ *
+ * Streams: transitions and event draws as in the persistent walk; dwell word d
+ * of packet p is lane d&3 of Philox4x32-10(key = seed, ctr = (d>>2 low,
+ * d>>2 high, p low, p high | 2^30)), xi = (word + 1/2) 2^-32.  The dwell is
+ * computed in FP32 and rounded to ticks of 2^-31 of the step (the packet
+ * clock and the path tallies are integers).
+ */
+typedef struct rddmc_time_step {
+    uint64_t seed;
+    uint64_t n_packets;     /* 1 .. 2^62 - 1 */
+    uint64_t max_steps;     /* transitions per packet before it is aborted; 0 = 2^62 */
+    double t_begin, t_end;  /* the step [t_n, t_{n+1}], t_end > t_begin */
+    int32_t start;          /* 1: every packet starts at the source at t_begin (the first step);
+                               0: packets resume from the state buffer */
+    int32_t chunk;          /* transitions a thread runs between refills: multiple of 4, 0 = 256 */
+    int32_t threads_per_cta; /* multiple of 32, at most 256; 0 = 256 */
+    int32_t ctas_per_sm;    /* 0 = occupancy limit */
+} rddmc_time_step;
+
+/* Bytes of the state buffer of a time-dependent run of n_packets (the
+ * persistent walk's state plus a dwell counter per packet); 0 if n_packets is
+ * out of range. */
+uint64_t rddmc_time_state_bytes(uint64_t n_packets);
+
+/*
+ * rddmc_time_step_launch -- enqueue one time step on `stream` (a memset and
+ * one kernel; no synchronisation).
+ *   d_state    device, 256-byte aligned, state_bytes >= rddmc_time_state_bytes:
+ *              per-packet state, kept between steps (caller-owned; step
+ *              `start` = 1 needs no initialisation).
+ *   d_tallies  device, the walk's tally buffer (rddmc_sizes.tally_bytes),
+ *              accumulated: emitted, escaped, aborted, transitions, event
+ *              draws, escape faces and histograms, as rddmc_read_tallies reads.
+ *   d_bins     device, ncell * J uint64, accumulated (+=): packets in state
+ *              s = cell * J + bin at t_end (the bin estimate).
+ *   d_path     device, ncell * J uint64, accumulated (+=): path length spent
+ *              in state s during the step, in ticks, 2^31 ticks = t_end -
+ *              t_begin (the path estimate).
+ *   d_counts   device, 4 uint64, accumulated: packets escaped during the step,
+ *              dwell draws, transitions, packets in a state at t_end.
+ * Errors: RDDMC_ERR_ARG (null or misaligned pointer, a field out of range),
+ * RDDMC_ERR_TABLE (table not precomputed), RDDMC_ERR_UNSUPPORTED (hybrid-mode
+ * table, or ncell * J >= 2^32), RDDMC_ERR_SIZE (a buffer too small),
+ * RDDMC_ERR_CUDA.  A packet that meets an MC hand-off is aborted and sets the
+ * unsupported-event status bit of the tallies.
+ */
+int rddmc_time_step_launch(const rddmc_grid* grid, const void* d_table, const rddmc_time_step* step, void* d_state,
+                           size_t state_bytes, void* d_tallies, size_t tally_bytes, uint64_t* d_bins,
+                           uint64_t* d_path, uint64_t* d_counts, void* stream);
+
 /* ----------------------------------------------------------------- batches
  * Many independent grids ("instances", each built and precomputed as above,
  * DDMC mode, any mix of slabs and 3D grids) walked by one persistent launch.

@@ -5,7 +5,8 @@
 //   eq. x-leakage and eq. z-leakage, the boundary / thin-neighbour form
 //   2/(3 dz (k dz + 2 lambda)), probabilities p_X = k_X / sum k accumulated in
 //   outcome order, 32-bit thresholds round-half-even(C 2^32) saturated at
-//   2^32 - 1, and the flag word (2-bit action per outcome, moving, thin).
+//   2^32 - 1, the flag word (2-bit action per outcome, moving, thin) and the
+//   mean dwell path 1 / sum_X k_X of the state.
 // FP64 throughout: 1 - p of thick states and far-wing bin means (dcalH ~ a dx /
 // (sqrt(pi) x^2) ~ 1e-8 against calH ~ 0.886) are below FP32 resolution.  This
 // file is compiled without fused multiply-adds so every product and sum is
@@ -35,7 +36,7 @@ template <int NDIM>
 __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ cdesc,
                             const double* __restrict__ edges, const double* __restrict__ phi,
                             uint32_t* __restrict__ rows, uint2* __restrict__ fast, float* __restrict__ tau_row,
-                            int64_t nrow) {
+                            float* __restrict__ rk, int64_t nrow) {
     constexpr int K = 2 + 2 * NDIM;
     constexpr int W = NDIM == 1 ? 4 : 8;  // words per row, the last holding the flags
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -103,6 +104,7 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
     // bytes carry everything a frequency move needs
     fast[r] = make_uint2(out[0], (fl & FLAG_FASTX) ? out[1] : 0u);
     tau_row[r] = (float)(k * dzmin);
+    rk[r] = (float)(1.0 / tot);  // mean dwell path 1 / K_s of the state (time-dependent walk)
     if (NDIM == 1) {
         reinterpret_cast<uint4*>(rows)[r] = make_uint4(out[0], out[1], out[2], fl);
     } else {
@@ -165,10 +167,11 @@ cudaError_t launch_precompute(const rddmc_grid& g, void* d_table, cudaStream_t s
     uint32_t* rows = (uint32_t*)(base + g.off_rows);
     uint2* fast = (uint2*)(base + g.off_fast);
     float* tau_row = (float*)(base + g.off_tau);
+    float* rk = (float*)(base + g.off_rk);
     if (g.ndim == 1)
-        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, nrow);
+        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, nrow);
     else
-        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, nrow);
+        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, nrow);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the u_par envelope table serves only the continuous MC of the hybrid scheme
     if (g.params.mode == RDDMC_MODE_HYBRID)

@@ -3,7 +3,8 @@
 // Device table buffer (caller-owned, filled by rddmc_precompute_leakage):
 //   [TableHeader | cell_class u32[ncell] | ClassDesc[n_class] | Rebin[n_class*nfaces]
 //    | cell velocity f64[3*ncell] (moving media only) | edges f64[J+1] | phi f64[J] | rows
-//    | fast heads uint2[n_class*J] | tau f32[n_class*J] | u_par split points f32x2[kUparN]]
+//    | fast heads uint2[n_class*J] | tau f32[n_class*J] | u_par split points f32x2[kUparN]
+//    | 1/K_s f32[n_class*J]]
 // every region 256-byte aligned.  Rows are n_class blocks of J rows; a row is
 // 16 bytes in a slab {thr0, thr1, thr2, flags} and 32 bytes in 3D
 // {thr0, thr1, thr2, flags, thr3, thr4, thr5, thr6}: the first 16 bytes always

@@ -1,0 +1,154 @@
+// walk_common.cuh -- what the DDMC walk kernels share: their parameter block,
+// Philox4x32-10 with precomputed round keys, shared-memory tallies and the
+// escape geometry of a packet that leaves the grid.
+#pragma once
+#include <cstdint>
+
+#include "grid.h"
+
+namespace rddmc {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kSmemHistMax = 8192;  // histogram entries kept in shared memory
+
+struct WalkParams {
+    const uint4* rows;
+    const uint2* fast;
+    const float* tau_row;     // tau_ij = k_ij dz per row (hybrid conversions)
+    const float2* upar;       // u_par envelope split points
+    const ClassDesc* cdesc;
+    const uint32_t* cell_class;
+    const Rebin* rebin;
+    const double* cell_v;     // km/s, 3 per cell (moving media)
+    const double* edges;
+    unsigned long long* cursor;
+    uint32_t* st_cell;
+    uint32_t* st_bin;
+    unsigned long long* st_t;
+    unsigned long long* st_e;
+    uint8_t* st_status;
+    unsigned long long* tally;
+    unsigned long long n_packets, max_steps, slice, mc_cap;
+    unsigned long long time_slice_ns;  // wall-time slice of the launch (0 = none)
+    uint32_t k0, k1;
+    uint32_t rk0[10], rk1[10];  // Philox round keys k + r * (Weyl constant)
+    int J, n_rows, n_class, ncell, chunk;
+    int n0, n01;
+    double R, dz[3], vth;
+    int resume, save_state, hist_in_smem, moving, hybrid;
+    int n[3];
+    float a, lambda;
+    int src_ncand[3], src_cand[3][2], src_nbin, src_bin[2];
+    // learned exit proposal (3D DDMC): bricks of prop_b^3 cells, brick
+    // coordinate (i + prop_sh) / prop_b of cell index i on every axis; the
+    // served region of a brick is its inner cube of side prop_r = prop_b -
+    // 2 prop_m
+    int prop_b, prop_sh, prop_nbx, prop_nby, prop_m, prop_r;
+    const float* prop_lk;
+    const float* prop_lp;
+    float prop_llo, prop_lhi;
+    unsigned long long* prop_qcount;
+    unsigned long long* prop_qpid;
+};
+
+// Philox4x32-10 with precomputed round keys (held in the kernel's parameter bank).
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const WalkParams& P) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ P.rk0[r], lo1, hi0 ^ c.w ^ P.rk1[r], lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned word_of(const uint4& r, unsigned q) {
+    return q == 0 ? r.x : (q == 1 ? r.y : (q == 2 ? r.z : r.w));
+}
+
+// Shared-memory tally update aggregated over the lanes that hit the same index.
+__device__ __forceinline__ void smem_tally(unsigned long long* s, unsigned idx) {
+    const unsigned active = __activemask();
+    const unsigned peers = __match_any_sync(active, idx);
+    const int leader = __ffs(peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(&s[idx], (unsigned long long)__popc(peers));
+}
+
+struct EscapeBins {
+    int hist;   // escape-frequency bin (0 below the grid, J+1 above)
+    int sb;     // impact-parameter bin, -1 if not tallied
+};
+
+// Escape through `face` of `cell` at `bin`.  A static slab cell tallies its bin.
+// Otherwise (3D, or a moving slab cell): a point on the face (two event draws
+// for the tangential axes), an isotropic outward direction (mu uniform on
+// (0,1], azimuth uniform), x uniform in the bin, all FP64;
+// x_obs = x + n.(v/v_th) and, in 3D, the impact parameter b = |r x n|.
+template <int NDIM>
+__device__ __noinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cell, unsigned bin, unsigned face,
+                                               unsigned long long pid, unsigned long long e, bool moving) {
+    EscapeBins out;
+    out.sb = -1;
+    if (NDIM == 1 && !moving) { out.hist = (int)bin + 1; return out; }
+    const int ax = (int)(face >> 1), side = (face & 1u) ? 1 : -1;
+    const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+    int idx[3];
+    idx[0] = (int)(cell % (unsigned)P.n0);
+    idx[1] = NDIM == 3 ? (int)((cell / (unsigned)P.n0) % (unsigned)(P.n01 / P.n0)) : 0;
+    idx[2] = NDIM == 3 ? (int)(cell / (unsigned)P.n01) : 0;
+    const double inv = 1.0 / 4294967296.0;
+    double r[3];
+    r[ax] = -P.R + (double)(idx[ax] + (side > 0 ? 1 : 0)) * P.dz[ax];
+    const double p1 = ((double)event_word(pid, e, P.k0, P.k1) + 0.5) * inv;
+    const double p2 = ((double)event_word(pid, e + 1, P.k0, P.k1) + 0.5) * inv;
+    r[t1] = (t1 < NDIM) ? -P.R + ((double)idx[t1] + p1) * P.dz[t1] : 0.0;
+    r[t2] = (t2 < NDIM) ? -P.R + ((double)idx[t2] + p2) * P.dz[t2] : 0.0;
+    const double mu = 1.0 - ((double)event_word(pid, e + 2, P.k0, P.k1) + 0.5) * inv;
+    const double ph = 2.0 * 3.14159265358979323846 * (((double)event_word(pid, e + 3, P.k0, P.k1) + 0.5) * inv);
+    const double xu = ((double)event_word(pid, e + 4, P.k0, P.k1) + 0.5) * inv;
+    const double x = P.edges[bin] + xu * (P.edges[bin + 1] - P.edges[bin]);
+    const double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    double n[3];
+    n[ax] = (double)side * mu;
+    n[t1] = st * cos(ph);
+    n[t2] = st * sin(ph);
+    double nu = 0.0;
+    if (moving) {
+        const double* v = P.cell_v + 3ull * cell;
+        nu = n[0] * (v[0] / P.vth) + n[1] * (v[1] / P.vth) + n[2] * (v[2] / P.vth);
+    }
+    const double xo = x + nu;
+    if (xo < P.edges[0]) {
+        out.hist = 0;
+    } else if (xo >= P.edges[P.J]) {
+        out.hist = P.J + 1;
+    } else {
+        int lo = 0, hi = P.J;  // edges[lo] <= xo < edges[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (xo >= P.edges[mid]) lo = mid; else hi = mid;
+        }
+        out.hist = lo + 1;
+    }
+    if (NDIM == 3) {
+        const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        const double rn = r[0] * n[0] + r[1] * n[1] + r[2] * n[2];
+        const double b = sqrt(fmax(0.0, rr - rn * rn)) / P.R;
+        int k = (int)(b / kSbMax * kNsb);
+        out.sb = k > kNsb - 1 ? kNsb - 1 : k;
+    }
+    return out;
+}
+
+// Parameter block of a walk launch (tables, state arrays, stream keys, source).
+void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P);
+
+}  // namespace rddmc

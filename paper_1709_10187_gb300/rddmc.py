@@ -34,7 +34,10 @@ EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc
             "rddmc_batch_launch", "rddmc_batch_read_tallies", "rddmc_batch_graph_create", "rddmc_batch_graph_launch",
             "rddmc_batch_graph_destroy", "rddmc_batch_autotune", "rddmc_cell_tau", "rddmc_fp_generate",
             "rddmc_mlp_param_count", "rddmc_mlp_work_bytes", "rddmc_mlp_to_bf16", "rddmc_mlp_forward",
-            "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_mlp_status", "rddmc_propose", "rddmc_status_string", "rddmc_version"]
+            "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_mlp_status", "rddmc_propose", "rddmc_time_state_bytes",
+            "rddmc_time_step_launch", "rddmc_status_string", "rddmc_version"]
+
+TIME_TICKS = 1 << 31  # ticks per time step in the path tallies of rddmc_time_step_launch
 
 
 class GridDesc(ctypes.Structure):
@@ -81,6 +84,12 @@ class Proposal(ctypes.Structure):
                 ("d_lp", ctypes.c_void_p), ("d_xc", ctypes.c_void_p), ("log_tau_lo", ctypes.c_double),
                 ("log_tau_hi", ctypes.c_double), ("d_queue_count", ctypes.c_void_p), ("d_queue_pid", ctypes.c_void_p),
                 ("n_bricks", ctypes.c_int32), ("margin", ctypes.c_int32)]
+
+
+class TimeStep(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_packets", ctypes.c_uint64), ("max_steps", ctypes.c_uint64),
+                ("t_begin", ctypes.c_double), ("t_end", ctypes.c_double), ("start", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class RDDMCError(RuntimeError):
@@ -139,6 +148,8 @@ def lib():
         L.rddmc_batch_graph_destroy.restype = None
         L.rddmc_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp, sz, vp, ctypes.POINTER(RunOpts),
                                            ctypes.POINTER(ctypes.c_double)]
+        L.rddmc_time_state_bytes.argtypes = [u64]
+        L.rddmc_time_step_launch.argtypes = [vp, vp, ctypes.POINTER(TimeStep), vp, sz, vp, sz, vp, vp, vp, vp]
         L.rddmc_status_string.argtypes = [i32]
         L.rddmc_status_string.restype = ctypes.c_char_p
         L.rddmc_version.argtypes = []
@@ -148,6 +159,7 @@ def lib():
                 getattr(L, name).restype = ctypes.c_int
         L.rddmc_mlp_param_count.restype = ctypes.c_uint64
         L.rddmc_mlp_work_bytes.restype = ctypes.c_uint64
+        L.rddmc_time_state_bytes.restype = ctypes.c_uint64
         _LIB = L
     return _LIB
 
@@ -221,6 +233,20 @@ def launch_packets_noalloc(grid, d_table: int, opts: RunOpts, d_tallies: int, ta
     _check("rddmc_launch_packets_noalloc", lib().rddmc_launch_packets_noalloc(
         ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(opts), ctypes.c_void_p(d_tallies),
         int(tally_bytes), ctypes.c_void_p(stream)))
+
+
+def time_state_bytes(n_packets: int) -> int:
+    """rddmc_time_state_bytes."""
+    return int(lib().rddmc_time_state_bytes(int(n_packets)))
+
+
+def time_step_launch(grid, d_table: int, step: TimeStep, d_state: int, state_bytes: int, d_tallies: int,
+                     tally_bytes: int, d_bins: int, d_path: int, d_counts: int, stream: int = 0):
+    """rddmc_time_step_launch (enqueues one time step; no synchronisation)."""
+    _check("rddmc_time_step_launch", lib().rddmc_time_step_launch(
+        ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(step), ctypes.c_void_p(d_state),
+        int(state_bytes), ctypes.c_void_p(d_tallies), int(tally_bytes), ctypes.c_void_p(d_bins),
+        ctypes.c_void_p(d_path), ctypes.c_void_p(d_counts), ctypes.c_void_p(stream)))
 
 
 def scatter_samples(grid, d_table: int, x_in: float, seed: int, n: int, d_out: int, stream: int = 0):
@@ -324,6 +350,38 @@ class Problem:
         self.reset()
         self.launch(n_packets, seed, **kw)
         return self.read()
+
+    def time_run(self, n_packets: int, seed: int, t_edges, max_steps: int = 0, chunk: int = 0,
+                 threads_per_cta: int = 0, ctas_per_sm: int = 0) -> dict:
+        """A flash of n_packets at the source at t_edges[0], advanced through the
+        steps [t_edges[n], t_edges[n+1]], one launch per step.  Returns per step
+        n: bins[n, s] (packets in state s = cell * J + bin at t_edges[n+1]),
+        path[n, s] (path length spent in s during the step, ticks converted to
+        length), esc[n], dwells[n], transitions[n], alive[n]; and the walk's
+        tallies."""
+        torch = self.torch
+        te = np.asarray(t_edges, dtype=np.float64)
+        nt = len(te) - 1
+        S = int(self.w.ncell) * self.J
+        need = time_state_bytes(n_packets)
+        if need == 0:
+            raise ValueError("n_packets out of range")
+        state = torch.empty(need, dtype=torch.uint8, device=self.device)
+        bins = torch.zeros((nt, S), dtype=torch.int64, device=self.device)
+        path = torch.zeros((nt, S), dtype=torch.int64, device=self.device)
+        counts = torch.zeros((nt, 4), dtype=torch.int64, device=self.device)
+        self.reset()
+        for n in range(nt):
+            st = TimeStep(seed, n_packets, max_steps, float(te[n]), float(te[n + 1]), 1 if n == 0 else 0, chunk,
+                          threads_per_cta, ctas_per_sm)
+            time_step_launch(self.grid, self.table.data_ptr(), st, state.data_ptr(), state.numel(),
+                             self.tally.data_ptr(), self.tally.numel() * 8, bins[n].data_ptr(), path[n].data_ptr(),
+                             counts[n].data_ptr(), self.stream())
+        c = counts.cpu().numpy().astype(np.uint64)
+        ticks = path.cpu().numpy().astype(np.float64)
+        return dict(bins=bins.cpu().numpy().astype(np.uint64), path=ticks * (np.diff(te) / TIME_TICKS)[:, None],
+                    path_ticks=path.cpu().numpy().astype(np.uint64), esc=c[:, 0], dwells=c[:, 1],
+                    transitions=c[:, 2], alive=c[:, 3], tallies=self.read())
 
     def scatter(self, x_in: float, seed: int, n: int):
         out = self.torch.empty(n, dtype=self.torch.float32, device=self.device)

@@ -97,3 +97,24 @@ def test_hubble_sphere_has_few_classes():
     n_class = R.grid_sizes(g, 1).n_class
     R.destroy_grid(g)
     assert 1 < n_class <= 64, n_class
+
+
+def test_time_step_validation_without_a_gpu():
+    """rddmc_time_step_launch checks its arguments before touching any buffer:
+    the pointers below are never dereferenced."""
+    g = _grid(W.TINY)
+    assert R.time_state_bytes(1000) >= R.grid_sizes(g, 1000).state_bytes + 8 * 1000
+    assert R.time_state_bytes(1 << 62) == 0
+    fake = 1 << 20  # 256-byte aligned, never dereferenced
+
+    def call(**kw):
+        st = R.TimeStep(1, 1000, 0, 0.0, 1.0, 1, 0, 0, 0)
+        for k, v in kw.items():
+            setattr(st, k, v)
+        return R.lib().rddmc_time_step_launch(g, fake, st, fake, 1 << 30, fake, 1 << 20, fake, fake, fake, None)
+
+    assert call() == R.ERR_TABLE          # no precompute on this grid
+    st = R.TimeStep(1, 1000, 0, 0.0, 1.0, 1, 0, 0, 0)
+    assert R.lib().rddmc_time_step_launch(g, fake, st, None, 1 << 30, fake, 1 << 20, fake, fake, fake, None) \
+        == R.ERR_ARG
+    R.destroy_grid(g)

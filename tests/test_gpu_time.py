@@ -1,0 +1,182 @@
+"""Parity of the time-dependent walk (Sec. 2.3 causality; eq. E_estimator bin
+and path estimates) on the GPU with the FP64 oracle and the exact
+continuous-time chain.
+
+The device walk visits the same sequence of states as the oracle for every
+packet (the transition and event streams are shared); only the clock differs:
+the device forms each dwell in FP32 and rounds it to 2^-31 of the step, the
+oracle in FP64.  A packet whose step-end crossing falls within that rounding
+of t_{n+1} (a relative 1e-7 of its elapsed time) is counted one transition
+earlier or later, so the per-step bin counts agree except for a few packets
+per thousand steps walked, and the path estimate agrees to about 1e-6.
+Against the chain the comparison is statistical, as for the oracle."""
+import numpy as np
+import pytest
+from scipy.special import erf
+from scipy.stats import chi2
+
+torch = pytest.importorskip("torch")
+
+from oracle import analytic as A  # noqa: E402
+from oracle import coracle as C  # noqa: E402
+from paper_1709_10187_gb300 import build as B  # noqa: E402
+from paper_1709_10187_gb300 import rddmc as R  # noqa: E402
+from paper_1709_10187_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+GREY = W.Workload("grey_slab_101x1", 1, (101, 1, 1), 1, -5.0, 5.0, 1.0e3, 1.0e4, 100_000, 0x5EED0901)
+
+CASES = [
+    (W.TINY, [0.0, 0.1, 0.3, 1.0, 3.0, 10.0]),
+    (W.SMALL, [0.0, 0.3, 1.0, 3.0, 10.0, 30.0]),
+    (W.SPHERE8_V, [0.0, 0.3, 1.0, 3.0, 10.0]),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def _flip_allowance(n, transitions_per_packet):
+    # a flip needs the FP32 clock to differ from the FP64 one by the distance of
+    # the crossing to t_{n+1}; with per-dwell relative errors ~1e-7 (partly
+    # systematic: 1/K_s and the tick scale are rounded once) the chance per
+    # packet and step is below ~1e-7 x transitions
+    return max(8, int(np.ceil(4e-7 * transitions_per_packet * n)) + 8)
+
+
+@pytest.mark.parametrize("w,t_edges", CASES, ids=lambda v: getattr(v, "name", "edges"))
+def test_time_walk_tracks_the_oracle(w, t_edges):
+    n = 20_000
+    p = R.Problem(w)
+    g = p.time_run(n, w.seed, t_edges)
+    og = C.Grid(w)
+    o = C.walk_time(og, og.table(), w.seed, 0, n, t_edges)
+    tp = o["transitions"] / n
+    allow = _flip_allowance(n, tp)
+    assert g["tallies"]["emitted"] == n and o["emitted"] == n
+    assert g["tallies"]["aborted"] == 0 and g["tallies"]["status"] == 0
+    worst = []
+    for k in range(len(t_edges) - 1):
+        db = int(np.abs(g["bins"][k].astype(np.int64) - o["bins"][k].astype(np.int64)).sum())
+        de = abs(int(g["esc"][k]) - int(o["esc"][k]))
+        rel_path = float(np.abs(g["path"][k] - o["path"][k]).sum() / o["path"][k].sum())
+        worst.append((db, de, rel_path))
+        assert db <= 2 * allow and de <= allow, (k, db, de, allow)
+        assert rel_path <= 1e-3, (k, rel_path)
+    # the same packets escaped (up to flips at the last step end) with the same
+    # escape tallies
+    dh = int(np.abs(g["tallies"]["hist"].astype(np.int64) - o["hist"].astype(np.int64)).sum())
+    assert dh <= 2 * allow, dh
+    assert abs(int(g["transitions"].sum()) - o["transitions"]) <= allow
+    assert abs(int(g["dwells"].sum()) - o["dwells"]) <= 2 * allow
+    print(f"\n{w.name}: {tp:.0f} transitions/packet; per step (|d bins|, |d esc|, rel path): {worst}")
+    p.close()
+
+
+def _invariants(g, n):
+    alive_end = g["alive"].astype(np.int64)
+    esc = g["esc"].astype(np.int64)
+    alive_start = np.concatenate([[n], alive_end[:-1]])
+    assert np.array_equal(alive_start - esc, alive_end)
+    assert np.array_equal(g["bins"].sum(axis=1).astype(np.int64), alive_end)
+    ticks = g["path_ticks"].sum(axis=1).astype(object)
+    for k in range(len(esc)):
+        # every packet alive at the step's end spent the whole step; an escaping
+        # one less
+        lo = R.TIME_TICKS * int(alive_end[k])
+        hi = R.TIME_TICKS * int(alive_end[k] + esc[k])
+        assert lo <= ticks[k] <= hi, (k, ticks[k], lo, hi)
+        if esc[k] == 0:
+            assert ticks[k] == lo
+
+
+def test_time_step_invariants_and_launch_shape_independence():
+    w = W.SMALL
+    te = [0.0, 0.3, 1.0, 3.0, 10.0, 30.0]
+    n = 30_000
+    p = R.Problem(w)
+    a = p.time_run(n, w.seed, te)
+    b = p.time_run(n, w.seed, te, chunk=16, threads_per_cta=128, ctas_per_sm=1)
+    c = p.time_run(n, w.seed, te, chunk=1024, threads_per_cta=96)
+    for r in (a, b, c):
+        _invariants(r, n)
+    # per-packet streams and integer clocks: identical under any launch shape
+    for r in (b, c):
+        for k in ("bins", "path_ticks", "esc", "dwells", "transitions", "alive"):
+            assert np.array_equal(a[k], r[k]), k
+        assert np.array_equal(a["tallies"]["hist"], r["tallies"]["hist"])
+    p.close()
+
+
+def test_watchdog_aborts_in_time_mode():
+    w = W.SMALL
+    n = 4000
+    p = R.Problem(w)
+    g = p.time_run(n, w.seed, [0.0, 10.0, 30.0], max_steps=500)
+    og = C.Grid(w)
+    o = C.walk_time(og, og.table(), w.seed, 0, n, [0.0, 10.0, 30.0], max_steps=500)
+    allow = _flip_allowance(n, 500)
+    assert o["aborted_time"] > n // 2
+    assert abs(int(g["tallies"]["aborted"]) - o["aborted_time"]) <= allow
+    assert abs(int(g["tallies"]["steps"]) - o["transitions"]) <= allow
+    for k in range(2):
+        assert int(np.abs(g["bins"][k].astype(np.int64) - o["bins"][k].astype(np.int64)).sum()) <= 2 * allow
+    # an aborted packet is in no state and took no dwell after its last transition
+    assert int(g["alive"][-1]) + int(g["esc"].sum()) + int(g["tallies"]["aborted"]) == n
+    p.close()
+
+
+@pytest.mark.parametrize("w,t_edges", CASES[:2], ids=lambda v: getattr(v, "name", "edges"))
+def test_time_walk_follows_the_continuous_time_chain(w, t_edges):
+    n = 400_000
+    p = R.Problem(w)
+    g = p.time_run(n, w.seed + 7, t_edges)
+    t = C.Grid(w).table()
+    occ, path, esc = A.chain_time(w, t, np.asarray(t_edges))
+    for k in range(len(t_edges) - 1):
+        e = occ[k] * n
+        o = g["bins"][k].astype(np.float64)
+        sel = e >= 20.0
+        z = (o[sel] - e[sel]) / np.sqrt(e[sel] * (1.0 - occ[k][sel]))
+        m = int(sel.sum())
+        assert np.abs(z).max() < 5.0 and int((np.abs(z) > 3.0).sum()) <= max(1, int(np.ceil(0.02 * m))), (k, z)
+        assert chi2.sf(float((z * z).sum()), m) > 1e-3, (k, float((z * z).sum()), m)
+        assert np.all(o[e < 1e-9] == 0)
+        pe = esc[k]
+        ze = (float(g["esc"][k]) - n * pe) / np.sqrt(max(n * pe * (1 - pe), 1e-12))
+        assert abs(ze) < 5.0 or abs(float(g["esc"][k]) - n * pe) < 3.0, (k, g["esc"][k], n * pe)
+        dt = t_edges[k + 1] - t_edges[k]
+        ep = path[k] * n
+        assert np.all(np.abs(g["path"][k] - ep) <= 5.0 * np.sqrt(dt * ep) + 1e-6 * dt * n), k
+    p.close()
+
+
+def test_grey_medium_bin_and_path_estimates_follow_fick_diffusion():
+    """The paper's grey test (Sec. 3): one grey bin over 101 cells; both
+    estimators against the point-source Gaussian of D = 1/(3k) and against the
+    exact chain."""
+    w = GREY
+    t = C.Grid(w).table()
+    k = float(t["k"][w.n[0] // 2])
+    D = 1.0 / (3.0 * k)
+    sig = np.array([0.10, 0.15, 0.20])
+    te = np.concatenate([[0.0], sig ** 2 / (2.0 * D)])
+    n = 2_000_000
+    p = R.Problem(w)
+    g = p.time_run(n, w.seed, te)
+    occ, path, _ = A.chain_time(w, t, te)
+    e = np.linspace(-w.R, w.R, w.n[0] + 1)
+    dz = 2.0 * w.R / w.n[0]
+    for q in range(len(sig)):
+        gauss = 0.5 * np.diff(erf(e / np.sqrt(2.0 * (2.0 * D * te[q + 1]))))
+        l1_chain = A.l1_distance(occ[q], gauss)
+        l1_bins = A.l1_distance(g["bins"][q].astype(np.float64), gauss)
+        assert l1_chain <= 0.2 * (dz / sig[q]) ** 2 + 1e-3
+        assert l1_bins <= l1_chain + 4.0 * np.sqrt(2.0 * w.n[0] / (np.pi * n)), (q, l1_bins, l1_chain)
+        # the path estimate is the step's time-averaged occupancy: the chain's
+        l1_path = A.l1_distance(g["path"][q], path[q])
+        assert l1_path <= 4.0 * np.sqrt(2.0 * w.n[0] / (np.pi * n)), (q, l1_path)
+    p.close()
