@@ -447,6 +447,94 @@ def _learned_vs_plain(R, torch, n=64, brick=16, margin=1, J=64, x_max=64.0, tau0
             "speedup_at_equal_l1": t_e / t_l, "reference_packets": 4 * npk}
 
 
+def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm=0):
+    """A flash of npk packets advanced through constant time steps, one launch
+    of the time-dependent walk per step (Sec. 2.3; eq. E_estimator), timed with
+    CUDA events around all launches (a warm-up pass over the first steps runs
+    before).  Physics summary at the `marks` times: for the grey test the L1
+    distance of the bin estimate from the Fick Gaussian (D = 1/(3k)); for the
+    resonant slab the slope d ln E_z / d|z/R| of the frequency-integrated path
+    estimate, beside the paper's fit -2.24 (t/t_diff)^-0.72 (Sec. 3)."""
+    prob = R.Problem(w)
+    s = prob.stream()
+    nt = len(t_edges) - 1
+    S = w.ncell * prob.J
+    state = torch.empty(R.time_state_bytes(npk), dtype=torch.uint8, device=prob.device)
+    bins = torch.zeros((nt, S), dtype=torch.int64, device=prob.device)
+    path = torch.zeros((nt, S), dtype=torch.int64, device=prob.device)
+    counts = torch.zeros((nt, 4), dtype=torch.int64, device=prob.device)
+
+    def steps(k_end):
+        for k in range(k_end):
+            st = R.TimeStep(w.seed, npk, 0, float(t_edges[k]), float(t_edges[k + 1]), 1 if k == 0 else 0, chunk, 0,
+                            ctas_per_sm)
+            R.time_step_launch(prob.grid, prob.table.data_ptr(), st, state.data_ptr(), state.numel(),
+                               prob.tally.data_ptr(), prob.tally.numel() * 8, bins[k].data_ptr(), path[k].data_ptr(),
+                               counts[k].data_ptr(), s)
+
+    steps(min(nt, 4))  # warm-up
+    for b in (bins, path, counts):
+        b.zero_()
+    prob.reset()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(torch.cuda.current_stream())
+    steps(nt)
+    a1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    dt = a0.elapsed_time(a1) / 1e3
+    c = counts.cpu().numpy()
+    tr, dw = int(c[:, 2].sum()), int(c[:, 1].sum())
+    out = {"workload": w.name, "packets": npk, "time_steps": nt, "dt": float(t_edges[1] - t_edges[0]), "s": dt,
+           "ms_per_time_step": 1e3 * dt / nt, "packet_steps_per_s": npk * nt / dt, "transitions_per_s": tr / dt,
+           "dwells_per_s": dw / dt, "transitions_per_packet": tr / npk, "escaped": int(c[:, 0].sum()),
+           "alive_at_end": int(c[-1, 3]), "launches": nt}
+    ks = [int(round(m / (t_edges[1] - t_edges[0]))) - 1 for m in marks]
+    b = bins.cpu().numpy()
+    pth = path.cpu().numpy().astype(np.float64)
+    z = w.cell_centres()[:, 0] / w.R
+    if kind == "grey":
+        k = float(R.cell_tau(prob.grid, prob.table.data_ptr(), w.n[0] // 2, prob.J)[0]) / (2.0 * w.R / w.n[0])
+        from scipy.special import erf
+        e = np.linspace(-w.R, w.R, w.n[0] + 1)
+        out["grey_l1_vs_fick"] = {}
+        for m, kk in zip(marks, ks):
+            g = 0.5 * np.diff(erf(e / np.sqrt(4.0 * t_edges[kk + 1] / (3.0 * k))))
+            out["grey_l1_vs_fick"][f"{m:.4g}"] = _l1(b[kk].astype(np.float64), g)
+    else:
+        t_diff = w.atau0_nominal ** (1.0 / 3.0) * w.R
+        sel = (np.abs(z) >= 0.05) & (np.abs(z) <= 0.8)
+        out["slope_dlnEz_dz"] = {}
+        for m, kk in zip(marks, ks):
+            ez = pth[kk].reshape(w.ncell, prob.J).sum(axis=1)
+            ok = sel & (ez > 0)
+            slope = float(np.polyfit(np.abs(z[ok]), np.log(ez[ok]), 1)[0])
+            out["slope_dlnEz_dz"][f"{m / t_diff:.2f}"] = {"measured": slope,
+                                                          "paper_fit": -2.24 * (m / t_diff) ** -0.72}
+    return out
+
+
+def _time_grey(R, torch, npk=10_000_000):
+    """Sec. 3 grey test: 101 cells, steps of 1e-3 t_diff, t_diff = k R^2 / 2c, to 0.16 t_diff."""
+    w = W.GREY101
+    p = R.Problem(w)
+    k = float(R.cell_tau(p.grid, p.table.data_ptr(), w.n[0] // 2, p.J)[0]) / (2.0 * w.R / w.n[0])
+    p.close()
+    t_diff = 0.5 * k * w.R ** 2
+    te = W.time_edges(1e-3 * t_diff, 0.16 * t_diff)
+    return _time_dependent(R, torch, w, npk, te, "grey", [f * t_diff for f in (0.01, 0.02, 0.04, 0.08, 0.16)])
+
+
+def _time_p2(R, torch, npk=10_000_000, t_frac=0.32):
+    """Sec. 3 time-dependent resonant slab: a tau0 = 1e9, T = 10 K, 101 cells, 51
+    bins of ~0.1 (a tau0)^(1/3), steps of 1e-3 (a tau0)^(1/3) R/c."""
+    w = W.P2
+    t_diff = w.atau0_nominal ** (1.0 / 3.0) * w.R
+    te = W.time_edges(1e-3 * t_diff, t_frac * t_diff)
+    marks = [f * t_diff for f in (0.01, 0.02, 0.04, 0.08, 0.16, 0.32) if f <= t_frac + 1e-9]
+    return _time_dependent(R, torch, w, npk, te, "slab", marks)
+
+
 def _extras(R, torch, only=None):
     out = {}
     jobs = [("c3_sphere_static", lambda: _sliced_rate(R, torch, R.Problem(W.C3), 1_000_000, W.C3.seed, 4096)),
@@ -457,6 +545,8 @@ def _extras(R, torch, only=None):
             ("c1_complete", lambda: _complete(R, torch, W.C1, W.C1.packets)),
             ("c2_widecore_complete", lambda: _complete(R, torch, W.C2_WIDECORE, W.C2_WIDECORE.packets)),
             ("batched_512", lambda: _batched(R, torch)),
+            ("time_grey_paper", lambda: _time_grey(R, torch)),
+            ("time_slab_atau1e9_paper", lambda: _time_p2(R, torch)),
             ("learned_vs_plain", lambda: _learned_vs_plain(R, torch))]
     if only:
         small = {"learned_small": lambda: _learned_vs_plain(R, torch, n=32, brick=8, tau0=1.0e6, npk=100_000,
@@ -466,6 +556,8 @@ def _extras(R, torch, only=None):
                                                          npk=200_000, ndata=1_500_000, iters=4000),
                  # a C2 subset run to completion: bounded below by its slowest packet (~3e9 transitions)
                  "c2_complete_1e5": lambda: _complete(R, torch, W.C2, 100_000),
+                 # a short time-dependent run for profiling: 1e6 packets, 16 steps
+                 "time_slab_small": lambda: _time_p2(R, torch, npk=1_000_000, t_frac=0.016),
                  "learned_c5_tau1e8": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0,
                                                                 tau0=1.0e8, npk=100_000, ndata=600_000, iters=4000),
                  "learned_c5_tau1e9": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0,
@@ -486,7 +578,7 @@ def _extras(R, torch, only=None):
 def _kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("walk.cu", "rddmc_internal.cuh"):
+    for f in ("walk.cu", "walk_common.cuh", "rddmc_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1709_10187_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -27,13 +27,15 @@
 // dwell words of a group come from at most two dwell blocks, the lower one
 // usually the block cached from the group before: two Philox calls per four
 // transitions in all.  Lanes take packets from a global cursor (one atomicAdd
-// per warp) and run at most `chunk` transitions between refills.
+// per warp) and run at most `chunk` transitions between refills (64 by
+// default), so a lane whose packet stopped early in its step takes a new one
+// while long-running packets continue.
 //
-// Tallies: the path estimate goes to shared memory when the grid's states fit
-// (u64 ticks per state, flushed with one atomic per touched state), else
-// straight to global memory; the bin estimate (one increment per packet per
-// step) and the escape tallies of the walk go to global memory and the
-// tally buffer's shared-memory staging, as in the persistent walk.
+// Tallies: the path and bin estimates go to shared memory when the grid's
+// states fit (ticks as a u32 low word plus a u32 carry count, so every update
+// is a native 32-bit shared atomic, and u32 bin counts; flushed with one
+// atomic per touched state), else straight to global memory; the escape tallies of the
+// walk use the tally buffer's shared-memory staging, as in the persistent walk.
 #include <cmath>
 #include <cstring>
 
@@ -43,12 +45,8 @@
 namespace rddmc {
 namespace {
 
-#ifndef RDDMC_TIME_MIN_BLOCKS
-#define RDDMC_TIME_MIN_BLOCKS 3  // resident 256-thread CTAs per SM the register budget targets
-#endif
-
 constexpr uint32_t kTicks = 1u << 31;  // ticks per time step
-constexpr int kSmemStatesMax = 6144;   // path entries kept in shared memory (48 KiB)
+constexpr size_t kSmemTallyMax = 110 * 1024;  // shared-memory budget per CTA for the per-state tallies
 
 struct TimeParams {
     const float* rk;                 // 1 / K_s per row
@@ -69,8 +67,10 @@ __device__ __forceinline__ uint4 trans_block(unsigned long long b, uint32_t pl, 
     return philox_rk(make_uint4((uint32_t)b, (uint32_t)(b >> 32), pl, ph), P);
 }
 
-template <int NDIM, bool SMEM_PATH>
-__global__ void __launch_bounds__(256, RDDMC_TIME_MIN_BLOCKS) time_kernel(const WalkParams P, const TimeParams T) {
+// MINB: resident 256-thread CTAs per SM the register budget targets (2: no
+// spills, 16 warps per SM; 3: 24 warps with a few spilled registers).
+template <int NDIM, bool SMEM_TALLY, int MINB>
+__global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, const TimeParams T) {
     constexpr int RW = NDIM == 1 ? 1 : 2;  // uint4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* s_cnt = reinterpret_cast<unsigned long long*>(smem_raw);  // kCounters
@@ -78,13 +78,21 @@ __global__ void __launch_bounds__(256, RDDMC_TIME_MIN_BLOCKS) time_kernel(const 
     unsigned long long* s_sb = s_face + 8;                                        // kNsb
     unsigned long long* s_hist = s_sb + kNsb;                                     // J+2 if in smem
     const int nhist = P.J + 2;
-    unsigned long long* s_path = s_hist + (P.hist_in_smem ? nhist : 0);          // n_states if SMEM_PATH
+    // per-state tallies: path ticks as two u32 words (low word and carries, so
+    // that every update is a native 32-bit shared atomic) and the bin counts
+    unsigned* s_plo = reinterpret_cast<unsigned*>(s_hist + (P.hist_in_smem ? nhist : 0));  // n_states if SMEM_TALLY
+    unsigned* s_phi = s_plo + (SMEM_TALLY ? T.n_states : 0);
+    unsigned* s_bins = s_phi + (SMEM_TALLY ? T.n_states : 0);
 
     for (int i = threadIdx.x; i < kCounters + 8 + kNsb; i += blockDim.x) s_cnt[i] = 0ull;
     if (P.hist_in_smem)
         for (int i = threadIdx.x; i < nhist; i += blockDim.x) s_hist[i] = 0ull;
-    if (SMEM_PATH)
-        for (int i = threadIdx.x; i < T.n_states; i += blockDim.x) s_path[i] = 0ull;
+    if (SMEM_TALLY)
+        for (int i = threadIdx.x; i < T.n_states; i += blockDim.x) {
+            s_plo[i] = 0u;
+            s_phi[i] = 0u;
+            s_bins[i] = 0u;
+        }
     __syncthreads();
 
     const uint4* rows = P.rows;
@@ -99,14 +107,20 @@ __global__ void __launch_bounds__(256, RDDMC_TIME_MIN_BLOCKS) time_kernel(const 
     uint32_t pl = 0, ph = 0;
     unsigned long long tbc = ~0ull;     // index of the cached dwell block
     uint4 rtc = make_uint4(0u, 0u, 0u, 0u);
+    unsigned long long tnc = ~0ull;     // index of the cached transition block
+    uint4 rnc = make_uint4(0u, 0u, 0u, 0u);
     unsigned long long n_steps = 0, n_edraw = 0, n_dwell = 0;
     unsigned n_emit = 0, n_esc = 0, n_abort = 0, n_clamp = 0, n_alive = 0, status_bits = 0;
 
     auto add_path = [&](unsigned ticks) {
         if (!ticks) return;
         const unsigned st = min(cell * J + min(s - cls * J, J - 1u), ns1);
-        if (SMEM_PATH) atomicAdd(&s_path[st], (unsigned long long)ticks);
-        else atomicAdd(&T.path[st], (unsigned long long)ticks);
+        if (SMEM_TALLY) {
+            const unsigned old = atomicAdd(&s_plo[st], ticks);  // ticks <= 2^31: at most one carry
+            if (old + ticks < old) atomicAdd(&s_phi[st], 1u);
+        } else {
+            atomicAdd(&T.path[st], (unsigned long long)ticks);
+        }
     };
 
     // One transition of the state on word w: every threshold, the outcome's
@@ -195,6 +209,12 @@ __global__ void __launch_bounds__(256, RDDMC_TIME_MIN_BLOCKS) time_kernel(const 
         return word_of(rtc, (unsigned)dd & 3u);
     };
 
+    auto trans_word = [&](unsigned long long tt) -> unsigned {
+        const unsigned long long b = tt >> 2;
+        if (b != tnc) { rnc = trans_block(b, pl, ph, P); tnc = b; }
+        return word_of(rnc, (unsigned)tt & 3u);
+    };
+
     for (;;) {
         // ---- warp-cooperative refill, repeated while lanes draw finished packets
         for (;;) {
@@ -242,6 +262,7 @@ __global__ void __launch_bounds__(256, RDDMC_TIME_MIN_BLOCKS) time_kernel(const 
                         pl = (uint32_t)pid;
                         ph = (uint32_t)(pid >> 32);
                         tbc = ~0ull;
+                        tnc = ~0ull;
                     }
                 }
             }
@@ -253,13 +274,11 @@ __global__ void __launch_bounds__(256, RDDMC_TIME_MIN_BLOCKS) time_kernel(const 
         const unsigned long long t0 = t, e0 = e;
         const unsigned long long lim = min(t + (unsigned long long)P.chunk, P.max_steps);
         int r = 0;
-        while (r == 0 && (t & 3ull) && t < lim) {
-            const unsigned long long b = t >> 2;
-            const uint4 rn = trans_block(b, pl, ph, P);
-            r = dwell_then_move(dwell_word(d), word_of(rn, (unsigned)t & 3u));
-        }
+        while (r == 0 && (t & 3ull) && t < lim) r = dwell_then_move(dwell_word(d), trans_word(t));
         while (r == 0 && t + 4ull <= lim) {
             const uint4 rn = trans_block(t >> 2, pl, ph, P);
+            tnc = t >> 2;
+            rnc = rn;
             const unsigned long long b0 = d >> 2;
             const unsigned p = (unsigned)d & 3u;
             const uint4 lo = (b0 == tbc) ? rtc : time_block(b0, pl, ph, P);
@@ -275,10 +294,7 @@ __global__ void __launch_bounds__(256, RDDMC_TIME_MIN_BLOCKS) time_kernel(const 
                 if (r) break;
             }
         }
-        while (r == 0 && t < lim) {  // fewer than four transitions left before the watchdog
-            const uint4 rn = trans_block(t >> 2, pl, ph, P);
-            r = dwell_then_move(dwell_word(d), word_of(rn, (unsigned)t & 3u));
-        }
+        while (r == 0 && t < lim) r = dwell_then_move(dwell_word(d), trans_word(t));  // short chunk end
         n_steps += t - t0;
         n_edraw += e - e0;
         if (r == 0 && t >= P.max_steps) {
@@ -290,7 +306,9 @@ __global__ void __launch_bounds__(256, RDDMC_TIME_MIN_BLOCKS) time_kernel(const 
             P.st_status[pid] = PK_DONE;
         } else if (r == 1) {
             const unsigned bin = min(s - cls * J, J - 1u);
-            atomicAdd(&T.bins[min(cell * J + bin, ns1)], 1ull);
+            const unsigned st = min(cell * J + bin, ns1);
+            if (SMEM_TALLY) atomicAdd(&s_bins[st], 1u);
+            else atomicAdd(&T.bins[st], 1ull);
             ++n_alive;
             P.st_cell[pid] = cell;
             P.st_bin[pid] = bin;
@@ -337,24 +355,36 @@ __global__ void __launch_bounds__(256, RDDMC_TIME_MIN_BLOCKS) time_kernel(const 
             if (s_hist[i]) atomicAdd(&P.tally[kHistOff + i], s_hist[i]);
     for (int i = threadIdx.x; i < kNsb; i += blockDim.x)
         if (s_sb[i]) atomicAdd(&P.tally[kHistOff + nhist + i], s_sb[i]);
-    if (SMEM_PATH)
-        for (int i = threadIdx.x; i < T.n_states; i += blockDim.x)
-            if (s_path[i]) atomicAdd(&T.path[i], s_path[i]);
+    if (SMEM_TALLY)
+        for (int i = threadIdx.x; i < T.n_states; i += blockDim.x) {
+            const unsigned long long v = ((unsigned long long)s_phi[i] << 32) | s_plo[i];
+            if (v) atomicAdd(&T.path[i], v);
+            if (s_bins[i]) atomicAdd(&T.bins[i], (unsigned long long)s_bins[i]);
+        }
 }
 
-template <int NDIM, bool SMEM_PATH>
-cudaError_t launch_time(const WalkParams& P, const TimeParams& T, int threads, size_t smem, int ctas, int nsm,
-                        cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(time_kernel<NDIM, SMEM_PATH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int NDIM, bool SMEM_TALLY, int MINB>
+cudaError_t launch_time_minb(const WalkParams& P, const TimeParams& T, int threads, size_t smem, int ctas, int nsm,
+                             cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(time_kernel<NDIM, SMEM_TALLY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     if (!ctas) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, time_kernel<NDIM, SMEM_PATH>, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, time_kernel<NDIM, SMEM_TALLY, MINB>, threads, smem);
         if (e != cudaSuccess) return e;
     }
     if (ctas < 1) ctas = 1;
-    time_kernel<NDIM, SMEM_PATH><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P, T);
+    time_kernel<NDIM, SMEM_TALLY, MINB><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P, T);
     return cudaGetLastError();
+}
+
+template <int NDIM, bool SMEM_TALLY>
+cudaError_t launch_time(const WalkParams& P, const TimeParams& T, int threads, size_t smem, int ctas, int nsm,
+                        cudaStream_t s) {
+    // default and ctas_per_sm >= 3: the 24-warp variant (faster on short steps);
+    // ctas_per_sm 1 or 2: the spill-free 16-warp one
+    return (ctas == 0 || ctas >= 3) ? launch_time_minb<NDIM, SMEM_TALLY, 3>(P, T, threads, smem, ctas, nsm, s)
+                                    : launch_time_minb<NDIM, SMEM_TALLY, 2>(P, T, threads, smem, ctas, nsm, s);
 }
 
 }  // namespace
@@ -397,7 +427,7 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
     w.opts.seed = ts->seed;
     w.opts.n_packets = ts->n_packets;
     w.opts.max_steps = ts->max_steps;
-    w.opts.chunk = ts->chunk;
+    w.opts.chunk = ts->chunk ? ts->chunk : 64;
     WalkParams P;
     fill_walk_params(*g, w, P);
     TimeParams T;
@@ -417,8 +447,10 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
     const int threads = ts->threads_per_cta ? ts->threads_per_cta : 256;
     size_t smem = (size_t)(kCounters + 8 + kNsb) * 8;
     if (P.hist_in_smem) smem += (size_t)(g->J + 2) * 8;
-    const bool smem_path = T.n_states <= kSmemStatesMax;
-    if (smem_path) smem += (size_t)T.n_states * 8;
+    // per-state tallies in shared memory while they fit the budget (u32 bin
+    // counts: a CTA walks fewer than 2^32 packets per step)
+    const bool smem_path = smem + (size_t)T.n_states * 12 <= kSmemTallyMax && ts->n_packets < (1ull << 32);
+    if (smem_path) smem += (size_t)T.n_states * 12;
     if (cudaMemsetAsync(P.cursor, 0, 8, s) != cudaSuccess) return RDDMC_ERR_CUDA;
     cudaError_t e;
     if (g->ndim == 1)

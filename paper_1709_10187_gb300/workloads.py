@@ -113,6 +113,10 @@ C3 = Workload("sphere_tau1e7_64c_128b", 3, (64, 64, 64), 128, -80.0, 80.0, 1.0e7
 C3_V20 = C3.with_(name="sphere_tau1e7_64c_128b_v20", vmax_kms=20.0)
 C3_V200 = C3.with_(name="sphere_tau1e7_64c_128b_v200", vmax_kms=200.0)
 
+# The grey diffusion test (Sec. 3): 101 cells, one frequency bin, so every state
+# has the same opacity and the walk is spatial diffusion with D = 1/(3k).
+GREY101 = Workload("grey_slab_101x1", 1, (101, 1, 1), 1, -5.0, 5.0, 1.0e3, 1.0e4, 10_000_000, 0x5EED0901)
+
 # Small grids for parity tests: several row tiles and ragged sizes, cheap enough
 # for the oracle to finish in seconds.
 TINY = Workload("slab_tiny_8x16", 1, (8, 1, 1), 16, -8.0, 8.0, 2.0e2, 1.0e4, 20_000, 0x5EED0101)
@@ -126,8 +130,14 @@ SPHERE8_V = SPHERE8.with_(name="sphere_tiny_8c_16b_v20", vmax_kms=20.0, seed=0x5
 SPHERE9_V = Workload("sphere_small_9c_21b_v20", 3, (9, 9, 9), 21, -21.0, 21.0, 3.0e3, 1.0e4, 10_000, 0x5EED0303,
                      sphere=True, vmax_kms=20.0)
 
-ALL = {w.name: w for w in (C1, C2, C1_WIDECORE, C2_WIDECORE, P1, P2, C3, C3_V20, C3_V200, TINY, SMALL, GREY_LIKE, SPHERE8, SPHERE8_V,
-                           SPHERE9_V)}
+ALL = {w.name: w for w in (C1, C2, C1_WIDECORE, C2_WIDECORE, P1, P2, C3, C3_V20, C3_V200, GREY101, TINY, SMALL,
+                           GREY_LIKE, SPHERE8, SPHERE8_V, SPHERE9_V)}
+
+
+def time_edges(dt: float, t_end: float) -> np.ndarray:
+    """Edges 0, dt, 2 dt, ... of constant time steps up to t_end (in R/c)."""
+    n = int(round(t_end / dt))
+    return np.arange(n + 1, dtype=np.float64) * dt
 
 
 def batched_instances(n: int = 512, seed: int = 0x5EED0004, packet_scale: float = 1.0):

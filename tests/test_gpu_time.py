@@ -25,7 +25,7 @@ from paper_1709_10187_gb300 import workloads as W  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-GREY = W.Workload("grey_slab_101x1", 1, (101, 1, 1), 1, -5.0, 5.0, 1.0e3, 1.0e4, 100_000, 0x5EED0901)
+GREY = W.GREY101
 
 CASES = [
     (W.TINY, [0.0, 0.1, 0.3, 1.0, 3.0, 10.0]),

@@ -17,7 +17,7 @@ from oracle import analytic as A
 from oracle import coracle as C
 from paper_1709_10187_gb300 import workloads as W
 
-GREY = W.Workload("grey_slab_101x1", 1, (101, 1, 1), 1, -5.0, 5.0, 1.0e3, 1.0e4, 100_000, 0x5EED0901)
+GREY = W.GREY101.with_(packets=100_000)
 
 
 def _check_against_chain(w, t_edges, n, seed):
