@@ -494,7 +494,8 @@ def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm
     pth = path.cpu().numpy().astype(np.float64)
     z = w.cell_centres()[:, 0] / w.R
     if kind == "grey":
-        k = float(R.cell_tau(prob.grid, prob.table.data_ptr(), w.n[0] // 2, prob.J)[0]) / (2.0 * w.R / w.n[0])
+        tau_c = R.cell_tau(prob.grid, prob.table.data_ptr(), w.n[0] // 2, prob.J, prob.stream())
+        k = float(tau_c[0]) / (2.0 * w.R / w.n[0])
         from scipy.special import erf
         e = np.linspace(-w.R, w.R, w.n[0] + 1)
         out["grey_l1_vs_fick"] = {}
@@ -518,7 +519,7 @@ def _time_grey(R, torch, npk=10_000_000):
     """Sec. 3 grey test: 101 cells, steps of 1e-3 t_diff, t_diff = k R^2 / 2c, to 0.16 t_diff."""
     w = W.GREY101
     p = R.Problem(w)
-    k = float(R.cell_tau(p.grid, p.table.data_ptr(), w.n[0] // 2, p.J)[0]) / (2.0 * w.R / w.n[0])
+    k = float(R.cell_tau(p.grid, p.table.data_ptr(), w.n[0] // 2, p.J, p.stream())[0]) / (2.0 * w.R / w.n[0])
     p.close()
     t_diff = 0.5 * k * w.R ** 2
     te = W.time_edges(1e-3 * t_diff, 0.16 * t_diff)

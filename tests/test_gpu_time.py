@@ -180,3 +180,30 @@ def test_grey_medium_bin_and_path_estimates_follow_fick_diffusion():
         l1_path = A.l1_distance(g["path"][q], path[q])
         assert l1_path <= 4.0 * np.sqrt(2.0 * w.n[0] / (np.pi * n)), (q, l1_path)
     p.close()
+
+
+def test_resonant_slab_profile_follows_the_paper_fit():
+    """Sec. 3, the time-dependent resonant slab (a tau0 = 1e9, T = 10 K, 101 x 51,
+    steps of 1e-3 t_diff, t_diff = (a tau0)^(1/3) R/c): the frequency-integrated
+    energy density is close to exponential in |z| with the paper's fit
+    d ln E_z / d|z/R| = -2.24 (t/t_diff)^-0.72.  The paper calls the fit
+    approximate; the path estimate's slope over 0.05 <= |z/R| <= 0.8 stays
+    within 15 % of it from 0.02 to 0.32 t_diff."""
+    w = W.P2
+    t_diff = w.atau0_nominal ** (1.0 / 3.0) * w.R
+    te = W.time_edges(1e-3 * t_diff, 0.32 * t_diff)
+    p = R.Problem(w)
+    g = p.time_run(1_000_000, w.seed, te)
+    z = w.cell_centres()[:, 0] / w.R
+    sel = (np.abs(z) >= 0.05) & (np.abs(z) <= 0.8)
+    out = []
+    for f in (0.02, 0.04, 0.08, 0.16, 0.32):
+        k = int(round(f * 1e3)) - 1
+        ez = g["path"][k].reshape(w.ncell, p.J).sum(axis=1)
+        ok = sel & (ez > 0)
+        slope = float(np.polyfit(np.abs(z[ok]), np.log(ez[ok]), 1)[0])
+        fit = -2.24 * f ** -0.72
+        out.append((f, slope, fit))
+        assert abs(slope / fit - 1.0) <= 0.15, (f, slope, fit)
+    print("\n(t/t_diff, measured slope, paper fit):", out)
+    p.close()
