@@ -343,7 +343,7 @@ typedef struct rddmc_time_step {
     double t_begin, t_end;  /* the step [t_n, t_{n+1}], t_end > t_begin */
     int32_t start;          /* 1: every packet starts at the source at t_begin (the first step);
                                0: packets resume from the state buffer */
-    int32_t chunk;          /* transitions a thread runs between refills: multiple of 4, 0 = 64 */
+    int32_t chunk;          /* transitions a thread runs between refills: multiple of 4, 0 = 256 */
     int32_t threads_per_cta; /* multiple of 32, at most 256; 0 = 256 */
     int32_t ctas_per_sm;    /* 0 = occupancy limit */
 } rddmc_time_step;

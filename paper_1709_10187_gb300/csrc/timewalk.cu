@@ -427,7 +427,7 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
     w.opts.seed = ts->seed;
     w.opts.n_packets = ts->n_packets;
     w.opts.max_steps = ts->max_steps;
-    w.opts.chunk = ts->chunk ? ts->chunk : 64;
+    w.opts.chunk = ts->chunk ? ts->chunk : 256;
     WalkParams P;
     fill_walk_params(*g, w, P);
     TimeParams T;
