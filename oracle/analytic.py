@@ -216,7 +216,44 @@ def chain_solve(w, table, edges=None):
                 escape_total=float(esc_so.sum()))
 
 
-def chain_time(w, table, t_edges, edges=None):
+def leak_matrices(w, table):
+    """For the leaks of eq. a_estimator: Lout[s, c*2ndim + f] = k_s P(f | s)
+    (the cell c of s leaves through face f), Lin[s, c'*2ndim + f'] = P(f | s)
+    times the expected k of the entered state of c' (f' the face c' is entered
+    through; Doppler rebins averaged), and Pf[s, f] = P(f | s), from the
+    quantised thresholds."""
+    J, nf = w.J, 2 * w.ndim
+    thr, flags, k = table["thr"], table["flags"], np.asarray(table["k"], dtype=np.float64)
+    S = thr.shape[0]
+    q = quantised_probs(thr)
+    Lout = np.zeros((S, w.ncell * nf))
+    Lin = np.zeros((S, w.ncell * nf))
+    for s in range(S):
+        c, j = divmod(s, J)
+        fl = int(flags[s])
+        for f in range(nf):
+            p = q[s, 2 + f]
+            if p == 0.0:
+                continue
+            Lout[s, c * nf + f] += k[s] * p
+            act = (fl >> (2 * (2 + f))) & 3
+            if act == ACT_ESCAPE:
+                continue
+            if act == ACT_TO_MC:
+                raise ValueError("leak_matrices handles DDMC-only tables")
+            nb = _neighbour(w, c, f // 2, 1 if f & 1 else -1)
+            if act == ACT_MOVE:
+                Lin[s, nb * nf + (f ^ 1)] += p * k[nb * J + j]
+            else:
+                m = int(table["rebin_m"][c * nf + f])
+                pr = float(table["rebin_thr"][c * nf + f]) / TWO32
+                for jn, pj in ((j + m, pr), (j + m + 1, 1.0 - pr)):
+                    jn = min(max(jn, 0), J - 1)
+                    Lin[s, nb * nf + (f ^ 1)] += p * pj * k[nb * J + jn]
+    return Lout, Lin, q[:, 2:]
+
+
+def chain_time(w, table, t_edges, edges=None, leaks=False):
     """Exact expectations of the time-dependent DDMC walk (Sec. 2.3): the walk
     is a continuous-time Markov chain whose state s is left at the total
     leakage rate K_s (per unit path length; c = 1) for the outcomes of the
@@ -224,7 +261,17 @@ def chain_time(w, table, t_edges, edges=None):
     Q = diag(K) (P - I).  For time steps [t_edges[n], t_edges[n+1]] returns
     the occupancy at each step's end (nt x S), the expected path length spent
     in each state during each step (nt x S), both per emitted packet, and the
-    escape probability per step (nt).  Dense: for small grids."""
+    escape probability per step (nt).  Dense: for small grids.
+
+    leaks=True also returns the expected optical depths of the leaks of eq.
+    a_estimator (nt x ncell x 2ndim x 2, leaving / entering each face) and the
+    expected number of leaks (same shape).  A leak out of s at time u ends a
+    dwell that began at the later of the previous jump and the step's start
+    (every step draws a fresh dwell), so by the memoryless property its
+    expected length sum over the step is P(f|s) times the completed-dwell mass
+    C_s = int p_s du - r_s(t_end), where r_s(t) = int p_s(u) exp(-K_s (t - u)) du
+    (the expected length of the dwell cut off at t_end) solves r' = p - K r.
+    [p, path, r] evolve together under one augmented matrix exponential."""
     P, esc = chain_matrix(w, table)
     S = P.shape[0]
     K = np.asarray(table["rate"], dtype=np.float64).sum(axis=1)
@@ -232,18 +279,42 @@ def chain_time(w, table, t_edges, edges=None):
     src_s, src_p = source_states(w, edges)
     p = np.zeros(S)
     p[src_s] = src_p
-    occ, path, esc_t = [], [], []
+    if leaks:
+        Lout, Lin, Pf = leak_matrices(w, table)
+        nf = 2 * w.ndim
+    occ, path, esc_t, lk, cnt = [], [], [], [], []
     for n in range(len(t_edges) - 1):
         h = float(t_edges[n + 1] - t_edges[n])
-        M = np.zeros((2 * S, 2 * S))
-        M[:S, :S] = Q * h
-        M[:S, S:] = np.eye(S) * h
-        E = sla.expm(M)  # top-left exp(Q h), top-right int_0^h exp(Q u) du
-        pn = p @ E[:S, :S]
-        path.append(p @ E[:S, S:])
+        if not leaks:
+            M = np.zeros((2 * S, 2 * S))
+            M[:S, :S] = Q * h
+            M[:S, S:] = np.eye(S) * h
+            E = sla.expm(M)  # top-left exp(Q h), top-right int_0^h exp(Q u) du
+            pn = p @ E[:S, :S]
+            path.append(p @ E[:S, S:])
+        else:
+            M = np.zeros((3 * S, 3 * S))
+            M[:S, :S] = Q * h
+            M[:S, S:2 * S] = np.eye(S) * h
+            M[:S, 2 * S:] = np.eye(S) * h
+            M[2 * S:, 2 * S:] = -np.diag(K) * h
+            E = sla.expm(M)
+            pn = p @ E[:S, :S]
+            ps = p @ E[:S, S:2 * S]
+            r = p @ E[:S, 2 * S:]
+            path.append(ps)
+            C = ps - r
+            lk.append(np.stack([(C @ Lout).reshape(w.ncell, nf), (C @ Lin).reshape(w.ncell, nf)], axis=-1))
+            ncount = (ps * K)[:, None] * Pf  # expected leaks per (state, face)
+            out_c = np.zeros((w.ncell, nf))
+            for f in range(nf):
+                np.add.at(out_c[:, f], np.arange(S) // w.J, ncount[:, f])
+            cnt.append(out_c)
         occ.append(pn)
         esc_t.append(p.sum() - pn.sum())
         p = pn
+    if leaks:
+        return np.array(occ), np.array(path), np.array(esc_t), np.array(lk), np.array(cnt)
     return np.array(occ), np.array(path), np.array(esc_t)
 
 

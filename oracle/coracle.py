@@ -58,7 +58,8 @@ def lib():
         L.orc_scatter_samples.restype = None
         L.orc_scatter_samples.argtypes = [d, d, u64, u64, vp]
         L.orc_walk_time.restype = ctypes.c_int
-        L.orc_walk_time.argtypes = [vp, vp, vp, vp, vp, vp, d, u64, u64, u64, vp, i32, u64, i32, vp, vp, vp, vp, vp]
+        L.orc_walk_time.argtypes = [vp, vp, vp, vp, vp, vp, d, u64, u64, u64, vp, i32, u64, i32, vp, vp, vp, vp, vp,
+                                    vp, vp]
         L.orc_fp_samples.restype = None
         L.orc_fp_samples.argtypes = [vp, i32, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp]
         L.orc_upar_table.restype = None
@@ -201,32 +202,38 @@ def replay_packet(grid: Grid, table: dict, seed: int, pid: int, n_trans: int, ma
 
 
 def walk_time(grid: Grid, table: dict, seed: int, p0: int, npk: int, t_edges, max_steps: int = (1 << 62),
-              nthreads: int = 0) -> dict:
+              nthreads: int = 0, leaks: bool = False) -> dict:
     """Time-dependent walk of packets [p0, p0+npk) emitted at t_edges[0]
     (orc_walk_time): per step n the packets in each state at its end (bins,
     nt x S), the path length spent in each state (path, nt x S) and the
-    escapes (esc, nt), plus the walk's tallies and transition/dwell counts."""
+    escapes (esc, nt), plus the walk's tallies and transition/dwell counts.
+    leaks=True adds the optical depths of the leaks of eq. a_estimator
+    (leak, nt x ncell x 2 ndim x 2: per face, leaving / entering the cell)."""
     if nthreads <= 0:
         nthreads = os.cpu_count() or 1
     te = np.ascontiguousarray(t_edges, dtype=np.float64)
     nt = len(te) - 1
     S = grid.ncell * grid.J
+    nf = 2 * grid.w.ndim
     bins = np.zeros(nt * S, dtype=np.uint64)
     path = np.zeros(nt * S, dtype=np.float64)
     esc = np.zeros(nt, dtype=np.uint64)
     tally = np.zeros(lib().orc_tally_len(grid.J), dtype=np.uint64)
     stats = np.zeros(3, dtype=np.uint64)
+    leak = np.zeros(nt * grid.ncell * nf * 2, dtype=np.float64) if leaks else None
     thr = np.ascontiguousarray(table["thr"].ravel())
     rate = np.ascontiguousarray(table["rate"].ravel())
     rc = lib().orc_walk_time(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
                              _ptr(table["rebin_thr"]), _ptr(rate), float(grid.w.x0), int(seed), int(p0), int(npk),
                              _ptr(te), int(nt), int(max_steps), int(nthreads), _ptr(bins), _ptr(path), _ptr(esc),
-                             _ptr(tally), _ptr(stats))
+                             _ptr(tally), _ptr(stats), _ptr(table["k"]) if leaks else None, _ptr(leak))
     if rc != 0:
         raise RuntimeError(f"orc_walk_time failed: {rc}")
     out = unpack_tally(tally, grid.J)
     out.update(bins=bins.reshape(nt, S), path=path.reshape(nt, S), esc=esc, transitions=int(stats[0]),
                dwells=int(stats[1]), aborted_time=int(stats[2]))
+    if leaks:
+        out["leak"] = leak.reshape(nt, grid.ncell, nf, 2)
     return out
 
 

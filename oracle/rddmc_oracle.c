@@ -931,13 +931,19 @@ typedef struct orc_time_args {
     uint64_t* bins;   /* per thread: nt x S */
     double* path;     /* per thread: nt x S */
     uint64_t* esc;    /* per thread: nt */
+    double* leak;     /* per thread: nt x ncell x 2 ndim x 2, or NULL */
     uint64_t steps, dwells, aborted;
 } orc_time_args;
 
 /* One DDMC transition of packet P in its current state (categorical draw on
- * the transition stream, action of the outcome).  Returns 1 if the packet
- * escaped, -1 if it met an MC state, 0 otherwise. */
-static int orc_time_transition(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t* t) {
+ * the transition stream, action of the outcome).  A spatial outcome is a leak
+ * through a face of the cell: if `leak` is set, the optical depth k dl of the
+ * dwell dl that ended in it is added for the cell it leaves (index 0 of its
+ * face) and, unless it escapes, for the cell it enters with that cell's k at
+ * the new bin (index 1 of the face it enters through; eq. a_estimator).
+ * Returns 1 if the packet escaped, -1 if it met an MC state, 0 otherwise. */
+static int orc_time_transition(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t* t, double dl,
+                               double* leak) {
     const orc_grid* g = A->g;
     const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim;
     int64_t c = orc_cell_of(g, P->idx);
@@ -948,8 +954,9 @@ static int orc_time_transition(orc_walk_args* A, uint64_t pk, orc_pstate* P, uin
     P->steps++;
     t[ORC_T_STEPS]++;
     unsigned act = (A->flags[s] >> (2 * o)) & 3u;
-    if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, P->j, o, pk, &P->e, t); return 1; }
     if (act == ORC_ACT_TO_MC) return -1;
+    if (o >= 2 && leak) leak[(c * nf + (o - 2)) * 2 + 0] += A->k[s] * dl;
+    if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, P->j, o, pk, &P->e, t); return 1; }
     if (o < 2) { P->j += o ? 1 : -1; return 0; }
     int face = o - 2, ax = face / 2, side = (face & 1) ? 1 : -1;
     if (act == ORC_ACT_REBIN) {
@@ -960,6 +967,10 @@ static int orc_time_transition(orc_walk_args* A, uint64_t pk, orc_pstate* P, uin
         P->j = jn;
     }
     P->idx[ax] += side;
+    if (leak) {
+        const int64_t cn = orc_cell_of(g, P->idx);
+        leak[(cn * nf + (face ^ 1)) * 2 + 1] += A->k[cn * J + P->j] * dl;
+    }
     return 0;
 }
 
@@ -969,6 +980,7 @@ static void* orc_time_thread(void* vp) {
     const orc_grid* g = A->g;
     const int J = g->J, K = orc_nout(g);
     const int64_t S = (int64_t)orc_ncell(g) * J;
+    const size_t L = (size_t)orc_ncell(g) * 2 * g->ndim * 2;
     for (uint64_t pk = A->p0; pk < A->p1; ++pk) {
         orc_pstate P;
         orc_start(A, pk, &P, A->tally);
@@ -993,7 +1005,7 @@ static void* orc_time_thread(void* vp) {
                 }
                 T->path[(size_t)n * S + s] += dl;
                 tau += dl;
-                int r = orc_time_transition(A, pk, &P, A->tally);
+                int r = orc_time_transition(A, pk, &P, A->tally, dl, T->leak ? T->leak + (size_t)n * L : NULL);
                 if (r == 1) { T->esc[n]++; done = 1; break; }
                 if (r == -1) { A->status = -2; done = 3; break; }
             }
@@ -1018,14 +1030,21 @@ static void* orc_time_thread(void* vp) {
  *   bins[n*S + s]: packets in state s at t_edges[n+1] (the bin estimate)
  *   path[n*S + s]: path length spent in state s during step n (the path estimate)
  *   esc[n]: packets escaped during step n;  tally: the walk's counters
+ *   leak[((n*ncell + c)*2ndim + f)*2 + io] (if leak and k are given): the
+ *       optical depths k dl of the leaks of eq. a_estimator through face f of
+ *       cell c during step n, io = 0 leaving the cell (k of the cell at the
+ *       bin it leaves), io = 1 entering it (k of the cell at the bin it
+ *       enters); dl is the dwell that ended in the leak.  The acceleration of
+ *       cell c is proportional to sum_f (leak[out] - leak[in]) n_f.
  * with S = ncell * J.  DDMC tables only.  stats[3] = {transitions, dwell draws,
  * aborted}.  Returns 0, -1 on bad input, -2 if a packet met an MC state.
  */
 int orc_walk_time(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
                   const uint32_t* rebin_thr, const double* rate, double x0, uint64_t seed, uint64_t p0, uint64_t np,
                   const double* t_edges, int nt, uint64_t max_steps, int nthreads, uint64_t* bins, double* path,
-                  uint64_t* esc, uint64_t* tally, uint64_t* stats) {
+                  uint64_t* esc, uint64_t* tally, uint64_t* stats, const double* k, double* leak) {
     if (!g || !thr || !flags || !rate || !t_edges || nt < 1 || !bins || !path || !esc || !tally || !stats) return -1;
+    if (leak && !k) return -1;
     if (p0 + np > ((uint64_t)1 << 62)) return -1;
     for (int n = 0; n < nt; ++n)
         if (!(t_edges[n + 1] > t_edges[n])) return -1;
@@ -1041,15 +1060,18 @@ int orc_walk_time(const orc_grid* g, const uint32_t* thr, const uint32_t* flags,
     uint64_t* tb = (uint64_t*)calloc((size_t)nthreads * nt * S, sizeof(uint64_t));
     double* tp = (double*)calloc((size_t)nthreads * nt * S, sizeof(double));
     uint64_t* te = (uint64_t*)calloc((size_t)nthreads * nt, sizeof(uint64_t));
+    const size_t LN = (size_t)nt * orc_ncell(g) * 2 * g->ndim * 2;
+    double* tlk = leak ? (double*)calloc((size_t)nthreads * LN, sizeof(double)) : NULL;
     for (int i = 0; i < nthreads; ++i) {
         orc_time_args* T = &args[i];
         orc_walk_args* A = &T->w;
         A->g = g; A->thr = thr; A->flags = flags; A->rebin_m = rebin_m; A->rebin_thr = rebin_thr;
-        A->rate = rate; A->src = &src; A->seed = seed; A->max_steps = max_steps;
+        A->rate = rate; A->src = &src; A->seed = seed; A->max_steps = max_steps; A->k = k;
         A->p0 = p0 + np * (uint64_t)i / nthreads;
         A->p1 = p0 + np * (uint64_t)(i + 1) / nthreads;
         A->tally = tl + (size_t)i * L;
         T->t_edges = t_edges; T->nt = nt;
+        T->leak = tlk ? tlk + (size_t)i * LN : NULL;
         T->bins = tb + (size_t)i * nt * S;
         T->path = tp + (size_t)i * nt * S;
         T->esc = te + (size_t)i * nt;
@@ -1066,12 +1088,14 @@ int orc_walk_time(const orc_grid* g, const uint32_t* thr, const uint32_t* flags,
             path[q] += tp[(size_t)i * nt * S + q];
         }
         for (int n = 0; n < nt; ++n) esc[n] += te[(size_t)i * nt + n];
+        if (tlk)
+            for (size_t q = 0; q < LN; ++q) leak[q] += tlk[(size_t)i * LN + q];
         stats[0] += args[i].w.tally[ORC_T_STEPS];
         stats[1] += args[i].dwells;
         stats[2] += args[i].aborted;
         if (args[i].w.status) status = args[i].w.status;
     }
-    free(th); free(args); free(tl); free(tb); free(tp); free(te);
+    free(th); free(args); free(tl); free(tb); free(tp); free(te); free(tlk);
     return status;
 }
 

@@ -101,3 +101,35 @@ def test_grey_medium_diffuses_like_the_fick_gaussian():
         dz = 2.0 * w.R / w.n[0]
         assert l1_chain <= 0.2 * (dz / sig[q]) ** 2 + 1e-3, (q, l1_chain)
         assert l1_mc <= l1_chain + 4.0 * np.sqrt(2.0 * w.n[0] / (np.pi * n)), (q, l1_mc)
+
+
+@pytest.mark.parametrize("w,t_edges,grad", [
+    (W.TINY, [0.0, 0.3, 1.0, 3.0], True),
+    (W.SMALL, [0.0, 1.0, 3.0, 10.0], True),
+    (W.SMALL, [0.0, 1.0, 3.0, 10.0], False),
+], ids=["tiny_gradient", "small_gradient", "small_uniform"])
+def test_leak_optical_depths_follow_the_chain(w, t_edges, grad):
+    """eq. a_estimator: per cell face and step, the summed optical depth k dl of
+    the packets leaking out of and into the cell, dl the dwell that ended in
+    the leak, k the cell's opacity at the bin it leaves / enters.  The
+    chain's expectation P(f|s) (int p_s du - int p_s(u) exp(-K_s (t_end - u)) du)
+    counts every dwell from the later of its previous jump and the step's start
+    (a fresh dwell per step).  A density gradient makes the entered cell's k
+    differ from the left one's.  Batch means of 20 disjoint packet sets give
+    the standard errors (t with 19 degrees of freedom)."""
+    n_rel = np.linspace(0.5, 2.0, w.ncell) if grad else None
+    g = C.Grid(w, n_rel=n_rel)
+    t = g.table()
+    te = np.asarray(t_edges)
+    _, _, _, lk, _ = A.chain_time(w, t, te, leaks=True)
+    B, m = 20, 3000
+    runs = np.stack([C.walk_time(g, t, w.seed, b * m, m, te, leaks=True)["leak"] / m for b in range(B)])
+    mean = runs.mean(axis=0)
+    se = runs.std(axis=0, ddof=1) / np.sqrt(B)
+    for k in range(len(te) - 1):
+        sel = (lk[k] >= 0.02 * lk[k].max()) & (se[k] > 0)
+        z = (mean[k][sel] - lk[k][sel]) / se[k][sel]
+        assert np.abs(z).max() < 6.0, (k, np.abs(z).max())
+        assert int((np.abs(z) > 3.5).sum()) <= max(1, int(np.ceil(0.02 * z.size))), (k, z)
+        # all entries together, the small ones included
+        assert abs(mean[k].sum() - lk[k].sum()) <= 5.0 * np.sqrt((se[k] ** 2).sum()), k
