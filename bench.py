@@ -447,7 +447,7 @@ def _learned_vs_plain(R, torch, n=64, brick=16, margin=1, J=64, x_max=64.0, tau0
             "speedup_at_equal_l1": t_e / t_l, "reference_packets": 4 * npk}
 
 
-def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm=0):
+def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm=0, with_leaks=False):
     """A flash of npk packets advanced through constant time steps, one launch
     of the time-dependent walk per step (Sec. 2.3; eq. E_estimator), timed with
     CUDA events around all launches (a warm-up pass over the first steps runs
@@ -463,6 +463,9 @@ def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm
     bins = torch.zeros((nt, S), dtype=torch.int64, device=prob.device)
     path = torch.zeros((nt, S), dtype=torch.int64, device=prob.device)
     counts = torch.zeros((nt, 4), dtype=torch.int64, device=prob.device)
+    nf = 2 * w.ndim
+    leak = torch.zeros((nt, w.ncell * nf * 2), dtype=torch.float64, device=prob.device)
+    use_leak = [False]
 
     def steps(k_end):
         for k in range(k_end):
@@ -470,7 +473,7 @@ def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm
                             ctas_per_sm)
             R.time_step_launch(prob.grid, prob.table.data_ptr(), st, state.data_ptr(), state.numel(),
                                prob.tally.data_ptr(), prob.tally.numel() * 8, bins[k].data_ptr(), path[k].data_ptr(),
-                               counts[k].data_ptr(), s)
+                               counts[k].data_ptr(), s, leak[k].data_ptr() if use_leak[0] else 0)
 
     steps(min(nt, 4))  # warm-up
     for b in (bins, path, counts):
@@ -489,6 +492,26 @@ def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm
            "ms_per_time_step": 1e3 * dt / nt, "packet_steps_per_s": npk * nt / dt, "transitions_per_s": tr / dt,
            "dwells_per_s": dw / dt, "transitions_per_packet": tr / npk, "escaped": int(c[:, 0].sum()),
            "alive_at_end": int(c[-1, 3]), "launches": nt}
+    if with_leaks:
+        # the same run with the leak tally of eq. a_estimator: its cost, and the
+        # net acceleration direction sum_f (out - in) n_f of the cells (slab:
+        # faces -z, +z) at the last mark
+        for b in (bins, path, counts):
+            b.zero_()
+        prob.reset()
+        use_leak[0] = True
+        torch.cuda.synchronize()
+        a0.record(torch.cuda.current_stream())
+        steps(nt)
+        a1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        dtl = a0.elapsed_time(a1) / 1e3
+        lk = leak.cpu().numpy().reshape(nt, w.ncell, nf, 2)[-1]
+        acc = (lk[:, 1, 0] - lk[:, 1, 1]) - (lk[:, 0, 0] - lk[:, 0, 1])
+        zc = w.cell_centres()[:, 0]
+        outward = float(np.mean(np.sign(acc[np.abs(zc) > 0.1 * w.R]) == np.sign(zc[np.abs(zc) > 0.1 * w.R])))
+        out["with_leak_estimator"] = {"s": dtl, "overhead": dtl / dt - 1.0,
+                                      "share_of_cells_accelerated_outward": outward}
     ks = [int(round(m / (t_edges[1] - t_edges[0]))) - 1 for m in marks]
     b = bins.cpu().numpy()
     pth = path.cpu().numpy().astype(np.float64)
@@ -533,7 +556,7 @@ def _time_p2(R, torch, npk=10_000_000, t_frac=0.32):
     t_diff = w.atau0_nominal ** (1.0 / 3.0) * w.R
     te = W.time_edges(1e-3 * t_diff, t_frac * t_diff)
     marks = [f * t_diff for f in (0.01, 0.02, 0.04, 0.08, 0.16, 0.32) if f <= t_frac + 1e-9]
-    return _time_dependent(R, torch, w, npk, te, "slab", marks)
+    return _time_dependent(R, torch, w, npk, te, "slab", marks, with_leaks=True)
 
 
 def _extras(R, torch, only=None):

@@ -369,6 +369,16 @@ uint64_t rddmc_time_state_bytes(uint64_t n_packets);
  *              t_begin (the path estimate).
  *   d_counts   device, 4 uint64, accumulated: packets escaped during the step,
  *              dwell draws, transitions, packets in a state at t_end.
+ *   d_leak     device, ncell * 2 ndim * 2 doubles, accumulated, or NULL: the
+ *              leaks of eq. a_estimator.  Entry (cell * 2 ndim + face) * 2 + io
+ *              sums k * dl over the packets that leave the cell through that
+ *              face (io = 0; k of the cell at the bin it leaves, escapes
+ *              included) or enter it through that face (io = 1; k of the cell
+ *              at the bin it enters), dl the dwell that ended in the leak, in
+ *              ticks (2^31 ticks = t_end - t_begin) times k in units of 1/R.
+ *              Faces in the outcome order -x, +x (-y, +y, -z, +z).  The
+ *              acceleration of a cell is proportional to sum over faces of
+ *              (out - in) times the face's outward normal.
  * Errors: RDDMC_ERR_ARG (null or misaligned pointer, a field out of range),
  * RDDMC_ERR_TABLE (table not precomputed), RDDMC_ERR_UNSUPPORTED (hybrid-mode
  * table, or ncell * J >= 2^32), RDDMC_ERR_SIZE (a buffer too small),
@@ -377,7 +387,7 @@ uint64_t rddmc_time_state_bytes(uint64_t n_packets);
  */
 int rddmc_time_step_launch(const rddmc_grid* grid, const void* d_table, const rddmc_time_step* step, void* d_state,
                            size_t state_bytes, void* d_tallies, size_t tally_bytes, uint64_t* d_bins,
-                           uint64_t* d_path, uint64_t* d_counts, void* stream);
+                           uint64_t* d_path, uint64_t* d_counts, double* d_leak, void* stream);
 
 /* ----------------------------------------------------------------- batches
  * Many independent grids ("instances", each built and precomputed as above,

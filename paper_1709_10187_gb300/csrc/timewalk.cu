@@ -27,15 +27,19 @@
 // dwell words of a group come from at most two dwell blocks, the lower one
 // usually the block cached from the group before: two Philox calls per four
 // transitions in all.  Lanes take packets from a global cursor (one atomicAdd
-// per warp) and run at most `chunk` transitions between refills (64 by
+// per warp) and run at most `chunk` transitions between refills (256 by
 // default), so a lane whose packet stopped early in its step takes a new one
 // while long-running packets continue.
 //
 // Tallies: the path and bin estimates go to shared memory when the grid's
 // states fit (ticks as a u32 low word plus a u32 carry count, so every update
 // is a native 32-bit shared atomic, and u32 bin counts; flushed with one
-// atomic per touched state), else straight to global memory; the escape tallies of the
-// walk use the tally buffer's shared-memory staging, as in the persistent walk.
+// atomic per touched state), else straight to global memory; the escape
+// tallies of the walk use the tally buffer's shared-memory staging, as in the
+// persistent walk.  With a leak buffer, the leaks of eq. a_estimator are summed
+// per cell face in FP64 (shared memory when small), in their own kernel
+// instantiation.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -54,6 +58,10 @@ struct TimeParams {
     unsigned long long* bins;        // [ncell * J] packets per state at t_{n+1}
     unsigned long long* path;        // [ncell * J] ticks spent per state during the step
     unsigned long long* counts;      // [4] escaped during the step, dwells, transitions, alive at t_{n+1}
+    double* leak;                    // [ncell * 2 NDIM * 2] k x ticks of leaks out of / into each face, or null
+    float inv_dz;                    // 1 / dz_min: k of a row = tau_row / dz_min
+    int leak_in_smem;
+    int leak_smem_off;               // byte offset of the leak block in dynamic shared memory
     float x_scale;                   // ln 2 * ticks per unit length: dwell ticks = -log2(u) * x_scale / K_s
     int start;                       // every packet starts at the source at t_n
     int n_states;
@@ -69,7 +77,7 @@ __device__ __forceinline__ uint4 trans_block(unsigned long long b, uint32_t pl, 
 
 // MINB: resident 256-thread CTAs per SM the register budget targets (2: no
 // spills, 16 warps per SM; 3: 24 warps with a few spilled registers).
-template <int NDIM, bool SMEM_TALLY, int MINB>
+template <int NDIM, bool SMEM_TALLY, int MINB, bool LEAK>
 __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, const TimeParams T) {
     constexpr int RW = NDIM == 1 ? 1 : 2;  // uint4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -83,6 +91,8 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
     unsigned* s_plo = reinterpret_cast<unsigned*>(s_hist + (P.hist_in_smem ? nhist : 0));  // n_states if SMEM_TALLY
     unsigned* s_phi = s_plo + (SMEM_TALLY ? T.n_states : 0);
     unsigned* s_bins = s_phi + (SMEM_TALLY ? T.n_states : 0);
+    const int n_leak = LEAK ? P.ncell * 2 * NDIM * 2 : 0;
+    double* s_leak = reinterpret_cast<double*>(smem_raw + T.leak_smem_off);  // n_leak if leak_in_smem
 
     for (int i = threadIdx.x; i < kCounters + 8 + kNsb; i += blockDim.x) s_cnt[i] = 0ull;
     if (P.hist_in_smem)
@@ -93,6 +103,8 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
             s_phi[i] = 0u;
             s_bins[i] = 0u;
         }
+    if (LEAK && T.leak_in_smem)
+        for (int i = threadIdx.x; i < n_leak; i += blockDim.x) s_leak[i] = 0.0;
     __syncthreads();
 
     const uint4* rows = P.rows;
@@ -123,10 +135,20 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
         }
     };
 
-    // One transition of the state on word w: every threshold, the outcome's
-    // action, spatial moves with the class lookup, Doppler rebins and escapes.
-    // Returns true when the packet escaped or met an unsupported event.
-    auto generic = [&](unsigned w) -> bool {
+    // Leak of eq. a_estimator through face slot `f` (cell * 2 NDIM + face) of a
+    // packet whose dwell was `ticks`: k of the row times the ticks.
+    auto add_leak = [&](unsigned f, unsigned io, unsigned row, unsigned ticks) {
+        const double v = (double)(__ldg(&P.tau_row[min(row, nr1)]) * T.inv_dz * (float)ticks);
+        const unsigned i = min(2u * f + io, (unsigned)n_leak - 1u);
+        if (T.leak_in_smem) atomicAdd(&s_leak[i], v);
+        else atomicAdd(&T.leak[i], v);
+    };
+
+    // One transition of the state on word w after a dwell of `ticks`: every
+    // threshold, the outcome's action, spatial moves with the class lookup,
+    // Doppler rebins and escapes.  Returns true when the packet escaped or met
+    // an unsupported event.
+    auto generic = [&](unsigned w, unsigned ticks) -> bool {
         const unsigned ri = min(s, nr1);
         const uint4 a = __ldg(&rows[ri * RW]);
         unsigned o = (unsigned)(w >= a.x) + (unsigned)(w >= a.y) + (unsigned)(w >= a.z);
@@ -144,6 +166,7 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
             return true;
         }
         const unsigned face = o - 2u;
+        if (LEAK && act != ACT_TO_MC) add_leak(cell * (2u * NDIM) + face, 0u, ri, ticks);
         if (act == ACT_ESCAPE) {
             const EscapeBins eb = escape_bins<NDIM>(P, cell, bin, face, pid, e, (fl & FLAG_MOVING) != 0u);
             if (NDIM == 3 || (fl & FLAG_MOVING)) e += 5;
@@ -173,6 +196,7 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
         cell = min((face & 1u) ? cell + stride : cell - stride, (unsigned)P.ncell - 1u);
         cls = __ldg(&P.cell_class[cell]);
         s = cls * J + nbin;
+        if (LEAK) add_leak(cell * (2u * NDIM) + (face ^ 1u), 1u, s, ticks);
         return false;
     };
 
@@ -200,7 +224,7 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
             s += (wt >= f.x) ? 1u : 0xffffffffu;
             return 0;
         }
-        return generic(wt) ? 2 : 0;
+        return generic(wt, dt) ? 2 : 0;
     };
 
     auto dwell_word = [&](unsigned long long dd) -> unsigned {
@@ -355,6 +379,9 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
             if (s_hist[i]) atomicAdd(&P.tally[kHistOff + i], s_hist[i]);
     for (int i = threadIdx.x; i < kNsb; i += blockDim.x)
         if (s_sb[i]) atomicAdd(&P.tally[kHistOff + nhist + i], s_sb[i]);
+    if (LEAK && T.leak_in_smem)
+        for (int i = threadIdx.x; i < n_leak; i += blockDim.x)
+            if (s_leak[i] != 0.0) atomicAdd(&T.leak[i], s_leak[i]);
     if (SMEM_TALLY)
         for (int i = threadIdx.x; i < T.n_states; i += blockDim.x) {
             const unsigned long long v = ((unsigned long long)s_phi[i] << 32) | s_plo[i];
@@ -363,18 +390,18 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
         }
 }
 
-template <int NDIM, bool SMEM_TALLY, int MINB>
+template <int NDIM, bool SMEM_TALLY, int MINB, bool LEAK>
 cudaError_t launch_time_minb(const WalkParams& P, const TimeParams& T, int threads, size_t smem, int ctas, int nsm,
                              cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(time_kernel<NDIM, SMEM_TALLY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(time_kernel<NDIM, SMEM_TALLY, MINB, LEAK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     if (!ctas) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, time_kernel<NDIM, SMEM_TALLY, MINB>, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, time_kernel<NDIM, SMEM_TALLY, MINB, LEAK>, threads, smem);
         if (e != cudaSuccess) return e;
     }
     if (ctas < 1) ctas = 1;
-    time_kernel<NDIM, SMEM_TALLY, MINB><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P, T);
+    time_kernel<NDIM, SMEM_TALLY, MINB, LEAK><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P, T);
     return cudaGetLastError();
 }
 
@@ -383,8 +410,13 @@ cudaError_t launch_time(const WalkParams& P, const TimeParams& T, int threads, s
                         cudaStream_t s) {
     // default and ctas_per_sm >= 3: the 24-warp variant (faster on short steps);
     // ctas_per_sm 1 or 2: the spill-free 16-warp one
-    return (ctas == 0 || ctas >= 3) ? launch_time_minb<NDIM, SMEM_TALLY, 3>(P, T, threads, smem, ctas, nsm, s)
-                                    : launch_time_minb<NDIM, SMEM_TALLY, 2>(P, T, threads, smem, ctas, nsm, s);
+    // the leak tally of eq. a_estimator is its own instantiation, so the default
+    // kernel carries none of its registers
+    if (T.leak)
+        return (ctas == 0 || ctas >= 3) ? launch_time_minb<NDIM, SMEM_TALLY, 3, true>(P, T, threads, smem, ctas, nsm, s)
+                                        : launch_time_minb<NDIM, SMEM_TALLY, 2, true>(P, T, threads, smem, ctas, nsm, s);
+    return (ctas == 0 || ctas >= 3) ? launch_time_minb<NDIM, SMEM_TALLY, 3, false>(P, T, threads, smem, ctas, nsm, s)
+                                    : launch_time_minb<NDIM, SMEM_TALLY, 2, false>(P, T, threads, smem, ctas, nsm, s);
 }
 
 }  // namespace
@@ -400,14 +432,15 @@ extern "C" uint64_t rddmc_time_state_bytes(uint64_t n_packets) {
 
 extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, const rddmc_time_step* ts,
                                       void* d_state, size_t state_bytes, void* d_tallies, size_t tally_bytes,
-                                      uint64_t* d_bins, uint64_t* d_path, uint64_t* d_counts, void* stream) {
+                                      uint64_t* d_bins, uint64_t* d_path, uint64_t* d_counts, double* d_leak,
+                                      void* stream) {
     using namespace rddmc;
     if (!g || !d_table || !ts || !d_state || !d_tallies || !d_bins || !d_path || !d_counts) return RDDMC_ERR_ARG;
+    if (((uintptr_t)d_state & 255u) || ((uintptr_t)d_tallies & 7u) || ((uintptr_t)d_bins & 7u) ||
+        ((uintptr_t)d_path & 7u) || ((uintptr_t)d_counts & 7u) || ((uintptr_t)d_leak & 7u))
+        return RDDMC_ERR_ARG;
     if (!g->precomputed) return RDDMC_ERR_TABLE;
     if (g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
-    if (((uintptr_t)d_state & 255u) || ((uintptr_t)d_tallies & 7u) || ((uintptr_t)d_bins & 7u) ||
-        ((uintptr_t)d_path & 7u) || ((uintptr_t)d_counts & 7u))
-        return RDDMC_ERR_ARG;
     if (ts->n_packets < 1 || ts->n_packets >= (1ull << 62)) return RDDMC_ERR_ARG;
     if (!(std::isfinite(ts->t_begin) && std::isfinite(ts->t_end) && ts->t_end > ts->t_begin)) return RDDMC_ERR_ARG;
     if (ts->chunk < 0 || ts->chunk % 4 || ts->chunk > (1 << 20)) return RDDMC_ERR_ARG;
@@ -439,6 +472,10 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
     T.counts = (unsigned long long*)d_counts;
     T.x_scale = (float)(0.69314718055994530942 * (double)kTicks / (ts->t_end - ts->t_begin));
     T.start = ts->start;
+    T.leak = d_leak;
+    double dzmin = 2.0 * g->R / g->n[0];
+    for (int a = 1; a < g->ndim; ++a) dzmin = std::min(dzmin, 2.0 * g->R / g->n[a]);
+    T.inv_dz = (float)(1.0 / dzmin);
     T.n_states = (int)std::min<uint64_t>((uint64_t)g->ncell * g->J, 0x7fffffffull);
 
     int dev = 0, nsm = 0;
@@ -451,6 +488,14 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
     // counts: a CTA walks fewer than 2^32 packets per step)
     const bool smem_path = smem + (size_t)T.n_states * 12 <= kSmemTallyMax && ts->n_packets < (1ull << 32);
     if (smem_path) smem += (size_t)T.n_states * 12;
+    // the leak block (eq. a_estimator) in shared memory when it is small
+    const size_t leak_bytes = d_leak ? (size_t)g->ncell * 2 * g->ndim * 2 * 8 : 0;
+    if (d_leak && leak_bytes <= 16384) {
+        smem = (smem + 15) & ~(size_t)15;
+        T.leak_smem_off = (int)smem;
+        T.leak_in_smem = 1;
+        smem += leak_bytes;
+    }
     if (cudaMemsetAsync(P.cursor, 0, 8, s) != cudaSuccess) return RDDMC_ERR_CUDA;
     cudaError_t e;
     if (g->ndim == 1)

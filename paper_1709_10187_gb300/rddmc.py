@@ -149,7 +149,7 @@ def lib():
         L.rddmc_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp, sz, vp, ctypes.POINTER(RunOpts),
                                            ctypes.POINTER(ctypes.c_double)]
         L.rddmc_time_state_bytes.argtypes = [u64]
-        L.rddmc_time_step_launch.argtypes = [vp, vp, ctypes.POINTER(TimeStep), vp, sz, vp, sz, vp, vp, vp, vp]
+        L.rddmc_time_step_launch.argtypes = [vp, vp, ctypes.POINTER(TimeStep), vp, sz, vp, sz, vp, vp, vp, vp, vp]
         L.rddmc_status_string.argtypes = [i32]
         L.rddmc_status_string.restype = ctypes.c_char_p
         L.rddmc_version.argtypes = []
@@ -241,12 +241,13 @@ def time_state_bytes(n_packets: int) -> int:
 
 
 def time_step_launch(grid, d_table: int, step: TimeStep, d_state: int, state_bytes: int, d_tallies: int,
-                     tally_bytes: int, d_bins: int, d_path: int, d_counts: int, stream: int = 0):
+                     tally_bytes: int, d_bins: int, d_path: int, d_counts: int, stream: int = 0, d_leak: int = 0):
     """rddmc_time_step_launch (enqueues one time step; no synchronisation)."""
     _check("rddmc_time_step_launch", lib().rddmc_time_step_launch(
         ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(step), ctypes.c_void_p(d_state),
         int(state_bytes), ctypes.c_void_p(d_tallies), int(tally_bytes), ctypes.c_void_p(d_bins),
-        ctypes.c_void_p(d_path), ctypes.c_void_p(d_counts), ctypes.c_void_p(stream)))
+        ctypes.c_void_p(d_path), ctypes.c_void_p(d_counts), ctypes.c_void_p(d_leak or None),
+        ctypes.c_void_p(stream)))
 
 
 def scatter_samples(grid, d_table: int, x_in: float, seed: int, n: int, d_out: int, stream: int = 0):
@@ -352,13 +353,15 @@ class Problem:
         return self.read()
 
     def time_run(self, n_packets: int, seed: int, t_edges, max_steps: int = 0, chunk: int = 0,
-                 threads_per_cta: int = 0, ctas_per_sm: int = 0) -> dict:
+                 threads_per_cta: int = 0, ctas_per_sm: int = 0, leaks: bool = False) -> dict:
         """A flash of n_packets at the source at t_edges[0], advanced through the
         steps [t_edges[n], t_edges[n+1]], one launch per step.  Returns per step
         n: bins[n, s] (packets in state s = cell * J + bin at t_edges[n+1]),
         path[n, s] (path length spent in s during the step, ticks converted to
-        length), esc[n], dwells[n], transitions[n], alive[n]; and the walk's
-        tallies."""
+        length), esc[n], dwells[n], transitions[n], alive[n]; the walk's
+        tallies; with leaks=True also leak[n, cell, face, io], the optical
+        depths k dl of the leaks out of (io = 0) and into (io = 1) each face
+        (eq. a_estimator)."""
         torch = self.torch
         te = np.asarray(t_edges, dtype=np.float64)
         nt = len(te) - 1
@@ -370,18 +373,25 @@ class Problem:
         bins = torch.zeros((nt, S), dtype=torch.int64, device=self.device)
         path = torch.zeros((nt, S), dtype=torch.int64, device=self.device)
         counts = torch.zeros((nt, 4), dtype=torch.int64, device=self.device)
+        nf = 2 * self.w.ndim
+        leak = torch.zeros((nt, int(self.w.ncell) * nf * 2), dtype=torch.float64, device=self.device) if leaks \
+            else None
         self.reset()
         for n in range(nt):
             st = TimeStep(seed, n_packets, max_steps, float(te[n]), float(te[n + 1]), 1 if n == 0 else 0, chunk,
                           threads_per_cta, ctas_per_sm)
             time_step_launch(self.grid, self.table.data_ptr(), st, state.data_ptr(), state.numel(),
                              self.tally.data_ptr(), self.tally.numel() * 8, bins[n].data_ptr(), path[n].data_ptr(),
-                             counts[n].data_ptr(), self.stream())
+                             counts[n].data_ptr(), self.stream(), leak[n].data_ptr() if leaks else 0)
         c = counts.cpu().numpy().astype(np.uint64)
         ticks = path.cpu().numpy().astype(np.float64)
-        return dict(bins=bins.cpu().numpy().astype(np.uint64), path=ticks * (np.diff(te) / TIME_TICKS)[:, None],
-                    path_ticks=path.cpu().numpy().astype(np.uint64), esc=c[:, 0], dwells=c[:, 1],
-                    transitions=c[:, 2], alive=c[:, 3], tallies=self.read())
+        out = dict(bins=bins.cpu().numpy().astype(np.uint64), path=ticks * (np.diff(te) / TIME_TICKS)[:, None],
+                   path_ticks=path.cpu().numpy().astype(np.uint64), esc=c[:, 0], dwells=c[:, 1],
+                   transitions=c[:, 2], alive=c[:, 3], tallies=self.read())
+        if leaks:
+            lk = leak.cpu().numpy() * (np.diff(te) / TIME_TICKS)[:, None]
+            out["leak"] = lk.reshape(nt, int(self.w.ncell), nf, 2)
+        return out
 
     def scatter(self, x_in: float, seed: int, n: int):
         out = self.torch.empty(n, dtype=self.torch.float32, device=self.device)

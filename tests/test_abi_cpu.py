@@ -111,10 +111,13 @@ def test_time_step_validation_without_a_gpu():
         st = R.TimeStep(1, 1000, 0, 0.0, 1.0, 1, 0, 0, 0)
         for k, v in kw.items():
             setattr(st, k, v)
-        return R.lib().rddmc_time_step_launch(g, fake, st, fake, 1 << 30, fake, 1 << 20, fake, fake, fake, None)
+        return R.lib().rddmc_time_step_launch(g, fake, st, fake, 1 << 30, fake, 1 << 20, fake, fake, fake, None,
+                                              None)
 
     assert call() == R.ERR_TABLE          # no precompute on this grid
     st = R.TimeStep(1, 1000, 0, 0.0, 1.0, 1, 0, 0, 0)
-    assert R.lib().rddmc_time_step_launch(g, fake, st, None, 1 << 30, fake, 1 << 20, fake, fake, fake, None) \
-        == R.ERR_ARG
+    assert R.lib().rddmc_time_step_launch(g, fake, st, None, 1 << 30, fake, 1 << 20, fake, fake, fake, None,
+                                          None) == R.ERR_ARG
+    assert R.lib().rddmc_time_step_launch(g, fake, st, fake, 1 << 30, fake, 1 << 20, fake, fake, fake, fake + 4,
+                                          None) == R.ERR_ARG   # misaligned leak buffer
     R.destroy_grid(g)

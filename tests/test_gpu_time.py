@@ -207,3 +207,51 @@ def test_resonant_slab_profile_follows_the_paper_fit():
         assert abs(slope / fit - 1.0) <= 0.15, (f, slope, fit)
     print("\n(t/t_diff, measured slope, paper fit):", out)
     p.close()
+
+
+@pytest.mark.parametrize("w,t_edges,grad", [
+    (W.TINY, [0.0, 0.3, 1.0, 3.0], True),
+    (W.SMALL, [0.0, 1.0, 3.0, 10.0], False),
+    (W.SPHERE8_V, [0.0, 0.3, 1.0, 3.0], False),
+], ids=["tiny_gradient", "small", "sphere_moving"])
+def test_leak_estimator_tracks_the_oracle(w, t_edges, grad):
+    """eq. a_estimator: the device's k dl sums per cell face (FP32 k and dwell,
+    FP64 sums) against the FP64 oracle on the same packets; the packets whose
+    clock flips a transition across a step end move a few leaks between steps."""
+    n = 20_000
+    n_rel = np.linspace(0.5, 2.0, w.ncell) if grad else None
+    p = R.Problem(w, n_rel=n_rel)
+    g = p.time_run(n, w.seed, t_edges, leaks=True)
+    og = C.Grid(w, n_rel=n_rel)
+    o = C.walk_time(og, og.table(), w.seed, 0, n, t_edges, leaks=True)
+    for k in range(len(t_edges) - 1):
+        rel = float(np.abs(g["leak"][k] - o["leak"][k]).sum() / o["leak"][k].sum())
+        assert rel <= 2e-3, (k, rel)
+    # the estimator leaves the other tallies alone
+    b = p.time_run(n, w.seed, t_edges)
+    assert np.array_equal(b["bins"], g["bins"]) and np.array_equal(b["path_ticks"], g["path_ticks"])
+    p.close()
+
+
+def test_leak_estimator_follows_the_chain():
+    """Batch means of 20 independent device runs against the chain's expected
+    leak optical depths, on a slab with a density gradient (t with 19 degrees
+    of freedom, as for the oracle's pin)."""
+    w = W.TINY
+    te = np.array([0.0, 0.3, 1.0, 3.0])
+    n_rel = np.linspace(0.5, 2.0, w.ncell)
+    _, _, _, lk, _ = A.chain_time(w, C.Grid(w, n_rel=n_rel).table(), te, leaks=True)
+    p = R.Problem(w, n_rel=n_rel)
+    B, m = 20, 50_000
+    runs = np.stack([p.time_run(m, 0xABC0 + b, te, leaks=True)["leak"] / m for b in range(B)])
+    mean = runs.mean(axis=0)
+    se = runs.std(axis=0, ddof=1) / np.sqrt(B)
+    for k in range(len(te) - 1):
+        sel = (lk[k] >= 0.02 * lk[k].max()) & (se[k] > 0)
+        z = (mean[k][sel] - lk[k][sel]) / se[k][sel]
+        assert np.abs(z).max() < 6.0, (k, np.abs(z).max())
+        # a face's out-entry and its neighbour's in-entry sum the same leaks, so
+        # exceedances come in pairs
+        assert int((np.abs(z) > 3.5).sum()) <= 2 * max(1, int(np.ceil(0.02 * z.size))), (k, z)
+        assert abs(mean[k].sum() - lk[k].sum()) <= 5.0 * np.sqrt((se[k] ** 2).sum()), k
+    p.close()

@@ -130,6 +130,8 @@ def test_leak_optical_depths_follow_the_chain(w, t_edges, grad):
         sel = (lk[k] >= 0.02 * lk[k].max()) & (se[k] > 0)
         z = (mean[k][sel] - lk[k][sel]) / se[k][sel]
         assert np.abs(z).max() < 6.0, (k, np.abs(z).max())
-        assert int((np.abs(z) > 3.5).sum()) <= max(1, int(np.ceil(0.02 * z.size))), (k, z)
+        # a face's out-entry and its neighbour's in-entry sum the same leaks, so
+        # exceedances come in pairs
+        assert int((np.abs(z) > 3.5).sum()) <= 2 * max(1, int(np.ceil(0.02 * z.size))), (k, z)
         # all entries together, the small ones included
         assert abs(mean[k].sum() - lk[k].sum()) <= 5.0 * np.sqrt((se[k] ** 2).sum()), k
