@@ -250,7 +250,7 @@ def leak_matrices(w, table):
                 for jn, pj in ((j + m, pr), (j + m + 1, 1.0 - pr)):
                     jn = min(max(jn, 0), J - 1)
                     Lin[s, nb * nf + (f ^ 1)] += p * pj * k[nb * J + jn]
-    return Lout, Lin, q[:, 2:]
+    return Lout, Lin, q[:, 2:2 + nf]
 
 
 def chain_time(w, table, t_edges, edges=None, leaks=False):

@@ -23,6 +23,7 @@ class OrcGrid(ctypes.Structure):
         ("R", ctypes.c_double), ("tau0", ctypes.c_double), ("T", ctypes.c_double),
         ("tau_ddmc", ctypes.c_double), ("lam", ctypes.c_double), ("f_mu", ctypes.c_double),
         ("edges", ctypes.c_void_p), ("n_rel", ctypes.c_void_p), ("v", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+        ("dust_abs", ctypes.c_double), ("dust_scat", ctypes.c_double),
     ]
 
 
@@ -114,7 +115,8 @@ def vth_kms(T: float) -> float:
 class Grid:
     """An oracle grid built from a workload; keeps the numpy buffers alive."""
 
-    def __init__(self, w, hybrid=False, tau_ddmc=5.0, lam=0.7104, f_mu=0.5, n_rel=None, edges=None):
+    def __init__(self, w, hybrid=False, tau_ddmc=5.0, lam=0.7104, f_mu=0.5, n_rel=None, edges=None, dust_abs=0.0,
+                 dust_scat=0.0):
         self.w = w
         e = w.edges() if edges is None else edges
         self.edges = np.ascontiguousarray(e, dtype=np.float64)
@@ -131,14 +133,16 @@ class Grid:
         g.R, g.tau0, g.T = w.R, w.tau0, w.T
         g.tau_ddmc, g.lam, g.f_mu = tau_ddmc, lam, f_mu
         g.edges, g.n_rel, g.v, g.mask = (_ptr(self.edges), _ptr(self.n_rel), _ptr(self.v), _ptr(self.mask))
+        g.dust_abs, g.dust_scat = float(dust_abs), float(dust_scat)  # grey dust k R at unit density (Sec. 2.6)
         self.g = g
         self.K = 2 + 2 * w.ndim
+        self.KT = self.K + (1 if dust_abs > 0.0 else 0)  # outcomes, dust absorption last
         self.ncell = w.ncell
         self.J = w.J
 
     def table(self):
         nS = self.ncell * self.J
-        K = self.K
+        K = self.KT  # with dust absorption one more outcome (the last)
         t = dict(
             thr=np.zeros(nS * (K - 1), dtype=np.uint32), flags=np.zeros(nS, dtype=np.uint32),
             rebin_m=np.zeros(self.ncell * 2 * self.w.ndim, dtype=np.int32),
@@ -155,14 +159,16 @@ class Grid:
 
 NSB = 64          # impact-parameter bins over b/R in [0, 1.28)
 SB_MAX = 1.28
-TALLY_NAMES = ["emitted", "escaped", "aborted", "steps", "mc_events", "conversions", "clamps", "event_draws"]
+TALLY_NAMES = ["emitted", "escaped", "aborted", "steps", "mc_events", "conversions", "clamps", "event_draws",
+               "absorbed"]
+_T_FACE, _T_HIST = 9, 15
 
 
 def unpack_tally(t: np.ndarray, J: int) -> dict:
     d = {name: int(t[i]) for i, name in enumerate(TALLY_NAMES)}
-    d["faces"] = t[8:14].astype(np.uint64).copy()
-    d["hist"] = t[14:14 + J + 2].astype(np.uint64).copy()
-    d["sb"] = t[14 + J + 2:14 + J + 2 + NSB].astype(np.uint64).copy()
+    d["faces"] = t[_T_FACE:_T_FACE + 6].astype(np.uint64).copy()
+    d["hist"] = t[_T_HIST:_T_HIST + J + 2].astype(np.uint64).copy()
+    d["sb"] = t[_T_HIST + J + 2:_T_HIST + J + 2 + NSB].astype(np.uint64).copy()
     return d
 
 

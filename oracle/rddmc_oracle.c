@@ -169,6 +169,8 @@ typedef struct orc_grid {
     const double* n_rel;  /* per-cell density scale, NULL = 1 */
     const double* v;      /* per-cell bulk velocity in km/s, 3 per cell, NULL = static */
     const uint8_t* mask;  /* per-cell 1 = medium, 0 = vacuum, NULL = all medium */
+    double dust_abs;      /* dust absorption k_a R at unit density (grey; Sec. 2.6), 0 = none */
+    double dust_scat;     /* dust scattering k_s R at unit density (grey), added to k_ij */
 } orc_grid;
 
 /* Actions stored two bits per outcome in the flags word. */
@@ -181,6 +183,10 @@ typedef struct orc_grid {
 
 static int64_t orc_ncell(const orc_grid* g) { return (int64_t)g->n[0] * g->n[1] * g->n[2]; }
 static int orc_nout(const orc_grid* g) { return 2 + 2 * g->ndim; }
+/* Dust absorption is one more outcome, K = orc_nout, after the leakage
+ * outcomes: thresholds per state orc_nthr = K - 1 (+1 with absorption). */
+static int orc_dusty(const orc_grid* g) { return g->dust_abs > 0.0; }
+static int orc_nthr(const orc_grid* g) { return orc_nout(g) - 1 + orc_dusty(g); }
 
 static int orc_in_medium(const orc_grid* g, const int idx[3]) {
     for (int a = 0; a < 3; ++a)
@@ -241,7 +247,8 @@ static uint32_t orc_quantise(double C) {
 int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* rebin_m,
                     uint32_t* rebin_thr, double* k_out, double* rate_out) {
     if (g->ndim != 1 && g->ndim != 3) return -1;
-    const int J = g->J, K = orc_nout(g);
+    if (g->dust_abs < 0.0 || g->dust_scat < 0.0 || (orc_dusty(g) && g->hybrid)) return -1;
+    const int J = g->J, K = orc_nout(g), NT = orc_nthr(g), KT = NT + 1;
     const int64_t nc = orc_ncell(g);
     const double a = orc_damping(g->T);
     double* phi = (double*)malloc(sizeof(double) * J);
@@ -259,6 +266,10 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
         int idx[3];
         orc_idx_of(g, c, idx);
         const double k0c = orc_k0(g, c);
+        /* grey dust per unit length: scattering adds to every k_ij, absorption
+         * is its own process (Sec. 2.6) */
+        const double nrel = g->n_rel ? g->n_rel[c] : 1.0;
+        const double ksc = g->dust_scat / g->R * nrel, kac = g->dust_abs / g->R * nrel;
         int moving = 0;
         if (g->v)
             for (int ax = 0; ax < 3; ++ax) moving |= (g->v[3 * c + ax] != 0.0);
@@ -278,16 +289,16 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
         for (int j = 0; j < J; ++j) {
             const int64_t s = c * J + j;
             const double dxj = g->edges[j + 1] - g->edges[j];
-            const double k = k0c * phi[j];
-            double rate[8] = {0};
-            unsigned act[8] = {0};
+            const double k = k0c * phi[j] + ksc;
+            double rate[9] = {0};
+            unsigned act[9] = {0};
             int thin = g->hybrid && (k * dzmin < g->tau_ddmc);
             /* frequency leakage, eq. x-leakage; no flux beyond the grid ends */
             for (int sd = 0; sd < 2; ++sd) {
                 int jn = j + (sd ? 1 : -1);
                 if (jn < 0 || jn >= J) { rate[sd] = 0.0; act[sd] = ORC_ACT_MOVE; continue; }
                 double dxn = g->edges[jn + 1] - g->edges[jn];
-                double kn = k0c * phi[jn];
+                double kn = k0c * phi[jn] + ksc;
                 rate[sd] = 1.0 / (dxj * (dxj / k + dxn / kn));
                 act[sd] = (g->hybrid && kn * dzmin < g->tau_ddmc) ? ORC_ACT_TO_MC : ORC_ACT_MOVE;
             }
@@ -318,19 +329,20 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
                         phin = (m < nmemo) ? memo_phi[m][j]
                                            : orc_bin_mean_H(a, g->edges[j] + delta, g->edges[j + 1] + delta);
                     }
-                    double knb = orc_k0(g, nb) * phin;
+                    double knb = orc_k0(g, nb) * phin + g->dust_scat / g->R * (g->n_rel ? g->n_rel[nb] : 1.0);
                     double dznb = dz;
                     if (g->hybrid && knb * dznb < g->tau_ddmc) { rate[o] = r_bnd; act[o] = ORC_ACT_TO_MC; continue; }
                     rate[o] = 1.0 / (3.0 * dz) * 2.0 / (k * dz + knb * dznb);
                     act[o] = (delta != 0.0) ? ORC_ACT_REBIN : ORC_ACT_MOVE;
                 }
             }
+            if (orc_dusty(g)) rate[K] = kac;  /* absorption, the last outcome */
             double tot = 0.0;
-            for (int o = 0; o < K; ++o) tot += rate[o];
+            for (int o = 0; o < KT; ++o) tot += rate[o];
             double C = 0.0;
-            for (int o = 0; o < K - 1; ++o) {
+            for (int o = 0; o < NT; ++o) {
                 C += rate[o] / tot;
-                thr[s * (K - 1) + o] = orc_quantise(C);
+                thr[s * NT + o] = orc_quantise(C);
             }
             uint32_t fl = 0;
             for (int o = 0; o < K; ++o) fl |= (act[o] & 3u) << (2 * o);
@@ -339,7 +351,7 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
             flags[s] = fl;
             if (k_out) k_out[s] = k;
             if (rate_out)
-                for (int o = 0; o < K; ++o) rate_out[s * K + o] = rate[o];
+                for (int o = 0; o < KT; ++o) rate_out[s * KT + o] = rate[o];
         }
     }
     free(phi);
@@ -361,8 +373,9 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
 #define ORC_T_CONVERSIONS 5
 #define ORC_T_CLAMPS 6
 #define ORC_T_EVENT_DRAWS 7
-#define ORC_T_FACE 8
-#define ORC_T_HIST 14
+#define ORC_T_ABSORBED 8
+#define ORC_T_FACE 9
+#define ORC_T_HIST 15
 #define ORC_NSB 64          /* impact-parameter bins over b/R in [0, 1.28); larger b in the last bin */
 #define ORC_SB_MAX 1.28
 
@@ -758,14 +771,14 @@ typedef struct orc_pstate {
     int idx[3];
     int j;
     uint64_t steps, e;
-    int done;      /* 0 in flight, 1 escaped, 2 aborted, 3 met an MC state */
+    int done;      /* 0 in flight, 1 escaped, 2 aborted, 3 met an MC state, 4 absorbed by dust */
 } orc_pstate;
 
 /* Advance packet pk by at most `limit` transitions (stopping at escape or at
  * the watchdog), accumulating tallies into t. */
 static void orc_advance(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t limit, uint64_t* t) {
     const orc_grid* g = A->g;
-    const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim;
+    const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim, NT = orc_nthr(g), KT = NT + 1;
     int64_t c = orc_cell_of(g, P->idx);
     if (A->flags[c * J + P->j] & ORC_FLAG_THIN) {
         /* only a source state can be thin: the packet starts as MC */
@@ -790,14 +803,15 @@ static void orc_advance(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t l
             /* categorical draw: outcome o iff thr[o-1] <= w < thr[o] */
             uint32_t w = orc_word(A->seed, pk, ORC_TRANS, P->steps);
             o = 0;
-            while (o < K - 1 && w >= A->thr[s * (K - 1) + o]) ++o;
+            while (o < NT && w >= A->thr[s * NT + o]) ++o;
         } else {
-            /* eq. l_min_2: dl_X = -ln(xi)/k_X for every process; eq. l_min_1: execute the smallest */
+            /* eq. l_min_2: dl_X = -ln(xi)/k_X for every process (absorption
+             * included); eq. l_min_1: execute the smallest */
             double best = INFINITY;
             o = -1;
-            for (int q = 0; q < K; ++q) {
-                double xi = orc_unif(orc_word(A->seed, pk, ORC_TRANS, 8 * P->steps + q));
-                double kx = A->rate[s * K + q];
+            for (int q = 0; q < KT; ++q) {
+                double xi = orc_unif(orc_word(A->seed, pk, ORC_TRANS, 16 * P->steps + q));
+                double kx = A->rate[s * KT + q];
                 if (kx <= 0.0) continue;
                 double dl = -log(xi) / kx;
                 if (dl < best) { best = dl; o = q; }
@@ -805,6 +819,7 @@ static void orc_advance(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t l
         }
         P->steps++;
         t[ORC_T_STEPS]++;
+        if (o == K) { t[ORC_T_ABSORBED]++; P->done = 4; return; }  /* absorbed by dust (Sec. 2.6) */
         unsigned act = (A->flags[s] >> (2 * o)) & 3u;
         if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, P->j, o, pk, &P->e, t); P->done = 1; return; }
         if (act == ORC_ACT_TO_MC) {
@@ -941,18 +956,20 @@ typedef struct orc_time_args {
  * dwell dl that ended in it is added for the cell it leaves (index 0 of its
  * face) and, unless it escapes, for the cell it enters with that cell's k at
  * the new bin (index 1 of the face it enters through; eq. a_estimator).
- * Returns 1 if the packet escaped, -1 if it met an MC state, 0 otherwise. */
+ * Returns 1 if the packet escaped, 2 if dust absorbed it, -1 if it met an MC
+ * state, 0 otherwise. */
 static int orc_time_transition(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t* t, double dl,
                                double* leak) {
     const orc_grid* g = A->g;
-    const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim;
+    const int J = g->J, K = orc_nout(g), nf = 2 * g->ndim, NT = orc_nthr(g);
     int64_t c = orc_cell_of(g, P->idx);
     const int64_t s = c * J + P->j;
     uint32_t w = orc_word(A->seed, pk, ORC_TRANS, P->steps);
     int o = 0;
-    while (o < K - 1 && w >= A->thr[s * (K - 1) + o]) ++o;
+    while (o < NT && w >= A->thr[s * NT + o]) ++o;
     P->steps++;
     t[ORC_T_STEPS]++;
+    if (o == K) { t[ORC_T_ABSORBED]++; return 2; }  /* absorbed by dust (Sec. 2.6) */
     unsigned act = (A->flags[s] >> (2 * o)) & 3u;
     if (act == ORC_ACT_TO_MC) return -1;
     if (o >= 2 && leak) leak[(c * nf + (o - 2)) * 2 + 0] += A->k[s] * dl;
@@ -978,7 +995,7 @@ static void* orc_time_thread(void* vp) {
     orc_time_args* T = (orc_time_args*)vp;
     orc_walk_args* A = &T->w;
     const orc_grid* g = A->g;
-    const int J = g->J, K = orc_nout(g);
+    const int J = g->J, KT = orc_nthr(g) + 1;
     const int64_t S = (int64_t)orc_ncell(g) * J;
     const size_t L = (size_t)orc_ncell(g) * 2 * g->ndim * 2;
     for (uint64_t pk = A->p0; pk < A->p1; ++pk) {
@@ -993,7 +1010,7 @@ static void* orc_time_thread(void* vp) {
                 if (P.steps >= A->max_steps) { T->aborted++; done = 2; break; }
                 const int64_t s = orc_cell_of(g, P.idx) * J + P.j;
                 double ksum = 0.0;
-                for (int q = 0; q < K; ++q) ksum += A->rate[s * K + q];
+                for (int q = 0; q < KT; ++q) ksum += A->rate[s * KT + q];  /* absorption included */
                 /* eq. l_min_2: the smallest of the exponential leakage lengths is Exp(sum k) */
                 const double dl = -log(orc_unif(orc_word(A->seed, pk, ORC_TIME, d++))) / ksum;
                 T->dwells++;
@@ -1007,6 +1024,7 @@ static void* orc_time_thread(void* vp) {
                 tau += dl;
                 int r = orc_time_transition(A, pk, &P, A->tally, dl, T->leak ? T->leak + (size_t)n * L : NULL);
                 if (r == 1) { T->esc[n]++; done = 1; break; }
+                if (r == 2) { done = 4; break; }
                 if (r == -1) { A->status = -2; done = 3; break; }
             }
         }

@@ -1,0 +1,117 @@
+"""Pins of the oracle's dust absorption (Sec. 2.6, the probabilistic method).
+
+Grey dust adds a scattering coefficient k_s to every k_ij of the leakage
+coefficients and an absorption process of coefficient k_a that competes with
+the leakage processes (one more exponential in eq. l_min_1/2, so one more
+outcome of the categorical draw, taken last).
+
+* A grey slab (one frequency bin) is a symmetric random walk on n cells with
+  killing: interior cells move left or right with probability p = r/(2r+k_a)
+  each (r = 1/(3 k dz^2), eq. z-leakage), boundary cells escape with the rate
+  r_b = 2/(3 dz (k dz + 2 lambda)).  The escape probability from the centre has
+  the closed form f = e_1 / (cosh(m theta) - p_1 cosh((m-1) theta)), cosh theta
+  = 1/(2p), m = (n-1)/2, with e_1, p_1 the boundary cell's escape and inward
+  probabilities (the two-term solution f_i = A cosh(theta (i - c)) of
+  f_i = p (f_{i-1} + f_{i+1}) with the boundary equation).
+* With frequency diffusion the walk is pinned to the exact absorbing chain:
+  escapes per bin, the absorbed fraction and the mean transition count.
+"""
+import numpy as np
+import pytest
+
+from oracle import analytic as A
+from oracle import coracle as C
+from paper_1709_10187_gb300 import workloads as W
+
+GREY21 = W.Workload("grey_slab_21x1", 1, (21, 1, 1), 1, -5.0, 5.0, 200.0, 1.0e4, 200_000, 0x5EED0D01)
+
+
+def _closed_form_escape(w, k, ka, lam=0.7104):
+    dz = 2.0 * w.R / w.n[0]
+    r = 1.0 / (3.0 * k * dz * dz)
+    rb = 2.0 / (3.0 * dz * (k * dz + 2.0 * lam))
+    p = r / (2.0 * r + ka)
+    e1 = rb / (rb + r + ka)
+    p1 = r / (rb + r + ka)
+    th = np.arccosh(1.0 / (2.0 * p))
+    m = (w.n[0] - 1) // 2
+    return e1 / (np.cosh(m * th) - p1 * np.cosh((m - 1) * th))
+
+
+def test_dust_scattering_adds_to_every_opacity():
+    w = W.SMALL
+    t0 = C.Grid(w).table()
+    n_rel = np.linspace(0.5, 2.0, w.ncell)
+    t1 = C.Grid(w, dust_scat=30.0, n_rel=n_rel).table()
+    t2 = C.Grid(w, n_rel=n_rel).table()
+    ks = np.repeat(30.0 / w.R * n_rel, w.J)
+    assert np.allclose(t1["k"] - t2["k"], ks, rtol=1e-12, atol=1e-12)
+    assert not np.array_equal(t0["thr"], t1["thr"])
+    # no absorption: no extra outcome
+    assert t1["thr"].shape == t0["thr"].shape and t1["rate"].shape == t0["rate"].shape
+
+
+@pytest.mark.parametrize("tau_a", [0.05, 0.5, 3.0])
+def test_grey_slab_escape_fraction_has_the_closed_form(tau_a):
+    w = GREY21
+    g = C.Grid(w, dust_abs=tau_a, dust_scat=5.0)
+    t = g.table()
+    k = float(t["k"][w.n[0] // 2])
+    assert k == pytest.approx(float(C.Grid(w).table()["k"][w.n[0] // 2]) + 5.0 / w.R, rel=1e-12)
+    f = _closed_form_escape(w, k, tau_a / w.R)
+    ch = A.chain_solve(w, t)
+    assert ch["escape_total"] == pytest.approx(f, rel=1e-6, abs=1e-9)
+    n = w.packets
+    r = C.walk(g, t, w.seed, 0, n)
+    assert r["emitted"] == n and r["escaped"] + r["absorbed"] == n and r["aborted"] == 0
+    z = (r["escaped"] - n * f) / np.sqrt(n * f * (1.0 - f))
+    assert abs(z) < 5.0, (r["escaped"], n * f)
+    # mean transitions (absorption is a transition) against the chain
+    assert abs(r["steps"] / n - ch["steps_mean"]) <= 5.0 * np.sqrt(ch["steps_var"] / n)
+
+
+def test_dusty_walk_follows_the_absorbing_chain():
+    w = W.SMALL.with_(packets=100_000)
+    g = C.Grid(w, dust_abs=0.3, dust_scat=2.0)
+    t = g.table()
+    assert t["thr"].shape[1] == 4 and t["rate"].shape[1] == 5
+    ch = A.chain_solve(w, t)
+    n = w.packets
+    r = C.walk(g, t, w.seed, 0, n)
+    pa = 1.0 - ch["escape_total"]
+    assert 0.05 < pa < 0.95
+    za = (r["absorbed"] - n * pa) / np.sqrt(n * pa * (1.0 - pa))
+    assert abs(za) < 5.0, (r["absorbed"], n * pa)
+    zmax, frac, pval = A.compare_counts_to_probs(r["hist"], ch["hist"], n)
+    assert zmax < 5.0 and frac <= 0.02 and pval > 1e-3, (zmax, frac, pval)
+    assert abs(r["steps"] / n - ch["steps_mean"]) <= 5.0 * np.sqrt(ch["steps_var"] / n)
+    # the literal competing exponentials (absorption one of them) agree in law
+    rl = C.walk(g, t, w.seed + 1, 0, n, literal=True)
+    zl = (rl["absorbed"] - n * pa) / np.sqrt(n * pa * (1.0 - pa))
+    assert abs(zl) < 5.0, (rl["absorbed"], n * pa)
+
+
+def test_dusty_time_walk_follows_the_chain():
+    """With dust the dwell rate K_s includes k_a (absorption competes in time
+    as well); occupancies per step against the chain."""
+    w = W.TINY
+    # k_a = 10 per R, comparable to the wing states' leakage rates (K_s from 9
+    # to 1e4), so that the dwell rate's absorption term matters
+    g = C.Grid(w, dust_abs=10.0)
+    t = g.table()
+    te = np.array([0.0, 0.05, 0.15, 0.4])
+    n = 40_000
+    r = C.walk_time(g, t, w.seed, 0, n, te)
+    occ, path, lost = A.chain_time(w, t, te)
+    for k in range(len(te) - 1):
+        e = occ[k] * n
+        sel = e >= 20.0
+        z = (r["bins"][k][sel] - e[sel]) / np.sqrt(e[sel] * (1.0 - occ[k][sel]))
+        assert np.abs(z).max() < 5.0, (k, np.abs(z).max())
+    # absorption happens at rate k_a while in a state: its expected count is the
+    # step-integrated occupancy times k_a; the chain's loss per step is escapes
+    # plus absorptions
+    absorbed_exp = float((path.sum(axis=0) * t["rate"][:, -1]).sum())
+    assert abs(r["absorbed"] / n - absorbed_exp) <= 5.0 * np.sqrt(absorbed_exp * (1 - absorbed_exp) / n)
+    done = (r["esc"].sum() + r["absorbed"]) / n
+    assert abs(done - lost.sum()) <= 5.0 * np.sqrt(lost.sum() * (1 - lost.sum()) / n)
