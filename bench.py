@@ -462,7 +462,7 @@ def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm
     state = torch.empty(R.time_state_bytes(npk), dtype=torch.uint8, device=prob.device)
     bins = torch.zeros((nt, S), dtype=torch.int64, device=prob.device)
     path = torch.zeros((nt, S), dtype=torch.int64, device=prob.device)
-    counts = torch.zeros((nt, 4), dtype=torch.int64, device=prob.device)
+    counts = torch.zeros((nt, 5), dtype=torch.int64, device=prob.device)
     nf = 2 * w.ndim
     leak = torch.zeros((nt, w.ncell * nf * 2), dtype=torch.float64, device=prob.device)
     use_leak = [False]

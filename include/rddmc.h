@@ -93,6 +93,13 @@ typedef struct rddmc_grid_desc {
  *   lambda    extrapolation distance of the boundary coefficient (0.7104).
  *   f_mu      flux directionality factor of eq. velocity-shift (1/2 isotropic).
  *   mode      RDDMC_MODE_DDMC or RDDMC_MODE_HYBRID.
+ *   dust_abs, dust_scat  grey dust (Sec. 2.6, the probabilistic method):
+ *             absorption and scattering optical depths k_a R and k_s R at
+ *             unit density (scaled by each cell's n_rel; >= 0).  Scattering
+ *             adds k_s to every k_ij of the leakage coefficients; absorption
+ *             is one more competing process, the last outcome of every
+ *             state's categorical draw, and an absorbed packet ends (counted
+ *             in rddmc_tallies.absorbed).  dust_abs > 0 requires DDMC mode.
  */
 typedef struct rddmc_leak_params {
     double tau_ddmc;
@@ -100,6 +107,8 @@ typedef struct rddmc_leak_params {
     double f_mu;
     int32_t mode;
     int32_t reserved;
+    double dust_abs;
+    double dust_scat;
 } rddmc_leak_params;
 
 /*
@@ -158,7 +167,8 @@ typedef struct rddmc_sizes {
     uint64_t state_bytes;        /* device state buffer for the n_packets asked for */
     int32_t n_class;             /* row blocks in the table */
     int32_t row_bytes;           /* 16 (slab) or 32 (3D) */
-    int32_t n_outcomes;          /* 4 (slab) or 8 (3D) */
+    int32_t n_outcomes;          /* 4 (slab) or 8 (3D), one more with dust absorption (known after
+                                    rddmc_precompute_leakage) */
     int32_t reserved;
 } rddmc_sizes;
 
@@ -174,6 +184,7 @@ typedef struct rddmc_tallies {
     uint64_t event_draws;  /* words taken from the packets' event streams */
     uint64_t proposals;    /* learned exit proposals taken */
     uint64_t proposed_steps; /* DDMC transitions the proposals stood in for (sampled) */
+    uint64_t absorbed;     /* packets absorbed by dust (Sec. 2.6) */
     int32_t status;        /* RDDMC_OK or a device-side error code */
     int32_t nbins;         /* J; the histogram has J + 2 entries */
     int32_t nfaces;        /* 2 (slab) or 6 (3D) */
@@ -294,7 +305,8 @@ int rddmc_read_tallies(const rddmc_grid* grid, const void* d_tallies, rddmc_tall
 /*
  * rddmc_table_rows -- expand the device table to one row per state (host), for
  * inspection and parity checks.  Synchronises `stream`.
- *   thr    host, ncell * J * (n_outcomes - 1) uint32 cumulative thresholds.
+ *   thr    host, ncell * J * (n_outcomes - 1) uint32 cumulative thresholds
+ *          (with dust absorption the last one is where absorption starts).
  *   flags  host, ncell * J uint32 flag words (2-bit action per outcome:
  *          0 move, 1 escape, 2 to MC, 3 move with Doppler rebin; bit 30 moving
  *          cell; bit 31 thin state).
@@ -367,8 +379,9 @@ uint64_t rddmc_time_state_bytes(uint64_t n_packets);
  *   d_path     device, ncell * J uint64, accumulated (+=): path length spent
  *              in state s during the step, in ticks, 2^31 ticks = t_end -
  *              t_begin (the path estimate).
- *   d_counts   device, 4 uint64, accumulated: packets escaped during the step,
- *              dwell draws, transitions, packets in a state at t_end.
+ *   d_counts   device, 5 uint64, accumulated: packets escaped during the step,
+ *              dwell draws, transitions, packets in a state at t_end, packets
+ *              absorbed by dust during the step.
  *   d_leak     device, ncell * 2 ndim * 2 doubles, accumulated, or NULL: the
  *              leaks of eq. a_estimator.  Entry (cell * 2 ndim + face) * 2 + io
  *              sums k * dl over the packets that leave the cell through that

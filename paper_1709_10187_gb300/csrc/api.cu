@@ -208,6 +208,7 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
     g->off_tau = off; off += align256((uint64_t)g->n_class * J * 4);
     g->off_upar = off; off += align256((uint64_t)kUparN * 8);
     g->off_rk = off; off += align256((uint64_t)g->n_class * J * 4);
+    g->off_abs = off; off += align256((uint64_t)g->n_class * J * 4);
     g->table_bytes = off;
     *out = g;
     return RDDMC_OK;
@@ -223,7 +224,7 @@ int rddmc_grid_sizes(const rddmc_grid* g, uint64_t n_packets, rddmc_sizes* out) 
     out->state_bytes = state_bytes_for(n_packets);
     out->n_class = g->n_class;
     out->row_bytes = g->row_bytes;
-    out->n_outcomes = g->K;
+    out->n_outcomes = g->K + (g->precomputed && g->dusty() ? 1 : 0);
     out->reserved = 0;
     return RDDMC_OK;
 }
@@ -236,6 +237,10 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
     if (!(p->tau_ddmc > 0.0) || !(p->lambda >= 0.0) || !(p->f_mu >= 0.0 && p->f_mu <= 1.0) ||
         (p->mode != RDDMC_MODE_DDMC && p->mode != RDDMC_MODE_HYBRID))
         return RDDMC_ERR_ARG;
+    if (!(p->dust_abs >= 0.0) || !(p->dust_scat >= 0.0) || !std::isfinite(p->dust_abs) ||
+        !std::isfinite(p->dust_scat))
+        return RDDMC_ERR_ARG;
+    if (p->dust_abs > 0.0 && p->mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     g->params = *p;
 
@@ -250,6 +255,8 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
         ClassDesc& D = cd[k];
         std::memset(&D, 0, sizeof(D));
         D.k0 = g->tau0 / g->R * g->n_rel[c];
+        D.ks = p->dust_scat / g->R * g->n_rel[c];
+        D.ka = p->dust_abs / g->R * g->n_rel[c];
         D.moving = (!g->v.empty() && (g->v[3 * c] != 0.0 || g->v[3 * c + 1] != 0.0 || g->v[3 * c + 2] != 0.0)) ? 1 : 0;
         for (int ax = 0; ax < g->ndim; ++ax)
             for (int sd = 0; sd < 2; ++sd) {
@@ -263,6 +270,7 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
                     const int64_t nb = g->cell_of(nidx);
                     D.face[f].exterior = 0;
                     D.face[f].k0_nb = g->tau0 / g->R * g->n_rel[nb];
+                    D.face[f].ks_nb = p->dust_scat / g->R * g->n_rel[nb];
                     if (!g->v.empty())
                         delta = p->f_mu * (double)side * ((g->v[3 * c + ax] - g->v[3 * nb + ax]) / g->vth);
                 }
@@ -333,7 +341,8 @@ int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_r
     if (o->time_slice_us > 0 && o->steps_per_launch == 0 && o->resume == 0 && !o->proposal) return RDDMC_ERR_ARG;
     if (o->proposal) {
         const rddmc_proposal* pr = o->proposal;
-        if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
+        // the learned proposal samples first passages without absorption
+        if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty()) return RDDMC_ERR_UNSUPPORTED;
         if (o->steps_per_launch == 0 && o->resume == 0 && o->time_slice_us == 0) return RDDMC_ERR_ARG;
         if (pr->brick < 1 || pr->brick > 64 || pr->offset < 0 || pr->offset >= pr->brick) return RDDMC_ERR_ARG;
         if (pr->margin < 0 || 2 * pr->margin >= pr->brick) return RDDMC_ERR_ARG;
@@ -365,6 +374,7 @@ int rddmc_read_tallies(const rddmc_grid* g, const void* d_tallies, rddmc_tallies
     out->event_draws = t[C_EVENT_DRAWS];
     out->proposals = t[C_PROPOSALS];
     out->proposed_steps = t[C_PROPOSED_STEPS];
+    out->absorbed = t[C_ABSORBED];
     out->status = RDDMC_OK;
     if (t[C_ABORTED]) out->status = RDDMC_ERR_STEP_LIMIT;
     if (t[C_STATUS_BITS] & STATUS_UNSUPPORTED_EVENT) out->status = RDDMC_ERR_UNSUPPORTED;
@@ -387,7 +397,15 @@ int rddmc_table_rows(const rddmc_grid* g, const void* d_table, uint32_t* thr, ui
                                     cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return RDDMC_ERR_CUDA;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return RDDMC_ERR_CUDA;
-    const int wpr = g->row_bytes / 4, K = g->K;
+    const int wpr = g->row_bytes / 4, K = g->K + (g->dusty() ? 1 : 0);
+    std::vector<uint32_t> ab;
+    if (g->dusty()) {
+        ab.resize(nrow);
+        if (cudaMemcpyAsync(ab.data(), (const char*)d_table + g->off_abs, nrow * 4, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return RDDMC_ERR_CUDA;
+    }
     for (int64_t c = 0; c < g->ncell; ++c) {
         const uint32_t k = g->cell_class[c];
         for (int j = 0; j < g->J; ++j) {
@@ -400,7 +418,8 @@ int rddmc_table_rows(const rddmc_grid* g, const void* d_table, uint32_t* thr, ui
             // stored words: thr0, thr1, thr2, flags[, thr3..thr6]; FLAG_FASTX is
             // an encoding detail of the walk and is not returned
             const uint32_t* r = &rows[((uint64_t)k * g->J + j) * wpr];
-            for (int o = 0; o < K - 1; ++o) thr[s_ * (K - 1) + o] = o < 3 ? r[o] : r[o + 1];
+            for (int o = 0; o < g->K - 1; ++o) thr[s_ * (K - 1) + o] = o < 3 ? r[o] : r[o + 1];
+            if (g->dusty()) thr[s_ * (K - 1) + g->K - 1] = ab[(uint64_t)k * g->J + j];
             flags[s_] = r[3] & ~FLAG_FASTX;
         }
     }

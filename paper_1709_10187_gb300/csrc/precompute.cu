@@ -6,7 +6,8 @@
 //   2/(3 dz (k dz + 2 lambda)), probabilities p_X = k_X / sum k accumulated in
 //   outcome order, 32-bit thresholds round-half-even(C 2^32) saturated at
 //   2^32 - 1, the flag word (2-bit action per outcome, moving, thin) and the
-//   mean dwell path 1 / sum_X k_X of the state.
+//   mean dwell path 1 / sum_X k_X of the state.  Grey dust (Sec. 2.6): k_s adds
+//   to every k_ij; k_a is one more outcome after the leakage ones.
 // FP64 throughout: 1 - p of thick states and far-wing bin means (dcalH ~ a dx /
 // (sqrt(pi) x^2) ~ 1e-8 against calH ~ 0.886) are below FP32 resolution.  This
 // file is compiled without fused multiply-adds so every product and sum is
@@ -36,7 +37,7 @@ template <int NDIM>
 __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ cdesc,
                             const double* __restrict__ edges, const double* __restrict__ phi,
                             uint32_t* __restrict__ rows, uint2* __restrict__ fast, float* __restrict__ tau_row,
-                            float* __restrict__ rk, int64_t nrow) {
+                            float* __restrict__ rk, uint32_t* __restrict__ abs_thr, int dusty, int64_t nrow) {
     constexpr int K = 2 + 2 * NDIM;
     constexpr int W = NDIM == 1 ? 4 : 8;  // words per row, the last holding the flags
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -50,7 +51,7 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
     for (int ax = 1; ax < NDIM; ++ax) dzmin = fmin(dzmin, h.dz[ax]);
 
     const double dxj = edges[j + 1] - edges[j];
-    const double k = D.k0 * phi[j];
+    const double k = D.k0 * phi[j] + D.ks;  // dust scattering adds to every k_ij (Sec. 2.6)
     double rate[K];
     uint32_t act[K];
     // frequency leakage, eq. x-leakage; zero flux beyond the grid ends
@@ -59,7 +60,7 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
         const int jn = j + (sd ? 1 : -1);
         if (jn < 0 || jn >= J) { rate[sd] = 0.0; act[sd] = ACT_MOVE; continue; }
         const double dxn = edges[jn + 1] - edges[jn];
-        const double kn = D.k0 * phi[jn];
+        const double kn = D.k0 * phi[jn] + D.ks;
         rate[sd] = 1.0 / (dxj * (dxj / k + dxn / kn));
         act[sd] = (hybrid && kn * dzmin < h.tau_ddmc) ? ACT_TO_MC : ACT_MOVE;
     }
@@ -77,7 +78,8 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
             // neighbour opacity over the Doppler-shifted bin (eq. velocity-shift)
             const double knb = F.k0_nb * (F.delta == 0.0 ? phi[j]
                                                          : voigt_bin_mean_f64(h.a, edges[j] + F.delta,
-                                                                              edges[j + 1] + F.delta));
+                                                                              edges[j + 1] + F.delta)) +
+                               F.ks_nb;
             const double dznb = dz;
             if (hybrid && knb * dznb < h.tau_ddmc) { rate[o] = r_bnd; act[o] = ACT_TO_MC; continue; }
             rate[o] = 1.0 / (3.0 * dz) * 2.0 / (k * dz + knb * dznb);
@@ -87,6 +89,9 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
     double tot = 0.0;
 #pragma unroll
     for (int o = 0; o < K; ++o) tot += rate[o];
+    // dust absorption: one more competing process, the last outcome; its lower
+    // threshold (the end of the last leakage outcome) is stored apart
+    if (dusty) tot += D.ka;
     uint32_t out[W - 1];
     double C = 0.0;
 #pragma unroll
@@ -94,6 +99,7 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
         C += rate[o] / tot;
         out[o] = quantise_dev(C);
     }
+    abs_thr[r] = dusty ? quantise_dev(C + rate[K - 1] / tot) : 0xffffffffu;
     uint32_t fl = 0;
 #pragma unroll
     for (int o = 0; o < K; ++o) fl |= (act[o] & 3u) << (2 * o);
@@ -168,10 +174,12 @@ cudaError_t launch_precompute(const rddmc_grid& g, void* d_table, cudaStream_t s
     uint2* fast = (uint2*)(base + g.off_fast);
     float* tau_row = (float*)(base + g.off_tau);
     float* rk = (float*)(base + g.off_rk);
+    uint32_t* abs_thr = (uint32_t*)(base + g.off_abs);
+    const int dusty = g.dusty() ? 1 : 0;
     if (g.ndim == 1)
-        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, nrow);
+        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, abs_thr, dusty, nrow);
     else
-        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, nrow);
+        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, abs_thr, dusty, nrow);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the u_par envelope table serves only the continuous MC of the hybrid scheme
     if (g.params.mode == RDDMC_MODE_HYBRID)

@@ -4,7 +4,11 @@
 //   [TableHeader | cell_class u32[ncell] | ClassDesc[n_class] | Rebin[n_class*nfaces]
 //    | cell velocity f64[3*ncell] (moving media only) | edges f64[J+1] | phi f64[J] | rows
 //    | fast heads uint2[n_class*J] | tau f32[n_class*J] | u_par split points f32x2[kUparN]
-//    | 1/K_s f32[n_class*J]]
+//    | 1/K_s f32[n_class*J] | dust absorption thresholds u32[n_class*J]]
+// With dust absorption (Sec. 2.6) the categorical draw has one more outcome,
+// absorption, after the leakage outcomes: the row thresholds are cumulative over
+// the leakage rates plus k_a, and the absorption threshold (where absorption
+// starts) is kept apart so that rows keep their size.
 // every region 256-byte aligned.  Rows are n_class blocks of J rows; a row is
 // 16 bytes in a slab {thr0, thr1, thr2, flags} and 32 bytes in 3D
 // {thr0, thr1, thr2, flags, thr3, thr4, thr5, thr6}: the first 16 bytes always
@@ -37,7 +41,7 @@ constexpr float kUparStep = 1.0f / 16.0f;
 enum Counter : int {
     C_EMITTED = 0, C_ESCAPED = 1, C_ABORTED = 2, C_STEPS = 3, C_MC_EVENTS = 4,
     C_CONVERSIONS = 5, C_CLAMPS = 6, C_EVENT_DRAWS = 7, C_STATUS_BITS = 8, C_PROPOSALS = 9,
-    C_PROPOSED_STEPS = 10,
+    C_PROPOSED_STEPS = 10, C_ABSORBED = 11,
 };
 
 // 2-bit actions per outcome in the flags word.
@@ -55,11 +59,13 @@ struct FaceDesc {
     int32_t exterior;   // 1: the neighbour is outside the grid or vacuum
     int32_t pad;
     double k0_nb;       // neighbour's line-centre coefficient (tau0/R * n_rel)
+    double ks_nb;       // neighbour's dust scattering coefficient
     double delta;       // comoving shift x' = x + delta on crossing (eq. velocity-shift)
 };
 
 struct ClassDesc {
     double k0;          // tau0/R * n_rel of the cells in this class
+    double ks, ka;      // grey dust scattering and absorption coefficients (Sec. 2.6)
     int32_t moving;     // the cells have non-zero bulk velocity
     int32_t pad;
     FaceDesc face[kMaxFaces];

@@ -57,7 +57,7 @@ struct TimeParams {
     unsigned long long* st_d;        // dwell words drawn per packet
     unsigned long long* bins;        // [ncell * J] packets per state at t_{n+1}
     unsigned long long* path;        // [ncell * J] ticks spent per state during the step
-    unsigned long long* counts;      // [4] escaped during the step, dwells, transitions, alive at t_{n+1}
+    unsigned long long* counts;      // [5] escaped during the step, dwells, transitions, alive at t_{n+1}, absorbed
     double* leak;                    // [ncell * 2 NDIM * 2] k x ticks of leaks out of / into each face, or null
     float inv_dz;                    // 1 / dz_min: k of a row = tau_row / dz_min
     int leak_in_smem;
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
     unsigned long long tnc = ~0ull;     // index of the cached transition block
     uint4 rnc = make_uint4(0u, 0u, 0u, 0u);
     unsigned long long n_steps = 0, n_edraw = 0, n_dwell = 0;
-    unsigned n_emit = 0, n_esc = 0, n_abort = 0, n_clamp = 0, n_alive = 0, status_bits = 0;
+    unsigned n_emit = 0, n_esc = 0, n_abort = 0, n_clamp = 0, n_alive = 0, n_absorbed = 0, status_bits = 0;
 
     auto add_path = [&](unsigned ticks) {
         if (!ticks) return;
@@ -155,6 +155,11 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
         if (NDIM == 3) {
             const uint4 b = __ldg(&rows[ri * RW + 1]);
             o += (unsigned)(w >= b.x) + (unsigned)(w >= b.y) + (unsigned)(w >= b.z) + (unsigned)(w >= b.w);
+        }
+        if (P.dust && o == 2u * NDIM + 1u && w >= __ldg(&P.abs_thr[ri])) {  // absorbed by dust (Sec. 2.6)
+            atomicAdd(&s_cnt[C_ABSORBED], 1ull);
+            ++n_absorbed;
+            return true;
         }
         const unsigned fl = a.w;
         const unsigned act = (fl >> (2u * o)) & 3u;
@@ -345,9 +350,10 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
     }
 
     // ---- flush: warp sums of the per-thread counters, then CTA totals to HBM
-    unsigned long long v[10] = {n_emit, n_esc, n_abort, n_steps, n_clamp, n_edraw, status_bits, n_dwell, n_alive, 0};
+    unsigned long long v[10] = {n_emit, n_esc,  n_abort, n_steps, n_clamp,
+                                n_edraw, status_bits, n_dwell, n_alive, n_absorbed};
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 0; i < 10; ++i) {
         unsigned long long x = v[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
@@ -365,6 +371,7 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
         if (v[7]) atomicAdd(&T.counts[1], v[7]);
         if (v[3]) atomicAdd(&T.counts[2], v[3]);
         if (v[8]) atomicAdd(&T.counts[3], v[8]);
+        if (v[9]) atomicAdd(&T.counts[4], v[9]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kCounters; i += blockDim.x) {

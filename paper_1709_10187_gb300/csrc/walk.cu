@@ -321,6 +321,10 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
             const uint4 b = __ldg(&rows[ri * RW + 1]);
             o += (unsigned)(w >= b.x) + (unsigned)(w >= b.y) + (unsigned)(w >= b.z) + (unsigned)(w >= b.w);
         }
+        if (P.dust && o == 2u * NDIM + 1u && w >= __ldg(&P.abs_thr[ri])) {  // absorbed by dust (Sec. 2.6)
+            atomicAdd(&s_cnt[C_ABSORBED], 1ull);
+            return true;
+        }
         const unsigned fl = a.w;
         const unsigned act = (fl >> (2u * o)) & 3u;
         const unsigned bin = min(s - cls * J, J - 1u);
@@ -790,6 +794,8 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     P.rebin = (const Rebin*)(tb + g.off_rebin);
     P.cell_v = (const double*)(tb + g.off_vel);
     P.edges = (const double*)(tb + g.off_edges);
+    P.abs_thr = (const uint32_t*)(tb + g.off_abs);
+    P.dust = g.dusty() ? 1 : 0;
     const uint64_t np = o.n_packets;
     uint64_t off = 256;
     P.cursor = (unsigned long long*)sb;
@@ -889,7 +895,7 @@ extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rdd
                              void* stream) {
     using namespace rddmc;
     if (!g || !d_table || !pr || !d_state || !d_tallies || !d_wf || !d_wb || !d_work) return RDDMC_ERR_ARG;
-    if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
+    if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty()) return RDDMC_ERR_UNSUPPORTED;
     if (batch < 64 || batch % 64 || nA != 6 * g->J || nB < 1 || nB > 41 || nC < 0 || nA + nB + nC > n_out ||
         n_out % 16)
         return RDDMC_ERR_ARG;

@@ -21,6 +21,8 @@ struct WalkParams {
     const Rebin* rebin;
     const double* cell_v;     // km/s, 3 per cell (moving media)
     const double* edges;
+    const uint32_t* abs_thr;  // per row: where dust absorption starts (dust only)
+    int dust;                 // the draw has the absorption outcome (Sec. 2.6)
     unsigned long long* cursor;
     uint32_t* st_cell;
     uint32_t* st_bin;

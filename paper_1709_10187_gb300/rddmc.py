@@ -49,7 +49,8 @@ class GridDesc(ctypes.Structure):
 
 class LeakParams(ctypes.Structure):
     _fields_ = [("tau_ddmc", ctypes.c_double), ("lam", ctypes.c_double), ("f_mu", ctypes.c_double),
-                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("dust_abs", ctypes.c_double),
+                ("dust_scat", ctypes.c_double)]
 
 
 class RunOpts(ctypes.Structure):
@@ -69,7 +70,7 @@ class Tallies(ctypes.Structure):
     _fields_ = [("emitted", ctypes.c_uint64), ("escaped", ctypes.c_uint64), ("aborted", ctypes.c_uint64),
                 ("steps", ctypes.c_uint64), ("mc_events", ctypes.c_uint64), ("conversions", ctypes.c_uint64),
                 ("clamps", ctypes.c_uint64), ("event_draws", ctypes.c_uint64), ("proposals", ctypes.c_uint64),
-                ("proposed_steps", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("proposed_steps", ctypes.c_uint64), ("absorbed", ctypes.c_uint64), ("status", ctypes.c_int32),
                 ("nbins", ctypes.c_int32), ("nfaces", ctypes.c_int32), ("nsb", ctypes.c_int32)]
 
 
@@ -296,7 +297,7 @@ class Problem:
     in caller-owned torch device buffers."""
 
     def __init__(self, w, mode=MODE_DDMC, layout=LAYOUT_DEDUP, tau_ddmc=5.0, lam=0.7104, f_mu=0.5,
-                 device="cuda", n_rel=None, edges=None, v_kms=None):
+                 device="cuda", n_rel=None, edges=None, v_kms=None, dust_abs=0.0, dust_scat=0.0):
         import torch
         self.torch = torch
         self.w = w
@@ -314,7 +315,7 @@ class Problem:
         self.tally = torch.zeros(int(s.tally_bytes) // 8, dtype=torch.int64, device=self.device)
         self.state = None
         self.state_packets = 0
-        self.params = LeakParams(tau_ddmc, lam, f_mu, mode, 0)
+        self.params = LeakParams(tau_ddmc, lam, f_mu, mode, 0, dust_abs, dust_scat)
         precompute_leakage(self.grid, self.params, self.table.data_ptr(), self.table.numel(), self.stream())
 
     def stream(self) -> int:
@@ -372,7 +373,7 @@ class Problem:
         state = torch.empty(need, dtype=torch.uint8, device=self.device)
         bins = torch.zeros((nt, S), dtype=torch.int64, device=self.device)
         path = torch.zeros((nt, S), dtype=torch.int64, device=self.device)
-        counts = torch.zeros((nt, 4), dtype=torch.int64, device=self.device)
+        counts = torch.zeros((nt, 5), dtype=torch.int64, device=self.device)
         nf = 2 * self.w.ndim
         leak = torch.zeros((nt, int(self.w.ncell) * nf * 2), dtype=torch.float64, device=self.device) if leaks \
             else None
@@ -387,7 +388,7 @@ class Problem:
         ticks = path.cpu().numpy().astype(np.float64)
         out = dict(bins=bins.cpu().numpy().astype(np.uint64), path=ticks * (np.diff(te) / TIME_TICKS)[:, None],
                    path_ticks=path.cpu().numpy().astype(np.uint64), esc=c[:, 0], dwells=c[:, 1],
-                   transitions=c[:, 2], alive=c[:, 3], tallies=self.read())
+                   transitions=c[:, 2], alive=c[:, 3], absorbed=c[:, 4], tallies=self.read())
         if leaks:
             lk = leak.cpu().numpy() * (np.diff(te) / TIME_TICKS)[:, None]
             out["leak"] = lk.reshape(nt, int(self.w.ncell), nf, 2)
@@ -402,7 +403,8 @@ class Problem:
         return read_packet_states(self.grid, self.state.data_ptr(), n_packets, first, count, self.stream())
 
     def rows(self):
-        return table_rows(self.grid, self.table.data_ptr(), self.w.ncell, self.J, self.K, self.stream())
+        K = grid_sizes(self.grid, 1).n_outcomes  # one more with dust absorption
+        return table_rows(self.grid, self.table.data_ptr(), self.w.ncell, self.J, K, self.stream())
 
     def close(self):
         destroy_grid(self.grid)

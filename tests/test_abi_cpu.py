@@ -121,3 +121,21 @@ def test_time_step_validation_without_a_gpu():
     assert R.lib().rddmc_time_step_launch(g, fake, st, fake, 1 << 30, fake, 1 << 20, fake, fake, fake, fake + 4,
                                           None) == R.ERR_ARG   # misaligned leak buffer
     R.destroy_grid(g)
+
+
+def test_dust_parameters_are_validated_without_a_gpu():
+    """rddmc_precompute_leakage rejects negative or non-finite dust and dust
+    absorption with the hybrid scheme before touching the table buffer."""
+    w = W.TINY
+    g = _grid(w)
+    s = R.grid_sizes(g, 1)
+    fake = 1 << 20  # 256-byte aligned, never dereferenced
+    bad = [(R.MODE_DDMC, -1.0, 0.0, R.ERR_ARG), (R.MODE_DDMC, 0.0, -2.0, R.ERR_ARG),
+           (R.MODE_DDMC, float("inf"), 0.0, R.ERR_ARG), (R.MODE_HYBRID, 0.5, 0.0, R.ERR_UNSUPPORTED)]
+    for mode, da, ds, want in bad:
+        p = R.LeakParams(5.0, 0.7104, 0.5, mode, 0, da, ds)
+        rc = R.lib().rddmc_precompute_leakage(g, p, fake, int(s.table_bytes), None)
+        assert rc == want, (mode, da, ds, rc)
+    # the outcome count grows by one only once a dusty table is precomputed
+    assert s.n_outcomes == 4
+    R.destroy_grid(g)
