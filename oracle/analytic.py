@@ -378,6 +378,49 @@ def R_IIA_wing(x, xp):
     return (2.0 * xp / (x + xp)) ** 2 * (np.exp(-zeta * zeta) / np.sqrt(np.pi) - zeta * ss.erfc(zeta))
 
 
+def redistribution_cdf_at(edges, xp, a, span=14.0):
+    """F(e | x') = int_{-inf}^{e} R_II-A(x, x') dx at every edge e (normalised by
+    the total, which is 1 up to the quadrature error), by adaptive
+    quadrature of R_II-A over the pieces between the edges, x' and -x' (the
+    kinks of R in x) and at the integers, within x' +- span (R is below
+    e^{-(span/2)^2} beyond)."""
+    lo, hi = xp - span, xp + span
+    unit = list(np.arange(np.ceil(lo), hi))  # unit pieces keep the adaptive rule local
+    cuts = sorted(set([lo, hi] + unit + [e for e in edges if lo < e < hi] + [p for p in (xp, -xp) if lo < p < hi]))
+    cum = [0.0]
+    for u, v in zip(cuts[:-1], cuts[1:]):
+        val, _ = si.quad(lambda x: R_IIA(x, xp, a), u, v, epsabs=1e-11, epsrel=1e-8, limit=100)
+        cum.append(cum[-1] + val)
+    cuts, cum = np.array(cuts), np.array(cum)
+    # normalised by the total mass (1 up to the quadrature error)
+    return np.interp(np.asarray(edges, dtype=np.float64), cuts, cum, left=0.0, right=cum[-1]) / cum[-1]
+
+
+def redistribution_cdf(edges, a, n_sub=3):
+    """Eq. R_discrete as cumulative probabilities: row j' holds, for the J-1
+    interior edges e_1..e_{J-1}, the average over x' in bin j' of F(e | x'), the
+    x' integral taken with n_sub Gauss-Legendre nodes (uniform weight in the
+    bin, as the equation's 1/dx_j' average).  Outgoing frequencies beyond the
+    grid ends fall in the end bins (no flux beyond the grid, as for the
+    leakage).  Returns (J, J-1)."""
+    e = np.asarray(edges, dtype=np.float64)
+    J = len(e) - 1
+    gx, gw = np.polynomial.legendre.leggauss(n_sub)
+    C = np.zeros((J, J - 1))
+    for jp in range(J):
+        for xg, wg in zip(gx, gw):
+            xp = 0.5 * (e[jp + 1] - e[jp]) * xg + 0.5 * (e[jp + 1] + e[jp])
+            F = redistribution_cdf_at(e, xp, a)
+            C[jp] += 0.5 * wg * F[1:J]
+    return C
+
+
+def redistribution_thresholds(C):
+    """32-bit thresholds of cumulative probabilities: round half to even of
+    C 2^32, saturated at 2^32 - 1 (the rule of the leakage thresholds)."""
+    return np.minimum(np.rint(np.asarray(C) * TWO32), TWO32 - 1).astype(np.uint32)
+
+
 def R_IIA_bin_probs(edges, xp, a, n_sub=8):
     """Probability of each outgoing-frequency bin, integrating R_II-A over the bin
     with Gauss-Legendre nodes."""

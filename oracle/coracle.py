@@ -23,7 +23,7 @@ class OrcGrid(ctypes.Structure):
         ("R", ctypes.c_double), ("tau0", ctypes.c_double), ("T", ctypes.c_double),
         ("tau_ddmc", ctypes.c_double), ("lam", ctypes.c_double), ("f_mu", ctypes.c_double),
         ("edges", ctypes.c_void_p), ("n_rel", ctypes.c_void_p), ("v", ctypes.c_void_p), ("mask", ctypes.c_void_p),
-        ("dust_abs", ctypes.c_double), ("dust_scat", ctypes.c_double),
+        ("dust_abs", ctypes.c_double), ("dust_scat", ctypes.c_double), ("redist", ctypes.c_void_p),
     ]
 
 
@@ -116,7 +116,7 @@ class Grid:
     """An oracle grid built from a workload; keeps the numpy buffers alive."""
 
     def __init__(self, w, hybrid=False, tau_ddmc=5.0, lam=0.7104, f_mu=0.5, n_rel=None, edges=None, dust_abs=0.0,
-                 dust_scat=0.0):
+                 dust_scat=0.0, redist=None):
         self.w = w
         e = w.edges() if edges is None else edges
         self.edges = np.ascontiguousarray(e, dtype=np.float64)
@@ -134,6 +134,9 @@ class Grid:
         g.tau_ddmc, g.lam, g.f_mu = tau_ddmc, lam, f_mu
         g.edges, g.n_rel, g.v, g.mask = (_ptr(self.edges), _ptr(self.n_rel), _ptr(self.v), _ptr(self.mask))
         g.dust_abs, g.dust_scat = float(dust_abs), float(dust_scat)  # grey dust k R at unit density (Sec. 2.6)
+        # frequency-grouped MC (Sec. 5.3): J x (J-1) thresholds of eq. R_discrete, kept alive with the grid
+        self.redist = None if redist is None else np.ascontiguousarray(redist, dtype=np.uint32)
+        g.redist = _ptr(self.redist)
         self.g = g
         self.K = 2 + 2 * w.ndim
         self.KT = self.K + (1 if dust_abs > 0.0 else 0)  # outcomes, dust absorption last

@@ -171,6 +171,8 @@ typedef struct orc_grid {
     const uint8_t* mask;  /* per-cell 1 = medium, 0 = vacuum, NULL = all medium */
     double dust_abs;      /* dust absorption k_a R at unit density (grey; Sec. 2.6), 0 = none */
     double dust_scat;     /* dust scattering k_s R at unit density (grey), added to k_ij */
+    const uint32_t* redist; /* hybrid only: frequency-grouped MC (Sec. 5.3) with these cumulative
+                               thresholds of eq. R_discrete, J rows of J-1; NULL = continuous MC */
 } orc_grid;
 
 /* Actions stored two bits per outcome in the flags word. */
@@ -709,7 +711,12 @@ static int orc_mc_run(orc_walk_args* A, orc_mc* m, uint64_t pk, uint64_t* e, uin
     for (uint64_t ev = 0;; ++ev) {
         if (ev >= cap) return 3;
         int64_t c = orc_cell_of(g, m->idx);
-        double k = orc_k0(g, c) * orc_voigt_H(a, m->x);
+        /* frequency grouping (Sec. 5.3): the bin-mean opacity of the packet's bin */
+        /* (a Doppler shift across a face may carry x past the grid ends: grouping
+         * then uses the end bin, as the leakage has no flux beyond them) */
+        int jb = orc_bin_of(g, m->x);
+        jb = jb < 0 ? 0 : (jb > g->J - 1 ? g->J - 1 : jb);
+        double k = g->redist ? A->k[c * g->J + jb] : orc_k0(g, c) * orc_voigt_H(a, m->x);
         double s = -log(orc_ev(A, pk, e)) / k;
         /* distance to the cell boundary along n */
         double dmin = INFINITY;
@@ -724,7 +731,19 @@ static int orc_mc_run(orc_walk_args* A, orc_mc* m, uint64_t pk, uint64_t* e, uin
         t[ORC_T_MC_EVENTS]++;
         if (s < dmin) {
             for (int q = 0; q < 3; ++q) m->r[q] += s * m->n[q];
-            m->x = orc_scatter(A, a, m->x, m->n, pk, e);
+            if (g->redist) {
+                /* frequency grouping: the new bin from the row of eq. R_discrete
+                 * (categorical draw on its thresholds), x uniform in it, a new
+                 * isotropic direction */
+                const int jp = jb;
+                const uint32_t w = orc_word(A->seed, pk, ORC_EVENT, (*e)++);
+                int jn = 0;
+                while (jn < g->J - 1 && w >= g->redist[(size_t)jp * (g->J - 1) + jn]) ++jn;
+                m->x = g->edges[jn] + orc_ev(A, pk, e) * (g->edges[jn + 1] - g->edges[jn]);
+                orc_iso_dir(A, pk, e, m->n);
+            } else {
+                m->x = orc_scatter(A, a, m->x, m->n, pk, e);
+            }
             int j = orc_bin_of(g, m->x);
             if (orc_is_thick(A, c, j)) {
                 t[ORC_T_CONVERSIONS]++;
