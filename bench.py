@@ -329,6 +329,38 @@ def _sliced_rate(R, torch, prob, npk, seed, slice_, launches=5, warm=2):
             "launches": launches}
 
 
+def _grouped_rate(R, torch, npk=1_000_000, slice_=4096):
+    """The C2 hybrid walk with frequency-grouped MC in thin states (Sec. 5.3):
+    the eq. R_discrete thresholds (512 x 511, FP64, timed) and the rates of the
+    sliced walk, beside the same walk with the continuous MC."""
+    prob = R.Problem(W.C2, mode=R.MODE_HYBRID)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record(torch.cuda.current_stream())
+    red = prob.redistribution(3)
+    a1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    t_pre = a0.elapsed_time(a1) / 1e3
+    s = prob.stream()
+    prob.ensure_state(npk)
+    prob.reset()
+    for i in range(2):
+        prob.launch(npk, W.C2.seed, steps_per_launch=slice_, resume=1 if i else 0, redist=red)
+    b = prob.read()
+    torch.cuda.synchronize()
+    a0.record(torch.cuda.current_stream())
+    for i in range(5):
+        prob.launch(npk, W.C2.seed, steps_per_launch=slice_, resume=1, redist=red)
+    a1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    dt = a0.elapsed_time(a1) / 1e3
+    e = prob.read()
+    del s
+    return {"redistribution_precompute_s": t_pre, "transitions_per_s": (e["steps"] - b["steps"]) / dt,
+            "mc_events_per_s": (e["mc_events"] - b["mc_events"]) / dt, "packets": npk, "slice": slice_,
+            "launches": 5}
+
+
 def _complete(R, torch, w, npk):
     """A run to completion: escaped packets/s over the wall time from launch to
     the last packet's escape (CUDA events around one launch)."""
@@ -566,6 +598,7 @@ def _extras(R, torch, only=None):
             ("c3_sphere_v200", lambda: _sliced_rate(R, torch, R.Problem(W.C3_V200), 1_000_000, W.C3.seed, 4096)),
             ("c2_hybrid", lambda: _sliced_rate(R, torch, R.Problem(W.C2, mode=R.MODE_HYBRID), 1_000_000,
                                                W.C2.seed, 4096)),
+            ("c2_hybrid_grouped", lambda: _grouped_rate(R, torch)),
             ("c1_complete", lambda: _complete(R, torch, W.C1, W.C1.packets)),
             ("c2_widecore_complete", lambda: _complete(R, torch, W.C2_WIDECORE, W.C2_WIDECORE.packets)),
             ("batched_512", lambda: _batched(R, torch)),

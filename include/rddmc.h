@@ -145,6 +145,12 @@ typedef struct rddmc_leak_params {
  *                 `chunk` (and at emission), so parking does not depend on
  *                 slicing.  Requires steps_per_launch > 0, resume = 1 or
  *                 time_slice_us > 0 so parked states are kept.
+ *   redist        NULL, or (hybrid tables only) the device thresholds of eq.
+ *                 R_discrete from rddmc_precompute_redistribution: the MC of
+ *                 thin states then groups frequency (Sec. 5.3), flying with the
+ *                 bin-mean opacity k_j and drawing each scattering's new bin
+ *                 from the row of the packet's bin (x uniform in it, a new
+ *                 isotropic direction) instead of the atom-velocity sampler.
  */
 typedef struct rddmc_run_opts {
     uint64_t seed;
@@ -158,6 +164,7 @@ typedef struct rddmc_run_opts {
     int32_t table_in_smem;
     int32_t time_slice_us;
     const struct rddmc_proposal* proposal;
+    const uint32_t* redist;
 } rddmc_run_opts;
 
 /* Buffer sizes for a grid (from rddmc_grid_sizes). */
@@ -328,6 +335,33 @@ int rddmc_table_rows(const rddmc_grid* grid, const void* d_table, uint32_t* thr,
 int rddmc_read_packet_states(const rddmc_grid* grid, const void* d_state, uint64_t n_packets, uint64_t first,
                              uint64_t count, uint32_t* cell, uint32_t* bin, uint64_t* steps, uint64_t* event_draws,
                              uint8_t* status, void* stream);
+
+/* --------------------------------------------- discrete frequency grouping
+ * Sec. 5.3, eq. R_discrete: the redistribution function averaged over
+ * incoming and outgoing bins, R_{j'->j} = (dx_j dx_j')^-1 iint_{j j'}
+ * R(x' -> x) dx dx', with R the angle-averaged redistribution of isotropic
+ * coherent scattering without recoil (Appendix A).  Row j' is stored as
+ * cumulative probabilities at the interior edges e_1..e_{J-1} (32-bit
+ * thresholds, round half to even of C 2^32, saturated at 2^32 - 1): the
+ * average over x' in bin j' of the fraction of outgoing frequencies below the
+ * edge.  Outgoing frequencies beyond the grid count in the end bins.  The x'
+ * average takes n_sub Gauss-Legendre nodes of the incoming bin; the integrals
+ * in x and in the atom velocity are FP64 Gauss-Legendre on pieces cut at the
+ * kinks of R.  The hybrid walk's MC uses the thresholds when rddmc_run_opts.
+ * redist points to them.
+ */
+
+/* Bytes of the redistribution buffer: J * (J - 1) uint32 (rounded up to 256);
+ * 0 for J < 2. */
+uint64_t rddmc_redistribution_bytes(const rddmc_grid* grid);
+
+/* Fill d_redist (device, 4-byte aligned, >= rddmc_redistribution_bytes) with
+ * the thresholds of eq. R_discrete.  d_table: the grid's precomputed table
+ * (its bin edges are read).  n_sub in [1, 8].  Enqueues one kernel on
+ * `stream`.  Errors: RDDMC_ERR_ARG, RDDMC_ERR_SIZE, RDDMC_ERR_TABLE,
+ * RDDMC_ERR_UNSUPPORTED (n_sub (J - 1) above 25 600), RDDMC_ERR_CUDA. */
+int rddmc_precompute_redistribution(const rddmc_grid* grid, const void* d_table, int n_sub, void* d_redist,
+                                    size_t bytes, void* stream);
 
 /* ------------------------------------------------------ time-dependent walk
  * Sec. 2.3 (causality within a time step) and eq. E_estimator (the 'bin' and

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librddmc.so")
-SOURCES = ["api.cu", "precompute.cu", "walk.cu", "timewalk.cu", "batch.cu", "learned.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "precompute.cu", "walk.cu", "timewalk.cu", "redist.cu", "batch.cu", "learned.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

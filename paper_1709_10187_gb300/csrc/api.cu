@@ -338,6 +338,8 @@ int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_r
     if (o->threads_per_cta && (o->threads_per_cta % 32 != 0 || o->threads_per_cta > 256)) return RDDMC_ERR_ARG;
     if (o->resume != 0 && o->resume != 1) return RDDMC_ERR_ARG;
     if (o->time_slice_us < 0) return RDDMC_ERR_ARG;
+    // frequency-grouped MC needs thin states, i.e. a hybrid table
+    if (o->redist && (g->params.mode != RDDMC_MODE_HYBRID || ((uintptr_t)o->redist & 3u))) return RDDMC_ERR_ARG;
     if (o->time_slice_us > 0 && o->steps_per_launch == 0 && o->resume == 0 && !o->proposal) return RDDMC_ERR_ARG;
     if (o->proposal) {
         const rddmc_proposal* pr = o->proposal;

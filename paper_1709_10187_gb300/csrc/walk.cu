@@ -192,7 +192,11 @@ __device__ __noinline__ McResult mc_excursion(const WalkParams& P, unsigned cell
     for (unsigned long long ev = 0; !done; ++ev) {
         if (ev >= P.mc_cap) { res.status = 2; break; }
         const unsigned cls = min(__ldg(&P.cell_class[min(m.cell, (unsigned)P.ncell - 1u)]), (unsigned)P.n_class - 1u);
-        const float k = (float)P.cdesc[cls].k0 * voigt_H_f32(P.a, m.x);
+        // frequency grouping (Sec. 5.3): the bin-mean opacity of the packet's bin
+        // (the end bin past the grid, where the leakage has no flux either)
+        const unsigned jb = (unsigned)min(max(bin_of(P, m.x), 0), P.J - 1);
+        const float k = P.redist ? __ldg(&P.tau_row[cls * (unsigned)P.J + jb]) * P.inv_dzmin
+                                 : (float)P.cdesc[cls].k0 * voigt_H_f32(P.a, m.x);
         const float sflight = -__logf(es.u01()) / k;
         float dmin = 3.0e38f;
         int fax = 0, fside = 1;
@@ -208,7 +212,21 @@ __device__ __noinline__ McResult mc_excursion(const WalkParams& P, unsigned cell
         if (sflight < dmin) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) m.r[q] += sflight * m.n[q];
-            m.x = scatter(P.a, m.x, m.n, P.upar, es);
+            if (P.redist) {
+                // the new bin from row jb of eq. R_discrete (categorical draw on
+                // its cumulative thresholds), x uniform in it, a new direction
+                const unsigned w = es.next();
+                const uint32_t* row = P.redist + (size_t)jb * (unsigned)(P.J - 1);
+                int lo = 0, hi = P.J - 1;  // number of thresholds <= w
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (w >= __ldg(&row[mid])) lo = mid + 1; else hi = mid;
+                }
+                m.x = (float)(P.edges[lo] + (double)es.u01() * (P.edges[lo + 1] - P.edges[lo]));
+                iso_dir(es, m.n);
+            } else {
+                m.x = scatter(P.a, m.x, m.n, P.upar, es);
+            }
             const int j = bin_of(P, m.x);
             if (thick_state<NDIM>(P, m.cell, j)) {
                 ++n_conv;
@@ -796,6 +814,12 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     P.edges = (const double*)(tb + g.off_edges);
     P.abs_thr = (const uint32_t*)(tb + g.off_abs);
     P.dust = g.dusty() ? 1 : 0;
+    P.redist = o.redist;
+    {
+        double dzmin = 2.0 * g.R / g.n[0];
+        for (int a = 1; a < g.ndim; ++a) dzmin = std::min(dzmin, 2.0 * g.R / g.n[a]);
+        P.inv_dzmin = (float)(1.0 / dzmin);
+    }
     const uint64_t np = o.n_packets;
     uint64_t off = 256;
     P.cursor = (unsigned long long*)sb;

@@ -23,6 +23,8 @@ struct WalkParams {
     const double* edges;
     const uint32_t* abs_thr;  // per row: where dust absorption starts (dust only)
     int dust;                 // the draw has the absorption outcome (Sec. 2.6)
+    const uint32_t* redist;   // hybrid: frequency-grouped MC (Sec. 5.3), J rows of J-1 thresholds, or null
+    float inv_dzmin;          // 1 / dz_min: k of a row = tau_row / dz_min
     unsigned long long* cursor;
     uint32_t* st_cell;
     uint32_t* st_bin;

@@ -35,7 +35,8 @@ EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc
             "rddmc_batch_graph_destroy", "rddmc_batch_autotune", "rddmc_cell_tau", "rddmc_fp_generate",
             "rddmc_mlp_param_count", "rddmc_mlp_work_bytes", "rddmc_mlp_to_bf16", "rddmc_mlp_forward",
             "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_mlp_status", "rddmc_propose", "rddmc_time_state_bytes",
-            "rddmc_time_step_launch", "rddmc_status_string", "rddmc_version"]
+            "rddmc_time_step_launch", "rddmc_redistribution_bytes", "rddmc_precompute_redistribution",
+            "rddmc_status_string", "rddmc_version"]
 
 TIME_TICKS = 1 << 31  # ticks per time step in the path tallies of rddmc_time_step_launch
 
@@ -57,7 +58,7 @@ class RunOpts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("n_packets", ctypes.c_uint64), ("max_steps", ctypes.c_uint64),
                 ("steps_per_launch", ctypes.c_uint64), ("resume", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("chunk", ctypes.c_int32), ("table_in_smem", ctypes.c_int32),
-                ("time_slice_us", ctypes.c_int32), ("proposal", ctypes.c_void_p)]
+                ("time_slice_us", ctypes.c_int32), ("proposal", ctypes.c_void_p), ("redist", ctypes.c_void_p)]
 
 
 class Sizes(ctypes.Structure):
@@ -150,6 +151,8 @@ def lib():
         L.rddmc_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp, sz, vp, ctypes.POINTER(RunOpts),
                                            ctypes.POINTER(ctypes.c_double)]
         L.rddmc_time_state_bytes.argtypes = [u64]
+        L.rddmc_redistribution_bytes.argtypes = [vp]
+        L.rddmc_precompute_redistribution.argtypes = [vp, vp, i32, vp, sz, vp]
         L.rddmc_time_step_launch.argtypes = [vp, vp, ctypes.POINTER(TimeStep), vp, sz, vp, sz, vp, vp, vp, vp, vp]
         L.rddmc_status_string.argtypes = [i32]
         L.rddmc_status_string.restype = ctypes.c_char_p
@@ -161,6 +164,7 @@ def lib():
         L.rddmc_mlp_param_count.restype = ctypes.c_uint64
         L.rddmc_mlp_work_bytes.restype = ctypes.c_uint64
         L.rddmc_time_state_bytes.restype = ctypes.c_uint64
+        L.rddmc_redistribution_bytes.restype = ctypes.c_uint64
         _LIB = L
     return _LIB
 
@@ -234,6 +238,18 @@ def launch_packets_noalloc(grid, d_table: int, opts: RunOpts, d_tallies: int, ta
     _check("rddmc_launch_packets_noalloc", lib().rddmc_launch_packets_noalloc(
         ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(opts), ctypes.c_void_p(d_tallies),
         int(tally_bytes), ctypes.c_void_p(stream)))
+
+
+def redistribution_bytes(grid) -> int:
+    """rddmc_redistribution_bytes."""
+    return int(lib().rddmc_redistribution_bytes(ctypes.c_void_p(grid)))
+
+
+def precompute_redistribution(grid, d_table: int, n_sub: int, d_redist: int, nbytes: int, stream: int = 0):
+    """rddmc_precompute_redistribution (eq. R_discrete thresholds; enqueued)."""
+    _check("rddmc_precompute_redistribution", lib().rddmc_precompute_redistribution(
+        ctypes.c_void_p(grid), ctypes.c_void_p(d_table), int(n_sub), ctypes.c_void_p(d_redist), int(nbytes),
+        ctypes.c_void_p(stream)))
 
 
 def time_state_bytes(n_packets: int) -> int:
@@ -338,10 +354,11 @@ class Problem:
 
     def launch(self, n_packets: int, seed: int, max_steps: int = 0, steps_per_launch: int = 0, resume: int = 0,
                ctas_per_sm: int = 0, threads_per_cta: int = 0, chunk: int = 0, table_in_smem: int = 0,
-               proposal: "Proposal" = None, time_slice_us: int = 0):
+               proposal: "Proposal" = None, time_slice_us: int = 0, redist=None):
         st = self.ensure_state(n_packets)
         o = RunOpts(seed, n_packets, max_steps, steps_per_launch, resume, ctas_per_sm, threads_per_cta, chunk,
-                    table_in_smem, time_slice_us, ctypes.addressof(proposal) if proposal is not None else None)
+                    table_in_smem, time_slice_us, ctypes.addressof(proposal) if proposal is not None else None,
+                    redist.data_ptr() if redist is not None else None)
         launch_packets(self.grid, self.table.data_ptr(), o, st.data_ptr(), st.numel(), self.tally.data_ptr(),
                        self.tally.numel() * 8, self.stream())
 
@@ -352,6 +369,15 @@ class Problem:
         self.reset()
         self.launch(n_packets, seed, **kw)
         return self.read()
+
+    def redistribution(self, n_sub: int = 3):
+        """Device thresholds of eq. R_discrete for this grid (uint32 tensor, J x (J-1)),
+        for launch(..., redist=...) on a hybrid table."""
+        torch = self.torch
+        nb = redistribution_bytes(self.grid)
+        buf = torch.empty(nb // 4, dtype=torch.int32, device=self.device)
+        precompute_redistribution(self.grid, self.table.data_ptr(), n_sub, buf.data_ptr(), nb, self.stream())
+        return buf
 
     def time_run(self, n_packets: int, seed: int, t_edges, max_steps: int = 0, chunk: int = 0,
                  threads_per_cta: int = 0, ctas_per_sm: int = 0, leaks: bool = False) -> dict:
