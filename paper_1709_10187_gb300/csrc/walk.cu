@@ -53,6 +53,7 @@ struct McPacket {
     int idx[3];
     unsigned cell;
     float r[3], n[3], x;
+    int bin;  // frequency grouping: the bin of x when known, else -1
 };
 
 __device__ __forceinline__ int bin_of(const WalkParams& P, float xf) {
@@ -168,6 +169,7 @@ __device__ __noinline__ McResult mc_excursion(const WalkParams& P, unsigned cell
     m.idx[1] = NDIM == 3 ? (int)((cell / (unsigned)P.n0) % (unsigned)P.n[1]) : 0;
     m.idx[2] = NDIM == 3 ? (int)(cell / (unsigned)P.n01) : 0;
     m.r[0] = m.r[1] = m.r[2] = 0.0f;
+    m.bin = (int)bin;
     McResult res;
     res.status = 2; res.cell = cell; res.bin = bin; res.hist = 0; res.sb = -1; res.face = 0;
     ++n_conv;
@@ -194,9 +196,15 @@ __device__ __noinline__ McResult mc_excursion(const WalkParams& P, unsigned cell
         const unsigned cls = min(__ldg(&P.cell_class[min(m.cell, (unsigned)P.ncell - 1u)]), (unsigned)P.n_class - 1u);
         // frequency grouping (Sec. 5.3): the bin-mean opacity of the packet's bin
         // (the end bin past the grid, where the leakage has no flux either)
-        const unsigned jb = (unsigned)min(max(bin_of(P, m.x), 0), P.J - 1);
-        const float k = P.redist ? __ldg(&P.tau_row[cls * (unsigned)P.J + jb]) * P.inv_dzmin
-                                 : (float)P.cdesc[cls].k0 * voigt_H_f32(P.a, m.x);
+        unsigned jb = 0;
+        float k;
+        if (P.redist) {
+            if (m.bin < 0) m.bin = min(max(bin_of(P, m.x), 0), P.J - 1);  // after a face crossing
+            jb = (unsigned)m.bin;
+            k = __ldg(&P.tau_row[cls * (unsigned)P.J + jb]) * P.inv_dzmin;
+        } else {
+            k = (float)P.cdesc[cls].k0 * voigt_H_f32(P.a, m.x);
+        }
         const float sflight = -__logf(es.u01()) / k;
         float dmin = 3.0e38f;
         int fax = 0, fside = 1;
@@ -224,10 +232,11 @@ __device__ __noinline__ McResult mc_excursion(const WalkParams& P, unsigned cell
                 }
                 m.x = (float)(P.edges[lo] + (double)es.u01() * (P.edges[lo + 1] - P.edges[lo]));
                 iso_dir(es, m.n);
+                m.bin = lo;
             } else {
                 m.x = scatter(P.a, m.x, m.n, P.upar, es);
             }
-            const int j = bin_of(P, m.x);
+            const int j = P.redist ? m.bin : bin_of(P, m.x);
             if (thick_state<NDIM>(P, m.cell, j)) {
                 ++n_conv;
                 res.status = 0; res.cell = m.cell; res.bin = (unsigned)j;
@@ -239,6 +248,7 @@ __device__ __noinline__ McResult mc_excursion(const WalkParams& P, unsigned cell
         for (int q = 0; q < 3; ++q) m.r[q] += dmin * m.n[q];
         m.r[fax] = face_coord<NDIM>(P, fax, m.idx[fax] + (fside > 0 ? 1 : 0));
         done = mc_cross<NDIM>(P, m, fax, fside, es, n_conv, res);
+        m.bin = -1;  // a crossing may shift x (Doppler, reflection): look the bin up again
     }
     e = es.e;
     return res;
