@@ -24,6 +24,7 @@ class OrcGrid(ctypes.Structure):
         ("tau_ddmc", ctypes.c_double), ("lam", ctypes.c_double), ("f_mu", ctypes.c_double),
         ("edges", ctypes.c_void_p), ("n_rel", ctypes.c_void_p), ("v", ctypes.c_void_p), ("mask", ctypes.c_void_p),
         ("dust_abs", ctypes.c_double), ("dust_scat", ctypes.c_double), ("redist", ctypes.c_void_p),
+        ("dust_weights", ctypes.c_int32), ("pad", ctypes.c_int32),
     ]
 
 
@@ -46,10 +47,13 @@ def lib():
         L.orc_philox4x32_10.restype = None
         L.orc_philox4x32_10.argtypes = [vp, vp, vp]
         L.orc_build_table.restype = i32
-        L.orc_build_table.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, vp]
+        L.orc_build_table.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, vp, vp]
         L.orc_tally_len.restype = i32
         L.orc_tally_len.argtypes = [i32]
         L.orc_walk_ddmc.restype = i32
+        L.orc_walk_weights.restype = i32
+        L.orc_walk_weights.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, d, u64, u64, u64, u64, i32,
+                                       vp, vp]
         L.orc_walk_ddmc.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, vp, vp, d, u64, u64, u64, u64, i32, i32,
                                     vp]
         L.orc_walk_slice.restype = i32
@@ -116,7 +120,7 @@ class Grid:
     """An oracle grid built from a workload; keeps the numpy buffers alive."""
 
     def __init__(self, w, hybrid=False, tau_ddmc=5.0, lam=0.7104, f_mu=0.5, n_rel=None, edges=None, dust_abs=0.0,
-                 dust_scat=0.0, redist=None):
+                 dust_scat=0.0, redist=None, dust_weights=False):
         self.w = w
         e = w.edges() if edges is None else edges
         self.edges = np.ascontiguousarray(e, dtype=np.float64)
@@ -137,9 +141,10 @@ class Grid:
         # frequency-grouped MC (Sec. 5.3): J x (J-1) thresholds of eq. R_discrete, kept alive with the grid
         self.redist = None if redist is None else np.ascontiguousarray(redist, dtype=np.uint32)
         g.redist = _ptr(self.redist)
+        g.dust_weights = 1 if dust_weights else 0  # continuous absorption by packet weights (Sec. 2.6)
         self.g = g
         self.K = 2 + 2 * w.ndim
-        self.KT = self.K + (1 if dust_abs > 0.0 else 0)  # outcomes, dust absorption last
+        self.KT = self.K + (1 if dust_abs > 0.0 and not dust_weights else 0)  # outcomes, dust absorption last
         self.ncell = w.ncell
         self.J = w.J
 
@@ -150,9 +155,10 @@ class Grid:
             thr=np.zeros(nS * (K - 1), dtype=np.uint32), flags=np.zeros(nS, dtype=np.uint32),
             rebin_m=np.zeros(self.ncell * 2 * self.w.ndim, dtype=np.int32),
             rebin_thr=np.zeros(self.ncell * 2 * self.w.ndim, dtype=np.uint32),
-            k=np.zeros(nS, dtype=np.float64), rate=np.zeros(nS * K, dtype=np.float64))
+            k=np.zeros(nS, dtype=np.float64), rate=np.zeros(nS * K, dtype=np.float64),
+            surv=np.zeros(nS, dtype=np.float64))
         rc = lib().orc_build_table(ctypes.byref(self.g), _ptr(t["thr"]), _ptr(t["flags"]), _ptr(t["rebin_m"]),
-                                   _ptr(t["rebin_thr"]), _ptr(t["k"]), _ptr(t["rate"]))
+                                   _ptr(t["rebin_thr"]), _ptr(t["k"]), _ptr(t["rate"]), _ptr(t["surv"]))
         if rc != 0:
             raise RuntimeError(f"orc_build_table failed: {rc}")
         t["thr"] = t["thr"].reshape(nS, K - 1)
@@ -172,6 +178,26 @@ def unpack_tally(t: np.ndarray, J: int) -> dict:
     d["faces"] = t[_T_FACE:_T_FACE + 6].astype(np.uint64).copy()
     d["hist"] = t[_T_HIST:_T_HIST + J + 2].astype(np.uint64).copy()
     d["sb"] = t[_T_HIST + J + 2:_T_HIST + J + 2 + NSB].astype(np.uint64).copy()
+    return d
+
+
+def walk_weights(grid: Grid, table: dict, seed: int, p0: int, npk: int, max_steps: int = (1 << 62),
+                 nthreads: int = 0) -> dict:
+    """The DDMC walk with continuous absorption by packet weights (orc_walk_weights;
+    a grid with dust_weights): the integer tallies plus the escaped weight, in
+    total (escaped_weight) and per escape-histogram bin (weight_hist, J + 2)."""
+    if nthreads <= 0:
+        nthreads = os.cpu_count() or 1
+    out = np.zeros(lib().orc_tally_len(grid.J), dtype=np.uint64)
+    wt = np.zeros(grid.J + 3, dtype=np.float64)
+    thr = np.ascontiguousarray(table["thr"].ravel())
+    rc = lib().orc_walk_weights(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
+                                _ptr(table["rebin_thr"]), _ptr(table["surv"]), float(grid.w.x0), int(seed), int(p0),
+                                int(npk), int(max_steps), int(nthreads), _ptr(out), _ptr(wt))
+    if rc != 0:
+        raise RuntimeError(f"orc_walk_weights failed: {rc}")
+    d = unpack_tally(out, grid.J)
+    d.update(escaped_weight=float(wt[0]), weight_hist=wt[1:].copy())
     return d
 
 

@@ -173,6 +173,9 @@ typedef struct orc_grid {
     double dust_scat;     /* dust scattering k_s R at unit density (grey), added to k_ij */
     const uint32_t* redist; /* hybrid only: frequency-grouped MC (Sec. 5.3) with these cumulative
                                thresholds of eq. R_discrete, J rows of J-1; NULL = continuous MC */
+    int32_t dust_weights; /* 1: continuous absorption (Sec. 2.6): no absorption outcome; the
+                             packet weight is multiplied by K_s / (K_s + k_a) per transition */
+    int32_t pad;
 } orc_grid;
 
 /* Actions stored two bits per outcome in the flags word. */
@@ -187,7 +190,8 @@ static int64_t orc_ncell(const orc_grid* g) { return (int64_t)g->n[0] * g->n[1] 
 static int orc_nout(const orc_grid* g) { return 2 + 2 * g->ndim; }
 /* Dust absorption is one more outcome, K = orc_nout, after the leakage
  * outcomes: thresholds per state orc_nthr = K - 1 (+1 with absorption). */
-static int orc_dusty(const orc_grid* g) { return g->dust_abs > 0.0; }
+static int orc_dusty(const orc_grid* g) { return g->dust_abs > 0.0 && !g->dust_weights; }
+#define ORC_W_MIN 1e-10  /* packets below this weight are eliminated (Sec. 2.6) */
 static int orc_nthr(const orc_grid* g) { return orc_nout(g) - 1 + orc_dusty(g); }
 
 static int orc_in_medium(const orc_grid* g, const int idx[3]) {
@@ -247,9 +251,9 @@ static uint32_t orc_quantise(double C) {
  * Returns 0, or -1 for an unsupported grid.
  */
 int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* rebin_m,
-                    uint32_t* rebin_thr, double* k_out, double* rate_out) {
+                    uint32_t* rebin_thr, double* k_out, double* rate_out, double* surv_out) {
     if (g->ndim != 1 && g->ndim != 3) return -1;
-    if (g->dust_abs < 0.0 || g->dust_scat < 0.0 || (orc_dusty(g) && g->hybrid)) return -1;
+    if (g->dust_abs < 0.0 || g->dust_scat < 0.0 || (g->dust_abs > 0.0 && g->hybrid)) return -1;
     const int J = g->J, K = orc_nout(g), NT = orc_nthr(g), KT = NT + 1;
     const int64_t nc = orc_ncell(g);
     const double a = orc_damping(g->T);
@@ -341,6 +345,9 @@ int orc_build_table(const orc_grid* g, uint32_t* thr, uint32_t* flags, int32_t* 
             if (orc_dusty(g)) rate[K] = kac;  /* absorption, the last outcome */
             double tot = 0.0;
             for (int o = 0; o < KT; ++o) tot += rate[o];
+            /* continuous absorption: the expected weight kept over one dwell,
+             * E[exp(-k_a dl)] = K_s / (K_s + k_a) for dl ~ Exp(K_s) */
+            if (surv_out) surv_out[s] = g->dust_weights ? tot / (tot + kac) : 1.0;
             double C = 0.0;
             for (int o = 0; o < NT; ++o) {
                 C += rate[o] / tot;
@@ -428,6 +435,8 @@ typedef struct orc_walk_args {
     uint64_t limit;      /* transitions per packet, UINT64_MAX = until escape or abort */
     const double* k;     /* k_ij per state (hybrid walk) */
     const double* upar;  /* (u1, u0) rejection-envelope split points per |x| grid point (hybrid) */
+    const double* surv;  /* continuous absorption: weight factor per state, NULL = none */
+    double* wtally;      /* per-thread escaped weight: [0] total, [1 + b] per histogram bin b */
     uint64_t* tally;     /* per-thread */
     int status;
 } orc_walk_args;
@@ -438,13 +447,13 @@ typedef struct orc_walk_args {
  * isotropic outward direction (mu uniform on (0,1], azimuth phi uniform) and x
  * uniform in the bin; tally x_obs = x + n.u_c (u = v/v_th) and, in 3D, the
  * impact parameter b = |r x n| of the escaping ray. */
-static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t pk, uint64_t* e, uint64_t* t) {
+static int orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t pk, uint64_t* e, uint64_t* t) {
     const orc_grid* g = A->g;
     const int J = g->J;
     int face = o - 2;
     t[ORC_T_ESCAPED]++;
     t[ORC_T_FACE + face]++;
-    if (g->ndim == 1 && !(A->flags[c * J + j] & ORC_FLAG_MOVING)) { t[ORC_T_HIST + 1 + j]++; return; }
+    if (g->ndim == 1 && !(A->flags[c * J + j] & ORC_FLAG_MOVING)) { t[ORC_T_HIST + 1 + j]++; return 1 + j; }
     int ax = face / 2, side = (face & 1) ? 1 : -1;
     int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
     int idx[3];
@@ -486,6 +495,7 @@ static void orc_escape(const orc_walk_args* A, int64_t c, int j, int o, uint64_t
         if (k > ORC_NSB - 1) k = ORC_NSB - 1;
         t[ORC_T_HIST + J + 2 + k]++;
     }
+    return b;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -791,6 +801,7 @@ typedef struct orc_pstate {
     int j;
     uint64_t steps, e;
     int done;      /* 0 in flight, 1 escaped, 2 aborted, 3 met an MC state, 4 absorbed by dust */
+    double w;      /* packet weight (continuous absorption) */
 } orc_pstate;
 
 /* Advance packet pk by at most `limit` transitions (stopping at escape or at
@@ -839,8 +850,15 @@ static void orc_advance(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t l
         P->steps++;
         t[ORC_T_STEPS]++;
         if (o == K) { t[ORC_T_ABSORBED]++; P->done = 4; return; }  /* absorbed by dust (Sec. 2.6) */
+        if (A->surv) P->w *= A->surv[s];  /* continuous absorption over the dwell in s */
         unsigned act = (A->flags[s] >> (2 * o)) & 3u;
-        if (act == ORC_ACT_ESCAPE) { orc_escape(A, c, P->j, o, pk, &P->e, t); P->done = 1; return; }
+        if (act == ORC_ACT_ESCAPE) {
+            const int b = orc_escape(A, c, P->j, o, pk, &P->e, t);
+            if (A->wtally) { A->wtally[0] += P->w; A->wtally[1 + b] += P->w; }  /* the escaped weight */
+            P->done = 1;
+            return;
+        }
+        if (A->surv && P->w < ORC_W_MIN) { t[ORC_T_ABSORBED]++; P->done = 4; return; }
         if (act == ORC_ACT_TO_MC) {
             if (!A->upar) { A->status = -2; t[ORC_T_ABORTED]++; P->done = 3; return; }
             orc_mc m;
@@ -876,6 +894,7 @@ static void orc_advance(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t l
 
 static void orc_start(orc_walk_args* A, uint64_t pk, orc_pstate* P, uint64_t* t) {
     memset(P, 0, sizeof(*P));
+    P->w = 1.0;
     orc_emit(A->src, orc_word(A->seed, pk, ORC_EVENT, P->e++), P->idx, &P->j);
     t[ORC_T_EMITTED]++;
 }
@@ -907,7 +926,7 @@ static void* orc_walk_thread(void* vp) {
 static int orc_walk_run(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
                         const uint32_t* rebin_thr, const double* rate, const double* k, double x0, uint64_t seed,
                         uint64_t p0, uint64_t np, uint64_t max_steps, int literal, uint64_t limit, int nthreads,
-                        uint64_t* tally) {
+                        uint64_t* tally, const double* surv, double* wtally) {
     double* upar = NULL;
     if (g->hybrid) {
         if (!k) return -1;
@@ -923,6 +942,8 @@ static int orc_walk_run(const orc_grid* g, const uint32_t* thr, const uint32_t* 
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
     orc_walk_args* args = (orc_walk_args*)calloc(nthreads, sizeof(orc_walk_args));
     uint64_t* tl = (uint64_t*)calloc((size_t)nthreads * L, sizeof(uint64_t));
+    const int LW = g->J + 3;
+    double* twl = wtally ? (double*)calloc((size_t)nthreads * LW, sizeof(double)) : NULL;
     for (int i = 0; i < nthreads; ++i) {
         orc_walk_args* A = &args[i];
         A->g = g; A->thr = thr; A->flags = flags; A->rebin_m = rebin_m; A->rebin_thr = rebin_thr;
@@ -930,6 +951,8 @@ static int orc_walk_run(const orc_grid* g, const uint32_t* thr, const uint32_t* 
         A->limit = limit;
         A->k = k;
         A->upar = upar;
+        A->surv = surv;
+        A->wtally = twl ? twl + (size_t)i * LW : NULL;
         A->p0 = p0 + np * (uint64_t)i / nthreads;
         A->p1 = p0 + np * (uint64_t)(i + 1) / nthreads;
         A->tally = tl + (size_t)i * L;
@@ -937,12 +960,15 @@ static int orc_walk_run(const orc_grid* g, const uint32_t* thr, const uint32_t* 
     }
     int status = 0;
     memset(tally, 0, sizeof(uint64_t) * L);
+    if (wtally) memset(wtally, 0, sizeof(double) * LW);
     for (int i = 0; i < nthreads; ++i) {
         pthread_join(th[i], NULL);
         for (int q = 0; q < L; ++q) tally[q] += tl[(size_t)i * L + q];
+        if (twl)
+            for (int q = 0; q < LW; ++q) wtally[q] += twl[(size_t)i * LW + q];
         if (args[i].status) status = args[i].status;
     }
-    free(th); free(args); free(tl); free(upar);
+    free(th); free(args); free(tl); free(upar); free(twl);
     return status;
 }
 
@@ -950,7 +976,24 @@ int orc_walk_ddmc(const orc_grid* g, const uint32_t* thr, const uint32_t* flags,
                   const uint32_t* rebin_thr, const double* rate, const double* k, double x0, uint64_t seed,
                   uint64_t p0, uint64_t np, uint64_t max_steps, int literal, int nthreads, uint64_t* tally) {
     return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, rate, k, x0, seed, p0, np, max_steps, literal,
-                        UINT64_MAX, nthreads, tally);
+                        UINT64_MAX, nthreads, tally, NULL, NULL);
+}
+
+/*
+ * The DDMC walk with continuous absorption by dust (Sec. 2.6, the weight
+ * method): a packet's weight is multiplied by surv[s] = K_s / (K_s + k_a) at
+ * each transition out of state s (the expected attenuation exp(-k_a dl) over
+ * its dwell dl ~ Exp(K_s); the categorical walk has no path length) and the
+ * packet is eliminated (counted as absorbed) once it falls below 1e-10.
+ * wtally (J + 3 doubles, overwritten): [0] total escaped weight, [1 + b] the
+ * escaped weight in escape-histogram bin b.  The grid needs dust_weights = 1.
+ */
+int orc_walk_weights(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
+                     const uint32_t* rebin_thr, const double* surv, double x0, uint64_t seed, uint64_t p0,
+                     uint64_t np, uint64_t max_steps, int nthreads, uint64_t* tally, double* wtally) {
+    if (!g || !surv || !wtally || !g->dust_weights || g->hybrid) return -1;
+    return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, NULL, NULL, x0, seed, p0, np, max_steps, 0, UINT64_MAX,
+                        nthreads, tally, surv, wtally);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1143,7 +1186,7 @@ int orc_walk_slice(const orc_grid* g, const uint32_t* thr, const uint32_t* flags
                    const uint32_t* rebin_thr, const double* k, double x0, uint64_t seed, uint64_t p0, uint64_t np,
                    uint64_t n_trans, int nthreads, uint64_t* tally) {
     return orc_walk_run(g, thr, flags, rebin_m, rebin_thr, NULL, k, x0, seed, p0, np, (uint64_t)1 << 62, 0, n_trans,
-                        nthreads, tally);
+                        nthreads, tally, NULL, NULL);
 }
 
 /*

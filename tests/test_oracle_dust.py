@@ -115,3 +115,49 @@ def test_dusty_time_walk_follows_the_chain():
     assert abs(r["absorbed"] / n - absorbed_exp) <= 5.0 * np.sqrt(absorbed_exp * (1 - absorbed_exp) / n)
     done = (r["esc"].sum() + r["absorbed"]) / n
     assert abs(done - lost.sum()) <= 5.0 * np.sqrt(lost.sum() * (1 - lost.sum()) / n)
+
+
+@pytest.mark.parametrize("tau_a", [0.3, 20.0])
+def test_weight_method_has_the_probabilistic_escape_in_expectation(tau_a):
+    """The continuous method of Sec. 2.6: weights multiplied by K_s/(K_s+k_a)
+    per transition (the expected exp(-k_a dl) over a dwell) give an escaped
+    weight whose expectation, in total and per escape bin, is the escape
+    probability of the probabilistic method (the absorbing chain); weights lie
+    in [0, 1], so the standard error is at most sqrt(p/n).  At tau_a = 20 many
+    packets fall below the 1e-10 elimination weight."""
+    w = W.SMALL.with_(packets=40_000)
+    n = w.packets
+    g = C.Grid(w, dust_abs=tau_a, dust_scat=2.0, dust_weights=True)
+    t = g.table()
+    assert t["thr"].shape[1] == 3  # no absorption outcome in the weight method
+    r = C.walk_weights(g, t, w.seed, 0, n)
+    ch = A.chain_solve(w, C.Grid(w, dust_abs=tau_a, dust_scat=2.0).table())
+    p = ch["escape_total"]
+    assert r["escaped"] + r["absorbed"] == n
+    assert abs(r["escaped_weight"] / n - p) <= 5.0 * np.sqrt(p / n) + 1e-10, (r["escaped_weight"] / n, p)
+    h = ch["hist"]
+    sel = h * n >= 20.0
+    assert np.all(np.abs(r["weight_hist"][sel] / n - h[sel]) <= 5.0 * np.sqrt(h[sel] / n))
+    if tau_a > 1.0:
+        assert r["absorbed"] > 0
+    # the weight method tallies every escape: at most as noisy as counting the
+    # probabilistic walk's escapes
+    assert r["escaped"] >= C.walk(C.Grid(w, dust_abs=tau_a, dust_scat=2.0),
+                                  C.Grid(w, dust_abs=tau_a, dust_scat=2.0).table(), w.seed, 0, n)["escaped"]
+
+
+@pytest.mark.parametrize("tau_a", [0.5, 3.0])
+def test_weight_method_on_the_grey_slab_has_the_closed_form(tau_a):
+    """The mean escaped weight of the grey slab equals the closed-form escape
+    probability of the random walk with killing; batch means of 20 packet sets
+    give the (small) standard error of the weights."""
+    w = GREY21
+    g = C.Grid(w, dust_abs=tau_a, dust_scat=5.0, dust_weights=True)
+    t = g.table()
+    f = _closed_form_escape(w, float(t["k"][w.n[0] // 2]), tau_a / w.R)
+    B, m = 20, 10_000
+    means = np.array([C.walk_weights(g, t, w.seed, b * m, m)["escaped_weight"] / m for b in range(B)])
+    se = means.std(ddof=1) / np.sqrt(B)
+    assert abs(means.mean() - f) <= 5.0 * se, (means.mean(), f, se)
+    # far tighter than counting the escapes of as many probabilistic packets
+    assert se < 0.5 * np.sqrt(f * (1.0 - f) / (B * m)), (se, np.sqrt(f * (1.0 - f) / (B * m)))
