@@ -50,6 +50,9 @@ extern "C" {
 #define RDDMC_MODE_DDMC 0         /* DDMC in every state (Sec. 3.2 test problems) */
 #define RDDMC_MODE_HYBRID 1       /* thin states hand off to continuous MC (Sec. 5.1-5.2) */
 
+#define RDDMC_DUST_PROBABILISTIC 0 /* dust absorption as a competing process (Sec. 2.6) */
+#define RDDMC_DUST_WEIGHTS 1       /* dust absorption by packet weights (Sec. 2.6) */
+
 #define RDDMC_LAYOUT_DEDUP 0      /* one row block per class of identical cells */
 #define RDDMC_LAYOUT_DENSE 1      /* one row block per cell */
 
@@ -100,13 +103,20 @@ typedef struct rddmc_grid_desc {
  *             is one more competing process, the last outcome of every
  *             state's categorical draw, and an absorbed packet ends (counted
  *             in rddmc_tallies.absorbed).  dust_abs > 0 requires DDMC mode.
+ *   dust_method RDDMC_DUST_PROBABILISTIC (0, above) or RDDMC_DUST_WEIGHTS (1,
+ *             the continuous method): no absorption outcome; each transition
+ *             out of state s multiplies the packet weight by K_s/(K_s + k_a),
+ *             the expected attenuation exp(-k_a dl) over its dwell, packets
+ *             below weight 1e-10 are eliminated (counted absorbed) and escapes
+ *             carry their weight (rddmc_tallies.escaped_weight,
+ *             rddmc_read_escape_weights).  The persistent walk only.
  */
 typedef struct rddmc_leak_params {
     double tau_ddmc;
     double lambda;
     double f_mu;
     int32_t mode;
-    int32_t reserved;
+    int32_t dust_method;
     double dust_abs;
     double dust_scat;
 } rddmc_leak_params;
@@ -191,7 +201,8 @@ typedef struct rddmc_tallies {
     uint64_t event_draws;  /* words taken from the packets' event streams */
     uint64_t proposals;    /* learned exit proposals taken */
     uint64_t proposed_steps; /* DDMC transitions the proposals stood in for (sampled) */
-    uint64_t absorbed;     /* packets absorbed by dust (Sec. 2.6) */
+    uint64_t absorbed;     /* packets absorbed by dust (Sec. 2.6), or eliminated below weight 1e-10 */
+    double escaped_weight; /* weight method: summed weight of the escaped packets (2^-32 resolution) */
     int32_t status;        /* RDDMC_OK or a device-side error code */
     int32_t nbins;         /* J; the histogram has J + 2 entries */
     int32_t nfaces;        /* 2 (slab) or 6 (3D) */
@@ -308,6 +319,11 @@ int rddmc_launch_packets(const rddmc_grid* grid, const void* d_table, const rddm
  */
 int rddmc_read_tallies(const rddmc_grid* grid, const void* d_tallies, rddmc_tallies* out, uint64_t* hist,
                        uint64_t* faces, uint64_t* sb, void* stream);
+
+/* Escaped weight per escape-histogram bin (weight method of dust absorption):
+ * host, J + 2 doubles, the bins of rddmc_read_tallies' hist.  Synchronises.
+ * Errors: RDDMC_ERR_ARG, RDDMC_ERR_CUDA. */
+int rddmc_read_escape_weights(const rddmc_grid* grid, const void* d_tallies, double* whist, void* stream);
 
 /*
  * rddmc_table_rows -- expand the device table to one row per state (host), for
@@ -647,7 +663,7 @@ int rddmc_scatter_samples(const rddmc_grid* grid, const void* d_table, double x_
  *   Arguments and results are those of rddmc_launch_packets without d_state
  *   and state_bytes.  A run to completion (steps_per_launch = 0, resume = 0)
  *   takes any packet count; time-sliced or resumed runs must fit their
- *   per-packet state in the array (about 1.3 million packets) and otherwise
+ *   per-packet state in the array (about 1 million packets) and otherwise
  *   get RDDMC_ERR_SIZE.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream

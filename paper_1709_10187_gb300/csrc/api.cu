@@ -44,10 +44,13 @@ uint64_t state_bytes_for(uint64_t np) {
     b += align256(np * 8);                // transitions so far
     b += align256(np * 8);                // event draws so far
     b += align256(np * 1);                // status
+    b += align256(np * 8);                // -ln(weight) in 2^-40 units (dust weight method)
     return b;
 }
 
-int tally_words(int J) { return kHistOff + J + 2 + kNsb; }
+// counters, faces, escape histogram, impact parameters, then the escaped
+// weight (u64, 2^-32 units): total and per escape-histogram bin
+int tally_words(int J) { return kHistOff + J + 2 + kNsb + J + 3; }
 uint64_t tally_bytes_for(int J) { return (uint64_t)tally_words(J) * 8ull; }
 
 }  // namespace rddmc
@@ -209,6 +212,7 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
     g->off_upar = off; off += align256((uint64_t)kUparN * 8);
     g->off_rk = off; off += align256((uint64_t)g->n_class * J * 4);
     g->off_abs = off; off += align256((uint64_t)g->n_class * J * 4);
+    g->off_wq = off; off += align256((uint64_t)g->n_class * J * 8);
     g->table_bytes = off;
     *out = g;
     return RDDMC_OK;
@@ -240,6 +244,7 @@ int rddmc_precompute_leakage(rddmc_grid* g, const rddmc_leak_params* p, void* d_
     if (!(p->dust_abs >= 0.0) || !(p->dust_scat >= 0.0) || !std::isfinite(p->dust_abs) ||
         !std::isfinite(p->dust_scat))
         return RDDMC_ERR_ARG;
+    if (p->dust_method != RDDMC_DUST_PROBABILISTIC && p->dust_method != RDDMC_DUST_WEIGHTS) return RDDMC_ERR_ARG;
     if (p->dust_abs > 0.0 && p->mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     g->params = *p;
@@ -344,7 +349,8 @@ int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_r
     if (o->proposal) {
         const rddmc_proposal* pr = o->proposal;
         // the learned proposal samples first passages without absorption
-        if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty()) return RDDMC_ERR_UNSUPPORTED;
+        if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty() || g->weighted())
+            return RDDMC_ERR_UNSUPPORTED;
         if (o->steps_per_launch == 0 && o->resume == 0 && o->time_slice_us == 0) return RDDMC_ERR_ARG;
         if (pr->brick < 1 || pr->brick > 64 || pr->offset < 0 || pr->offset >= pr->brick) return RDDMC_ERR_ARG;
         if (pr->margin < 0 || 2 * pr->margin >= pr->brick) return RDDMC_ERR_ARG;
@@ -377,6 +383,7 @@ int rddmc_read_tallies(const rddmc_grid* g, const void* d_tallies, rddmc_tallies
     out->proposals = t[C_PROPOSALS];
     out->proposed_steps = t[C_PROPOSED_STEPS];
     out->absorbed = t[C_ABSORBED];
+    out->escaped_weight = (double)t[kHistOff + g->J + 2 + kNsb] * (1.0 / 4294967296.0);
     out->status = RDDMC_OK;
     if (t[C_ABORTED]) out->status = RDDMC_ERR_STEP_LIMIT;
     if (t[C_STATUS_BITS] & STATUS_UNSUPPORTED_EVENT) out->status = RDDMC_ERR_UNSUPPORTED;
@@ -386,6 +393,19 @@ int rddmc_read_tallies(const rddmc_grid* g, const void* d_tallies, rddmc_tallies
     if (hist) std::memcpy(hist, t.data() + kHistOff, (size_t)(g->J + 2) * 8);
     if (faces) std::memcpy(faces, t.data() + kFaceOff, (size_t)g->nfaces * 8);
     if (sb) std::memcpy(sb, t.data() + kHistOff + g->J + 2, (size_t)kNsb * 8);
+    return RDDMC_OK;
+}
+
+int rddmc_read_escape_weights(const rddmc_grid* g, const void* d_tallies, double* whist, void* stream) {
+    if (!g || !d_tallies || !whist) return RDDMC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<uint64_t> t(g->J + 2);
+    const uint64_t off = (uint64_t)(kHistOff + g->J + 2 + kNsb + 1) * 8;
+    if (cudaMemcpyAsync(t.data(), (const char*)d_tallies + off, t.size() * 8, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return RDDMC_ERR_CUDA;
+    for (size_t i = 0; i < t.size(); ++i) whist[i] = (double)t[i] * (1.0 / 4294967296.0);
     return RDDMC_OK;
 }
 

@@ -392,7 +392,7 @@ int rddmc_batch_create(const rddmc_grid* const* grids, const void* const* d_tabl
         const rddmc_grid* g = grids[i];
         if (!g || !d_tables[i] || ((uintptr_t)d_tables[i] & 255u) || n_packets[i] == 0) { delete b; return RDDMC_ERR_ARG; }
         if (!g->precomputed) { delete b; return RDDMC_ERR_TABLE; }
-        if (g->params.mode != RDDMC_MODE_DDMC || g->dusty()) { delete b; return RDDMC_ERR_UNSUPPORTED; }
+        if (g->params.mode != RDDMC_MODE_DDMC || g->dusty() || g->weighted()) { delete b; return RDDMC_ERR_UNSUPPORTED; }
         const char* tb = (const char*)d_tables[i];
         InstDesc D;
         std::memset(&D, 0, sizeof(D));

@@ -33,11 +33,13 @@ struct rddmc_grid {
     int src_bin[2] = {0, 0};
     // table layout (byte offsets)
     uint64_t off_class = 0, off_cdesc = 0, off_rebin = 0, off_vel = 0, off_edges = 0, off_phi = 0,
-             off_rows = 0, off_fast = 0, off_tau = 0, off_upar = 0, off_rk = 0, off_abs = 0, table_bytes = 0;
+             off_rows = 0, off_fast = 0, off_tau = 0, off_upar = 0, off_rk = 0, off_abs = 0, off_wq = 0, table_bytes = 0;
     // leakage parameters of the last precompute
     rddmc_leak_params params{};
     bool precomputed = false;
-    bool dusty() const { return params.dust_abs > 0.0; }  // absorption outcome present
+    // dust absorption as an outcome of the draw, or by packet weights (Sec. 2.6)
+    bool dusty() const { return params.dust_abs > 0.0 && params.dust_method == RDDMC_DUST_PROBABILISTIC; }
+    bool weighted() const { return params.dust_abs > 0.0 && params.dust_method == RDDMC_DUST_WEIGHTS; }
 
     bool in_medium(const int idx[3]) const;
     int64_t cell_of(const int idx[3]) const { return idx[0] + (int64_t)n[0] * (idx[1] + (int64_t)n[1] * idx[2]); }

@@ -141,7 +141,8 @@ int rddmc_fp_generate(const rddmc_grid* const* grids, const void* const* d_table
         const rddmc_grid* g = grids[l];
         if (!g || !d_tables[l]) return RDDMC_ERR_ARG;
         if (!g->precomputed) return RDDMC_ERR_TABLE;
-        if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty()) return RDDMC_ERR_UNSUPPORTED;
+        if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty() || g->weighted())
+            return RDDMC_ERR_UNSUPPORTED;
         if (J < 0) J = g->J;
         if (g->J != J) return RDDMC_ERR_ARG;
         int idx[3] = {g->n[0] / 2, g->n[1] / 2, g->n[2] / 2};

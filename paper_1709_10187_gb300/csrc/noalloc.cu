@@ -64,7 +64,7 @@ extern "C" int rddmc_launch_packets_noalloc(const rddmc_grid* g, const void* d_t
     if (tally_bytes < rddmc::tally_bytes_for(g->J)) return RDDMC_ERR_SIZE;
     // A run to completion only uses the packet cursor; time-sliced or resumed
     // runs keep every packet's state in the array, which bounds their packet
-    // count (about 1.3 million packets).
+    // count (about 1 million packets).
     const bool sliced = o->steps_per_launch != 0 || o->resume != 0 || o->time_slice_us != 0;
     const uint64_t need = sliced ? rddmc::state_bytes_for(o->n_packets) : 256ull;
     if (need > (uint64_t)RDDMC_NOALLOC_SCRATCH_BYTES) return RDDMC_ERR_SIZE;

@@ -447,7 +447,8 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
         ((uintptr_t)d_path & 7u) || ((uintptr_t)d_counts & 7u) || ((uintptr_t)d_leak & 7u))
         return RDDMC_ERR_ARG;
     if (!g->precomputed) return RDDMC_ERR_TABLE;
-    if (g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
+    // dust by packet weights is the persistent walk's method only
+    if (g->params.mode != RDDMC_MODE_DDMC || g->weighted()) return RDDMC_ERR_UNSUPPORTED;
     if (ts->n_packets < 1 || ts->n_packets >= (1ull << 62)) return RDDMC_ERR_ARG;
     if (!(std::isfinite(ts->t_begin) && std::isfinite(ts->t_end) && ts->t_end > ts->t_begin)) return RDDMC_ERR_ARG;
     if (ts->chunk < 0 || ts->chunk % 4 || ts->chunk > (1 << 20)) return RDDMC_ERR_ARG;

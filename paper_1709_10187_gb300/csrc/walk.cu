@@ -34,6 +34,9 @@
 namespace rddmc {
 namespace {
 
+// weight method: -ln(1e-10) in 2^-40 units, the elimination weight of Sec. 2.6
+constexpr unsigned long long kLwMin = 25317190836906ull;
+
 #ifndef RDDMC_WALK_MIN_BLOCKS
 #define RDDMC_WALK_MIN_BLOCKS 4  // resident 256-thread CTAs per SM the register budget targets
 #endif
@@ -288,7 +291,7 @@ __device__ __forceinline__ bool prop_takes(const WalkParams& P, unsigned cell, u
     return l >= P.prop_llo && l <= P.prop_lhi;
 }
 
-template <int NDIM, bool SMEM_ROWS, bool HYBRID, bool PROPOSE>
+template <int NDIM, bool SMEM_ROWS, bool HYBRID, bool PROPOSE, bool WEIGHT>
 __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const WalkParams P) {
     constexpr int RW = NDIM == 1 ? 1 : 2;  // uint4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -314,6 +317,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
     const unsigned long long t_begin = P.time_slice_ns ? global_ns() : 0ull;
     bool have = false, exhausted = false;
     unsigned long long pid = 0, t = 0, e = 0, t_stop = 0;
+    unsigned long long lw = 0;  // weight method: -ln(packet weight) in 2^-40 units
     unsigned cell = 0, cls = 0, s = 0;  // s = cls * J + bin: the row of the state
     unsigned long long n_steps = 0, n_edraw = 0, n_mc = 0;
     unsigned n_emit = 0, n_esc = 0, n_abort = 0, n_clamp = 0, status_bits = 0, n_conv = 0;
@@ -338,11 +342,22 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         return true;
     };
 
+    // Weight method of dust absorption (Sec. 2.6): a packet whose weight fell
+    // below 1e-10 is eliminated and counted absorbed.
+    auto faded = [&]() -> bool {
+        if (WEIGHT && lw > kLwMin) {
+            atomicAdd(&s_cnt[C_ABSORBED], 1ull);
+            return true;
+        }
+        return false;
+    };
+
     // One full transition: every threshold, the outcome's action, spatial moves
     // with the class lookup, Doppler rebins and escapes.  Returns true when the
     // packet has finished.
     auto generic = [&](unsigned w) -> bool {
         const unsigned ri = min(s, nr1);
+        if (WEIGHT) lw += __ldg(&P.wq[ri]);  // the weight kept over the dwell in this state
         const uint4 a = __ldg(&rows[ri * RW]);
         unsigned o = (unsigned)(w >= a.x) + (unsigned)(w >= a.y) + (unsigned)(w >= a.z);
         if (NDIM == 3) {
@@ -357,7 +372,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         const unsigned act = (fl >> (2u * o)) & 3u;
         const unsigned bin = min(s - cls * J, J - 1u);
         if (o < 2u) {
-            if (act == ACT_MOVE) { s += o ? 1u : 0xffffffffu; return false; }
+            if (act == ACT_MOVE) { s += o ? 1u : 0xffffffffu; return faded(); }
             if (HYBRID && act == ACT_TO_MC)  // leak into a thin bin of this cell
                 return after_mc(mc_excursion<NDIM>(P, cell, o ? min(bin + 1u, J - 1u) : (bin ? bin - 1u : 0u), -1,
                                                    pid, e, n_mc, n_conv));
@@ -373,6 +388,12 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
             else atomicAdd(&P.tally[kHistOff + eb.hist], 1ull);
             if (eb.sb >= 0) smem_tally(s_sb, (unsigned)eb.sb);
             smem_tally(s_face, face);
+            if (WEIGHT) {  // the escaped weight, 2^-32 units
+                const unsigned long long ww =
+                    (unsigned long long)llrint(exp(-(double)lw * 9.094947017729282e-13) * 4294967296.0);
+                atomicAdd(&P.tally[P.hist_off_w], ww);
+                atomicAdd(&P.tally[P.hist_off_w + 1 + eb.hist], ww);
+            }
             ++n_esc;
             return true;
         }
@@ -398,7 +419,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         cell = min((face & 1u) ? cell + stride : cell - stride, (unsigned)P.ncell - 1u);
         cls = __ldg(&P.cell_class[cell]);
         s = cls * J + nbin;
-        return false;
+        return faded();
     };
 
     for (;;) {
@@ -421,6 +442,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
                         bin = P.st_bin[pid];
                         t = P.st_t[pid];
                         e = P.st_e[pid];
+                        if (WEIGHT) lw = P.st_lw[pid];
                         have = true;
                     } else if (st == PK_FRESH) {
                         // event draw 0: bit 31-a picks the centre cell on axis a, bit 28 the bin
@@ -433,6 +455,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
                         bin = (unsigned)P.src_bin[(P.src_nbin == 2) ? ((w >> 28) & 1u) : 0u];
                         t = 0;
                         e = 1;
+                        lw = 0;
                         ++n_emit;
                         have = true;
                     }
@@ -464,6 +487,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
             P.st_bin[pid] = min(s - cls * J, J - 1u);
             P.st_t[pid] = t;
             P.st_e[pid] = e;
+            if (WEIGHT) P.st_lw[pid] = lw;
             P.st_status[pid] = PK_INFLIGHT;
             have = false;
             exhausted = true;
@@ -476,6 +500,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
             P.st_bin[pid] = min(s - cls * J, J - 1u);
             P.st_t[pid] = t;
             P.st_e[pid] = e;
+            if (WEIGHT) P.st_lw[pid] = lw;
             P.st_status[pid] = PK_PARKED;
             // one queue atomic per warp: the lanes parking now share a block of slots
             const unsigned grp = __activemask();
@@ -512,7 +537,9 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
 #define RDDMC_FAST(W, Q)                                                                  \
     {                                                                                     \
         const uint2 f_ = SMEM_ROWS ? fast[min(s, nr1)] : __ldg(&fast[min(s, nr1)]);       \
-        if ((W) < f_.y) {                                                                 \
+        const unsigned long long wq_ = WEIGHT ? __ldg(&P.wq[min(s, nr1)]) : 0ull;         \
+        if ((W) < f_.y && (!WEIGHT || lw + wq_ <= kLwMin)) {                              \
+            if (WEIGHT) lw += wq_;                                                        \
             s += ((W) >= f_.x) ? 1u : 0xffffffffu;                                        \
         } else {                                                                          \
             q = (Q);                                                                      \
@@ -561,6 +588,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
             P.st_bin[pid] = min(s - cls * J, J - 1u);
             P.st_t[pid] = t;
             P.st_e[pid] = e;
+            if (WEIGHT) P.st_lw[pid] = lw;
             P.st_status[pid] = PK_INFLIGHT;
             have = false;
         }
@@ -602,26 +630,27 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         if (s_sb[i]) atomicAdd(&P.tally[kHistOff + nhist + i], s_sb[i]);
 }
 
-template <int NDIM, bool SMEM, bool HYBRID, bool PROPOSE>
+template <int NDIM, bool SMEM, bool HYBRID, bool PROPOSE, bool WEIGHT>
 cudaError_t launch_variant(const WalkParams& P, int threads, size_t smem, int ctas, int nsm, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<NDIM, SMEM, HYBRID, PROPOSE>,
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<NDIM, SMEM, HYBRID, PROPOSE, WEIGHT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (!ctas) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, walk_kernel<NDIM, SMEM, HYBRID, PROPOSE>, threads,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, walk_kernel<NDIM, SMEM, HYBRID, PROPOSE, WEIGHT>, threads,
                                                           smem);
         if (e != cudaSuccess) return e;
     }
     if (ctas < 1) ctas = 1;
-    walk_kernel<NDIM, SMEM, HYBRID, PROPOSE><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P);
+    walk_kernel<NDIM, SMEM, HYBRID, PROPOSE, WEIGHT><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P);
     return cudaGetLastError();
 }
 
 template <int NDIM, bool SMEM>
 cudaError_t launch_mode(const WalkParams& P, int threads, size_t smem, int ctas, int nsm, cudaStream_t s) {
-    if (NDIM == 3 && P.prop_b) return launch_variant<NDIM, SMEM, false, true>(P, threads, smem, ctas, nsm, s);
-    return P.hybrid ? launch_variant<NDIM, SMEM, true, false>(P, threads, smem, ctas, nsm, s)
-                    : launch_variant<NDIM, SMEM, false, false>(P, threads, smem, ctas, nsm, s);
+    if (NDIM == 3 && P.prop_b) return launch_variant<NDIM, SMEM, false, true, false>(P, threads, smem, ctas, nsm, s);
+    if (P.weights) return launch_variant<NDIM, SMEM, false, false, true>(P, threads, smem, ctas, nsm, s);
+    return P.hybrid ? launch_variant<NDIM, SMEM, true, false, false>(P, threads, smem, ctas, nsm, s)
+                    : launch_variant<NDIM, SMEM, false, false, false>(P, threads, smem, ctas, nsm, s);
 }
 
 // One scattering per thread at x_in with incoming direction +e_z; sample i
@@ -825,6 +854,9 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     P.abs_thr = (const uint32_t*)(tb + g.off_abs);
     P.dust = g.dusty() ? 1 : 0;
     P.redist = o.redist;
+    P.wq = (const unsigned long long*)(tb + g.off_wq);
+    P.weights = g.weighted() ? 1 : 0;
+    P.hist_off_w = kHistOff + g.J + 2 + kNsb;
     {
         double dzmin = 2.0 * g.R / g.n[0];
         for (int a = 1; a < g.ndim; ++a) dzmin = std::min(dzmin, 2.0 * g.R / g.n[a]);
@@ -837,7 +869,8 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     P.st_bin = (uint32_t*)(sb + off); off += align256(np * 4);
     P.st_t = (unsigned long long*)(sb + off); off += align256(np * 8);
     P.st_e = (unsigned long long*)(sb + off); off += align256(np * 8);
-    P.st_status = (uint8_t*)(sb + off);
+    P.st_status = (uint8_t*)(sb + off); off += align256(np * 1);
+    P.st_lw = (unsigned long long*)(sb + off);
     P.tally = w.d_tally;
     P.n_packets = np;
     P.max_steps = o.max_steps ? o.max_steps : (1ull << 62);
@@ -929,7 +962,8 @@ extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rdd
                              void* stream) {
     using namespace rddmc;
     if (!g || !d_table || !pr || !d_state || !d_tallies || !d_wf || !d_wb || !d_work) return RDDMC_ERR_ARG;
-    if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty()) return RDDMC_ERR_UNSUPPORTED;
+    if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty() || g->weighted())
+        return RDDMC_ERR_UNSUPPORTED;
     if (batch < 64 || batch % 64 || nA != 6 * g->J || nB < 1 || nB > 41 || nC < 0 || nA + nB + nC > n_out ||
         n_out % 16)
         return RDDMC_ERR_ARG;

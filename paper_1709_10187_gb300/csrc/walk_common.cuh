@@ -25,6 +25,10 @@ struct WalkParams {
     int dust;                 // the draw has the absorption outcome (Sec. 2.6)
     const uint32_t* redist;   // hybrid: frequency-grouped MC (Sec. 5.3), J rows of J-1 thresholds, or null
     float inv_dzmin;          // 1 / dz_min: k of a row = tau_row / dz_min
+    const unsigned long long* wq;  // dust weight method: -ln(weight kept per dwell) per row, 2^-40 units
+    unsigned long long* st_lw;     // per packet: accumulated -ln(weight), 2^-40 units
+    int weights;                   // the dust weight method is on (Sec. 2.6)
+    int hist_off_w;                // tally word of the escaped weight (then one per escape bin)
     unsigned long long* cursor;
     uint32_t* st_cell;
     uint32_t* st_bin;

@@ -25,6 +25,7 @@ OK, ERR_ARG, ERR_UNSUPPORTED, ERR_SIZE, ERR_CUDA, ERR_STEP_LIMIT, ERR_TABLE, ERR
 GEOM_SLAB_1D, GEOM_CART_3D = 1, 3
 MODE_DDMC, MODE_HYBRID = 0, 1
 LAYOUT_DEDUP, LAYOUT_DENSE = 0, 1
+DUST_PROBABILISTIC, DUST_WEIGHTS = 0, 1
 NSB = 64  # impact-parameter bins of the surface-brightness histogram
 
 EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc_precompute_leakage",
@@ -36,6 +37,7 @@ EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc
             "rddmc_mlp_param_count", "rddmc_mlp_work_bytes", "rddmc_mlp_to_bf16", "rddmc_mlp_forward",
             "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_mlp_status", "rddmc_propose", "rddmc_time_state_bytes",
             "rddmc_time_step_launch", "rddmc_redistribution_bytes", "rddmc_precompute_redistribution",
+            "rddmc_read_escape_weights",
             "rddmc_status_string", "rddmc_version"]
 
 TIME_TICKS = 1 << 31  # ticks per time step in the path tallies of rddmc_time_step_launch
@@ -50,7 +52,7 @@ class GridDesc(ctypes.Structure):
 
 class LeakParams(ctypes.Structure):
     _fields_ = [("tau_ddmc", ctypes.c_double), ("lam", ctypes.c_double), ("f_mu", ctypes.c_double),
-                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("dust_abs", ctypes.c_double),
+                ("mode", ctypes.c_int32), ("dust_method", ctypes.c_int32), ("dust_abs", ctypes.c_double),
                 ("dust_scat", ctypes.c_double)]
 
 
@@ -71,7 +73,8 @@ class Tallies(ctypes.Structure):
     _fields_ = [("emitted", ctypes.c_uint64), ("escaped", ctypes.c_uint64), ("aborted", ctypes.c_uint64),
                 ("steps", ctypes.c_uint64), ("mc_events", ctypes.c_uint64), ("conversions", ctypes.c_uint64),
                 ("clamps", ctypes.c_uint64), ("event_draws", ctypes.c_uint64), ("proposals", ctypes.c_uint64),
-                ("proposed_steps", ctypes.c_uint64), ("absorbed", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("proposed_steps", ctypes.c_uint64), ("absorbed", ctypes.c_uint64),
+                ("escaped_weight", ctypes.c_double), ("status", ctypes.c_int32),
                 ("nbins", ctypes.c_int32), ("nfaces", ctypes.c_int32), ("nsb", ctypes.c_int32)]
 
 
@@ -152,6 +155,7 @@ def lib():
                                            ctypes.POINTER(ctypes.c_double)]
         L.rddmc_time_state_bytes.argtypes = [u64]
         L.rddmc_redistribution_bytes.argtypes = [vp]
+        L.rddmc_read_escape_weights.argtypes = [vp, vp, vp, vp]
         L.rddmc_precompute_redistribution.argtypes = [vp, vp, i32, vp, sz, vp]
         L.rddmc_time_step_launch.argtypes = [vp, vp, ctypes.POINTER(TimeStep), vp, sz, vp, sz, vp, vp, vp, vp, vp]
         L.rddmc_status_string.argtypes = [i32]
@@ -282,7 +286,11 @@ def read_tallies(grid, d_tallies: int, J: int, nfaces: int, stream: int = 0) -> 
     _check("rddmc_read_tallies", lib().rddmc_read_tallies(ctypes.c_void_p(grid), ctypes.c_void_p(d_tallies),
                                                           ctypes.byref(t), _np_ptr(hist), _np_ptr(faces),
                                                           _np_ptr(sb), ctypes.c_void_p(stream)))
-    d = {k: int(getattr(t, k)) for k, _ in Tallies._fields_}
+    d = {k: getattr(t, k) if k == "escaped_weight" else int(getattr(t, k)) for k, _ in Tallies._fields_}
+    whist = np.zeros(J + 2, dtype=np.float64)
+    _check("rddmc_read_escape_weights", lib().rddmc_read_escape_weights(
+        ctypes.c_void_p(grid), ctypes.c_void_p(d_tallies), _np_ptr(whist), ctypes.c_void_p(stream)))
+    d["weight_hist"] = whist
     d["hist"] = hist
     d["faces"] = faces
     d["sb"] = sb
@@ -313,7 +321,8 @@ class Problem:
     in caller-owned torch device buffers."""
 
     def __init__(self, w, mode=MODE_DDMC, layout=LAYOUT_DEDUP, tau_ddmc=5.0, lam=0.7104, f_mu=0.5,
-                 device="cuda", n_rel=None, edges=None, v_kms=None, dust_abs=0.0, dust_scat=0.0):
+                 device="cuda", n_rel=None, edges=None, v_kms=None, dust_abs=0.0, dust_scat=0.0,
+                 dust_weights=False):
         import torch
         self.torch = torch
         self.w = w
@@ -331,7 +340,8 @@ class Problem:
         self.tally = torch.zeros(int(s.tally_bytes) // 8, dtype=torch.int64, device=self.device)
         self.state = None
         self.state_packets = 0
-        self.params = LeakParams(tau_ddmc, lam, f_mu, mode, 0, dust_abs, dust_scat)
+        self.params = LeakParams(tau_ddmc, lam, f_mu, mode, DUST_WEIGHTS if dust_weights else DUST_PROBABILISTIC,
+                                 dust_abs, dust_scat)
         precompute_leakage(self.grid, self.params, self.table.data_ptr(), self.table.numel(), self.stream())
 
     def stream(self) -> int:

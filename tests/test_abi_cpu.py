@@ -46,8 +46,8 @@ def test_dedup_classes_and_sizes():
     # uniform static slab: left boundary cell, interior cells, right boundary cell
     assert s.n_class == 3 and s.row_bytes == 16 and s.n_outcomes == 4
     assert s.table_bytes >= 3 * 512 * 16
-    assert s.tally_bytes == (22 + 512 + 2 + 64) * 8
-    assert s.state_bytes >= 10_000_000 * 25
+    assert s.tally_bytes == (22 + 512 + 2 + 64 + 512 + 3) * 8
+    assert s.state_bytes >= 10_000_000 * 33
     R.destroy_grid(g)
     g = _grid(W.C2, layout=R.LAYOUT_DENSE)
     assert R.grid_sizes(g, 1).n_class == 256

@@ -118,3 +118,65 @@ def test_dust_is_refused_where_the_method_has_no_absorption():
         R.Batch([p], [100])
     assert ei.value.status == R.ERR_UNSUPPORTED
     p.close()
+
+
+@pytest.mark.parametrize("w,tau_a", [(W.TINY, 0.5), (W.SMALL, 0.3), (W.SMALL, 20.0), (W.SPHERE8_V, 0.5)],
+                         ids=["tiny", "small", "small_strong", "sphere_moving"])
+def test_weight_method_tracks_the_oracle(w, tau_a):
+    """The weight method (Sec. 2.6): the device sums -ln of the per-dwell weight
+    factors exactly in 2^-40 units and forms each escaped weight once; the
+    oracle multiplies FP64 factors.  Integer tallies agree count for count (a
+    packet whose weight lands within rounding of the 1e-10 elimination weight
+    could differ: none does here), the escaped weight to 1e-6."""
+    n = 20_000
+    p = R.Problem(w, dust_abs=tau_a, dust_scat=1.0, dust_weights=True)
+    og = C.Grid(w, dust_abs=tau_a, dust_scat=1.0, dust_weights=True)
+    t = og.table()
+    thr, _ = p.rows()
+    m = w.mask()
+    sel = np.ones(w.ncell * w.J, bool) if m is None else np.repeat(m.astype(bool), w.J)
+    t = dict(t)
+    t["thr"] = np.where(sel[:, None], thr, t["thr"]).astype(np.uint32)
+    g = p.run(n, w.seed)
+    o = C.walk_weights(og, t, w.seed, 0, n)
+    for k in ("emitted", "escaped", "absorbed", "steps", "event_draws"):
+        assert g[k] == o[k], (k, g[k], o[k])
+    assert np.array_equal(g["hist"], o["hist"])
+    assert abs(g["escaped_weight"] - o["escaped_weight"]) <= 1e-6 * o["escaped_weight"]
+    assert np.abs(g["weight_hist"] - o["weight_hist"]).max() <= 1e-6 * o["escaped_weight"]
+    if tau_a > 1.0:
+        assert g["absorbed"] > 0
+    p.close()
+
+
+def test_weight_method_and_probabilistic_method_agree_in_expectation():
+    w = W.SMALL
+    n = 200_000
+    pw = R.Problem(w, dust_abs=0.3, dust_scat=1.0, dust_weights=True)
+    pp = R.Problem(w, dust_abs=0.3, dust_scat=1.0)
+    a = pw.run(n, w.seed)
+    b = pp.run(n, w.seed + 1)
+    f = b["escaped"] / n
+    assert abs(a["escaped_weight"] / n - f) <= 5.0 * np.sqrt(f * (1 - f) / n), (a["escaped_weight"] / n, f)
+    pw.close()
+    pp.close()
+
+
+def test_weight_method_does_not_depend_on_slicing():
+    """The log-weight is saved with the packet state between slices: sliced
+    launches give the same integer tallies and escaped weight bit for bit."""
+    w = W.SMALL
+    n = 20_000
+    p = R.Problem(w, dust_abs=20.0, dust_scat=1.0, dust_weights=True)
+    a = p.run(n, w.seed)
+    p.reset()
+    p.launch(n, w.seed, steps_per_launch=256)
+    for _ in range(100_000):
+        r = p.read()
+        if r["escaped"] + r["absorbed"] + r["aborted"] == n:
+            break
+        p.launch(n, w.seed, steps_per_launch=256, resume=1)
+    for k in ("escaped", "absorbed", "steps", "event_draws"):
+        assert r[k] == a[k], k
+    assert r["escaped_weight"] == a["escaped_weight"] and np.array_equal(r["weight_hist"], a["weight_hist"])
+    p.close()
