@@ -139,3 +139,20 @@ def test_dust_parameters_are_validated_without_a_gpu():
     # the outcome count grows by one only once a dusty table is precomputed
     assert s.n_outcomes == 4
     R.destroy_grid(g)
+
+
+def test_redistribution_sizes_and_validation_without_a_gpu():
+    g = _grid(W.SMALL)
+    J = W.SMALL.J
+    assert R.redistribution_bytes(g) == (J * (J - 1) * 4 + 255) // 256 * 256
+    fake = 1 << 20
+    nb = R.redistribution_bytes(g)
+    L = R.lib()
+    assert L.rddmc_precompute_redistribution(g, fake, 0, fake, nb, None) == R.ERR_ARG      # n_sub < 1
+    assert L.rddmc_precompute_redistribution(g, fake, 9, fake, nb, None) == R.ERR_ARG      # n_sub > 8
+    assert L.rddmc_precompute_redistribution(g, fake, 3, fake, nb - 256, None) == R.ERR_SIZE
+    assert L.rddmc_precompute_redistribution(g, fake, 3, fake, nb, None) == R.ERR_TABLE    # no precompute yet
+    R.destroy_grid(g)
+    g1 = _grid(W.Workload("one_bin", 1, (3, 1, 1), 1, -1.0, 1.0, 10.0, 1.0e4, 1, 1))
+    assert R.redistribution_bytes(g1) == 0
+    R.destroy_grid(g1)
