@@ -64,7 +64,7 @@ def lib():
         L.orc_scatter_samples.argtypes = [d, d, u64, u64, vp]
         L.orc_walk_time.restype = ctypes.c_int
         L.orc_walk_time.argtypes = [vp, vp, vp, vp, vp, vp, d, u64, u64, u64, vp, i32, u64, i32, vp, vp, vp, vp, vp,
-                                    vp, vp]
+                                    vp, vp, vp, vp]
         L.orc_fp_samples.restype = None
         L.orc_fp_samples.argtypes = [vp, i32, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp]
         L.orc_upar_table.restype = None
@@ -256,12 +256,16 @@ def walk_time(grid: Grid, table: dict, seed: int, p0: int, npk: int, t_edges, ma
     tally = np.zeros(lib().orc_tally_len(grid.J), dtype=np.uint64)
     stats = np.zeros(3, dtype=np.uint64)
     leak = np.zeros(nt * grid.ncell * nf * 2, dtype=np.float64) if leaks else None
+    weighted = bool(grid.g.dust_weights)
+    wbins = np.zeros(nt * S, dtype=np.float64) if weighted else None
+    wpath = np.zeros(nt * S, dtype=np.float64) if weighted else None
     thr = np.ascontiguousarray(table["thr"].ravel())
     rate = np.ascontiguousarray(table["rate"].ravel())
     rc = lib().orc_walk_time(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
                              _ptr(table["rebin_thr"]), _ptr(rate), float(grid.w.x0), int(seed), int(p0), int(npk),
                              _ptr(te), int(nt), int(max_steps), int(nthreads), _ptr(bins), _ptr(path), _ptr(esc),
-                             _ptr(tally), _ptr(stats), _ptr(table["k"]) if leaks else None, _ptr(leak))
+                             _ptr(tally), _ptr(stats), _ptr(table["k"]) if leaks else None, _ptr(leak), _ptr(wbins),
+                             _ptr(wpath))
     if rc != 0:
         raise RuntimeError(f"orc_walk_time failed: {rc}")
     out = unpack_tally(tally, grid.J)
@@ -269,6 +273,9 @@ def walk_time(grid: Grid, table: dict, seed: int, p0: int, npk: int, t_edges, ma
                dwells=int(stats[1]), aborted_time=int(stats[2]))
     if leaks:
         out["leak"] = leak.reshape(nt, grid.ncell, nf, 2)
+    if weighted:  # dust by packet weights: weighted bin and path estimates
+        out["wbins"] = wbins.reshape(nt, S)
+        out["wpath"] = wpath.reshape(nt, S)
     return out
 
 

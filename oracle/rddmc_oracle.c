@@ -1009,6 +1009,8 @@ typedef struct orc_time_args {
     double* path;     /* per thread: nt x S */
     uint64_t* esc;    /* per thread: nt */
     double* leak;     /* per thread: nt x ncell x 2 ndim x 2, or NULL */
+    double* wbins;    /* dust weights, per thread: nt x S weights in each state at t_end, or NULL */
+    double* wpath;    /* dust weights, per thread: nt x S weighted path per state, or NULL */
     uint64_t steps, dwells, aborted;
 } orc_time_args;
 
@@ -1066,6 +1068,7 @@ static void* orc_time_thread(void* vp) {
         double tau = T->t_edges[0];
         uint64_t d = 0;  /* dwell draws */
         int done = 0;
+        double wgt = 1.0;  /* dust weights: the packet weight */
         for (int n = 0; n < T->nt && !done; ++n) {
             const double t_end = T->t_edges[n + 1];
             for (;;) {
@@ -1076,17 +1079,32 @@ static void* orc_time_thread(void* vp) {
                 /* eq. l_min_2: the smallest of the exponential leakage lengths is Exp(sum k) */
                 const double dl = -log(orc_unif(orc_word(A->seed, pk, ORC_TIME, d++))) / ksum;
                 T->dwells++;
+                /* dust by weights (Sec. 2.6): over a path l the weight falls by
+                 * exp(-k_a l); the path estimate takes the weight averaged along
+                 * it, w (1 - e^{-k_a l}) / (k_a l) */
+                const double ka = g->dust_weights ? g->dust_abs / g->R * (g->n_rel ? g->n_rel[s / J] : 1.0) : 0.0;
                 if (tau + dl > t_end) {          /* causality: stay in the state until t_end */
-                    T->path[(size_t)n * S + s] += t_end - tau;
+                    const double l = t_end - tau;
+                    T->path[(size_t)n * S + s] += l;
+                    if (T->wpath) {
+                        T->wpath[(size_t)n * S + s] += ka > 0.0 ? wgt * -expm1(-ka * l) / ka : wgt * l;
+                        wgt *= exp(-ka * l);
+                        T->wbins[(size_t)n * S + s] += wgt;
+                    }
                     tau = t_end;
                     T->bins[(size_t)n * S + s]++;
                     break;
                 }
                 T->path[(size_t)n * S + s] += dl;
+                if (T->wpath) {
+                    T->wpath[(size_t)n * S + s] += ka > 0.0 ? wgt * -expm1(-ka * dl) / ka : wgt * dl;
+                    wgt *= exp(-ka * dl);
+                }
                 tau += dl;
                 int r = orc_time_transition(A, pk, &P, A->tally, dl, T->leak ? T->leak + (size_t)n * L : NULL);
                 if (r == 1) { T->esc[n]++; done = 1; break; }
                 if (r == 2) { done = 4; break; }
+                if (T->wpath && wgt < ORC_W_MIN) { A->tally[ORC_T_ABSORBED]++; done = 4; break; }
                 if (r == -1) { A->status = -2; done = 3; break; }
             }
         }
@@ -1116,15 +1134,21 @@ static void* orc_time_thread(void* vp) {
  *       bin it leaves), io = 1 entering it (k of the cell at the bin it
  *       enters); dl is the dwell that ended in the leak.  The acceleration of
  *       cell c is proportional to sum_f (leak[out] - leak[in]) n_f.
+ *   wbins, wpath (required with dust weights, else NULL; nt x S): the bin and
+ *       path estimates weighted by packet weight (Sec. 2.6: the weight falls by
+ *       exp(-k_a l) over a path l; the path estimate takes the weight averaged
+ *       along the path); packets below weight 1e-10 are eliminated.
  * with S = ncell * J.  DDMC tables only.  stats[3] = {transitions, dwell draws,
  * aborted}.  Returns 0, -1 on bad input, -2 if a packet met an MC state.
  */
 int orc_walk_time(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
                   const uint32_t* rebin_thr, const double* rate, double x0, uint64_t seed, uint64_t p0, uint64_t np,
                   const double* t_edges, int nt, uint64_t max_steps, int nthreads, uint64_t* bins, double* path,
-                  uint64_t* esc, uint64_t* tally, uint64_t* stats, const double* k, double* leak) {
+                  uint64_t* esc, uint64_t* tally, uint64_t* stats, const double* k, double* leak, double* wbins,
+                  double* wpath) {
     if (!g || !thr || !flags || !rate || !t_edges || nt < 1 || !bins || !path || !esc || !tally || !stats) return -1;
     if (leak && !k) return -1;
+    if ((!wbins) != (!wpath) || ((wbins != NULL) != (g->dust_weights != 0))) return -1;
     if (p0 + np > ((uint64_t)1 << 62)) return -1;
     for (int n = 0; n < nt; ++n)
         if (!(t_edges[n + 1] > t_edges[n])) return -1;
@@ -1142,6 +1166,8 @@ int orc_walk_time(const orc_grid* g, const uint32_t* thr, const uint32_t* flags,
     uint64_t* te = (uint64_t*)calloc((size_t)nthreads * nt, sizeof(uint64_t));
     const size_t LN = (size_t)nt * orc_ncell(g) * 2 * g->ndim * 2;
     double* tlk = leak ? (double*)calloc((size_t)nthreads * LN, sizeof(double)) : NULL;
+    double* twb = wbins ? (double*)calloc((size_t)nthreads * nt * S, sizeof(double)) : NULL;
+    double* twp = wpath ? (double*)calloc((size_t)nthreads * nt * S, sizeof(double)) : NULL;
     for (int i = 0; i < nthreads; ++i) {
         orc_time_args* T = &args[i];
         orc_walk_args* A = &T->w;
@@ -1152,6 +1178,8 @@ int orc_walk_time(const orc_grid* g, const uint32_t* thr, const uint32_t* flags,
         A->tally = tl + (size_t)i * L;
         T->t_edges = t_edges; T->nt = nt;
         T->leak = tlk ? tlk + (size_t)i * LN : NULL;
+        T->wbins = twb ? twb + (size_t)i * nt * S : NULL;
+        T->wpath = twp ? twp + (size_t)i * nt * S : NULL;
         T->bins = tb + (size_t)i * nt * S;
         T->path = tp + (size_t)i * nt * S;
         T->esc = te + (size_t)i * nt;
@@ -1170,12 +1198,17 @@ int orc_walk_time(const orc_grid* g, const uint32_t* thr, const uint32_t* flags,
         for (int n = 0; n < nt; ++n) esc[n] += te[(size_t)i * nt + n];
         if (tlk)
             for (size_t q = 0; q < LN; ++q) leak[q] += tlk[(size_t)i * LN + q];
+        if (twb)
+            for (size_t q = 0; q < (size_t)nt * S; ++q) {
+                wbins[q] += twb[(size_t)i * nt * S + q];
+                wpath[q] += twp[(size_t)i * nt * S + q];
+            }
         stats[0] += args[i].w.tally[ORC_T_STEPS];
         stats[1] += args[i].dwells;
         stats[2] += args[i].aborted;
         if (args[i].w.status) status = args[i].w.status;
     }
-    free(th); free(args); free(tl); free(tb); free(tp); free(te); free(tlk);
+    free(th); free(args); free(tl); free(tb); free(tp); free(te); free(tlk); free(twb); free(twp);
     return status;
 }
 

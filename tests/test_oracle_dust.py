@@ -161,3 +161,29 @@ def test_weight_method_on_the_grey_slab_has_the_closed_form(tau_a):
     assert abs(means.mean() - f) <= 5.0 * se, (means.mean(), f, se)
     # far tighter than counting the escapes of as many probabilistic packets
     assert se < 0.5 * np.sqrt(f * (1.0 - f) / (B * m)), (se, np.sqrt(f * (1.0 - f) / (B * m)))
+
+
+def test_weighted_time_estimates_follow_the_absorbing_chain():
+    """Dust by packet weights in the time-dependent walk (Sec. 2.6): over a path
+    l the weight falls by exp(-k_a l), the path estimate takes the weight
+    averaged along the path.  In expectation the weighted bin and path
+    estimates are the occupancy and step-integrated occupancy of the chain
+    with absorption as a competing process.  A density gradient makes k_a, and
+    so the weights, differ between packets; weights lie in [0, 1], so a state's
+    weighted count varies at most as its count."""
+    w = W.TINY
+    te = np.array([0.0, 0.05, 0.15, 0.4])
+    n = 60_000
+    n_rel = np.linspace(0.5, 2.0, w.ncell)
+    g = C.Grid(w, dust_abs=10.0, dust_weights=True, n_rel=n_rel)
+    r = C.walk_time(g, g.table(), w.seed, 0, n, te)
+    occ, path, _ = A.chain_time(w, C.Grid(w, dust_abs=10.0, n_rel=n_rel).table(), te)
+    for k in range(len(te) - 1):
+        e = occ[k] * n
+        sel = e >= 20.0
+        assert np.all(np.abs(r["wbins"][k][sel] - e[sel]) <= 5.0 * np.sqrt(e[sel])), k
+        dt = te[k + 1] - te[k]
+        ep = path[k] * n
+        assert np.all(np.abs(r["wpath"][k] - ep) <= 5.0 * np.sqrt(dt * ep) + 1e-9), k
+        # the weights do fall: the weighted estimates lie below the unweighted ones
+        assert r["wbins"][k].sum() < r["bins"][k].sum() and r["wpath"][k].sum() < r["path"][k].sum()
