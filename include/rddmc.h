@@ -109,7 +109,8 @@ typedef struct rddmc_grid_desc {
  *             the expected attenuation exp(-k_a dl) over its dwell, packets
  *             below weight 1e-10 are eliminated (counted absorbed) and escapes
  *             carry their weight (rddmc_tallies.escaped_weight,
- *             rddmc_read_escape_weights).  The persistent walk only.
+ *             rddmc_read_escape_weights).  The time-dependent walk attenuates
+ *             by exp(-k_a l) over each path l and reports weighted estimates.
  */
 typedef struct rddmc_leak_params {
     double tau_ddmc;
@@ -442,6 +443,13 @@ uint64_t rddmc_time_state_bytes(uint64_t n_packets);
  *              Faces in the outcome order -x, +x (-y, +y, -z, +z).  The
  *              acceleration of a cell is proportional to sum over faces of
  *              (out - in) times the face's outward normal.
+ *   d_wbins, d_wpath  device, ncell * J doubles each, accumulated; required
+ *              with dust by weights (Sec. 2.6), else NULL: the bin estimate
+ *              weighted by packet weight at t_end, and the path estimate (in
+ *              ticks) weighted by the weight averaged along each path, the
+ *              weight falling by exp(-k_a l) over a path l; packets below
+ *              weight 1e-10 are eliminated (counted absorbed).  Not together
+ *              with d_leak.
  * Errors: RDDMC_ERR_ARG (null or misaligned pointer, a field out of range),
  * RDDMC_ERR_TABLE (table not precomputed), RDDMC_ERR_UNSUPPORTED (hybrid-mode
  * table, or ncell * J >= 2^32), RDDMC_ERR_SIZE (a buffer too small),
@@ -450,7 +458,8 @@ uint64_t rddmc_time_state_bytes(uint64_t n_packets);
  */
 int rddmc_time_step_launch(const rddmc_grid* grid, const void* d_table, const rddmc_time_step* step, void* d_state,
                            size_t state_bytes, void* d_tallies, size_t tally_bytes, uint64_t* d_bins,
-                           uint64_t* d_path, uint64_t* d_counts, double* d_leak, void* stream);
+                           uint64_t* d_path, uint64_t* d_counts, double* d_leak, double* d_wbins, double* d_wpath,
+                           void* stream);
 
 /* ----------------------------------------------------------------- batches
  * Many independent grids ("instances", each built and precomputed as above,

@@ -213,6 +213,7 @@ int rddmc_build_grid(const rddmc_grid_desc* d, rddmc_grid** out) {
     g->off_rk = off; off += align256((uint64_t)g->n_class * J * 4);
     g->off_abs = off; off += align256((uint64_t)g->n_class * J * 4);
     g->off_wq = off; off += align256((uint64_t)g->n_class * J * 8);
+    g->off_ka = off; off += align256((uint64_t)g->n_class * J * 4);
     g->table_bytes = off;
     *out = g;
     return RDDMC_OK;

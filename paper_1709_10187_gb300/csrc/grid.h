@@ -33,7 +33,7 @@ struct rddmc_grid {
     int src_bin[2] = {0, 0};
     // table layout (byte offsets)
     uint64_t off_class = 0, off_cdesc = 0, off_rebin = 0, off_vel = 0, off_edges = 0, off_phi = 0,
-             off_rows = 0, off_fast = 0, off_tau = 0, off_upar = 0, off_rk = 0, off_abs = 0, off_wq = 0, table_bytes = 0;
+             off_rows = 0, off_fast = 0, off_tau = 0, off_upar = 0, off_rk = 0, off_abs = 0, off_wq = 0, off_ka = 0, table_bytes = 0;
     // leakage parameters of the last precompute
     rddmc_leak_params params{};
     bool precomputed = false;

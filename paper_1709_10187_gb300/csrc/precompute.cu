@@ -38,7 +38,8 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
                             const double* __restrict__ edges, const double* __restrict__ phi,
                             uint32_t* __restrict__ rows, uint2* __restrict__ fast, float* __restrict__ tau_row,
                             float* __restrict__ rk, uint32_t* __restrict__ abs_thr, int dusty,
-                            unsigned long long* __restrict__ wq, int weighted, int64_t nrow) {
+                            unsigned long long* __restrict__ wq, float* __restrict__ ka_row, int weighted,
+                            int64_t nrow) {
     constexpr int K = 2 + 2 * NDIM;
     constexpr int W = NDIM == 1 ? 4 : 8;  // words per row, the last holding the flags
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,6 +105,7 @@ __global__ void rows_kernel(const TableHeader h, const ClassDesc* __restrict__ c
     // weight method: -ln of the weight kept over one dwell, ln(1 + k_a / K_s),
     // in 2^-40 units (the walk sums these exactly)
     wq[r] = weighted ? (unsigned long long)llrint(log1p(D.ka / tot) * 1099511627776.0) : 0ull;
+    ka_row[r] = weighted ? (float)D.ka : 0.0f;  // the time walk attenuates by exp(-k_a l)
     uint32_t fl = 0;
 #pragma unroll
     for (int o = 0; o < K; ++o) fl |= (act[o] & 3u) << (2 * o);
@@ -182,10 +184,13 @@ cudaError_t launch_precompute(const rddmc_grid& g, void* d_table, cudaStream_t s
     const int dusty = g.dusty() ? 1 : 0;
     unsigned long long* wq = (unsigned long long*)(base + g.off_wq);
     const int weighted = g.weighted() ? 1 : 0;
+    float* ka_row = (float*)(base + g.off_ka);
     if (g.ndim == 1)
-        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, abs_thr, dusty, wq, weighted, nrow);
+        rows_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, abs_thr,
+                                                            dusty, wq, ka_row, weighted, nrow);
     else
-        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, abs_thr, dusty, wq, weighted, nrow);
+        rows_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(h, cd, edges, phi, rows, fast, tau_row, rk, abs_thr,
+                                                            dusty, wq, ka_row, weighted, nrow);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the u_par envelope table serves only the continuous MC of the hybrid scheme
     if (g.params.mode == RDDMC_MODE_HYBRID)

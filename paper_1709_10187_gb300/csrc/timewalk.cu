@@ -65,6 +65,13 @@ struct TimeParams {
     float x_scale;                   // ln 2 * ticks per unit length: dwell ticks = -log2(u) * x_scale / K_s
     int start;                       // every packet starts at the source at t_n
     int n_states;
+    // dust by packet weights (Sec. 2.6): k_a per row (1/R units), the packet
+    // weights, and the weighted bin and path estimates (FP64; path in ticks)
+    const float* ka;
+    float* st_w;
+    double* wbins;
+    double* wpath;
+    float tick_len;                  // step length / 2^31
 };
 
 __device__ __forceinline__ uint4 time_block(unsigned long long b, uint32_t pl, uint32_t ph, const WalkParams& P) {
@@ -77,7 +84,7 @@ __device__ __forceinline__ uint4 trans_block(unsigned long long b, uint32_t pl, 
 
 // MINB: resident 256-thread CTAs per SM the register budget targets (2: no
 // spills, 16 warps per SM; 3: 24 warps with a few spilled registers).
-template <int NDIM, bool SMEM_TALLY, int MINB, bool LEAK>
+template <int NDIM, bool SMEM_TALLY, int MINB, bool LEAK, bool WEIGHT>
 __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, const TimeParams T) {
     constexpr int RW = NDIM == 1 ? 1 : 2;  // uint4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -119,6 +126,7 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
     uint32_t pl = 0, ph = 0;
     unsigned long long tbc = ~0ull;     // index of the cached dwell block
     uint4 rtc = make_uint4(0u, 0u, 0u, 0u);
+    float wgt = 1.0f;                   // dust by weights: the packet weight
     unsigned long long tnc = ~0ull;     // index of the cached transition block
     uint4 rnc = make_uint4(0u, 0u, 0u, 0u);
     unsigned long long n_steps = 0, n_edraw = 0, n_dwell = 0;
@@ -208,6 +216,17 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
     // One dwell on dwell word wd and, if the packet is still inside the step,
     // one transition on word wt.  Returns 0 (moved), 1 (stopped at t_{n+1}) or
     // 2 (finished: escaped or unsupported event).
+    // Dust by weights: over `ticks` of path the weight falls by exp(-k_a l);
+    // the weighted path estimate takes the weight averaged along the path.
+    auto attenuate = [&](unsigned ri, unsigned ticks) {
+        const float l = (float)ticks;
+        const float ta = __ldg(&T.ka[ri]) * l * T.tick_len;
+        const float avg = ta > 1e-4f ? -expm1f(-ta) / ta : 1.0f - 0.5f * ta;
+        const unsigned st = min(cell * J + min(s - cls * J, J - 1u), ns1);
+        atomicAdd(&T.wpath[st], (double)(wgt * l * avg));
+        wgt *= expf(-ta);
+    };
+
     auto dwell_then_move = [&](unsigned wd, unsigned wt) -> int {
         const unsigned ri = min(s, nr1);
         ++d;
@@ -218,18 +237,28 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
         const unsigned rem = kTicks - el;
         if (dt > rem) {  // causality: the packet stays in its state until t_{n+1}
             add_path(rem);
+            if (WEIGHT) attenuate(ri, rem);
             el = kTicks;
             return 1;
         }
         add_path(dt);
+        if (WEIGHT) attenuate(ri, dt);
         el += dt;
         ++t;
         const uint2 f = __ldg(&P.fast[ri]);
+        int r;
         if (wt < f.y) {
             s += (wt >= f.x) ? 1u : 0xffffffffu;
-            return 0;
+            r = 0;
+        } else {
+            r = generic(wt, dt) ? 2 : 0;
         }
-        return generic(wt, dt) ? 2 : 0;
+        if (WEIGHT && r == 0 && wgt < 1e-10f) {  // eliminated below the paper's w_min
+            atomicAdd(&s_cnt[C_ABSORBED], 1ull);
+            ++n_absorbed;
+            r = 2;
+        }
+        return r;
     };
 
     auto dwell_word = [&](unsigned long long dd) -> unsigned {
@@ -266,6 +295,7 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
                         t = P.st_t[pid];
                         e = P.st_e[pid];
                         d = T.st_d[pid];
+                        if (WEIGHT) wgt = T.st_w[pid];
                         have = true;
                     } else if (st == PK_FRESH) {
                         // event draw 0: bit 31-a picks the centre cell on axis a, bit 28 the bin
@@ -279,6 +309,7 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
                         t = 0;
                         e = 1;
                         d = 0;
+                        wgt = 1.0f;
                         ++n_emit;
                         ++n_edraw;  // the source draw
                         have = true;
@@ -338,6 +369,10 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
             const unsigned st = min(cell * J + bin, ns1);
             if (SMEM_TALLY) atomicAdd(&s_bins[st], 1u);
             else atomicAdd(&T.bins[st], 1ull);
+            if (WEIGHT) {
+                atomicAdd(&T.wbins[st], (double)wgt);
+                T.st_w[pid] = wgt;
+            }
             ++n_alive;
             P.st_cell[pid] = cell;
             P.st_bin[pid] = bin;
@@ -397,18 +432,18 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
         }
 }
 
-template <int NDIM, bool SMEM_TALLY, int MINB, bool LEAK>
+template <int NDIM, bool SMEM_TALLY, int MINB, bool LEAK, bool WEIGHT>
 cudaError_t launch_time_minb(const WalkParams& P, const TimeParams& T, int threads, size_t smem, int ctas, int nsm,
                              cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(time_kernel<NDIM, SMEM_TALLY, MINB, LEAK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(time_kernel<NDIM, SMEM_TALLY, MINB, LEAK, WEIGHT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     if (!ctas) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, time_kernel<NDIM, SMEM_TALLY, MINB, LEAK>, threads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, time_kernel<NDIM, SMEM_TALLY, MINB, LEAK, WEIGHT>, threads, smem);
         if (e != cudaSuccess) return e;
     }
     if (ctas < 1) ctas = 1;
-    time_kernel<NDIM, SMEM_TALLY, MINB, LEAK><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P, T);
+    time_kernel<NDIM, SMEM_TALLY, MINB, LEAK, WEIGHT><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P, T);
     return cudaGetLastError();
 }
 
@@ -419,16 +454,20 @@ cudaError_t launch_time(const WalkParams& P, const TimeParams& T, int threads, s
     // ctas_per_sm 1 or 2: the spill-free 16-warp one
     // the leak tally of eq. a_estimator is its own instantiation, so the default
     // kernel carries none of its registers
+    if (T.wbins)  // dust by weights: its own instantiation (no leak tally alongside)
+        return launch_time_minb<NDIM, SMEM_TALLY, 3, false, true>(P, T, threads, smem, ctas, nsm, s);
     if (T.leak)
-        return (ctas == 0 || ctas >= 3) ? launch_time_minb<NDIM, SMEM_TALLY, 3, true>(P, T, threads, smem, ctas, nsm, s)
-                                        : launch_time_minb<NDIM, SMEM_TALLY, 2, true>(P, T, threads, smem, ctas, nsm, s);
-    return (ctas == 0 || ctas >= 3) ? launch_time_minb<NDIM, SMEM_TALLY, 3, false>(P, T, threads, smem, ctas, nsm, s)
-                                    : launch_time_minb<NDIM, SMEM_TALLY, 2, false>(P, T, threads, smem, ctas, nsm, s);
+        return (ctas == 0 || ctas >= 3)
+                   ? launch_time_minb<NDIM, SMEM_TALLY, 3, true, false>(P, T, threads, smem, ctas, nsm, s)
+                   : launch_time_minb<NDIM, SMEM_TALLY, 2, true, false>(P, T, threads, smem, ctas, nsm, s);
+    return (ctas == 0 || ctas >= 3) ? launch_time_minb<NDIM, SMEM_TALLY, 3, false, false>(P, T, threads, smem, ctas, nsm, s)
+                                    : launch_time_minb<NDIM, SMEM_TALLY, 2, false, false>(P, T, threads, smem, ctas, nsm, s);
 }
 
 }  // namespace
 
-uint64_t time_state_bytes_for(uint64_t np) { return state_bytes_for(np) + align256(np * 8); }
+// walk state | dwell counters u64[np] | packet weights f32[np] (dust by weights)
+uint64_t time_state_bytes_for(uint64_t np) { return state_bytes_for(np) + align256(np * 8) + align256(np * 4); }
 
 }  // namespace rddmc
 
@@ -440,7 +479,7 @@ extern "C" uint64_t rddmc_time_state_bytes(uint64_t n_packets) {
 extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, const rddmc_time_step* ts,
                                       void* d_state, size_t state_bytes, void* d_tallies, size_t tally_bytes,
                                       uint64_t* d_bins, uint64_t* d_path, uint64_t* d_counts, double* d_leak,
-                                      void* stream) {
+                                      double* d_wbins, double* d_wpath, void* stream) {
     using namespace rddmc;
     if (!g || !d_table || !ts || !d_state || !d_tallies || !d_bins || !d_path || !d_counts) return RDDMC_ERR_ARG;
     if (((uintptr_t)d_state & 255u) || ((uintptr_t)d_tallies & 7u) || ((uintptr_t)d_bins & 7u) ||
@@ -448,7 +487,12 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
         return RDDMC_ERR_ARG;
     if (!g->precomputed) return RDDMC_ERR_TABLE;
     // dust by packet weights is the persistent walk's method only
-    if (g->params.mode != RDDMC_MODE_DDMC || g->weighted()) return RDDMC_ERR_UNSUPPORTED;
+    if (g->params.mode != RDDMC_MODE_DDMC) return RDDMC_ERR_UNSUPPORTED;
+    // weighted estimates exactly with dust by weights, and not with the leak tally
+    if ((!d_wbins) != (!d_wpath) || ((d_wbins != nullptr) != g->weighted()) || ((uintptr_t)d_wbins & 7u) ||
+        ((uintptr_t)d_wpath & 7u))
+        return RDDMC_ERR_ARG;
+    if (d_wbins && d_leak) return RDDMC_ERR_UNSUPPORTED;
     if (ts->n_packets < 1 || ts->n_packets >= (1ull << 62)) return RDDMC_ERR_ARG;
     if (!(std::isfinite(ts->t_begin) && std::isfinite(ts->t_end) && ts->t_end > ts->t_begin)) return RDDMC_ERR_ARG;
     if (ts->chunk < 0 || ts->chunk % 4 || ts->chunk > (1 << 20)) return RDDMC_ERR_ARG;
@@ -481,6 +525,11 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
     T.x_scale = (float)(0.69314718055994530942 * (double)kTicks / (ts->t_end - ts->t_begin));
     T.start = ts->start;
     T.leak = d_leak;
+    T.ka = (const float*)((const char*)d_table + g->off_ka);
+    T.st_w = (float*)((char*)T.st_d + align256(ts->n_packets * 8));
+    T.wbins = d_wbins;
+    T.wpath = d_wpath;
+    T.tick_len = (float)((ts->t_end - ts->t_begin) / (double)kTicks);
     double dzmin = 2.0 * g->R / g->n[0];
     for (int a = 1; a < g->ndim; ++a) dzmin = std::min(dzmin, 2.0 * g->R / g->n[a]);
     T.inv_dz = (float)(1.0 / dzmin);

@@ -157,7 +157,8 @@ def lib():
         L.rddmc_redistribution_bytes.argtypes = [vp]
         L.rddmc_read_escape_weights.argtypes = [vp, vp, vp, vp]
         L.rddmc_precompute_redistribution.argtypes = [vp, vp, i32, vp, sz, vp]
-        L.rddmc_time_step_launch.argtypes = [vp, vp, ctypes.POINTER(TimeStep), vp, sz, vp, sz, vp, vp, vp, vp, vp]
+        L.rddmc_time_step_launch.argtypes = [vp, vp, ctypes.POINTER(TimeStep), vp, sz, vp, sz, vp, vp, vp, vp, vp, vp,
+                                             vp]
         L.rddmc_status_string.argtypes = [i32]
         L.rddmc_status_string.restype = ctypes.c_char_p
         L.rddmc_version.argtypes = []
@@ -262,13 +263,14 @@ def time_state_bytes(n_packets: int) -> int:
 
 
 def time_step_launch(grid, d_table: int, step: TimeStep, d_state: int, state_bytes: int, d_tallies: int,
-                     tally_bytes: int, d_bins: int, d_path: int, d_counts: int, stream: int = 0, d_leak: int = 0):
+                     tally_bytes: int, d_bins: int, d_path: int, d_counts: int, stream: int = 0, d_leak: int = 0,
+                     d_wbins: int = 0, d_wpath: int = 0):
     """rddmc_time_step_launch (enqueues one time step; no synchronisation)."""
     _check("rddmc_time_step_launch", lib().rddmc_time_step_launch(
         ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(step), ctypes.c_void_p(d_state),
         int(state_bytes), ctypes.c_void_p(d_tallies), int(tally_bytes), ctypes.c_void_p(d_bins),
         ctypes.c_void_p(d_path), ctypes.c_void_p(d_counts), ctypes.c_void_p(d_leak or None),
-        ctypes.c_void_p(stream)))
+        ctypes.c_void_p(d_wbins or None), ctypes.c_void_p(d_wpath or None), ctypes.c_void_p(stream)))
 
 
 def scatter_samples(grid, d_table: int, x_in: float, seed: int, n: int, d_out: int, stream: int = 0):
@@ -413,18 +415,25 @@ class Problem:
         nf = 2 * self.w.ndim
         leak = torch.zeros((nt, int(self.w.ncell) * nf * 2), dtype=torch.float64, device=self.device) if leaks \
             else None
+        weighted = self.params.dust_abs > 0.0 and self.params.dust_method == DUST_WEIGHTS
+        wb = torch.zeros((nt, S), dtype=torch.float64, device=self.device) if weighted else None
+        wp = torch.zeros((nt, S), dtype=torch.float64, device=self.device) if weighted else None
         self.reset()
         for n in range(nt):
             st = TimeStep(seed, n_packets, max_steps, float(te[n]), float(te[n + 1]), 1 if n == 0 else 0, chunk,
                           threads_per_cta, ctas_per_sm)
             time_step_launch(self.grid, self.table.data_ptr(), st, state.data_ptr(), state.numel(),
                              self.tally.data_ptr(), self.tally.numel() * 8, bins[n].data_ptr(), path[n].data_ptr(),
-                             counts[n].data_ptr(), self.stream(), leak[n].data_ptr() if leaks else 0)
+                             counts[n].data_ptr(), self.stream(), leak[n].data_ptr() if leaks else 0,
+                             wb[n].data_ptr() if weighted else 0, wp[n].data_ptr() if weighted else 0)
         c = counts.cpu().numpy().astype(np.uint64)
         ticks = path.cpu().numpy().astype(np.float64)
         out = dict(bins=bins.cpu().numpy().astype(np.uint64), path=ticks * (np.diff(te) / TIME_TICKS)[:, None],
                    path_ticks=path.cpu().numpy().astype(np.uint64), esc=c[:, 0], dwells=c[:, 1],
                    transitions=c[:, 2], alive=c[:, 3], absorbed=c[:, 4], tallies=self.read())
+        if weighted:  # dust by weights: weighted bin and path (length) estimates
+            out["wbins"] = wb.cpu().numpy()
+            out["wpath"] = wp.cpu().numpy() * (np.diff(te) / TIME_TICKS)[:, None]
         if leaks:
             lk = leak.cpu().numpy() * (np.diff(te) / TIME_TICKS)[:, None]
             out["leak"] = lk.reshape(nt, int(self.w.ncell), nf, 2)

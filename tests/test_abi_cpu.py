@@ -112,14 +112,14 @@ def test_time_step_validation_without_a_gpu():
         for k, v in kw.items():
             setattr(st, k, v)
         return R.lib().rddmc_time_step_launch(g, fake, st, fake, 1 << 30, fake, 1 << 20, fake, fake, fake, None,
-                                              None)
+                                              None, None, None)
 
     assert call() == R.ERR_TABLE          # no precompute on this grid
     st = R.TimeStep(1, 1000, 0, 0.0, 1.0, 1, 0, 0, 0)
     assert R.lib().rddmc_time_step_launch(g, fake, st, None, 1 << 30, fake, 1 << 20, fake, fake, fake, None,
-                                          None) == R.ERR_ARG
+                                          None, None, None) == R.ERR_ARG
     assert R.lib().rddmc_time_step_launch(g, fake, st, fake, 1 << 30, fake, 1 << 20, fake, fake, fake, fake + 4,
-                                          None) == R.ERR_ARG   # misaligned leak buffer
+                                          None, None, None) == R.ERR_ARG   # misaligned leak buffer
     R.destroy_grid(g)
 
 

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 GREY21 = W.Workload("grey_slab_21x1", 1, (21, 1, 1), 1, -5.0, 5.0, 200.0, 1.0e4, 1_000_000, 0x5EED0D01)
 
-CASES = [  # workload, dust_abs, dust_scat, density gradient
+CASES = [  # workload, dust_abs, dust_scat, density gradient (probabilistic method)
     (W.TINY, 0.5, 0.0, False),
     (W.SMALL, 0.3, 2.0, True),
     (W.SPHERE8_V, 0.2, 1.0, False),
@@ -179,4 +179,29 @@ def test_weight_method_does_not_depend_on_slicing():
     for k in ("escaped", "absorbed", "steps", "event_draws"):
         assert r[k] == a[k], k
     assert r["escaped_weight"] == a["escaped_weight"] and np.array_equal(r["weight_hist"], a["weight_hist"])
+    p.close()
+
+
+def test_weighted_time_estimates_track_the_oracle():
+    """Dust by weights in the time-dependent walk: the device attenuates each
+    path l by exp(-k_a l) in FP32 and sums weighted estimates in FP64; the
+    oracle in FP64.  Same state sequences, so the weighted bin and path
+    estimates agree to the FP32 rounding and the clock's step-end flips."""
+    w = W.TINY
+    te = [0.0, 0.05, 0.15, 0.4]
+    n = 20_000
+    n_rel = np.linspace(0.5, 2.0, w.ncell)
+    p = R.Problem(w, n_rel=n_rel, dust_abs=10.0, dust_weights=True)
+    g = p.time_run(n, w.seed, te)
+    og = C.Grid(w, n_rel=n_rel, dust_abs=10.0, dust_weights=True)
+    o = C.walk_time(og, og.table(), w.seed, 0, n, te)
+    for k in range(len(te) - 1):
+        rb = float(np.abs(g["wbins"][k] - o["wbins"][k]).sum() / o["wbins"][k].sum())
+        rp = float(np.abs(g["wpath"][k] - o["wpath"][k]).sum() / o["wpath"][k].sum())
+        assert rb <= 2e-3 and rp <= 2e-3, (k, rb, rp)
+    assert abs(int(g["tallies"]["absorbed"]) - int(o["absorbed"])) <= 8
+    # the leak tally does not combine with weights
+    with pytest.raises(R.RDDMCError) as ei:
+        p.time_run(100, w.seed, te, leaks=True)
+    assert ei.value.status == R.ERR_UNSUPPORTED
     p.close()
