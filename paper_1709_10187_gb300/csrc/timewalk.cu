@@ -38,7 +38,11 @@
 // tallies of the walk use the tally buffer's shared-memory staging, as in the
 // persistent walk.  With a leak buffer, the leaks of eq. a_estimator are summed
 // per cell face in FP64 (shared memory when small), in their own kernel
-// instantiation.
+// instantiation.  With dust by packet weights (Sec. 2.6), another
+// instantiation attenuates each path l by exp(-k_a l), keeps the weight with
+// the packet between steps, eliminates packets below 1e-10 and sums weighted
+// bin and path estimates in FP64 (the path weighted by the weight averaged
+// along it).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
