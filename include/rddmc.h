@@ -274,7 +274,9 @@ int rddmc_reset_tallies(const rddmc_grid* grid, void* d_tallies, size_t tally_by
 /*
  * rddmc_launch_packets -- walk packets (Sec. 2.3) with one persistent kernel.
  * Each thread holds one packet: it draws one word of the packet's transition
- * stream per transition, gathers the 16/32-byte row of its state and takes the
+ * stream per transition, gathers the 8-byte head of its state's row (its two
+ * frequency thresholds) and, unless the word falls in a plain frequency move,
+ * the full 16/32-byte row, and takes the
  * outcome whose threshold interval holds the word (the categorical form of the
  * competing exponentials of eq. l_min_1/2: the argmin of independent
  * exponentials with rates k_X is X with probability k_X / sum k).  Packets
@@ -674,9 +676,14 @@ int rddmc_scatter_samples(const rddmc_grid* grid, const void* d_table, double x_
  *   takes any packet count; time-sliced or resumed runs must fit their
  *   per-packet state in the array (about 1 million packets) and otherwise
  *   get RDDMC_ERR_SIZE.
- *   The first call on a device looks up the array's device address (once per
- *   device, with that device current); make that first call before any stream
- *   capture.  All calls share the array and it keeps the previous call's
+ *   Argument checks are rddmc_launch_packets' own (one shared routine); a
+ *   learned proposal (opts->proposal) gets RDDMC_ERR_UNSUPPORTED, because its
+ *   parked packets need a caller-owned state buffer.
+ *   Every call looks up the array's device address on the current device
+ *   (a host-side query, so the address stays right after a cudaDeviceReset);
+ *   the first call on a device also loads the library's device code there,
+ *   so make that first call before any stream capture.  All calls share the
+ *   array and it keeps the previous call's
  *   contents: the cursor is reset by every launch, and resume = 1 continues the
  *   packets the previous call saved there.  Calls whose work overlaps on the
  *   GPU race on the array and must be serialised by the caller.

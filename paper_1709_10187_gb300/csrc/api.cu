@@ -334,9 +334,23 @@ int rddmc_reset_tallies(const rddmc_grid* g, void* d_tallies, size_t tally_bytes
 
 int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_run_opts* o, void* d_state,
                          size_t state_bytes, void* d_tallies, size_t tally_bytes, void* stream) {
-    if (!g || !d_table || !o || !d_state || !d_tallies) return RDDMC_ERR_ARG;
+    const int rc = check_walk_launch(g, d_table, o, d_state, false, d_tallies, tally_bytes);
+    if (rc != RDDMC_OK) return rc;
+    if (state_bytes < state_bytes_for(o->n_packets)) return RDDMC_ERR_SIZE;
+    WalkLaunch w{d_table, d_state, (unsigned long long*)d_tallies, *o};
+    return cuda_status(launch_walk(*g, w, (cudaStream_t)stream));
+}
+
+}  // extern "C"
+
+namespace rddmc {
+
+int check_walk_launch(const rddmc_grid* g, const void* d_table, const rddmc_run_opts* o, const void* d_state,
+                      bool library_state, const void* d_tallies, size_t tally_bytes) {
+    if (!g || !d_table || !o || (!library_state && !d_state) || !d_tallies) return RDDMC_ERR_ARG;
     if (!g->precomputed) return RDDMC_ERR_TABLE;
-    if (((uintptr_t)d_table & 255u) || ((uintptr_t)d_state & 255u) || ((uintptr_t)d_tallies & 7u))
+    if (((uintptr_t)d_table & 255u) || (!library_state && ((uintptr_t)d_state & 255u)) ||
+        ((uintptr_t)d_tallies & 7u))
         return RDDMC_ERR_ARG;
     if (o->n_packets == 0 || o->n_packets >= (1ull << 63)) return RDDMC_ERR_ARG;
     if (o->steps_per_launch % 4 != 0) return RDDMC_ERR_ARG;
@@ -359,11 +373,13 @@ int rddmc_launch_packets(const rddmc_grid* g, const void* d_table, const rddmc_r
         if (!pr->d_brick_lk || !pr->d_lp || !pr->d_xc || !pr->d_queue_count || !pr->d_queue_pid)
             return RDDMC_ERR_ARG;
     }
-    if (state_bytes < state_bytes_for(o->n_packets)) return RDDMC_ERR_SIZE;
     if (tally_bytes < tally_bytes_for(g->J)) return RDDMC_ERR_SIZE;
-    WalkLaunch w{d_table, d_state, (unsigned long long*)d_tallies, *o};
-    return cuda_status(launch_walk(*g, w, (cudaStream_t)stream));
+    return RDDMC_OK;
 }
+
+}  // namespace rddmc
+
+extern "C" {
 
 int rddmc_read_tallies(const rddmc_grid* g, const void* d_tallies, rddmc_tallies* out, uint64_t* hist,
                        uint64_t* faces, uint64_t* sb, void* stream) {

@@ -65,6 +65,13 @@ cudaError_t launch_walk(const rddmc_grid& g, const WalkLaunch& w, cudaStream_t s
 cudaError_t launch_scatter_samples(const rddmc_grid& g, const void* d_table, double x_in, uint64_t seed, uint64_t n,
                                    float* d_out, cudaStream_t s);
 
+// Argument checks of a walk launch, shared by rddmc_launch_packets and
+// rddmc_launch_packets_noalloc: everything but the size of the packet-state
+// buffer.  library_state: the state is the library's own array, so d_state is
+// not checked.  Returns RDDMC_OK or the status the entry point returns.
+int check_walk_launch(const rddmc_grid* g, const void* d_table, const rddmc_run_opts* o, const void* d_state,
+                      bool library_state, const void* d_tallies, size_t tally_bytes);
+
 uint64_t state_bytes_for(uint64_t n_packets);
 uint64_t tally_bytes_for(int J);
 int tally_words(int J);

@@ -156,3 +156,32 @@ def test_redistribution_sizes_and_validation_without_a_gpu():
     g1 = _grid(W.Workload("one_bin", 1, (3, 1, 1), 1, -1.0, 1.0, 10.0, 1.0e4, 1, 1))
     assert R.redistribution_bytes(g1) == 0
     R.destroy_grid(g1)
+
+
+def test_noalloc_launch_checks_its_arguments_like_launch_packets():
+    """rddmc_launch_packets_noalloc runs the checks of rddmc_launch_packets
+    (one shared routine), so both return the same status for the same bad
+    arguments; here on a grid without a table, where no pointer is touched."""
+    import ctypes
+    g = _grid(W.TINY)
+    fake = 1 << 20  # 256-byte aligned, never dereferenced
+    L = R.lib()
+    tb = int(R.grid_sizes(g, 1).tally_bytes)
+
+    def both(table, opts, tally):
+        a = L.rddmc_launch_packets(g, table, ctypes.byref(opts), fake, 1 << 30, tally, tb, None)
+        b = L.rddmc_launch_packets_noalloc(g, table, ctypes.byref(opts), tally, tb, None)
+        return a, b
+
+    o = R.RunOpts(1, 1000, 0, 0, 0, 0, 0, 0, 0, 0)
+    assert both(None, o, fake) == (R.ERR_ARG, R.ERR_ARG)      # no table
+    assert both(fake, o, None) == (R.ERR_ARG, R.ERR_ARG)      # no tallies
+    assert both(fake, o, fake) == (R.ERR_TABLE, R.ERR_TABLE)  # table not precomputed
+    bad = R.RunOpts(1, 0, 0, 0, 0, 0, 0, 0, 0, 0)             # no packets: still the table first
+    assert both(fake, bad, fake) == (R.ERR_TABLE, R.ERR_TABLE)
+    assert L.rddmc_launch_packets_noalloc(None, fake, ctypes.byref(o), fake, tb, None) == R.ERR_ARG
+    # a learned proposal needs a caller-owned state buffer
+    pr = R.Proposal()
+    op = R.RunOpts(1, 1000, 0, 64, 0, 0, 0, 0, 0, 0, ctypes.addressof(pr), None)
+    assert L.rddmc_launch_packets_noalloc(g, fake, ctypes.byref(op), fake, tb, None) == R.ERR_UNSUPPORTED
+    R.destroy_grid(g)
