@@ -31,14 +31,13 @@ from paper_1709_10187_gb300 import workloads as W  # noqa: E402
 
 METRIC = "packet transitions/s (rDDMC walk, tau0=1e7 slab)"
 UNIT = "transitions/s"
-# Algorithmic integer work per transition: Philox4x32-10 is 10 rounds of two
-# 32x32->64 multiplies (hi and lo: 4 ops), 4 xors and 2 key additions = 100 ops
-# per call, one call per 4 transitions (25); the categorical choice is 3
-# compares, 2 adds, a shift and a mask for the action, its test and the move (9).
-OPS_PER_TRANSITION = 34
-ROW_BYTES = 16
+# Gather bytes per transition of the slab walk: the 8-byte fast head of the
+# state's row (a frequency move, ~all transitions at this resolution); the
+# generic step's 16-byte row is read on the rare other outcomes.
+GATHER_BYTES = 8
 PEAK_SM_MHZ = 2070.0  # maximum SM clock of a GB300
 N_SM = 152
+SMSP_PER_SM = 4       # warp schedulers per SM, one instruction issued per cycle each
 
 
 def _peaks():
@@ -49,14 +48,15 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _profile_traffic():
-    """DRAM bytes per transition of the walk kernel from the committed ncu summary, if any."""
+def _profile_walk():
+    """Counters of one ncu capture of the bench's walk launch (committed under
+    profiles/): DRAM bytes and issued instructions per launch, with the kernel
+    source hash and launch configuration they were taken on."""
     p = os.path.join(ROOT, "profiles", "walk_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f)
-    return d
+        return json.load(f)
 
 
 class ClockSampler:
@@ -243,7 +243,8 @@ def run_native(args, rank, world, local_rank):
         # (rddmc_precompute_leakage), the slice runs, and the tallies come back
         # to the host (rddmc_read_tallies, synchronising).
         e2e_steps = max(1, min(args.steps, 5))
-        h2d = int(R.grid_sizes(prob.grid, 1).table_bytes - prob.J * ROW_BYTES * R.grid_sizes(prob.grid, 1).n_class)
+        sz = R.grid_sizes(prob.grid, 1)
+        h2d = int(sz.table_bytes - prob.J * sz.row_bytes * sz.n_class)
         t0 = time.perf_counter()
         e2e_trans = 0
         for i in range(e2e_steps):
@@ -264,14 +265,34 @@ def run_native(args, rank, world, local_rank):
     peaks, peak_kind = _peaks()
     mean_launch_s = float(np.mean(launch_ms)) / 1e3
     trans_per_launch = trans / args.steps
-    achieved_tops = OPS_PER_TRANSITION * trans_per_launch / mean_launch_s / 1e12
-    alu_peak = N_SM * 128 * PEAK_SM_MHZ * 1e6 / 1e12
-    prof = _profile_traffic()
-    traffic = None
-    if (prof and prof.get("kernel_hash") == _kernel_hash() and prof.get("packets") == npk
-            and prof.get("slice_transitions") == slice_):
-        traffic = prof["dram_bytes_per_launch"]  # one ncu capture of this launch configuration
-    gather_gbs = ROW_BYTES * trans_per_launch / mean_launch_s / 1e9
+    # issue-slot roofline: issued instructions per transition from the committed
+    # ncu capture of this launch (smsp__inst_executed.sum over the launch's
+    # transitions), valid while the kernel source and configuration match it
+    prof = _profile_walk()
+    current = bool(prof and prof.get("kernel_hash") == _kernel_hash() and prof.get("packets") == npk
+                   and prof.get("slice_transitions") == slice_)
+    traffic = prof["dram_bytes_per_launch"] if current else None
+    inst = prof.get("warp_inst_per_transition") if current else None
+    issue_peak = N_SM * SMSP_PER_SM * PEAK_SM_MHZ * 1e6 * 32 / 1e12  # lane-instructions, T/s
+    achieved = inst * 32 * trans_per_launch / mean_launch_s / 1e12 if inst else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": issue_peak, "unit": "T lane-instr/s",
+            "frac": achieved / issue_peak if achieved else None, "traffic": traffic,
+            "note": (f"issued instructions: {inst * 32:.2f} lane-instructions per transition (ncu "
+                     f"smsp__inst_executed, profiles/walk_kernel_traffic.json); peak = {N_SM} SMs x "
+                     f"{SMSP_PER_SM} schedulers x 1 warp-instruction/cycle x {PEAK_SM_MHZ:.0f} MHz")
+            if inst else "no ncu capture of the current walk kernel: issue fraction not stated"}
+    if world == 1 and not args.no_gather:
+        with torch.cuda.stream(stream):
+            gp = _gather_peaks(R, torch)
+        l1 = gp["l1_8B_32KiB"]
+        gather_gbs = GATHER_BYTES * trans_per_launch / mean_launch_s / 1e9
+        roof["gather"] = {"achieved": gather_gbs, "peak": l1["GB_per_s"], "unit": "GB/s",
+                          "frac": gather_gbs / l1["GB_per_s"],
+                          "note": f"{GATHER_BYTES}-byte fast heads per transition against the measured random "
+                                  "dependent-gather rate of 8-byte rows from a 32 KiB table through L1 (the "
+                                  "C2 table's footprint; rddmc_gather_probe, best of two occupancies)",
+                          "probe": gp}
+        roof["gather_frac"] = roof["gather"]["frac"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -281,17 +302,22 @@ def run_native(args, rank, world, local_rank):
                    "l2": "inputs larger than L2: 1e7-packet state (250 MB) streamed every step; the 24 KiB "
                          "leakage table stays L1/L2-resident by design",
                    "schedule": sched},
-        "escaped_packets_per_s": esc_tot / tsec_max,
-        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": alu_peak, "unit": "TOP/s",
-                     "frac": achieved_tops / alu_peak, "traffic": traffic,
-                     "note": f"{OPS_PER_TRANSITION} integer ops/transition; peak = {N_SM} SMs x 128 lanes x "
-                             f"{PEAK_SM_MHZ:.0f} MHz; gather {gather_gbs:.0f} GB/s of 16-byte rows"},
+        "escaped_packets_per_s": None,
+        "escaped_in_timed_region_per_s": esc_tot / tsec_max,
+        "roofline": roof,
         "clocks": clk,
         "gpu_launches": args.steps,
         "e2e": {"value": e2e_tot / e2e_dt_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "peaks_source": peak_kind,
     }
+    if world == 1 and not args.no_complete:
+        # escaped packets/s at tau0 = 1e7: a 1e5-packet subset of the workload
+        # walked to escape (each packet ~3e8 transitions, the slowest ~3e9)
+        with torch.cuda.stream(stream):
+            comp = _complete_sliced(R, torch, w, 100_000)
+        line["escaped_packets_per_s"] = comp["escaped_per_s"]
+        line["completed_subset"] = comp
     if world == 1 and not args.no_extras:
         with torch.cuda.stream(stream):
             line["extras"] = _extras(R, torch)
@@ -305,6 +331,68 @@ def run_native(args, rank, world, local_rank):
 # Measured after the timed region, on one GPU: the other workloads of the
 # method and the learned proposal against the plain walk.  Each is timed with
 # CUDA events or a device synchronisation on both sides.
+
+def _gather_peaks(R, torch, threads=256):
+    """Random dependent-gather rates (rddmc_gather_probe) at the table
+    footprints the walks use: 32 KiB through L1 (the C2 slab table) and in
+    shared memory, 2 MiB (served by L2), 1 GiB (served by HBM); 8- and 16-byte
+    rows.  Each rate is the better of 4 CTAs/SM (the walk's occupancy) and as
+    many as fit, timed with CUDA events on the current stream after one
+    untimed launch."""
+    cases = [("l1_8B_32KiB", 32 << 10, 8, False, 16384), ("l1_16B_32KiB", 32 << 10, 16, False, 16384),
+             ("smem_8B_32KiB", 32 << 10, 8, True, 16384), ("l2_8B_2MiB", 2 << 20, 8, False, 4096),
+             ("l2_16B_2MiB", 2 << 20, 16, False, 4096), ("hbm_8B_1GiB", 1 << 30, 8, False, 1024),
+             ("hbm_16B_1GiB", 1 << 30, 16, False, 1024)]
+    st = torch.cuda.current_stream().cuda_stream
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = {}
+    buf = None
+    for name, nbytes, rb, smem, chain in cases:
+        if buf is None or buf.numel() < nbytes:
+            buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        best = None
+        for i, ctas in enumerate((4, 0)):
+            R.gather_probe(buf.data_ptr(), nbytes, rb, smem, chain, ctas, threads, 7, i == 0, sink.data_ptr(), st)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            n = R.gather_probe(buf.data_ptr(), nbytes, rb, smem, chain, ctas, threads, 8, False, sink.data_ptr(), st)
+            a1.record()
+            torch.cuda.synchronize()
+            rate = n / (a0.elapsed_time(a1) / 1e3)
+            if best is None or rate > best["gathers_per_s"]:
+                best = {"gathers_per_s": rate, "GB_per_s": rate * rb / 1e9, "ctas_per_sm": ctas or "max"}
+        out[name] = best
+    del buf
+    return out
+
+
+def _complete_sliced(R, torch, w, npk, slice_=1 << 24):
+    """npk packets of the workload walked to escape in step slices of slice_
+    transitions (every launch short), timed with CUDA events from the first
+    launch to the last packet's escape: escaped packets/s and transitions/s
+    of the completed run, its histogram, and the transitions per packet."""
+    prob = R.Problem(w)
+    prob.ensure_state(npk)
+    prob.run(min(npk, 2000), w.seed + 1, steps_per_launch=slice_)  # warm-up
+    prob.reset()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a0.record()
+    n = 0
+    while True:
+        prob.launch(npk, w.seed, steps_per_launch=slice_, resume=1 if n else 0)
+        n += 1
+        t = prob.read()
+        if t["escaped"] + t["aborted"] == npk:
+            break
+    a1.record()
+    torch.cuda.synchronize()
+    dt = a0.elapsed_time(a1) / 1e3
+    prob.close()
+    return {"workload": w.name, "packets": npk, "s": dt, "launches": n, "slice_transitions": slice_,
+            "escaped": t["escaped"], "aborted": t["aborted"], "escaped_per_s": t["escaped"] / dt,
+            "transitions_per_s": t["steps"] / dt, "transitions_per_packet": t["steps"] / npk}
+
 
 def _sliced_rate(R, torch, prob, npk, seed, slice_, launches=5, warm=2):
     """Transitions/s (and MC events/s) of time-sliced launches over npk packets."""
@@ -635,7 +723,7 @@ def _extras(R, torch, only=None):
 def _kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("walk.cu", "walk_common.cuh", "rddmc_internal.cuh"):
+    for f in ("walk.cu", "walk_common.cuh", "escape.cuh", "rddmc_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1709_10187_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -653,6 +741,9 @@ def main():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--table-in-smem", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gather", action="store_true", help="skip the gather-rate probe (no gather fraction)")
+    ap.add_argument("--no-complete", action="store_true",
+                    help="skip the completed 1e5-packet subset (no escaped packets/s)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads and the learned-vs-plain comparison")
     ap.add_argument("--extra", default="", help="run only this extra (c3_sphere_static, c3_sphere_v20, "

@@ -661,6 +661,33 @@ int rddmc_scatter_samples(const rddmc_grid* grid, const void* d_table, double x_
                           float* d_out, void* stream);
 
 /*
+ * rddmc_gather_probe -- the memory system's rate of random dependent gathers,
+ * the access the walk makes once per transition (a row of its leakage table,
+ * at an address that depends on the previous row).  The paper has no
+ * counterpart: this measures the denominator of the walk's gather roofline.
+ * Every thread of a persistent grid (ctas_per_sm CTAs of threads_per_cta
+ * threads on each SM; ctas_per_sm = 0, or more than fit, launches as many as
+ * fit) follows `chain` links through d_table, each link one row_bytes load
+ * whose first word is the next row's index.  With in_smem each CTA first
+ * copies the table into shared memory and chases there; otherwise the loads
+ * go through L1, and the table's size decides where they are served (L1, L2
+ * or HBM).  Time the call with events on `stream`; rate = *gathers / time.
+ *   d_table      device, table_bytes, 256-byte aligned, caller-owned; with
+ *                fill = 1 this call first writes a single-cycle permutation
+ *                of its rows into it (row r -> (a r + c) mod n), which later
+ *                calls with fill = 0 may reuse.
+ *   table_bytes  row_bytes x n rows, n a power of two, 64 <= n <= 2^32;
+ *                at most 200 KiB with in_smem (else RDDMC_ERR_SIZE).
+ *   row_bytes    8 or 16.
+ *   d_sink       device, one u64 the kernel may write (keeps the loads live).
+ *   gathers      host out: the number of loads the launch makes.
+ * Returns RDDMC_ERR_ARG for bad arguments, RDDMC_ERR_CUDA for a failed launch.
+ */
+int rddmc_gather_probe(void* d_table, uint64_t table_bytes, int row_bytes, int in_smem, uint32_t chain,
+                       int ctas_per_sm, int threads_per_cta, uint64_t seed, int fill, unsigned long long* d_sink,
+                       uint64_t* gathers, void* stream);
+
+/*
  * rddmc_launch_packets_noalloc -- rddmc_launch_packets for callers that cannot
  * allocate device memory.  The paper has no counterpart: this is a deployment
  * variant.  A caller that cannot call cudaMalloc (for example a plug-in inside

@@ -2,8 +2,10 @@
 
 Each translation unit of ``csrc/`` is compiled by its own nvcc process (in
 parallel), then linked into one shared library exporting the C-ABI of
-``include/rddmc.h``.  ``--fmad=false`` keeps FP64 products and sums rounded as
-written (the leakage thresholds are decided in FP64).
+``include/rddmc.h``.  The FP64 tables (leakage thresholds, eq. R_discrete
+thresholds) are compiled with ``--fmad=false`` so their products and sums stay
+rounded as written; the walk kernels keep fused multiply-adds for their FP32
+arithmetic (their FP64 escape geometry rounds each step explicitly).
 """
 import concurrent.futures as cf
 import os
@@ -15,7 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librddmc.so")
-SOURCES = ["api.cu", "precompute.cu", "walk.cu", "timewalk.cu", "redist.cu", "batch.cu", "learned.cu", "noalloc.cu"]
+# translation units whose device code must not contract a*b+c into an FMA
+NO_FMA = {"precompute.cu", "redist.cu"}
+SOURCES = ["api.cu", "precompute.cu", "walk.cu", "timewalk.cu", "redist.cu", "batch.cu", "learned.cu", "noalloc.cu", "gather.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,7 +33,7 @@ def nvcc() -> str:
 def _flags():
     # RDDMC_NVCC_EXTRA: extra nvcc options for tuning builds (e.g. -DRDDMC_WALK_MIN_BLOCKS=4)
     extra = os.environ.get("RDDMC_NVCC_EXTRA", "").split()
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-O2",
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC] + extra
 
 
@@ -51,7 +55,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
-        cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        fma = ["--fmad=false"] if src in NO_FMA else []
+        cmd = [cc] + flags + fma + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

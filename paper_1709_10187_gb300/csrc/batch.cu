@@ -21,6 +21,7 @@
 #include <new>
 #include <vector>
 
+#include "escape.cuh"
 #include "grid.h"
 
 namespace rddmc {
@@ -80,52 +81,14 @@ __device__ __noinline__ void batch_escape(const BatchParams& P, const InstDesc& 
     if (D.ndim == 1 && !moving) {
         hist = (int)bin + 1;
     } else {
-        const int ax = (int)(face >> 1), side = (face & 1u) ? 1 : -1;
-        const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
         int idx[3];
         idx[0] = (int)(cell % (unsigned)D.n0);
         idx[1] = D.ndim == 3 ? (int)((cell / (unsigned)D.n0) % (unsigned)D.n1) : 0;
         idx[2] = D.ndim == 3 ? (int)(cell / (unsigned)D.n01) : 0;
-        const double inv = 1.0 / 4294967296.0;
-        double r[3];
-        r[ax] = -D.R + (double)(idx[ax] + (side > 0 ? 1 : 0)) * D.dz[ax];
-        const double p1 = ((double)event_word(gid, e, P.k0, P.k1) + 0.5) * inv;
-        const double p2 = ((double)event_word(gid, e + 1, P.k0, P.k1) + 0.5) * inv;
-        r[t1] = (t1 < D.ndim) ? -D.R + ((double)idx[t1] + p1) * D.dz[t1] : 0.0;
-        r[t2] = (t2 < D.ndim) ? -D.R + ((double)idx[t2] + p2) * D.dz[t2] : 0.0;
-        const double mu = 1.0 - ((double)event_word(gid, e + 2, P.k0, P.k1) + 0.5) * inv;
-        const double ph = 2.0 * 3.14159265358979323846 * (((double)event_word(gid, e + 3, P.k0, P.k1) + 0.5) * inv);
-        const double xu = ((double)event_word(gid, e + 4, P.k0, P.k1) + 0.5) * inv;
-        const double x = D.edges[bin] + xu * (D.edges[bin + 1] - D.edges[bin]);
-        const double st = sqrt(fmax(0.0, 1.0 - mu * mu));
-        double n[3];
-        n[ax] = (double)side * mu;
-        n[t1] = st * cos(ph);
-        n[t2] = st * sin(ph);
-        double nu = 0.0;
-        if (moving) {
-            const double* v = D.cell_v + 3ull * cell;
-            nu = n[0] * (v[0] / D.vth) + n[1] * (v[1] / D.vth) + n[2] * (v[2] / D.vth);
-        }
-        const double xo = x + nu;
-        if (xo < D.edges[0]) {
-            hist = 0;
-        } else if (xo >= D.edges[D.J]) {
-            hist = D.J + 1;
-        } else {
-            int lo = 0, hi = D.J;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (xo >= D.edges[mid]) lo = mid; else hi = mid;
-            }
-            hist = lo + 1;
-        }
-        if (D.ndim == 3) {
-            const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-            const double rn = r[0] * n[0] + r[1] * n[1] + r[2] * n[2];
-            const double b = sqrt(fmax(0.0, rr - rn * rn)) / D.R;
-            sb = min((int)(b / kSbMax * kNsb), kNsb - 1);
-        }
+        const EscapeFrame F{D.ndim, D.J, D.R, D.vth, D.dz, D.edges, moving ? D.cell_v + 3ull * cell : nullptr};
+        const EscapeBins eb = escape_geometry(F, idx, bin, face, gid, e, P.k0, P.k1);
+        hist = eb.hist;
+        sb = eb.sb;
     }
     atomicAdd(&T[kHistOff + hist], 1ull);
     atomicAdd(&T[kFaceOff + face], 1ull);

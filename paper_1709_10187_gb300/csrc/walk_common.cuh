@@ -4,6 +4,7 @@
 #pragma once
 #include <cstdint>
 
+#include "escape.cuh"
 #include "grid.h"
 
 namespace rddmc {
@@ -90,70 +91,23 @@ __device__ __forceinline__ void smem_tally(unsigned long long* s, unsigned idx) 
     if ((int)(threadIdx.x & 31) == leader) atomicAdd(&s[idx], (unsigned long long)__popc(peers));
 }
 
-struct EscapeBins {
-    int hist;   // escape-frequency bin (0 below the grid, J+1 above)
-    int sb;     // impact-parameter bin, -1 if not tallied
-};
-
-// Escape through `face` of `cell` at `bin`.  A static slab cell tallies its bin.
-// Otherwise (3D, or a moving slab cell): a point on the face (two event draws
-// for the tangential axes), an isotropic outward direction (mu uniform on
-// (0,1], azimuth uniform), x uniform in the bin, all FP64;
-// x_obs = x + n.(v/v_th) and, in 3D, the impact parameter b = |r x n|.
+// Escape through `face` of `cell` at `bin`.  A static slab cell tallies its
+// bin; otherwise the escape geometry above decides the bins.
 template <int NDIM>
-__device__ __noinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cell, unsigned bin, unsigned face,
-                                               unsigned long long pid, unsigned long long e, bool moving) {
-    EscapeBins out;
-    out.sb = -1;
-    if (NDIM == 1 && !moving) { out.hist = (int)bin + 1; return out; }
-    const int ax = (int)(face >> 1), side = (face & 1u) ? 1 : -1;
-    const int t1 = (ax + 1) % 3, t2 = (ax + 2) % 3;
+__device__ __forceinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cell, unsigned bin, unsigned face,
+                                                  unsigned long long pid, unsigned long long e, bool moving) {
+    if (NDIM == 1 && !moving) {
+        EscapeBins out;
+        out.hist = (int)bin + 1;
+        out.sb = -1;
+        return out;
+    }
     int idx[3];
     idx[0] = (int)(cell % (unsigned)P.n0);
     idx[1] = NDIM == 3 ? (int)((cell / (unsigned)P.n0) % (unsigned)(P.n01 / P.n0)) : 0;
     idx[2] = NDIM == 3 ? (int)(cell / (unsigned)P.n01) : 0;
-    const double inv = 1.0 / 4294967296.0;
-    double r[3];
-    r[ax] = -P.R + (double)(idx[ax] + (side > 0 ? 1 : 0)) * P.dz[ax];
-    const double p1 = ((double)event_word(pid, e, P.k0, P.k1) + 0.5) * inv;
-    const double p2 = ((double)event_word(pid, e + 1, P.k0, P.k1) + 0.5) * inv;
-    r[t1] = (t1 < NDIM) ? -P.R + ((double)idx[t1] + p1) * P.dz[t1] : 0.0;
-    r[t2] = (t2 < NDIM) ? -P.R + ((double)idx[t2] + p2) * P.dz[t2] : 0.0;
-    const double mu = 1.0 - ((double)event_word(pid, e + 2, P.k0, P.k1) + 0.5) * inv;
-    const double ph = 2.0 * 3.14159265358979323846 * (((double)event_word(pid, e + 3, P.k0, P.k1) + 0.5) * inv);
-    const double xu = ((double)event_word(pid, e + 4, P.k0, P.k1) + 0.5) * inv;
-    const double x = P.edges[bin] + xu * (P.edges[bin + 1] - P.edges[bin]);
-    const double st = sqrt(fmax(0.0, 1.0 - mu * mu));
-    double n[3];
-    n[ax] = (double)side * mu;
-    n[t1] = st * cos(ph);
-    n[t2] = st * sin(ph);
-    double nu = 0.0;
-    if (moving) {
-        const double* v = P.cell_v + 3ull * cell;
-        nu = n[0] * (v[0] / P.vth) + n[1] * (v[1] / P.vth) + n[2] * (v[2] / P.vth);
-    }
-    const double xo = x + nu;
-    if (xo < P.edges[0]) {
-        out.hist = 0;
-    } else if (xo >= P.edges[P.J]) {
-        out.hist = P.J + 1;
-    } else {
-        int lo = 0, hi = P.J;  // edges[lo] <= xo < edges[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (xo >= P.edges[mid]) lo = mid; else hi = mid;
-        }
-        out.hist = lo + 1;
-    }
-    if (NDIM == 3) {
-        const double rr = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        const double rn = r[0] * n[0] + r[1] * n[1] + r[2] * n[2];
-        const double b = sqrt(fmax(0.0, rr - rn * rn)) / P.R;
-        int k = (int)(b / kSbMax * kNsb);
-        out.sb = k > kNsb - 1 ? kNsb - 1 : k;
-    }
-    return out;
+    const EscapeFrame F{NDIM, P.J, P.R, P.vth, P.dz, P.edges, moving ? P.cell_v + 3ull * cell : nullptr};
+    return escape_geometry(F, idx, bin, face, pid, e, P.k0, P.k1);
 }
 
 // Parameter block of a walk launch (tables, state arrays, stream keys, source).

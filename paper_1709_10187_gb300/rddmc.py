@@ -30,7 +30,7 @@ NSB = 64  # impact-parameter bins of the surface-brightness histogram
 
 EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc_precompute_leakage",
             "rddmc_reset_tallies", "rddmc_launch_packets", "rddmc_read_tallies", "rddmc_table_rows",
-            "rddmc_read_packet_states", "rddmc_launch_packets_noalloc", "rddmc_scatter_samples",
+            "rddmc_read_packet_states", "rddmc_launch_packets_noalloc", "rddmc_gather_probe", "rddmc_scatter_samples",
             "rddmc_batch_create", "rddmc_batch_destroy", "rddmc_batch_sizes", "rddmc_batch_upload",
             "rddmc_batch_launch", "rddmc_batch_read_tallies", "rddmc_batch_graph_create", "rddmc_batch_graph_launch",
             "rddmc_batch_graph_destroy", "rddmc_batch_autotune", "rddmc_cell_tau", "rddmc_fp_generate",
@@ -126,6 +126,8 @@ def lib():
         L.rddmc_table_rows.argtypes = [vp, vp, vp, vp, vp]
         L.rddmc_read_packet_states.argtypes = [vp, vp, u64, u64, u64, vp, vp, vp, vp, vp, vp]
         L.rddmc_launch_packets_noalloc.argtypes = [vp, vp, ctypes.POINTER(RunOpts), vp, sz, vp]
+        L.rddmc_gather_probe.argtypes = [vp, u64, i32, i32, ctypes.c_uint32, i32, i32, u64, i32, vp,
+                                         ctypes.POINTER(u64), vp]
         L.rddmc_scatter_samples.argtypes = [vp, vp, ctypes.c_double, u64, u64, vp, vp]
         L.rddmc_cell_tau.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
         L.rddmc_fp_generate.argtypes = [vp, vp, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp,
@@ -243,6 +245,18 @@ def launch_packets_noalloc(grid, d_table: int, opts: RunOpts, d_tallies: int, ta
     _check("rddmc_launch_packets_noalloc", lib().rddmc_launch_packets_noalloc(
         ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(opts), ctypes.c_void_p(d_tallies),
         int(tally_bytes), ctypes.c_void_p(stream)))
+
+
+def gather_probe(d_table: int, table_bytes: int, row_bytes: int, in_smem: bool, chain: int, ctas_per_sm: int,
+                 threads_per_cta: int, seed: int, fill: bool, d_sink: int, stream: int = 0) -> int:
+    """rddmc_gather_probe: launch the random dependent-gather chase; returns the
+    number of loads the launch makes (time it with events on `stream`)."""
+    n = ctypes.c_uint64(0)
+    _check("rddmc_gather_probe", lib().rddmc_gather_probe(
+        ctypes.c_void_p(d_table), int(table_bytes), int(row_bytes), int(bool(in_smem)), int(chain), int(ctas_per_sm),
+        int(threads_per_cta), int(seed), int(bool(fill)), ctypes.c_void_p(d_sink), ctypes.byref(n),
+        ctypes.c_void_p(stream)))
+    return int(n.value)
 
 
 def redistribution_bytes(grid) -> int:

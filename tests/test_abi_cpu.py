@@ -185,3 +185,23 @@ def test_noalloc_launch_checks_its_arguments_like_launch_packets():
     op = R.RunOpts(1, 1000, 0, 64, 0, 0, 0, 0, 0, 0, ctypes.addressof(pr), None)
     assert L.rddmc_launch_packets_noalloc(g, fake, ctypes.byref(op), fake, tb, None) == R.ERR_UNSUPPORTED
     R.destroy_grid(g)
+
+
+def test_gather_probe_checks_its_arguments_without_a_gpu():
+    """rddmc_gather_probe rejects bad sizes before any launch."""
+    import ctypes
+    L = R.lib()
+    fake = 1 << 20
+    n = ctypes.c_uint64(0)
+
+    def call(nbytes, rb, smem=0, chain=16, ctas=0, threads=256, table=fake, sink=fake):
+        return L.rddmc_gather_probe(table, nbytes, rb, smem, chain, ctas, threads, 1, 0, sink, ctypes.byref(n), None)
+
+    assert call(4096, 12) == R.ERR_ARG            # row size
+    assert call(3000 * 8, 8) == R.ERR_ARG         # not a power of two
+    assert call(32 * 8, 8) == R.ERR_ARG           # fewer than 64 rows
+    assert call(4096, 8, chain=0) == R.ERR_ARG
+    assert call(4096, 8, threads=100) == R.ERR_ARG
+    assert call(4096, 8, table=fake + 16) == R.ERR_ARG
+    assert call(4096, 8, sink=None) == R.ERR_ARG
+    assert call(256 << 10, 8, smem=1) == R.ERR_SIZE

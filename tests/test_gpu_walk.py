@@ -175,6 +175,37 @@ def test_wide_core_grid_walk_is_bit_exact():
     _same_tallies(R.Problem(w).run(n, w.seed), C.walk(og, dict(ot, thr=thr, flags=flags), w.seed, 0, n))
 
 
+def test_c2_completed_subset_matches_the_exact_chain():
+    # 1e5 packets of the tau0 = 1e7 slab (256 cells x 512 uniform bins) walked
+    # to escape in step slices of 2^24 transitions: ~3e13 transitions, the
+    # slowest packet ~3e9.  The spectrum, the face counts and the mean number
+    # of transitions against the exact absorbing chain of the oracle's table
+    # (the device table is bit-identical on this grid).
+    w = W.C2
+    og, ot = _oracle(w)
+    ch = A.chain_solve(w, ot)
+    n = 100_000
+    p = R.Problem(w)
+    thr, flags = p.rows()
+    assert np.array_equal(thr, ot["thr"]) and np.array_equal(flags, ot["flags"])
+    p.reset()
+    launches = 0
+    while True:
+        p.launch(n, w.seed, steps_per_launch=1 << 24, resume=1 if launches else 0)
+        launches += 1
+        t = p.read()
+        if t["escaped"] + t["aborted"] == n:
+            break
+        assert launches < 2000
+    assert t["escaped"] == n and t["aborted"] == 0
+    zmax, frac, pval = A.compare_counts_to_probs(t["hist"], ch["hist"], n)
+    assert zmax < 5.0 and frac <= 0.02 and pval > 1e-3, (zmax, frac, pval)
+    fz = (t["faces"][:2] - n * ch["faces"][:2]) / np.sqrt(n * ch["faces"][:2] * (1 - ch["faces"][:2]))
+    assert np.all(np.abs(fz) < 4.0), fz
+    zs = (t["steps"] / n - ch["steps_mean"]) / np.sqrt(ch["steps_var"] / n)
+    assert abs(zs) < 4.0, (t["steps"] / n, ch["steps_mean"])
+
+
 def test_c2_wide_core_run_to_completion_matches_chain():
     # every one of 1e6 packets of the tau0 = 1e7 slab on the wide-core grid walked
     # to escape (~2e4 transitions each), against the exact chain's spectrum and
