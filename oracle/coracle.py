@@ -67,6 +67,9 @@ def lib():
                                     vp, vp, vp, vp]
         L.orc_fp_samples.restype = None
         L.orc_fp_samples.argtypes = [vp, i32, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp]
+        L.orc_fp_region_samples.restype = None
+        L.orc_fp_region_samples.argtypes = [ctypes.POINTER(OrcGrid), vp, vp, vp, vp, i32, i32, i32, i32, vp, i32, vp,
+                                            vp, u64, u64, u64, u64, vp, vp]
         L.orc_upar_table.restype = None
         L.orc_upar_table.argtypes = [d, vp]
         _LIB = L
@@ -334,4 +337,23 @@ def fp_samples(rows: np.ndarray, b: int, jlo, jhi, seed: int, p0: int, n: int, c
     steps = np.zeros(n, dtype=np.uint64)
     lib().orc_fp_samples(_ptr(rows), int(L), int(J), int(b), _ptr(jlo), _ptr(jhi), int(seed), int(p0), int(n),
                          int(cap), _ptr(out), _ptr(steps))
+    return out.reshape(n, 8), steps
+
+
+def fp_region_samples(grid: Grid, table: dict, bl: int, sh: int, m: int, nbx: int, bricks, off, bins, seed: int,
+                      p0: int, n: int, cap: int):
+    """First passages out of the regions (inner cubes) of bricks of the grid's
+    own medium (see orc_fp_region_samples): records [n x 8] {brick, start bin,
+    start cell, exit face, exit bin, exit cell on the face, rebin draws, 0} and
+    transition counts."""
+    bricks = np.ascontiguousarray(bricks, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    out = np.zeros(8 * n, dtype=np.int32)
+    steps = np.zeros(n, dtype=np.uint64)
+    thr = np.ascontiguousarray(table["thr"].ravel())
+    lib().orc_fp_region_samples(ctypes.byref(grid.g), _ptr(thr), _ptr(table["flags"]), _ptr(table["rebin_m"]),
+                                _ptr(table["rebin_thr"]), int(bl), int(sh), int(m), int(nbx), _ptr(bricks),
+                                int(len(bricks)), _ptr(off), _ptr(bins), int(seed), int(p0), int(n), int(cap),
+                                _ptr(out), _ptr(steps))
     return out.reshape(n, 8), steps

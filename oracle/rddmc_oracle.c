@@ -1347,3 +1347,77 @@ void orc_fp_samples(const uint32_t* rows, int L, int J, int b, const int32_t* jl
         steps[i] = t;
     }
 }
+
+/* First passages out of non-uniform regions of a grid's own medium (training
+ * data of the learned proposal for media that vary from cell to cell).  The
+ * grid is cut into bricks of bl^3 cells, brick coordinate (i + sh) / bl of cell
+ * index i on every axis (brick index axis 0 fastest, nbx bricks per axis); a
+ * brick's region is its inner cube of side r = bl - 2 m.  Sample i uses packet
+ * pk = p0 + i: event draw 0 picks the brick bricks[k], k = (w0 nel) >> 32;
+ * draw 1 the start cell of the region, (w1 r^3) >> 32 (axis 0 fastest); draw 2
+ * the start bin among that brick's listed bins bins[off[k] ..  off[k+1]).  The
+ * packet then takes the walk's own transitions on the grid's table (Sec. 2.3;
+ * Doppler rebins take the next event draws) until an outcome would carry it
+ * out of the region: that crossing is not made, and the sample records the
+ * face, the bin and the cell on the face it leaves from.  Out, per sample (8
+ * ints): brick, start bin, start cell (region-local index), exit face (6: none
+ * within cap transitions), exit bin, exit cell on the face (the other two axes,
+ * lower axis first, u + r v), event draws taken by rebins, 0; steps: the
+ * transitions taken, the crossing one included. */
+void orc_fp_region_samples(const orc_grid* g, const uint32_t* thr, const uint32_t* flags, const int32_t* rebin_m,
+                           const uint32_t* rebin_thr, int bl, int sh, int m, int nbx, const int32_t* bricks,
+                           int nel, const int32_t* off, const int32_t* bins, uint64_t seed, uint64_t p0, uint64_t n,
+                           uint64_t cap, int32_t* out, uint64_t* steps) {
+    const int J = g->J, NT = orc_nthr(g), nf = 2 * g->ndim, r = bl - 2 * m;
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t pk = p0 + i;
+        const uint32_t w0 = orc_word(seed, pk, ORC_EVENT, 0);
+        const uint32_t w1 = orc_word(seed, pk, ORC_EVENT, 1);
+        const uint32_t w2 = orc_word(seed, pk, ORC_EVENT, 2);
+        const int k = (int)(((uint64_t)w0 * (uint64_t)nel) >> 32);
+        const int br = bricks[k];
+        const int bc[3] = {br % nbx, (br / nbx) % nbx, br / (nbx * nbx)};
+        const int mc = (int)(((uint64_t)w1 * (uint64_t)(r * r * r)) >> 32);
+        int l[3] = {mc % r, (mc / r) % r, mc / (r * r)};
+        int base[3];
+        for (int a = 0; a < 3; ++a) base[a] = bc[a] * bl - sh + m;
+        const int cnt = off[k + 1] - off[k];
+        int j = bins[off[k] + (int)(((uint64_t)w2 * (uint64_t)cnt) >> 32)];
+        out[8 * i + 0] = br;
+        out[8 * i + 1] = j;
+        out[8 * i + 2] = mc;
+        uint64_t e = 3, t = 0;
+        int face = 6, pos = -1;
+        while (t < cap) {
+            int idx[3] = {base[0] + l[0], base[1] + l[1], base[2] + l[2]};
+            const int64_t c = orc_cell_of(g, idx);
+            const int64_t st = c * J + j;
+            const uint32_t wt = orc_word(seed, pk, ORC_TRANS, t);
+            ++t;
+            int o = 0;
+            while (o < NT && wt >= thr[st * NT + o]) ++o;
+            const unsigned act = (flags[st] >> (2 * o)) & 3u;
+            if (o < 2) { j += o ? 1 : -1; continue; }
+            const int f = o - 2, ax = f / 2, side = (f & 1) ? 1 : -1;
+            if (l[ax] + side < 0 || l[ax] + side >= r) {
+                face = f;
+                const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
+                pos = l[u] + r * l[v];
+                break;
+            }
+            if (act == ORC_ACT_ESCAPE || act == ORC_ACT_TO_MC) break;  /* not inside a region: no sample */
+            if (act == ORC_ACT_REBIN) {
+                const uint32_t wr = orc_word(seed, pk, ORC_EVENT, e++);
+                int jn = j + rebin_m[c * nf + f] + (wr >= rebin_thr[c * nf + f] ? 1 : 0);
+                j = jn < 0 ? 0 : (jn > J - 1 ? J - 1 : jn);
+            }
+            l[ax] += side;
+        }
+        out[8 * i + 3] = face;
+        out[8 * i + 4] = j;
+        out[8 * i + 5] = pos;
+        out[8 * i + 6] = (int32_t)(e - 3);
+        out[8 * i + 7] = 0;
+        steps[i] = t;
+    }
+}

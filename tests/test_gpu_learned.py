@@ -66,16 +66,18 @@ def test_network_loss_and_gradients_match_fp64_reference(proposal):
         off += o * i + o
     for s, o in offs:
         flat[s:s + o] = w_f[s:s + o]
-    lo, g_ref = M.loss_and_grad(flat, p.n_out, p.nA, p.nB, X.float().cpu().numpy(), tA.cpu().numpy(),
-                                tB.cpu().numpy(), p.nC, p.S, tC.cpu().numpy())
+    lo, g_ref, g_abs = M.loss_and_grad(flat, p.n_out, p.nA, p.nB, X.float().cpu().numpy(), tA.cpu().numpy(),
+                                       tB.cpu().numpy(), p.nC, p.S, tC.cpu().numpy(), scales=True)
     assert float(loss.item()) / Bsz == pytest.approx(lo, rel=1e-2)
-    off = 0
-    for (o, i) in M.shapes(p.n_out):
-        for size in (o * i, o):
-            a, b = g_gpu[off:off + size], g_ref[off:off + size]
-            assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-7, (off, np.linalg.norm(a - b),
-                                                                              np.linalg.norm(b))
-            off += size
+    # element by element: the device stores activations and back-propagated
+    # gradients in BF16 (relative rounding 2^-9 per stored value, compounded
+    # over up to three layers) where the FP64 network keeps them exact, so each
+    # parameter's gradient may differ by a few 2^-9 of the sum of the absolute
+    # terms it adds up; 3e-2 of that sum is the bound
+    err = np.abs(g_gpu - g_ref)
+    bound = 3e-2 * g_abs + 1e-7
+    worst = int(np.argmax(err / bound))
+    assert np.all(err <= bound), (worst, g_gpu[worst], g_ref[worst], g_abs[worst], float((err / (g_abs + 1e-30)).max()))
 
 
 def test_training_learns_the_first_passage_distribution(proposal):
@@ -132,7 +134,8 @@ def _bf16(x):
 def _device_rounded_grads(layers, X, tA, tB, nA, nB, n_out):
     """Loss and gradients in FP64 with BF16 rounding exactly where the device
     stores BF16: hidden activations, the logit gradient used in products, and
-    the back-propagated gradients; bias gradients sum the unrounded values."""
+    the back-propagated gradients; bias gradients sum the unrounded values.
+    Also returns, per parameter, the sum of the absolute terms of its gradient."""
     B = X.shape[0]
     hs = [X]
     for l, (W, b) in enumerate(layers[:3]):
@@ -151,16 +154,20 @@ def _device_rounded_grads(layers, X, tA, tB, nA, nB, n_out):
             g[r, t] -= 1.0
     g /= B
     grads = [None] * 4
+    mags = [None] * 4
     gb = _bf16(g)
     grads[3] = (gb.T @ hs[3], g.sum(axis=0))
+    mags[3] = (np.abs(gb).T @ np.abs(hs[3]), np.abs(g).sum(axis=0))
     d = gb
     for l in (2, 1, 0):
         W_next = layers[l + 1][0]
         df = (d @ W_next) * (hs[l + 1] > 0)
         db = _bf16(df)
         grads[l] = (db.T @ hs[l], df.sum(axis=0))
+        mags[l] = (np.abs(db).T @ np.abs(hs[l]), np.abs(df).sum(axis=0))
         d = db
-    return loss / B, np.concatenate([np.concatenate([gw.ravel(), gbias]) for gw, gbias in grads])
+    flat = lambda gs: np.concatenate([np.concatenate([gw.ravel(), gbias]) for gw, gbias in gs])
+    return loss / B, flat(grads), flat(mags)
 
 
 @pytest.mark.parametrize("n_out,nA,nB", [(64, 40, 16), (128, 96, 32), (320, 288, 32)])
@@ -195,14 +202,17 @@ def test_network_gradients_for_narrow_and_wide_heads(n_out, nA, nB):
         off += o * i
         layers.append((W, w64[off:off + o]))
         off += o
-    lo, g_ref = _device_rounded_grads(layers, X.float().cpu().numpy().astype(np.float64), tA.cpu().numpy(),
-                                      tB.cpu().numpy(), nA, nB, n_out)
+    lo, g_ref, g_abs = _device_rounded_grads(layers, X.float().cpu().numpy().astype(np.float64), tA.cpu().numpy(),
+                                             tB.cpu().numpy(), nA, nB, n_out)
     assert float(loss.item()) / batch == pytest.approx(lo, rel=1e-4)
     g = grad.cpu().numpy().astype(np.float64)
-    off = 0
-    for (o, i) in M.shapes(n_out):
-        for size in (o * i, o):
-            a, b = g[off:off + size], g_ref[off:off + size]
-            assert np.linalg.norm(a - b) <= 2e-3 * np.linalg.norm(b) + 1e-7, (n_out, off, np.linalg.norm(a - b),
-                                                                              np.linalg.norm(b))
-            off += size
+    # element by element: with BF16 rounding where the device rounds, what is
+    # left is FP32 accumulation and the rare value that rounds to the other
+    # BF16 neighbour (its FP32 and FP64 forms straddle a rounding boundary),
+    # which moves one term of a sum by one BF16 step (2^-8 of it): 8e-3 of the
+    # sum of the absolute terms allows two such steps in one parameter
+    err = np.abs(g - g_ref)
+    bound = 8e-3 * g_abs + 1e-7
+    worst = int(np.argmax(err / bound))
+    assert np.all(err <= bound), (n_out, worst, g[worst], g_ref[worst], g_abs[worst],
+                                  float((err / (g_abs + 1e-30)).max()))

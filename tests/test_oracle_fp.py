@@ -15,6 +15,7 @@ import itertools
 import numpy as np
 import pytest
 
+from oracle import analytic as A
 from oracle import coracle as C
 from paper_1709_10187_gb300 import workloads as W
 
@@ -169,3 +170,111 @@ def test_exit_position_is_on_the_exit_face_and_cap_is_flagged():
     c = out[:, 2]
     c0, c1, c2 = c % b, (c // b) % b, c // (b * b)
     assert np.all((c0 <= c1) & (c1 <= c2) & (2 * c2 <= b - 1))
+
+
+# ---------------------------------------------------------------------------
+# First passages out of a region of a medium that varies from cell to cell
+
+def _region_chain(w, t, base, r):
+    """Exact absorption law of the walk inside the region [base, base + r)^3 of
+    grid w with table t (the oracle's dense table): transitions by the quantised
+    thresholds, Doppler rebins across faces by (m, thr), exits recorded as
+    (face, bin, cell on the face)."""
+    J = w.J
+    n0, n1 = w.n[0], w.n[1]
+    thr = t["thr"].astype(np.float64)
+    K = thr.shape[1] + 1
+    cum = np.concatenate([np.zeros((thr.shape[0], 1)), thr, np.full((thr.shape[0], 1), 2.0 ** 32)], axis=1)
+    p_out = np.diff(cum, axis=1) / 2.0 ** 32
+    flags = t["flags"]
+    nf = 6
+    n_t = r ** 3 * J
+    sid = lambda l, j: ((l[0] + r * (l[1] + r * l[2])) * J + j)
+    Q = np.zeros((n_t, n_t))
+    absorb, Rrows, Rcols, Rvals = {}, [], [], []
+    for l in itertools.product(range(r), repeat=3):
+        c = (base[0] + l[0]) + n0 * ((base[1] + l[1]) + n1 * (base[2] + l[2]))
+        for j in range(J):
+            s = sid(l, j)
+            st = c * J + j
+            for o in range(K):
+                p = p_out[st, o]
+                if p == 0.0:
+                    continue
+                if o < 2:
+                    Q[s, sid(l, j + (1 if o else -1))] += p
+                    continue
+                f = o - 2
+                ax, side = f // 2, (1 if f & 1 else -1)
+                n = list(l)
+                n[ax] += side
+                if not (0 <= n[ax] < r):
+                    u, v = _other_axes(ax)
+                    key = (f, j, l[u] + r * l[v])
+                    col = absorb.setdefault(key, len(absorb))
+                    Rrows.append(s); Rcols.append(col); Rvals.append(p)
+                    continue
+                act = (int(flags[st]) >> (2 * o)) & 3
+                if act == 3:  # Doppler rebin across the face
+                    m = int(t["rebin_m"][c * nf + f])
+                    pr = float(t["rebin_thr"][c * nf + f]) / 2.0 ** 32
+                    for jn, pj in ((j + m, pr), (j + m + 1, 1.0 - pr)):
+                        jn = min(max(jn, 0), J - 1)
+                        if pj > 0:
+                            Q[s, sid(n, jn)] += p * pj
+                else:
+                    assert act == 0
+                    Q[s, sid(n, j)] += p
+    R_ = np.zeros((n_t, len(absorb)))
+    for a, b_, v in zip(Rrows, Rcols, Rvals):
+        R_[a, b_] += v
+    A = np.eye(n_t) - Q
+    B = np.linalg.solve(A, R_)
+    T = np.linalg.solve(A, np.ones(n_t))
+    T2 = np.linalg.solve(A, 2.0 * T - 1.0)  # E[T^2] per start state
+    return B, absorb, (T, T2), sid
+
+
+def test_region_first_passages_match_the_exact_chain_of_a_moving_clumpy_region():
+    # an 8^3 grid with a cell-resolution lognormal density and turbulent
+    # velocity (so rows differ from cell to cell and crossings rebin); one
+    # brick of 8^3 with a margin of 2: the region is the central 4^3 cells
+    med = W.clumpy_medium(n=8, J=10, x_max=10.0, tau0=300.0, brick=1, sigma_v_kms=20.0, packets=1, seed=0x5EED0710)
+    w = med.workload
+    g = C.Grid(w, n_rel=med.n_rel)
+    g.v = np.ascontiguousarray(med.v_kms, dtype=np.float64)
+    g.g.v = C._ptr(g.v)
+    t = g.table()
+    assert len(set(map(tuple, t["thr"].reshape(w.ncell, -1)[:, :7].tolist()))) > 100  # cells differ
+    bl, m, r = 8, 2, 4
+    bins = np.arange(2, 8, dtype=np.int32)  # the listed start bins
+    B, absorb, (T, T2), sid = _region_chain(w, t, (m, m, m), r)
+    n = 120_000
+    out, steps = C.fp_region_samples(g, t, bl, 0, m, 1, [0], [0, len(bins)], bins, 0xF00D, 0, n, 10_000_000)
+    assert np.all(out[:, 0] == 0) and np.all(out[:, 3] < 6)
+    assert out[:, 6].sum() > 0  # crossings inside the region were rebinned
+    # start states: uniform over the region's cells and the listed bins
+    cells = np.bincount(out[:, 2], minlength=r ** 3)
+    assert abs(cells.std() / cells.mean()) < 0.06
+    starts = [sid((c % r, (c // r) % r, c // (r * r)), j) for c in range(r ** 3) for j in bins]
+    p_exit = B[starts].mean(axis=0)
+    assert abs(p_exit.sum() - 1.0) < 1e-9
+    keys = [(int(f), int(j), int(p)) for f, j, p in out[:, [3, 4, 5]]]
+    cnt = np.zeros(len(absorb))
+    for k in keys:
+        cnt[absorb[k]] += 1
+    zmax, frac, pval = A.compare_counts_to_probs(cnt, p_exit, n)
+    assert zmax < 5.0 and frac <= 0.02 and pval > 1e-3, (zmax, frac, pval)
+    # exit (face, bin) marginal, and the mean number of transitions
+    fb = {}
+    for (f, j, _), col in absorb.items():
+        fb.setdefault((f, j), []).append(col)
+    km = list(fb)
+    pm = np.array([p_exit[fb[k]].sum() for k in km])
+    cm = np.array([cnt[fb[k]].sum() for k in km])
+    zmax, frac, pval = A.compare_counts_to_probs(cm, pm, n)
+    assert zmax < 5.0 and pval > 1e-3, (zmax, pval)
+    tm = T[starts].mean()
+    var = T2[starts].mean() - tm * tm
+    z = (steps.astype(np.float64).mean() - tm) / np.sqrt(var / n)
+    assert abs(z) < 4.0, (steps.mean(), tm, z)
