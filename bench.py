@@ -567,6 +567,134 @@ def _learned_vs_plain(R, torch, n=64, brick=16, margin=1, J=64, x_max=64.0, tau0
             "speedup_at_equal_l1": t_e / t_l, "reference_packets": 4 * npk}
 
 
+def _equal_l1(runs_l, runs_p, ref_hist, n_ref, npk, targets=(0.02, 0.01), n_boot=200, seed=0x5EED0B00):
+    """Learned against plain at equal escape-spectrum L1, from independent seed
+    runs of npk packets per arm (each run: (seconds, histogram)) and an
+    independent plain reference of n_ref packets.
+
+    Model of an arm's expected L1 against the reference at N packets:
+    L1(N)^2 = B^2 + K^2 (1/N + 1/n_ref), with K = sqrt(2/pi) sum_b sqrt(p_b (1 -
+    p_b)) the multinomial noise constant of the spectrum p (taken from the
+    reference): E|X| = sqrt(2/pi) sd for each bin's normal fluctuation, and the
+    arm's and the reference's noise add.  B, the arm's bias floor, is the part
+    of the pooled runs' L1 the noise does not explain (0 for an unbiased arm,
+    up to noise).  The packets an arm needs for a target L1 follow from its
+    model, the wall time from its measured seconds per packet.  The measured
+    cumulative curves L1(first m runs) are reported beside the model.  Errors:
+    bootstrap over the runs (resampled with replacement)."""
+    ref = np.asarray(ref_hist, dtype=np.float64)
+    ref = ref / ref.sum()
+    K = float(np.sqrt(2.0 / np.pi) * np.sqrt(ref * (1.0 - ref)).sum())
+    rng = np.random.default_rng(seed)
+
+    def curve(runs, order):
+        acc = np.zeros_like(ref)
+        l1s, ts, t = [], [], 0.0
+        for i in order:
+            sec, h = runs[i]
+            acc = acc + np.asarray(h, dtype=np.float64)
+            t += sec
+            l1s.append(float(np.abs(acc / acc.sum() - ref).sum()))
+            ts.append(t)
+        return np.array(l1s), np.array(ts)
+
+    def arm(runs, order):
+        l1s, ts = curve(runs, order)
+        n = len(l1s) * npk
+        noise2 = K * K * (1.0 / n + 1.0 / n_ref)
+        b2 = max(l1s[-1] ** 2 - noise2, 0.0)
+        return b2, ts[-1] / n, l1s, ts
+
+    def need(b2, tgt):
+        d = tgt * tgt - b2 - K * K / n_ref
+        return K * K / d if d > 0 else float("inf")
+
+    def summary(order_l, order_p):
+        bl, spp_l, l1l, tl = arm(runs_l, order_l)
+        bp, spp_p, l1p, tp = arm(runs_p, order_p)
+        out = {"bias_floor_learned": np.sqrt(bl), "bias_floor_plain": np.sqrt(bp),
+               "s_per_packet_learned": spp_l, "s_per_packet_plain": spp_p}
+        for tgt in targets:
+            nl, npl = need(bl, tgt), need(0.0, tgt)  # the plain walk is unbiased
+            out[f"s_to_{tgt:g}_learned"] = nl * spp_l
+            out[f"s_to_{tgt:g}_plain"] = npl * spp_p
+            out[f"speedup_at_{tgt:g}"] = (npl * spp_p) / (nl * spp_l) if np.isfinite(nl) else 0.0
+        return out, (l1l, tl, l1p, tp)
+
+    n = len(runs_l)
+    base, (l1l, tl, l1p, tp) = summary(range(n), range(len(runs_p)))
+    boots = [summary(rng.integers(0, n, n), rng.integers(0, len(runs_p), len(runs_p)))[0] for _ in range(n_boot)]
+    res = {"runs_per_arm": n, "packets_per_run": npk, "reference_packets": n_ref, "noise_constant_K": K,
+           "curve_learned": {"packets": [int((i + 1) * npk) for i in range(n)], "s": tl.tolist(), "l1": l1l.tolist()},
+           "curve_plain": {"packets": [int((i + 1) * npk) for i in range(len(tp))], "s": tp.tolist(),
+                           "l1": l1p.tolist()},
+           "curve_model_unbiased": [float(K * np.sqrt(1.0 / ((i + 1) * npk) + 1.0 / n_ref)) for i in range(n)]}
+    for k, v in base.items():
+        vals = np.array([b[k] for b in boots], dtype=np.float64)
+        fin = vals[np.isfinite(vals)]
+        res[k] = {"value": float(v), "err": float(fin.std()) if fin.size > 1 else None,
+                  "bootstrap_finite": int(fin.size)}
+    return res
+
+
+def _learned_c5(R, torch, tau0=1.0e7, npk=100_000, runs=8, n_ref=10_000_000, ndata=4_000_000, iters=4000,
+                brick=16, margin=1, n=128, J=256, x_max=256.0):
+    """The learned proposal on the clumpy workload at cell resolution (128^3
+    cells x 256 bins over [-256, 256], lognormal density sigma_ln = 1 with
+    spectral slope -11/3, turbulent velocity 10 km/s per component, tau0 at
+    the mean density): region proposals over 16^3-cell bricks (14^3 inner
+    cubes) trained on first passages the plain walk takes through the medium's
+    own regions, then `runs` independent runs of npk packets per arm against a
+    plain reference of n_ref packets (_equal_l1)."""
+    from paper_1709_10187_gb300 import learned as Lr
+    out = {"workload": f"clumpy_cells_{n}c_{J}b_tau{tau0:.0e}", "tau0": tau0}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+
+    med = W.clumpy_medium(n=n, J=J, x_max=x_max, tau0=tau0, brick=1, packets=npk)
+    out["precompute_s"], prob = timed(lambda: R.Problem.clumpy(med))
+    out["table_bytes"] = int(prob.table.numel())
+    out["setup_s"], prop = timed(lambda: Lr.RegionProposal(prob, med.n_rel, med.v_kms, brick, margin, tau_lo=5.0,
+                                                           tau_hi=1.0e12))
+    out["data_s"], data = timed(lambda: prop.generate(ndata, seed=11))
+    held = prop.generate(65536, seed=12, p0=1 << 40)
+    out["train_s"], _ = timed(lambda: prop.train(data, iters=iters, batch=8192, lr=2e-3))
+    out["heldout_loss"] = prop.mean_loss(held)
+    out.update(train_samples=ndata, train_iters=iters, region=brick - 2 * margin, n_out=prop.n_out)
+    del data, held
+    prop.run(n_packets=2000, seed=1)  # warm-up
+    prob.run(2000, 1)
+    runs_l, runs_p, lt, pt = [], [], [], []
+    for i in range(runs):
+        s, r = timed(lambda: prop.run(n_packets=npk, seed=0xC5000 + i))
+        runs_l.append((s, r["hist"]))
+        lt.append((r["steps"] / npk, r["proposals"] / npk, r["launches"], r["aborted"]))
+        s, r = timed(lambda: prob.run(npk, 0xC5100 + i))
+        runs_p.append((s, r["hist"]))
+        pt.append((r["steps"] / npk, r["aborted"]))
+    ref = np.zeros(J + 2)
+    t_ref = 0.0
+    chunk = 1_000_000
+    for k in range(0, n_ref, chunk):
+        s, r = timed(lambda: prob.run(min(chunk, n_ref - k), 0xC5200 + k // chunk))
+        ref += r["hist"]
+        t_ref += s
+    out["reference_s"] = t_ref
+    out["learned_transitions_per_packet"] = float(np.mean([x[0] for x in lt]))
+    out["learned_proposals_per_packet"] = float(np.mean([x[1] for x in lt]))
+    out["learned_launches_per_run"] = float(np.mean([x[2] for x in lt]))
+    out["plain_transitions_per_packet"] = float(np.mean([x[0] for x in pt]))
+    out["aborted"] = int(sum(x[3] for x in lt) + sum(x[1] for x in pt))
+    out["equal_l1"] = _equal_l1(runs_l, runs_p, ref, n_ref, npk)
+    prob.close()
+    return out
+
+
 def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm=0, with_leaks=False):
     """A flash of npk packets advanced through constant time steps, one launch
     of the time-dependent walk per step (Sec. 2.3; eq. E_estimator), timed with

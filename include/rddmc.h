@@ -597,7 +597,57 @@ typedef struct rddmc_proposal {
     unsigned long long* d_queue_pid;
     int32_t n_bricks;
     int32_t margin;
+    /* Region mode, for media that vary from cell to cell: n_bricks x 8 floats
+     * summarising each brick's inner cube (see rddmc_fp_region); features are
+     * taken in the world frame (no symmetry fold or mirror) from the summary,
+     * the bin and the packet's own cell.  NULL: uniform bricks (the fold). */
+    const float* d_summary;
 } rddmc_proposal;
+
+/* Regions of a medium that varies from cell to cell, for training the
+ * proposal there (an extension beyond the paper, like the proposal itself).
+ * The grid is cut into bricks of `brick` cells per edge (boundaries at cell
+ * indices = offset mod brick, brick index axis 0 fastest, partial bricks
+ * counted); a brick's region is its inner cube of side brick - 2 margin.
+ *   d_bricks    device, n_eligible brick indices the samples start in (bricks
+ *               wholly inside the grid, margin >= 1, so regions are interior).
+ *   d_bin_off   device, n_eligible + 1 offsets into d_bins.
+ *   d_bins      device, the start bins of listed brick k:
+ *               d_bins[d_bin_off[k] .. d_bin_off[k+1]).
+ *   d_summary   device, 8 floats per lattice brick summarising its region:
+ *               log10(k0 dz) at the geometric-mean density, the standard
+ *               deviation of log10 n, the slope of log10 n per axis against
+ *               the cell position (2l + 1)/r - 1, the mean and rms comoving
+ *               shift f_mu (v_c - v_nb).e / v_th over the region's interior
+ *               faces, and one unused value. */
+typedef struct rddmc_fp_region {
+    int32_t brick;
+    int32_t offset;
+    int32_t margin;
+    int32_t n_eligible;
+    const int32_t* d_bricks;
+    const int32_t* d_bin_off;
+    const int32_t* d_bins;
+    const float* d_summary;
+} rddmc_fp_region;
+
+/* First passages out of regions of the grid's own medium (3D, DDMC mode, no
+ * dust): sample i is packet p0 + i under `seed`; event draws 0-2 pick the
+ * brick, the start cell of its region (axis 0 fastest) and the start bin from
+ * the brick's list; the packet then takes the walk's own transitions (Sec. 2.3,
+ * Doppler rebins across faces taking the next event draws) until an outcome
+ * would carry it out of the region, which is not made.  d_out (device, 8 int32
+ * per sample): brick, start bin, start cell, exit face (6: none within cap
+ * transitions), exit bin, exit cell on the face (the other two axes, lower
+ * axis first, u + r v with r the region's side), event draws taken by rebins,
+ * 0; d_steps (device, u64): transitions taken, the crossing one included.
+ * With `train` (its d_lk unused) also the network inputs (world frame, from
+ * the region's summary, the start bin and the start cell's density) and the
+ * targets: face * J + exit bin, the log2 step bucket, face * r^2 + exit cell
+ * (-1 without an exit). */
+int rddmc_fp_region_generate(const rddmc_grid* grid, const void* d_table, const rddmc_fp_region* region,
+                             uint64_t seed, uint64_t p0, uint64_t n, uint64_t cap, int32_t* d_out, uint64_t* d_steps,
+                             const rddmc_fp_train* train, void* stream);
 
 /* Serve the parked packets of a walk with the trained network: features of
  * the packet's cell folded into its brick's fundamental domain, tensor-core

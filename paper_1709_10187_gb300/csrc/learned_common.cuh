@@ -64,6 +64,48 @@ __device__ __forceinline__ void features(float lk, float lp, float x, const int 
     for (int i = 0; i < kFeat; ++i) out[i] = __float2bfloat16(f[i]);
 }
 
+// Summary of a region (a brick's inner cube) of a medium that varies from cell
+// to cell, kRegionSum floats per brick, computed by the caller from the medium:
+// [0] log10(k0 dz) at the region's geometric-mean density, [1] the standard
+// deviation of log10 n over its cells, [2..4] the least-squares slope of
+// log10 n per axis against the cell position (2l + 1)/r - 1, [5] the mean and
+// [6] the rms of the comoving shift f_mu (v_c - v_nb).e_a / v_th over the
+// region's interior faces (in Doppler widths; the same for both directions of
+// a crossing), [7] unused.
+constexpr int kRegionSum = 8;
+
+// Network inputs for a packet in such a region, in the world frame (no
+// symmetry fold: the region has none): region size in tau at line centre and
+// at the bin, the start cell's log10 density relative to the region's mean,
+// the frequency (x / x_max, |x| / x_max, one Fourier pair), the region's
+// density spread and slopes, its mean and rms Doppler shift per crossing, and
+// the cell's position (2 l + 1) / r - 1 per axis.
+__device__ __forceinline__ void features_region(const float* __restrict__ sm, float lp, float x, float dlog,
+                                                const int l[3], int r, const FeatConst& C, __nv_bfloat16* out) {
+    float f[kFeat];
+    f[0] = (sm[0] + C.log_b) * 0.1f;
+    f[1] = (sm[0] + lp + C.log_b) * 0.2f;
+    f[2] = dlog;
+    const float xs = x * C.inv_xs;
+    f[3] = xs;
+    f[4] = fabsf(xs);
+    float sn, cs;
+    sincospif(xs, &sn, &cs);
+    f[5] = sn;
+    f[6] = cs;
+    f[7] = sm[1] * 2.0f;
+    f[8] = sm[2];
+    f[9] = sm[3];
+    f[10] = sm[4];
+    f[11] = sm[5] * 4.0f;
+    f[12] = sm[6] * 4.0f;
+    const float inv_r = 1.0f / (float)r;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) f[13 + a] = (float)(2 * l[a] + 1) * inv_r - 1.0f;
+#pragma unroll
+    for (int i = 0; i < kFeat; ++i) out[i] = __float2bfloat16(f[i]);
+}
+
 __device__ __forceinline__ int step_bucket(unsigned long long t) {
     int k = 63 - __clzll((long long)(t | 1ull));
     return k < kStepBuckets - 1 ? k : kStepBuckets - 1;

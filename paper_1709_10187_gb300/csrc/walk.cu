@@ -678,6 +678,15 @@ __device__ __forceinline__ void brick_base(const WalkParams& P, const unsigned i
     for (int a = 0; a < 3; ++a) base[a] = (((int)ic[a] + sh) / b) * b - sh + P.prop_m;
 }
 
+// A cell's inner-cube base and its local coordinates there (world frame).
+__device__ __forceinline__ void region_local(const WalkParams& P, unsigned cell, int base[3], int l[3]) {
+    unsigned ic[3];
+    cell_coords(P, cell, ic);
+    brick_base(P, ic, base);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) l[a] = min(max((int)ic[a] - base[a], 0), P.prop_r - 1);
+}
+
 __device__ __forceinline__ void fold_parked(const WalkParams& P, unsigned cell, int base[3], int C[3], int perm[3],
                                             bool flip[3]) {
     unsigned ic[3];
@@ -704,6 +713,16 @@ __global__ void propose_features_kernel(const WalkParams P, const float* __restr
     const unsigned long long pid = P.prop_qpid[q0 + r];
     const unsigned cell = min(P.st_cell[pid], (unsigned)P.ncell - 1u);
     unsigned j = min(P.st_bin[pid], (unsigned)P.J - 1u);
+    if (P.prop_sum) {
+        // region mode: world frame, the region's summary and the cell's own density
+        int base[3], l[3];
+        region_local(P, cell, base, l);
+        const float* sm = P.prop_sum + (size_t)brick_of(P, cell) * kRegionSum;
+        const unsigned cls = min(__ldg(&P.cell_class[cell]), (unsigned)P.n_class - 1u);
+        const float dlog = log10f((float)(P.cdesc[cls].k0 * P.dz[0])) - sm[0];
+        features_region(sm, P.prop_lp[j], xc[j], dlog, l, P.prop_r, fc, X + r * kFeat);
+        return;
+    }
     if (xc[j] < 0.0f) j = (unsigned)P.J - 1u - j;
     int base[3], C[3], perm[3];
     bool flip[3];
@@ -741,7 +760,8 @@ __global__ void propose_place_kernel(const WalkParams P, const float* __restrict
     const unsigned long long pid = P.prop_qpid[q0 + r];
     const unsigned cell = min(P.st_cell[pid], (unsigned)P.ncell - 1u);
     const unsigned bin = min(P.st_bin[pid], J - 1u);
-    const bool mirror = xc[bin] < 0.0f;
+    const bool region = P.prop_sum != nullptr;  // world frame: no fold, no mirror
+    const bool mirror = !region && xc[bin] < 0.0f;
     EventStream es;
     es.init(pid, P.st_e[pid], P.k0, P.k1);
     const unsigned long long e_start = es.e;
@@ -769,7 +789,13 @@ __global__ void propose_place_kernel(const WalkParams P, const float* __restrict
     }
     int base[3], C[3], perm[3];
     bool flip[3];
-    fold_parked(P, cell, base, C, perm, flip);
+    if (region) {
+        region_local(P, cell, base, C);
+        perm[0] = 0; perm[1] = 1; perm[2] = 2;
+        flip[0] = flip[1] = flip[2] = false;
+    } else {
+        fold_parked(P, cell, base, C, perm, flip);
+    }
     const int cax = fc_ >> 1, cside = fc_ & 1;
     int cc[3];
     cc[cax] = cside ? b - 1 : 0;
@@ -822,6 +848,120 @@ __global__ void propose_place_kernel(const WalkParams P, const float* __restrict
     atomicAdd(&T[C_EVENT_DRAWS], es.e - e_start);
 }
 
+// First passages out of the regions (brick inner cubes) of the grid's own
+// medium, for training the proposal on media that vary from cell to cell.
+// Sample i is packet p0 + i: event draws 0-2 pick the brick (from the listed
+// ones), the start cell of its region and the start bin (from the brick's
+// listed bins); the packet then takes the walk's transitions on the grid's
+// table (transition stream; Doppler rebins take the next event draws) until an
+// outcome would carry it out of the region.  That crossing is not made: the
+// sample records the face, the bin and the cell on the face it would leave
+// from (the proposal's placement makes the crossing).
+struct FpRegionParams {
+    const int32_t* bricks;
+    const int32_t* bin_off;
+    const int32_t* bins;
+    int n_el;
+    unsigned long long p0, n, cap;
+    int32_t* out;
+    unsigned long long* steps;
+    // training targets and features (null: records only)
+    __nv_bfloat16* X;
+    int32_t *tA, *tB, *tC;
+    const float* lp;
+    const float* xc;
+    FeatConst fc;
+};
+
+__global__ void __launch_bounds__(256) fp_region_kernel(const WalkParams P, const FpRegionParams F) {
+    const unsigned J = (unsigned)P.J, nr1 = (unsigned)P.n_rows - 1u;
+    const int r = P.prop_r, bl = P.prop_b;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < F.n; i += stride) {
+        const unsigned long long pid = F.p0 + i;
+        EventStream es;
+        es.init(pid, 0, P.k0, P.k1);
+        const unsigned w0 = es.next(), w1 = es.next(), w2 = es.next();
+        const int k = min((int)(((unsigned long long)w0 * (unsigned long long)F.n_el) >> 32), F.n_el - 1);
+        const int br = F.bricks[k];
+        const int bc[3] = {br % P.prop_nbx, (br / P.prop_nbx) % P.prop_nby, br / (P.prop_nbx * P.prop_nby)};
+        const int mc = (int)(((unsigned long long)w1 * (unsigned long long)(r * r * r)) >> 32);
+        int l[3] = {mc % r, (mc / r) % r, mc / (r * r)};
+        int base[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) base[a] = bc[a] * bl - P.prop_sh + P.prop_m;
+        const int cnt = F.bin_off[k + 1] - F.bin_off[k];
+        int j = F.bins[F.bin_off[k] + min((int)(((unsigned long long)w2 * (unsigned long long)cnt) >> 32), cnt - 1)];
+        const int j0 = j;
+        const int l0[3] = {l[0], l[1], l[2]};
+        const uint32_t pl = (uint32_t)pid, ph = (uint32_t)(pid >> 32);
+        int face = 6, pos = -1;
+        unsigned long long t = 0;
+        while (t < F.cap && face == 6) {
+            const unsigned long long blk = t >> 2;
+            const uint4 rw = philox_rk(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), pl, ph), P);
+            bool stop = false;
+            for (unsigned q = (unsigned)(t & 3u); q < 4u && t < F.cap; ++q) {
+                const unsigned w = word_of(rw, q);
+                ++t;
+                int wc[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) wc[a] = min(max(base[a] + l[a], 0), P.n[a] - 1);
+                const unsigned cell = (unsigned)wc[0] + (unsigned)P.n0 * (unsigned)wc[1] + (unsigned)P.n01 * (unsigned)wc[2];
+                const unsigned cls = min(__ldg(&P.cell_class[min(cell, (unsigned)P.ncell - 1u)]), (unsigned)P.n_class - 1u);
+                const unsigned sidx = min(cls * J + (unsigned)j, nr1);
+                const uint2 f = __ldg(&P.fast[sidx]);
+                if (w < f.y) { j += (w >= f.x) ? 1 : -1; continue; }
+                const uint4 a = __ldg(&P.rows[2u * sidx]), c = __ldg(&P.rows[2u * sidx + 1u]);
+                const unsigned o = (unsigned)(w >= a.x) + (unsigned)(w >= a.y) + (unsigned)(w >= a.z) +
+                                   (unsigned)(w >= c.x) + (unsigned)(w >= c.y) + (unsigned)(w >= c.z) +
+                                   (unsigned)(w >= c.w);
+                if (o < 2u) { j += o ? 1 : -1; continue; }
+                const int fc_ = (int)o - 2, ax = fc_ >> 1, side = (fc_ & 1) ? 1 : -1;
+                if (l[ax] + side < 0 || l[ax] + side >= r) {
+                    face = fc_;
+                    const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;  // the other two axes, lower first
+                    pos = l[u] + r * l[v];
+                    break;
+                }
+                const unsigned act = (a.w >> (2u * o)) & 3u;
+                if (act == ACT_ESCAPE || act == ACT_TO_MC) { stop = true; break; }  // not inside a region
+                if (act == ACT_REBIN) {
+                    const Rebin rb = P.rebin[cls * 6u + (unsigned)fc_];
+                    const unsigned wr = es.next();
+                    const int jn = j + rb.m + (wr >= rb.thr ? 1 : 0);
+                    j = jn < 0 ? 0 : (jn > (int)J - 1 ? (int)J - 1 : jn);
+                }
+                l[ax] += side;
+            }
+            if (stop) break;
+        }
+        int32_t* o8 = F.out + 8 * i;
+        o8[0] = br;
+        o8[1] = j0;
+        o8[2] = mc;
+        o8[3] = face;
+        o8[4] = j;
+        o8[5] = pos;
+        o8[6] = (int32_t)(es.e - 3ull);
+        o8[7] = 0;
+        F.steps[i] = t;
+        if (F.X) {
+            int wc0[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) wc0[a] = min(max(base[a] + l0[a], 0), P.n[a] - 1);
+            const unsigned c0 = (unsigned)wc0[0] + (unsigned)P.n0 * (unsigned)wc0[1] + (unsigned)P.n01 * (unsigned)wc0[2];
+            const unsigned cls0 = min(__ldg(&P.cell_class[min(c0, (unsigned)P.ncell - 1u)]), (unsigned)P.n_class - 1u);
+            const float* sm = P.prop_sum + (size_t)br * kRegionSum;
+            const float dlog = log10f((float)(P.cdesc[cls0].k0 * P.dz[0])) - sm[0];
+            features_region(sm, F.lp[j0], F.xc[j0], dlog, l0, r, F.fc, F.X + kFeat * i);
+            F.tA[i] = face < 6 ? face * (int)J + min(max(j, 0), (int)J - 1) : -1;
+            F.tB[i] = step_bucket(t);
+            if (F.tC) F.tC[i] = face < 6 ? face * r * r + pos : -1;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_scatter_samples(const rddmc_grid& g, const void* d_table, double x_in, uint64_t seed, uint64_t n,
@@ -864,13 +1004,15 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     }
     const uint64_t np = o.n_packets;
     uint64_t off = 256;
-    P.cursor = (unsigned long long*)sb;
-    P.st_cell = (uint32_t*)(sb + off); off += align256(np * 4);
-    P.st_bin = (uint32_t*)(sb + off); off += align256(np * 4);
-    P.st_t = (unsigned long long*)(sb + off); off += align256(np * 8);
-    P.st_e = (unsigned long long*)(sb + off); off += align256(np * 8);
-    P.st_status = (uint8_t*)(sb + off); off += align256(np * 1);
-    P.st_lw = (unsigned long long*)(sb + off);
+    if (sb) {  // the packet-state arrays (first-passage generation has none)
+        P.cursor = (unsigned long long*)sb;
+        P.st_cell = (uint32_t*)(sb + off); off += align256(np * 4);
+        P.st_bin = (uint32_t*)(sb + off); off += align256(np * 4);
+        P.st_t = (unsigned long long*)(sb + off); off += align256(np * 8);
+        P.st_e = (unsigned long long*)(sb + off); off += align256(np * 8);
+        P.st_status = (uint8_t*)(sb + off); off += align256(np * 1);
+        P.st_lw = (unsigned long long*)(sb + off);
+    }
     P.tally = w.d_tally;
     P.n_packets = np;
     P.max_steps = o.max_steps ? o.max_steps : (1ull << 62);
@@ -919,6 +1061,7 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
         P.prop_lhi = (float)pr->log_tau_hi;
         P.prop_qcount = pr->d_queue_count;
         P.prop_qpid = pr->d_queue_pid;
+        P.prop_sum = pr->d_summary;
         P.save_state = 1;
     }
 }
@@ -1009,5 +1152,64 @@ extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rdd
     if (cudaMemsetAsync(pr->d_queue_count, 0, 8, s) != cudaSuccess) return RDDMC_ERR_CUDA;
     if (n_served) *n_served = cnt;
     // no final synchronisation: work queued next on `stream` runs after these kernels
+    return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
+}
+
+extern "C" int rddmc_fp_region_generate(const rddmc_grid* g, const void* d_table, const rddmc_fp_region* reg,
+                                        uint64_t seed, uint64_t p0, uint64_t n, uint64_t cap, int32_t* d_out,
+                                        uint64_t* d_steps, const rddmc_fp_train* train, void* stream) {
+    using namespace rddmc;
+    if (!g || !d_table || !reg || !d_out || !d_steps || n == 0 || cap == 0) return RDDMC_ERR_ARG;
+    if (!g->precomputed) return RDDMC_ERR_TABLE;
+    if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty() || g->weighted())
+        return RDDMC_ERR_UNSUPPORTED;
+    if (reg->brick < 1 || reg->brick > 64 || reg->offset < 0 || reg->offset >= reg->brick) return RDDMC_ERR_ARG;
+    if (reg->margin < 0 || 2 * reg->margin >= reg->brick) return RDDMC_ERR_ARG;
+    if (reg->n_eligible < 1 || !reg->d_bricks || !reg->d_bin_off || !reg->d_bins || !reg->d_summary)
+        return RDDMC_ERR_ARG;
+    rddmc_proposal pr;
+    std::memset(&pr, 0, sizeof(pr));
+    pr.brick = reg->brick;
+    pr.offset = reg->offset;
+    pr.margin = reg->margin;
+    pr.d_summary = reg->d_summary;
+    WalkLaunch w;
+    std::memset(&w, 0, sizeof(w));
+    w.d_table = d_table;
+    w.opts.seed = seed;
+    w.opts.n_packets = 1;
+    w.opts.proposal = &pr;
+    WalkParams P;
+    fill_walk_params(*g, w, P);
+    FpRegionParams F;
+    std::memset(&F, 0, sizeof(F));
+    F.bricks = reg->d_bricks;
+    F.bin_off = reg->d_bin_off;
+    F.bins = reg->d_bins;
+    F.n_el = reg->n_eligible;
+    F.p0 = p0;
+    F.n = n;
+    F.cap = cap;
+    F.out = d_out;
+    F.steps = (unsigned long long*)d_steps;
+    if (train) {
+        if (!train->d_x || !train->d_ta || !train->d_tb || !train->d_lp || !train->d_xc) return RDDMC_ERR_ARG;
+        F.X = (__nv_bfloat16*)train->d_x;
+        F.tA = train->d_ta;
+        F.tB = train->d_tb;
+        F.tC = train->d_tc;
+        F.lp = train->d_lp;
+        F.xc = train->d_xc;
+        F.fc.log_b = log10f((float)(reg->brick - 2 * reg->margin));
+        F.fc.log_a = (float)log10(g->a);
+        F.fc.inv_xs = (float)(1.0 / std::max(std::fabs(g->edges.front()), std::fabs(g->edges.back())));
+    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RDDMC_ERR_CUDA;
+    const unsigned long long want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < (unsigned long long)nsm * 8 ? want : (unsigned long long)nsm * 8);
+    fp_region_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(P, F);
     return cudaGetLastError() == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
 }

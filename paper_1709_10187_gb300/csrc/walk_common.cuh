@@ -58,6 +58,9 @@ struct WalkParams {
     float prop_llo, prop_lhi;
     unsigned long long* prop_qcount;
     unsigned long long* prop_qpid;
+    // region mode (media that vary from cell to cell): kRegionSum floats per
+    // brick summarising its inner cube; null for uniform bricks (symmetry fold)
+    const float* prop_sum;
 };
 
 // Philox4x32-10 with precomputed round keys (held in the kernel's parameter bank).

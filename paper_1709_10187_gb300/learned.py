@@ -241,3 +241,171 @@ class ExitProposal:
         t = problem.read()
         t["launches"], t["rounds"], t["served"] = launches, rounds, served
         return t
+
+
+# ----------------------------------------------------------------------------- media that vary cell by cell
+F_MU = 0.5  # angle factor of the comoving shift across a face (eq. velocity-shift)
+
+
+def region_summaries(w: W.Workload, n_rel, v_kms, brick: int, margin: int, offset: int = 0):
+    """Per lattice brick (axis 0 fastest, partial bricks included) the 8
+    floats of rddmc_fp_region.d_summary for its inner cube (side brick - 2
+    margin), and whether the brick lies wholly inside the grid.  Host-side
+    description of the medium: no step of the walk."""
+    n = w.n[0]
+    assert w.ndim == 3 and w.n[1] == n and w.n[2] == n
+    nbx, cidx, sh = W.brick_lattice(n, brick, offset)
+    r = brick - 2 * margin
+    dz = 2.0 * w.R / n
+    vth = 12.85 * np.sqrt(w.T / 1.0e4)
+    lg = np.log10(np.asarray(n_rel, dtype=np.float64)).reshape(n, n, n)       # [i2, i1, i0]
+    v = (np.zeros((n, n, n, 3)) if v_kms is None else np.asarray(v_kms, dtype=np.float64).reshape(n, n, n, 3))
+    u = (2.0 * np.arange(r) + 1.0) / r - 1.0
+    out = np.zeros((nbx ** 3, 8), dtype=np.float32)
+    full = np.zeros(nbx ** 3, dtype=bool)
+    lk0 = np.log10(w.tau0 / w.R * dz)
+    for b2 in range(nbx):
+        for b1 in range(nbx):
+            for b0 in range(nbx):
+                bi = b0 + nbx * (b1 + nbx * b2)
+                lo = [bb * brick - sh for bb in (b0, b1, b2)]
+                if min(lo) < 0 or max(lo) + brick > n:
+                    continue
+                full[bi] = True
+                s = [slice(lo[a] + margin, lo[a] + margin + r) for a in (2, 1, 0)]  # [i2, i1, i0]
+                y = lg[s[0], s[1], s[2]]
+                mu = y.mean()
+                out[bi, 0] = lk0 + mu
+                out[bi, 1] = y.std()
+                dy = y - mu
+                den = (u * u).sum() * r * r
+                out[bi, 2] = (dy * u[None, None, :]).sum() / den   # axis 0 (x): last array index
+                out[bi, 3] = (dy * u[None, :, None]).sum() / den
+                out[bi, 4] = (dy * u[:, None, None]).sum() / den
+                vv = v[s[0], s[1], s[2]]
+                d = [F_MU * (vv[:, :, :-1, 0] - vv[:, :, 1:, 0]) / vth,
+                     F_MU * (vv[:, :-1, :, 1] - vv[:, 1:, :, 1]) / vth,
+                     F_MU * (vv[:-1, :, :, 2] - vv[1:, :, :, 2]) / vth]
+                d = np.concatenate([x.ravel() for x in d])
+                out[bi, 5] = d.mean() if d.size else 0.0
+                out[bi, 6] = np.sqrt((d * d).mean()) if d.size else 0.0
+    return out, full
+
+
+class RegionProposal(ExitProposal):
+    """The learned exit proposal for a medium that varies from cell to cell.
+
+    Regions are the inner cubes (side r = brick - 2 margin) of a brick lattice
+    over the target grid.  First passages are generated on the target's own
+    table (rddmc_fp_region_generate: the walk's transitions, Doppler rebins
+    included), and the network is conditioned on a summary of the region
+    (its mean density and spread, density slopes, mean and rms Doppler shift
+    per crossing), the start cell's density, position and bin, in the world
+    frame.  The proposal is an approximation of the region's exact exit law;
+    the plain walk judges its escape spectrum."""
+
+    def __init__(self, problem, n_rel, v_kms, brick: int, margin: int, offset: int = 0, tau_lo=5.0, tau_hi=1.0e12,
+                 hidden_seed=0x5EED0611):
+        import torch
+        self.torch = torch
+        self.device = problem.device
+        self.problem = problem
+        w = problem.w
+        self.target = w
+        self.J = w.J
+        self.lattice, self.margin, self.offset = int(brick), int(margin), int(offset)
+        self.b = self.lattice - 2 * self.margin           # the region's side
+        self.dz = 2.0 * w.R / w.n[0]
+        self.tau_lo, self.tau_hi = float(tau_lo), float(tau_hi)
+        summ, full = region_summaries(w, n_rel, v_kms, self.lattice, self.margin, self.offset)
+        self.summary_np, self.full = summ, full
+        # log10 of the bin-mean profile phi_j from the target's own rows (any cell)
+        tau = R.cell_tau(problem.grid, problem.table.data_ptr(), 0, self.J, problem.stream()).astype(np.float64)
+        nrel0 = float(np.asarray(n_rel).reshape(-1)[0])
+        lp = (np.log10(np.maximum(tau, 1e-300)) - np.log10(w.tau0 / w.R * nrel0 * self.dz)).astype(np.float32)
+        # eligible states, decided in FP32 exactly as the walk decides them
+        llo, lhi = np.float32(np.log10(self.tau_lo)), np.float32(np.log10(self.tau_hi))
+        bricks, off, bins = [], [0], []
+        for bi in np.nonzero(full)[0]:
+            l = np.float32(summ[bi, 0]) + lp
+            ok = np.nonzero((l >= llo) & (l <= lhi))[0]
+            if ok.size:
+                bricks.append(int(bi))
+                bins.extend(int(j) for j in ok)
+                off.append(len(bins))
+        if not bricks:
+            raise ValueError("no brick has bins in the requested optical-depth range")
+        lk = np.full(len(full), -1.0e30, dtype=np.float32)
+        lk[bricks] = summ[bricks, 0]
+        t = lambda a, dt: torch.as_tensor(np.asarray(a), dtype=dt, device=self.device)
+        self.bricks = t(np.array(bricks, np.int32), torch.int32)
+        self.bin_off = t(np.array(off, np.int32), torch.int32)
+        self.bins = t(np.array(bins, np.int32), torch.int32)
+        self.summary = t(summ.reshape(-1), torch.float32)
+        self.brick_lk = t(lk, torch.float32)
+        self.lp = t(lp, torch.float32)
+        self.lk = t(np.zeros(1, np.float32), torch.float32)  # unused in region mode
+        self.xc = t((0.5 * (w.edges()[1:] + w.edges()[:-1])).astype(np.float32), torch.float32)
+        self.levels = []
+        self.nA = 6 * self.J
+        self.nB = N_STEP_BUCKETS
+        self.S = self.b * self.b
+        self.nC = 6 * self.S
+        self.n_out = ((self.nA + self.nB + self.nC + 15) // 16) * 16
+        n_par = R.mlp_param_count(self.n_out)
+        rng = np.random.default_rng(hidden_seed)
+        flat = []
+        for (o, i) in [(128, 16), (128, 128), (128, 128), (self.n_out, 128)]:
+            flat.append(rng.normal(0.0, np.sqrt(2.0 / i), o * i))   # He initialisation
+            flat.append(np.zeros(o))
+        flat = np.concatenate(flat).astype(np.float32)
+        assert flat.size == n_par
+        self.wf = t(flat, torch.float32)
+        self.wb = torch.empty(n_par, dtype=torch.bfloat16, device=self.device)
+        R.mlp_to_bf16(self.n_out, self.wf.data_ptr(), self.wb.data_ptr(), self.stream())
+        self.m = torch.zeros_like(self.wf)
+        self.v = torch.zeros_like(self.wf)
+        self.grad = torch.zeros_like(self.wf)
+        self.step = 0
+
+    def region_struct(self):
+        return R.FpRegion(self.lattice, self.offset, self.margin, int(self.bricks.numel()), self.bricks.data_ptr(),
+                          self.bin_off.data_ptr(), self.bins.data_ptr(), self.summary.data_ptr())
+
+    def generate(self, n: int, seed: int, p0: int = 0, cap: int = 10_000_000) -> dict:
+        """n first passages out of the target's regions with network inputs and targets (device tensors)."""
+        torch = self.torch
+        out = torch.empty(8 * n, dtype=torch.int32, device=self.device)
+        steps = torch.empty(n, dtype=torch.int64, device=self.device)
+        X = torch.empty((n, 16), dtype=torch.bfloat16, device=self.device)
+        tA = torch.empty(n, dtype=torch.int32, device=self.device)
+        tB = torch.empty(n, dtype=torch.int32, device=self.device)
+        tC = torch.empty(n, dtype=torch.int32, device=self.device)
+        tr = R.FpTrain(X.data_ptr(), tA.data_ptr(), tB.data_ptr(), self.lk.data_ptr(), self.lp.data_ptr(),
+                       self.xc.data_ptr(), tC.data_ptr())
+        R.fp_region_generate(self.problem.grid, self.problem.table.data_ptr(), self.region_struct(), seed, p0, n, cap,
+                             out.data_ptr(), steps.data_ptr(), tr, self.stream())
+        return dict(X=X, tA=tA, tB=tB, tC=tC, rec=out.view(n, 8), steps=steps)
+
+    def attach(self, problem, brick_rho=None, offset: int = 0, batch: int = 4096, margin: int = 0,
+               exclude_surface: bool = False):
+        """Proposal state for walking the target (the lattice and margin are the
+        proposal's own; brick_rho, offset and margin arguments are ignored)."""
+        torch = self.torch
+        return dict(
+            lk=self.brick_lk, count=torch.zeros(1, dtype=torch.int64, device=self.device),
+            offset=self.offset, lattice=self.lattice, margin=self.margin, batch=batch,
+            work=torch.empty(R.mlp_work_bytes(batch, self.n_out) + 256 + batch * 32 + 256 + batch * self.n_out * 4
+                             + 4096, dtype=torch.uint8, device=self.device))
+
+    def proposal(self, att, qpid, tau_lo: float, tau_hi: float):
+        return R.Proposal(att["lattice"], att["offset"], att["lk"].data_ptr(), self.lp.data_ptr(), self.xc.data_ptr(),
+                          np.log10(tau_lo), np.log10(tau_hi), att["count"].data_ptr(), qpid.data_ptr(),
+                          int(att["lk"].numel()), att["margin"], self.summary.data_ptr())
+
+    def run(self, problem=None, brick_rho=None, n_packets: int = 0, seed: int = 0, **kw) -> dict:
+        """Walk n_packets on the target with proposals (see ExitProposal.run);
+        the eligibility band is the proposal's own tau_lo, tau_hi."""
+        kw.setdefault("tau_lo", self.tau_lo)
+        kw.setdefault("tau_hi", self.tau_hi)
+        return ExitProposal.run(self, self.problem if problem is None else problem, None, n_packets, seed, **kw)

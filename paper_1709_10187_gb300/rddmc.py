@@ -34,6 +34,7 @@ EXPORTED = ["rddmc_build_grid", "rddmc_destroy_grid", "rddmc_grid_sizes", "rddmc
             "rddmc_batch_create", "rddmc_batch_destroy", "rddmc_batch_sizes", "rddmc_batch_upload",
             "rddmc_batch_launch", "rddmc_batch_read_tallies", "rddmc_batch_graph_create", "rddmc_batch_graph_launch",
             "rddmc_batch_graph_destroy", "rddmc_batch_autotune", "rddmc_cell_tau", "rddmc_fp_generate",
+            "rddmc_fp_region_generate",
             "rddmc_mlp_param_count", "rddmc_mlp_work_bytes", "rddmc_mlp_to_bf16", "rddmc_mlp_forward",
             "rddmc_mlp_loss_grad", "rddmc_mlp_adam", "rddmc_mlp_status", "rddmc_propose", "rddmc_time_state_bytes",
             "rddmc_time_step_launch", "rddmc_redistribution_bytes", "rddmc_precompute_redistribution",
@@ -88,7 +89,13 @@ class Proposal(ctypes.Structure):
     _fields_ = [("brick", ctypes.c_int32), ("offset", ctypes.c_int32), ("d_brick_lk", ctypes.c_void_p),
                 ("d_lp", ctypes.c_void_p), ("d_xc", ctypes.c_void_p), ("log_tau_lo", ctypes.c_double),
                 ("log_tau_hi", ctypes.c_double), ("d_queue_count", ctypes.c_void_p), ("d_queue_pid", ctypes.c_void_p),
-                ("n_bricks", ctypes.c_int32), ("margin", ctypes.c_int32)]
+                ("n_bricks", ctypes.c_int32), ("margin", ctypes.c_int32), ("d_summary", ctypes.c_void_p)]
+
+
+class FpRegion(ctypes.Structure):
+    _fields_ = [("brick", ctypes.c_int32), ("offset", ctypes.c_int32), ("margin", ctypes.c_int32),
+                ("n_eligible", ctypes.c_int32), ("d_bricks", ctypes.c_void_p), ("d_bin_off", ctypes.c_void_p),
+                ("d_bins", ctypes.c_void_p), ("d_summary", ctypes.c_void_p)]
 
 
 class TimeStep(ctypes.Structure):
@@ -132,6 +139,8 @@ def lib():
         L.rddmc_cell_tau.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
         L.rddmc_fp_generate.argtypes = [vp, vp, i32, i32, vp, vp, u64, u64, u64, u64, vp, vp,
                                         ctypes.POINTER(FpTrain), vp]
+        L.rddmc_fp_region_generate.argtypes = [vp, vp, ctypes.POINTER(FpRegion), u64, u64, u64, u64, vp, vp,
+                                                ctypes.POINTER(FpTrain), vp]
         L.rddmc_propose.argtypes = [vp, vp, ctypes.POINTER(Proposal), u64, u64, vp, vp, i32, i32, i32, i32, vp, vp, i32,
                                     vp, ctypes.POINTER(ctypes.c_uint64), vp]
         L.rddmc_mlp_param_count.argtypes = [i32]
@@ -582,6 +591,15 @@ def fp_generate(grids, d_tables, b, jlo, jhi, seed, p0, n, cap, d_out, d_steps, 
     _check("rddmc_fp_generate", lib().rddmc_fp_generate(
         g, t, int(L), int(b), _np_ptr(lo), _np_ptr(hi), int(seed), int(p0), int(n), int(cap), ctypes.c_void_p(d_out),
         ctypes.c_void_p(d_steps), ctypes.byref(train) if train is not None else None, ctypes.c_void_p(stream)))
+
+
+def fp_region_generate(grid, d_table: int, region: FpRegion, seed: int, p0: int, n: int, cap: int, d_out: int,
+                       d_steps: int, train: Optional[FpTrain] = None, stream: int = 0):
+    """rddmc_fp_region_generate: first passages out of regions of the grid's own medium."""
+    _check("rddmc_fp_region_generate", lib().rddmc_fp_region_generate(
+        ctypes.c_void_p(grid), ctypes.c_void_p(d_table), ctypes.byref(region), int(seed), int(p0), int(n), int(cap),
+        ctypes.c_void_p(d_out), ctypes.c_void_p(d_steps), ctypes.byref(train) if train is not None else None,
+        ctypes.c_void_p(stream)))
 
 
 def mlp_param_count(n_out: int) -> int:

@@ -1,0 +1,34 @@
+"""Host logic of the benchmark's learned-against-plain protocol, on synthetic
+multinomial spectra whose bias and noise are known."""
+import numpy as np
+
+import bench
+
+
+def _spectra(p, npk, runs, rng, sec):
+    return [(sec, rng.multinomial(npk, p).astype(np.float64)) for _ in range(runs)]
+
+
+def test_equal_l1_recovers_bias_floor_and_time_ratio():
+    rng = np.random.default_rng(1)
+    x = np.linspace(-6, 6, 60)
+    p = np.exp(-0.5 * x * x)
+    p /= p.sum()
+    npk, n_ref = 20_000, 4_000_000
+    ref = rng.multinomial(n_ref, p)
+    # unbiased arms: the "learned" one is twice as fast per packet
+    runs_p = _spectra(p, npk, 8, rng, 2.0)
+    runs_l = _spectra(p, npk, 8, rng, 1.0)
+    r = bench._equal_l1(runs_l, runs_p, ref, n_ref, npk, n_boot=50)
+    assert r["bias_floor_plain"]["value"] < 0.01 and r["bias_floor_learned"]["value"] < 0.01
+    assert 1.3 < r["speedup_at_0.02"]["value"] < 3.2, r["speedup_at_0.02"]
+    assert len(r["curve_learned"]["l1"]) == 8 and r["curve_learned"]["l1"][-1] < r["curve_learned"]["l1"][0]
+    # a biased learned arm: L1 distance 0.03 from the truth; the floor shows, and
+    # the 1 % target is out of its reach
+    q = p * (1.0 + 0.3 * np.sin(x))
+    q /= q.sum()
+    b = float(np.abs(q - p).sum())
+    runs_b = _spectra(q, npk, 8, rng, 1.0)
+    r = bench._equal_l1(runs_b, runs_p, ref, n_ref, npk, n_boot=50)
+    assert abs(r["bias_floor_learned"]["value"] - b) < 0.35 * b, (r["bias_floor_learned"], b)
+    assert r["speedup_at_0.01"]["value"] == 0.0 or b < 0.01
