@@ -468,24 +468,29 @@ def _complete(R, torch, w, npk):
             "transitions_per_packet": t["steps"] / npk}
 
 
-def _batched(R, torch, packet_scale=0.01, max_steps=1_000_000):
+def _batched(R, torch, packet_scale=0.01, max_steps=0, trial_packets=600_000):
     """The batched workload: 512 slab/sphere instances in one persistent launch,
-    schedule picked by the autotuner, replayed from a captured CUDA graph."""
+    schedule picked by the autotuner, replayed from a captured CUDA graph.
+    max_steps = 0: no watchdog, every packet is walked to escape.  The
+    autotuner's trial takes a GPU-filling share of every instance's packets
+    (about trial_packets in all), each for at most 65536 transitions: the
+    schedules' throughput on the run's own instances."""
     ws = W.batched_instances(512, packet_scale=packet_scale)
     npk = [w.packets for w in ws]
     t0 = time.perf_counter()
     probs = [R.Problem(w) for w in ws]
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
-    b = R.Batch(probs, npk, trial_fraction=0.02)
+    b = R.Batch(probs, npk, trial_fraction=min(1.0, trial_packets / float(sum(npk))))
     base = R.RunOpts(0xBA7C4, 0, max_steps, 0, 0, 0, 0, 0, 0, 0)
+    t0 = time.perf_counter()
     best, trial_rate = b.autotune(base)
+    t_tune = time.perf_counter() - t0
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
         ge = b.graph(best)
         try:
-            b.graph_launch(ge)  # warm-up replay
             b.tally.zero_()
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -502,12 +507,12 @@ def _batched(R, torch, packet_scale=0.01, max_steps=1_000_000):
         finally:
             R.Batch.graph_destroy(ge)
     torch.cuda.current_stream().wait_stream(side)
-    return {"instances": len(ws), "packets": int(sum(npk)), "max_steps": max_steps,
+    return {"instances": len(ws), "packets": int(sum(npk)), "packet_scale": packet_scale, "max_steps": max_steps,
             "transitions_per_s": tot["steps"] / dt, "escaped_per_s": tot["escaped"] / dt,
-            "escaped": tot["escaped"], "aborted": tot["aborted"], "ms": dt * 1e3,
+            "escaped": tot["escaped"], "aborted": tot["aborted"], "transitions": tot["steps"], "ms": dt * 1e3,
             "schedule": {"threads_per_cta": best.threads_per_cta, "ctas_per_sm": best.ctas_per_sm,
                          "chunk": best.chunk},
-            "autotune_trial_transitions_per_s": trial_rate, "setup_s": t_setup}
+            "autotune_trial_transitions_per_s": trial_rate, "autotune_s": t_tune, "setup_s": t_setup}
 
 
 def _l1(a, b):
@@ -516,14 +521,55 @@ def _l1(a, b):
     return float(np.abs(a / a.sum() - b / b.sum()).sum())
 
 
-def _learned_vs_plain(R, torch, n=64, brick=16, margin=1, J=64, x_max=64.0, tau0=1.0e7, npk=400_000,
-                      ndata=1_500_000, iters=4000):
-    """Escape spectrum of the clumpy 3D medium by the plain walk and by the walk
-    with the learned exit proposal (trained here on first passages the plain
-    walk generates), each compared with an independent plain reference of 4x
-    the packets; then plain at the packet count that gives the learned run's
-    L1, so both are timed at equal escape-spectrum error."""
+def _arms(torch, learned_run, plain_run, npk, runs, n_ref, seed0):
+    """`runs` independent runs of npk packets per arm (learned_run(n, seed) and
+    plain_run(n, seed) return the walk's tallies), timed with a device
+    synchronisation on both sides, and an independent plain reference of n_ref
+    packets from its own seeds."""
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+
+    learned_run(2000, seed0 - 1)  # warm-up
+    plain_run(2000, seed0 - 1)
+    runs_l, runs_p, stats = [], [], {"learned_transitions": 0, "learned_proposals": 0, "learned_launches": 0,
+                                     "plain_transitions": 0, "aborted": 0}
+    for i in range(runs):
+        s, r = timed(lambda: learned_run(npk, seed0 + i))
+        runs_l.append((s, r["hist"]))
+        stats["learned_transitions"] += r["steps"]
+        stats["learned_proposals"] += r["proposals"]
+        stats["learned_launches"] += r["launches"]
+        stats["aborted"] += r["aborted"]
+        s, r = timed(lambda: plain_run(npk, seed0 + 0x100 + i))
+        runs_p.append((s, r["hist"]))
+        stats["plain_transitions"] += r["steps"]
+        stats["aborted"] += r["aborted"]
+    ref, t_ref, chunk = None, 0.0, 1_000_000
+    for k in range(0, n_ref, chunk):
+        s, r = timed(lambda: plain_run(min(chunk, n_ref - k), seed0 + 0x200 + k // chunk))
+        ref = r["hist"].astype(np.float64) if ref is None else ref + r["hist"]
+        t_ref += s
+    out = {"reference_s": t_ref, "learned_transitions_per_packet": stats["learned_transitions"] / (runs * npk),
+           "learned_proposals_per_packet": stats["learned_proposals"] / (runs * npk),
+           "learned_launches_per_run": stats["learned_launches"] / runs,
+           "plain_transitions_per_packet": stats["plain_transitions"] / (runs * npk), "aborted": stats["aborted"],
+           "equal_l1": _equal_l1(runs_l, runs_p, ref, n_ref, npk)}
+    return out
+
+
+def _learned_bricks(R, torch, n=64, brick=16, margin=1, J=64, x_max=64.0, tau0=1.0e7, npk=400_000, runs=4,
+                    n_ref=6_400_000, ndata=1_500_000, iters=4000, time_slice_us=1000):
+    """The exact uniform-brick proposal on the clumpy medium drawn per brick
+    (the "clumpy bricks" variant: density and velocity constant inside each
+    16^3-cell brick, so a brick's inner cube is a uniform medium whose first
+    passages the network learns from uniform cubes), against the plain walk
+    at equal escape-spectrum L1 (_arms, _equal_l1)."""
     from paper_1709_10187_gb300 import learned as Lr
+    out = {"workload": f"clumpy_bricks_{n}c_{J}b_brick{brick}_tau{tau0:.0e}", "tau0": tau0}
     med = W.clumpy_medium(n=n, J=J, x_max=x_max, tau0=tau0, brick=brick, packets=npk)
     prob = R.Problem.clumpy(med)
     rho = med.brick_rho
@@ -532,39 +578,19 @@ def _learned_vs_plain(R, torch, n=64, brick=16, margin=1, J=64, x_max=64.0, tau0
     prop = Lr.ExitProposal(med.workload, brick - 2 * margin, levels, tau_lo=5.0, tau_hi=1.0e12)
     data = prop.generate(ndata, seed=11, cap=50_000_000)
     torch.cuda.synchronize()
-    t_data = time.perf_counter() - t0
+    out["data_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     prop.train(data, iters=iters, batch=8192, lr=2e-3)
     torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    out["train_s"] = time.perf_counter() - t0
     del data
-    seed = 0xC0FFEE
-    kw = dict(margin=margin, tau_lo=5.0, tau_hi=1.0e12)
-    prop.run(prob, rho, 2000, seed + 7, **kw)  # warm-up
-    prob.run(2000, seed + 7)
-
-    def timed(fn):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        out = fn()
-        torch.cuda.synchronize()
-        return time.perf_counter() - t, out
-
-    t_l, lr = timed(lambda: prop.run(prob, rho, npk, seed, **kw))
-    t_p, pl = timed(lambda: prob.run(npk, seed))
-    ref = prob.run(4 * npk, seed + 1)
-    l1_l, l1_p = _l1(lr["hist"], ref["hist"]), _l1(pl["hist"], ref["hist"])
-    # plain at the learned run's L1 (L1 ~ N^-1/2 while noise dominates)
-    n_eq = int(min(4 * npk, max(npk // 16, npk * (l1_p / max(l1_l, 1e-12)) ** 2)))
-    t_e, pe = timed(lambda: prob.run(n_eq, seed + 2))
-    return {"workload": f"clumpy_{n}c_{J}b_brick{brick}_tau{tau0:.0e}", "packets": npk,
-            "proposal_region": brick - 2 * margin, "levels": len(prop.levels),
-            "train_samples": ndata, "train_iters": iters, "data_s": t_data, "train_s": t_train,
-            "learned": {"s": t_l, "l1": l1_l, "transitions_per_packet": lr["steps"] / npk,
-                        "proposals_per_packet": lr["proposals"] / npk, "launches": lr["launches"]},
-            "plain": {"s": t_p, "l1": l1_p, "transitions_per_packet": pl["steps"] / npk},
-            "plain_at_equal_l1": {"packets": n_eq, "s": t_e, "l1": _l1(pe["hist"], ref["hist"])},
-            "speedup_at_equal_l1": t_e / t_l, "reference_packets": 4 * npk}
+    out.update(train_samples=ndata, train_iters=iters, region=brick - 2 * margin, levels=len(prop.levels),
+               time_slice_us=time_slice_us)
+    kw = dict(margin=margin, tau_lo=5.0, tau_hi=1.0e12, time_slice_us=time_slice_us)
+    out.update(_arms(torch, lambda n_, s_: prop.run(prob, rho, n_, s_, **kw), lambda n_, s_: prob.run(n_, s_),
+                     npk, runs, n_ref, 0xB0000))
+    prob.close()
+    return out
 
 
 def _equal_l1(runs_l, runs_p, ref_hist, n_ref, npk, targets=(0.02, 0.01), n_boot=200, seed=0x5EED0B00):
@@ -638,14 +664,15 @@ def _equal_l1(runs_l, runs_p, ref_hist, n_ref, npk, targets=(0.02, 0.01), n_boot
 
 
 def _learned_c5(R, torch, tau0=1.0e7, npk=100_000, runs=8, n_ref=10_000_000, ndata=4_000_000, iters=4000,
-                brick=16, margin=1, n=128, J=256, x_max=256.0):
+                brick=16, margin=1, n=128, J=256, x_max=256.0, time_slice_us=1000):
     """The learned proposal on the clumpy workload at cell resolution (128^3
     cells x 256 bins over [-256, 256], lognormal density sigma_ln = 1 with
     spectral slope -11/3, turbulent velocity 10 km/s per component, tau0 at
-    the mean density): region proposals over 16^3-cell bricks (14^3 inner
-    cubes) trained on first passages the plain walk takes through the medium's
-    own regions, then `runs` independent runs of npk packets per arm against a
-    plain reference of n_ref packets (_equal_l1)."""
+    the mean density): region proposals over bricks of `brick` cells (inner
+    cubes of brick - 2 margin) trained on first passages the plain walk takes
+    through the medium's own regions, then `runs` independent runs of npk
+    packets per arm against a plain reference of n_ref packets (_arms,
+    _equal_l1)."""
     from paper_1709_10187_gb300 import learned as Lr
     out = {"workload": f"clumpy_cells_{n}c_{J}b_tau{tau0:.0e}", "tau0": tau0}
 
@@ -665,32 +692,11 @@ def _learned_c5(R, torch, tau0=1.0e7, npk=100_000, runs=8, n_ref=10_000_000, nda
     held = prop.generate(65536, seed=12, p0=1 << 40)
     out["train_s"], _ = timed(lambda: prop.train(data, iters=iters, batch=8192, lr=2e-3))
     out["heldout_loss"] = prop.mean_loss(held)
-    out.update(train_samples=ndata, train_iters=iters, region=brick - 2 * margin, n_out=prop.n_out)
+    out.update(train_samples=ndata, train_iters=iters, region=brick - 2 * margin, n_out=prop.n_out,
+               time_slice_us=time_slice_us)
     del data, held
-    prop.run(n_packets=2000, seed=1)  # warm-up
-    prob.run(2000, 1)
-    runs_l, runs_p, lt, pt = [], [], [], []
-    for i in range(runs):
-        s, r = timed(lambda: prop.run(n_packets=npk, seed=0xC5000 + i))
-        runs_l.append((s, r["hist"]))
-        lt.append((r["steps"] / npk, r["proposals"] / npk, r["launches"], r["aborted"]))
-        s, r = timed(lambda: prob.run(npk, 0xC5100 + i))
-        runs_p.append((s, r["hist"]))
-        pt.append((r["steps"] / npk, r["aborted"]))
-    ref = np.zeros(J + 2)
-    t_ref = 0.0
-    chunk = 1_000_000
-    for k in range(0, n_ref, chunk):
-        s, r = timed(lambda: prob.run(min(chunk, n_ref - k), 0xC5200 + k // chunk))
-        ref += r["hist"]
-        t_ref += s
-    out["reference_s"] = t_ref
-    out["learned_transitions_per_packet"] = float(np.mean([x[0] for x in lt]))
-    out["learned_proposals_per_packet"] = float(np.mean([x[1] for x in lt]))
-    out["learned_launches_per_run"] = float(np.mean([x[2] for x in lt]))
-    out["plain_transitions_per_packet"] = float(np.mean([x[0] for x in pt]))
-    out["aborted"] = int(sum(x[3] for x in lt) + sum(x[1] for x in pt))
-    out["equal_l1"] = _equal_l1(runs_l, runs_p, ref, n_ref, npk)
+    out.update(_arms(torch, lambda n_, s_: prop.run(n_packets=n_, seed=s_, time_slice_us=time_slice_us),
+                     lambda n_, s_: prob.run(n_, s_), npk, runs, n_ref, 0xC5000))
     prob.close()
     return out
 
@@ -820,21 +826,22 @@ def _extras(R, torch, only=None):
             ("batched_512", lambda: _batched(R, torch)),
             ("time_grey_paper", lambda: _time_grey(R, torch)),
             ("time_slab_atau1e9_paper", lambda: _time_p2(R, torch)),
-            ("learned_vs_plain", lambda: _learned_vs_plain(R, torch))]
+            ("learned_bricks", lambda: _learned_bricks(R, torch)),
+            ("learned_c5", lambda: _learned_c5(R, torch, tau0=1.0e7, npk=400_000, runs=4, n_ref=6_400_000,
+                                               time_slice_us=2000))]
     if only:
-        small = {"learned_small": lambda: _learned_vs_plain(R, torch, n=32, brick=8, tau0=1.0e6, npk=100_000,
-                                                            ndata=300_000, iters=300),
-                 # the clumpy workload's grid and frequency grid: 128^3 cells x 256 bins over [-256, 256]
-                 "learned_c5": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0, tau0=1.0e7,
-                                                         npk=200_000, ndata=1_500_000, iters=4000),
-                 # a C2 subset run to completion: bounded below by its slowest packet (~3e9 transitions)
-                 "c2_complete_1e5": lambda: _complete(R, torch, W.C2, 100_000),
+        small = {"learned_small": lambda: _learned_bricks(R, torch, n=32, brick=8, tau0=1.0e6, npk=100_000,
+                                                          n_ref=1_600_000, ndata=300_000, iters=300),
+                 "learned_c5_tau1e8": lambda: _learned_c5(R, torch, tau0=1.0e8, npk=50_000, runs=4, n_ref=800_000,
+                                                          ndata=2_000_000, time_slice_us=2000),
+                 "learned_c5_tau1e9": lambda: _learned_c5(R, torch, tau0=1.0e9, npk=5_000, runs=4, n_ref=80_000,
+                                                          ndata=500_000, time_slice_us=2000),
+                 # the batched workload at its full size (1.1e8 packets, ~7.8e14 transitions: ~30 min)
+                 "batched_512_full": lambda: _batched(R, torch, packet_scale=1.0),
+                 # a 1e5-packet subset of the tau0 = 1e7 slab walked to escape (~5 min)
+                 "c2_complete_1e5": lambda: _complete_sliced(R, torch, W.C2, 100_000),
                  # a short time-dependent run for profiling: 1e6 packets, 16 steps
-                 "time_slab_small": lambda: _time_p2(R, torch, npk=1_000_000, t_frac=0.016),
-                 "learned_c5_tau1e8": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0,
-                                                                tau0=1.0e8, npk=100_000, ndata=600_000, iters=4000),
-                 "learned_c5_tau1e9": lambda: _learned_vs_plain(R, torch, n=128, brick=16, J=256, x_max=256.0,
-                                                                tau0=1.0e9, npk=20_000, ndata=300_000, iters=3000)}
+                 "time_slab_small": lambda: _time_p2(R, torch, npk=1_000_000, t_frac=0.016)}
         jobs = [(k, f) for k, f in jobs + list(small.items()) if k == only]
         if not jobs:
             raise SystemExit(f"unknown extra {only!r}")
@@ -875,7 +882,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads and the learned-vs-plain comparison")
     ap.add_argument("--extra", default="", help="run only this extra (c3_sphere_static, c3_sphere_v20, "
-                    "c3_sphere_v200, c2_hybrid, c1_complete, c2_widecore_complete, c2_complete_1e5, batched_512, learned_vs_plain, learned_small, learned_c5, learned_c5_tau1e8, learned_c5_tau1e9) and print it")
+                    "c3_sphere_v200, c2_hybrid, c2_hybrid_grouped, c1_complete, c2_widecore_complete, batched_512, "
+                    "time_grey_paper, time_slab_atau1e9_paper, learned_bricks, learned_c5; opt-in only: "
+                    "learned_small, learned_c5_tau1e8, learned_c5_tau1e9, batched_512_full, c2_complete_1e5, "
+                    "time_slab_small) and print it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -517,7 +517,10 @@ void rddmc_batch_graph_destroy(void* graph_exec);
  * (threads_per_cta 128 or 256, ctas_per_sm at full or one-less occupancy,
  * chunk 64, 256 or 1024), timed with CUDA events, and return the one with the
  * most transitions per second in *best (and the rate in *best_rate, may be
- * NULL).  Synchronises `stream` and overwrites d_tallies. */
+ * NULL).  Each trial packet walks at most 65536 transitions (or
+ * base->max_steps if lower): the trial measures throughput on the run's own
+ * instances, so choose a trial_fraction that fills the GPU.  *best keeps
+ * base->max_steps.  Synchronises `stream` and overwrites d_tallies. */
 int rddmc_batch_autotune(const rddmc_batch* batch, const void* d_desc, const rddmc_run_opts* base, void* d_scratch,
                          size_t scratch_bytes, void* d_tallies, size_t tally_bytes, void* stream,
                          rddmc_run_opts* best, double* best_rate);

@@ -227,21 +227,29 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const BatchParams P) {
                 ++blk;
                 rn = bphilox(make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), pl, ph), P);
                 unsigned q;
-#define RDDMC_BFAST(W, Q)                                \
-    {                                                    \
-        const uint2 f_ = __ldg(&fast[min(s, nr1)]);      \
-        if ((W) < f_.y) {                                \
-            s += ((W) >= f_.x) ? 1u : 0xffffffffu;       \
-        } else {                                         \
-            q = (Q);                                     \
-            goto slow;                                   \
-        }                                                \
-    }
-                RDDMC_BFAST(r.x, 0u)
-                RDDMC_BFAST(r.y, 1u)
-                RDDMC_BFAST(r.z, 2u)
-                RDDMC_BFAST(r.w, 3u)
-#undef RDDMC_BFAST
+                {
+                    // four transitions as one branch-free chain of head loads
+                    // (clamped speculative states), checked at its end, as in
+                    // the single-grid walk
+                    const unsigned s0 = s;
+                    const uint2 f0 = __ldg(&fast[min(s0, nr1)]);
+                    const unsigned s1 = s0 + ((r.x >= f0.x) ? 1u : 0xffffffffu);
+                    const uint2 f1 = __ldg(&fast[min(s1, nr1)]);
+                    const unsigned s2 = s1 + ((r.y >= f1.x) ? 1u : 0xffffffffu);
+                    const uint2 f2 = __ldg(&fast[min(s2, nr1)]);
+                    const unsigned s3 = s2 + ((r.z >= f2.x) ? 1u : 0xffffffffu);
+                    const uint2 f3 = __ldg(&fast[min(s3, nr1)]);
+                    const unsigned s4 = s3 + ((r.w >= f3.x) ? 1u : 0xffffffffu);
+                    const bool ok0 = r.x < f0.y, ok1 = r.y < f1.y, ok2 = r.z < f2.y, ok3 = r.w < f3.y;
+                    if (ok0 && ok1 && ok2 && ok3) {
+                        s = s4;
+                        ++g;
+                        continue;
+                    }
+                    q = !ok0 ? 0u : (!ok1 ? 1u : (!ok2 ? 2u : 3u));
+                    s = !ok0 ? s0 : (!ok1 ? s1 : (!ok2 ? s2 : s3));
+                    goto slow;
+                }
                 ++g;
                 continue;
             slow:
@@ -499,7 +507,13 @@ void rddmc_batch_graph_destroy(void* graph_exec) {
 
 // Time every candidate schedule on the trial subset (trial_fraction of each
 // instance's packets, set by rddmc_batch_upload) with CUDA events and return
-// the one with the highest transitions/s in *best.  Clobbers d_tallies.
+// the one with the highest transitions/s in *best.  A trial walks each of its
+// packets for at most kTrialSteps transitions (or base->max_steps if lower):
+// it measures the schedule's throughput on the run's own instances while the
+// GPU is full, not the time to the last escape, so a run without a watchdog
+// is tuned in a bounded time.  Clobbers d_tallies.
+constexpr unsigned long long kTrialSteps = 1ull << 16;  // transitions per trial packet
+
 int rddmc_batch_autotune(const rddmc_batch* b, const void* d_desc, const rddmc_run_opts* base, void* d_scratch,
                          size_t scratch_bytes, void* d_tallies, size_t tally_bytes, void* stream,
                          rddmc_run_opts* best, double* best_rate) {
@@ -520,6 +534,7 @@ int rddmc_batch_autotune(const rddmc_batch* b, const void* d_desc, const rddmc_r
         for (int ctas : {occ, std::max(1, occ - 1)}) {
             for (int ch : chunk_c) {
                 rddmc_run_opts o = *base;
+                o.max_steps = (base->max_steps && base->max_steps < kTrialSteps) ? base->max_steps : kTrialSteps;
                 o.threads_per_cta = th;
                 o.ctas_per_sm = ctas;
                 o.chunk = ch;

@@ -9,8 +9,10 @@
 // competing exponentials of eq. l_min_1/2.
 //
 // Frequency moves dominate (the core of the line, Sec. 4.2), so the fast path
-// reads only the state's 8-byte fast head {thr0, thr1 or 0}, staged in shared
-// memory: when w < thr1 the packet moves one bin down (w < thr0) or up.
+// reads only the state's 8-byte fast head {thr0, thr1 or 0} (through L1, or
+// staged in shared memory): when w < thr1 the packet moves one bin down
+// (w < thr0) or up.  A group of four transitions runs as one branch-free chain
+// of head loads, checked at its end.
 // Everything else -- spatial moves, Doppler rebins, escapes through exterior
 // faces, and frequency outcomes that are not plain moves (their head holds 0)
 // -- goes through one generic step that reads the full row (through L1) and
@@ -546,6 +548,34 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
             goto slow;                                                                    \
         }                                                                                 \
     }
+                if (!WEIGHT) {
+                    // The group's four transitions as one branch-free chain: each
+                    // head is loaded at the state the previous transition would
+                    // reach by a frequency move (index clamped, so a speculative
+                    // state past a non-move stays in bounds), then the chain is
+                    // checked.  With no branch between the loads the scheduler
+                    // fills their latency with the next group's Philox rounds.
+                    const unsigned s0 = s;
+                    const uint2 f0 = SMEM_ROWS ? fast[min(s0, nr1)] : __ldg(&fast[min(s0, nr1)]);
+                    const unsigned s1 = s0 + ((r.x >= f0.x) ? 1u : 0xffffffffu);
+                    const uint2 f1 = SMEM_ROWS ? fast[min(s1, nr1)] : __ldg(&fast[min(s1, nr1)]);
+                    const unsigned s2 = s1 + ((r.y >= f1.x) ? 1u : 0xffffffffu);
+                    const uint2 f2 = SMEM_ROWS ? fast[min(s2, nr1)] : __ldg(&fast[min(s2, nr1)]);
+                    const unsigned s3 = s2 + ((r.z >= f2.x) ? 1u : 0xffffffffu);
+                    const uint2 f3 = SMEM_ROWS ? fast[min(s3, nr1)] : __ldg(&fast[min(s3, nr1)]);
+                    const unsigned s4 = s3 + ((r.w >= f3.x) ? 1u : 0xffffffffu);
+                    const bool ok0 = r.x < f0.y, ok1 = r.y < f1.y, ok2 = r.z < f2.y, ok3 = r.w < f3.y;
+                    if (ok0 && ok1 && ok2 && ok3) {
+                        s = s4;
+                        ++g;
+                        continue;
+                    }
+                    // the first transition that is not a plain frequency move
+                    // takes the generic step from the state before it
+                    q = !ok0 ? 0u : (!ok1 ? 1u : (!ok2 ? 2u : 3u));
+                    s = !ok0 ? s0 : (!ok1 ? s1 : (!ok2 ? s2 : s3));
+                    goto slow;
+                }
                 RDDMC_FAST(r.x, 0u)
                 RDDMC_FAST(r.y, 1u)
                 RDDMC_FAST(r.z, 2u)
