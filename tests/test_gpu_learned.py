@@ -66,18 +66,37 @@ def test_network_loss_and_gradients_match_fp64_reference(proposal):
         off += o * i + o
     for s, o in offs:
         flat[s:s + o] = w_f[s:s + o]
-    lo, g_ref, g_abs = M.loss_and_grad(flat, p.n_out, p.nA, p.nB, X.float().cpu().numpy(), tA.cpu().numpy(),
-                                       tB.cpu().numpy(), p.nC, p.S, tC.cpu().numpy(), scales=True)
+    lo, g_ref = M.loss_and_grad(flat, p.n_out, p.nA, p.nB, X.float().cpu().numpy(), tA.cpu().numpy(),
+                                tB.cpu().numpy(), p.nC, p.S, tC.cpu().numpy())
     assert float(loss.item()) / Bsz == pytest.approx(lo, rel=1e-2)
-    # element by element: the device stores activations and back-propagated
-    # gradients in BF16 (relative rounding 2^-9 per stored value, compounded
-    # over up to three layers) where the FP64 network keeps them exact, so each
-    # parameter's gradient may differ by a few 2^-9 of the sum of the absolute
-    # terms it adds up; 3e-2 of that sum is the bound
-    err = np.abs(g_gpu - g_ref)
-    bound = 3e-2 * g_abs + 1e-7
+    # against the FP64 network, which keeps activations exact where the device
+    # stores BF16: storage can flip a ReLU mask, which adds terms the exact
+    # network does not have, so this comparison is per parameter block (3e-2
+    # of its norm)
+    off = 0
+    for (o, i) in M.shapes(p.n_out):
+        for size in (o * i, o):
+            a, b = g_gpu[off:off + size], g_ref[off:off + size]
+            assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-7, (off, np.linalg.norm(a - b),
+                                                                              np.linalg.norm(b))
+            off += size
+    # element by element against the FP64 reference that rounds to BF16 where
+    # the device does, with all three heads: what is left is FP32 accumulation
+    # and the rare value whose FP32 and FP64 forms straddle a BF16 rounding
+    # boundary (one BF16 step, 2^-8, of one term of a sum): every parameter
+    # within 8e-3 of the sum of the absolute terms its gradient adds up
+    layers, k = [], 0
+    for (o, i) in M.shapes(p.n_out):
+        layers.append((w_bf[k:k + o * i].reshape(o, i), w_f[k + o * i:k + o * i + o]))
+        k += o * i + o
+    lo2, g_rnd, g_abs = _device_rounded_grads(layers, X.float().cpu().numpy().astype(np.float64), tA.cpu().numpy(),
+                                              tB.cpu().numpy(), p.nA, p.nB, p.n_out, p.nC, p.S, tC.cpu().numpy())
+    assert float(loss.item()) / Bsz == pytest.approx(lo2, rel=1e-4)
+    err = np.abs(g_gpu - g_rnd)
+    bound = 8e-3 * g_abs + 1e-7
     worst = int(np.argmax(err / bound))
-    assert np.all(err <= bound), (worst, g_gpu[worst], g_ref[worst], g_abs[worst], float((err / (g_abs + 1e-30)).max()))
+    assert np.all(err <= bound), (worst, g_gpu[worst], g_rnd[worst], g_abs[worst],
+                                  float((err / (g_abs + 1e-30)).max()))
 
 
 def test_training_learns_the_first_passage_distribution(proposal):
@@ -131,10 +150,12 @@ def _bf16(x):
     return torch.tensor(np.asarray(x), dtype=torch.float32).to(torch.bfloat16).double().numpy()
 
 
-def _device_rounded_grads(layers, X, tA, tB, nA, nB, n_out):
+def _device_rounded_grads(layers, X, tA, tB, nA, nB, n_out, nC=0, S=0, tC=None):
     """Loss and gradients in FP64 with BF16 rounding exactly where the device
     stores BF16: hidden activations, the logit gradient used in products, and
     the back-propagated gradients; bias gradients sum the unrounded values.
+    Rows with a negative head-A target take no part (but count in the mean);
+    head C, when present, is a softmax over the S logits of the target's slice.
     Also returns, per parameter, the sum of the absolute terms of its gradient."""
     B = X.shape[0]
     hs = [X]
@@ -145,7 +166,13 @@ def _device_rounded_grads(layers, X, tA, tB, nA, nB, n_out):
     g = np.zeros_like(z)
     loss = 0.0
     for r in range(B):
-        for lo, hi, t in ((0, nA, tA[r]), (nA, nA + nB, nA + tB[r])):
+        if tA[r] < 0:
+            continue
+        heads = [(0, nA, tA[r]), (nA, nA + nB, nA + tB[r])]
+        if nC and tC is not None and tC[r] >= 0:
+            lo = nA + nB + (tC[r] // S) * S
+            heads.append((lo, lo + S, nA + nB + tC[r]))
+        for lo, hi, t in heads:
             zz = z[r, lo:hi]
             m = zz.max()
             lse = m + np.log(np.exp(zz - m).sum())
