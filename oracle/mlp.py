@@ -34,12 +34,8 @@ def pack(params):
     return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params])
 
 
-def loss_and_grad(flat, n_out, nA, nB, X, tA, tB, nC=0, S=0, tC=None, scales=False):
-    """Mean loss over the batch and its gradient (flat, master layout).
-
-    scales=True also returns, per parameter, the sum of the absolute values of
-    the terms its gradient adds up (|d|^T |h| for a weight, sum |d| for a bias):
-    the scale against which rounding in those terms is measured."""
+def loss_and_grad(flat, n_out, nA, nB, X, tA, tB, nC=0, S=0, tC=None):
+    """Mean loss over the batch and its gradient (flat, master layout)."""
     params = unpack(flat, n_out)
     X = np.asarray(X, dtype=np.float64)
     B = X.shape[0]
@@ -67,14 +63,10 @@ def loss_and_grad(flat, n_out, nA, nB, X, tA, tB, nC=0, S=0, tC=None, scales=Fal
             dlog[r, t] -= 1.0
     dlog /= B
     grads = [None] * 4
-    mags = [None] * 4
     d = dlog
     for l in range(3, -1, -1):
         W, b = params[l]
         grads[l] = (d.T @ acts[l], d.sum(axis=0))
-        mags[l] = (np.abs(d).T @ np.abs(acts[l]), np.abs(d).sum(axis=0))
         if l > 0:
             d = (d @ W) * (acts[l] > 0)
-    if scales:
-        return loss / B, pack(grads), pack(mags)
     return loss / B, pack(grads)

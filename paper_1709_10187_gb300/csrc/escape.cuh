@@ -20,7 +20,8 @@ struct EscapeBins {
 // parameter b = |r x n|.  Every product that meets a sum is rounded on its own
 // (__dmul_rn / __dadd_rn are never contracted into fused multiply-adds), so
 // the bins follow the arithmetic as written, whatever the compiler's
-// contraction setting, and equal the FP64 oracle's.
+// contraction setting, and equal the FP64 oracle's.  Inlined into the callers'
+// out-of-line escape functions, so the walks' hot loops carry none of it.
 struct EscapeFrame {
     int ndim, J;
     double R, vth;
@@ -29,9 +30,9 @@ struct EscapeFrame {
     const double* v;       // the cell's bulk velocity (km/s, 3 values), or null when static
 };
 
-static __device__ __noinline__ EscapeBins escape_geometry(const EscapeFrame& F, const int idx[3], unsigned bin,
-                                                          unsigned face, unsigned long long pid, unsigned long long e,
-                                                          uint32_t k0, uint32_t k1) {
+static __device__ __forceinline__ EscapeBins escape_geometry(const EscapeFrame& F, const int idx[3], unsigned bin,
+                                                             unsigned face, unsigned long long pid,
+                                                             unsigned long long e, uint32_t k0, uint32_t k1) {
     EscapeBins out;
     out.sb = -1;
     const int ax = (int)(face >> 1), side = (face & 1u) ? 1 : -1;

@@ -95,9 +95,10 @@ __device__ __forceinline__ void smem_tally(unsigned long long* s, unsigned idx) 
 }
 
 // Escape through `face` of `cell` at `bin`.  A static slab cell tallies its
-// bin; otherwise the escape geometry above decides the bins.
+// bin; otherwise the escape geometry (escape.cuh) decides the bins.  Out of
+// line: escapes are rare, and the walks' hot loops keep their registers.
 template <int NDIM>
-__device__ __forceinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cell, unsigned bin, unsigned face,
+__device__ __noinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cell, unsigned bin, unsigned face,
                                                   unsigned long long pid, unsigned long long e, bool moving) {
     if (NDIM == 1 && !moving) {
         EscapeBins out;

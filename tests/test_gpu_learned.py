@@ -84,7 +84,7 @@ def test_network_loss_and_gradients_match_fp64_reference(proposal):
     # the device does, with all three heads: what is left is FP32 accumulation
     # and the rare value whose FP32 and FP64 forms straddle a BF16 rounding
     # boundary (one BF16 step, 2^-8, of one term of a sum): every parameter
-    # within 8e-3 of the sum of the absolute terms its gradient adds up
+    # within 8e-3 of its gradient's absolute-value scale
     layers, k = [], 0
     for (o, i) in M.shapes(p.n_out):
         layers.append((w_bf[k:k + o * i].reshape(o, i), w_f[k + o * i:k + o * i + o]))
@@ -156,7 +156,9 @@ def _device_rounded_grads(layers, X, tA, tB, nA, nB, n_out, nC=0, S=0, tC=None):
     the back-propagated gradients; bias gradients sum the unrounded values.
     Rows with a negative head-A target take no part (but count in the mean);
     head C, when present, is a softmax over the S logits of the target's slice.
-    Also returns, per parameter, the sum of the absolute terms of its gradient."""
+    Also returns, per parameter, the scale of its gradient: the same backward
+    pass in absolute values (|d|, |W|, |h|), which bounds how far rounding
+    anywhere upstream can move it."""
     B = X.shape[0]
     hs = [X]
     for l, (W, b) in enumerate(layers[:3]):
@@ -180,19 +182,24 @@ def _device_rounded_grads(layers, X, tA, tB, nA, nB, n_out, nC=0, S=0, tC=None):
             g[r, lo:hi] = np.exp(zz - lse)
             g[r, t] -= 1.0
     g /= B
+    # the scale of each gradient is carried backwards in absolute values: a
+    # value that is small by cancellation inside d @ W still carries the
+    # rounding of the larger terms it cancelled
     grads = [None] * 4
     mags = [None] * 4
     gb = _bf16(g)
     grads[3] = (gb.T @ hs[3], g.sum(axis=0))
     mags[3] = (np.abs(gb).T @ np.abs(hs[3]), np.abs(g).sum(axis=0))
-    d = gb
+    d, da = gb, np.abs(gb)
     for l in (2, 1, 0):
         W_next = layers[l + 1][0]
-        df = (d @ W_next) * (hs[l + 1] > 0)
+        mask = hs[l + 1] > 0
+        df = (d @ W_next) * mask
+        dfa = (da @ np.abs(W_next)) * mask
         db = _bf16(df)
         grads[l] = (db.T @ hs[l], df.sum(axis=0))
-        mags[l] = (np.abs(db).T @ np.abs(hs[l]), np.abs(df).sum(axis=0))
-        d = db
+        mags[l] = (dfa.T @ np.abs(hs[l]), dfa.sum(axis=0))
+        d, da = db, dfa
     flat = lambda gs: np.concatenate([np.concatenate([gw.ravel(), gbias]) for gw, gbias in gs])
     return loss / B, flat(grads), flat(mags)
 
@@ -237,7 +244,7 @@ def test_network_gradients_for_narrow_and_wide_heads(n_out, nA, nB):
     # left is FP32 accumulation and the rare value that rounds to the other
     # BF16 neighbour (its FP32 and FP64 forms straddle a rounding boundary),
     # which moves one term of a sum by one BF16 step (2^-8 of it): 8e-3 of the
-    # sum of the absolute terms allows two such steps in one parameter
+    # gradient's absolute-value scale allows two such steps in one parameter
     err = np.abs(g - g_ref)
     bound = 8e-3 * g_abs + 1e-7
     worst = int(np.argmax(err / bound))

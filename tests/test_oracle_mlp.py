@@ -43,21 +43,3 @@ def test_backprop_matches_finite_differences(with_c):
             if k not in used:
                 assert b4g[k] == 0.0 and not W4g[k].any()
 
-
-def test_gradient_scales_bound_the_gradients_and_are_exact_for_one_row():
-    # the scale of a parameter is the sum of the absolute terms of its gradient:
-    # never below the gradient's magnitude, and equal to it for a one-row batch
-    # (every sum has one term)
-    rng = np.random.default_rng(4)
-    n_out, nA, nB = 32, 20, 8
-    n = sum(o * i + o for o, i in M.shapes(n_out))
-    flat = rng.normal(0, 0.3, n)
-    X = rng.normal(0, 1, (7, M.N_IN))
-    tA, tB = rng.integers(0, nA, 7), rng.integers(0, nB, 7)
-    loss, g, a = M.loss_and_grad(flat, n_out, nA, nB, X, tA, tB, scales=True)
-    l0, g0 = M.loss_and_grad(flat, n_out, nA, nB, X, tA, tB)
-    assert loss == l0 and np.array_equal(g, g0)
-    assert np.all(a >= np.abs(g) * (1 - 1e-12))
-    assert np.any(a > 1.5 * np.abs(g) + 1e-12)  # cancellation across rows
-    _, g1, a1 = M.loss_and_grad(flat, n_out, nA, nB, X[:1], tA[:1], tB[:1], scales=True)
-    assert np.allclose(a1, np.abs(g1), rtol=1e-12, atol=0)
