@@ -563,6 +563,7 @@ int rddmc_batch_autotune(const rddmc_batch* b, const void* d_desc, const rddmc_r
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != RDDMC_OK) return rc;
+    bo.max_steps = base->max_steps;  // the trials' transition cap is not the run's watchdog
     *best = bo;
     if (best_rate) *best_rate = best_r;
     return RDDMC_OK;
