@@ -366,11 +366,13 @@ def _gather_peaks(R, torch, threads=256):
     return out
 
 
-def _complete_sliced(R, torch, w, npk, slice_=1 << 24):
+def _complete_sliced(R, torch, w, npk, slice_=1 << 24, tail_packets=16_384):
     """npk packets of the workload walked to escape in step slices of slice_
     transitions (every launch short), timed with CUDA events from the first
     launch to the last packet's escape: escaped packets/s and transitions/s
-    of the completed run, its histogram, and the transitions per packet."""
+    of the completed run, its histogram, and the transitions per packet.
+    Once fewer than tail_packets are left, the launches take the walk's
+    latency fast path (identical results)."""
     prob = R.Problem(w)
     prob.ensure_state(npk)
     prob.run(min(npk, 2000), w.seed + 1, steps_per_launch=slice_)  # warm-up
@@ -378,18 +380,22 @@ def _complete_sliced(R, torch, w, npk, slice_=1 << 24):
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a0.record()
-    n = 0
+    n, left, n_lat = 0, npk, 0
     while True:
-        prob.launch(npk, w.seed, steps_per_launch=slice_, resume=1 if n else 0)
+        lat = 1 if left < tail_packets else 0
+        n_lat += lat
+        prob.launch(npk, w.seed, steps_per_launch=slice_, resume=1 if n else 0, latency=lat)
         n += 1
         t = prob.read()
-        if t["escaped"] + t["aborted"] == npk:
+        left = npk - t["escaped"] - t["aborted"]
+        if left == 0:
             break
     a1.record()
     torch.cuda.synchronize()
     dt = a0.elapsed_time(a1) / 1e3
     prob.close()
-    return {"workload": w.name, "packets": npk, "s": dt, "launches": n, "slice_transitions": slice_,
+    return {"workload": w.name, "packets": npk, "s": dt, "launches": n, "latency_launches": n_lat,
+            "slice_transitions": slice_,
             "escaped": t["escaped"], "aborted": t["aborted"], "escaped_per_s": t["escaped"] / dt,
             "transitions_per_s": t["steps"] / dt, "transitions_per_packet": t["steps"] / npk}
 
@@ -826,7 +832,7 @@ def _extras(R, torch, only=None):
             ("batched_512", lambda: _batched(R, torch)),
             ("time_grey_paper", lambda: _time_grey(R, torch)),
             ("time_slab_atau1e9_paper", lambda: _time_p2(R, torch)),
-            ("learned_bricks", lambda: _learned_bricks(R, torch)),
+            ("learned_bricks", lambda: _learned_bricks(R, torch, time_slice_us=4000)),
             ("learned_c5", lambda: _learned_c5(R, torch, tau0=1.0e7, npk=400_000, runs=4, n_ref=6_400_000,
                                                brick=8, margin=1, time_slice_us=8000))]
     if only:

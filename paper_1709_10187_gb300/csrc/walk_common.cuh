@@ -45,6 +45,7 @@ struct WalkParams {
     int n0, n01;
     double R, dz[3], vth;
     int resume, save_state, hist_in_smem, moving, hybrid;
+    int latency;              // the latency fast path (few packets left)
     int n[3];
     float a, lambda;
     int src_ncand[3], src_cand[3][2], src_nbin, src_bin[2];
