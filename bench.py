@@ -366,13 +366,11 @@ def _gather_peaks(R, torch, threads=256):
     return out
 
 
-def _complete_sliced(R, torch, w, npk, slice_=1 << 24, tail_packets=16_384):
+def _complete_sliced(R, torch, w, npk, slice_=1 << 24):
     """npk packets of the workload walked to escape in step slices of slice_
     transitions (every launch short), timed with CUDA events from the first
     launch to the last packet's escape: escaped packets/s and transitions/s
-    of the completed run, its histogram, and the transitions per packet.
-    Once fewer than tail_packets are left, the launches take the walk's
-    latency fast path (identical results)."""
+    of the completed run, and the transitions per packet."""
     prob = R.Problem(w)
     prob.ensure_state(npk)
     prob.run(min(npk, 2000), w.seed + 1, steps_per_launch=slice_)  # warm-up
@@ -380,22 +378,18 @@ def _complete_sliced(R, torch, w, npk, slice_=1 << 24, tail_packets=16_384):
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a0.record()
-    n, left, n_lat = 0, npk, 0
+    n = 0
     while True:
-        lat = 1 if left < tail_packets else 0
-        n_lat += lat
-        prob.launch(npk, w.seed, steps_per_launch=slice_, resume=1 if n else 0, latency=lat)
+        prob.launch(npk, w.seed, steps_per_launch=slice_, resume=1 if n else 0)
         n += 1
         t = prob.read()
-        left = npk - t["escaped"] - t["aborted"]
-        if left == 0:
+        if t["escaped"] + t["aborted"] == npk:
             break
     a1.record()
     torch.cuda.synchronize()
     dt = a0.elapsed_time(a1) / 1e3
     prob.close()
-    return {"workload": w.name, "packets": npk, "s": dt, "launches": n, "latency_launches": n_lat,
-            "slice_transitions": slice_,
+    return {"workload": w.name, "packets": npk, "s": dt, "launches": n, "slice_transitions": slice_,
             "escaped": t["escaped"], "aborted": t["aborted"], "escaped_per_s": t["escaped"] / dt,
             "transitions_per_s": t["steps"] / dt, "transitions_per_packet": t["steps"] / npk}
 

@@ -162,14 +162,6 @@ typedef struct rddmc_leak_params {
  *                 bin-mean opacity k_j and drawing each scattering's new bin
  *                 from the row of the packet's bin (x uniform in it, a new
  *                 isotropic direction) instead of the atom-velocity sampler.
- *   latency       0: the throughput fast path (one head load per transition).
- *                 1: for runs where few packets are left to walk (the end of a
- *                 run to completion): each group of four transitions loads
- *                 the heads of the seven states its frequency moves can reach
- *                 at once, so a lone packet waits for one load per four
- *                 transitions instead of four, at 1.75 loads per transition.
- *                 Slab and 3D DDMC tables without proposals, dust weights or
- *                 table_in_smem; ignored otherwise.  Results are identical.
  */
 typedef struct rddmc_run_opts {
     uint64_t seed;
@@ -184,8 +176,6 @@ typedef struct rddmc_run_opts {
     int32_t time_slice_us;
     const struct rddmc_proposal* proposal;
     const uint32_t* redist;
-    int32_t latency;
-    int32_t reserved;
 } rddmc_run_opts;
 
 /* Buffer sizes for a grid (from rddmc_grid_sizes). */

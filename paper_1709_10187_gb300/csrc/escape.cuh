@@ -20,8 +20,9 @@ struct EscapeBins {
 // parameter b = |r x n|.  Every product that meets a sum is rounded on its own
 // (__dmul_rn / __dadd_rn are never contracted into fused multiply-adds), so
 // the bins follow the arithmetic as written, whatever the compiler's
-// contraction setting, and equal the FP64 oracle's.  Inlined into the callers'
-// out-of-line escape functions, so the walks' hot loops carry none of it.
+// contraction setting, and equal the FP64 oracle's.  Callers keep it out of
+// their hot loops: inlined into an out-of-line escape function, or called
+// through escape_geometry_ool.
 struct EscapeFrame {
     int ndim, J;
     double R, vth;
@@ -80,6 +81,13 @@ static __device__ __forceinline__ EscapeBins escape_geometry(const EscapeFrame& 
         out.sb = k > kNsb - 1 ? kNsb - 1 : k;
     }
     return out;
+}
+
+// The same, as an out-of-line call.
+static __device__ __noinline__ EscapeBins escape_geometry_ool(const EscapeFrame& F, const int idx[3], unsigned bin,
+                                                             unsigned face, unsigned long long pid,
+                                                             unsigned long long e, uint32_t k0, uint32_t k1) {
+    return escape_geometry(F, idx, bin, face, pid, e, k0, k1);
 }
 
 }  // namespace rddmc

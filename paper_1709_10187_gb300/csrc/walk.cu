@@ -293,11 +293,7 @@ __device__ __forceinline__ bool prop_takes(const WalkParams& P, unsigned cell, u
     return l >= P.prop_llo && l <= P.prop_lhi;
 }
 
-// LAT: the latency fast path for runs where few packets are left (run option
-// `latency`): a group's four frequency moves can only reach the seven states
-// s-3 .. s+3, so their heads are loaded together and the group waits for one
-// load instead of four.
-template <int NDIM, bool SMEM_ROWS, bool HYBRID, bool PROPOSE, bool WEIGHT, bool LAT = false>
+template <int NDIM, bool SMEM_ROWS, bool HYBRID, bool PROPOSE, bool WEIGHT>
 __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const WalkParams P) {
     constexpr int RW = NDIM == 1 ? 1 : 2;  // uint4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -388,7 +384,7 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         }
         const unsigned face = o - 2u;
         if (act == ACT_ESCAPE) {
-            const EscapeBins eb = escape_bins<NDIM>(P, cell, bin, face, pid, e, (fl & FLAG_MOVING) != 0u);
+            const EscapeBins eb = escape_bins_inl<NDIM>(P, cell, bin, face, pid, e, (fl & FLAG_MOVING) != 0u);
             if (NDIM == 3 || (fl & FLAG_MOVING)) e += 5;
             if (P.hist_in_smem) smem_tally(s_hist, (unsigned)eb.hist);
             else atomicAdd(&P.tally[kHistOff + eb.hist], 1ull);
@@ -552,34 +548,6 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
             goto slow;                                                                    \
         }                                                                                 \
     }
-                if (LAT) {
-                    // heads of every state the four frequency moves can reach
-                    const int s0 = (int)s;
-                    const unsigned n1 = nr1;
-                    const uint2 hm3 = __ldg(&fast[min((unsigned)max(s0 - 3, 0), n1)]);
-                    const uint2 hm2 = __ldg(&fast[min((unsigned)max(s0 - 2, 0), n1)]);
-                    const uint2 hm1 = __ldg(&fast[min((unsigned)max(s0 - 1, 0), n1)]);
-                    const uint2 h00 = __ldg(&fast[min((unsigned)s0, n1)]);
-                    const uint2 hp1 = __ldg(&fast[min((unsigned)(s0 + 1), n1)]);
-                    const uint2 hp2 = __ldg(&fast[min((unsigned)(s0 + 2), n1)]);
-                    const uint2 hp3 = __ldg(&fast[min((unsigned)(s0 + 3), n1)]);
-                    const int d1 = (r.x >= h00.x) ? 1 : -1;
-                    const uint2 g1 = d1 > 0 ? hp1 : hm1;
-                    const int d2 = d1 + ((r.y >= g1.x) ? 1 : -1);
-                    const uint2 g2 = d2 > 0 ? hp2 : (d2 < 0 ? hm2 : h00);
-                    const int d3 = d2 + ((r.z >= g2.x) ? 1 : -1);
-                    const uint2 g3 = d3 == 3 ? hp3 : (d3 == 1 ? hp1 : (d3 == -1 ? hm1 : hm3));
-                    const int d4 = d3 + ((r.w >= g3.x) ? 1 : -1);
-                    const bool ok0 = r.x < h00.y, ok1 = r.y < g1.y, ok2 = r.z < g2.y, ok3 = r.w < g3.y;
-                    if (ok0 && ok1 && ok2 && ok3) {
-                        s = (unsigned)(s0 + d4);
-                        ++g;
-                        continue;
-                    }
-                    q = !ok0 ? 0u : (!ok1 ? 1u : (!ok2 ? 2u : 3u));
-                    s = (unsigned)(s0 + (!ok0 ? 0 : (!ok1 ? d1 : (!ok2 ? d2 : d3))));
-                    goto slow;
-                }
                 if (!WEIGHT) {
                     // The group's four transitions as one branch-free chain: each
                     // head is loaded at the state the previous transition would
@@ -692,26 +660,24 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         if (s_sb[i]) atomicAdd(&P.tally[kHistOff + nhist + i], s_sb[i]);
 }
 
-template <int NDIM, bool SMEM, bool HYBRID, bool PROPOSE, bool WEIGHT, bool LAT = false>
+template <int NDIM, bool SMEM, bool HYBRID, bool PROPOSE, bool WEIGHT>
 cudaError_t launch_variant(const WalkParams& P, int threads, size_t smem, int ctas, int nsm, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<NDIM, SMEM, HYBRID, PROPOSE, WEIGHT, LAT>,
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<NDIM, SMEM, HYBRID, PROPOSE, WEIGHT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (!ctas) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, walk_kernel<NDIM, SMEM, HYBRID, PROPOSE, WEIGHT, LAT>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, walk_kernel<NDIM, SMEM, HYBRID, PROPOSE, WEIGHT>,
                                                           threads, smem);
         if (e != cudaSuccess) return e;
     }
     if (ctas < 1) ctas = 1;
-    walk_kernel<NDIM, SMEM, HYBRID, PROPOSE, WEIGHT, LAT><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P);
+    walk_kernel<NDIM, SMEM, HYBRID, PROPOSE, WEIGHT><<<(unsigned)(ctas * nsm), threads, smem, s>>>(P);
     return cudaGetLastError();
 }
 
 template <int NDIM, bool SMEM>
 cudaError_t launch_mode(const WalkParams& P, int threads, size_t smem, int ctas, int nsm, cudaStream_t s) {
     if (NDIM == 3 && P.prop_b) return launch_variant<NDIM, SMEM, false, true, false>(P, threads, smem, ctas, nsm, s);
-    if (!SMEM && P.latency && !P.weights && !P.hybrid)
-        return launch_variant<NDIM, false, false, false, false, true>(P, threads, smem, ctas, nsm, s);
     if (P.weights) return launch_variant<NDIM, SMEM, false, false, true>(P, threads, smem, ctas, nsm, s);
     return P.hybrid ? launch_variant<NDIM, SMEM, true, false, false>(P, threads, smem, ctas, nsm, s)
                     : launch_variant<NDIM, SMEM, false, false, false>(P, threads, smem, ctas, nsm, s);
@@ -1058,7 +1024,6 @@ void fill_walk_params(const rddmc_grid& g, const WalkLaunch& w, WalkParams& P) {
     P.abs_thr = (const uint32_t*)(tb + g.off_abs);
     P.dust = g.dusty() ? 1 : 0;
     P.redist = o.redist;
-    P.latency = o.latency ? 1 : 0;
     P.wq = (const unsigned long long*)(tb + g.off_wq);
     P.weights = g.weighted() ? 1 : 0;
     P.hist_off_w = kHistOff + g.J + 2 + kNsb;

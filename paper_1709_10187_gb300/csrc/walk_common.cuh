@@ -45,7 +45,6 @@ struct WalkParams {
     int n0, n01;
     double R, dz[3], vth;
     int resume, save_state, hist_in_smem, moving, hybrid;
-    int latency;              // the latency fast path (few packets left)
     int n[3];
     float a, lambda;
     int src_ncand[3], src_cand[3][2], src_nbin, src_bin[2];
@@ -96,11 +95,14 @@ __device__ __forceinline__ void smem_tally(unsigned long long* s, unsigned idx) 
 }
 
 // Escape through `face` of `cell` at `bin`.  A static slab cell tallies its
-// bin; otherwise the escape geometry (escape.cuh) decides the bins.  Out of
-// line: escapes are rare, and the walks' hot loops keep their registers.
-template <int NDIM>
-__device__ __noinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cell, unsigned bin, unsigned face,
-                                                  unsigned long long pid, unsigned long long e, bool moving) {
+// bin; otherwise the escape geometry (escape.cuh) decides the bins.  OOL:
+// the geometry is an out-of-line call and the rest inline (the persistent
+// walk, measured faster this way); otherwise the whole function is out of
+// line (the time-dependent walk, whose hot loop keeps its registers then).
+template <int NDIM, bool OOL>
+__device__ __forceinline__ EscapeBins escape_bins_body(const WalkParams& P, unsigned cell, unsigned bin,
+                                                       unsigned face, unsigned long long pid, unsigned long long e,
+                                                       bool moving) {
     if (NDIM == 1 && !moving) {
         EscapeBins out;
         out.hist = (int)bin + 1;
@@ -112,7 +114,20 @@ __device__ __noinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cel
     idx[1] = NDIM == 3 ? (int)((cell / (unsigned)P.n0) % (unsigned)(P.n01 / P.n0)) : 0;
     idx[2] = NDIM == 3 ? (int)(cell / (unsigned)P.n01) : 0;
     const EscapeFrame F{NDIM, P.J, P.R, P.vth, P.dz, P.edges, moving ? P.cell_v + 3ull * cell : nullptr};
-    return escape_geometry(F, idx, bin, face, pid, e, P.k0, P.k1);
+    return OOL ? escape_geometry_ool(F, idx, bin, face, pid, e, P.k0, P.k1)
+               : escape_geometry(F, idx, bin, face, pid, e, P.k0, P.k1);
+}
+
+template <int NDIM>
+__device__ __noinline__ EscapeBins escape_bins(const WalkParams& P, unsigned cell, unsigned bin, unsigned face,
+                                               unsigned long long pid, unsigned long long e, bool moving) {
+    return escape_bins_body<NDIM, false>(P, cell, bin, face, pid, e, moving);
+}
+
+template <int NDIM>
+__device__ __forceinline__ EscapeBins escape_bins_inl(const WalkParams& P, unsigned cell, unsigned bin, unsigned face,
+                                                      unsigned long long pid, unsigned long long e, bool moving) {
+    return escape_bins_body<NDIM, true>(P, cell, bin, face, pid, e, moving);
 }
 
 // Parameter block of a walk launch (tables, state arrays, stream keys, source).

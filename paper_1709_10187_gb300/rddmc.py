@@ -61,8 +61,7 @@ class RunOpts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("n_packets", ctypes.c_uint64), ("max_steps", ctypes.c_uint64),
                 ("steps_per_launch", ctypes.c_uint64), ("resume", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("chunk", ctypes.c_int32), ("table_in_smem", ctypes.c_int32),
-                ("time_slice_us", ctypes.c_int32), ("proposal", ctypes.c_void_p), ("redist", ctypes.c_void_p),
-                ("latency", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("time_slice_us", ctypes.c_int32), ("proposal", ctypes.c_void_p), ("redist", ctypes.c_void_p)]
 
 
 class Sizes(ctypes.Structure):
@@ -390,11 +389,11 @@ class Problem:
 
     def launch(self, n_packets: int, seed: int, max_steps: int = 0, steps_per_launch: int = 0, resume: int = 0,
                ctas_per_sm: int = 0, threads_per_cta: int = 0, chunk: int = 0, table_in_smem: int = 0,
-               proposal: "Proposal" = None, time_slice_us: int = 0, redist=None, latency: int = 0):
+               proposal: "Proposal" = None, time_slice_us: int = 0, redist=None):
         st = self.ensure_state(n_packets)
         o = RunOpts(seed, n_packets, max_steps, steps_per_launch, resume, ctas_per_sm, threads_per_cta, chunk,
                     table_in_smem, time_slice_us, ctypes.addressof(proposal) if proposal is not None else None,
-                    redist.data_ptr() if redist is not None else None, int(latency))
+                    redist.data_ptr() if redist is not None else None)
         launch_packets(self.grid, self.table.data_ptr(), o, st.data_ptr(), st.numel(), self.tally.data_ptr(),
                        self.tally.numel() * 8, self.stream())
 
