@@ -836,8 +836,9 @@ def _extras(R, torch, only=None):
                                                           ndata=2_000_000, brick=8, margin=1, time_slice_us=8000),
                  "learned_c5_tau1e9": lambda: _learned_c5(R, torch, tau0=1.0e9, npk=5_000, runs=4, n_ref=80_000,
                                                           ndata=500_000, brick=8, margin=1, time_slice_us=8000),
-                 # the batched workload at its full size (1.1e8 packets, ~7.8e14 transitions: ~30 min)
-                 "batched_512_full": lambda: _batched(R, torch, packet_scale=1.0),
+                 # the batched workload at its full size (1.1e8 packets, ~7.8e14 transitions: ~30 min); the
+                 # watchdog (2e10 transitions, ~10x the slowest packet expected) only bounds the launch
+                 "batched_512_full": lambda: _batched(R, torch, packet_scale=1.0, max_steps=20_000_000_000),
                  # a 1e5-packet subset of the tau0 = 1e7 slab walked to escape (~5 min)
                  "c2_complete_1e5": lambda: _complete_sliced(R, torch, W.C2, 100_000),
                  # a short time-dependent run for profiling: 1e6 packets, 16 steps

@@ -13,9 +13,10 @@
 // block with K not a multiple of 64.  One elected thread issues the block's
 // tcgen05.mma instructions into a TMEM accumulator of 128 lanes x NT columns,
 // commits them to an mbarrier and waits before reusing the shared memory;
-// after the last block every warp reads its 32 lanes back with tcgen05.ld for
-// the epilogue.  Waits are bounded: a wait that runs out sets the error word
-// and the tile's outputs are left unwritten.
+// after the last block every warp reads its 32 lanes back with tcgen05.ld and
+// turns each 32 x 32 block around in shared memory, so that the epilogue's
+// stores run along rows.  Waits are bounded: a wait that runs out sets the
+// error word and the tile's outputs are left unwritten.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -207,8 +208,13 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok_s) {
-        // warp w reads TMEM lanes 32w..32w+31: thread t holds row m0 + 32w + t
-        const int row = m0 + warp * 32 + lane;
+        // warp w reads TMEM lanes 32w..32w+31 (thread t holds row m0 + 32w + t,
+        // 32 columns at a time), then turns each 32 x 32 block around through
+        // shared memory (the operand staging area, free now that the products
+        // completed; 33-float rows keep both passes free of bank conflicts) so
+        // that lane l writes column c0 + l: every store covers consecutive
+        // columns of one row
+        float* st = reinterpret_cast<float*>(sA) + warp * (32 * 33);
         for (int c0 = 0; c0 < NT; c0 += 32) {
             uint32_t v[32];
             const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
@@ -223,26 +229,30 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                 : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (row < M) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int n = n0 + c0 + j;
-                    if (c0 + j >= NT || n >= N) continue;
-                    const float x = __uint_as_float(v[j]);
-                    const size_t o = (size_t)row * ldc + n;
-                    if (EPI == RELU_BF16) {
-                        outb[o] = __float2bfloat16(fmaxf(x + bias[n], 0.0f));
-                    } else if (EPI == LINEAR_F32) {
-                        outf[o] = x + bias[n];
-                    } else if (EPI == MASK_BF16) {
-                        const float y = __bfloat162float(mask[(size_t)row * ldmask + n]) > 0.0f ? x : 0.0f;
-                        outb[o] = __float2bfloat16(y);
-                        outf[o] = y;
-                    } else {
-                        atomicAdd(&outf[o], x);
-                    }
+            for (int j = 0; j < 32; ++j) st[lane * 33 + j] = __uint_as_float(v[j]);
+            __syncwarp();
+            const int n = n0 + c0 + lane;
+            const bool col_ok = c0 + lane < NT && n < N;
+            const float b = (col_ok && (EPI == RELU_BF16 || EPI == LINEAR_F32)) ? bias[n] : 0.0f;
+            for (int r = 0; r < 32; ++r) {
+                const int row = m0 + warp * 32 + r;
+                if (row >= M || !col_ok) continue;
+                const float x = st[r * 33 + lane];
+                const size_t o = (size_t)row * ldc + n;
+                if (EPI == RELU_BF16) {
+                    outb[o] = __float2bfloat16(fmaxf(x + b, 0.0f));
+                } else if (EPI == LINEAR_F32) {
+                    outf[o] = x + b;
+                } else if (EPI == MASK_BF16) {
+                    const float y = __bfloat162float(mask[(size_t)row * ldmask + n]) > 0.0f ? x : 0.0f;
+                    outb[o] = __float2bfloat16(y);
+                    outf[o] = y;
+                } else {
+                    atomicAdd(&outf[o], x);
                 }
             }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
