@@ -826,8 +826,10 @@ def _extras(R, torch, only=None):
             ("batched_512", lambda: _batched(R, torch)),
             ("time_grey_paper", lambda: _time_grey(R, torch)),
             ("time_slab_atau1e9_paper", lambda: _time_p2(R, torch)),
-            ("learned_bricks", lambda: _learned_bricks(R, torch, time_slice_us=4000)),
-            ("learned_c5", lambda: _learned_c5(R, torch, tau0=1.0e7, npk=400_000, runs=4, n_ref=6_400_000,
+            # eight seeded runs of 2e5 packets per arm against a 1e7-packet plain reference
+            ("learned_bricks", lambda: _learned_bricks(R, torch, npk=200_000, runs=8, n_ref=10_000_000,
+                                                       time_slice_us=4000)),
+            ("learned_c5", lambda: _learned_c5(R, torch, tau0=1.0e7, npk=200_000, runs=8, n_ref=10_000_000,
                                                brick=8, margin=1, time_slice_us=8000))]
     if only:
         small = {"learned_small": lambda: _learned_bricks(R, torch, n=32, brick=8, tau0=1.0e6, npk=100_000,
@@ -836,7 +838,7 @@ def _extras(R, torch, only=None):
                                                           ndata=2_000_000, brick=8, margin=1, time_slice_us=8000),
                  "learned_c5_tau1e9": lambda: _learned_c5(R, torch, tau0=1.0e9, npk=5_000, runs=4, n_ref=80_000,
                                                           ndata=500_000, brick=8, margin=1, time_slice_us=8000),
-                 # the batched workload at its full size (1.1e8 packets, ~7.8e14 transitions: ~30 min); the
+                 # the batched workload at its full size (1.1e8 packets, ~7.8e14 transitions: ~14 min); the
                  # watchdog (2e10 transitions, ~10x the slowest packet expected) only bounds the launch
                  "batched_512_full": lambda: _batched(R, torch, packet_scale=1.0, max_steps=20_000_000_000),
                  # a 1e5-packet subset of the tau0 = 1e7 slab walked to escape (~5 min)

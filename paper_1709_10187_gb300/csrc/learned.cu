@@ -363,17 +363,13 @@ MlpWork mlp_work(void* d_work, int Bsz, int n_out) {
 // Device status of the tensor-core products (set when a bounded wait runs out).
 __device__ unsigned g_tc_err = 0;
 
-// The status word's device address, looked up once per device.
+// The status word's device address, looked up on every call (a cheap host
+// call; a cached address would go stale when the device is reset and the
+// module loaded again).
 unsigned* tc_err_ptr() {
-    static unsigned* addr[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!addr[dev]) {
-        void* a = nullptr;
-        if (cudaGetSymbolAddress(&a, g_tc_err) != cudaSuccess) return nullptr;
-        addr[dev] = (unsigned*)a;
-    }
-    return addr[dev];
+    void* a = nullptr;
+    if (cudaGetSymbolAddress(&a, g_tc_err) != cudaSuccess) return nullptr;
+    return (unsigned*)a;
 }
 
 // C = epi(A W^T (+ bias)) on tcgen05 (umma.cuh): A [M x K], W [N x K], both K

@@ -760,32 +760,52 @@ __global__ void propose_features_kernel(const WalkParams P, const float* __restr
     features(P.prop_lk[brick_of(P, cell)], P.prop_lp[j], xc[j], C, P.prop_r, fc, X + r * kFeat);
 }
 
-// Inverse-CDF draw from softmax(z[0..n)) with uniform u in (0,1).
-__device__ __forceinline__ int softmax_draw(const float* __restrict__ z, int n, float u) {
+// Inverse-CDF draw from softmax(z[0..n)) with uniform u in (0,1), by one
+// warp: every lane reads a strided share of the row (coalesced), the maximum
+// and the sum of exponentials are warp reductions (the sum broadcast from lane
+// 0 so that every lane holds the same value), and the running sum advances 32
+// entries at a time by a warp scan; the first entry whose running sum reaches
+// u times the total is drawn.  Warp-uniform result.
+__device__ __forceinline__ int softmax_draw_warp(const float* __restrict__ z, int n, float u, unsigned lane) {
     float mx = -3.0e38f;
-    for (int c = 0; c < n; ++c) mx = fmaxf(mx, z[c]);
+    for (int c = (int)lane; c < n; c += 32) mx = fmaxf(mx, z[c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
     float sum = 0.0f;
-    for (int c = 0; c < n; ++c) sum += __expf(z[c] - mx);
-    const float target = u * sum;
+    for (int c = (int)lane; c < n; c += 32) sum += __expf(z[c] - mx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+    const float target = u * __shfl_sync(FULL, sum, 0);
     float acc = 0.0f;
-    for (int c = 0; c < n; ++c) {
-        acc += __expf(z[c] - mx);
-        if (acc >= target) return c;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int c = c0 + (int)lane;
+        float v = c < n ? __expf(z[c] - mx) : 0.0f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(FULL, v, o);
+            if ((int)lane >= o) v += y;
+        }
+        const unsigned hit = __ballot_sync(FULL, c < n && acc + v >= target);
+        if (hit) return c0 + __ffs(hit) - 1;
+        acc += __shfl_sync(FULL, v, 31);
     }
     return n - 1;
 }
 
 // Sample an exit for each queued packet from its logits and place the packet
-// across the exit face; one thread per packet.  Event draws, in order: the exit
-// (face, bin) of head A, the step bucket of head B and a uniform inside it,
-// then the exit cell on the face -- one draw from head C's slice of that face
-// when nC > 0, else two uniform coordinates -- then the crossing's own draws
-// (a Doppler rebin, or the five of an escape).
+// across the exit face; one warp per packet (blockDim a multiple of 32).  The
+// warp reads the packet's logits together and every lane takes the same event
+// draws, in order: the exit (face, bin) of head A, the step bucket of head B
+// and a uniform inside it, then the exit cell on the face -- one draw from
+// head C's slice of that face when nC > 0, else two uniform coordinates --
+// then lane 0 makes the crossing with its own draws (a Doppler rebin, or the
+// five of an escape).
 __global__ void propose_place_kernel(const WalkParams P, const float* __restrict__ xc,
                                      const float* __restrict__ logits, int n_out, int nA, int nB, int nC,
                                      unsigned long long q0, unsigned long long cnt) {
-    const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= cnt) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long r = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= cnt) return;  // warp-uniform
     const unsigned J = (unsigned)P.J;
     const unsigned long long pid = P.prop_qpid[q0 + r];
     const unsigned cell = min(P.st_cell[pid], (unsigned)P.ncell - 1u);
@@ -797,9 +817,9 @@ __global__ void propose_place_kernel(const WalkParams P, const float* __restrict
     const unsigned long long e_start = es.e;
     const float* z = logits + r * (unsigned long long)n_out;
     // head A: exit face (folded frame) x exit bin
-    const int ca = softmax_draw(z, nA, es.u01());
+    const int ca = softmax_draw_warp(z, nA, es.u01(), lane);
     // head B: log2 step bucket
-    const int kb = min(softmax_draw(z + nA, nB, es.u01()), 40);
+    const int kb = min(softmax_draw_warp(z + nA, nB, es.u01(), lane), 40);
     const unsigned long long steps = (1ull << kb) + (unsigned long long)(es.u01() * (float)(1ull << kb));
     const int b = P.prop_r;  // side of the served inner cube
     const int fc_ = ca / (int)J;
@@ -810,13 +830,14 @@ __global__ void propose_place_kernel(const WalkParams P, const float* __restrict
     int q1, q2;
     if (nC > 0) {
         const int S = b * b;
-        const int pq = softmax_draw(z + nA + nB + fc_ * S, S, es.u01());
+        const int pq = softmax_draw_warp(z + nA + nB + fc_ * S, S, es.u01(), lane);
         q1 = pq % b;
         q2 = pq / b;
     } else {
         q1 = min((int)(es.u01() * (float)b), b - 1);
         q2 = min((int)(es.u01() * (float)b), b - 1);
     }
+    if (lane != 0u) return;
     int base[3], C[3], perm[3];
     bool flip[3];
     if (region) {
@@ -1175,8 +1196,8 @@ extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rdd
         if (cudaGetLastError() != cudaSuccess) return RDDMC_ERR_CUDA;
         const int rc = rddmc_mlp_forward(n_out, d_wf, d_wb, X, rows, d_work, logits, stream);
         if (rc != RDDMC_OK) return rc;
-        propose_place_kernel<<<(unsigned)((c + 127) / 128), 128, 0, s>>>(P, pr->d_xc, logits, n_out, nA, nB, nC,
-                                                                          q0, c);
+        propose_place_kernel<<<(unsigned)((c + 3) / 4), 128, 0, s>>>(P, pr->d_xc, logits, n_out, nA, nB, nC, q0,
+                                                                      c);  // a warp per packet
         if (cudaGetLastError() != cudaSuccess) return RDDMC_ERR_CUDA;
     }
     if (cudaMemsetAsync(pr->d_queue_count, 0, 8, s) != cudaSuccess) return RDDMC_ERR_CUDA;
