@@ -826,10 +826,10 @@ def _extras(R, torch, only=None):
             ("batched_512", lambda: _batched(R, torch)),
             ("time_grey_paper", lambda: _time_grey(R, torch)),
             ("time_slab_atau1e9_paper", lambda: _time_p2(R, torch)),
-            # eight seeded runs of 2e5 packets per arm against a 1e7-packet plain reference
-            ("learned_bricks", lambda: _learned_bricks(R, torch, npk=200_000, runs=8, n_ref=10_000_000,
+            # eight seeded runs of 4e5 packets per arm against a 1e7-packet plain reference
+            ("learned_bricks", lambda: _learned_bricks(R, torch, npk=400_000, runs=8, n_ref=10_000_000,
                                                        time_slice_us=4000)),
-            ("learned_c5", lambda: _learned_c5(R, torch, tau0=1.0e7, npk=200_000, runs=8, n_ref=10_000_000,
+            ("learned_c5", lambda: _learned_c5(R, torch, tau0=1.0e7, npk=400_000, runs=8, n_ref=10_000_000,
                                                brick=8, margin=1, time_slice_us=8000))]
     if only:
         small = {"learned_small": lambda: _learned_bricks(R, torch, n=32, brick=8, tau0=1.0e6, npk=100_000,
