@@ -131,6 +131,27 @@ def _cpu_sample(seconds_target=12.0, slice_=4096):
                        f"({r['steps']} transitions, {dt:.1f} s, FP64 C oracle, {cores} threads)"), dt
 
 
+def _cpu_completed():
+    """The FP64 oracle on completed packet subsets (every packet walked to
+    escape), on all host cores: C1 and the paper's two a tau0 = 1e9 slabs in
+    full, C2 and C3 on subsets.  Transitions/s and escaped packets/s, in total
+    and per core.  The batched instances are left out: their packet lengths
+    span five decades, so no bounded subset represents them."""
+    from oracle import coracle as C
+    cores = os.cpu_count() or 1
+    out = {"cores": cores, "kind": "oracle"}
+    for w, npk in ((W.C1, W.C1.packets), (W.P2, W.P2.packets), (W.P1, W.P1.packets), (W.C3, 1000), (W.C2, 100)):
+        g = C.Grid(w)
+        tb = g.table()
+        t0 = time.perf_counter()
+        r = C.walk(g, tb, w.seed, 0, npk, nthreads=cores)
+        dt = time.perf_counter() - t0
+        out[w.name] = {"packets": npk, "s": dt, "escaped": int(r["escaped"]), "transitions": int(r["steps"]),
+                       "transitions_per_s": r["steps"] / dt, "transitions_per_s_per_core": r["steps"] / dt / cores,
+                       "escaped_per_s": r["escaped"] / dt}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -323,6 +344,8 @@ def run_native(args, rank, world, local_rank):
             line["extras"] = _extras(R, torch)
     if world == 1 and not args.no_cpu_baseline:
         cb, _ = _cpu_sample()
+        if args.cpu_baseline_completed:
+            cb["completed"] = _cpu_completed()
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
 
@@ -879,6 +902,9 @@ def main():
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--table-in-smem", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-completed", action="store_true",
+                    help="also time the oracle on completed packet subsets (C1, P1, P2 in full; C2, C3 subsets; "
+                         "several minutes of host time)")
     ap.add_argument("--no-gather", action="store_true", help="skip the gather-rate probe (no gather fraction)")
     ap.add_argument("--no-complete", action="store_true",
                     help="skip the completed 1e5-packet subset (no escaped packets/s)")

@@ -235,8 +235,6 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
             const int n = n0 + c0 + lane;
             const bool col_ok = c0 + lane < NT && n < N;
             const float b = (col_ok && (EPI == RELU_BF16 || EPI == LINEAR_F32)) ? bias[n] : 0.0f;
-            // unrolled so that the mask loads of several rows are in flight together
-#pragma unroll 8
             for (int r = 0; r < 32; ++r) {
                 const int row = m0 + warp * 32 + r;
                 if (row >= M || !col_ok) continue;
