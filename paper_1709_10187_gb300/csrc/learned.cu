@@ -382,9 +382,15 @@ cudaError_t gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const 
     unsigned* err = tc_err_ptr();
     if (!err || K % 16 || N % 16 || ksplit < 1 || (ksplit > 1 && EPI != umma::F32_ADD)) return cudaErrorInvalidValue;
     const int NT = std::min(256, N);
+    // two staging areas when a split has more than one K block of 128 (the copy
+    // of the next block overlaps the products of this one)
+    const int kpanels = (K + umma::kPanel - 1) / umma::kPanel;
+    const int per_split = (kpanels + ksplit - 1) / ksplit;
+    const bool staged_k = K <= 128 && K % umma::kPanel != 0;
+    const int nstage = (!staged_k && per_split > umma::kMaxPanels) ? 2 : 1;
     // at least 80 KiB of shared memory: at most two CTAs per SM, so their TMEM
     // accumulators (<= 256 columns each) always fit the SM's 512 columns
-    const size_t smem = std::max<size_t>(umma::smem_bytes(NT), 80 * 1024);
+    const size_t smem = std::max<size_t>(umma::smem_bytes(NT, nstage), 80 * 1024);
     dim3 grid((N + NT - 1) / NT, (M + umma::kTileM - 1) / umma::kTileM, ksplit);
     CUtensorMap mapA, mapW;
     std::memset(&mapA, 0, sizeof(mapA));
@@ -397,7 +403,7 @@ cudaError_t gemm_tc(int M, int N, int K, const __nv_bfloat16* A, int lda, const 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, umma::kThreads, smem, s>>>(M, N, K, NT, A, lda, W, ldw, mapA, mapW, bias, mask, ldmask, outb, outf,
-                                            ldc, err);
+                                            ldc, nstage, err);
     return cudaGetLastError();
 }
 

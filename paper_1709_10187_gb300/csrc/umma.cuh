@@ -29,6 +29,7 @@ namespace umma {
 constexpr int kTileM = 128;
 constexpr int kThreads = 128;
 constexpr int kPanel = 64;  // BF16 per 128-byte swizzled row
+constexpr int kMaxPanels = 2;  // a K block is at most 128 wide
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -132,15 +133,18 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
                                                            const float* __restrict__ bias,
                                                            const __nv_bfloat16* __restrict__ mask, int ldmask,
                                                            __nv_bfloat16* __restrict__ outb, float* __restrict__ outf,
-                                                           int ldc, unsigned* err) {
+                                                           int ldc, int nstage, unsigned* err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int kMaxPanels = 2;  // a K block is at most 128 wide
-    unsigned char* sA = base;
-    unsigned char* sB = sA + (size_t)kMaxPanels * kTileM * 128;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + (size_t)kMaxPanels * NT * 128);
-    uint64_t* tbar = mbar + 1;
-    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(mbar + 2);
+    // nstage (1 or 2) staging areas of one K block each: A panels, then W panels
+    const size_t stage_bytes = (size_t)kMaxPanels * (kTileM + NT) * 128;
+    unsigned char* sA = base;  // stage 0's A panels (also the epilogue's scratch)
+    auto stage_a = [&](int st) { return base + (size_t)st * stage_bytes; };
+    auto stage_b = [&](int st) { return base + (size_t)st * stage_bytes + (size_t)kMaxPanels * kTileM * 128; };
+    // per stage: tbar (its TMA copy landed) and mbar (its products completed)
+    uint64_t* tbar = reinterpret_cast<uint64_t*>(base + (size_t)nstage * stage_bytes);
+    uint64_t* mbar = tbar + 2;
+    uint32_t* taddr_s = reinterpret_cast<uint32_t*>(tbar + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kTileM, n0 = blockIdx.x * NT;
@@ -157,13 +161,12 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(tbar)));
+        for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(tbar + i)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (!TMA) {  // one block: K <= 128
-        stage(A, lda, m0, kTileM, min(kTileM, M - m0), K, sA);
-        stage(W, ldw, n0, NT, min(NT, N - n0), K, sB);
+        stage(A, lda, m0, kTileM, min(kTileM, M - m0), K, stage_a(0));
+        stage(W, ldw, n0, NT, min(NT, N - n0), K, stage_b(0));
         asm volatile("fence.proxy.async.shared::cta;");  // generic-proxy stores -> tensor-core reads
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -171,32 +174,75 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *taddr_s;
 
-    // one thread stages (TMA), issues and waits, block by block; the smem of a
-    // block is reused only after its products completed
+    // One thread stages (TMA), issues and waits.  With two stages the copy of
+    // K block b+1 is issued as soon as its stage is free (the products of block
+    // b-1 completed), so it lands while block b's products run; with one stage
+    // each block is copied, multiplied and waited for in turn.  Use k of a
+    // stage completes phase k of its two mbarriers (parity k & 1); a stage is
+    // rewritten only after its previous use was waited for, so no barrier runs
+    // two phases ahead of its wait.
     __shared__ int ok_s;
     if (threadIdx.x == 0) {
         bool ok = true;
-        uint32_t phase = 0;
         if (TMA) {
-            for (int p = p_begin; p < p_end && ok; p += kMaxPanels, phase ^= 1u) {
+            const int nb = (p_end - p_begin + kMaxPanels - 1) / kMaxPanels;
+            auto issue = [&](int blk) {
+                const int st = nstage == 2 ? (blk & 1) : 0;
+                const int p = p_begin + blk * kMaxPanels;
                 const int np = min(kMaxPanels, p_end - p);
                 const uint32_t bytes = (uint32_t)(np * (kTileM + NT) * 128);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                             :: "r"(smem_u32(tbar)), "r"(bytes) : "memory");
+                             :: "r"(smem_u32(tbar + st)), "r"(bytes) : "memory");
                 for (int q = 0; q < np; ++q) {
-                    tma_load_2d(sA + (size_t)q * kTileM * 128, &mapA, (p + q) * kPanel, m0, tbar);
-                    tma_load_2d(sB + (size_t)q * NT * 128, &mapW, (p + q) * kPanel, n0, tbar);
+                    tma_load_2d(stage_a(st) + (size_t)q * kTileM * 128, &mapA, (p + q) * kPanel, m0, tbar + st);
+                    tma_load_2d(stage_b(st) + (size_t)q * NT * 128, &mapW, (p + q) * kPanel, n0, tbar + st);
                 }
-                ok = wait_parity(tbar, phase);
-                if (!ok) break;
+            };
+            int pend = 0;  // copies issued and not yet waited for
+            issue(0);
+            pend = 1;
+            int b = 0;
+            for (; b < nb; ++b) {
+                const int st = nstage == 2 ? (b & 1) : 0;
+                const uint32_t use = nstage == 2 ? (uint32_t)(b >> 1) : (uint32_t)b;
+                if (nstage == 2 && b + 1 < nb) {
+                    // stage of block b+1 last held block b-1: wait for its products
+                    if (b >= 1 && !(ok = wait_parity(mbar + ((b + 1) & 1), (uint32_t)((b - 1) >> 1) & 1u))) break;
+                    issue(b + 1);
+                    ++pend;
+                }
+                if (!(ok = wait_parity(tbar + st, use & 1u))) break;
+                --pend;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                mma_block(tmem, sA, sB, NT, 4 * np, p == p_begin);  // columns past K were zero-filled
+                const int np = min(kMaxPanels, p_end - (p_begin + b * kMaxPanels));
+                mma_block(tmem, stage_a(st), stage_b(st), NT, 4 * np, b == 0);  // columns past K were zero-filled
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(smem_u32(mbar)));
-                ok = wait_parity(mbar, phase);
+                             :: "r"(smem_u32(mbar + st)));
+                if (nstage == 1) {
+                    if (!(ok = wait_parity(mbar, use & 1u))) break;
+                    if (b + 1 < nb) {
+                        issue(b + 1);
+                        ++pend;
+                    }
+                }
+            }
+            if (ok && nstage == 2) {
+                // the last commit covers every product issued before it
+                const int bl = nb - 1;
+                ok = wait_parity(mbar + (bl & 1), (uint32_t)(bl >> 1) & 1u);
+            }
+            if (!ok) {
+                // a wait ran out: give the copies still in flight another bounded
+                // wait before the CTA leaves (their stages' next phases)
+                for (int i = 0; i < pend && i < 2; ++i) {
+                    const int blk = b + i;  // the copies of blocks b (and b+1) were issued, not waited
+                    const int st = nstage == 2 ? (blk & 1) : 0;
+                    const uint32_t use = nstage == 2 ? (uint32_t)(blk >> 1) : (uint32_t)blk;
+                    wait_parity(tbar + st, use & 1u);
+                }
             }
         } else {
-            mma_block(tmem, sA, sB, NT, K / 16, true);  // only the staged K columns
+            mma_block(tmem, stage_a(0), stage_b(0), NT, K / 16, true);  // only the staged K columns
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(mbar)));
             ok = wait_parity(mbar, 0);
@@ -216,6 +262,19 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
         // columns of one row
         float* st = reinterpret_cast<float*>(sA) + warp * (32 * 33);
         for (int c0 = 0; c0 < NT; c0 += 32) {
+            // the ReLU mask of this warp's 32 rows at column n0 + c0 + lane, loaded
+            // before the accumulator so that the 32 loads are in flight together
+            // (indices clamped into the matrix: rows and columns past it are
+            // loaded but not stored)
+            float mk[32];
+            if (EPI == MASK_BF16) {
+                const int nn = min(n0 + c0 + lane, N - 1);
+#pragma unroll
+                for (int r = 0; r < 32; ++r) {
+                    const int row = min(m0 + warp * 32 + r, M - 1);
+                    mk[r] = __bfloat162float(mask[(size_t)row * ldmask + nn]);
+                }
+            }
             uint32_t v[32];
             const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
             asm volatile(
@@ -235,6 +294,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
             const int n = n0 + c0 + lane;
             const bool col_ok = c0 + lane < NT && n < N;
             const float b = (col_ok && (EPI == RELU_BF16 || EPI == LINEAR_F32)) ? bias[n] : 0.0f;
+#pragma unroll
             for (int r = 0; r < 32; ++r) {
                 const int row = m0 + warp * 32 + r;
                 if (row >= M || !col_ok) continue;
@@ -245,7 +305,7 @@ __global__ void __launch_bounds__(kThreads) gemm_tc_kernel(int M, int N, int K, 
                 } else if (EPI == LINEAR_F32) {
                     outf[o] = x + b;
                 } else if (EPI == MASK_BF16) {
-                    const float y = __bfloat162float(mask[(size_t)row * ldmask + n]) > 0.0f ? x : 0.0f;
+                    const float y = mk[r] > 0.0f ? x : 0.0f;
                     outb[o] = __float2bfloat16(y);
                     outf[o] = y;
                 } else {
@@ -280,10 +340,11 @@ __global__ void transpose_bf16_kernel(const __nv_bfloat16* __restrict__ in, int 
     }
 }
 
-// Dynamic shared memory of a 128 x NT tile: two 64-column panels of A and W
-// (+1 KiB alignment slack, two mbarriers and the TMEM address).
-__host__ __device__ constexpr size_t smem_bytes(int nt) {
-    return 1024 + (size_t)2 * (kTileM + nt) * 128 + 64;
+// Dynamic shared memory of a 128 x NT tile with `stages` staging areas of two
+// 64-column panels of A and W each (+1 KiB alignment slack, four mbarriers and
+// the TMEM address).
+__host__ __device__ constexpr size_t smem_bytes(int nt, int stages) {
+    return 1024 + (size_t)stages * kMaxPanels * (kTileM + nt) * 128 + 64;
 }
 
 // 2D BF16 tensor map of a row-major [rows x cols] matrix with leading
