@@ -724,6 +724,20 @@ def _learned_c5(R, torch, tau0=1.0e7, npk=100_000, runs=8, n_ref=10_000_000, nda
     return out
 
 
+def _c5_plain(R, torch, n=64, J=256, x_max=256.0, tau0=1.0e7, npk=400_000, slice_=65536, warm=4):
+    """Transitions/s of the plain walk on the cell-resolution lognormal medium
+    (n^3 cells x J bins, every cell its own density and velocity): npk packets
+    in launches of slice_ transitions each, timed after `warm` launches have
+    carried the packets away from the source (_sliced_rate)."""
+    med = W.clumpy_medium(n=n, J=J, x_max=x_max, tau0=tau0, brick=1, packets=npk)
+    prob = R.Problem.clumpy(med)
+    out = {"workload": f"clumpy_cells_{n}c_{J}b_tau{tau0:.0e}", "table_bytes": int(prob.table.numel()),
+           "untimed_transitions_per_packet": warm * slice_}
+    out.update(_sliced_rate(R, torch, prob, npk, 0xC5064, slice_, warm=warm))
+    prob.close()
+    return out
+
+
 def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm=0, with_leaks=False):
     """A flash of npk packets advanced through constant time steps, one launch
     of the time-dependent walk per step (Sec. 2.3; eq. E_estimator), timed with
@@ -866,6 +880,9 @@ def _extras(R, torch, only=None):
                  "batched_512_full": lambda: _batched(R, torch, packet_scale=1.0, max_steps=20_000_000_000),
                  # a 1e5-packet subset of the tau0 = 1e7 slab walked to escape (~5 min)
                  "c2_complete_1e5": lambda: _complete_sliced(R, torch, W.C2, 100_000),
+                 # the plain walk on a 64^3-cell lognormal medium (256 bins, tau0 = 1e7, a 3 GB table): the
+                 # cell-resolution workload at a size a counter capture can hold
+                 "c5_cells_64_plain": lambda: _c5_plain(R, torch, n=64),
                  # a short time-dependent run for profiling: 1e6 packets, 16 steps
                  "time_slab_small": lambda: _time_p2(R, torch, npk=1_000_000, t_frac=0.016)}
         jobs = [(k, f) for k, f in jobs + list(small.items()) if k == only]
@@ -914,7 +931,7 @@ def main():
                     "c3_sphere_v200, c2_hybrid, c2_hybrid_grouped, c1_complete, c2_widecore_complete, batched_512, "
                     "time_grey_paper, time_slab_atau1e9_paper, learned_bricks, learned_c5; opt-in only: "
                     "learned_small, learned_c5_tau1e8, learned_c5_tau1e9, batched_512_full, c2_complete_1e5, "
-                    "time_slab_small) and print it")
+                    "time_slab_small, c5_cells_64_plain) and print it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
