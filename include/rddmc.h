@@ -411,6 +411,12 @@ typedef struct rddmc_time_step {
     int32_t chunk;          /* transitions a thread runs between refills: multiple of 4, 0 = 256 */
     int32_t threads_per_cta; /* multiple of 32, at most 256; 0 = 256 */
     int32_t ctas_per_sm;    /* 0 = occupancy limit */
+    int32_t regroup;        /* lanes still walking their packets break off, so that the lanes whose
+                               packets reached t_end take new ones, once fewer than this many of a
+                               warp's lanes are walking (packets keep their state in registers and
+                               continue; results do not change): 0 = library default (8),
+                               -1 = never, at most 32 */
+    int32_t reserved;       /* 0 */
 } rddmc_time_step;
 
 /* Bytes of the state buffer of a time-dependent run of n_packets (the

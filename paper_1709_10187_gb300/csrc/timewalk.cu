@@ -29,7 +29,12 @@
 // transitions in all.  Lanes take packets from a global cursor (one atomicAdd
 // per warp) and run at most `chunk` transitions between refills (256 by
 // default), so a lane whose packet stopped early in its step takes a new one
-// while long-running packets continue.
+// while long-running packets continue.  When fewer than `regroup` lanes of a
+// warp are still walking (8 by default), they break off after their group of
+// four, keeping packet, clock and cached blocks in registers, so that the
+// stopped lanes take new packets before the warp walks on: in thick media a
+// packet takes only a few transitions per step, and without the break a warp
+// waits for its slowest lane.
 //
 // Tallies: the path and bin estimates go to shared memory when the grid's
 // states fit (ticks as a u32 low word plus a u32 carry count, so every update
@@ -55,6 +60,7 @@ namespace {
 
 constexpr uint32_t kTicks = 1u << 31;  // ticks per time step
 constexpr size_t kSmemTallyMax = 110 * 1024;  // shared-memory budget per CTA for the per-state tallies
+constexpr int kRegroupDefault = 8;  // a warp regroups when fewer than a quarter of its lanes still walk
 
 struct TimeParams {
     const float* rk;                 // 1 / K_s per row
@@ -76,6 +82,7 @@ struct TimeParams {
     double* wbins;
     double* wpath;
     float tick_len;                  // step length / 2^31
+    int regroup;                     // lanes break off their packets when fewer than this many walk (0: never)
 };
 
 __device__ __forceinline__ uint4 time_block(unsigned long long b, uint32_t pl, uint32_t ph, const WalkParams& P) {
@@ -332,14 +339,25 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
             }
         }
         if (__all_sync(FULL, !have)) break;  // every lane is out of packets
+        // once the cursor has run dry, lanes that stop cannot take new packets
+        const bool dry = __any_sync(FULL, exhausted);
         if (!have) continue;
 
         // ---- up to `chunk` dwells: single ones up to t = 0 mod 4, then groups of four
         const unsigned long long t0 = t, e0 = e;
         const unsigned long long lim = min(t + (unsigned long long)P.chunk, P.max_steps);
         int r = 0;
+        bool cut = false;
         while (r == 0 && (t & 3ull) && t < lim) r = dwell_then_move(dwell_word(d), trans_word(t));
         while (r == 0 && t + 4ull <= lim) {
+            // Regroup: packets take different numbers of dwells to reach t_{n+1},
+            // so once fewer than `regroup` lanes are still walking, they break
+            // off (keeping their packets, blocks and clocks in registers) and the
+            // stopped lanes take new packets before the warp walks on.
+            if (T.regroup && !dry && __popc(__activemask()) < (unsigned)T.regroup) {
+                cut = true;
+                break;
+            }
             const uint4 rn = trans_block(t >> 2, pl, ph, P);
             tnc = t >> 2;
             rnc = rn;
@@ -358,7 +376,8 @@ __global__ void __launch_bounds__(256, MINB) time_kernel(const WalkParams P, con
                 if (r) break;
             }
         }
-        while (r == 0 && t < lim) r = dwell_then_move(dwell_word(d), trans_word(t));  // short chunk end
+        if (!cut)
+            while (r == 0 && t < lim) r = dwell_then_move(dwell_word(d), trans_word(t));  // short chunk end
         n_steps += t - t0;
         n_edraw += e - e0;
         if (r == 0 && t >= P.max_steps) {
@@ -503,6 +522,7 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
     if (ts->threads_per_cta < 0 || ts->threads_per_cta % 32 || ts->threads_per_cta > 256 || ts->ctas_per_sm < 0 ||
         ts->ctas_per_sm > 32 || (ts->start != 0 && ts->start != 1))
         return RDDMC_ERR_ARG;
+    if (ts->regroup < -1 || ts->regroup > 32 || ts->reserved != 0) return RDDMC_ERR_ARG;
     if ((uint64_t)g->ncell * (uint64_t)g->J > 0xffffffffull) return RDDMC_ERR_UNSUPPORTED;
     if (state_bytes < time_state_bytes_for(ts->n_packets)) return RDDMC_ERR_SIZE;
     if (tally_bytes < tally_bytes_for(g->J)) return RDDMC_ERR_SIZE;
@@ -534,6 +554,7 @@ extern "C" int rddmc_time_step_launch(const rddmc_grid* g, const void* d_table, 
     T.wbins = d_wbins;
     T.wpath = d_wpath;
     T.tick_len = (float)((ts->t_end - ts->t_begin) / (double)kTicks);
+    T.regroup = ts->regroup < 0 ? 0 : (ts->regroup ? ts->regroup : kRegroupDefault);
     double dzmin = 2.0 * g->R / g->n[0];
     for (int a = 1; a < g->ndim; ++a) dzmin = std::min(dzmin, 2.0 * g->R / g->n[a]);
     T.inv_dz = (float)(1.0 / dzmin);

@@ -101,7 +101,8 @@ class FpRegion(ctypes.Structure):
 class TimeStep(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("n_packets", ctypes.c_uint64), ("max_steps", ctypes.c_uint64),
                 ("t_begin", ctypes.c_double), ("t_end", ctypes.c_double), ("start", ctypes.c_int32),
-                ("chunk", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("chunk", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("regroup", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class RDDMCError(RuntimeError):
@@ -415,7 +416,7 @@ class Problem:
         return buf
 
     def time_run(self, n_packets: int, seed: int, t_edges, max_steps: int = 0, chunk: int = 0,
-                 threads_per_cta: int = 0, ctas_per_sm: int = 0, leaks: bool = False) -> dict:
+                 threads_per_cta: int = 0, ctas_per_sm: int = 0, leaks: bool = False, regroup: int = 0) -> dict:
         """A flash of n_packets at the source at t_edges[0], advanced through the
         steps [t_edges[n], t_edges[n+1]], one launch per step.  Returns per step
         n: bins[n, s] (packets in state s = cell * J + bin at t_edges[n+1]),
@@ -444,7 +445,7 @@ class Problem:
         self.reset()
         for n in range(nt):
             st = TimeStep(seed, n_packets, max_steps, float(te[n]), float(te[n + 1]), 1 if n == 0 else 0, chunk,
-                          threads_per_cta, ctas_per_sm)
+                          threads_per_cta, ctas_per_sm, regroup)
             time_step_launch(self.grid, self.table.data_ptr(), st, state.data_ptr(), state.numel(),
                              self.tally.data_ptr(), self.tally.numel() * 8, bins[n].data_ptr(), path[n].data_ptr(),
                              counts[n].data_ptr(), self.stream(), leak[n].data_ptr() if leaks else 0,

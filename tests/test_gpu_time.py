@@ -111,6 +111,47 @@ def test_time_step_invariants_and_launch_shape_independence():
     p.close()
 
 
+def test_regrouping_changes_no_result():
+    # A warp regroups when fewer than `regroup` lanes still walk: the others break
+    # off, keeping their packets, so that the stopped lanes take new ones.  Each
+    # packet's streams and integer clock are its own, so every integer estimate
+    # is identical whether and when warps regroup; on the resonant slab, where a
+    # packet takes a few transitions per step, regrouping happens in every launch.
+    t_diff = W.P2.atau0_nominal ** (1.0 / 3.0) * W.P2.R
+    for w, n, te in ((W.SMALL, 30_000, [0.0, 0.3, 1.0, 3.0, 10.0, 30.0]),
+                     (W.P2, 200_000, W.time_edges(1e-3 * t_diff, 8e-3 * t_diff))):
+        p = R.Problem(w)
+        ref = p.time_run(n, w.seed, te, regroup=-1, leaks=True)
+        _invariants(ref, n)
+        for rg in (0, 4, 8, 16, 24, 32):
+            r = p.time_run(n, w.seed, te, regroup=rg, leaks=True)
+            for k in ("bins", "path_ticks", "esc", "dwells", "transitions", "alive"):
+                assert np.array_equal(ref[k], r[k]), (w.name, rg, k)
+            assert np.array_equal(ref["tallies"]["hist"], r["tallies"]["hist"])
+            # the leak sums are FP64 atomics: equal up to the order of additions
+            assert np.allclose(ref["leak"], r["leak"], rtol=1e-12, atol=1e-300), (w.name, rg)
+        p.close()
+
+
+def test_regroup_argument_checked():
+    import ctypes
+    w = W.TINY
+    p = R.Problem(w)
+    n = 1000
+    st = torch.empty(R.time_state_bytes(n), dtype=torch.uint8, device=p.device)
+    buf = torch.zeros(3 * w.ncell * p.J + 5, dtype=torch.int64, device=p.device)
+    S = w.ncell * p.J
+    L = R.lib()
+    for rg, res in ((-2, 0), (33, 0), (0, 1)):
+        ts = R.TimeStep(w.seed, n, 0, 0.0, 1.0, 1, 0, 0, 0, rg, res)
+        rc = L.rddmc_time_step_launch(p.grid, p.table.data_ptr(), ctypes.byref(ts), st.data_ptr(), st.numel(),
+                                      p.tally.data_ptr(), p.tally.numel() * 8, buf.data_ptr(),
+                                      buf.data_ptr() + 8 * S, buf.data_ptr() + 16 * S, None, None, None,
+                                      p.stream())
+        assert rc == R.ERR_ARG, (rg, res, rc)
+    p.close()
+
+
 def test_watchdog_aborts_in_time_mode():
     w = W.SMALL
     n = 4000
