@@ -670,7 +670,12 @@ int rddmc_fp_region_generate(const rddmc_grid* grid, const void* d_table, const 
  * or escape tally as the face's row says), and the packet set in flight again.  Clears the queue.
  * Reads the queue's count with one synchronisation of `stream`, then enqueues
  * the work on `stream` without waiting for it (work queued after it on the
- * same stream sees its results). */
+ * same stream sees its results).
+ * Errors: RDDMC_ERR_ARG (null pointers, including the proposal's device
+ * buffers; d_table, d_state or d_work not 256-byte aligned, d_tallies not
+ * 8-byte aligned; n_packets outside [1, 2^63); head sizes or brick geometry
+ * that do not match the grid), RDDMC_ERR_TABLE (table not precomputed),
+ * RDDMC_ERR_UNSUPPORTED (not a 3D DDMC grid without dust), RDDMC_ERR_CUDA. */
 int rddmc_propose(const rddmc_grid* grid, const void* d_table, const rddmc_proposal* proposal, uint64_t seed,
                   uint64_t n_packets, void* d_state, void* d_tallies, int n_out, int nA, int nB, int nC,
                   const float* d_wf, const void* d_wb, int batch, void* d_work, uint64_t* n_served, void* stream);

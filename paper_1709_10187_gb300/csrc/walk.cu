@@ -1160,8 +1160,15 @@ extern "C" int rddmc_propose(const rddmc_grid* g, const void* d_table, const rdd
                              void* stream) {
     using namespace rddmc;
     if (!g || !d_table || !pr || !d_state || !d_tallies || !d_wf || !d_wb || !d_work) return RDDMC_ERR_ARG;
+    if (!g->precomputed) return RDDMC_ERR_TABLE;
     if (g->ndim != 3 || g->params.mode != RDDMC_MODE_DDMC || g->dusty() || g->weighted())
         return RDDMC_ERR_UNSUPPORTED;
+    // the buffers the walk with this proposal was launched on (as rddmc_launch_packets checks them)
+    if (((uintptr_t)d_table & 255u) || ((uintptr_t)d_state & 255u) || ((uintptr_t)d_tallies & 7u) ||
+        ((uintptr_t)d_work & 255u))
+        return RDDMC_ERR_ARG;
+    if (n_packets == 0 || n_packets >= (1ull << 63)) return RDDMC_ERR_ARG;
+    if (!pr->d_brick_lk || !pr->d_lp || !pr->d_xc || !pr->d_queue_count || !pr->d_queue_pid) return RDDMC_ERR_ARG;
     if (batch < 64 || batch % 64 || nA != 6 * g->J || nB < 1 || nB > 41 || nC < 0 || nA + nB + nC > n_out ||
         n_out % 16)
         return RDDMC_ERR_ARG;

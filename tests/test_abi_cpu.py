@@ -187,6 +187,30 @@ def test_noalloc_launch_checks_its_arguments_like_launch_packets():
     R.destroy_grid(g)
 
 
+def test_propose_checks_its_arguments_without_a_gpu():
+    """rddmc_propose refuses a grid without a table, null buffers (the
+    proposal's device buffers included) and misaligned ones before it touches
+    any of them; here with fake device addresses that are never dereferenced."""
+    import ctypes
+    L = R.lib()
+    fake = 1 << 20  # 256-byte aligned, never dereferenced
+    g = _grid(W.SPHERE8)
+    J = W.SPHERE8.J
+    served = ctypes.c_uint64(0)
+
+    def call(pr, table=fake, state=fake, tally=fake, work=fake, n=1000, grid=g):
+        return L.rddmc_propose(grid, table, ctypes.byref(pr), 1, n, state, tally, 6 * J + 16, 6 * J, 8, 0,
+                               fake, fake, 64, work, ctypes.byref(served), None)
+
+    full = R.Proposal(8, 0, fake, fake, fake, 0.0, 12.0, fake, fake, 1, 0, None)
+    assert call(full) == R.ERR_TABLE                       # table not precomputed
+    assert call(full, table=None) == R.ERR_ARG
+    assert call(full, state=None) == R.ERR_ARG
+    assert call(full, work=None) == R.ERR_ARG
+    assert call(full, grid=None) == R.ERR_ARG
+    R.destroy_grid(g)
+
+
 def test_gather_probe_checks_its_arguments_without_a_gpu():
     """rddmc_gather_probe rejects bad sizes before any launch."""
     import ctypes
