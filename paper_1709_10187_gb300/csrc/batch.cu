@@ -338,6 +338,16 @@ cudaError_t enqueue(const rddmc_batch* b, const BatchParams& P, const rddmc_run_
     return cudaGetLastError();
 }
 
+// The buffers of a batched launch (the same rules for a launch, a graph and the
+// autotuner's trials, checked before anything is written to them).
+int check_buffers(const rddmc_batch* b, const void* d_desc, const void* d_scratch, size_t scratch_bytes,
+                  const void* d_tallies, size_t tally_bytes) {
+    if (!b || !d_desc || !d_scratch || !d_tallies) return RDDMC_ERR_ARG;
+    if (((uintptr_t)d_desc & 255u) || ((uintptr_t)d_scratch & 7u) || ((uintptr_t)d_tallies & 7u)) return RDDMC_ERR_ARG;
+    if (scratch_bytes < 256 || tally_bytes < b->tally_words * 8ull) return RDDMC_ERR_SIZE;
+    return RDDMC_OK;
+}
+
 int check_opts(const rddmc_run_opts* o) {
     if (!o) return RDDMC_ERR_ARG;
     if (o->steps_per_launch != 0 || o->resume != 0 || o->time_slice_us != 0) return RDDMC_ERR_UNSUPPORTED;
@@ -361,7 +371,11 @@ int rddmc_batch_create(const rddmc_grid* const* grids, const void* const* d_tabl
     uint64_t tw = 0;
     for (int i = 0; i < n_inst; ++i) {
         const rddmc_grid* g = grids[i];
-        if (!g || !d_tables[i] || ((uintptr_t)d_tables[i] & 255u) || n_packets[i] == 0) { delete b; return RDDMC_ERR_ARG; }
+        if (!g || !d_tables[i] || ((uintptr_t)d_tables[i] & 255u) || n_packets[i] == 0 ||
+            n_packets[i] >= (1ull << 62) - b->off.back()) {  // global packet ids stay below 2^62
+            delete b;
+            return RDDMC_ERR_ARG;
+        }
         if (!g->precomputed) { delete b; return RDDMC_ERR_TABLE; }
         if (g->params.mode != RDDMC_MODE_DDMC || g->dusty() || g->weighted()) { delete b; return RDDMC_ERR_UNSUPPORTED; }
         const char* tb = (const char*)d_tables[i];
@@ -438,11 +452,10 @@ int rddmc_batch_upload(rddmc_batch* b, double trial_fraction, void* d_desc, size
 
 int rddmc_batch_launch(const rddmc_batch* b, const void* d_desc, const rddmc_run_opts* o, int trial, void* d_scratch,
                        size_t scratch_bytes, void* d_tallies, size_t tally_bytes, void* stream) {
-    if (!b || !d_desc || !d_scratch || !d_tallies) return RDDMC_ERR_ARG;
-    const int rc = check_opts(o);
+    int rc = check_buffers(b, d_desc, d_scratch, scratch_bytes, d_tallies, tally_bytes);
     if (rc != RDDMC_OK) return rc;
-    if (scratch_bytes < 256 || tally_bytes < b->tally_words * 8ull) return RDDMC_ERR_SIZE;
-    if (((uintptr_t)d_scratch & 7u) || ((uintptr_t)d_tallies & 7u)) return RDDMC_ERR_ARG;
+    rc = check_opts(o);
+    if (rc != RDDMC_OK) return rc;
     BatchParams P;
     fill_params(b, d_desc, trial != 0, o, d_scratch, d_tallies, P);
     return enqueue(b, P, o, (cudaStream_t)stream) == cudaSuccess ? RDDMC_OK : RDDMC_ERR_CUDA;
@@ -462,10 +475,10 @@ int rddmc_batch_graph_create(const rddmc_batch* b, const void* d_desc, const rdd
                              void** graph_exec) {
     if (!graph_exec) return RDDMC_ERR_ARG;
     *graph_exec = nullptr;
-    if (!b || !d_desc || !d_scratch || !d_tallies) return RDDMC_ERR_ARG;
-    int rc = check_opts(o);
+    int rc = check_buffers(b, d_desc, d_scratch, scratch_bytes, d_tallies, tally_bytes);
     if (rc != RDDMC_OK) return rc;
-    if (scratch_bytes < 256 || tally_bytes < b->tally_words * 8ull) return RDDMC_ERR_SIZE;
+    rc = check_opts(o);
+    if (rc != RDDMC_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (!s) return RDDMC_ERR_ARG;  // the legacy default stream cannot be captured
     BatchParams P;
@@ -518,6 +531,11 @@ int rddmc_batch_autotune(const rddmc_batch* b, const void* d_desc, const rddmc_r
                          size_t scratch_bytes, void* d_tallies, size_t tally_bytes, void* stream,
                          rddmc_run_opts* best, double* best_rate) {
     if (!b || !base || !best) return RDDMC_ERR_ARG;
+    // every trial zeroes and reads the whole tally buffer: check it first
+    int rc = check_buffers(b, d_desc, d_scratch, scratch_bytes, d_tallies, tally_bytes);
+    if (rc != RDDMC_OK) return rc;
+    rc = check_opts(base);
+    if (rc != RDDMC_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const int threads_c[] = {128, 256};
     const int chunk_c[] = {64, 256, 1024};
@@ -528,7 +546,6 @@ int rddmc_batch_autotune(const rddmc_batch* b, const void* d_desc, const rddmc_r
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return RDDMC_ERR_CUDA; }
     double best_r = -1.0;
     rddmc_run_opts bo = *base;
-    int rc = RDDMC_OK;
     for (int th : threads_c) {
         const int occ = th == 128 ? std::max(1, occ128) : std::max(1, b->default_ctas);
         for (int ctas : {occ, std::max(1, occ - 1)}) {

@@ -96,3 +96,33 @@ def test_batched_workload_subset_conserves_and_matches_oracle():
                 _same(t, C.walk(og, ot, SEED, int(off[i]), npk[i], max_steps=2_000_000))
                 checked += 1
     assert checked >= 1
+
+
+def test_batch_buffers_checked_before_any_write():
+    # the autotuner zeroes and reads the whole tally buffer in every trial, and a
+    # graph captures the launch: both check the buffers first, as a launch does
+    import ctypes
+    probs = [R.Problem(w) for w in MIX[:2]]
+    b = R.Batch(probs, NPK[:2])
+    L = R.lib()
+    nb = b.tally.numel() * 8
+    b.tally.fill_(0x5A5A)
+    torch.cuda.synchronize()
+    best = R.RunOpts()
+    rate = ctypes.c_double(0.0)
+    o = _opts()
+    rc = L.rddmc_batch_autotune(b.h, b.desc.data_ptr(), ctypes.byref(o), b.scratch.data_ptr(),
+                                b.scratch.numel() * 8, b.tally.data_ptr(), nb - 8, b.stream(), ctypes.byref(best),
+                                ctypes.byref(rate))
+    assert rc == R.ERR_SIZE
+    torch.cuda.synchronize()
+    assert bool((b.tally == 0x5A5A).all()), "a refused autotune wrote to the tally buffer"
+    side = torch.cuda.Stream()
+    ge = ctypes.c_void_p(0)
+    for scratch, tally in ((b.scratch.data_ptr() + 4, b.tally.data_ptr()), (b.scratch.data_ptr(), b.tally.data_ptr() + 4)):
+        rc = L.rddmc_batch_graph_create(b.h, b.desc.data_ptr(), ctypes.byref(o), scratch, 248, tally, nb - 8,
+                                        side.cuda_stream, ctypes.byref(ge))
+        assert rc in (R.ERR_ARG, R.ERR_SIZE) and not ge.value, rc
+    rc = L.rddmc_batch_launch(b.h, b.desc.data_ptr() + 8, ctypes.byref(o), 0, b.scratch.data_ptr(),
+                              b.scratch.numel() * 8, b.tally.data_ptr(), nb, b.stream())
+    assert rc == R.ERR_ARG
