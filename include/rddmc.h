@@ -376,7 +376,9 @@ uint64_t rddmc_redistribution_bytes(const rddmc_grid* grid);
 
 /* Fill d_redist (device, 4-byte aligned, >= rddmc_redistribution_bytes) with
  * the thresholds of eq. R_discrete.  d_table: the grid's precomputed table
- * (its bin edges are read).  n_sub in [1, 8].  Enqueues one kernel on
+ * (256-byte aligned; its bin edges are read).  A launch reads J - 1
+ * thresholds for each of the J bins of its own grid, so the buffer it is given
+ * must be the one filled for that grid.  n_sub in [1, 8].  Enqueues one kernel on
  * `stream`.  Errors: RDDMC_ERR_ARG, RDDMC_ERR_SIZE, RDDMC_ERR_TABLE,
  * RDDMC_ERR_UNSUPPORTED (n_sub (J - 1) above 25 600), RDDMC_ERR_CUDA. */
 int rddmc_precompute_redistribution(const rddmc_grid* grid, const void* d_table, int n_sub, void* d_redist,

@@ -176,7 +176,7 @@ extern "C" uint64_t rddmc_redistribution_bytes(const rddmc_grid* g) {
 extern "C" int rddmc_precompute_redistribution(const rddmc_grid* g, const void* d_table, int n_sub, void* d_redist,
                                                size_t bytes, void* stream) {
     using namespace rddmc;
-    if (!g || !d_table || !d_redist || ((uintptr_t)d_redist & 3u)) return RDDMC_ERR_ARG;
+    if (!g || !d_table || !d_redist || ((uintptr_t)d_table & 255u) || ((uintptr_t)d_redist & 3u)) return RDDMC_ERR_ARG;
     if (n_sub < 1 || n_sub > kMaxSub || g->J < 2) return RDDMC_ERR_ARG;
     if (bytes < (size_t)g->J * (size_t)(g->J - 1) * 4u) return RDDMC_ERR_SIZE;
     if (!g->precomputed) return RDDMC_ERR_TABLE;  // the bin edges are read from the table
