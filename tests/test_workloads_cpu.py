@@ -1,0 +1,52 @@
+"""The seeded input recipes match the statistics the clumpy-medium configuration
+states: a Gaussian random field with power spectrum P(k) ~ k^(-11/3), a
+lognormal density with sigma_ln = 1 and unit mean in expectation, turbulent
+velocities with sigma = 10 km/s per component, and fields held constant over
+the bricks of the stated lattice."""
+import numpy as np
+
+from paper_1709_10187_gb300 import workloads as W
+
+
+def _shell_spectrum(g):
+    n = g.shape[0]
+    p = np.abs(np.fft.fftn(g)) ** 2
+    k = np.sqrt(sum(np.meshgrid(*[np.fft.fftfreq(n) ** 2] * 3, indexing="ij")))
+    kb = np.round(k * n).astype(int)
+    num = np.bincount(kb.ravel(), weights=p.ravel())
+    cnt = np.bincount(kb.ravel())
+    shells = np.arange(len(num))
+    sel = (shells >= 2) & (shells <= n // 3) & (cnt > 0)
+    return shells[sel] / n, num[sel] / cnt[sel]
+
+
+def test_random_field_has_the_stated_spectral_slope():
+    rng = np.random.default_rng(3)
+    for slope in (-11.0 / 3.0, -2.0):
+        g = W.gaussian_random_field(64, slope, rng)
+        assert abs(g.mean()) < 1e-12 and abs(g.std() - 1.0) < 1e-12
+        k, pk = _shell_spectrum(g)
+        fit = np.polyfit(np.log(k), np.log(pk), 1)[0]
+        assert abs(fit - slope) < 0.1, (slope, fit)
+
+
+def test_clumpy_medium_statistics_and_brick_lattice():
+    med = W.clumpy_medium(n=64, J=8, x_max=8.0, brick=1, packets=1, seed=0x5EED0005)
+    ln = np.log(med.n_rel)
+    assert abs(ln.std() - 1.0) < 1e-9                      # sigma_ln = 1
+    assert abs(ln.mean() + 0.5) < 1e-9                     # mean of ln rho = -sigma_ln^2 / 2
+    assert 0.6 < med.n_rel.mean() < 1.6                    # <rho> = 1 in expectation (a steep spectrum: few modes)
+    assert np.allclose(med.v_kms.std(axis=0), 10.0, rtol=1e-9)
+    assert np.allclose(med.v_kms.mean(axis=0), 0.0, atol=1e-9)
+    # bricks of 8 cells with a boundary at cell index 3: values constant over
+    # every brick, partial bricks at the faces
+    mb = W.clumpy_medium(n=16, J=8, x_max=8.0, brick=8, offset=3, packets=1, seed=11)
+    nbx, c, sh = W.brick_lattice(16, 8, 3)
+    assert nbx == 3 and sh == 5 and c[2] == 0 and c[3] == 1 and c[10] == 1 and c[11] == 2
+    rho = mb.n_rel.reshape(16, 16, 16)  # (z, y, x), axis 0 fastest in the flat array
+    for bz in range(nbx):
+        for by in range(nbx):
+            for bx in range(nbx):
+                blk = rho[np.ix_(c == bz, c == by, c == bx)]
+                assert np.all(blk == blk.flat[0])
+    assert mb.full.sum() == 1  # only the middle brick lies wholly inside the cube
