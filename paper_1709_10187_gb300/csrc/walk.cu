@@ -421,7 +421,6 @@ __global__ void __launch_bounds__(256, RDDMC_WALK_MIN_BLOCKS) walk_kernel(const 
         }
         const unsigned ax = face >> 1;
         const unsigned stride = NDIM == 1 ? 1u : (ax == 0 ? 1u : (ax == 1 ? (unsigned)P.n0 : (unsigned)P.n01));
-        const unsigned old_cell = cell;
         cell = min((face & 1u) ? cell + stride : cell - stride, (unsigned)P.ncell - 1u);
         cls = __ldg(&P.cell_class[cell]);
         s = cls * J + nbin;
