@@ -68,6 +68,69 @@ def test_walk_matches_exact_chain(w):
     assert ch["faces"][0] == pytest.approx(0.5, abs=1e-7)
 
 
+@pytest.mark.parametrize("w", [W.SPHERE8, W.SPHERE9_V], ids=lambda w: w.name)
+def test_3d_walk_matches_exact_chain(w):
+    # three axes, the class of every entered cell, the vacuum around a sphere
+    # and (moving) Doppler rebins across faces: the exact chain's escapes per
+    # face and mean transitions; for static cells also the spectrum
+    g = C.Grid(w)
+    t = g.table()
+    ch = A.chain_solve(w, t)
+    assert ch["escape_total"] == pytest.approx(1.0, abs=1e-9)
+    r = C.walk(g, t, w.seed, 0, w.packets)
+    N = w.packets
+    assert r["emitted"] == N and r["escaped"] == N and r["aborted"] == 0
+    pf = ch["faces"][:6]
+    fz = (r["faces"][:6] - N * pf) / np.sqrt(N * pf * (1 - pf))
+    assert np.all(np.abs(fz) < 4.0), fz
+    assert np.allclose(pf, 1.0 / 6.0, atol=2e-3)  # a centred sphere: every face direction alike
+    zs = (r["steps"] / N - ch["steps_mean"]) / np.sqrt(ch["steps_var"] / N)
+    assert abs(zs) < 4.0, zs
+    if w.vmax_kms == 0.0:
+        zmax, frac, pval = A.compare_counts_to_probs(r["hist"], ch["hist"], N)
+        assert zmax < 5.0 and frac <= 0.02 and pval > 1e-3, (zmax, frac, pval)
+    else:
+        _rebins_match_chain(w, g, t, ch)
+
+
+def _rebins_match_chain(w, g, t, ch, batches=10):
+    # Faces and transitions are blind to the frequency (the sphere is symmetric
+    # under x -> -x); the rebins are not.  From the chain's expected visits v_s:
+    # rebins per packet sum_s v_s sum_{rebin faces f} p_sf, and clamped rebins
+    # per packet, where j + m_f + B leaves [0, J-1] with B = 1 at probability
+    # 1 - thr_f / 2^32 (eq. velocity-shift, reading R6).  Observed: the event
+    # draws less the source draw and the five of each 3D escape, and the clamp
+    # count; batch means over independent packet ranges for the error.
+    J, nf = w.J, 6
+    q = A.quantised_probs(t["thr"])
+    v = ch["visits"]
+    reb = np.zeros(q.shape[0])
+    clamp = np.zeros(q.shape[0])
+    for f in range(nf):
+        o = 2 + f
+        is_reb = ((t["flags"].astype(np.int64) >> (2 * o)) & 3) == A.ACT_REBIN
+        s = np.nonzero(is_reb & (q[:, o] > 0))[0]
+        c, j = np.divmod(s, J)
+        m = t["rebin_m"][c * nf + f].astype(np.int64)
+        p1 = 1.0 - t["rebin_thr"][c * nf + f].astype(np.float64) / 2.0 ** 32
+        out0 = ((j + m) < 0) | ((j + m) > J - 1)
+        out1 = ((j + m + 1) < 0) | ((j + m + 1) > J - 1)
+        reb[s] += q[s, o]
+        clamp[s] += q[s, o] * ((1.0 - p1) * out0 + p1 * out1)
+    e_reb, e_clamp = float(v @ reb), float(v @ clamp)
+    nb = w.packets // batches
+    obs_reb, obs_clamp = [], []
+    for b in range(batches):
+        rb = C.walk(g, t, w.seed, b * nb, nb)
+        obs_reb.append((rb["event_draws"] - 6 * nb) / nb)
+        obs_clamp.append(rb["clamps"] / nb)
+    for name, o, e in (("rebins", obs_reb, e_reb), ("clamps", obs_clamp, e_clamp)):
+        o = np.asarray(o)
+        z = (o.mean() - e) / (o.std(ddof=1) / np.sqrt(batches))
+        assert abs(z) < 4.0, (name, o.mean(), e, z)
+    assert e_reb > 100.0 and e_clamp > 10.0  # both are common enough to be tested
+
+
 def test_competing_exponentials_match_categorical_form():
     # eq. l_min_1/2 executed literally in FP64 (one exponential per process) must
     # agree in distribution with the categorical draw on quantised probabilities.
