@@ -70,11 +70,13 @@ def test_grey_slab_escape_fraction_has_the_closed_form(tau_a):
     assert abs(r["steps"] / n - ch["steps_mean"]) <= 5.0 * np.sqrt(ch["steps_var"] / n)
 
 
-def test_dusty_walk_follows_the_absorbing_chain():
-    w = W.SMALL.with_(packets=100_000)
-    g = C.Grid(w, dust_abs=0.3, dust_scat=2.0)
+@pytest.mark.parametrize("w,ka", [(W.SMALL.with_(packets=100_000), 0.3), (W.SPHERE8.with_(packets=40_000), 0.5)],
+                         ids=["slab", "sphere"])
+def test_dusty_walk_follows_the_absorbing_chain(w, ka):
+    g = C.Grid(w, dust_abs=ka, dust_scat=2.0)
     t = g.table()
-    assert t["thr"].shape[1] == 4 and t["rate"].shape[1] == 5
+    K = 2 + 2 * w.ndim
+    assert t["thr"].shape[1] == K and t["rate"].shape[1] == K + 1
     ch = A.chain_solve(w, t)
     n = w.packets
     r = C.walk(g, t, w.seed, 0, n)
