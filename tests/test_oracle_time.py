@@ -18,6 +18,9 @@ from oracle import coracle as C
 from paper_1709_10187_gb300 import workloads as W
 
 GREY = W.GREY101.with_(packets=100_000)
+# a 4^3 cube in a Hubble-like flow: every interior crossing rebins (eq. velocity-shift)
+MOVING_CUBE = W.Workload("cube_4c_10b_v60", 3, (4, 4, 4), 10, -10.0, 10.0, 300.0, 1.0e4, 40_000, 0x5EED0A11,
+                         vmax_kms=60.0)
 
 
 def _check_against_chain(w, t_edges, n, seed, path_slack_dt=0.0):
@@ -65,8 +68,7 @@ def test_time_walk_in_a_moving_cube_follows_the_chain():
     # flow, where every interior crossing shifts the bin, against the chain whose
     # spatial outcomes split over the rebinned bins (the same pins as the slabs:
     # occupancy per state, escapes and path per step)
-    w = W.Workload("cube_4c_10b_v60", 3, (4, 4, 4), 10, -10.0, 10.0, 300.0, 1.0e4, 40_000, 0x5EED0A11,
-                   vmax_kms=60.0)
+    w = MOVING_CUBE
     g = C.Grid(w)
     t = g.table()
     nf = 6
@@ -129,7 +131,11 @@ def test_grey_medium_diffuses_like_the_fick_gaussian():
     (W.TINY, [0.0, 0.3, 1.0, 3.0], True),
     (W.SMALL, [0.0, 1.0, 3.0, 10.0], True),
     (W.SMALL, [0.0, 1.0, 3.0, 10.0], False),
-], ids=["tiny_gradient", "small_gradient", "small_uniform"])
+    # 3D, every entered state reached through a rebin; tau0 = 50 so that
+    # leaks are common (the sums are then near normal) and packets stay out of
+    # the thin wing states, where eq. z-leakage's rate 1/(3 k dz^2) explodes
+    (MOVING_CUBE.with_(tau0=50.0), [0.0, 0.1, 0.4, 1.2], False),
+], ids=["tiny_gradient", "small_gradient", "small_uniform", "moving_cube"])
 def test_leak_optical_depths_follow_the_chain(w, t_edges, grad):
     """eq. a_estimator: per cell face and step, the summed optical depth k dl of
     the packets leaking out of and into the cell, dl the dwell that ended in
@@ -144,7 +150,7 @@ def test_leak_optical_depths_follow_the_chain(w, t_edges, grad):
     t = g.table()
     te = np.asarray(t_edges)
     _, _, _, lk, _ = A.chain_time(w, t, te, leaks=True)
-    B, m = 20, 3000
+    B, m = 20, (10_000 if w.ndim == 3 else 3000)
     runs = np.stack([C.walk_time(g, t, w.seed, b * m, m, te, leaks=True)["leak"] / m for b in range(B)])
     mean = runs.mean(axis=0)
     se = runs.std(axis=0, ddof=1) / np.sqrt(B)
