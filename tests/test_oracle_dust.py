@@ -119,19 +119,19 @@ def test_dusty_time_walk_follows_the_chain():
     assert abs(done - lost.sum()) <= 5.0 * np.sqrt(lost.sum() * (1 - lost.sum()) / n)
 
 
-@pytest.mark.parametrize("tau_a", [0.3, 20.0])
-def test_weight_method_has_the_probabilistic_escape_in_expectation(tau_a):
+@pytest.mark.parametrize("w,tau_a", [(W.SMALL.with_(packets=40_000), 0.3), (W.SMALL.with_(packets=40_000), 20.0),
+                                     (W.SPHERE8.with_(packets=20_000), 0.5)], ids=["slab_0.3", "slab_20", "sphere_0.5"])
+def test_weight_method_has_the_probabilistic_escape_in_expectation(w, tau_a):
     """The continuous method of Sec. 2.6: weights multiplied by K_s/(K_s+k_a)
     per transition (the expected exp(-k_a dl) over a dwell) give an escaped
     weight whose expectation, in total and per escape bin, is the escape
     probability of the probabilistic method (the absorbing chain); weights lie
     in [0, 1], so the standard error is at most sqrt(p/n).  At tau_a = 20 many
     packets fall below the 1e-10 elimination weight."""
-    w = W.SMALL.with_(packets=40_000)
     n = w.packets
     g = C.Grid(w, dust_abs=tau_a, dust_scat=2.0, dust_weights=True)
     t = g.table()
-    assert t["thr"].shape[1] == 3  # no absorption outcome in the weight method
+    assert t["thr"].shape[1] == 1 + 2 * w.ndim  # no absorption outcome in the weight method
     r = C.walk_weights(g, t, w.seed, 0, n)
     ch = A.chain_solve(w, C.Grid(w, dust_abs=tau_a, dust_scat=2.0).table())
     p = ch["escape_total"]
