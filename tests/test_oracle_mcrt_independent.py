@@ -100,9 +100,11 @@ def _perp_basis(nv):
 
 
 def independent_mcrt(w, n, seed):
-    """Escape histogram (J + 2 bins) and scatterings per photon of the
-    one-cell static slab w, by straightforward MCRT (the slab normal is the z
-    component of the direction)."""
+    """Escape histogram (J + 2 bins), scatterings per photon and crossings of
+    the cell faces per photon (the escape included) of the uniform static slab
+    w, by straightforward MCRT (the slab normal is the z component of the
+    direction).  Photons start uniformly in the source cells (the centre cell,
+    or the two that meet at the midplane)."""
     rng = np.random.default_rng(seed)
     a = C.damping(w.T)
     k0 = w.tau0 / w.R
@@ -113,7 +115,12 @@ def independent_mcrt(w, n, seed):
     else:  # x0 = 0 on an edge: the two bins that meet there, equally likely
         j = int(np.searchsorted(edges, 0.0))
         xlo, xhi = edges[j - 1], edges[j + 1]
-    z = w.R * (2.0 * rng.random(n) - 1.0)
+    nz = w.n[0]
+    dz = 2.0 * w.R / nz
+    half = dz / 2.0 if nz % 2 else dz
+    z = half * (2.0 * rng.random(n) - 1.0)
+    faces = -w.R + dz * np.arange(1, nz)  # interior faces
+    ncross = np.zeros(n, dtype=np.int64)
     nv = _isotropic(rng, n)
     x = xlo + (xhi - xlo) * rng.random(n)
     nscat = np.zeros(n, dtype=np.int64)
@@ -123,6 +130,9 @@ def independent_mcrt(w, n, seed):
         s = rng.exponential(1.0, alive.size) / (k0 * _voigt(a, x[alive]))
         zn = z[alive] + s * nv[alive, 2]
         out = np.abs(zn) > w.R
+        zc = np.clip(zn, -w.R, w.R)
+        lo, hi = np.minimum(z[alive], zc), np.maximum(z[alive], zc)
+        ncross[alive] += ((faces[None, :] > lo[:, None]) & (faces[None, :] < hi[:, None])).sum(axis=1) + out
         x_esc[alive[out]] = x[alive[out]]
         sc = alive[~out]
         z[sc] = zn[~out]
@@ -140,7 +150,7 @@ def independent_mcrt(w, n, seed):
         alive = sc
     j = np.searchsorted(edges, x_esc, side="right")  # 0 below the grid, J + 1 above
     hist = np.bincount(np.clip(j, 0, w.J + 1), minlength=w.J + 2)
-    return hist, nscat
+    return hist, nscat, ncross
 
 
 def _oracle_mcrt(w, n):
@@ -185,7 +195,7 @@ def test_independent_mcrt_samples_the_atom_velocity_density():
 def test_oracle_mcrt_matches_an_independent_mcrt():
     w = SLAB
     r = _oracle_mcrt(w, N)
-    hist_i, nscat = independent_mcrt(w, N, 0x1DE9)
+    hist_i, nscat, _ = independent_mcrt(w, N, 0x1DE9)
     zmax, pval = _two_sample(r["hist"], hist_i)
     assert zmax < 5.0 and pval > 1e-3, (zmax, pval)
     # the oracle counts every flight: the scatterings plus the escaping one
@@ -196,3 +206,18 @@ def test_oracle_mcrt_matches_an_independent_mcrt():
     # a test with power: photons scatter many times and most leave the source
     # bins' neighbourhood (|x| < 0.6) before escaping
     assert m_i > 20.0 and r["hist"][w.J // 2 - 3: w.J // 2 + 3].sum() < 0.3 * N
+
+
+def test_oracle_mcrt_crosses_thin_cells_like_an_independent_mcrt():
+    # four thin cells: flights cross interior faces into thin neighbours, which
+    # the oracle's MC continues (a new flight from the face, memoryless) and
+    # counts as events; photons start in the two central cells
+    w = SLAB.with_(name="thin_slab_tau10_4x60", n=(4, 1, 1), seed=0x5EED0412)
+    r = _oracle_mcrt(w, N)
+    hist_i, nscat, ncross = independent_mcrt(w, N, 0x1DEA)
+    zmax, pval = _two_sample(r["hist"], hist_i)
+    assert zmax < 5.0 and pval > 1e-3, (zmax, pval)
+    ev = nscat + ncross
+    zs = (r["mc_events"] / N - ev.mean()) / np.sqrt(2.0 * ev.var() / N)
+    assert abs(zs) < 4.0, (r["mc_events"] / N, ev.mean())
+    assert ncross.mean() > 2.0  # interior crossings happen
