@@ -738,7 +738,8 @@ def _c5_plain(R, torch, n=64, J=256, x_max=256.0, tau0=1.0e7, npk=400_000, slice
     return out
 
 
-def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm=0, with_leaks=False):
+def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm=0, with_leaks=False,
+                    compare_regroup=False):
     """A flash of npk packets advanced through constant time steps, one launch
     of the time-dependent walk per step (Sec. 2.3; eq. E_estimator), timed with
     CUDA events around all launches (a warm-up pass over the first steps runs
@@ -757,11 +758,12 @@ def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm
     nf = 2 * w.ndim
     leak = torch.zeros((nt, w.ncell * nf * 2), dtype=torch.float64, device=prob.device)
     use_leak = [False]
+    regroup = [0]  # 0: the library default; -1: warps never regroup
 
     def steps(k_end):
         for k in range(k_end):
             st = R.TimeStep(w.seed, npk, 0, float(t_edges[k]), float(t_edges[k + 1]), 1 if k == 0 else 0, chunk, 0,
-                            ctas_per_sm)
+                            ctas_per_sm, regroup[0])
             R.time_step_launch(prob.grid, prob.table.data_ptr(), st, state.data_ptr(), state.numel(),
                                prob.tally.data_ptr(), prob.tally.numel() * 8, bins[k].data_ptr(), path[k].data_ptr(),
                                counts[k].data_ptr(), s, leak[k].data_ptr() if use_leak[0] else 0)
@@ -803,6 +805,24 @@ def _time_dependent(R, torch, w, npk, t_edges, kind, marks, chunk=0, ctas_per_sm
         outward = float(np.mean(np.sign(acc[np.abs(zc) > 0.1 * w.R]) == np.sign(zc[np.abs(zc) > 0.1 * w.R])))
         out["with_leak_estimator"] = {"s": dtl, "overhead": dtl / dt - 1.0,
                                       "share_of_cells_accelerated_outward": outward}
+    if compare_regroup:
+        # the same run with warps that never regroup (rddmc_time_step.regroup =
+        # -1): the estimates are identical, only the time differs
+        b_ref, p_ref = bins.clone(), path.clone()
+        for b in (bins, path, counts):
+            b.zero_()
+        prob.reset()
+        use_leak[0] = False
+        regroup[0] = -1
+        torch.cuda.synchronize()
+        a0.record(torch.cuda.current_stream())
+        steps(nt)
+        a1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        dtr = a0.elapsed_time(a1) / 1e3
+        same = bool(torch.equal(bins, b_ref) and torch.equal(path, p_ref))
+        out["without_regrouping"] = {"s": dtr, "regrouping_speedup": dtr / dt, "estimates_identical": same}
+        regroup[0] = 0
     ks = [int(round(m / (t_edges[1] - t_edges[0]))) - 1 for m in marks]
     b = bins.cpu().numpy()
     pth = path.cpu().numpy().astype(np.float64)
@@ -847,7 +867,7 @@ def _time_p2(R, torch, npk=10_000_000, t_frac=0.32):
     t_diff = w.atau0_nominal ** (1.0 / 3.0) * w.R
     te = W.time_edges(1e-3 * t_diff, t_frac * t_diff)
     marks = [f * t_diff for f in (0.01, 0.02, 0.04, 0.08, 0.16, 0.32) if f <= t_frac + 1e-9]
-    return _time_dependent(R, torch, w, npk, te, "slab", marks, with_leaks=True)
+    return _time_dependent(R, torch, w, npk, te, "slab", marks, with_leaks=True, compare_regroup=True)
 
 
 def _extras(R, torch, only=None):
