@@ -221,3 +221,69 @@ def test_oracle_mcrt_crosses_thin_cells_like_an_independent_mcrt():
     zs = (r["mc_events"] / N - ev.mean()) / np.sqrt(2.0 * ev.var() / N)
     assert abs(zs) < 4.0, (r["mc_events"] / N, ev.mean())
     assert ncross.mean() > 2.0  # interior crossings happen
+
+
+def independent_grouped_mcrt(w, probs, kbin, n, seed):
+    """Frequency-grouped MCRT (Sec. 5.3) of the uniform static slab w: flights
+    with the bin-mean opacity kbin[j] of the photon's bin, every scattering
+    draws the new bin from row j of `probs` (eq. R_discrete) and a new
+    isotropic direction.  Returns the escape histogram over the bins (J + 2,
+    no photon leaves the grid) and the events per photon (scatterings plus
+    crossings of interior faces plus the escape)."""
+    rng = np.random.default_rng(seed)
+    nz = w.n[0]
+    dz = 2.0 * w.R / nz
+    half = dz / 2.0 if nz % 2 else dz
+    faces = -w.R + dz * np.arange(1, nz)
+    edges = w.edges()
+    j = np.full(n, int(np.searchsorted(edges, 0.0, side="right") - 1))
+    z = half * (2.0 * rng.random(n) - 1.0)
+    mu = 2.0 * rng.random(n) - 1.0
+    events = np.zeros(n, dtype=np.int64)
+    j_esc = np.empty(n, dtype=np.int64)
+    cum = np.cumsum(probs, axis=1)
+    alive = np.arange(n)
+    while alive.size:
+        s = rng.exponential(1.0, alive.size) / kbin[j[alive]]
+        zn = z[alive] + s * mu[alive]
+        out = np.abs(zn) > w.R
+        zc = np.clip(zn, -w.R, w.R)
+        lo, hi = np.minimum(z[alive], zc), np.maximum(z[alive], zc)
+        events[alive] += ((faces[None, :] > lo[:, None]) & (faces[None, :] < hi[:, None])).sum(axis=1) + 1
+        j_esc[alive[out]] = j[alive[out]]
+        sc = alive[~out]
+        z[sc] = zn[~out]
+        u = rng.random(sc.size)
+        j[sc] = np.minimum((u[:, None] >= cum[j[sc]]).sum(axis=1), w.J - 1)
+        mu[sc] = 2.0 * rng.random(sc.size) - 1.0
+        alive = sc
+    return np.bincount(j_esc + 1, minlength=w.J + 2), events
+
+
+def test_oracle_grouped_mc_matches_an_independent_grouped_mcrt():
+    # Sec. 5.3: the bin-mean opacity (here from adaptive quadrature of the exact
+    # Voigt profile over each bin) and the rows of eq. R_discrete (pinned by
+    # the scattering sampler in their own tests) drive a three-cell thin slab
+    import scipy.integrate as si
+    from oracle import analytic as A
+    w = W.Workload("grouped_slab_tau8_3x9", 1, (3, 1, 1), 9, -6.0, 6.0, 8.0, 1.0e4, N, 0x5EED0413)
+    a = C.damping(w.T)
+    edges = w.edges()
+    thr = A.redistribution_thresholds(A.redistribution_cdf(edges, a, 3))
+    g = C.Grid(w, hybrid=True, tau_ddmc=1e30, redist=thr)
+    r = _oracle_mcrt(w, N)  # without grouping: a different law
+    t = g.table()
+    rg = C.walk(g, t, w.seed, 0, N)
+    assert rg["escaped"] == N and rg["aborted"] == 0 and rg["steps"] == 0
+    kbin = np.array([w.tau0 / w.R * si.quad(lambda x: _voigt(a, x), lo, hi, epsabs=1e-13, limit=200)[0] / (hi - lo)
+                     for lo, hi in zip(edges[:-1], edges[1:])])
+    c = np.concatenate([np.zeros((w.J, 1)), thr.astype(np.float64) / 2.0 ** 32, np.ones((w.J, 1))], axis=1)
+    probs = np.diff(c, axis=1)
+    hist_i, ev = independent_grouped_mcrt(w, probs, kbin, N, 0x1DEB)
+    zmax, pval = _two_sample(rg["hist"], hist_i)
+    assert zmax < 5.0 and pval > 1e-3, (zmax, pval)
+    zs = (rg["mc_events"] / N - ev.mean()) / np.sqrt(2.0 * ev.var() / N)
+    assert abs(zs) < 4.0, (rg["mc_events"] / N, ev.mean())
+    # grouping changes the law: the continuous MC of the same slab differs
+    zmax_c, pval_c = _two_sample(r["hist"], hist_i)
+    assert pval_c < 1e-3 or ev.mean() > 1.05 * (r["mc_events"] / N) or ev.mean() < 0.95 * (r["mc_events"] / N)
