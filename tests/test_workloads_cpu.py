@@ -50,3 +50,34 @@ def test_clumpy_medium_statistics_and_brick_lattice():
                 blk = rho[np.ix_(c == bz, c == by, c == bx)]
                 assert np.all(blk == blk.flat[0])
     assert mb.full.sum() == 1  # only the middle brick lies wholly inside the cube
+
+
+def test_batched_instances_follow_their_stated_laws():
+    # 512 instances: slab or sphere with p = 1/2; tau0 log-uniform in [1e4, 1e8],
+    # T log-uniform in [1e2, 1e5] K, 32..256 cells (a sphere: the nearest cube
+    # root per axis), 128..512 bins, packets log-uniform in [1e4, 1e6]; bins at
+    # least a Doppler width wide and the grid covering 4 (a tau0)^(1/3)
+    from scipy.stats import kstest
+    ws = W.batched_instances()
+    assert len(ws) == 512
+    sph = np.array([w.sphere for w in ws])
+    assert abs(sph.mean() - 0.5) < 4.0 * np.sqrt(0.25 / 512)
+    lt = np.log10([w.tau0 for w in ws])
+    lT = np.log10([w.T for w in ws])
+    lp = np.log10([w.packets for w in ws])
+    assert lt.min() >= 4.0 and lt.max() <= 8.0 and kstest((lt - 4.0) / 4.0, "uniform").pvalue > 1e-3
+    assert lT.min() >= 2.0 and lT.max() <= 5.0 and kstest((lT - 2.0) / 3.0, "uniform").pvalue > 1e-3
+    assert lp.min() >= 4.0 - 1e-9 and lp.max() <= 6.0 + 1e-9 and kstest((lp - 4.0) / 2.0, "uniform").pvalue > 1e-3
+    for w in ws:
+        assert 128 <= w.J <= 512
+        if w.sphere:
+            assert w.ndim == 3 and w.n[0] == w.n[1] == w.n[2] and 3 <= w.n[0] <= 6  # cube roots of 32..256
+        else:
+            assert w.ndim == 1 and 32 <= w.n[0] <= 256
+        a = 4.702e-4 / np.sqrt(w.T / 1.0e4)
+        dx = (w.x_max - w.x_min) / w.J
+        assert dx >= 1.0 - 1e-12 and w.x_max >= 4.0 * (a * w.tau0) ** (1.0 / 3.0) - 1e-9
+    # the 1 % scale the default benchmark walks keeps each instance's law, scaled
+    small = W.batched_instances(packet_scale=0.01)
+    assert all(s.packets == max(1, round(0.01 * w.packets)) or abs(s.packets - 0.01 * w.packets) <= 1.0
+               for s, w in zip(small, ws))
