@@ -81,3 +81,24 @@ def test_batched_instances_follow_their_stated_laws():
     small = W.batched_instances(packet_scale=0.01)
     assert all(s.packets == max(1, round(0.01 * w.packets)) or abs(s.packets - 0.01 * w.packets) <= 1.0
                for s, w in zip(small, ws))
+
+
+def test_named_configurations_carry_their_stated_sizes():
+    from oracle import coracle as C
+    # the slab (C1, C2) and sphere (C3) configurations
+    for w, cells, bins, xm, tau0, npk in ((W.C1, (64, 1, 1), 128, 30.0, 1.0e5, 100_000),
+                                         (W.C2, (256, 1, 1), 512, 60.0, 1.0e7, 10_000_000),
+                                         (W.C3, (64, 64, 64), 128, 80.0, 1.0e7, 10_000_000)):
+        assert (w.n, w.J, w.x_max, -w.x_min, w.tau0, w.packets, w.T) == (cells, bins, xm, xm, tau0, npk, 1.0e4)
+    assert W.C3.sphere and W.C3_V20.vmax_kms == 20.0 and W.C3_V200.vmax_kms == 200.0
+    # the paper's a tau0 = 1e9, T = 10 K slab: |x| <= 2.5 (a tau0)^(1/3); Fig. 2 with
+    # dz ~ 0.01 R, dx ~ 0.05 (a tau0)^(1/3) (P1); the time-dependent test and the
+    # n_z = 101, n_x = 51 choice with dz ~ 0.02 R, dx ~ 0.1 (a tau0)^(1/3) (P2)
+    for w, dz, dx in ((W.P1, 0.01, 0.05), (W.P2, 0.02, 0.1)):
+        atau = C.damping(w.T) * w.tau0
+        assert w.T == 10.0 and abs(atau / 1.0e9 - 1.0) < 1e-5
+        s = atau ** (1.0 / 3.0)
+        assert abs(w.x_max / (2.5 * s) - 1.0) < 1e-3 and w.x_min == -w.x_max
+        assert abs((2.0 * w.R / w.n[0]) / (dz * w.R) - 1.0) < 0.02
+        assert abs(((w.x_max - w.x_min) / w.J) / (dx * s) - 1.0) < 0.02
+    assert (W.P2.n[0], W.P2.J) == (101, 51)
