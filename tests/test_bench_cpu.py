@@ -32,3 +32,27 @@ def test_equal_l1_recovers_bias_floor_and_time_ratio():
     r = bench._equal_l1(runs_b, runs_p, ref, n_ref, npk, n_boot=50)
     assert abs(r["bias_floor_learned"]["value"] - b) < 0.35 * b, (r["bias_floor_learned"], b)
     assert r["speedup_at_0.01"]["value"] == 0.0 or b < 0.01
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the reference arm (the FP64 oracle on the host cores) needs no GPU: one
+    # JSON line with the contract's keys, its own e2e block and no host copies
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "dtype",
+              "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
