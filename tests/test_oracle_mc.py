@@ -106,3 +106,18 @@ def test_hybrid_walk_conserves_packets_and_is_symmetric(w):
     f = r["faces"][: 2 * w.ndim].astype(float)
     z = (f - w.packets / len(f)) / np.sqrt(w.packets / len(f))
     assert np.all(np.abs(z) < 4.5)
+
+
+def test_optically_thin_limit_escapes_with_the_source_spectrum():
+    # tau0 -> 0: the hybrid oracle's packets leave without scattering, in the
+    # source bins (x0 = 0 is the edge between the two central bins, each
+    # chosen with probability 1/2)
+    w = W.Workload("slab_thin", 1, (16, 1, 1), 32, -8.0, 8.0, 1.0e-3, 1.0e4, 200_000, 0x5EED0811)
+    g = C.Grid(w, hybrid=True)
+    r = C.walk(g, g.table(), w.seed, 0, w.packets)
+    h = r["hist"][1:-1].astype(np.float64)
+    assert r["escaped"] == w.packets and r["steps"] == 0
+    src = h[w.J // 2 - 1] + h[w.J // 2]
+    assert src / h.sum() >= 0.995, src / h.sum()
+    z = (h[w.J // 2] - src / 2) / np.sqrt(src / 4)
+    assert abs(z) < 4.0, z
