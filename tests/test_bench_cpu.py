@@ -56,3 +56,16 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+
+
+def test_walk_counters_describe_the_current_walk_source():
+    # the bench states the walk's issue fraction and DRAM traffic from a committed
+    # ncu capture only while the walk's sources hash to the captured ones; a
+    # change to them needs a new capture (or, for a host-only change, evidence
+    # that the device code is unchanged, recorded beside the hash)
+    import json
+    import os
+    p = os.path.join(os.path.dirname(bench.__file__), "profiles", "walk_kernel_traffic.json")
+    d = json.load(open(p))
+    assert d["kernel_hash"] == bench._kernel_hash()
+    assert d["packets"] == 10_000_000 and d["slice_transitions"] == 4096
