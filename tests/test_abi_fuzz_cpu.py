@@ -52,7 +52,7 @@ DEFECTS = ["none", "none", "none", "R", "tau0", "T", "edges_repeat", "edges_nan"
            "velocity_nan", "moving_nonuniform", "mask_source"]
 
 
-@settings(max_examples=500, deadline=None)
+@settings(max_examples=500, deadline=None, derandomize=True, database=None)
 @given(st.data())
 def test_build_grid_accepts_exactly_the_valid_descriptions(data):
     # a valid description with at most one defect; the expected status is
